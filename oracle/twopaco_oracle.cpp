@@ -1,0 +1,400 @@
+/*
+ * CPU oracle for TwoPaCo junction detection (arXiv 1602.05856).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing on the product path links, loads or calls
+ * this file: only the tests, the smoke check and the benchmark's CPU-baseline
+ * leg do. It shares no code, header, table or constant with the CUDA library;
+ * the two meet only in the seeded input generator.
+ *
+ * It is deliberately plain and slow: every k-mer is rebuilt from scratch at
+ * every position, sets are std::unordered_map / std::unordered_set, and every
+ * loop follows the text it cites.
+ *
+ * Entry points (extern "C", loaded with ctypes):
+ *
+ *   oracle_junctions   The definition of J(S, k): a vertex of G(S, k) is a
+ *                      junction iff it is a bifurcation (more than one
+ *                      distinct in-edge or out-edge) or a sentinel (first or
+ *                      last k-mer of an input string) -- section
+ *                      "Preliminaries". With both_strands the graph is the
+ *                      comprehensive graph G(s) U G(s-bar) and every k-mer is
+ *                      stored in its normalized form, the lexicographically
+ *                      smaller of itself and its reverse complement (the
+ *                      reverse-complement paragraph after Algorithm 2).
+ *                      PINNED by the tests against the Fig. 1 example, a
+ *                      brute-force explicit-graph compactor and invariants.
+ *
+ *   oracle_alg1_exact  Algorithm 1 (Filter-Junctions) run naively: E is an
+ *                      exact set of normalized (k+1)-mers. With every position
+ *                      marked it must return J(S, k) (section "Single Round
+ *                      Algorithm"). PINNED by equality with the definition
+ *                      and by the brute-force compactor.
+ *
+ *   oracle_pass1       The first pass of Algorithm 2 with the vertex-keyed
+ *                      split-block Bloom filter that the CUDA library uses as
+ *                      E, restated here from its written specification (see
+ *                      pass1_* below). It reproduces the candidate set C_temp
+ *                      bit for bit. PINNED by invariants only: C_temp
+ *                      contains J, is a candidate set (all occurrences of a
+ *                      k-mer agree), and equals J when the filter has no
+ *                      collisions; the exact bit layout is a design choice of
+ *                      this project, not the paper's.
+ *
+ * Conventions shared with the library (stated, not shared as code):
+ *   bases A,C,G,T (either case) are 0,1,2,3; a k-mer is the integer with its
+ *   first base most significant, so integer order is lexicographic order and
+ *   the complement of base x is 3 - x. Positions are 0-based k-mer starts:
+ *   i in [0, |s| - k]. Strings are never joined.
+ */
+#include <cstdint>
+#include <cstring>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+typedef unsigned __int128 u128;
+
+namespace {
+
+enum { ORACLE_OK = 0, ORACLE_EINVAL = -1, ORACLE_EBADBASE = -2 };
+
+int base_code(uint8_t c) {
+  switch (c) {
+    case 'A': case 'a': return 0;
+    case 'C': case 'c': return 1;
+    case 'G': case 'g': return 2;
+    case 'T': case 't': return 3;
+    default: return -1;
+  }
+}
+
+struct KmerHash {
+  size_t operator()(u128 x) const {
+    uint64_t lo = (uint64_t)x, hi = (uint64_t)(x >> 64);
+    return std::hash<uint64_t>()(lo ^ (lo >> 31) ^ (hi * 0x9E3779B97F4A7C15ull));
+  }
+};
+
+// The string of length len starting at codes[start], as an integer.
+u128 word_at(const std::vector<uint8_t>& codes, uint64_t start, int len) {
+  u128 x = 0;
+  for (int j = 0; j < len; ++j) x = (x << 2) | codes[start + j];
+  return x;
+}
+
+// Reverse complement of a len-base word: read backwards, complement each base.
+u128 reverse_complement(u128 x, int len) {
+  u128 y = 0;
+  for (int j = 0; j < len; ++j) {
+    y = (y << 2) | (u128)(3 - (int)(x & 3));
+    x >>= 2;
+  }
+  return y;
+}
+
+// Normalized form (reverse-complement paragraph after Algorithm 2).
+u128 normalized(u128 x, int len, int both_strands) {
+  if (!both_strands) return x;
+  u128 r = reverse_complement(x, len);
+  return r < x ? r : x;
+}
+
+int encode_all(const uint8_t* seq, uint64_t m, std::vector<uint8_t>* codes) {
+  codes->resize(m);
+  for (uint64_t g = 0; g < m; ++g) {
+    int c = base_code(seq[g]);
+    if (c < 0) return ORACLE_EBADBASE;
+    (*codes)[g] = (uint8_t)c;
+  }
+  return ORACLE_OK;
+}
+
+int popcount4(uint8_t x) { return (x & 1) + ((x >> 1) & 1) + ((x >> 2) & 1) + ((x >> 3) & 1); }
+
+struct Degrees {
+  uint8_t in = 0;   // bit c set: edge c.v exists
+  uint8_t out = 0;  // bit c set: edge v.c exists
+};
+
+}  // namespace
+
+extern "C" {
+
+/*
+ * J(S, k) by definition ("Preliminaries"; normalized forms per the
+ * reverse-complement paragraph after Algorithm 2).
+ *   seq      all strings concatenated (ASCII, m = offsets[n] bytes)
+ *   offsets  n + 1 entries; string t is seq[offsets[t] .. offsets[t+1])
+ *   flags    m bytes, written: flags[g] = 1 iff the k-mer starting at
+ *            global byte g is a junction (0 where no k-mer starts)
+ *   n_distinct  optional: number of distinct (normalized) k-mers
+ */
+int oracle_junctions(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
+                     int both_strands, uint8_t* flags, uint64_t* n_distinct) {
+  if (k < 1 || k > 63) return ORACLE_EINVAL;
+  const uint64_t m = offsets[n];
+  std::vector<uint8_t> codes;
+  int rc = encode_all(seq, m, &codes);
+  if (rc) return rc;
+  std::memset(flags, 0, m);
+
+  // Step 1-2: every occurrence contributes the edges that enter and leave
+  // its k-mer, in the orientation of the normalized form.
+  std::unordered_map<u128, Degrees, KmerHash> deg;
+  std::unordered_set<u128, KmerHash> sentinels;
+  for (uint64_t t = 0; t < n; ++t) {
+    const uint64_t s0 = offsets[t], len = offsets[t + 1] - offsets[t];
+    if (len < (uint64_t)k) continue;
+    for (uint64_t i = 0; i + k <= len; ++i) {
+      u128 v = word_at(codes, s0 + i, k);
+      u128 r = both_strands ? reverse_complement(v, k) : v;
+      u128 key = (both_strands && r < v) ? r : v;
+      Degrees& d = deg[key];
+      const bool has_pred = i >= 1, has_succ = i + k < len;
+      if (key == v) {  // forward occurrence of the normalized k-mer
+        if (has_pred) d.in |= (uint8_t)(1u << codes[s0 + i - 1]);
+        if (has_succ) d.out |= (uint8_t)(1u << codes[s0 + i + k]);
+      }
+      if (both_strands && key == r) {  // occurrence on the other strand
+        if (has_succ) d.in |= (uint8_t)(1u << (3 - codes[s0 + i + k]));
+        if (has_pred) d.out |= (uint8_t)(1u << (3 - codes[s0 + i - 1]));
+      }
+    }
+    // Step 3: first and last k-mer of the string are sentinels.
+    sentinels.insert(normalized(word_at(codes, s0, k), k, both_strands));
+    sentinels.insert(normalized(word_at(codes, s0 + len - k, k), k, both_strands));
+  }
+  // Step 4: junction = sentinel or bifurcation.
+  for (uint64_t t = 0; t < n; ++t) {
+    const uint64_t s0 = offsets[t], len = offsets[t + 1] - offsets[t];
+    if (len < (uint64_t)k) continue;
+    for (uint64_t i = 0; i + k <= len; ++i) {
+      u128 key = normalized(word_at(codes, s0 + i, k), k, both_strands);
+      const Degrees& d = deg[key];
+      bool junction = sentinels.count(key) || popcount4(d.in) > 1 || popcount4(d.out) > 1;
+      flags[s0 + i] = junction ? 1 : 0;
+    }
+  }
+  if (n_distinct) *n_distinct = deg.size();
+  return ORACLE_OK;
+}
+
+/*
+ * Algorithm 1 (Filter-Junctions) with E an exact set of normalized
+ * (k+1)-mers. marks (m bytes) is C on entry and the reduced C on exit.
+ * Loop bounds follow the 0-based reading 1 <= i < |s| - k, which leaves
+ * the two sentinel positions 0 and |s| - k untouched (they stay as given).
+ * The sentinel test is on the k-mer, not the position.
+ */
+int oracle_alg1_exact(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
+                      int both_strands, uint8_t* marks) {
+  if (k < 1 || k > 63) return ORACLE_EINVAL;
+  const uint64_t m = offsets[n];
+  std::vector<uint8_t> codes;
+  int rc = encode_all(seq, m, &codes);
+  if (rc) return rc;
+  std::unordered_set<u128, KmerHash> E, sentinels;
+  for (uint64_t t = 0; t < n; ++t) {
+    const uint64_t s0 = offsets[t], len = offsets[t + 1] - offsets[t];
+    if (len < (uint64_t)k) continue;
+    sentinels.insert(normalized(word_at(codes, s0, k), k, both_strands));
+    sentinels.insert(normalized(word_at(codes, s0 + len - k, k), k, both_strands));
+  }
+  // Loop 1: insert the two (k+1)-mers that contain the k-mer at i.
+  for (uint64_t t = 0; t < n; ++t) {
+    const uint64_t s0 = offsets[t], len = offsets[t + 1] - offsets[t];
+    for (uint64_t i = 1; i + k < len; ++i) {
+      if (!marks[s0 + i]) continue;
+      E.insert(normalized(word_at(codes, s0 + i, k + 1), k + 1, both_strands));
+      E.insert(normalized(word_at(codes, s0 + i - 1, k + 1), k + 1, both_strands));
+    }
+  }
+  // Loop 2: count existing edges around every marked non-sentinel k-mer.
+  for (uint64_t t = 0; t < n; ++t) {
+    const uint64_t s0 = offsets[t], len = offsets[t + 1] - offsets[t];
+    for (uint64_t i = 1; i + k < len; ++i) {
+      if (!marks[s0 + i]) continue;
+      u128 v = word_at(codes, s0 + i, k);
+      if (sentinels.count(normalized(v, k, both_strands))) continue;
+      int in = 0, out = 0;
+      for (int c = 0; c < 4; ++c) {
+        u128 vc = (v << 2) | (u128)c;                    // v . c
+        u128 cv = ((u128)c << (2 * k)) | v;              // c . v
+        if (E.count(normalized(vc, k + 1, both_strands))) ++out;
+        if (E.count(normalized(cv, k + 1, both_strands))) ++in;
+      }
+      if (in == 1 && out == 1) marks[s0 + i] = 0;
+    }
+  }
+  return ORACLE_OK;
+}
+
+/* ---------------------------------------------------------------------------
+ * First pass with the vertex-keyed split-block Bloom filter.
+ *
+ * Specification (restated independently by the CUDA library):
+ *   mix64(z)  = splitmix64 finalizer (Steele, Lea & Flood 2014):
+ *               z ^= z >> 30; z *= 0xbf58476d1ce4e5b9;
+ *               z ^= z >> 27; z *= 0x94d049bb133111eb; z ^= z >> 31.
+ *   V = hi * 2^64 + lo, the normalized k-mer.
+ *   H = mix64(lo ^ mix64(hi));  G = mix64(H ^ 0x9e3779b97f4a7c15)
+ *   The filter has b bits = b/256 blocks of eight 32-bit words.
+ *   block = H >> (64 - log2(b/256))  (0 when b = 256)
+ *   o     = (G >> 61) & 6           first word used (even)
+ *   word t = (o + u) & 7 for u < h; base_t = (uint32(G) * SALT[t]) >> 27
+ *   SALT[t] = first 32 bits of the fractional part of the cube root of the
+ *            (t+1)-th prime, forced odd.
+ *   item j sets / tests bit (base_t + j) & 31 in each of those h words.
+ *   items: j = 4a + c for the (predecessor a, successor c) pair of an
+ *          occurrence read in the orientation of the normalized form
+ *          (palindromes: both orientations); j = 16 marks a sentinel.
+ *   round class: bin = H & (q - 1); a position is active iff its bin is in
+ *          [bin_lo, bin_hi).
+ *   Loop 1: every active position inserts item 16 if it is the first or
+ *          last k-mer of its string, else its pair item(s).
+ *   Loop 2: an active position stays marked iff it is a sentinel position,
+ *          or item 16 is present, or at least two pair items are present.
+ * ------------------------------------------------------------------------- */
+namespace {
+
+uint64_t mix64(uint64_t z) {
+  z ^= z >> 30;
+  z *= 0xbf58476d1ce4e5b9ull;
+  z ^= z >> 27;
+  z *= 0x94d049bb133111ebull;
+  z ^= z >> 31;
+  return z;
+}
+
+const uint32_t kSalt[8] = {0x428a2f99u, 0x71374491u, 0xb5c0fbcfu, 0xe9b5dba5u,
+                           0x3956c25bu, 0x59f111f1u, 0x923f82a5u, 0xab1c5ed5u};
+
+struct FilterSpot {
+  uint64_t block;
+  uint64_t H;
+  uint32_t word[8];  // word index t for u < h
+  uint32_t base[8];  // bit base for that word
+};
+
+FilterSpot locate(u128 V, int lg_blocks, int h) {
+  FilterSpot f;
+  uint64_t lo = (uint64_t)V, hi = (uint64_t)(V >> 64);
+  f.H = mix64(lo ^ mix64(hi));
+  uint64_t G = mix64(f.H ^ 0x9e3779b97f4a7c15ull);
+  f.block = lg_blocks ? (f.H >> (64 - lg_blocks)) : 0;
+  uint32_t o = (uint32_t)((G >> 61) & 6);
+  for (int u = 0; u < h; ++u) {
+    uint32_t t = (o + (uint32_t)u) & 7u;
+    f.word[u] = t;
+    f.base[u] = ((uint32_t)G * kSalt[t]) >> 27;
+  }
+  return f;
+}
+
+void filter_insert(std::vector<uint32_t>& F, const FilterSpot& f, int h, int item) {
+  for (int u = 0; u < h; ++u)
+    F[f.block * 8 + f.word[u]] |= 1u << ((f.base[u] + (uint32_t)item) & 31u);
+}
+
+bool filter_has(const std::vector<uint32_t>& F, const FilterSpot& f, int h, int item) {
+  for (int u = 0; u < h; ++u)
+    if (!((F[f.block * 8 + f.word[u]] >> ((f.base[u] + (uint32_t)item) & 31u)) & 1u)) return false;
+  return true;
+}
+
+}  // namespace
+
+/*
+ * marks: m bytes, written: 1 where the position is active and survives the
+ * first pass, else 0. counters (optional, 2 entries): active positions,
+ * surviving positions.
+ */
+int oracle_pass1(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
+                 int both_strands, uint64_t filter_bits, int hashes, uint64_t q,
+                 uint64_t bin_lo, uint64_t bin_hi, uint8_t* marks, uint64_t* counters) {
+  if (k < 1 || k > 63 || hashes < 1 || hashes > 8) return ORACLE_EINVAL;
+  if (filter_bits < 256 || (filter_bits & (filter_bits - 1))) return ORACLE_EINVAL;
+  if (q < 1 || (q & (q - 1))) return ORACLE_EINVAL;
+  const uint64_t m = offsets[n];
+  std::vector<uint8_t> codes;
+  int rc = encode_all(seq, m, &codes);
+  if (rc) return rc;
+  std::memset(marks, 0, m);
+  int lg_blocks = 0;
+  while ((256ull << lg_blocks) < filter_bits) ++lg_blocks;
+  std::vector<uint32_t> F(filter_bits / 32, 0u);
+  uint64_t active = 0, kept = 0;
+
+  for (int loop = 1; loop <= 2; ++loop) {
+    for (uint64_t t = 0; t < n; ++t) {
+      const uint64_t s0 = offsets[t], len = offsets[t + 1] - offsets[t];
+      if (len < (uint64_t)k) continue;
+      for (uint64_t i = 0; i + k <= len; ++i) {
+        u128 v = word_at(codes, s0 + i, k);
+        u128 r = both_strands ? reverse_complement(v, k) : v;
+        u128 key = (both_strands && r < v) ? r : v;
+        FilterSpot f = locate(key, lg_blocks, hashes);
+        uint64_t bin = f.H & (q - 1);
+        if (bin < bin_lo || bin >= bin_hi) continue;
+        const bool sentinel_pos = (i == 0) || (i + k == len);
+        if (loop == 1) {
+          ++active;
+          if (sentinel_pos) {
+            filter_insert(F, f, hashes, 16);
+          } else {
+            int a = codes[s0 + i - 1], c = codes[s0 + i + k];
+            if (key == v) filter_insert(F, f, hashes, 4 * a + c);
+            if (both_strands && key == r) filter_insert(F, f, hashes, 4 * (3 - c) + (3 - a));
+          }
+        } else {
+          bool keep = sentinel_pos || filter_has(F, f, hashes, 16);
+          if (!keep) {
+            int present = 0;
+            for (int j = 0; j < 16; ++j) present += filter_has(F, f, hashes, j) ? 1 : 0;
+            keep = present >= 2;
+          }
+          if (keep) {
+            marks[s0 + i] = 1;
+            ++kept;
+          }
+        }
+      }
+    }
+  }
+  if (counters) {
+    counters[0] = active;
+    counters[1] = kept;
+  }
+  return ORACLE_OK;
+}
+
+/*
+ * Greedy class cut of the multiple-rounds heuristic (section "Multiple
+ * Rounds"): scan the q counters in order and close a class as soon as adding
+ * the next counter would push its sum above (sum of all counters) / l, while
+ * giving every class at least one bin; the last class takes what is left.
+ * The comparison sum <= total / l is made exactly, as l * sum <= total.
+ * cuts: l + 1 entries, class r owns bins [cuts[r], cuts[r+1]).
+ */
+int oracle_partition_cuts(const uint64_t* counts, uint64_t q, int l, uint64_t* cuts) {
+  if (l < 1 || q < (uint64_t)l) return ORACLE_EINVAL;
+  u128 total = 0;
+  for (uint64_t j = 0; j < q; ++j) total += counts[j];
+  uint64_t j = 0;
+  cuts[0] = 0;
+  for (int r = 0; r < l - 1; ++r) {
+    u128 sum = 0;
+    uint64_t start = j;
+    // at least one bin, and leave at least one bin for each later class
+    while (j < q - (uint64_t)(l - 1 - r)) {
+      if (j > start && (sum + counts[j]) * (u128)l > total) break;
+      sum += counts[j];
+      ++j;
+    }
+    cuts[r + 1] = j;
+  }
+  cuts[l] = q;
+  return ORACLE_OK;
+}
+
+}  // extern "C"

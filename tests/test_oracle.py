@@ -1,0 +1,250 @@
+"""Pins of the CPU oracle against the paper and against brute force (no GPU)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1602_05856_gb300 import genomes as G
+from tests import brute
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "fig1_junctions.txt")
+
+
+def _golden_rows():
+    rows = []
+    with open(GOLDEN) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            strands, k, seq, *pos = line.split()
+            rows.append((strands == "both", int(k), seq, [int(p) for p in pos]))
+    return rows
+
+
+def _as_lists(res):
+    return [list(map(int, r)) for r in res]
+
+
+@pytest.mark.parametrize("both,k", [(False, 2), (True, 2), (True, 3)])
+def test_fig1_worked_example(both, k):
+    rows = [r for r in _golden_rows() if r[0] == both and r[1] == k]
+    seqs = [r[2] for r in rows]
+    got = _as_lists(O.junctions(seqs, k, both_strands=both))
+    assert got == [r[3] for r in rows]
+    assert got == _as_lists(O.alg1_exact(seqs, k, both_strands=both))
+
+
+def test_fig1_false_junction_gc_absent():
+    # Fig. 1d: "GC" (position 2) is only a junction if a false edge is seen.
+    got = O.junctions(["TGGCACGTC", "TGGCACTTC"], 2, both_strands=False)
+    assert all(2 not in r for r in _as_lists(got))
+
+
+def _random_cases():
+    cases = []
+    seed = 11
+    for k in list(range(1, 9)) + [15, 25, 31, 63]:
+        for both in (False, True):
+            for alpha in (b"ACGT", b"AC", b"ACG"):
+                lo = max(1, k - 3)
+                hi = max(k + 40, 3 * k)
+                cases.append((seed, k, both, alpha, lo, hi))
+                seed += 1
+    return cases
+
+
+@pytest.mark.parametrize("seed,k,both,alpha,lo,hi", _random_cases())
+def test_definition_matches_brute_force(seed, k, both, alpha, lo, hi):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 6))
+    seqs = [bytes(s).decode() for s in G.random_strings(seed, n, lo, hi, alpha)]
+    if seed % 3 == 0:  # plant a reverse-complement pair and a repeat
+        seqs.append(brute.revcomp(seqs[0]))
+        seqs.append(seqs[0][: len(seqs[0]) // 2] + seqs[-1])
+    got = _as_lists(O.junctions(seqs, k, both_strands=both))
+    assert got == brute.junction_positions(seqs, k, both)
+    assert got == _as_lists(O.alg1_exact(seqs, k, both_strands=both))
+
+
+SPECIAL = [
+    ("homopolymer", ["A" * 40], 5),
+    ("homopolymer_rc", ["T" * 30, "A" * 12], 7),
+    ("dinucleotide_repeat", ["AC" * 25], 4),
+    ("tandem", ["ACGTTGCA" * 8], 6),
+    ("palindromes_even_k", ["ACGTACGTAATTGCGCAT", "GAATTCGAATTC"], 4),
+    ("shorter_than_k", ["ACG", "ACGTACGTAC"], 5),
+    ("exactly_k", ["ACGTA", "CCCCGGGG"], 5),
+    ("self_rc_string", ["AAGCTT", "GGATCC" * 3], 6),
+    ("k1", ["ACGTTTACG"], 1),
+]
+
+
+@pytest.mark.parametrize("name,seqs,k", SPECIAL, ids=[s[0] for s in SPECIAL])
+@pytest.mark.parametrize("both", [False, True])
+def test_special_cases(name, seqs, k, both):
+    got = _as_lists(O.junctions(seqs, k, both_strands=both))
+    assert got == brute.junction_positions(seqs, k, both)
+
+
+def test_homopolymer_every_position_is_sentinel():
+    # The only k-mer of A^L is both the first and the last k-mer: a sentinel.
+    got = _as_lists(O.junctions(["A" * 30], 4))
+    assert got == [list(range(27))]
+
+
+def test_short_strings_have_no_positions():
+    got = _as_lists(O.junctions(["ACGT", "ACGTACGTAA"], 8))
+    assert got[0] == [] and got[1] == [0, 2]
+
+
+@pytest.mark.parametrize("k,both", [(3, False), (4, True), (5, True), (9, False), (12, True)])
+def test_observation1_compaction_bijection(k, both):
+    """Junction-flanked substrings are exactly the maximal non-branching paths."""
+    seqs = [bytes(s).decode() for s in G.random_strings(100 + k, 4, 30, 90, b"ACG")]
+    seqs.append(seqs[1][5:40] + seqs[2][:30])
+    all_texts = brute.texts(seqs, both)
+    # adding the reverse complements does not change G_comp nor its sentinels
+    pos = _as_lists(O.junctions(all_texts, k, both_strands=both))
+    assert pos[: len(seqs)] == _as_lists(O.junctions(seqs, k, both_strands=both))
+    assert brute.paths_from_positions(all_texts, k, pos) == brute.compacted_paths(seqs, k, both)
+
+
+def test_spelling_invariant_plain_single_slice():
+    """Consecutive junction-flanked segments, overlapped by k-1, re-spell each genome."""
+    seqs = [s[:20000] for s in G.named_set("plain_single", scale=0.05)]
+    k = 25
+    res = O.junctions(seqs, k)
+    for s, pos in zip(seqs, res):
+        pos = [int(p) for p in pos]
+        assert pos[0] == 0 and pos[-1] == s.size - k
+        spelled = bytes(s[pos[0]:pos[0] + k])
+        for a, b in zip(pos, pos[1:]):
+            spelled += bytes(s[a + k:b + k])
+        assert spelled == bytes(s)
+
+
+def test_reverse_complement_symmetry():
+    seqs = [bytes(s).decode() for s in G.random_strings(7, 5, 50, 400, b"ACGT")]
+    seqs += [seqs[0][10:200], brute.revcomp(seqs[1][:150])]
+    k = 7
+    fwd = _as_lists(O.junctions(seqs, k))
+    rev = _as_lists(O.junctions([brute.revcomp(s) for s in seqs], k))
+    for s, f, r in zip(seqs, fwd, rev):
+        assert sorted(len(s) - k - p for p in f) == r
+
+
+def test_duplicate_and_permutation_invariance():
+    seqs = [bytes(s).decode() for s in G.random_strings(5, 4, 80, 300, b"ACGT")]
+    k = 6
+    base = _as_lists(O.junctions(seqs, k))
+    perm = _as_lists(O.junctions(seqs[::-1], k))
+    assert perm == base[::-1]
+    dup = _as_lists(O.junctions(seqs + [seqs[2]], k))
+    assert dup[:4] == base and dup[4] == base[2]
+
+
+def test_lowercase_and_bad_bytes():
+    assert _as_lists(O.junctions(["tggcacgtc", "TGGCACTTC"], 2, both_strands=False)) == \
+        [[0, 4, 7], [0, 4, 7]]
+    with pytest.raises(O.OracleError):
+        O.junctions(["ACGNT"], 2)
+    with pytest.raises(O.OracleError):
+        O.junctions(["ACGT"], 0)
+    with pytest.raises(O.OracleError):
+        O.junctions(["ACGT"], 64)
+
+
+def test_empty_input():
+    assert O.junctions([], 5) == []
+    assert _as_lists(O.junctions(["", "AC"], 5)) == [[], []]
+
+
+# --- first pass with the split-block filter ---------------------------------
+
+def _occurrence_groups(seqs, k):
+    groups = {}
+    for t, s in enumerate(seqs):
+        for i in range(len(s) - k + 1):
+            v = s[i:i + k]
+            key = min(v, brute.revcomp(v))
+            groups.setdefault(key, []).append((t, i))
+    return groups
+
+
+@pytest.mark.parametrize("bits,h", [(256, 1), (1 << 12, 3), (1 << 16, 4), (1 << 20, 8)])
+def test_pass1_candidate_set_contains_junctions(bits, h):
+    seqs = [bytes(s).decode() for s in G.random_strings(3, 5, 100, 2000, b"ACGT")]
+    seqs += [seqs[0][50:900], seqs[1][:300] + seqs[2][100:700]]
+    k = 9
+    marks, off, active, kept = O.pass1_marks(seqs, k, bits, h)
+    flags, _, _ = O.junction_flags(seqs, k)
+    assert active == sum(max(0, len(s) - k + 1) for s in seqs)
+    assert int(marks.sum()) == kept
+    assert np.all(marks >= flags), "a junction was unmarked"
+    # candidate-set property: all occurrences of a k-mer agree
+    for occ in _occurrence_groups(seqs, k).values():
+        vals = {int(marks[int(off[t]) + i]) for t, i in occ}
+        assert len(vals) == 1
+
+
+def test_pass1_saturated_filter_keeps_everything():
+    seqs = [bytes(s).decode() for s in G.random_strings(4, 3, 3000, 4000, b"ACGT")]
+    marks, off, active, kept = O.pass1_marks(seqs, 11, 256, 1)
+    assert kept == active
+
+
+def test_pass1_sparse_filter_is_exact():
+    seqs = [bytes(s).decode() for s in G.random_strings(9, 4, 200, 800, b"ACGT")]
+    seqs.append(seqs[0][100:500])
+    marks, off, active, kept = O.pass1_marks(seqs, 8, 1 << 30, 8)
+    flags, _, _ = O.junction_flags(seqs, 8)
+    assert np.array_equal(marks, flags)
+
+
+def test_pass1_classes_partition_positions():
+    seqs = [bytes(s).decode() for s in G.random_strings(12, 3, 500, 1500, b"ACGT")]
+    k, q = 10, 64
+    cuts = [0, 5, 21, 22, 64]
+    flags, _, _ = O.junction_flags(seqs, k)
+    total = sum(len(s) - k + 1 for s in seqs)
+    union = np.zeros_like(flags)
+    n_active = 0
+    for r in range(4):
+        m, _, a, kept = O.pass1_marks(seqs, k, 1 << 14, 3, q=q, bin_lo=cuts[r], bin_hi=cuts[r + 1])
+        assert not np.any(union & m), "rounds overlap"
+        union |= m
+        n_active += a
+    assert n_active == total
+    assert np.all(union >= flags)
+
+
+# --- greedy class cut ----------------------------------------------------------
+
+def test_partition_cuts_examples():
+    assert list(O.partition_cuts([1, 1, 1, 1], 2)) == [0, 2, 4]
+    assert list(O.partition_cuts([5, 1, 1, 1], 2)) == [0, 1, 4]
+    assert list(O.partition_cuts([1, 1, 1, 1], 1)) == [0, 4]
+    assert list(O.partition_cuts([0, 0, 0, 9], 3)) == [0, 2, 3, 4]
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_partition_cuts_greedy_property(seed):
+    rng = np.random.default_rng(seed)
+    q = int(rng.integers(4, 200))
+    ell = int(rng.integers(1, min(q, 17) + 1))
+    counts = rng.integers(0, 50, size=q) * (rng.random(q) < 0.8)
+    cuts = [int(c) for c in O.partition_cuts(counts, ell)]
+    total = int(counts.sum())
+    assert cuts[0] == 0 and cuts[-1] == q and len(cuts) == ell + 1
+    for r in range(ell):
+        lo, hi = cuts[r], cuts[r + 1]
+        assert hi > lo, "every class owns at least one bin"
+        if r < ell - 1:
+            s = int(counts[lo:hi].sum())
+            # maximal: one more bin would exceed the share, unless the class is a
+            # single bin or the next bin is reserved for a later class
+            if hi - lo > 1:
+                assert s * ell <= total
+            if hi < q - (ell - 1 - r):
+                assert (s + int(counts[hi])) * ell > total or hi - lo == 0
