@@ -241,10 +241,11 @@ int oracle_alg1_exact(const uint8_t* seq, const uint64_t* offsets, uint64_t n, i
  *   The filter has b bits = b/256 blocks of eight 32-bit words.
  *   block = H >> (64 - log2(b/256))  (0 when b = 256)
  *   o     = (G >> 61) & 6           first word used (even)
- *   word t = (o + u) & 7 for u < h; base_t = (uint32(G) * SALT[t]) >> 27
- *   SALT[t] = first 32 bits of the fractional part of the cube root of the
- *            (t+1)-th prime, forced odd.
- *   item j sets / tests bit (base_t + j) & 31 in each of those h words.
+ *   for u < h: word t_u = (o + u) & 7 of the block, with bit base
+ *           base_u = (uint32(G) * SALT[u]) >> 27
+ *   SALT[u] = first 32 bits of the fractional part of the cube root of the
+ *            (u+1)-th prime, forced odd.
+ *   item j sets / tests bit (base_u + j) & 31 of word t_u, for every u < h.
  *   items: j = 4a + c for the (predecessor a, successor c) pair of an
  *          occurrence read in the orientation of the normalized form
  *          (palindromes: both orientations); j = 16 marks a sentinel.
@@ -286,7 +287,7 @@ FilterSpot locate(u128 V, int lg_blocks, int h) {
   for (int u = 0; u < h; ++u) {
     uint32_t t = (o + (uint32_t)u) & 7u;
     f.word[u] = t;
-    f.base[u] = ((uint32_t)G * kSalt[t]) >> 27;
+    f.base[u] = ((uint32_t)G * kSalt[u]) >> 27;
   }
   return f;
 }
