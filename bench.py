@@ -1,0 +1,360 @@
+#!/usr/bin/env python3
+"""Throughput of two-pass junction detection (Gbp/s of genome input).
+
+One step = one full build over the bacterial-size genome set (7 related
+genomes of 4.6-5.6 Mbp, k = 25, a 2^28-bit filter with 4 hashes, 1 round):
+pack, pass 1 (filter insert + probe), pass 2 (exact table insert +
+classify) and the emit of sorted junction positions, all from ASCII already
+resident in device memory. The input (35 MB) is smaller than L2, so a
+512 MiB buffer is written between timed steps to flush it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank runs an independent replica of the workload on
+its own GPU (the build of one genome set does not shard); ``value`` is the
+bases of all replicas over the slowest rank's time. ``--impl reference``
+times the CPU oracle on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gbp/s genome input through both passes, k=25, 1 GB300; % roofline; p99 latency"
+UNIT = "Gbp/s"
+WORKLOAD = "bacterial_set"
+K = 25
+FILTER_BITS = 1 << 28
+HASHES = 4
+ROUNDS = 1
+FLUSH_BYTES = 512 << 20
+CPU_SAMPLE_BASES = 8_000_000     # cpu_baseline leg: about 10 s of oracle work
+REF_STEP_BASES = 2_000_000       # reference arm: bases per step
+
+
+def workload_config(total_bases: int) -> dict:
+    return {
+        "workload": ("bacterial_set: 7 related genomes of 4.6-5.6 Mbp (seed 1603; 50% GC ancestor, "
+                     "1% SNPs, 0.1% indels, 20 inversions/transpositions of 1-50 kbp, "
+                     "1.5 kbp repeat x30)"),
+        "total_bases": int(total_bases),
+        "k": K, "filter_bits": FILTER_BITS, "hashes": HASHES, "rounds": ROUNDS,
+        "both_strands": True,
+        "l2": f"flushed between timed steps ({FLUSH_BYTES >> 20} MiB write); input 35 MB < L2",
+    }
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def sample_prefix(seqs, total):
+    """A bounded sample: the same-length prefix of every genome, ~total bases."""
+    per = max(1, total // len(seqs))
+    return [s[:per] for s in seqs]
+
+
+def oracle_gbps(seqs, k) -> float:
+    import oracle
+    from paper_1602_05856_gb300 import genomes
+    bases, off = genomes.concat(seqs)
+    t = time.perf_counter()
+    oracle.junctions((bases, off), k)
+    return bases.size / (time.perf_counter() - t) / 1e9
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            if self.uuid and self.uuid not in f[1] and f[1] not in self.uuid:
+                continue
+            rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[6:10]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# Algorithmic work of every kernel per launch, from the run's own counters:
+# (unit, amount, kind) where kind names the roofline denominator.
+def kernel_work(name, st, m, n_seqs, table_bytes):
+    pos = st["positions"]
+    cand = st["pass1_marks"]
+    junc = st["pass2_marks"]
+    if name == "pass1_insert":
+        return pos, "l2_or"        # one random filter sector (read + ORs) per position
+    if name == "pass1_probe":
+        return pos, "l2_read"      # one random filter sector read per position
+    if name == "pass2_insert":
+        return cand, "l2_or"       # one table slot (CAS + OR) per candidate
+    if name == "pass2_classify":
+        return cand, "l2_read"     # one table slot read per candidate
+    if name == "pack":
+        return m + m / 4, "hbm"    # ASCII read + packed write (bytes)
+    if name == "table_clear":
+        return table_bytes, "hbm"
+    if name == "emit_write":
+        return m / 8 + 8 * junc, "hbm"
+    if name == "emit_count":
+        return m / 8, "hbm"
+    return None, None
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1602_05856_gb300 import build, genomes, twopaco as T
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    seqs = genomes.named_set(WORKLOAD)
+    bases, off = genomes.concat(seqs)
+    m, n = int(off[-1]), len(seqs)
+    opts = T.Options(hashes=HASHES)
+    run = T.DeviceBuild(bases, off, K, FILTER_BITS, ROUNDS, opts, device=f"cuda:{local}")
+    stream = torch.cuda.current_stream(dev)
+
+    # roofline denominators measured on this GPU: random 32-byte sectors of a
+    # buffer the size of the filter
+    import ctypes
+    peaks = ctypes.CDLL(build.build_peaks())
+    peaks.peaks_l2_random_rate.restype = ctypes.c_double
+    peaks.peaks_l2_random_rate.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int]
+    l2_read = peaks.peaks_l2_random_rate(0, FILTER_BITS // 8, 64, 5)
+    l2_or = peaks.peaks_l2_random_rate(1, FILTER_BITS // 8, 64, 5)
+
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(max(args.warmup, 0)):
+        run.run(stream)
+    st = run.stats(stream)  # raises on any recorded failure
+    torch.cuda.synchronize(dev)
+
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", "") or "")
+    sampler = ClockSampler(uuid)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    launches0 = T.twopaco_kernel_launches()
+    T.twopaco_profile_enable(True)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        run.run(stream)
+        ends[i].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    barrier(world)
+    clocks = sampler.stop()
+    launches = T.twopaco_kernel_launches() - launches0
+    prof = T.twopaco_profile_kernels()
+    T.twopaco_profile_enable(False)
+    st = run.stats(stream)
+
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = statistics.mean(step_ms)
+    ms_max = max_over_ranks(ms, world)
+    value = world * m / (ms_max * 1e-3) / 1e9
+
+    # end to end through the host API: pinned host input in, host result out
+    pinned = torch.empty(m, dtype=torch.uint8, pin_memory=True)
+    pinned.numpy()[:] = bases
+    host = pinned.numpy()
+    host_seqs = [host[int(off[t]):int(off[t + 1])] for t in range(n)]
+    e2e_t = []
+    got = None
+    for i in range(args.e2e_steps + 1):
+        t0 = time.perf_counter()
+        got, est = T.twopaco_build_ex(host_seqs, K, FILTER_BITS, ROUNDS, opts)
+        if i:
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(statistics.mean(e2e_t), world)
+    junctions = sum(g.size for g in got)
+    assert junctions == st["pass2_marks"], "host API and device run disagree"
+
+    # roofline of the dominant kernel
+    table_bytes = st["table_slots"] * (16 if K <= 31 else 32)
+    top = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    name, rec = top
+    per_launch_ms = rec["ms"] / rec["launches"]
+    amount, kind = kernel_work(name, st, m, n, table_bytes)
+    peaks_json = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = float(peaks_json.get("hbm_gbs", 6800.0))
+    if kind == "hbm":
+        achieved = amount / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks_json else "fallback 6.8 TB/s"}
+    else:
+        pk = (l2_read if kind == "l2_read" else l2_or) / 1e9
+        achieved = amount / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "l2", "achieved": achieved, "peak": pk, "unit": "Gsector/s",
+                "frac": achieved / pk if pk > 0 else None, "traffic": None,
+                "peak_source": ("measured in this run: random 32-byte sector "
+                                + ("reads" if kind == "l2_read" else "64-bit ORs")
+                                + f" over a {FILTER_BITS // 8 >> 20} MiB buffer")}
+    roof["kernel"] = name
+    roof["kernel_ms"] = per_launch_ms
+
+    kernels = {k: {"launches": v["launches"], "ms_per_launch": v["ms"] / v["launches"],
+                   "share": v["ms"] / sum(x["ms"] for x in prof.values())}
+               for k, v in prof.items()}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        sample = sample_prefix(seqs, CPU_SAMPLE_BASES)
+        cpu = {"value": oracle_gbps(sample, K), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{sum(s.size for s in sample)} bases: the first "
+                         f"{sample[0].size} bases of each of the 7 genomes, single thread"}
+    lat = sorted(step_ms)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": workload_config(m) | {"parallelism": f"replicas{world}" if world > 1 else "single"},
+        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+        "e2e": {"value": world * m / e2e_s / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": m + 8 * (n + 1),
+                "d2h_bytes_per_step": 8 * (n + 1) + 8 * junctions,
+                "api": "twopaco_build_ex (allocates, copies in, runs, copies out)"},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "stats": {k: st[k] for k in ("positions", "pass1_marks", "pass2_marks", "table_slots")},
+        "kernels": kernels,
+        "l2_peaks_gsector_s": {"read": l2_read / 1e9, "or": l2_or / 1e9},
+        "timed_wall_s": wall,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_1602_05856_gb300 import genomes
+    import oracle
+    seqs = genomes.named_set(WORKLOAD)
+    m = sum(s.size for s in seqs)
+    sample = sample_prefix(seqs, REF_STEP_BASES)
+    sb, so = genomes.concat(sample)
+    for _ in range(max(args.warmup, 0)):
+        oracle.junctions((sb, so), K)
+    ts = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.junctions((sb, so), K)
+        ts.append(time.perf_counter() - t)
+    sec = statistics.mean(ts)
+    value = sb.size / sec / 1e9
+    desc = (f"{sb.size} bases per step: the first {sample[0].size} bases of each of the 7 genomes; "
+            "CPU oracle (plain definition), single thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": workload_config(m) | {"parallelism": "single"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * twopaco.h -- C ABI of the GB300 junction-detection library.
+ *
+ * The library finds J(S, k): every position of every input string whose
+ * k-mer is a junction of the de Bruijn graph G(S, k) -- a bifurcation (more
+ * than one distinct incoming or outgoing edge) or a sentinel (the first or
+ * last k-mer of an input string) (Minkin, Pham & Medvedev, "TwoPaCo",
+ * arXiv 1602.05856, section "Preliminaries"). By default the graph is the
+ * comprehensive graph G(s) U G(s-bar) over both strands, with k-mers stored
+ * in normalized form (paragraph after Algorithm 2). Junction positions
+ * determine the compacted graph (Observation 1, section "Reduction to the
+ * Problem of Finding Junction Positions").
+ *
+ * The work follows Algorithm 3 (TwoPaCo): the k-mers are split into
+ * `rounds` classes (section "Multiple Rounds"), and every round runs
+ * Algorithm 2 (Filter-Junctions-Two-Pass): Algorithm 1 (Filter-Junctions)
+ * once with a Bloom filter of `filter_bits` bits, then once with an exact
+ * hash table on the surviving candidates. Every step runs in CUDA kernels
+ * on the current device; nothing falls back to the CPU.
+ *
+ * Conventions for every entry point:
+ *   - Input bytes are A, C, G, T in either case; any other byte is an error
+ *     (TWOPACO_EBADBASE). Strings are never joined: no k-mer spans two strings.
+ *   - Positions are 0-based k-mer starts i in [0, |s| - k]; a string shorter
+ *     than k has none.
+ *   - Return value: TWOPACO_OK (0) or a negative TWOPACO_E* code.
+ *   - k in [1, 63]; filter_bits a power of two >= 256; rounds >= 1;
+ *     options->hashes in [1, 8]; options->partition_bins a power of two
+ *     >= rounds. Anything else is TWOPACO_EINVAL.
+ *   - Calls on different workspaces may run concurrently from different host
+ *     threads; calls that share a workspace must be serialised by the caller.
+ */
+#ifndef TWOPACO_H_
+#define TWOPACO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TWOPACO_OK 0
+#define TWOPACO_EINVAL (-1)    /* an argument is out of range */
+#define TWOPACO_EBADBASE (-2)  /* an input byte is not one of ACGTacgt */
+#define TWOPACO_ENOMEM (-3)    /* device or pinned-host allocation failed */
+#define TWOPACO_ETIMEOUT (-4)  /* a bounded device wait gave up */
+#define TWOPACO_ECUDA (-5)     /* a CUDA runtime call failed */
+#define TWOPACO_EOVERFLOW (-6) /* the pass-2 table or the output buffer is too small */
+
+typedef struct twopaco_options {
+  int hashes;              /* bits per filter item, 1..8 (paper default 4) */
+  int both_strands;        /* 1: comprehensive graph (default); 0: single strand */
+  uint32_t partition_bins; /* q of the rounds heuristic, power of two (65536) */
+  uint64_t table_slots;    /* pass-2 table capacity in slots; 0 = automatic */
+  void* cuda_stream;       /* cudaStream_t to launch on, borrowed; NULL = default */
+} twopaco_options;
+
+/* Counters of one run, in the spirit of Table 4 (marks after each pass). */
+typedef struct twopaco_stats {
+  uint64_t positions;      /* k-mer positions in the input */
+  uint64_t pass1_marks;    /* candidates left after pass 1, summed over rounds */
+  uint64_t pass2_marks;    /* junction positions (marks after pass 2) */
+  uint64_t table_slots;    /* largest pass-2 table used in any round */
+  uint64_t bad_base_index; /* first invalid byte, or UINT64_MAX if none */
+  uint32_t overflow;       /* nonzero: the pass-2 table or output ran out of room */
+  uint32_t timeout;        /* nonzero: a bounded device wait gave up */
+} twopaco_stats;
+
+/* Result of twopaco_build: library-owned host memory. */
+typedef struct twopaco_result {
+  uint64_t n_seqs;
+  uint64_t* offsets;   /* n_seqs + 1 entries: junctions of string t are      */
+  uint64_t* positions; /* positions[offsets[t] .. offsets[t+1]), ascending   */
+  twopaco_stats stats;
+} twopaco_result;
+
+/* Fill `opt` with the defaults listed in twopaco_options. */
+void twopaco_default_options(twopaco_options* opt);
+
+/* Static description of a return code; never NULL. */
+const char* twopaco_strerror(int code);
+
+/*
+ * Host-to-host build (Algorithm 3 with Algorithm 2 in every round).
+ *   seqs[t], lengths[t]  the n_seqs input strings (host memory, borrowed,
+ *                        read before the call returns; seqs may be NULL
+ *                        when n_seqs == 0)
+ *   *out                 receives a result allocated by the library; free
+ *                        it with twopaco_result_free. Left NULL on error.
+ * Allocates device memory for the input and the workspace, copies the input
+ * in, runs, copies the result out and frees everything before returning. If
+ * the pass-2 table overflows it is grown and the run repeated.
+ */
+int twopaco_build(const char* const* seqs, const uint64_t* lengths, uint64_t n_seqs, int k,
+                  uint64_t filter_bits, int rounds, twopaco_result** out);
+
+/* As twopaco_build, with options (NULL = defaults). */
+int twopaco_build_ex(const char* const* seqs, const uint64_t* lengths, uint64_t n_seqs, int k,
+                     uint64_t filter_bits, int rounds, const twopaco_options* opt,
+                     twopaco_result** out);
+
+/* Release a result returned by twopaco_build*. NULL is ignored. */
+void twopaco_result_free(twopaco_result* res);
+
+/*
+ * Device workspace size, in bytes, for a device-resident run of
+ * `total_bases` bases in `n_seqs` strings. The workspace holds the 2-bit
+ * packed input, the filter (filter_bits / 8 bytes), two position bitmaps,
+ * the pass-2 table and small counters.
+ */
+int twopaco_workspace_size(uint64_t total_bases, uint64_t n_seqs, int k, uint64_t filter_bits,
+                           int rounds, const twopaco_options* opt, uint64_t* bytes);
+
+/*
+ * Device-resident run; all pointers are device memory owned by the caller.
+ *   d_bases      total_bases bytes: the strings back to back
+ *   d_offsets    n_seqs + 1 uint64: string t is d_bases[d_offsets[t] .. d_offsets[t+1]),
+ *                d_offsets[0] == 0 and d_offsets[n_seqs] == total_bases
+ *   d_workspace  at least twopaco_workspace_size(...) bytes, 256-byte aligned
+ *   d_out_offsets    n_seqs + 1 uint64, written (as in twopaco_result)
+ *   d_out_positions  out_capacity uint64, written; out_capacity >= the number
+ *                    of k-mer positions can never overflow
+ * Launches every kernel on options->cuda_stream and returns without
+ * synchronising. Device-side failures (a bad byte, a full table or output,
+ * a wait that gave up) are recorded in the workspace: read them with
+ * twopaco_read_stats once the stream has reached this point. Host-side
+ * argument errors are returned directly and launch nothing.
+ */
+int twopaco_run_device(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_seqs,
+                       uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
+                       const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
+                       uint64_t* d_out_offsets, uint64_t* d_out_positions, uint64_t out_capacity);
+
+/*
+ * Copy the counters of the last run on this workspace into *stats,
+ * synchronising `cuda_stream` (NULL = default stream) first. Returns
+ * TWOPACO_EBADBASE / TWOPACO_EOVERFLOW / TWOPACO_ETIMEOUT when the run
+ * recorded that failure (stats is still filled), else TWOPACO_OK.
+ */
+int twopaco_read_stats(const void* d_workspace, void* cuda_stream, twopaco_stats* stats);
+
+/* Which internal state twopaco_read_state copies out. */
+#define TWOPACO_STATE_CANDIDATES 0 /* C_temp of the last round: ceil(total_bases/32) uint32 words */
+#define TWOPACO_STATE_JUNCTIONS 1  /* C_final: ceil(total_bases/32) uint32 words */
+#define TWOPACO_STATE_BINS 2       /* partition counters e_i (rounds > 1): q uint32 */
+#define TWOPACO_STATE_CUTS 3       /* class boundaries: rounds + 1 uint32 */
+
+/*
+ * Copy internal state of the last run on this workspace to host memory, for
+ * verification. Bitmaps hold one bit per input base (bit g % 32 of word
+ * g / 32 is the k-mer starting at global base g). Class r of Algorithm 3
+ * owns the partition bins [cuts[r], cuts[r+1]) (section "Multiple Rounds").
+ * Synchronises `cuda_stream` first. `bytes` may not exceed the state's size.
+ */
+int twopaco_read_state(const void* d_workspace, int which, void* host_dst, uint64_t bytes,
+                       void* cuda_stream);
+
+/* Kernels launched by this library in this process so far (monotonic). */
+unsigned long long twopaco_kernel_launches(void);
+
+/*
+ * Per-kernel timing (off by default). While enabled, every kernel launch of
+ * the library is bracketed by two CUDA events recorded on its launch stream.
+ * twopaco_profile_enable(on) discards what was collected and switches the
+ * recording on or off (returns 0).
+ * twopaco_profile_kernels waits for the recorded events and fills, for each
+ * distinct kernel (in first-launch order, at most `capacity` of them), its
+ * name (static string), launch count and summed device time in ms. Any
+ * output pointer may be NULL. Returns the number of distinct kernels, or
+ * TWOPACO_ECUDA.
+ */
+int twopaco_profile_enable(int on);
+int twopaco_profile_kernels(const char** names, unsigned long long* launches, double* total_ms,
+                            int capacity);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TWOPACO_H_ */

@@ -1,0 +1,341 @@
+// C-ABI layer of the junction-detection library: argument checks, workspace
+// layout, the launch sequence of one run, and the host-to-host build.
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "twopaco.h"
+#include "twopaco_internal.h"
+
+namespace twopaco {
+namespace {
+
+constexpr uint64_t kAlign = 256;
+
+uint64_t align_up(uint64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool is_pow2(uint64_t x) { return x && !(x & (x - 1)); }
+
+uint64_t next_pow2(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+int log2_exact(uint64_t x) {
+  int l = 0;
+  while ((1ull << l) < x) ++l;
+  return l;
+}
+
+twopaco_options resolve(const twopaco_options* opt) {
+  twopaco_options o;
+  twopaco_default_options(&o);
+  if (opt) o = *opt;
+  return o;
+}
+
+int validate(uint64_t n_seqs, int k, uint64_t filter_bits, int rounds, const twopaco_options& o) {
+  if (k < 1 || k > 63) return TWOPACO_EINVAL;
+  if (filter_bits < 256 || !is_pow2(filter_bits) || filter_bits > (1ull << 40)) return TWOPACO_EINVAL;
+  if (rounds < 1) return TWOPACO_EINVAL;
+  if (o.hashes < 1 || o.hashes > 8) return TWOPACO_EINVAL;
+  if (o.both_strands != 0 && o.both_strands != 1) return TWOPACO_EINVAL;
+  if (!is_pow2(o.partition_bins) || o.partition_bins < (uint32_t)rounds) return TWOPACO_EINVAL;
+  if (rounds > 1 && o.partition_bins < 2) return TWOPACO_EINVAL;
+  if (n_seqs >= (1ull << 32)) return TWOPACO_EINVAL;
+  return TWOPACO_OK;
+}
+
+struct Layout {
+  uint64_t header, packed, filter, ctemp, cfinal, tile_count, tile_prefix, bins, cuts, table;
+  uint64_t total;
+  uint64_t packed_words, bitmap_words, n_tiles, table_slots;
+};
+
+uint64_t auto_table_slots(uint64_t m, int rounds) {
+  uint64_t per_round = (m + (uint64_t)rounds - 1) / (uint64_t)rounds;
+  uint64_t want = 2 * per_round;
+  if (want < 1024) want = 1024;
+  return next_pow2(want);
+}
+
+Layout layout(uint64_t m, int k, uint64_t filter_bits, int rounds, const twopaco_options& o) {
+  Layout L{};
+  L.packed_words = (m + 15) / 16 + kPackPadWords;
+  L.bitmap_words = (m + 31) / 32;
+  L.n_tiles = (L.bitmap_words + kEmitTileWords - 1) / kEmitTileWords;
+  L.table_slots = o.table_slots ? next_pow2(o.table_slots) : auto_table_slots(m, rounds);
+  uint64_t at = 0;
+  L.header = at;
+  at += align_up(sizeof(DevHeader));
+  L.packed = at;
+  at += align_up(L.packed_words * 4);
+  L.filter = at;
+  at += align_up(filter_bits / 8);
+  L.ctemp = at;
+  at += align_up((L.bitmap_words + 8) * 4);
+  L.cfinal = at;
+  at += align_up((L.bitmap_words + 8) * 4);
+  L.tile_count = at;
+  at += align_up((L.n_tiles + 1) * 4);
+  L.tile_prefix = at;
+  at += align_up((L.n_tiles + 1) * 8);
+  L.bins = at;
+  if (rounds > 1) at += align_up((uint64_t)o.partition_bins * 4 + ((uint64_t)o.partition_bins + 1) * 8);
+  L.cuts = at;
+  at += align_up(((uint64_t)rounds + 1) * 4);
+  L.table = at;
+  at += align_up(L.table_slots * table_slot_bytes(k));
+  L.total = at;
+  return L;
+}
+
+RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_seqs, uint64_t m,
+                  int k, uint64_t filter_bits, int rounds, const twopaco_options& o,
+                  const Layout& L, void* ws, uint64_t* d_out_offsets, uint64_t* d_out_positions,
+                  uint64_t out_capacity) {
+  char* base = static_cast<char*>(ws);
+  RunView v{};
+  v.bases = d_bases;
+  v.offsets = d_offsets;
+  v.n_seqs = (uint32_t)n_seqs;
+  v.m = m;
+  v.k = k;
+  v.both = o.both_strands;
+  v.hashes = o.hashes;
+  v.rounds = rounds;
+  v.lg_blocks = log2_exact(filter_bits / 256);
+  v.qmask = o.partition_bins - 1u;
+  v.hdr = reinterpret_cast<DevHeader*>(base + L.header);
+  v.packed = reinterpret_cast<uint32_t*>(base + L.packed);
+  v.packed_words = L.packed_words;
+  v.filter = reinterpret_cast<unsigned long long*>(base + L.filter);
+  v.filter_words64 = filter_bits / 64;
+  v.ctemp = reinterpret_cast<uint32_t*>(base + L.ctemp);
+  v.cfinal = reinterpret_cast<uint32_t*>(base + L.cfinal);
+  v.bitmap_words = L.bitmap_words;
+  v.table = base + L.table;
+  v.table_max_slots = L.table_slots;
+  v.bins = rounds > 1 ? reinterpret_cast<uint32_t*>(base + L.bins) : nullptr;
+  v.cuts = reinterpret_cast<uint32_t*>(base + L.cuts);
+  v.tile_count = reinterpret_cast<uint32_t*>(base + L.tile_count);
+  v.tile_prefix = reinterpret_cast<uint64_t*>(base + L.tile_prefix);
+  v.n_tiles = L.n_tiles;
+  v.out_offsets = d_out_offsets;
+  v.out_positions = d_out_positions;
+  v.out_capacity = out_capacity;
+  return v;
+}
+
+int cuda_code(cudaError_t e) {
+  if (e == cudaSuccess) return TWOPACO_OK;
+  if (e == cudaErrorMemoryAllocation) return TWOPACO_ENOMEM;
+  return TWOPACO_ECUDA;
+}
+
+}  // namespace
+}  // namespace twopaco
+
+using namespace twopaco;
+
+extern "C" {
+
+void twopaco_default_options(twopaco_options* opt) {
+  if (!opt) return;
+  opt->hashes = 4;
+  opt->both_strands = 1;
+  opt->partition_bins = 65536;
+  opt->table_slots = 0;
+  opt->cuda_stream = nullptr;
+}
+
+const char* twopaco_strerror(int code) {
+  switch (code) {
+    case TWOPACO_OK: return "ok";
+    case TWOPACO_EINVAL: return "invalid argument";
+    case TWOPACO_EBADBASE: return "input byte is not one of ACGTacgt";
+    case TWOPACO_ENOMEM: return "out of memory";
+    case TWOPACO_ETIMEOUT: return "a bounded device wait gave up";
+    case TWOPACO_ECUDA: return "CUDA error";
+    case TWOPACO_EOVERFLOW: return "pass-2 table or output buffer too small";
+    default: return "unknown error";
+  }
+}
+
+int twopaco_workspace_size(uint64_t total_bases, uint64_t n_seqs, int k, uint64_t filter_bits,
+                           int rounds, const twopaco_options* opt, uint64_t* bytes) {
+  const twopaco_options o = resolve(opt);
+  int rc = validate(n_seqs, k, filter_bits, rounds, o);
+  if (rc) return rc;
+  if (!bytes) return TWOPACO_EINVAL;
+  *bytes = layout(total_bases, k, filter_bits, rounds, o).total;
+  return TWOPACO_OK;
+}
+
+int twopaco_run_device(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_seqs,
+                       uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
+                       const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
+                       uint64_t* d_out_offsets, uint64_t* d_out_positions, uint64_t out_capacity) {
+  const twopaco_options o = resolve(opt);
+  int rc = validate(n_seqs, k, filter_bits, rounds, o);
+  if (rc) return rc;
+  if (total_bases > 0 && (n_seqs == 0 || !d_bases || !d_offsets)) return TWOPACO_EINVAL;
+  if (n_seqs > 0 && !d_offsets) return TWOPACO_EINVAL;
+  if (!d_out_offsets || (out_capacity && !d_out_positions)) return TWOPACO_EINVAL;
+  if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) % kAlign)) return TWOPACO_EINVAL;
+  const Layout L = layout(total_bases, k, filter_bits, rounds, o);
+  if (workspace_bytes < L.total) return TWOPACO_EINVAL;
+  const RunView v = make_view(d_bases, d_offsets, n_seqs, total_bases, k, filter_bits, rounds, o, L,
+                              d_workspace, d_out_offsets, d_out_positions, out_capacity);
+  cudaStream_t s = static_cast<cudaStream_t>(o.cuda_stream);
+  if (launch_init(v, s) < 0) return TWOPACO_ECUDA;
+  if (launch_pack(v, s) < 0) return TWOPACO_ECUDA;
+  if (rounds > 1 && launch_partition(v, rounds, s) < 0) return TWOPACO_ECUDA;
+  for (int r = 0; r < rounds; ++r)
+    if (launch_round(v, r, rounds, s) < 0) return TWOPACO_ECUDA;
+  if (launch_emit(v, s) < 0) return TWOPACO_ECUDA;
+  return TWOPACO_OK;
+}
+
+int twopaco_read_stats(const void* d_workspace, void* cuda_stream, twopaco_stats* stats) {
+  if (!d_workspace || !stats) return TWOPACO_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_code(e);
+  DevHeader h;
+  e = cudaMemcpy(&h, d_workspace, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_code(e);
+  stats->positions = h.positions;
+  stats->pass1_marks = h.pass1_kept;
+  stats->pass2_marks = h.pass2_kept;
+  stats->table_slots = h.table_max;
+  stats->bad_base_index = h.bad_index;
+  stats->overflow = h.overflow;
+  stats->timeout = h.timeout;
+  if (h.bad_index != ~0ull) return TWOPACO_EBADBASE;
+  if (h.timeout) return TWOPACO_ETIMEOUT;
+  if (h.overflow) return TWOPACO_EOVERFLOW;
+  return TWOPACO_OK;
+}
+
+int twopaco_read_state(const void* d_workspace, int which, void* host_dst, uint64_t bytes,
+                       void* cuda_stream) {
+  if (!d_workspace || (!host_dst && bytes)) return TWOPACO_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_code(e);
+  DevHeader h;
+  e = cudaMemcpy(&h, d_workspace, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_code(e);
+  const void* src = nullptr;
+  uint64_t avail = 0;
+  switch (which) {
+    case TWOPACO_STATE_CANDIDATES: src = h.ctemp; avail = h.bitmap_words * 4; break;
+    case TWOPACO_STATE_JUNCTIONS: src = h.cfinal; avail = h.bitmap_words * 4; break;
+    case TWOPACO_STATE_BINS: src = h.bins; avail = h.bins ? h.q * 4 : 0; break;
+    case TWOPACO_STATE_CUTS: src = h.cuts; avail = (h.rounds + 1) * 4; break;
+    default: return TWOPACO_EINVAL;
+  }
+  if (bytes > avail) return TWOPACO_EINVAL;
+  if (!bytes) return TWOPACO_OK;
+  return cuda_code(cudaMemcpy(host_dst, src, bytes, cudaMemcpyDeviceToHost));
+}
+
+void twopaco_result_free(twopaco_result* res) {
+  if (!res) return;
+  std::free(res->offsets);
+  std::free(res->positions);
+  std::free(res);
+}
+
+int twopaco_build(const char* const* seqs, const uint64_t* lengths, uint64_t n_seqs, int k,
+                  uint64_t filter_bits, int rounds, twopaco_result** out) {
+  return twopaco_build_ex(seqs, lengths, n_seqs, k, filter_bits, rounds, nullptr, out);
+}
+
+int twopaco_build_ex(const char* const* seqs, const uint64_t* lengths, uint64_t n_seqs, int k,
+                     uint64_t filter_bits, int rounds, const twopaco_options* opt,
+                     twopaco_result** out) {
+  if (!out) return TWOPACO_EINVAL;
+  *out = nullptr;
+  twopaco_options o = resolve(opt);
+  int rc = validate(n_seqs, k, filter_bits, rounds, o);
+  if (rc) return rc;
+  if (n_seqs && (!seqs || !lengths)) return TWOPACO_EINVAL;
+  std::vector<uint64_t> offsets(n_seqs + 1, 0);
+  uint64_t positions = 0;
+  for (uint64_t t = 0; t < n_seqs; ++t) {
+    if (lengths[t] && !seqs[t]) return TWOPACO_EINVAL;
+    offsets[t + 1] = offsets[t] + lengths[t];
+    if (lengths[t] >= (uint64_t)k) positions += lengths[t] - (uint64_t)k + 1;
+  }
+  const uint64_t m = offsets[n_seqs];
+  cudaStream_t s = static_cast<cudaStream_t>(o.cuda_stream);
+
+  uint8_t* d_bases = nullptr;
+  uint64_t* d_off = nullptr;
+  uint64_t* d_out_off = nullptr;
+  uint64_t* d_pos = nullptr;
+  void* d_ws = nullptr;
+  twopaco_result* res = nullptr;
+  twopaco_stats st{};
+  auto fail = [&](int code) {
+    cudaStreamSynchronize(s);
+    cudaFree(d_bases);
+    cudaFree(d_off);
+    cudaFree(d_out_off);
+    cudaFree(d_pos);
+    cudaFree(d_ws);
+    if (res) twopaco_result_free(res);
+    return code;
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&d_bases, m ? m : 1)) != cudaSuccess) return fail(cuda_code(e));
+  if ((e = cudaMalloc(&d_off, (n_seqs + 1) * 8)) != cudaSuccess) return fail(cuda_code(e));
+  if ((e = cudaMalloc(&d_out_off, (n_seqs + 1) * 8)) != cudaSuccess) return fail(cuda_code(e));
+  if ((e = cudaMalloc(&d_pos, (positions ? positions : 1) * 8)) != cudaSuccess) return fail(cuda_code(e));
+  for (uint64_t t = 0; t < n_seqs; ++t) {
+    if (!lengths[t]) continue;
+    e = cudaMemcpyAsync(d_bases + offsets[t], seqs[t], lengths[t], cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(cuda_code(e));
+  }
+  e = cudaMemcpyAsync(d_off, offsets.data(), (n_seqs + 1) * 8, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return fail(cuda_code(e));
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_code(e));
+
+  for (int attempt = 0;; ++attempt) {
+    uint64_t ws = 0;
+    if ((rc = twopaco_workspace_size(m, n_seqs, k, filter_bits, rounds, &o, &ws))) return fail(rc);
+    if ((e = cudaMalloc(&d_ws, ws)) != cudaSuccess) return fail(cuda_code(e));
+    rc = twopaco_run_device(d_bases, d_off, n_seqs, m, k, filter_bits, rounds, &o, d_ws, ws,
+                            d_out_off, d_pos, positions);
+    if (rc) return fail(rc);
+    rc = twopaco_read_stats(d_ws, o.cuda_stream, &st);
+    if (rc != TWOPACO_EOVERFLOW || attempt >= 4) break;
+    // The table was too small for this input: grow it and run again.
+    const Layout L = layout(m, k, filter_bits, rounds, o);
+    o.table_slots = L.table_slots * 4;
+    cudaFree(d_ws);
+    d_ws = nullptr;
+  }
+  if (rc) return fail(rc);
+
+  res = static_cast<twopaco_result*>(std::calloc(1, sizeof(twopaco_result)));
+  if (!res) return fail(TWOPACO_ENOMEM);
+  res->n_seqs = n_seqs;
+  res->stats = st;
+  res->offsets = static_cast<uint64_t*>(std::malloc((n_seqs + 1) * 8));
+  res->positions = static_cast<uint64_t*>(std::malloc((st.pass2_marks ? st.pass2_marks : 1) * 8));
+  if (!res->offsets || !res->positions) return fail(TWOPACO_ENOMEM);
+  if ((e = cudaMemcpy(res->offsets, d_out_off, (n_seqs + 1) * 8, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return fail(cuda_code(e));
+  if (st.pass2_marks &&
+      (e = cudaMemcpy(res->positions, d_pos, st.pass2_marks * 8, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return fail(cuda_code(e));
+  twopaco_result* done = res;
+  res = nullptr;
+  fail(TWOPACO_OK);
+  *out = done;
+  return TWOPACO_OK;
+}
+
+}  // extern "C"

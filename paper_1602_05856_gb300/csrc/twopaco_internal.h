@@ -1,0 +1,82 @@
+// Internal declarations shared by the kernels and the C-ABI layer of the
+// junction-detection library. Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace twopaco {
+
+// Counters and failure flags kept at the start of the workspace.
+struct DevHeader {
+  unsigned long long bad_index;    // smallest invalid byte index, ~0 if none
+  unsigned long long positions;    // k-mer positions in the input
+  unsigned long long pass1_kept;   // candidates after pass 1, all rounds
+  unsigned long long pass2_kept;   // junction positions
+  unsigned long long round_kept;   // candidates after pass 1, current round
+  unsigned long long table_slots;  // pass-2 table capacity of the current round
+  unsigned long long table_max;    // largest capacity used by any round
+  unsigned int overflow;           // table or output out of room
+  unsigned int timeout;            // a bounded wait gave up
+  // where the last run left its bitmaps and partition state (for inspection)
+  uint32_t* ctemp;
+  uint32_t* cfinal;
+  uint32_t* bins;
+  uint32_t* cuts;
+  unsigned long long bitmap_words;
+  unsigned long long q;
+  unsigned long long rounds;
+};
+
+// Device view of one run: every buffer lives inside the workspace except the
+// caller's input and output arrays.
+struct RunView {
+  const uint8_t* bases;     // caller's ASCII, m bytes
+  const uint64_t* offsets;  // caller's n + 1 string offsets
+  uint32_t n_seqs;
+  uint64_t m;               // total bases
+  int k;
+  int both;                 // comprehensive graph
+  int hashes;               // bits per filter item
+  int rounds;               // classes of Algorithm 3
+  int lg_blocks;            // log2(filter_bits / 256)
+  uint32_t qmask;           // partition_bins - 1
+  DevHeader* hdr;
+  uint32_t* packed;         // 2-bit packed input, ceil(m/16) + pad words
+  uint64_t packed_words;    // words written by the pack kernel (incl. pad)
+  unsigned long long* filter;  // filter_bits / 64 words
+  uint64_t filter_words64;
+  uint32_t* ctemp;          // C_temp bitmap, one bit per base
+  uint32_t* cfinal;         // C_final bitmap
+  uint64_t bitmap_words;    // ceil(m/32)
+  void* table;              // pass-2 slots
+  uint64_t table_max_slots;
+  uint32_t* bins;           // partition counters (q), rounds > 1
+  uint32_t* cuts;           // rounds + 1 class boundaries
+  uint32_t* tile_count;     // emit: junctions per tile
+  uint64_t* tile_prefix;    // emit: exclusive prefix per tile
+  uint64_t n_tiles;
+  uint64_t* out_offsets;    // caller's n + 1
+  uint64_t* out_positions;  // caller's capacity
+  uint64_t out_capacity;
+};
+
+constexpr int kBlock = 256;             // threads per block of the position kernels
+constexpr int kEmitTileWords = 256;     // bitmap words per emit tile (8192 positions)
+constexpr uint64_t kPackPadWords = 8;   // zero words after the packed input
+
+// Kernel launch helpers (twopaco_kernels.cu). Each returns the number of
+// kernels it launched, or -1 after a launch error.
+int launch_init(const RunView& v, cudaStream_t s);
+int launch_pack(const RunView& v, cudaStream_t s);
+int launch_partition(const RunView& v, int rounds, cudaStream_t s);
+int launch_round(const RunView& v, int round, int rounds, cudaStream_t s);
+int launch_emit(const RunView& v, cudaStream_t s);
+
+// Bytes per pass-2 slot for this k.
+inline uint64_t table_slot_bytes(int k) { return k <= 31 ? 16 : 32; }
+
+// Process-wide count of kernels launched by the library.
+void count_launches(int n);
+
+}  // namespace twopaco

@@ -1,0 +1,88 @@
+// Roofline denominators for the filter kernels: the rate at which this GPU
+// serves random 32-byte sector reads and random 64-bit atomic ORs from a
+// buffer of a given size (L2-resident when it is smaller than L2).
+// Not part of the junction method; the benchmark calls it before timing.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace {
+
+__device__ __forceinline__ uint64_t mix(uint64_t z) {
+  z ^= z >> 33;
+  z *= 0xff51afd7ed558ccdull;
+  z ^= z >> 33;
+  z *= 0xc4ceb9fe1a85ec53ull;
+  z ^= z >> 33;
+  return z;
+}
+
+__global__ void __launch_bounds__(256) sector_reads(const ulonglong2* __restrict__ buf,
+                                                   uint64_t block_mask, int iters,
+                                                   unsigned long long* sink) {
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t acc = 0;
+  uint64_t h = mix(tid + 1);
+  for (int it = 0; it < iters; ++it) {
+    h = mix(h + 0x9e3779b97f4a7c15ull);
+    const uint64_t b = h & block_mask;
+    const ulonglong2 a = __ldcg(buf + 2 * b), c = __ldcg(buf + 2 * b + 1);
+    acc ^= a.x ^ a.y ^ c.x ^ c.y;
+  }
+  if (acc == 0x1234567ull) sink[0] = acc;  // keeps the loads alive
+}
+
+__global__ void __launch_bounds__(256) sector_ors(unsigned long long* __restrict__ buf,
+                                                 uint64_t block_mask, int iters) {
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t h = mix(tid + 7);
+  for (int it = 0; it < iters; ++it) {
+    h = mix(h + 0x9e3779b97f4a7c15ull);
+    const uint64_t b = h & block_mask;
+    atomicOr(buf + 4 * b + ((h >> 40) & 3), 1ull << ((h >> 48) & 63));
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+// mode 0: random sector reads; mode 1: random 64-bit ORs (one per sector).
+// buf_bytes: power of two >= 32. Returns sector operations per second, or a
+// negative value on a CUDA error. Allocates and frees its own buffer.
+double peaks_l2_random_rate(int mode, uint64_t buf_bytes, int iters, int reps) {
+  void* buf = nullptr;
+  unsigned long long* sink = nullptr;
+  if (cudaMalloc(&buf, buf_bytes) != cudaSuccess) return -1.0;
+  if (cudaMalloc(&sink, 8) != cudaSuccess) { cudaFree(buf); return -1.0; }
+  cudaMemset(buf, 0, buf_bytes);
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (mode == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sector_reads, 256, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sector_ors, 256, 0);
+  const unsigned grid = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
+  const uint64_t mask = buf_bytes / 32 - 1;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  double best = 0.0;
+  for (int r = 0; r <= reps; ++r) {  // first launch is a warm-up
+    cudaEventRecord(a);
+    if (mode == 0) sector_reads<<<grid, 256>>>(static_cast<const ulonglong2*>(buf), mask, iters, sink);
+    else sector_ors<<<grid, 256>>>(static_cast<unsigned long long*>(buf), mask, iters);
+    cudaEventRecord(b);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    const double rate = (double)grid * 256.0 * iters / (ms * 1e-3);
+    if (r > 0 && rate > best) best = rate;
+  }
+  const bool bad = cudaGetLastError() != cudaSuccess;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(sink);
+  cudaFree(buf);
+  return bad ? -1.0 : best;
+}
+
+}  // extern "C"

@@ -1,0 +1,281 @@
+"""Python binding of the C ABI in ``include/twopaco.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+part of the computation: the junction detection runs in the CUDA kernels of
+``libtwopaco.so``. If the library is not built this module raises on first
+use -- there is no CPU path.
+
+``DeviceBuild`` adds the device-resident workflow on top of the same calls,
+with PyTorch used only to own device memory and to name the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtwopaco.so")
+
+OK, EINVAL, EBADBASE, ENOMEM, ETIMEOUT, ECUDA, EOVERFLOW = 0, -1, -2, -3, -4, -5, -6
+STATE_CANDIDATES, STATE_JUNCTIONS, STATE_BINS, STATE_CUTS = 0, 1, 2, 3
+
+
+class TwopacoError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = _lib().twopaco_strerror(code).decode() if _LIB is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("hashes", ctypes.c_int), ("both_strands", ctypes.c_int),
+                ("partition_bins", ctypes.c_uint32), ("table_slots", ctypes.c_uint64),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("positions", ctypes.c_uint64), ("pass1_marks", ctypes.c_uint64),
+                ("pass2_marks", ctypes.c_uint64), ("table_slots", ctypes.c_uint64),
+                ("bad_base_index", ctypes.c_uint64), ("overflow", ctypes.c_uint32),
+                ("timeout", ctypes.c_uint32)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("n_seqs", ctypes.c_uint64), ("offsets", ctypes.POINTER(ctypes.c_uint64)),
+                ("positions", ctypes.POINTER(ctypes.c_uint64)), ("stats", _Stats)]
+
+
+_LIB: Optional[ctypes.CDLL] = None
+
+
+def _lib() -> ctypes.CDLL:
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_1602_05856_gb300.build.build() (there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, U64, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
+        L.twopaco_strerror.argtypes = [I]
+        L.twopaco_strerror.restype = ctypes.c_char_p
+        L.twopaco_default_options.argtypes = [ctypes.POINTER(_Options)]
+        L.twopaco_default_options.restype = None
+        L.twopaco_build_ex.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(U64), U64, I,
+                                       U64, I, ctypes.POINTER(_Options),
+                                       ctypes.POINTER(ctypes.POINTER(_Result))]
+        L.twopaco_build_ex.restype = I
+        L.twopaco_build.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(U64), U64, I,
+                                    U64, I, ctypes.POINTER(ctypes.POINTER(_Result))]
+        L.twopaco_build.restype = I
+        L.twopaco_result_free.argtypes = [ctypes.POINTER(_Result)]
+        L.twopaco_result_free.restype = None
+        L.twopaco_workspace_size.argtypes = [U64, U64, I, U64, I, ctypes.POINTER(_Options),
+                                             ctypes.POINTER(U64)]
+        L.twopaco_workspace_size.restype = I
+        L.twopaco_run_device.argtypes = [P, P, U64, U64, I, U64, I, ctypes.POINTER(_Options), P, U64,
+                                         P, P, U64]
+        L.twopaco_run_device.restype = I
+        L.twopaco_read_stats.argtypes = [P, P, ctypes.POINTER(_Stats)]
+        L.twopaco_read_stats.restype = I
+        L.twopaco_read_state.argtypes = [P, I, P, U64, P]
+        L.twopaco_read_state.restype = I
+        L.twopaco_kernel_launches.argtypes = []
+        L.twopaco_kernel_launches.restype = ctypes.c_ulonglong
+        L.twopaco_profile_enable.argtypes = [I]
+        L.twopaco_profile_enable.restype = I
+        L.twopaco_profile_kernels.argtypes = [ctypes.POINTER(ctypes.c_char_p),
+                                              ctypes.POINTER(ctypes.c_ulonglong),
+                                              ctypes.POINTER(ctypes.c_double), I]
+        L.twopaco_profile_kernels.restype = I
+        _LIB = L
+    return _LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load ``libtwopaco.so`` (raises if it is not built)."""
+    return _lib()
+
+
+@dataclass
+class Options:
+    hashes: int = 4
+    both_strands: bool = True
+    partition_bins: int = 65536
+    table_slots: int = 0
+    cuda_stream: int = 0  # cudaStream_t as an integer; 0 = default stream
+
+    def _c(self) -> _Options:
+        return _Options(int(self.hashes), int(bool(self.both_strands)), int(self.partition_bins),
+                        int(self.table_slots), ctypes.c_void_p(int(self.cuda_stream) or None))
+
+
+def _stats_dict(s: _Stats) -> Dict[str, int]:
+    return {f: int(getattr(s, f)) for f, _ in _Stats._fields_}
+
+
+def _as_bytes(s) -> np.ndarray:
+    if isinstance(s, str):
+        return np.frombuffer(s.encode("ascii"), np.uint8)
+    if isinstance(s, (bytes, bytearray, memoryview)):
+        return np.frombuffer(bytes(s), np.uint8)
+    return np.ascontiguousarray(s, dtype=np.uint8)
+
+
+def twopaco_strerror(code: int) -> str:
+    return _lib().twopaco_strerror(int(code)).decode()
+
+
+def twopaco_kernel_launches() -> int:
+    return int(_lib().twopaco_kernel_launches())
+
+
+def twopaco_profile_enable(on: bool) -> None:
+    _lib().twopaco_profile_enable(int(bool(on)))
+
+
+def twopaco_profile_kernels() -> Dict[str, Dict[str, float]]:
+    """{kernel name: {"launches": n, "ms": summed device time}} since profiling was enabled."""
+    cap = 64
+    names = (ctypes.c_char_p * cap)()
+    cnt = (ctypes.c_ulonglong * cap)()
+    ms = (ctypes.c_double * cap)()
+    n = _lib().twopaco_profile_kernels(names, cnt, ms, cap)
+    if n < 0:
+        raise TwopacoError(n, "twopaco_profile_kernels")
+    return {names[i].decode(): {"launches": int(cnt[i]), "ms": float(ms[i])} for i in range(min(n, cap))}
+
+
+def twopaco_build_ex(seqs: Sequence, k: int, filter_bits: int, rounds: int = 1,
+                     options: Optional[Options] = None):
+    """Host-to-host build: (list of junction-position arrays, stats dict)."""
+    L = _lib()
+    arrs = [_as_bytes(s) for s in seqs]
+    n = len(arrs)
+    ptrs = (ctypes.c_void_p * max(n, 1))(*[a.ctypes.data if a.size else None for a in arrs])
+    lens = (ctypes.c_uint64 * max(n, 1))(*[a.size for a in arrs])
+    out = ctypes.POINTER(_Result)()
+    opt = (options or Options())._c()
+    rc = L.twopaco_build_ex(ptrs, lens, n, int(k), int(filter_bits), int(rounds),
+                            ctypes.byref(opt), ctypes.byref(out))
+    if rc != OK:
+        raise TwopacoError(rc, "twopaco_build_ex")
+    try:
+        r = out.contents
+        off = np.ctypeslib.as_array(r.offsets, shape=(n + 1,)).copy()
+        total = int(off[-1])
+        pos = (np.ctypeslib.as_array(r.positions, shape=(total,)).copy() if total
+               else np.zeros(0, np.uint64))
+        stats = _stats_dict(r.stats)
+    finally:
+        L.twopaco_result_free(out)
+    return [pos[off[t]:off[t + 1]] for t in range(n)], stats
+
+
+def twopaco_build(seqs: Sequence, k: int, filter_bits: int, rounds: int = 1):
+    return twopaco_build_ex(seqs, k, filter_bits, rounds, None)
+
+
+def twopaco_workspace_size(total_bases: int, n_seqs: int, k: int, filter_bits: int, rounds: int = 1,
+                           options: Optional[Options] = None) -> int:
+    b = ctypes.c_uint64(0)
+    opt = (options or Options())._c()
+    rc = _lib().twopaco_workspace_size(int(total_bases), int(n_seqs), int(k), int(filter_bits),
+                                       int(rounds), ctypes.byref(opt), ctypes.byref(b))
+    if rc != OK:
+        raise TwopacoError(rc, "twopaco_workspace_size")
+    return int(b.value)
+
+
+def twopaco_run_device(d_bases: int, d_offsets: int, n_seqs: int, total_bases: int, k: int,
+                       filter_bits: int, rounds: int, options: Optional[Options], d_workspace: int,
+                       workspace_bytes: int, d_out_offsets: int, d_out_positions: int,
+                       out_capacity: int) -> None:
+    opt = (options or Options())._c()
+    rc = _lib().twopaco_run_device(d_bases or None, d_offsets or None, int(n_seqs), int(total_bases),
+                                   int(k), int(filter_bits), int(rounds), ctypes.byref(opt),
+                                   d_workspace or None, int(workspace_bytes), d_out_offsets or None,
+                                   d_out_positions or None, int(out_capacity))
+    if rc != OK:
+        raise TwopacoError(rc, "twopaco_run_device")
+
+
+def twopaco_read_stats(d_workspace: int, cuda_stream: int = 0, check: bool = True) -> Dict[str, int]:
+    s = _Stats()
+    rc = _lib().twopaco_read_stats(d_workspace or None, cuda_stream or None, ctypes.byref(s))
+    if check and rc != OK:
+        raise TwopacoError(rc, "twopaco_read_stats")
+    d = _stats_dict(s)
+    d["rc"] = int(rc)
+    return d
+
+
+def twopaco_read_state(d_workspace: int, which: int, count: int, cuda_stream: int = 0) -> np.ndarray:
+    out = np.zeros(max(int(count), 1), np.uint32)
+    rc = _lib().twopaco_read_state(d_workspace or None, int(which), out.ctypes.data, int(count) * 4,
+                                   cuda_stream or None)
+    if rc != OK:
+        raise TwopacoError(rc, "twopaco_read_state")
+    return out[:int(count)]
+
+
+class DeviceBuild:
+    """Device-resident runs over one input, with buffers owned by PyTorch.
+
+    ``bases`` (uint8) and ``offsets`` (n + 1 entries) may be host arrays or
+    CUDA tensors; they are made resident once. ``run()`` launches one full
+    build on ``stream`` (default: the current stream) without synchronising.
+    """
+
+    def __init__(self, bases, offsets, k: int, filter_bits: int, rounds: int = 1,
+                 options: Optional[Options] = None, device: str = "cuda"):
+        import torch
+        self.torch = torch
+        self.k, self.filter_bits, self.rounds = int(k), int(filter_bits), int(rounds)
+        self.options = options or Options()
+        dev = torch.device(device)
+        self.bases = torch.as_tensor(np.asarray(bases, dtype=np.uint8) if not torch.is_tensor(bases)
+                                     else bases, device=dev).contiguous()
+        off = offsets.cpu().numpy() if torch.is_tensor(offsets) else np.asarray(offsets)
+        off = off.astype(np.uint64)
+        self.n_seqs = off.size - 1
+        self.total_bases = int(off[-1])
+        self.positions_upper = int(sum(max(0, int(off[t + 1] - off[t]) - self.k + 1)
+                                       for t in range(self.n_seqs)))
+        self.offsets = torch.as_tensor(off.view(np.int64), device=dev).contiguous()
+        self.ws_bytes = twopaco_workspace_size(self.total_bases, self.n_seqs, self.k,
+                                               self.filter_bits, self.rounds, self.options)
+        self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=dev)
+        base = self.workspace.data_ptr()
+        self.ws_ptr = (base + 255) // 256 * 256
+        self.out_offsets = torch.zeros(self.n_seqs + 1, dtype=torch.int64, device=dev)
+        self.capacity = max(self.positions_upper, 1)
+        self.out_positions = torch.empty(self.capacity, dtype=torch.int64, device=dev)
+
+    def _stream(self, stream) -> int:
+        if stream is None:
+            stream = self.torch.cuda.current_stream()
+        return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+    def run(self, stream=None) -> None:
+        opt = Options(self.options.hashes, self.options.both_strands, self.options.partition_bins,
+                      self.options.table_slots, self._stream(stream))
+        twopaco_run_device(self.bases.data_ptr() if self.total_bases else 0, self.offsets.data_ptr(),
+                           self.n_seqs, self.total_bases, self.k, self.filter_bits, self.rounds, opt,
+                           self.ws_ptr, self.ws_bytes, self.out_offsets.data_ptr(),
+                           self.out_positions.data_ptr(), self.capacity)
+
+    def stats(self, stream=None, check: bool = True) -> Dict[str, int]:
+        return twopaco_read_stats(self.ws_ptr, self._stream(stream), check)
+
+    def state(self, which: int, count: int, stream=None) -> np.ndarray:
+        return twopaco_read_state(self.ws_ptr, which, count, self._stream(stream))
+
+    def result(self, stream=None) -> List[np.ndarray]:
+        self.stats(stream)
+        off = self.out_offsets.cpu().numpy().view(np.uint64)
+        pos = self.out_positions[: int(off[-1])].cpu().numpy().view(np.uint64)
+        return [pos[off[t]:off[t + 1]] for t in range(self.n_seqs)]

@@ -1,0 +1,60 @@
+"""The C-ABI library builds, loads and exports every declared symbol (no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "twopaco.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(twopaco_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for want in ("twopaco_build", "twopaco_build_ex", "twopaco_result_free", "twopaco_strerror",
+                 "twopaco_run_device", "twopaco_workspace_size", "twopaco_read_stats"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1602_05856_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_side_argument_checks():
+    from paper_1602_05856_gb300 import build, twopaco as T
+    build.build()
+    assert T.twopaco_strerror(T.EINVAL) == "invalid argument"
+    ok = T.twopaco_workspace_size(1000, 2, 25, 1 << 20, 1)
+    assert ok > (1 << 20) // 8
+    bad = [dict(k=0), dict(k=64), dict(filter_bits=100), dict(filter_bits=3 << 10), dict(rounds=0),
+           dict(options=T.Options(hashes=0)), dict(options=T.Options(hashes=9)),
+           dict(options=T.Options(partition_bins=1000)), dict(rounds=8, options=T.Options(partition_bins=4))]
+    for b in bad:
+        args = dict(total_bases=1000, n_seqs=2, k=25, filter_bits=1 << 20, rounds=1)
+        args.update(b)
+        with pytest.raises(T.TwopacoError) as e:
+            T.twopaco_workspace_size(**args)
+        assert e.value.code == T.EINVAL
+    # a null workspace is rejected before anything is launched
+    with pytest.raises(T.TwopacoError) as e:
+        T.twopaco_run_device(0, 0, 0, 0, 25, 1 << 20, 1, None, 0, 0, 0, 0, 0)
+    assert e.value.code == T.EINVAL
+
+
+def test_workspace_grows_with_input_and_filter():
+    from paper_1602_05856_gb300 import build, twopaco as T
+    build.build()
+    a = T.twopaco_workspace_size(10**6, 4, 25, 1 << 20, 1)
+    b = T.twopaco_workspace_size(10**7, 4, 25, 1 << 20, 1)
+    c = T.twopaco_workspace_size(10**6, 4, 25, 1 << 26, 1)
+    d = T.twopaco_workspace_size(10**6, 4, 63, 1 << 20, 1)
+    assert b > a and c - a >= ((1 << 26) - (1 << 20)) // 8 and d > a

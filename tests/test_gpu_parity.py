@@ -1,0 +1,269 @@
+"""GPU path vs the CPU oracle, through the C ABI. Integer work: bit-exact.
+
+Every comparison is element by element: the junction positions of every
+string, and (where stated) the pass-1 candidate bitmap C_temp against the
+oracle's restatement of the same filter.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1602_05856_gb300 import genomes as G
+from tests import brute
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1602_05856_gb300 import build
+    build.build()
+    from paper_1602_05856_gb300 import twopaco
+    twopaco.load()
+
+
+def T():
+    from paper_1602_05856_gb300 import twopaco
+    return twopaco
+
+
+def _eq(got, want):
+    assert len(got) == len(want)
+    for t, (g, w) in enumerate(zip(got, want)):
+        g = np.asarray(g, dtype=np.uint64)
+        w = np.asarray(w, dtype=np.uint64)
+        if not np.array_equal(g, w):
+            extra = np.setdiff1d(g, w)[:10]
+            miss = np.setdiff1d(w, g)[:10]
+            raise AssertionError(f"string {t}: {g.size} vs {w.size} junctions; "
+                                 f"extra {extra}, missing {miss}")
+
+
+def _bits_to_marks(words: np.ndarray, m: int) -> np.ndarray:
+    b = np.unpackbits(words.view(np.uint8), bitorder="little")
+    return b[:m]
+
+
+@functools.lru_cache(maxsize=None)
+def _named(name, scale):
+    return G.named_set(name, scale)
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_named(name, scale, k):
+    seqs = _named(name, scale)
+    return O.junctions(G.concat(seqs), k)
+
+
+# --- worked example ----------------------------------------------------------
+
+@pytest.mark.parametrize("both,k,want", [
+    (False, 2, [[0, 4, 7], [0, 4, 7]]),
+    (True, 2, [[0, 2, 3, 4, 6, 7], [0, 2, 3, 4, 7]]),
+    (True, 3, [[0, 3, 4, 5, 6], [0, 3, 6]]),
+])
+def test_fig1_worked_example(both, k, want):
+    for bits, h in ((256, 1), (1 << 16, 4)):
+        got, st = T().twopaco_build_ex(["TGGCACGTC", "TGGCACTTC"], k, bits, 1,
+                                       T().Options(hashes=h, both_strands=both))
+        _eq(got, want)
+        assert st["pass2_marks"] == sum(len(w) for w in want)
+
+
+# --- random small inputs, every k path -------------------------------------------
+
+KS = [1, 2, 3, 4, 5, 7, 8, 12, 15, 16, 17, 24, 25, 31, 32, 33, 40, 47, 48, 62, 63]
+
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("both", [True, False])
+def test_random_inputs_match_oracle(k, both):
+    rng = np.random.default_rng(1000 + k + 100 * both)
+    seqs = [bytes(s).decode() for s in G.random_strings(int(rng.integers(1 << 30)), 6, 0, 3000,
+                                                        b"ACGT")]
+    seqs += [bytes(s).decode() for s in G.random_strings(int(rng.integers(1 << 30)), 3, 50, 700,
+                                                         b"AC")]
+    seqs.append(brute.revcomp(seqs[0]))
+    seqs.append(seqs[1][100:900] + seqs[2][:400])
+    seqs.append("A" * (k + 5))
+    want = O.junctions(seqs, k, both_strands=both)
+    for bits, h, rounds in ((256, 1, 1), (1 << 12, 3, 1), (1 << 18, 8, 1), (1 << 14, 4, 3)):
+        got, _ = T().twopaco_build_ex(seqs, k, bits, rounds,
+                                      T().Options(hashes=h, both_strands=both, partition_bins=64))
+        _eq(got, want)
+
+
+def test_small_strings_match_brute_force():
+    for seed in range(20):
+        k = 1 + seed % 9
+        seqs = [bytes(s).decode() for s in G.random_strings(seed, 4, 0, 40, b"ACG")]
+        got, _ = T().twopaco_build_ex(seqs, k, 1 << 10, 1, T().Options(hashes=2))
+        _eq(got, brute.junction_positions(seqs, k, True))
+
+
+# --- pass 1 against the oracle's model of the same filter ------------------------
+
+@pytest.mark.parametrize("k,bits,h,both", [(25, 1 << 20, 3, True), (31, 1 << 18, 4, True),
+                                           (9, 1 << 14, 2, False), (47, 1 << 20, 8, True),
+                                           (63, 1 << 16, 5, True)])
+def test_pass1_candidates_bit_exact(k, bits, h, both):
+    seqs = _named("plain_single", 0.1)
+    bases, off = G.concat(seqs)
+    run = T().DeviceBuild(bases, off, k, bits, 1, T().Options(hashes=h, both_strands=both))
+    run.run()
+    got = run.result()
+    st = run.stats()
+    m = int(off[-1])
+    ctemp = _bits_to_marks(run.state(T().STATE_CANDIDATES, (m + 31) // 32), m)
+    marks, _, active, kept = O.pass1_marks((bases, off), k, bits, h, both_strands=both)
+    assert np.array_equal(ctemp, marks)
+    assert st["pass1_marks"] == kept and st["positions"] == active
+    _eq(got, O.junctions((bases, off), k, both_strands=both))
+
+
+# --- the named workloads ------------------------------------------------------------
+
+def test_plain_single_full_size():
+    """4 related 1 Mbp genomes, k=25, 2^24-bit filter, 3 hashes, 1 round."""
+    seqs = _named("plain_single", 1.0)
+    bases, off = G.concat(seqs)
+    run = T().DeviceBuild(bases, off, 25, 1 << 24, 1, T().Options(hashes=3))
+    run.run()
+    _eq(run.result(), _oracle_named("plain_single", 1.0, 25))
+    m = int(off[-1])
+    ctemp = _bits_to_marks(run.state(T().STATE_CANDIDATES, (m + 31) // 32), m)
+    marks, _, _, kept = O.pass1_marks((bases, off), 25, 1 << 24, 3)
+    assert np.array_equal(ctemp, marks) and run.stats()["pass1_marks"] == kept
+
+
+@pytest.mark.parametrize("k", [25, 31])
+def test_bacterial_set_full_size(k):
+    """7 genomes of 4.6-5.6 Mbp, 2^28-bit filter, 4 hashes: the benchmarked launch."""
+    seqs = _named("bacterial_set", 1.0)
+    bases, off = G.concat(seqs)
+    run = T().DeviceBuild(bases, off, k, 1 << 28, 1, T().Options(hashes=4))
+    run.run()
+    run.run()  # a second run on the same workspace must not see the first
+    _eq(run.result(), _oracle_named("bacterial_set", 1.0, k))
+
+
+@pytest.mark.parametrize("k", [15, 25, 31, 63])
+def test_batched_set_scaled(k):
+    """62 uneven genomes (scaled to ~250 kbp each) for every k of the batched workload."""
+    seqs = _named("batched_set", 0.05)
+    got, st = T().twopaco_build_ex(seqs, k, 1 << 24, 1, T().Options(hashes=4))
+    _eq(got, _oracle_named("batched_set", 0.05, k))
+
+
+# --- invariances -------------------------------------------------------------------
+
+def test_rounds_filter_and_hash_invariance():
+    seqs = _named("plain_single", 0.25)
+    bases, off = G.concat(seqs)
+    want = O.junctions((bases, off), 25)
+    for bits, h, rounds in ((1 << 22, 4, 1), (1 << 22, 4, 2), (1 << 20, 3, 4), (1 << 16, 2, 16),
+                            (256, 1, 1), (1 << 26, 8, 5), (1 << 22, 6, 7)):
+        run = T().DeviceBuild(bases, off, 25, bits, rounds,
+                              T().Options(hashes=h, partition_bins=1024))
+        run.run()
+        _eq(run.result(), want)
+        st = run.stats()
+        assert st["pass2_marks"] == sum(w.size for w in want)
+        if rounds > 1:
+            bins = run.state(T().STATE_BINS, 1024)
+            cuts = run.state(T().STATE_CUTS, rounds + 1)
+            assert list(cuts) == [int(c) for c in O.partition_cuts(bins, rounds)]
+            # the counters count distinct k-mers, less those the pre-pass filter
+            # already showed as present
+            assert int(bins.sum()) <= O.junction_flags((bases, off), 25)[2]
+
+
+# --- edge cases ---------------------------------------------------------------------
+
+def test_empty_and_short_inputs():
+    got, st = T().twopaco_build_ex([], 25, 1 << 16, 1)
+    assert got == [] and st["pass2_marks"] == 0
+    got, st = T().twopaco_build_ex(["", "ACGT", "A" * 24], 25, 1 << 16, 1)
+    assert [g.size for g in got] == [0, 0, 0] and st["positions"] == 0
+    got, _ = T().twopaco_build_ex(["ACGTACGTAC", "CCCCCCCCCC", "A"], 10, 1 << 16, 1)
+    _eq(got, [[0], [0], []])
+
+
+def test_many_tiny_strings():
+    rng = np.random.default_rng(5)
+    seqs = [bytes(s).decode() for s in G.random_strings(77, 3000, 0, 60, b"ACGT")]
+    for i in range(0, 3000, 7):  # shared pieces, so junctions appear inside strings
+        seqs[i] = seqs[i][:30] + seqs[(i * 13) % 3000][:40]
+    k = int(rng.integers(11, 16))
+    got, _ = T().twopaco_build_ex(seqs, k, 1 << 16, 1, T().Options(hashes=3))
+    _eq(got, O.junctions(seqs, k))
+
+
+def test_lowercase_input():
+    seqs = [bytes(s).decode() for s in G.random_strings(8, 3, 500, 900, b"ACGT")]
+    low = [s.lower() if i % 2 else s for i, s in enumerate(seqs)]
+    got, _ = T().twopaco_build_ex(low, 13, 1 << 16, 1)
+    _eq(got, O.junctions(seqs, 13))
+
+
+def test_unaligned_device_input():
+    import torch
+    seqs = _named("plain_single", 0.01)
+    bases, off = G.concat(seqs)
+    k, bits = 21, 1 << 18
+    raw = torch.zeros(bases.size + 64, dtype=torch.uint8, device="cuda")
+    raw[3:3 + bases.size] = torch.from_numpy(bases).cuda()
+    d_off = torch.from_numpy(off.view(np.int64)).cuda()
+    ws = T().twopaco_workspace_size(bases.size, len(seqs), k, bits, 1)
+    wst = torch.empty(ws + 256, dtype=torch.uint8, device="cuda")
+    wsp = (wst.data_ptr() + 255) // 256 * 256
+    out_off = torch.zeros(len(seqs) + 1, dtype=torch.int64, device="cuda")
+    out_pos = torch.zeros(bases.size, dtype=torch.int64, device="cuda")
+    T().twopaco_run_device(raw.data_ptr() + 3, d_off.data_ptr(), len(seqs), bases.size, k, bits, 1,
+                           None, wsp, ws, out_off.data_ptr(), out_pos.data_ptr(), bases.size)
+    T().twopaco_read_stats(wsp)
+    o = out_off.cpu().numpy()
+    p = out_pos.cpu().numpy()
+    _eq([p[o[t]:o[t + 1]] for t in range(len(seqs))], O.junctions((bases, off), k))
+
+
+def test_bad_base_is_reported():
+    seqs = ["ACGTACGTTTGACCA", "ACGTNACGT", "ACGTX"]
+    with pytest.raises(T().TwopacoError) as e:
+        T().twopaco_build_ex(seqs, 5, 1 << 12, 1)
+    assert e.value.code == T().EBADBASE
+    bases, off = G.concat([np.frombuffer(s.encode(), np.uint8) for s in seqs])
+    run = T().DeviceBuild(bases, off, 5, 1 << 12, 1)
+    run.run()
+    st = run.stats(check=False)
+    assert st["rc"] == T().EBADBASE and st["bad_base_index"] == 15 + 4
+
+
+def test_table_overflow_is_reported_and_recovered():
+    seqs = _named("plain_single", 0.05)
+    bases, off = G.concat(seqs)
+    opts = T().Options(hashes=3, table_slots=1024)
+    run = T().DeviceBuild(bases, off, 25, 1 << 18, 1, opts)
+    run.run()
+    st = run.stats(check=False)
+    assert st["rc"] == T().EOVERFLOW and st["overflow"]
+    got, st = T().twopaco_build_ex(seqs, 25, 1 << 18, 1, opts)  # grows the table and reruns
+    _eq(got, O.junctions((bases, off), 25))
+    assert st["table_slots"] > 1024
+
+
+def test_non_default_stream_and_repeat():
+    import torch
+    seqs = _named("plain_single", 0.05)
+    bases, off = G.concat(seqs)
+    want = O.junctions((bases, off), 25)
+    run = T().DeviceBuild(bases, off, 25, 1 << 20, 2, T().Options(hashes=4, partition_bins=256))
+    s = torch.cuda.Stream()
+    for _ in range(3):
+        run.run(stream=s)
+    _eq(run.result(stream=s), want)
