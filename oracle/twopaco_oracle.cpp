@@ -237,14 +237,12 @@ int oracle_alg1_exact(const uint8_t* seq, const uint64_t* offsets, uint64_t n, i
  *               z ^= z >> 30; z *= 0xbf58476d1ce4e5b9;
  *               z ^= z >> 27; z *= 0x94d049bb133111eb; z ^= z >> 31.
  *   V = hi * 2^64 + lo, the normalized k-mer.
- *   H = mix64(lo ^ mix64(hi));  G = mix64(H ^ 0x9e3779b97f4a7c15)
- *   The filter has b bits = b/256 blocks of eight 32-bit words.
+ *   H = mix64(lo ^ mix64(hi));  G = H * 0x9e3779b97f4a7c15 (mod 2^64)
+ *   The filter has b bits = b/256 blocks of eight 32-bit words; a k-mer
+ *   uses one 64-bit half-pair of its block: 32-bit words 2*o and 2*o + 1.
  *   block = H >> (64 - log2(b/256))  (0 when b = 256)
- *   o     = (G >> 61) & 6           first word used (even)
- *   for u < h: word t_u = (o + u) & 7 of the block, with bit base
- *           base_u = (uint32(G) * SALT[u]) >> 27
- *   SALT[u] = first 32 bits of the fractional part of the cube root of the
- *            (u+1)-th prime, forced odd.
+ *   o     = G >> 62
+ *   for u < h: word t_u = 2*o + (u & 1), bit base base_u = (G >> (57 - 5u)) & 31
  *   item j sets / tests bit (base_u + j) & 31 of word t_u, for every u < h.
  *   items: j = 4a + c for the (predecessor a, successor c) pair of an
  *          occurrence read in the orientation of the normalized form
@@ -267,13 +265,10 @@ uint64_t mix64(uint64_t z) {
   return z;
 }
 
-const uint32_t kSalt[8] = {0x428a2f99u, 0x71374491u, 0xb5c0fbcfu, 0xe9b5dba5u,
-                           0x3956c25bu, 0x59f111f1u, 0x923f82a5u, 0xab1c5ed5u};
-
 struct FilterSpot {
   uint64_t block;
   uint64_t H;
-  uint32_t word[8];  // word index t for u < h
+  uint32_t word[8];  // word index t_u for u < h
   uint32_t base[8];  // bit base for that word
 };
 
@@ -281,13 +276,12 @@ FilterSpot locate(u128 V, int lg_blocks, int h) {
   FilterSpot f;
   uint64_t lo = (uint64_t)V, hi = (uint64_t)(V >> 64);
   f.H = mix64(lo ^ mix64(hi));
-  uint64_t G = mix64(f.H ^ 0x9e3779b97f4a7c15ull);
+  uint64_t G = f.H * 0x9e3779b97f4a7c15ull;
   f.block = lg_blocks ? (f.H >> (64 - lg_blocks)) : 0;
-  uint32_t o = (uint32_t)((G >> 61) & 6);
+  uint32_t o = (uint32_t)(G >> 62);
   for (int u = 0; u < h; ++u) {
-    uint32_t t = (o + (uint32_t)u) & 7u;
-    f.word[u] = t;
-    f.base[u] = ((uint32_t)G * kSalt[u]) >> 27;
+    f.word[u] = 2 * o + ((uint32_t)u & 1u);
+    f.base[u] = (uint32_t)(G >> (57 - 5 * u)) & 31u;
   }
   return f;
 }
