@@ -25,6 +25,7 @@
  *     than k has none.
  *   - Return value: TWOPACO_OK (0) or a negative TWOPACO_E* code.
  *   - k in [1, 63]; filter_bits a power of two >= 256; rounds >= 1;
+ *     total_bases < 2^48;
  *     options->hashes in [1, 8]; options->partition_bins a power of two
  *     >= rounds. Anything else is TWOPACO_EINVAL.
  *   - Calls on different workspaces may run concurrently from different host
@@ -53,6 +54,9 @@ typedef struct twopaco_options {
   int both_strands;        /* 1: comprehensive graph (default); 0: single strand */
   uint32_t partition_bins; /* q of the rounds heuristic, power of two (65536) */
   uint64_t table_slots;    /* pass-2 table capacity in slots; 0 = automatic */
+  uint64_t candidate_records; /* pass-2 candidate list capacity; 0 = automatic
+                                 (a quarter of a round's positions). A round with
+                                 more candidates stays correct but slower. */
   void* cuda_stream;       /* cudaStream_t to launch on, borrowed; NULL = default */
 } twopaco_options;
 

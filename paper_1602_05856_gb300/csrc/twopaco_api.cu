@@ -47,10 +47,16 @@ int validate(uint64_t n_seqs, int k, uint64_t filter_bits, int rounds, const two
   return TWOPACO_OK;
 }
 
+int validate_size(uint64_t total_bases) {
+  return total_bases >= (1ull << 48) ? TWOPACO_EINVAL : TWOPACO_OK;  // positions fit 48 bits
+}
+
 struct Layout {
   uint64_t header, packed, filter, ctemp, cfinal, tile_count, tile_prefix, bins, cuts, table;
+  uint64_t cands, lc, segs;
   uint64_t total;
-  uint64_t packed_words, bitmap_words, n_tiles, table_slots;
+  uint64_t packed_words, bitmap_words, n_tiles, table_slots, cand_cap;
+  int lc_log2;
 };
 
 uint64_t auto_table_slots(uint64_t m, int rounds) {
@@ -87,6 +93,20 @@ Layout layout(uint64_t m, int k, uint64_t filter_bits, int rounds, const twopaco
   at += align_up(((uint64_t)rounds + 1) * 4);
   L.table = at;
   at += align_up(L.table_slots * table_slot_bytes(k));
+  // candidate list: a quarter of the positions of a round by default; a
+  // longer round falls back to walking C_temp
+  const uint64_t per_round = (m + (uint64_t)rounds - 1) / (uint64_t)rounds;
+  L.cand_cap = o.candidate_records ? o.candidate_records
+                                   : (per_round / 4 > (1u << 16) ? per_round / 4 : (1u << 16));
+  L.cands = at;
+  at += align_up(L.cand_cap * cand_record_bytes(k));
+  // linear-counting bitmap: 2^lc_log2 >= the list's capacity (at least 2^16 bits)
+  L.lc_log2 = 16;
+  while ((1ull << L.lc_log2) < L.cand_cap && L.lc_log2 < 36) ++L.lc_log2;
+  L.lc = at;
+  at += align_up((1ull << L.lc_log2) / 8);
+  L.segs = at;
+  at += align_up((uint64_t)kMaxSegments * 4);
   L.total = at;
   return L;
 }
@@ -117,6 +137,11 @@ RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_
   v.bitmap_words = L.bitmap_words;
   v.table = base + L.table;
   v.table_max_slots = L.table_slots;
+  v.cands = reinterpret_cast<uint64_t*>(base + L.cands);
+  v.cand_cap = L.cand_cap;
+  v.lc_bits = reinterpret_cast<uint32_t*>(base + L.lc);
+  v.lc_log2 = L.lc_log2;
+  v.seg_count = reinterpret_cast<uint32_t*>(base + L.segs);
   v.bins = rounds > 1 ? reinterpret_cast<uint32_t*>(base + L.bins) : nullptr;
   v.cuts = reinterpret_cast<uint32_t*>(base + L.cuts);
   v.tile_count = reinterpret_cast<uint32_t*>(base + L.tile_count);
@@ -147,6 +172,7 @@ void twopaco_default_options(twopaco_options* opt) {
   opt->both_strands = 1;
   opt->partition_bins = 65536;
   opt->table_slots = 0;
+  opt->candidate_records = 0;
   opt->cuda_stream = nullptr;
 }
 
@@ -168,7 +194,7 @@ int twopaco_workspace_size(uint64_t total_bases, uint64_t n_seqs, int k, uint64_
   const twopaco_options o = resolve(opt);
   int rc = validate(n_seqs, k, filter_bits, rounds, o);
   if (rc) return rc;
-  if (!bytes) return TWOPACO_EINVAL;
+  if (!bytes || validate_size(total_bases)) return TWOPACO_EINVAL;
   *bytes = layout(total_bases, k, filter_bits, rounds, o).total;
   return TWOPACO_OK;
 }
@@ -180,6 +206,7 @@ int twopaco_run_device(const uint8_t* d_bases, const uint64_t* d_offsets, uint64
   const twopaco_options o = resolve(opt);
   int rc = validate(n_seqs, k, filter_bits, rounds, o);
   if (rc) return rc;
+  if (validate_size(total_bases)) return TWOPACO_EINVAL;
   if (total_bases > 0 && (n_seqs == 0 || !d_bases || !d_offsets)) return TWOPACO_EINVAL;
   if (n_seqs > 0 && !d_offsets) return TWOPACO_EINVAL;
   if (!d_out_offsets || (out_capacity && !d_out_positions)) return TWOPACO_EINVAL;

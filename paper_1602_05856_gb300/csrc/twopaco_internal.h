@@ -16,6 +16,9 @@ struct DevHeader {
   unsigned long long round_kept;   // candidates after pass 1, current round
   unsigned long long table_slots;  // pass-2 table capacity of the current round
   unsigned long long table_max;    // largest capacity used by any round
+  unsigned long long lc_set;       // linear-counting bits set this round
+  unsigned int cand_overflow;      // a warp's list segment ran out of room this round
+  unsigned int round_listed;       // pass 2 of this round reads the list (else C_temp)
   unsigned int overflow;           // table or output out of room
   unsigned int timeout;            // a bounded wait gave up
   // where the last run left its bitmaps and partition state (for inspection)
@@ -51,6 +54,14 @@ struct RunView {
   uint64_t bitmap_words;    // ceil(m/32)
   void* table;              // pass-2 slots
   uint64_t table_max_slots;
+  uint64_t* cands;          // positions of the pass-1 survivors, for pass 2
+  uint64_t cand_cap;        // records the list can hold
+  uint32_t* seg_count;      // candidates per list segment (one segment per probe warp)
+  uint32_t n_segments;      // warps of the probe grid (set per launch)
+  uint64_t seg_cap;         // records per segment (set per launch)
+  uint32_t seg_warps;       // pass-2 warps per segment (set per launch)
+  uint32_t* lc_bits;        // linear-counting bitmap, 2^lc_log2 bits
+  int lc_log2;
   uint32_t* bins;           // partition counters (q), rounds > 1
   uint32_t* cuts;           // rounds + 1 class boundaries
   uint32_t* tile_count;     // emit: junctions per tile
@@ -64,6 +75,7 @@ struct RunView {
 constexpr int kBlock = 256;             // threads per block of the position kernels
 constexpr int kEmitTileWords = 256;     // bitmap words per emit tile (8192 positions)
 constexpr uint64_t kPackPadWords = 8;   // zero words after the packed input
+constexpr uint32_t kMaxSegments = 65536; // candidate-list segments (probe warps) at most
 
 // Kernel launch helpers (twopaco_kernels.cu). Each returns the number of
 // kernels it launched, or -1 after a launch error.
@@ -75,6 +87,9 @@ int launch_emit(const RunView& v, cudaStream_t s);
 
 // Bytes per pass-2 slot for this k.
 inline uint64_t table_slot_bytes(int k) { return k <= 31 ? 16 : 32; }
+
+// Bytes per candidate record (a global position).
+inline uint64_t cand_record_bytes(int) { return 8; }
 
 // Process-wide count of kernels launched by the library.
 void count_launches(int n);

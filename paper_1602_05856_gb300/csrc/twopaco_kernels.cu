@@ -3,10 +3,14 @@
 // One run = pack, then per round (Algorithm 3, section "Multiple Rounds")
 // the two passes of Algorithm 2 (Filter-Junctions-Two-Pass), each an
 // instance of Algorithm 1 (Filter-Junctions): an insert loop and a probe
-// loop over every position, separated by a kernel boundary (the barrier of
-// section "Parallelization Scheme"); then one emit of the junction
-// positions. Every kernel walks positions with one thread per position, so a
-// warp covers 32 consecutive positions and its ballot is one bitmap word.
+// loop, separated by a kernel boundary (the barrier of section
+// "Parallelization Scheme"); then one emit of the junction positions.
+//
+// The first pass visits every position. A thread takes kR consecutive
+// positions and rolls the forward and reverse-complement k-mer words from
+// one to the next, so a warp covers 32 * kR consecutive positions. The
+// second pass visits only the candidates the first pass left, from a compact
+// list.
 //
 // Encoding: A,C,G,T = 0,1,2,3, 16 bases per 32-bit word, first base in the
 // two most significant bits. A k-mer is the integer with its first base most
@@ -17,11 +21,10 @@
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 namespace twopaco {
-
-constexpr int TWOPACO_ECUDA_INTERNAL = -5;
 
 namespace {
 
@@ -69,6 +72,8 @@ struct Timed {
   }
 };
 
+constexpr int kR = 8;  // consecutive positions per thread in the first pass
+
 // ---------------------------------------------------------------------------
 // k-mer words
 // ---------------------------------------------------------------------------
@@ -91,6 +96,17 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z;
 }
 
+template <int KW>
+__device__ __forceinline__ uint64_t key_hash(const Key& v) {
+  return KW == 1 ? mix64(v.lo) : mix64(v.lo ^ mix64(v.hi));
+}
+
+// Second hash word: H times the 64-bit golden ratio; only its high bits are used.
+__device__ __forceinline__ uint64_t second_hash(uint64_t H) { return H * 0x9e3779b97f4a7c15ull; }
+
+// Start slot of a k-mer in the pass-2 table (bits above the partition bins).
+__device__ __forceinline__ uint64_t slot_hash(uint64_t H) { return H >> 16; }
+
 // Reverse the order of the 32 two-bit groups of x.
 __device__ __forceinline__ uint64_t rev_pairs(uint64_t x) {
   const uint64_t b = __brevll(x);
@@ -101,26 +117,28 @@ __device__ __forceinline__ uint32_t base_at(const uint32_t* __restrict__ packed,
   return (__ldg(packed + (g >> 4)) >> (30u - 2u * (uint32_t)(g & 15))) & 3u;
 }
 
-// The k-mer starting at base g and the base right after it. KW = 1 for
-// k <= 31 (one 64-bit word), 2 for 32 <= k <= 63.
-template <int KW>
-__device__ __forceinline__ Key load_kmer(const uint32_t* __restrict__ packed, uint64_t g, int k,
-                                         uint32_t* succ) {
+// 32 bases starting at base g, first base in the two most significant bits.
+__device__ __forceinline__ uint64_t bases32(const uint32_t* __restrict__ packed, uint64_t g) {
   const uint32_t* p = packed + (g >> 4);
   const uint32_t o2 = 2u * (uint32_t)(g & 15);
-  const uint32_t w0 = __ldg(p), w1 = __ldg(p + 1), w2 = __ldg(p + 2);
-  uint64_t a = ((uint64_t)w0 << 32) | w1;  // bases 16w .. 16w+31
-  if (o2) a = (a << o2) | (w2 >> (32u - o2));  // bases g .. g+31
+  const uint32_t w0 = __ldg(p), w1 = __ldg(p + 1);
+  uint64_t a = ((uint64_t)w0 << 32) | w1;
+  if (o2) a = (a << o2) | (__ldg(p + 2) >> (32u - o2));
+  return a;
+}
+
+// The k-mer starting at base g. KW = 1 for k <= 31 (one 64-bit word), 2 for
+// 32 <= k <= 63.
+template <int KW>
+__device__ __forceinline__ Key load_kmer(const uint32_t* __restrict__ packed, uint64_t g, int k) {
+  const uint64_t a = bases32(packed, g);
   Key v;
   if (KW == 1) {
     v.hi = 0;
     v.lo = a >> (64 - 2 * k);
-    *succ = (uint32_t)(a >> (62 - 2 * k)) & 3u;
   } else {
-    const uint32_t w3 = __ldg(p + 3), w4 = __ldg(p + 4);
-    uint64_t b = ((uint64_t)w2 << 32) | w3;
-    if (o2) b = (b << o2) | (w4 >> (32u - o2));  // bases g+32 .. g+63
-    const int sh = 128 - 2 * k;                  // 2 .. 64
+    const uint64_t b = bases32(packed, g + 32);
+    const int sh = 128 - 2 * k;  // 2 .. 64
     if (sh == 64) {
       v.hi = 0;
       v.lo = a;
@@ -128,7 +146,6 @@ __device__ __forceinline__ Key load_kmer(const uint32_t* __restrict__ packed, ui
       v.hi = a >> sh;
       v.lo = (b >> sh) | (a << (64 - sh));
     }
-    *succ = (uint32_t)(b >> (62 - 2 * (k - 32))) & 3u;
   }
   return v;
 }
@@ -154,12 +171,23 @@ __device__ __forceinline__ Key revcomp(const Key& v, int k) {
   return r;
 }
 
+// Slide the k-mer one base to the right: f gains base b at its end, r (the
+// reverse complement) gains 3 - b at its start.
 template <int KW>
-__device__ __forceinline__ uint64_t key_hash(const Key& v) {
-  return KW == 1 ? mix64(v.lo) : mix64(v.lo ^ mix64(v.hi));
+__device__ __forceinline__ void roll(Key& f, Key& r, uint32_t b, int k) {
+  if (KW == 1) {
+    f.lo = ((f.lo << 2) | b) & ((1ull << (2 * k)) - 1ull);
+    r.lo = (r.lo >> 2) | ((uint64_t)(3u - b) << (2 * k - 2));
+  } else {
+    const int hb = 2 * k - 64;  // bits of the high word, 0 .. 62
+    f.hi = ((f.hi << 2) | (f.lo >> 62)) & ((1ull << hb) - 1ull);
+    f.lo = (f.lo << 2) | b;
+    r.lo = (r.lo >> 2) | (r.hi << 62);
+    r.hi >>= 2;
+    if (hb >= 2) r.hi |= (uint64_t)(3u - b) << (hb - 2);
+    else r.lo |= (uint64_t)(3u - b) << 62;
+  }
 }
-
-__device__ __forceinline__ uint64_t second_hash(uint64_t H) { return mix64(H ^ 0x9e3779b97f4a7c15ull); }
 
 // ---------------------------------------------------------------------------
 // Positions and occurrences
@@ -189,20 +217,14 @@ struct Occ {
 };
 
 template <int KW>
-__device__ __forceinline__ bool read_occurrence(const RunView& v, uint64_t g, Occ* oc) {
-  const Bounds b = seq_bounds(v, g);
-  if (g + (uint64_t)v.k > b.end) return false;  // no k-mer starts here
-  uint32_t succ;
-  const Key f = load_kmer<KW>(v.packed, g, v.k, &succ);
-  const bool has_pred = g > b.start, has_succ = g + (uint64_t)v.k < b.end;
-  const uint32_t pred = has_pred ? base_at(v.packed, g - 1) : 0u;
-  const Key r = v.both ? revcomp<KW>(f, v.k) : f;
+__device__ __forceinline__ void make_occ(const RunView& v, const Key& f, const Key& r,
+                                         uint32_t pred, uint32_t succ, bool sentinel, Occ* oc) {
   const bool use_f = !v.both || !key_less(r, f);  // f is the normalized form
   const bool use_r = v.both && !key_less(f, r);   // r is (palindromes: both)
   oc->key = use_f ? f : r;
   oc->H = key_hash<KW>(oc->key);
-  oc->sentinel = !has_pred || !has_succ;
-  if (oc->sentinel) {
+  oc->sentinel = sentinel;
+  if (sentinel) {
     oc->items = 1u << 16;
     oc->tbits = 1u << 8;
   } else {
@@ -219,7 +241,69 @@ __device__ __forceinline__ bool read_occurrence(const RunView& v, uint64_t g, Oc
     oc->items = items;
     oc->tbits = tb;
   }
+}
+
+// The occurrence at global position g, read from scratch; false if no k-mer
+// starts at g.
+template <int KW>
+__device__ __forceinline__ bool read_occurrence(const RunView& v, uint64_t g, Occ* oc) {
+  const Bounds b = seq_bounds(v, g);
+  if (g + (uint64_t)v.k > b.end) return false;
+  const Key f = load_kmer<KW>(v.packed, g, v.k);
+  const bool has_pred = g > b.start, has_succ = g + (uint64_t)v.k < b.end;
+  const uint32_t pred = has_pred ? base_at(v.packed, g - 1) : 0u;
+  const uint32_t succ = has_succ ? base_at(v.packed, g + v.k) : 0u;
+  const Key r = v.both ? revcomp<KW>(f, v.k) : f;
+  make_occ<KW>(v, f, r, pred, succ, !has_pred || !has_succ, oc);
   return true;
+}
+
+// Visit the kR consecutive positions p0 .. p0 + kR - 1 (p0 < m), rolling the
+// k-mer from each position to the next within a string and reading it from
+// scratch after a string boundary. fn(i, p, valid, occ) runs for every i,
+// with i a compile-time constant once unrolled.
+template <int KW, typename F>
+__device__ __forceinline__ void walk(const RunView& v, uint64_t p0, F&& fn) {
+  const int k = v.k;
+  Bounds b = seq_bounds(v, p0);
+  // bases p0 + k .. p0 + k + kR - 1: the successor of each position, which is
+  // also the base that enters the k-mer when it slides to the next position
+  const uint32_t next = (uint32_t)(bases32(v.packed, p0 + (uint64_t)k) >> 32);
+  Key f{0, 0}, r{0, 0};
+  bool fresh = true;
+#pragma unroll
+  for (int i = 0; i < kR; ++i) {
+    const uint64_t p = p0 + i;
+    Occ oc;
+    bool valid = false;
+    if (p < v.m) {
+      if (p >= b.end) {
+        b = seq_bounds(v, p);
+        fresh = true;
+      }
+      if (p + (uint64_t)k <= b.end) {
+        valid = true;
+        uint32_t pred;
+        if (fresh) {
+          f = load_kmer<KW>(v.packed, p, k);
+          if (v.both) r = revcomp<KW>(f, k);
+          pred = p > b.start ? base_at(v.packed, p - 1) : 0u;
+          fresh = false;
+        } else {
+          // the first base of the previous k-mer
+          if (KW == 1) pred = (uint32_t)(f.lo >> (2 * k - 2)) & 3u;
+          else pred = (uint32_t)(k == 32 ? f.lo >> 62 : f.hi >> (2 * k - 66)) & 3u;
+          roll<KW>(f, r, i > 0 ? (next >> (32 - 2 * i)) & 3u : 0u, k);
+        }
+        const uint32_t succ = (next >> (30 - 2 * i)) & 3u;
+        const bool sentinel = p == b.start || p + (uint64_t)k == b.end;
+        make_occ<KW>(v, f, v.both ? r : f, pred, succ, sentinel, &oc);
+      } else {
+        fresh = true;
+      }
+    }
+    fn(i, p, valid, oc);
+  }
 }
 
 __device__ __forceinline__ bool in_round(const RunView& v, uint64_t H, int round) {
@@ -228,73 +312,45 @@ __device__ __forceinline__ bool in_round(const RunView& v, uint64_t H, int round
 }
 
 // ---------------------------------------------------------------------------
-// Split-block filter: a block is one 32-byte sector of eight 32-bit words.
-// A k-mer picks a block (top bits of H), an even first word o and, for each
-// of its h words, a bit base; item j sets bit (base + j) & 31 of each word.
-// All 17 items of one k-mer therefore sit in one sector: one load answers
-// every probe of the k-mer, and an insert is at most ceil(h/2) 64-bit ORs.
+// First-pass filter: b bits = b/256 blocks of four 64-bit words. A k-mer owns
+// one 64-bit word: block from the top bits of H, word o from the top two bits
+// of G. Each of its h bits u has a 5-bit base cut from G, in the low (u even)
+// or high (u odd) half; item j sets bit (base_u + j) & 31 of that half. All 17
+// items of a k-mer live in one word: an insert is one 64-bit atomic OR and a
+// probe is one 8-byte load that answers all of its items at once.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ uint32_t salt(int u) {
-  // First 32 fractional bits of the cube roots of 2, 3, 5, 7, 11, 13, 17, 19,
-  // made odd.
-  constexpr uint32_t s[8] = {0x428a2f99u, 0x71374491u, 0xb5c0fbcfu, 0xe9b5dba5u,
-                             0x3956c25bu, 0x59f111f1u, 0x923f82a5u, 0xab1c5ed5u};
-  return s[u];
-}
-
-struct Spot {
-  unsigned long long* blk;  // the block's four 64-bit words
-  uint32_t o2;              // first logical 64-bit pair (word o = 2 * o2)
-  uint32_t base[8];
-};
-
-__device__ __forceinline__ Spot filter_spot(const RunView& v, uint64_t H) {
-  Spot s;
-  const uint64_t G = second_hash(H);
+__device__ __forceinline__ unsigned long long* filter_word(const RunView& v, uint64_t H, uint64_t G) {
   const uint64_t block = v.lg_blocks ? (H >> (64 - v.lg_blocks)) : 0ull;
-  s.blk = v.filter + block * 4;
-  s.o2 = (uint32_t)(G >> 62);
-  const uint32_t g32 = (uint32_t)G;
+  return v.filter + block * 4 + (G >> 62);
+}
+
+__device__ __forceinline__ uint32_t bit_base(uint64_t G, int u) {
+  const int sh = 57 - 5 * u;  // u is a compile-time constant once unrolled
+  if (sh >= 32) return ((uint32_t)(G >> 32) >> (sh - 32)) & 31u;
+  return (uint32_t)(G >> sh) & 31u;
+}
+
+template <int HB>
+__device__ __forceinline__ uint64_t item_bits(uint64_t G, uint32_t j) {
+  uint32_t lo = 0, hi = 0;
 #pragma unroll
-  for (int u = 0; u < 8; ++u) s.base[u] = (g32 * salt(u)) >> 27;
-  return s;
+  for (int u = 0; u < HB; ++u) {
+    const uint32_t b = 1u << ((bit_base(G, u) + j) & 31u);
+    if (u & 1) hi |= b; else lo |= b;
+  }
+  return ((uint64_t)hi << 32) | lo;
 }
 
-// Bits of item j in logical 64-bit pair U (logical words 2U and 2U+1).
-__device__ __forceinline__ uint64_t item_bits(const Spot& s, int U, uint32_t j, int h) {
-  uint64_t m = 0;
-  if (2 * U < h) m |= 1ull << ((s.base[2 * U] + j) & 31u);
-  if (2 * U + 1 < h) m |= (1ull << ((s.base[2 * U + 1] + j) & 31u)) << 32;
-  return m;
-}
-
-__device__ __forceinline__ uint64_t pick4(const uint64_t P[4], uint32_t i) {
-  const uint64_t x = (i & 1) ? P[1] : P[0];
-  const uint64_t y = (i & 1) ? P[3] : P[2];
-  return (i & 2) ? y : x;
-}
-
-__device__ __forceinline__ void load_block(const unsigned long long* blk, uint64_t P[4]) {
-  const ulonglong2 a = __ldcg(reinterpret_cast<const ulonglong2*>(blk));
-  const ulonglong2 b = __ldcg(reinterpret_cast<const ulonglong2*>(blk) + 1);
-  P[0] = a.x;
-  P[1] = a.y;
-  P[2] = b.x;
-  P[3] = b.y;
-}
-
-// Bit j of the result: item j is present (all of its h bits are set).
-__device__ __forceinline__ uint32_t present_items(const Spot& s, const uint64_t P[4], int h) {
+// Bit j of the result: item j is present (all of its HB bits are set).
+template <int HB>
+__device__ __forceinline__ uint32_t present_items(uint64_t G, uint64_t w) {
+  const uint32_t lo = (uint32_t)w, hi = (uint32_t)(w >> 32);
   uint32_t pres = 0x1FFFFu;
 #pragma unroll
-  for (int U = 0; U < 4; ++U) {
-    if (2 * U < h) {
-      const uint64_t L = pick4(P, (s.o2 + U) & 3u);
-      const uint32_t lo = (uint32_t)L, hi = (uint32_t)(L >> 32);
-      pres &= __funnelshift_r(lo, lo, s.base[2 * U]);
-      if (2 * U + 1 < h) pres &= __funnelshift_r(hi, hi, s.base[2 * U + 1]);
-    }
+  for (int u = 0; u < HB; ++u) {
+    const uint32_t x = (u & 1) ? hi : lo;
+    pres &= __funnelshift_r(x, x, bit_base(G, u));
   }
   return pres & 0x1FFFFu;
 }
@@ -340,9 +396,9 @@ __device__ __forceinline__ void cas128(unsigned long long* addr, uint64_t cmp_lo
 // Insert (key, bits); false if every slot was tried (the table is full).
 template <int KW>
 __device__ __forceinline__ bool table_insert(const RunView& v, uint64_t cap, const Key& key,
-                                             uint64_t G, uint32_t bits) {
+                                             uint64_t start, uint32_t bits) {
   const uint64_t mask = cap - 1;
-  uint64_t i = G & mask;
+  uint64_t i = start & mask;
   for (uint64_t probe = 0; probe < cap; ++probe, i = (i + 1) & mask) {
     unsigned int* mword;
     if (KW == 1) {
@@ -370,15 +426,15 @@ __device__ __forceinline__ bool table_insert(const RunView& v, uint64_t cap, con
 
 // Mask of key, or -1 if absent.
 template <int KW>
-__device__ __forceinline__ int table_find(const RunView& v, uint64_t cap, const Key& key, uint64_t G) {
+__device__ __forceinline__ int table_find(const RunView& v, uint64_t cap, const Key& key, uint64_t start) {
   const uint64_t mask = cap - 1;
-  uint64_t i = G & mask;
+  uint64_t i = start & mask;
   for (uint64_t probe = 0; probe < cap; ++probe, i = (i + 1) & mask) {
     if (KW == 1) {
       const Slot1* s = static_cast<const Slot1*>(v.table) + i;
-      const unsigned long long cur = __ldcg(&s->key);
-      if (cur == key.lo) return (int)__ldcg(&s->mask);
-      if (cur == kEmpty) return -1;
+      const ulonglong2 w = __ldcg(reinterpret_cast<const ulonglong2*>(s));
+      if (w.x == key.lo) return (int)(unsigned int)w.y;
+      if (w.x == kEmpty) return -1;
     } else {
       const Slot2* s = static_cast<const Slot2*>(v.table) + i;
       const ulonglong2 w = __ldcg(reinterpret_cast<const ulonglong2*>(&s->w0));
@@ -389,8 +445,12 @@ __device__ __forceinline__ int table_find(const RunView& v, uint64_t cap, const 
   return -1;
 }
 
+__device__ __forceinline__ bool is_junction_mask(int mk) {
+  return ((mk >> 8) & 1) || __popc(mk & 15) > 1 || __popc((mk >> 4) & 15) > 1;
+}
+
 // ---------------------------------------------------------------------------
-// Block reductions (blockDim.x == kBlock)
+// Reductions
 // ---------------------------------------------------------------------------
 
 template <typename T>
@@ -400,7 +460,7 @@ __device__ __forceinline__ T warp_sum(T x) {
   return x;
 }
 
-// Exclusive scan of x over the block; *total receives the block sum.
+// Exclusive scan of x over the block (blockDim.x == kBlock); *total gets the sum.
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* total) {
   __shared__ uint32_t warp_tot[kBlock / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -424,6 +484,20 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* t
   return before + inc - x;
 }
 
+// Sum a counter over the block's threads into *dst (one atomic per block).
+__device__ __forceinline__ void block_add(unsigned long long x, unsigned long long* dst) {
+  __shared__ unsigned long long part[kBlock / 32];
+  x = warp_sum(x);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < kBlock / 32; ++w) t += part[w];
+    if (t) atomicAdd(dst, t);
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
@@ -436,6 +510,9 @@ __global__ void init_kernel(RunView v) {
     h->pass1_kept = 0;
     h->pass2_kept = 0;
     h->round_kept = 0;
+    h->lc_set = 0;
+    h->cand_overflow = 0;
+    h->round_listed = 0;
     h->table_slots = 0;
     h->table_max = 0;
     h->overflow = 0;
@@ -467,7 +544,7 @@ __device__ __forceinline__ uint32_t pack4(uint32_t x, uint32_t* bad) {
   return ((c & 3u) << 6) | (((c >> 8) & 3u) << 4) | (((c >> 16) & 3u) << 2) | ((c >> 24) & 3u);
 }
 
-// Section 8(a) step a0: ASCII -> 2-bit words, 16 bytes (one 128-bit load) per thread.
+// ASCII -> 2-bit words, 16 bytes (one 128-bit load) per thread.
 __global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
   const bool vec = (reinterpret_cast<uintptr_t>(v.bases) & 15) == 0;
   const uint64_t stride = (uint64_t)gridDim.x * kBlock;
@@ -499,99 +576,144 @@ __global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
 }
 
 // Algorithm 1, insert loop, first pass: every active position records its
-// item(s) in the filter; a 64-bit OR is skipped when its bits are already set.
-template <int KW, bool ROUNDS>
+// item(s) in its k-mer's filter word with one atomic OR.
+template <int KW, bool ROUNDS, int HB>
 __global__ void __launch_bounds__(kBlock) pass1_insert_kernel(RunView v, int round) {
-  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
-  for (uint64_t g = (uint64_t)blockIdx.x * kBlock + threadIdx.x; g < v.m; g += stride) {
-    Occ oc;
-    if (!read_occurrence<KW>(v, g, &oc)) continue;
-    if (ROUNDS && !in_round(v, oc.H, round)) continue;
-    const Spot s = filter_spot(v, oc.H);
-    uint64_t P[4];
-    load_block(s.blk, P);
-    const uint32_t j1 = __ffs(oc.items) - 1, j2 = 31 - __clz(oc.items);
-#pragma unroll
-    for (int U = 0; U < 4; ++U) {
-      if (2 * U < v.hashes) {
-        const uint64_t m = item_bits(s, U, j1, v.hashes) | item_bits(s, U, j2, v.hashes);
-        const uint32_t phys = (s.o2 + U) & 3u;
-        if ((pick4(P, phys) & m) != m) atomicOr(s.blk + phys, (unsigned long long)m);
-      }
-    }
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock * kR;
+  for (uint64_t p0 = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) * kR; p0 < v.m; p0 += stride) {
+    walk<KW>(v, p0, [&](int, uint64_t, bool valid, const Occ& oc) {
+      if (!valid || (ROUNDS && !in_round(v, oc.H, round))) return;
+      const uint64_t G = second_hash(oc.H);
+      const uint32_t j1 = __ffs(oc.items) - 1, j2 = 31 - __clz(oc.items);
+      uint64_t m = item_bits<HB>(G, j1);
+      if (j2 != j1) m |= item_bits<HB>(G, j2);
+      atomicOr(filter_word(v, oc.H, G), (unsigned long long)m);
+    });
   }
 }
 
 // Algorithm 1, probe loop, first pass: a position stays a candidate iff it is
 // a sentinel position, its k-mer's sentinel item is present, or at least two
 // of its 16 (predecessor, successor) items are present -- i.e. the filter
-// does not show exactly one in-edge and one out-edge. Writes C_temp.
-template <int KW, bool ROUNDS>
-__global__ void __launch_bounds__(kBlock) pass1_probe_kernel(RunView v, int round) {
-  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+// does not show exactly one in-edge and one out-edge. Writes C_temp, appends
+// every candidate's position to the warp's own segment of the pass-2 list,
+// and sets the candidate's bit in a linear-counting bitmap that estimates how
+// many distinct k-mers survive.
+template <int KW, bool ROUNDS, int HB>
+__global__ void __launch_bounds__(kBlock, 4) pass1_probe_kernel(RunView v, int round) {
   const int lane = threadIdx.x & 31;
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock * kR;
+  constexpr int kLanesPerWord = 32 / kR;
   unsigned long long kept = 0, valid_n = 0;
-  for (uint64_t g0 = (uint64_t)blockIdx.x * kBlock; g0 < v.m; g0 += stride) {
-    const uint64_t g = g0 + threadIdx.x;
-    bool keep = false, valid = false;
-    Occ oc;
-    if (g < v.m && read_occurrence<KW>(v, g, &oc)) {
-      valid = true;
-      if (!ROUNDS || in_round(v, oc.H, round)) {
+  const uint32_t warp_id = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  uint64_t* seg = v.cands + (uint64_t)warp_id * v.seg_cap;
+  uint64_t seg_used = 0;
+  for (uint64_t wbase = ((uint64_t)blockIdx.x * kBlock + (threadIdx.x & ~31u)) * kR; wbase < v.m;
+       wbase += stride) {
+    const uint64_t p0 = wbase + (uint64_t)lane * kR;
+    uint64_t word[kR], G[kR];
+    uint32_t probe_bits = 0, sent_bits = 0, valid_bits = 0;
+    if (p0 < v.m) {
+      walk<KW>(v, p0, [&](int i, uint64_t, bool valid, const Occ& oc) {
+        if (!valid) return;
+        valid_bits |= 1u << i;
+        if (ROUNDS && !in_round(v, oc.H, round)) return;
+        G[i] = second_hash(oc.H);
         if (oc.sentinel) {
-          keep = true;
+          sent_bits |= 1u << i;
         } else {
-          const Spot s = filter_spot(v, oc.H);
-          uint64_t P[4];
-          load_block(s.blk, P);
-          const uint32_t pres = present_items(s, P, v.hashes);
-          keep = (pres >> 16) || __popc(pres & 0xFFFFu) >= 2;
+          word[i] = __ldcg(filter_word(v, oc.H, G[i]));
+          probe_bits |= 1u << i;
         }
+      });
+    }
+    uint32_t keep_bits = sent_bits;
+#pragma unroll
+    for (int i = 0; i < kR; ++i) {
+      if ((probe_bits >> i) & 1u) {
+        const uint32_t pres = present_items<HB>(G[i], word[i]);
+        if ((pres >> 16) || __popc(pres & 0xFFFFu) >= 2) keep_bits |= 1u << i;
+      }
+      if ((keep_bits >> i) & 1u) {
+        const uint64_t idx = (G[i] * 0xff51afd7ed558ccdull) >> (64 - v.lc_log2);
+        atomicOr(v.lc_bits + (idx >> 5), 1u << (idx & 31));
       }
     }
-    const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-    const uint32_t vb = __ballot_sync(0xffffffffu, valid);
-    if (lane == 0) {
-      const uint64_t w = g >> 5;
-      if (w < v.bitmap_words) v.ctemp[w] = bal;
-      kept += __popc(bal);
-      valid_n += __popc(vb);
+    // C_temp: kLanesPerWord lanes make up one 32-bit word
+    uint32_t wv = keep_bits << (kR * (lane % kLanesPerWord));
+#pragma unroll
+    for (int o = 1; o < kLanesPerWord; o <<= 1) wv |= __shfl_xor_sync(0xffffffffu, wv, o);
+    if (lane % kLanesPerWord == 0) {
+      const uint64_t w = (wbase >> 5) + lane / kLanesPerWord;
+      if (w < v.bitmap_words) v.ctemp[w] = wv;
     }
+    // candidate list: the warp appends to its own segment, in position order
+    const uint32_t c = __popc(keep_bits);
+    uint32_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    uint64_t at = seg_used + (inc - c);
+    uint32_t bits = keep_bits;
+    while (bits) {
+      const int i = __ffs(bits) - 1;
+      bits &= bits - 1;
+      if (at < v.seg_cap) seg[at] = p0 + (uint64_t)i;
+      ++at;
+    }
+    seg_used += __shfl_sync(0xffffffffu, inc, 31);
+    kept += c;
+    valid_n += __popc(valid_bits);
   }
-  __shared__ unsigned long long red[2][kBlock / 32];
   if (lane == 0) {
-    red[0][threadIdx.x >> 5] = kept;
-    red[1][threadIdx.x >> 5] = valid_n;
+    v.seg_count[warp_id] = (uint32_t)(seg_used < v.seg_cap ? seg_used : v.seg_cap);
+    if (seg_used > v.seg_cap) v.hdr->cand_overflow = 1;
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long a = 0, b = 0;
-    for (int w = 0; w < kBlock / 32; ++w) {
-      a += red[0][w];
-      b += red[1][w];
-    }
-    if (a) {
-      atomicAdd(&v.hdr->pass1_kept, a);
-      atomicAdd(&v.hdr->round_kept, a);
-    }
-    if (round == 0 && b) atomicAdd(&v.hdr->positions, b);
-  }
+  block_add(kept, &v.hdr->pass1_kept);
+  block_add(kept, &v.hdr->round_kept);
+  if (round == 0) block_add(valid_n, &v.hdr->positions);
 }
 
-// Size the pass-2 table of this round from the number of candidates:
-// the next power of two >= 2 x candidates (at least 1024), capped by the
-// workspace.
+// Bits set in the linear-counting bitmap.
+__global__ void __launch_bounds__(kBlock) lc_count_kernel(RunView v) {
+  const uint64_t words = (1ull << v.lc_log2) / 32;
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+  unsigned long long c = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < words; i += stride)
+    c += __popc(__ldcg(v.lc_bits + i));
+  block_add(c, &v.hdr->lc_set);
+}
+
+// Size the pass-2 table of this round: twice the number of distinct
+// candidate k-mers, estimated by linear counting (Whang, Vander-Zanden &
+// Taylor 1990) from the bits the probe set, rounded up to a power of two (at
+// least 1024) and capped by the workspace. A saturated bitmap falls back to
+// twice the number of candidate positions. The estimate only sets the table's
+// size; an undersized table is detected and reported, never silently wrong.
 __global__ void table_setup_kernel(RunView v) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const unsigned long long kept = v.hdr->round_kept;
-    unsigned long long want = 2ull * kept;
+    const unsigned long long set = v.hdr->lc_set;
+    const double M = (double)(1ull << v.lc_log2);
+    unsigned long long distinct = kept;
+    if ((double)set < 0.9 * M) {
+      const double est = -M * log1p(-(double)set / M);
+      const unsigned long long e = (unsigned long long)(est * 1.1) + 64ull;
+      if (e < distinct) distinct = e;
+    }
+    unsigned long long want = 2ull * distinct;
     if (want < 1024ull) want = 1024ull;
     unsigned long long cap = 1ull;
     while (cap < want) cap <<= 1;
     if (cap > v.table_max_slots) cap = v.table_max_slots;
     v.hdr->table_slots = cap;
     if (cap > v.hdr->table_max) v.hdr->table_max = cap;
+    v.hdr->round_listed = v.hdr->cand_overflow ? 0u : 1u;
+    v.hdr->cand_overflow = 0;
     v.hdr->round_kept = 0;
+    v.hdr->lc_set = 0;
   }
 }
 
@@ -612,67 +734,81 @@ __global__ void __launch_bounds__(kBlock) table_clear_kernel(RunView v) {
 }
 
 // Algorithm 1, insert loop, second pass: every candidate ORs its in/out bases
-// (or the sentinel bit) into the exact table entry of its k-mer.
+// (or the sentinel bit) into the exact table entry of its k-mer. Reads the
+// candidate list; if the list overflowed, walks C_temp instead.
 template <int KW>
 __global__ void __launch_bounds__(kBlock) pass2_insert_kernel(RunView v) {
   const uint64_t cap = *(volatile unsigned long long*)&v.hdr->table_slots;
-  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
-  for (uint64_t g = (uint64_t)blockIdx.x * kBlock + threadIdx.x; g < v.m; g += stride) {
-    if (!((__ldg(v.ctemp + (g >> 5)) >> (g & 31)) & 1u)) continue;
+  auto insert = [&](uint64_t g) {
     Occ oc;
-    if (!read_occurrence<KW>(v, g, &oc)) continue;
-    if (!table_insert<KW>(v, cap, oc.key, second_hash(oc.H), oc.tbits)) v.hdr->overflow = 1;
+    if (!read_occurrence<KW>(v, g, &oc)) return;
+    if (!table_insert<KW>(v, cap, oc.key, slot_hash(oc.H), oc.tbits)) v.hdr->overflow = 1;
+  };
+  if (*(volatile unsigned int*)&v.hdr->round_listed) {
+    // seg_warps warps per list segment
+    const uint32_t gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const uint32_t sgm = gw / v.seg_warps;
+    if (sgm >= v.n_segments) return;
+    const uint64_t* seg = v.cands + (uint64_t)sgm * v.seg_cap;
+    const uint32_t n = v.seg_count[sgm];
+    for (uint32_t j = (gw % v.seg_warps) * 32 + (threadIdx.x & 31); j < n; j += 32 * v.seg_warps)
+      insert(__ldcs(seg + j));
+    return;
   }
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+  for (uint64_t g = (uint64_t)blockIdx.x * kBlock + threadIdx.x; g < v.m; g += stride)
+    if ((__ldg(v.ctemp + (g >> 5)) >> (g & 31)) & 1u) insert(g);
 }
 
 // Algorithm 1, probe loop, second pass: a candidate is a junction iff its
-// k-mer is a sentinel or has more than one distinct in- or out-base.
+// k-mer is a sentinel or has more than one distinct in- or out-base. Sets
+// the junction's bit of C_final (cleared before the first round).
 template <int KW>
-__global__ void __launch_bounds__(kBlock) pass2_classify_kernel(RunView v, int round) {
+__global__ void __launch_bounds__(kBlock) pass2_classify_kernel(RunView v) {
   const uint64_t cap = *(volatile unsigned long long*)&v.hdr->table_slots;
-  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
-  const int lane = threadIdx.x & 31;
   unsigned long long found = 0;
-  for (uint64_t g0 = (uint64_t)blockIdx.x * kBlock; g0 < v.m; g0 += stride) {
-    const uint64_t g = g0 + threadIdx.x;
-    const uint64_t w = g >> 5;
-    const uint32_t cw = (w < v.bitmap_words) ? __ldg(v.ctemp + w) : 0u;
-    bool junction = false;
-    if (cw && ((cw >> lane) & 1u)) {
-      Occ oc;
-      if (read_occurrence<KW>(v, g, &oc)) {
-        const int mk = table_find<KW>(v, cap, oc.key, second_hash(oc.H));
-        if (mk < 0) {
-          v.hdr->overflow = 1;
-          junction = true;
-        } else {
-          junction = ((mk >> 8) & 1) || __popc(mk & 15) > 1 || __popc((mk >> 4) & 15) > 1;
-        }
-      }
+  auto classify = [&](uint64_t g) {
+    Occ oc;
+    if (!read_occurrence<KW>(v, g, &oc)) return;
+    const int mk = table_find<KW>(v, cap, oc.key, slot_hash(oc.H));
+    if (mk < 0) v.hdr->overflow = 1;
+    if (mk < 0 || is_junction_mask(mk)) {
+      atomicOr(v.cfinal + (g >> 5), 1u << (g & 31));
+      ++found;
     }
-    const uint32_t bal = __ballot_sync(0xffffffffu, junction);
-    if (lane == 0 && w < v.bitmap_words) {
-      v.cfinal[w] = (round == 0) ? bal : (v.cfinal[w] | bal);
-      found += __popc(bal);
+  };
+  if (*(volatile unsigned int*)&v.hdr->round_listed) {
+    const uint32_t gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const uint32_t sgm = gw / v.seg_warps;
+    if (sgm < v.n_segments) {
+      const uint64_t* seg = v.cands + (uint64_t)sgm * v.seg_cap;
+      const uint32_t n = v.seg_count[sgm];
+      for (uint32_t j = (gw % v.seg_warps) * 32 + (threadIdx.x & 31); j < n; j += 32 * v.seg_warps)
+        classify(__ldcs(seg + j));
     }
+  } else {
+    const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+    for (uint64_t g = (uint64_t)blockIdx.x * kBlock + threadIdx.x; g < v.m; g += stride)
+      if ((__ldg(v.ctemp + (g >> 5)) >> (g & 31)) & 1u) classify(g);
   }
-  if (lane == 0 && found) atomicAdd(&v.hdr->pass2_kept, found);
+  block_add(found, &v.hdr->pass2_kept);
 }
 
 // Partition counters (section "Multiple Rounds"): a Bloom pre-pass over all
 // k-mers; counter f(k-mer) grows when the k-mer was not yet in the filter.
-template <int KW>
+template <int KW, int HB>
 __global__ void __launch_bounds__(kBlock) partition_count_kernel(RunView v) {
-  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
-  for (uint64_t g = (uint64_t)blockIdx.x * kBlock + threadIdx.x; g < v.m; g += stride) {
-    Occ oc;
-    if (!read_occurrence<KW>(v, g, &oc)) continue;
-    const Spot s = filter_spot(v, oc.H);
-    const uint64_t m = item_bits(s, 0, 17u, v.hashes);
-    const uint32_t phys = s.o2 & 3u;
-    if ((__ldcg(s.blk + phys) & m) == m) continue;
-    const unsigned long long old = atomicOr(s.blk + phys, (unsigned long long)m);
-    if ((old & m) != m) atomicAdd(v.bins + ((uint32_t)oc.H & v.qmask), 1u);
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock * kR;
+  for (uint64_t p0 = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) * kR; p0 < v.m; p0 += stride) {
+    walk<KW>(v, p0, [&](int, uint64_t, bool valid, const Occ& oc) {
+      if (!valid) return;
+      const uint64_t G = second_hash(oc.H);
+      const uint64_t m = item_bits<HB>(G, 17u);
+      unsigned long long* w = filter_word(v, oc.H, G);
+      if ((__ldcg(w) & m) == m) return;
+      const unsigned long long old = atomicOr(w, (unsigned long long)m);
+      if ((old & m) != m) atomicAdd(v.bins + ((uint32_t)oc.H & v.qmask), 1u);
+    });
   }
 }
 
@@ -789,11 +925,12 @@ __global__ void __launch_bounds__(kBlock) emit_write_kernel(RunView v) {
     uint32_t tot;
     const uint32_t excl = block_exclusive_scan(__popc(bits), &tot);
     uint64_t at = v.tile_prefix[tile] + excl;
+    Bounds bd{1, 0};
     while (bits) {
       const uint32_t b = __ffs(bits) - 1;
       bits &= bits - 1;
       const uint64_t g = w * 32 + b;
-      const Bounds bd = seq_bounds(v, g);
+      if (g < bd.start || g >= bd.end) bd = seq_bounds(v, g);
       if (at < v.out_capacity) v.out_positions[at] = g - bd.start;
       ++at;
     }
@@ -817,7 +954,6 @@ __global__ void __launch_bounds__(kBlock) emit_offsets_kernel(RunView v) {
 // Launch helpers
 // ---------------------------------------------------------------------------
 
-
 int sm_count() {
   int dev = 0, n = 0;
   cudaGetDevice(&dev);
@@ -825,6 +961,7 @@ int sm_count() {
   return n > 0 ? n : 1;
 }
 
+// Grid of at most (SMs x resident blocks per SM) blocks for work_items threads.
 template <typename K>
 unsigned grid_for(K kernel, int block, uint64_t work_items) {
   int per_sm = 0;
@@ -846,26 +983,51 @@ int done(int n) {
 void count_launches(int n) { g_launches.fetch_add((unsigned long long)n); }
 
 int launch_init(const RunView& v, cudaStream_t s) {
-  { Timed t("init", s); init_kernel<<<1, 32, 0, s>>>(v); }
+  {
+    Timed t("init", s);
+    init_kernel<<<1, 32, 0, s>>>(v);
+  }
   return done(1);
 }
 
 int launch_pack(const RunView& v, cudaStream_t s) {
   if (v.packed_words == 0) return 0;
-  { Timed t("pack", s); pack_kernel<<<grid_for(pack_kernel, kBlock, v.packed_words), kBlock, 0, s>>>(v); }
+  {
+    Timed t("pack", s);
+    pack_kernel<<<grid_for(pack_kernel, kBlock, v.packed_words), kBlock, 0, s>>>(v);
+  }
   return done(1);
+}
+
+// Run f with the filter's bits per item as a compile-time constant.
+template <typename F>
+void with_hashes(int h, F&& f) {
+  switch (h) {
+    case 1: f(std::integral_constant<int, 1>{}); break;
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 3: f(std::integral_constant<int, 3>{}); break;
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    case 5: f(std::integral_constant<int, 5>{}); break;
+    case 6: f(std::integral_constant<int, 6>{}); break;
+    case 7: f(std::integral_constant<int, 7>{}); break;
+    default: f(std::integral_constant<int, 8>{}); break;
+  }
 }
 
 int launch_partition(const RunView& v, int rounds, cudaStream_t s) {
   if (v.m == 0) return 0;
   if (cudaMemsetAsync(v.filter, 0, v.filter_words64 * 8, s) != cudaSuccess) return -1;
   if (cudaMemsetAsync(v.bins, 0, (uint64_t)(v.qmask + 1u) * 4, s) != cudaSuccess) return -1;
+  const uint64_t threads = (v.m + kR - 1) / kR;
   {
     Timed t("partition_count", s);
-    if (v.k <= 31)
-      partition_count_kernel<1><<<grid_for(partition_count_kernel<1>, kBlock, v.m), kBlock, 0, s>>>(v);
-    else
-      partition_count_kernel<2><<<grid_for(partition_count_kernel<2>, kBlock, v.m), kBlock, 0, s>>>(v);
+    with_hashes(v.hashes, [&](auto hb) {
+      constexpr int HB = decltype(hb)::value;
+      if (v.k <= 31)
+        partition_count_kernel<1, HB><<<grid_for(partition_count_kernel<1, HB>, kBlock, threads), kBlock, 0, s>>>(v);
+      else
+        partition_count_kernel<2, HB><<<grid_for(partition_count_kernel<2, HB>, kBlock, threads), kBlock, 0, s>>>(v);
+    });
   }
   uint64_t* prefix = reinterpret_cast<uint64_t*>(v.bins + (v.qmask + 1u));
   {
@@ -875,43 +1037,67 @@ int launch_partition(const RunView& v, int rounds, cudaStream_t s) {
   return done(2);
 }
 
-template <int KW>
-int round_impl(const RunView& v, int round, bool rounds_on, cudaStream_t s) {
+template <int KW, bool RD, int HB>
+int round_impl(const RunView& v, int round, cudaStream_t s) {
   if (cudaMemsetAsync(v.filter, 0, v.filter_words64 * 8, s) != cudaSuccess) return -1;
-  const unsigned gm = grid_for(pass1_probe_kernel<KW, true>, kBlock, v.m);
+  if (cudaMemsetAsync(v.lc_bits, 0, (1ull << v.lc_log2) / 8, s) != cudaSuccess) return -1;
+  if (round == 0 && cudaMemsetAsync(v.cfinal, 0, v.bitmap_words * 4, s) != cudaSuccess) return -1;
+  const uint64_t threads = (v.m + kR - 1) / kR;
   {
     Timed t("pass1_insert", s);
-    if (rounds_on) pass1_insert_kernel<KW, true><<<gm, kBlock, 0, s>>>(v, round);
-    else pass1_insert_kernel<KW, false><<<gm, kBlock, 0, s>>>(v, round);
+    pass1_insert_kernel<KW, RD, HB>
+        <<<grid_for(pass1_insert_kernel<KW, RD, HB>, kBlock, threads), kBlock, 0, s>>>(v, round);
   }
+  // one candidate-list segment per probe warp
+  RunView pv = v;
+  unsigned grid = grid_for(pass1_probe_kernel<KW, RD, HB>, kBlock, threads);
+  if (grid * (kBlock / 32) > kMaxSegments) grid = kMaxSegments / (kBlock / 32);
+  pv.n_segments = grid * (kBlock / 32);
+  pv.seg_cap = v.cand_cap / pv.n_segments;
   {
     Timed t("pass1_probe", s);
-    if (rounds_on) pass1_probe_kernel<KW, true><<<gm, kBlock, 0, s>>>(v, round);
-    else pass1_probe_kernel<KW, false><<<gm, kBlock, 0, s>>>(v, round);
+    pass1_probe_kernel<KW, RD, HB><<<grid, kBlock, 0, s>>>(pv, round);
+  }
+  {
+    Timed t("lc_count", s);
+    lc_count_kernel<<<grid_for(lc_count_kernel, kBlock, (1ull << v.lc_log2) / 32), kBlock, 0, s>>>(pv);
   }
   {
     Timed t("table_setup", s);
-    table_setup_kernel<<<1, 32, 0, s>>>(v);
+    table_setup_kernel<<<1, 32, 0, s>>>(pv);
   }
   {
     Timed t("table_clear", s);
-    table_clear_kernel<KW><<<grid_for(table_clear_kernel<KW>, kBlock, v.table_max_slots), kBlock, 0, s>>>(v);
+    table_clear_kernel<KW><<<grid_for(table_clear_kernel<KW>, kBlock, v.table_max_slots), kBlock, 0, s>>>(pv);
   }
+  // pass 2: enough warps per list segment to fill the GPU (a walk of C_temp
+  // if a segment overflowed reuses the same grid)
+  const uint32_t want_warps = (uint32_t)sm_count() * 64u;
+  pv.seg_warps = (want_warps + pv.n_segments - 1) / pv.n_segments;
+  if (pv.seg_warps < 1) pv.seg_warps = 1;
+  const unsigned g2 = (unsigned)(((uint64_t)pv.n_segments * pv.seg_warps * 32 + kBlock - 1) / kBlock);
   {
     Timed t("pass2_insert", s);
-    pass2_insert_kernel<KW><<<gm, kBlock, 0, s>>>(v);
+    pass2_insert_kernel<KW><<<g2, kBlock, 0, s>>>(pv);
   }
   {
     Timed t("pass2_classify", s);
-    pass2_classify_kernel<KW><<<gm, kBlock, 0, s>>>(v, round);
+    pass2_classify_kernel<KW><<<g2, kBlock, 0, s>>>(pv);
   }
-  return done(6);
+  return done(7);
 }
 
 int launch_round(const RunView& v, int round, int rounds, cudaStream_t s) {
   if (v.m == 0) return 0;
-  const bool on = rounds > 1;
-  return v.k <= 31 ? round_impl<1>(v, round, on, s) : round_impl<2>(v, round, on, s);
+  int rc = 0;
+  with_hashes(v.hashes, [&](auto hb) {
+    constexpr int HB = decltype(hb)::value;
+    if (v.k <= 31)
+      rc = rounds > 1 ? round_impl<1, true, HB>(v, round, s) : round_impl<1, false, HB>(v, round, s);
+    else
+      rc = rounds > 1 ? round_impl<2, true, HB>(v, round, s) : round_impl<2, false, HB>(v, round, s);
+  });
+  return rc;
 }
 
 int launch_emit(const RunView& v, cudaStream_t s) {
@@ -966,9 +1152,9 @@ extern "C" int twopaco_profile_kernels(const char** names, unsigned long long* l
   std::vector<double> ms;
   std::vector<const char*> ptr;
   for (auto& r : g_prof) {
-    if (cudaEventSynchronize(r.stop) != cudaSuccess) return TWOPACO_ECUDA_INTERNAL;
+    if (cudaEventSynchronize(r.stop) != cudaSuccess) return -5;
     float t = 0.f;
-    if (cudaEventElapsedTime(&t, r.start, r.stop) != cudaSuccess) return TWOPACO_ECUDA_INTERNAL;
+    if (cudaEventElapsedTime(&t, r.start, r.stop) != cudaSuccess) return -5;
     size_t i = 0;
     while (i < seen.size() && seen[i] != r.name) ++i;
     if (i == seen.size()) {

@@ -34,7 +34,7 @@ class TwopacoError(RuntimeError):
 class _Options(ctypes.Structure):
     _fields_ = [("hashes", ctypes.c_int), ("both_strands", ctypes.c_int),
                 ("partition_bins", ctypes.c_uint32), ("table_slots", ctypes.c_uint64),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("candidate_records", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p)]
 
 
 class _Stats(ctypes.Structure):
@@ -107,10 +107,12 @@ class Options:
     partition_bins: int = 65536
     table_slots: int = 0
     cuda_stream: int = 0  # cudaStream_t as an integer; 0 = default stream
+    candidate_records: int = 0
 
     def _c(self) -> _Options:
         return _Options(int(self.hashes), int(bool(self.both_strands)), int(self.partition_bins),
-                        int(self.table_slots), ctypes.c_void_p(int(self.cuda_stream) or None))
+                        int(self.table_slots), int(self.candidate_records),
+                        ctypes.c_void_p(int(self.cuda_stream) or None))
 
 
 def _stats_dict(s: _Stats) -> Dict[str, int]:
@@ -262,7 +264,7 @@ class DeviceBuild:
 
     def run(self, stream=None) -> None:
         opt = Options(self.options.hashes, self.options.both_strands, self.options.partition_bins,
-                      self.options.table_slots, self._stream(stream))
+                      self.options.table_slots, self._stream(stream), self.options.candidate_records)
         twopaco_run_device(self.bases.data_ptr() if self.total_bases else 0, self.offsets.data_ptr(),
                            self.n_seqs, self.total_bases, self.k, self.filter_bits, self.rounds, opt,
                            self.ws_ptr, self.ws_bytes, self.out_offsets.data_ptr(),

@@ -267,3 +267,18 @@ def test_non_default_stream_and_repeat():
     for _ in range(3):
         run.run(stream=s)
     _eq(run.result(stream=s), want)
+
+
+def test_candidate_list_overflow_falls_back_to_bitmap_walk():
+    """A candidate list too short for the round: pass 2 walks C_temp instead."""
+    seqs = _named("plain_single", 0.1)
+    bases, off = G.concat(seqs)
+    want = O.junctions((bases, off), 25)
+    for recs in (1, 1000, 100000):
+        run = T().DeviceBuild(bases, off, 25, 1 << 18, 1,
+                              T().Options(hashes=3, candidate_records=recs))
+        run.run()
+        _eq(run.result(), want)
+    got, _ = T().twopaco_build_ex(seqs, 25, 1 << 18, 2,
+                                  T().Options(hashes=3, candidate_records=500, partition_bins=64))
+    _eq(got, want)
