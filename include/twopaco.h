@@ -144,6 +144,32 @@ int twopaco_run_device(const uint8_t* d_bases, const uint64_t* d_offsets, uint64
  */
 int twopaco_read_stats(const void* d_workspace, void* cuda_stream, twopaco_stats* stats);
 
+/*
+ * Reusable build context. It keeps device buffers (input, workspace, output)
+ * and pinned host buffers for the result across calls, growing them only
+ * when an input needs more, so repeated builds do no allocation. One context
+ * serves one host thread at a time; it launches on its own CUDA stream on
+ * the device that was current when it was created.
+ */
+typedef struct twopaco_context twopaco_context;
+
+/* Create a context on the current device. *ctx is NULL on error. */
+int twopaco_context_create(twopaco_context** ctx);
+
+/* Release a context and every buffer it holds. NULL is ignored. */
+void twopaco_context_destroy(twopaco_context* ctx);
+
+/*
+ * As twopaco_build_ex, through a context: host strings in (pageable or
+ * pinned), result in *out. out->offsets and out->positions point into the
+ * context's pinned buffers and stay valid until the next call on this
+ * context or its destruction; do not pass *out to twopaco_result_free.
+ * options->cuda_stream is ignored (the context's own stream is used).
+ */
+int twopaco_build_ctx(twopaco_context* ctx, const char* const* seqs, const uint64_t* lengths,
+                      uint64_t n_seqs, int k, uint64_t filter_bits, int rounds,
+                      const twopaco_options* opt, twopaco_result* out);
+
 /* Which internal state twopaco_read_state copies out. */
 #define TWOPACO_STATE_CANDIDATES 0 /* C_temp of the last round: ceil(total_bases/32) uint32 words */
 #define TWOPACO_STATE_JUNCTIONS 1  /* C_final: ceil(total_bases/32) uint32 words */

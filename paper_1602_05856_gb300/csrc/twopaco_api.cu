@@ -2,6 +2,7 @@
 // layout, the launch sequence of one run, and the host-to-host build.
 #include <cstdlib>
 #include <cstring>
+#include <new>
 #include <vector>
 
 #include "twopaco.h"
@@ -138,6 +139,7 @@ RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_
   v.table = base + L.table;
   v.table_max_slots = L.table_slots;
   v.cands = reinterpret_cast<uint64_t*>(base + L.cands);
+  v.narrow = m <= (1ull << 32) ? 1 : 0;
   v.cand_cap = L.cand_cap;
   v.lc_bits = reinterpret_cast<uint32_t*>(base + L.lc);
   v.lc_log2 = L.lc_log2;
@@ -236,10 +238,10 @@ int twopaco_read_stats(const void* d_workspace, void* cuda_stream, twopaco_stats
   stats->pass1_marks = h.pass1_kept;
   stats->pass2_marks = h.pass2_kept;
   stats->table_slots = h.table_max;
-  stats->bad_base_index = h.bad_index;
+  stats->bad_base_index = h.bad_inv ? ~h.bad_inv : ~0ull;
   stats->overflow = h.overflow;
   stats->timeout = h.timeout;
-  if (h.bad_index != ~0ull) return TWOPACO_EBADBASE;
+  if (h.bad_inv) return TWOPACO_EBADBASE;
   if (h.timeout) return TWOPACO_ETIMEOUT;
   if (h.overflow) return TWOPACO_EOVERFLOW;
   return TWOPACO_OK;
@@ -363,6 +365,169 @@ int twopaco_build_ex(const char* const* seqs, const uint64_t* lengths, uint64_t 
   fail(TWOPACO_OK);
   *out = done;
   return TWOPACO_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Reusable context
+// ---------------------------------------------------------------------------
+
+struct twopaco_context {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  uint8_t* d_bases = nullptr;
+  uint64_t cap_bases = 0;
+  uint64_t* d_off = nullptr;
+  uint64_t cap_d_off = 0;
+  uint64_t* d_out_off = nullptr;
+  uint64_t cap_d_out_off = 0;
+  uint64_t* d_pos = nullptr;
+  uint64_t cap_pos = 0;
+  void* d_ws = nullptr;
+  uint64_t cap_ws = 0;
+  uint64_t* h_off = nullptr;      // pinned: input offsets
+  uint64_t cap_h_off = 0;
+  uint64_t* h_out_off = nullptr;  // pinned: result offsets
+  uint64_t cap_h_out_off = 0;
+  uint64_t* h_pos = nullptr;      // pinned: result positions
+  uint64_t cap_hpos = 0;
+};
+
+namespace {
+
+// Grow a device buffer to at least `need` bytes (contents are not kept).
+template <typename T>
+cudaError_t grow_device(T** p, uint64_t* cap, uint64_t need) {
+  if (*cap >= need && *p) return cudaSuccess;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), need ? need : 1);
+  if (e == cudaSuccess) *cap = need;
+  return e;
+}
+
+template <typename T>
+cudaError_t grow_pinned(T** p, uint64_t* cap, uint64_t need) {
+  if (*cap >= need && *p) return cudaSuccess;
+  if (*p) cudaFreeHost(*p);
+  *p = nullptr;
+  *cap = 0;
+  cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(p), need ? need : 1);
+  if (e == cudaSuccess) *cap = need;
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int twopaco_context_create(twopaco_context** ctx) {
+  if (!ctx) return TWOPACO_EINVAL;
+  *ctx = nullptr;
+  twopaco_context* c = new (std::nothrow) twopaco_context();
+  if (!c) return TWOPACO_ENOMEM;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_code(e);
+  }
+  *ctx = c;
+  return TWOPACO_OK;
+}
+
+void twopaco_context_destroy(twopaco_context* c) {
+  if (!c) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  cudaFree(c->d_bases);
+  cudaFree(c->d_off);
+  cudaFree(c->d_out_off);
+  cudaFree(c->d_pos);
+  cudaFree(c->d_ws);
+  cudaFreeHost(c->h_off);
+  cudaFreeHost(c->h_out_off);
+  cudaFreeHost(c->h_pos);
+  cudaStreamDestroy(c->stream);
+  cudaSetDevice(prev);
+  delete c;
+}
+
+int twopaco_build_ctx(twopaco_context* c, const char* const* seqs, const uint64_t* lengths,
+                      uint64_t n_seqs, int k, uint64_t filter_bits, int rounds,
+                      const twopaco_options* opt, twopaco_result* out) {
+  if (!c || !out) return TWOPACO_EINVAL;
+  twopaco_options o = resolve(opt);
+  int rc = validate(n_seqs, k, filter_bits, rounds, o);
+  if (rc) return rc;
+  if (n_seqs && (!seqs || !lengths)) return TWOPACO_EINVAL;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != c->device) cudaSetDevice(c->device);
+  o.cuda_stream = c->stream;
+  auto finish = [&](int code) {
+    if (prev != c->device) cudaSetDevice(prev);
+    return code;
+  };
+  cudaError_t e;
+  const uint64_t off_bytes = (n_seqs + 1) * 8;
+  if ((e = grow_pinned(&c->h_off, &c->cap_h_off, off_bytes)) != cudaSuccess ||
+      (e = grow_pinned(&c->h_out_off, &c->cap_h_out_off, off_bytes)) != cudaSuccess ||
+      (e = grow_device(&c->d_off, &c->cap_d_off, off_bytes)) != cudaSuccess ||
+      (e = grow_device(&c->d_out_off, &c->cap_d_out_off, off_bytes)) != cudaSuccess)
+    return finish(cuda_code(e));
+  uint64_t positions = 0;
+  c->h_off[0] = 0;
+  for (uint64_t t = 0; t < n_seqs; ++t) {
+    if (lengths[t] && !seqs[t]) return finish(TWOPACO_EINVAL);
+    c->h_off[t + 1] = c->h_off[t] + lengths[t];
+    if (lengths[t] >= (uint64_t)k) positions += lengths[t] - (uint64_t)k + 1;
+  }
+  const uint64_t m = c->h_off[n_seqs];
+  if (validate_size(m)) return finish(TWOPACO_EINVAL);
+  if ((e = grow_device(&c->d_bases, &c->cap_bases, m)) != cudaSuccess) return finish(cuda_code(e));
+  if ((e = grow_device(&c->d_pos, &c->cap_pos, (positions ? positions : 1) * 8)) != cudaSuccess)
+    return finish(cuda_code(e));
+  for (uint64_t t = 0; t < n_seqs; ++t) {
+    if (!lengths[t]) continue;
+    e = cudaMemcpyAsync(c->d_bases + c->h_off[t], seqs[t], lengths[t], cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return finish(cuda_code(e));
+  }
+  e = cudaMemcpyAsync(c->d_off, c->h_off, (n_seqs + 1) * 8, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return finish(cuda_code(e));
+  twopaco_stats st{};
+  for (int attempt = 0;; ++attempt) {
+    uint64_t ws = 0;
+    if ((rc = twopaco_workspace_size(m, n_seqs, k, filter_bits, rounds, &o, &ws))) return finish(rc);
+    if ((e = grow_device(reinterpret_cast<char**>(&c->d_ws), &c->cap_ws, ws)) != cudaSuccess)
+      return finish(cuda_code(e));
+    rc = twopaco_run_device(c->d_bases, c->d_off, n_seqs, m, k, filter_bits, rounds, &o, c->d_ws, ws,
+                            c->d_out_off, c->d_pos, positions);
+    if (rc) return finish(rc);
+    e = cudaMemcpyAsync(c->h_out_off, c->d_out_off, (n_seqs + 1) * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return finish(cuda_code(e));
+    rc = twopaco_read_stats(c->d_ws, c->stream, &st);
+    if (rc != TWOPACO_EOVERFLOW || attempt >= 4) break;
+    o.table_slots = layout(m, k, filter_bits, rounds, o).table_slots * 4;
+  }
+  if (rc) return finish(rc);
+  const uint64_t total = c->h_out_off[n_seqs];
+  if ((e = grow_pinned(&c->h_pos, &c->cap_hpos, (total ? total : 1) * 8)) != cudaSuccess)
+    return finish(cuda_code(e));
+  if (total) {
+    e = cudaMemcpyAsync(c->h_pos, c->d_pos, total * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return finish(cuda_code(e));
+  }
+  out->n_seqs = n_seqs;
+  out->offsets = c->h_out_off;
+  out->positions = c->h_pos;
+  out->stats = st;
+  return finish(TWOPACO_OK);
 }
 
 }  // extern "C"

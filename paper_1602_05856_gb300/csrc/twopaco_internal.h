@@ -9,7 +9,7 @@ namespace twopaco {
 
 // Counters and failure flags kept at the start of the workspace.
 struct DevHeader {
-  unsigned long long bad_index;    // smallest invalid byte index, ~0 if none
+  unsigned long long bad_inv;      // ~(smallest invalid byte index), 0 if none
   unsigned long long positions;    // k-mer positions in the input
   unsigned long long pass1_kept;   // candidates after pass 1, all rounds
   unsigned long long pass2_kept;   // junction positions
@@ -19,6 +19,9 @@ struct DevHeader {
   unsigned long long lc_set;       // linear-counting bits set this round
   unsigned int cand_overflow;      // a warp's list segment ran out of room this round
   unsigned int round_listed;       // pass 2 of this round reads the list (else C_temp)
+  unsigned int lc_blocks_done;     // blocks of lc_count finished this round
+  unsigned int pad0;
+  unsigned long long emit_ticket;  // next emit tile to claim
   unsigned int overflow;           // table or output out of room
   unsigned int timeout;            // a bounded wait gave up
   // where the last run left its bitmaps and partition state (for inspection)
@@ -55,6 +58,7 @@ struct RunView {
   void* table;              // pass-2 slots
   uint64_t table_max_slots;
   uint64_t* cands;          // positions of the pass-1 survivors, for pass 2
+  int narrow;               // m <= 2^32: the list holds 32-bit positions
   uint64_t cand_cap;        // records the list can hold
   uint32_t* seg_count;      // candidates per list segment (one segment per probe warp)
   uint32_t n_segments;      // warps of the probe grid (set per launch)
@@ -73,20 +77,23 @@ struct RunView {
 };
 
 constexpr int kBlock = 256;             // threads per block of the position kernels
-constexpr int kEmitTileWords = 256;     // bitmap words per emit tile (8192 positions)
+constexpr int kEmitWordsPerThread = 16;
+constexpr int kEmitTileWords = kBlock * kEmitWordsPerThread;  // bitmap words per emit tile
 constexpr uint64_t kPackPadWords = 8;   // zero words after the packed input
 constexpr uint32_t kMaxSegments = 65536; // candidate-list segments (probe warps) at most
 
 // Kernel launch helpers (twopaco_kernels.cu). Each returns the number of
 // kernels it launched, or -1 after a launch error.
-int launch_init(const RunView& v, cudaStream_t s);
+int launch_init(const RunView& v, cudaStream_t s);  // clears the header
 int launch_pack(const RunView& v, cudaStream_t s);
 int launch_partition(const RunView& v, int rounds, cudaStream_t s);
 int launch_round(const RunView& v, int round, int rounds, cudaStream_t s);
 int launch_emit(const RunView& v, cudaStream_t s);
 
-// Bytes per pass-2 slot for this k.
-inline uint64_t table_slot_bytes(int k) { return k <= 31 ? 16 : 32; }
+// Pass-2 slot layout for this k: 0 = one 64-bit word (key << 9 | mask, k <= 27),
+// 1 = 16 bytes (k <= 31), 2 = 32 bytes (128-bit key).
+inline int table_slot_kind(int k) { return k <= 27 ? 0 : (k <= 31 ? 1 : 2); }
+inline uint64_t table_slot_bytes(int k) { return 8ull << table_slot_kind(k); }
 
 // Bytes per candidate record (a global position).
 inline uint64_t cand_record_bytes(int) { return 8; }

@@ -375,6 +375,7 @@ struct alignas(32) Slot2 {
 };
 
 constexpr unsigned long long kEmpty = ~0ull;
+constexpr int kMaskBits = 9;
 
 __device__ __forceinline__ void cas128(unsigned long long* addr, uint64_t cmp_lo, uint64_t cmp_hi,
                                        uint64_t new_lo, uint64_t new_hi, uint64_t* old_lo,
@@ -393,44 +394,63 @@ __device__ __forceinline__ void cas128(unsigned long long* addr, uint64_t cmp_lo
   *old_hi = oh;
 }
 
-// Insert (key, bits); false if every slot was tried (the table is full).
-template <int KW>
+// Insert (key, bits) into a table of TS-kind slots (table_slot_kind); false
+// if every slot was tried (the table is full). Bits already present are not
+// written again.
+template <int TS>
 __device__ __forceinline__ bool table_insert(const RunView& v, uint64_t cap, const Key& key,
                                              uint64_t start, uint32_t bits) {
   const uint64_t mask = cap - 1;
   uint64_t i = start & mask;
   for (uint64_t probe = 0; probe < cap; ++probe, i = (i + 1) & mask) {
-    unsigned int* mword;
-    if (KW == 1) {
+    if (TS == 0) {
+      // one word: key << 9 | mask bits; never all ones for a key < 2^54
+      unsigned long long* s = static_cast<unsigned long long*>(v.table) + i;
+      unsigned long long cur = __ldcg(s);
+      if (cur == kEmpty) {
+        cur = atomicCAS(s, kEmpty, (key.lo << kMaskBits) | bits);
+        if (cur == kEmpty) return true;
+      }
+      if ((cur >> kMaskBits) != key.lo) continue;
+      if ((cur & bits) != bits) atomicOr(s, (unsigned long long)bits);
+      return true;
+    } else if (TS == 1) {
       Slot1* s = static_cast<Slot1*>(v.table) + i;
-      unsigned long long cur = __ldcg(&s->key);
+      const ulonglong2 w = __ldcg(reinterpret_cast<const ulonglong2*>(s));
+      unsigned long long cur = w.x;
+      uint32_t have = (uint32_t)w.y;
       if (cur == kEmpty) {
         cur = atomicCAS(&s->key, kEmpty, (unsigned long long)key.lo);
         if (cur == kEmpty) cur = key.lo;
+        have = 0;
       }
       if (cur != key.lo) continue;
-      mword = &s->mask;
+      if ((have & bits) != bits) atomicOr(&s->mask, bits);
+      return true;
     } else {
       Slot2* s = static_cast<Slot2*>(v.table) + i;
       uint64_t ol, oh;
       cas128(&s->w0, kEmpty, kEmpty, key.lo, key.hi, &ol, &oh);
       const bool mine = (ol == kEmpty && oh == kEmpty) || (ol == key.lo && oh == key.hi);
       if (!mine) continue;
-      mword = &s->mask;
+      if ((__ldcg(&s->mask) & bits) != bits) atomicOr(&s->mask, bits);
+      return true;
     }
-    if ((__ldcg(mword) & bits) != bits) atomicOr(mword, bits);
-    return true;
   }
   return false;
 }
 
 // Mask of key, or -1 if absent.
-template <int KW>
+template <int TS>
 __device__ __forceinline__ int table_find(const RunView& v, uint64_t cap, const Key& key, uint64_t start) {
   const uint64_t mask = cap - 1;
   uint64_t i = start & mask;
   for (uint64_t probe = 0; probe < cap; ++probe, i = (i + 1) & mask) {
-    if (KW == 1) {
+    if (TS == 0) {
+      const unsigned long long cur = __ldcg(static_cast<const unsigned long long*>(v.table) + i);
+      if (cur == kEmpty) return -1;
+      if ((cur >> kMaskBits) == key.lo) return (int)(cur & ((1u << kMaskBits) - 1u));
+    } else if (TS == 1) {
       const Slot1* s = static_cast<const Slot1*>(v.table) + i;
       const ulonglong2 w = __ldcg(reinterpret_cast<const ulonglong2*>(s));
       if (w.x == key.lo) return (int)(unsigned int)w.y;
@@ -502,35 +522,6 @@ __device__ __forceinline__ void block_add(unsigned long long x, unsigned long lo
 // Kernels
 // ---------------------------------------------------------------------------
 
-__global__ void init_kernel(RunView v) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    DevHeader* h = v.hdr;
-    h->bad_index = ~0ull;
-    h->positions = 0;
-    h->pass1_kept = 0;
-    h->pass2_kept = 0;
-    h->round_kept = 0;
-    h->lc_set = 0;
-    h->cand_overflow = 0;
-    h->round_listed = 0;
-    h->table_slots = 0;
-    h->table_max = 0;
-    h->overflow = 0;
-    h->timeout = 0;
-    h->ctemp = v.ctemp;
-    h->cfinal = v.cfinal;
-    h->bins = v.bins;
-    h->cuts = v.cuts;
-    h->bitmap_words = v.bitmap_words;
-    h->q = (unsigned long long)v.qmask + 1ull;
-    h->rounds = (unsigned long long)v.rounds;
-    if (v.cuts) {  // one class holding every bin until the partition step runs
-      v.cuts[0] = 0;
-      v.cuts[1] = v.qmask + 1u;
-    }
-  }
-}
-
 // Four ASCII bytes -> four 2-bit codes (first byte in bits 7-6); *bad gets
 // 0xFF in every byte that is not one of ACGTacgt.
 __device__ __forceinline__ uint32_t pack4(uint32_t x, uint32_t* bad) {
@@ -544,35 +535,66 @@ __device__ __forceinline__ uint32_t pack4(uint32_t x, uint32_t* bad) {
   return ((c & 3u) << 6) | (((c >> 8) & 3u) << 4) | (((c >> 16) & 3u) << 2) | ((c >> 24) & 3u);
 }
 
-// ASCII -> 2-bit words, 16 bytes (one 128-bit load) per thread.
-__global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
-  const bool vec = (reinterpret_cast<uintptr_t>(v.bases) & 15) == 0;
-  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
-  for (uint64_t w = (uint64_t)blockIdx.x * kBlock + threadIdx.x; w < v.packed_words; w += stride) {
-    const uint64_t g = w * 16;
-    uint32_t out = 0;
-    uint64_t bad_at = ~0ull;
-    if (vec && g + 16 <= v.m) {
-      const uint4 q = __ldcs(reinterpret_cast<const uint4*>(v.bases + g));
-      const uint32_t part[4] = {q.x, q.y, q.z, q.w};
+// Sixteen ASCII bytes at g (or fewer at the end of the input) -> one word;
+// *bad_at gets the index of the first invalid byte.
+__device__ __forceinline__ uint32_t pack16(const RunView& v, uint64_t g, uint4 q, bool full,
+                                           uint64_t* bad_at) {
+  uint32_t out = 0;
+  if (full) {
+    const uint32_t part[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        uint32_t bad;
-        out |= pack4(part[c], &bad) << (24 - 8 * c);
-        if (bad && bad_at == ~0ull) bad_at = g + 4 * c + (__ffs(bad) - 1) / 8;
-      }
-    } else if (g < v.m) {
-      for (int i = 0; i < 16 && g + i < v.m; ++i) {
-        const uint32_t c = v.bases[g + i];
-        uint32_t bad;
-        const uint32_t code = pack4(c | 0x61616100u, &bad) >> 6;  // pad bytes are 'a'
-        if ((bad & 0xFFu) && bad_at == ~0ull) bad_at = g + i;
-        out |= code << (30 - 2 * i);
-      }
+    for (int c = 0; c < 4; ++c) {
+      uint32_t bad;
+      out |= pack4(part[c], &bad) << (24 - 8 * c);
+      if (bad && *bad_at == ~0ull) *bad_at = g + 4 * c + (__ffs(bad) - 1) / 8;
     }
-    v.packed[w] = out;
-    if (bad_at != ~0ull) atomicMin(&v.hdr->bad_index, (unsigned long long)bad_at);
+  } else if (g < v.m) {
+    for (int i = 0; i < 16 && g + i < v.m; ++i) {
+      const uint32_t c = v.bases[g + i];
+      uint32_t bad;
+      const uint32_t code = pack4(c | 0x61616100u, &bad) >> 6;  // pad bytes are 'a'
+      if ((bad & 0xFFu) && *bad_at == ~0ull) *bad_at = g + i;
+      out |= code << (30 - 2 * i);
+    }
   }
+  return out;
+}
+
+// ASCII -> 2-bit words: 64 bytes (four 128-bit loads in flight) per thread.
+// Block 0 also records where this run keeps its bitmaps (for inspection).
+__global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    DevHeader* h = v.hdr;
+    h->ctemp = v.ctemp;
+    h->cfinal = v.cfinal;
+    h->bins = v.bins;
+    h->cuts = v.cuts;
+    h->bitmap_words = v.bitmap_words;
+    h->q = (unsigned long long)v.qmask + 1ull;
+    h->rounds = (unsigned long long)v.rounds;
+  }
+  const bool vec = (reinterpret_cast<uintptr_t>(v.bases) & 15) == 0;
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock * 4;
+  uint64_t bad_at = ~0ull;
+  for (uint64_t w0 = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) * 4; w0 < v.packed_words; w0 += stride) {
+    uint4 q[4];
+    bool full[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint64_t g = (w0 + j) * 16;
+      full[j] = vec && g + 16 <= v.m;
+      if (full[j]) q[j] = __ldcs(reinterpret_cast<const uint4*>(v.bases + g));
+    }
+    uint32_t out[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[j] = pack16(v, (w0 + j) * 16, q[j], full[j], &bad_at);
+    if (w0 + 4 <= v.packed_words) {
+      *reinterpret_cast<uint4*>(v.packed + w0) = make_uint4(out[0], out[1], out[2], out[3]);
+    } else {
+      for (int j = 0; j < 4 && w0 + j < v.packed_words; ++j) v.packed[w0 + j] = out[j];
+    }
+  }
+  if (bad_at != ~0ull) atomicMax(&v.hdr->bad_inv, ~(unsigned long long)bad_at);
 }
 
 // Algorithm 1, insert loop, first pass: every active position records its
@@ -600,13 +622,14 @@ __global__ void __launch_bounds__(kBlock) pass1_insert_kernel(RunView v, int rou
 // and sets the candidate's bit in a linear-counting bitmap that estimates how
 // many distinct k-mers survive.
 template <int KW, bool ROUNDS, int HB>
-__global__ void __launch_bounds__(kBlock, 4) pass1_probe_kernel(RunView v, int round) {
+__global__ void __launch_bounds__(kBlock, 3) pass1_probe_kernel(RunView v, int round) {
   const int lane = threadIdx.x & 31;
   const uint64_t stride = (uint64_t)gridDim.x * kBlock * kR;
   constexpr int kLanesPerWord = 32 / kR;
   unsigned long long kept = 0, valid_n = 0;
   const uint32_t warp_id = (blockIdx.x * kBlock + threadIdx.x) >> 5;
-  uint64_t* seg = v.cands + (uint64_t)warp_id * v.seg_cap;
+  uint64_t* seg = v.cands + (uint64_t)warp_id * v.seg_cap;  // wide records
+  uint32_t* seg32 = reinterpret_cast<uint32_t*>(v.cands) + (uint64_t)warp_id * v.seg_cap;
   uint64_t seg_used = 0;
   for (uint64_t wbase = ((uint64_t)blockIdx.x * kBlock + (threadIdx.x & ~31u)) * kR; wbase < v.m;
        wbase += stride) {
@@ -660,7 +683,10 @@ __global__ void __launch_bounds__(kBlock, 4) pass1_probe_kernel(RunView v, int r
     while (bits) {
       const int i = __ffs(bits) - 1;
       bits &= bits - 1;
-      if (at < v.seg_cap) seg[at] = p0 + (uint64_t)i;
+      if (at < v.seg_cap) {
+        if (v.narrow) seg32[at] = (uint32_t)(p0 + (uint64_t)i);
+        else seg[at] = p0 + (uint64_t)i;
+      }
       ++at;
     }
     seg_used += __shfl_sync(0xffffffffu, inc, 31);
@@ -676,53 +702,60 @@ __global__ void __launch_bounds__(kBlock, 4) pass1_probe_kernel(RunView v, int r
   if (round == 0) block_add(valid_n, &v.hdr->positions);
 }
 
-// Bits set in the linear-counting bitmap.
-__global__ void __launch_bounds__(kBlock) lc_count_kernel(RunView v) {
-  const uint64_t words = (1ull << v.lc_log2) / 32;
-  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
-  unsigned long long c = 0;
-  for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < words; i += stride)
-    c += __popc(__ldcg(v.lc_bits + i));
-  block_add(c, &v.hdr->lc_set);
-}
-
 // Size the pass-2 table of this round: twice the number of distinct
 // candidate k-mers, estimated by linear counting (Whang, Vander-Zanden &
 // Taylor 1990) from the bits the probe set, rounded up to a power of two (at
 // least 1024) and capped by the workspace. A saturated bitmap falls back to
 // twice the number of candidate positions. The estimate only sets the table's
 // size; an undersized table is detected and reported, never silently wrong.
-__global__ void table_setup_kernel(RunView v) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const unsigned long long kept = v.hdr->round_kept;
-    const unsigned long long set = v.hdr->lc_set;
-    const double M = (double)(1ull << v.lc_log2);
-    unsigned long long distinct = kept;
-    if ((double)set < 0.9 * M) {
-      const double est = -M * log1p(-(double)set / M);
-      const unsigned long long e = (unsigned long long)(est * 1.1) + 64ull;
-      if (e < distinct) distinct = e;
-    }
-    unsigned long long want = 2ull * distinct;
-    if (want < 1024ull) want = 1024ull;
-    unsigned long long cap = 1ull;
-    while (cap < want) cap <<= 1;
-    if (cap > v.table_max_slots) cap = v.table_max_slots;
-    v.hdr->table_slots = cap;
-    if (cap > v.hdr->table_max) v.hdr->table_max = cap;
-    v.hdr->round_listed = v.hdr->cand_overflow ? 0u : 1u;
-    v.hdr->cand_overflow = 0;
-    v.hdr->round_kept = 0;
-    v.hdr->lc_set = 0;
+// Every block counts its share of the bitmap; the last block to finish sizes
+// the table.
+__global__ void __launch_bounds__(kBlock) table_setup_kernel(RunView v) {
+  const uint64_t words = (1ull << v.lc_log2) / 32;
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+  unsigned long long c = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < words; i += stride)
+    c += __popc(__ldcg(v.lc_bits + i));
+  block_add(c, &v.hdr->lc_set);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&v.hdr->lc_blocks_done, 1u) == gridDim.x - 1;
   }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  const unsigned long long kept = *(volatile unsigned long long*)&v.hdr->round_kept;
+  const unsigned long long set = *(volatile unsigned long long*)&v.hdr->lc_set;
+  const double M = (double)(1ull << v.lc_log2);
+  unsigned long long distinct = kept;
+  if ((double)set < 0.9 * M) {
+    const double est = -M * log1p(-(double)set / M);
+    const unsigned long long e = (unsigned long long)(est * 1.1) + 64ull;
+    if (e < distinct) distinct = e;
+  }
+  unsigned long long want = 2ull * distinct;
+  if (want < 1024ull) want = 1024ull;
+  unsigned long long cap = 1ull;
+  while (cap < want) cap <<= 1;
+  if (cap > v.table_max_slots) cap = v.table_max_slots;
+  v.hdr->table_slots = cap;
+  if (cap > v.hdr->table_max) v.hdr->table_max = cap;
+  v.hdr->round_listed = *(volatile unsigned int*)&v.hdr->cand_overflow ? 0u : 1u;
+  v.hdr->cand_overflow = 0;
+  v.hdr->round_kept = 0;
+  v.hdr->lc_set = 0;
+  v.hdr->lc_blocks_done = 0;
 }
 
-template <int KW>
+template <int TS>
 __global__ void __launch_bounds__(kBlock) table_clear_kernel(RunView v) {
   const uint64_t cap = *(volatile unsigned long long*)&v.hdr->table_slots;
   const uint64_t stride = (uint64_t)gridDim.x * kBlock;
   for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < cap; i += stride) {
-    if (KW == 1) {
+    if (TS == 0) {
+      static_cast<unsigned long long*>(v.table)[i] = kEmpty;
+    } else if (TS == 1) {
       Slot1* s = static_cast<Slot1*>(v.table) + i;
       *reinterpret_cast<ulonglong2*>(s) = make_ulonglong2(kEmpty, 0ull);
     } else {
@@ -733,44 +766,76 @@ __global__ void __launch_bounds__(kBlock) table_clear_kernel(RunView v) {
   }
 }
 
+// Candidate i of the list (32-bit records when the input has at most 2^32 bases).
+__device__ __forceinline__ uint64_t list_at(const RunView& v, uint64_t i) {
+  return v.narrow ? (uint64_t)__ldcs(reinterpret_cast<const uint32_t*>(v.cands) + i) : __ldcs(v.cands + i);
+}
+
 // Algorithm 1, insert loop, second pass: every candidate ORs its in/out bases
 // (or the sentinel bit) into the exact table entry of its k-mer. Reads the
 // candidate list; if the list overflowed, walks C_temp instead.
-template <int KW>
+constexpr int kP2 = 1;  // candidates per thread and step in pass 2 (1 measured fastest)
+
+// The list segment and the slice of it that this thread visits: candidate
+// indices first + j for j = j0, j0 + jstep, ... < n.
+struct ListSlice {
+  uint64_t first;
+  uint32_t j0, jstep, n;
+};
+
+__device__ __forceinline__ bool list_slice(const RunView& v, ListSlice* ls) {
+  const uint32_t gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const uint32_t sgm = gw / v.seg_warps;
+  if (sgm >= v.n_segments) return false;
+  ls->first = (uint64_t)sgm * v.seg_cap;
+  ls->n = v.seg_count[sgm];
+  ls->j0 = (gw % v.seg_warps) * 32 * kP2 + (threadIdx.x & 31);
+  ls->jstep = 32 * kP2 * v.seg_warps;
+  return true;
+}
+
+// Algorithm 1, insert loop, second pass: every candidate ORs its in/out bases
+// (or the sentinel bit) into the exact table entry of its k-mer. Reads the
+// candidate list (kP2 candidates per thread at a time, so that their loads
+// overlap); if the list overflowed, walks C_temp instead.
+template <int KW, int TS>
 __global__ void __launch_bounds__(kBlock) pass2_insert_kernel(RunView v) {
   const uint64_t cap = *(volatile unsigned long long*)&v.hdr->table_slots;
-  auto insert = [&](uint64_t g) {
-    Occ oc;
-    if (!read_occurrence<KW>(v, g, &oc)) return;
-    if (!table_insert<KW>(v, cap, oc.key, slot_hash(oc.H), oc.tbits)) v.hdr->overflow = 1;
-  };
   if (*(volatile unsigned int*)&v.hdr->round_listed) {
-    // seg_warps warps per list segment
-    const uint32_t gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
-    const uint32_t sgm = gw / v.seg_warps;
-    if (sgm >= v.n_segments) return;
-    const uint64_t* seg = v.cands + (uint64_t)sgm * v.seg_cap;
-    const uint32_t n = v.seg_count[sgm];
-    for (uint32_t j = (gw % v.seg_warps) * 32 + (threadIdx.x & 31); j < n; j += 32 * v.seg_warps)
-      insert(__ldcs(seg + j));
+    ListSlice ls;
+    if (!list_slice(v, &ls)) return;
+    for (uint32_t j = ls.j0; j < ls.n; j += ls.jstep) {
+      Occ oc[kP2];
+      bool ok[kP2];
+#pragma unroll
+      for (int u = 0; u < kP2; ++u) {
+        const uint32_t jj = j + 32 * u;
+        ok[u] = jj < ls.n && read_occurrence<KW>(v, list_at(v, ls.first + jj), &oc[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kP2; ++u)
+        if (ok[u] && !table_insert<TS>(v, cap, oc[u].key, slot_hash(oc[u].H), oc[u].tbits))
+          v.hdr->overflow = 1;
+    }
     return;
   }
   const uint64_t stride = (uint64_t)gridDim.x * kBlock;
-  for (uint64_t g = (uint64_t)blockIdx.x * kBlock + threadIdx.x; g < v.m; g += stride)
-    if ((__ldg(v.ctemp + (g >> 5)) >> (g & 31)) & 1u) insert(g);
+  for (uint64_t g = (uint64_t)blockIdx.x * kBlock + threadIdx.x; g < v.m; g += stride) {
+    if (!((__ldg(v.ctemp + (g >> 5)) >> (g & 31)) & 1u)) continue;
+    Occ oc;
+    if (!read_occurrence<KW>(v, g, &oc)) continue;
+    if (!table_insert<TS>(v, cap, oc.key, slot_hash(oc.H), oc.tbits)) v.hdr->overflow = 1;
+  }
 }
 
 // Algorithm 1, probe loop, second pass: a candidate is a junction iff its
 // k-mer is a sentinel or has more than one distinct in- or out-base. Sets
 // the junction's bit of C_final (cleared before the first round).
-template <int KW>
+template <int KW, int TS>
 __global__ void __launch_bounds__(kBlock) pass2_classify_kernel(RunView v) {
   const uint64_t cap = *(volatile unsigned long long*)&v.hdr->table_slots;
   unsigned long long found = 0;
-  auto classify = [&](uint64_t g) {
-    Occ oc;
-    if (!read_occurrence<KW>(v, g, &oc)) return;
-    const int mk = table_find<KW>(v, cap, oc.key, slot_hash(oc.H));
+  auto mark = [&](uint64_t g, int mk) {
     if (mk < 0) v.hdr->overflow = 1;
     if (mk < 0 || is_junction_mask(mk)) {
       atomicOr(v.cfinal + (g >> 5), 1u << (g & 31));
@@ -778,18 +843,34 @@ __global__ void __launch_bounds__(kBlock) pass2_classify_kernel(RunView v) {
     }
   };
   if (*(volatile unsigned int*)&v.hdr->round_listed) {
-    const uint32_t gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
-    const uint32_t sgm = gw / v.seg_warps;
-    if (sgm < v.n_segments) {
-      const uint64_t* seg = v.cands + (uint64_t)sgm * v.seg_cap;
-      const uint32_t n = v.seg_count[sgm];
-      for (uint32_t j = (gw % v.seg_warps) * 32 + (threadIdx.x & 31); j < n; j += 32 * v.seg_warps)
-        classify(__ldcs(seg + j));
+    ListSlice ls;
+    if (list_slice(v, &ls)) {
+      for (uint32_t j = ls.j0; j < ls.n; j += ls.jstep) {
+        Occ oc[kP2];
+        uint64_t g[kP2];
+        bool ok[kP2];
+#pragma unroll
+        for (int u = 0; u < kP2; ++u) {
+          const uint32_t jj = j + 32 * u;
+          g[u] = jj < ls.n ? list_at(v, ls.first + jj) : 0;
+          ok[u] = jj < ls.n && read_occurrence<KW>(v, g[u], &oc[u]);
+        }
+        int mk[kP2];
+#pragma unroll
+        for (int u = 0; u < kP2; ++u) mk[u] = ok[u] ? table_find<TS>(v, cap, oc[u].key, slot_hash(oc[u].H)) : 0;
+#pragma unroll
+        for (int u = 0; u < kP2; ++u)
+          if (ok[u]) mark(g[u], mk[u]);
+      }
     }
   } else {
     const uint64_t stride = (uint64_t)gridDim.x * kBlock;
-    for (uint64_t g = (uint64_t)blockIdx.x * kBlock + threadIdx.x; g < v.m; g += stride)
-      if ((__ldg(v.ctemp + (g >> 5)) >> (g & 31)) & 1u) classify(g);
+    for (uint64_t g = (uint64_t)blockIdx.x * kBlock + threadIdx.x; g < v.m; g += stride) {
+      if (!((__ldg(v.ctemp + (g >> 5)) >> (g & 31)) & 1u)) continue;
+      Occ oc;
+      if (!read_occurrence<KW>(v, g, &oc)) continue;
+      mark(g, table_find<TS>(v, cap, oc.key, slot_hash(oc.H)));
+    }
   }
   block_add(found, &v.hdr->pass2_kept);
 }
@@ -870,84 +951,113 @@ __global__ void __launch_bounds__(1024) partition_cut_kernel(RunView v, int roun
   }
 }
 
-// Emit, step 1: junctions per tile of kEmitTileWords bitmap words.
-__global__ void __launch_bounds__(kBlock) emit_count_kernel(RunView v) {
-  for (uint64_t tile = blockIdx.x; tile < v.n_tiles; tile += gridDim.x) {
-    const uint64_t w = tile * kEmitTileWords + threadIdx.x;
-    uint32_t c = (w < v.bitmap_words) ? __popc(v.cfinal[w]) : 0u;
+// Emit (single pass): tiles of kEmitTileWords bitmap words are claimed in
+// order from a ticket; each publishes its junction count, looks back over its
+// predecessors for the exclusive prefix (decoupled look-back, Merrill &
+// Garland 2016), publishes its inclusive prefix and writes the position of
+// every junction within its string, in ascending order (C_final of
+// Algorithm 3). Tiles are claimed in order, so every wait is on a block that
+// is already running; a wait that exceeds kSpinLimit polls sets the timeout
+// flag and gives up (the result is then reported as invalid).
+constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagPrefix = 2ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__global__ void __launch_bounds__(kBlock) emit_kernel(RunView v) {
+  __shared__ unsigned long long tile_s, prefix_s;
+  volatile unsigned long long* status =
+      reinterpret_cast<volatile unsigned long long*>(v.tile_prefix);  // n_tiles entries, zeroed per run
+  for (;;) {
+    if (threadIdx.x == 0) tile_s = atomicAdd(&v.hdr->emit_ticket, 1ull);
+    __syncthreads();
+    const uint64_t tile = tile_s;
+    if (tile >= v.n_tiles) break;
+    // word q * kBlock + threadIdx.x of the tile, for q < kEmitWordsPerThread:
+    // in step q the block holds kBlock consecutive words
+    const uint64_t base = tile * kEmitTileWords + threadIdx.x;
+    uint32_t words[kEmitWordsPerThread];
+    uint32_t c = 0;
+#pragma unroll
+    for (int q = 0; q < kEmitWordsPerThread; ++q) {
+      const uint64_t w = base + (uint64_t)q * kBlock;
+      words[q] = (w < v.bitmap_words) ? __ldcg(v.cfinal + w) : 0u;
+      c += __popc(words[q]);
+    }
     uint32_t tot;
     block_exclusive_scan(c, &tot);
-    if (threadIdx.x == 0) v.tile_count[tile] = tot;
-  }
-}
-
-// Emit, step 2: exclusive prefix over tiles (one block); flags a short output.
-__global__ void __launch_bounds__(1024) emit_scan_kernel(RunView v) {
-  __shared__ unsigned long long wsum[32];
-  __shared__ unsigned long long carry_s;
-  if (threadIdx.x == 0) carry_s = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (uint64_t base = 0; base < v.n_tiles; base += 1024) {
-    const uint64_t i = base + threadIdx.x;
-    const unsigned long long x = (i < v.n_tiles) ? v.tile_count[i] : 0ull;
-    unsigned long long inc = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
+    if (threadIdx.x == 0) {
+      unsigned long long prefix = 0;
+      if (tile == 0) {
+        status[0] = kFlagPrefix | tot;
+      } else {
+        status[tile] = kFlagAgg | tot;
+        uint64_t j = tile - 1;
+        uint32_t spins = 0;
+        for (;;) {
+          const unsigned long long st = status[j];
+          if (st & kFlagPrefix) {
+            prefix += st & kValMask;
+            break;
+          }
+          if (st & kFlagAgg) {
+            prefix += st & kValMask;
+            --j;  // tile 0 only ever holds a prefix, so j stays >= 0
+            continue;
+          }
+          if (++spins > kSpinLimit) {
+            v.hdr->timeout = 1;
+            break;
+          }
+          __nanosleep(32);
+        }
+        status[tile] = kFlagPrefix | (prefix + tot);
+      }
+      prefix_s = prefix;
     }
-    if (lane == 31) wsum[wid] = inc;
     __syncthreads();
-    unsigned long long before = 0, all = 0;
-    for (int w = 0; w < 32; ++w) {
-      before += (w < wid) ? wsum[w] : 0ull;
-      all += wsum[w];
-    }
-    const unsigned long long c0 = carry_s;
-    if (i < v.n_tiles) v.tile_prefix[i] = c0 + before + inc - x;
-    __syncthreads();
-    if (threadIdx.x == 0) carry_s = c0 + all;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    v.tile_prefix[v.n_tiles] = carry_s;
-    if (carry_s > v.out_capacity) v.hdr->overflow = 1;
-  }
-}
-
-// Emit, step 3: every junction bit becomes its position within its string,
-// in ascending order (C_final of Algorithm 3).
-__global__ void __launch_bounds__(kBlock) emit_write_kernel(RunView v) {
-  for (uint64_t tile = blockIdx.x; tile < v.n_tiles; tile += gridDim.x) {
-    const uint64_t w = tile * kEmitTileWords + threadIdx.x;
-    uint32_t bits = (w < v.bitmap_words) ? v.cfinal[w] : 0u;
-    uint32_t tot;
-    const uint32_t excl = block_exclusive_scan(__popc(bits), &tot);
-    uint64_t at = v.tile_prefix[tile] + excl;
+    uint64_t at_base = prefix_s;
     Bounds bd{1, 0};
-    while (bits) {
-      const uint32_t b = __ffs(bits) - 1;
-      bits &= bits - 1;
-      const uint64_t g = w * 32 + b;
-      if (g < bd.start || g >= bd.end) bd = seq_bounds(v, g);
-      if (at < v.out_capacity) v.out_positions[at] = g - bd.start;
-      ++at;
+#pragma unroll
+    for (int q = 0; q < kEmitWordsPerThread; ++q) {
+      uint32_t step_tot;
+      uint64_t at = at_base + block_exclusive_scan(__popc(words[q]), &step_tot);
+      at_base += step_tot;
+      uint32_t bits = words[q];
+      const uint64_t w = base + (uint64_t)q * kBlock;
+      while (bits) {
+        const uint32_t b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        const uint64_t g = w * 32 + b;
+        if (g < bd.start || g >= bd.end) bd = seq_bounds(v, g);
+        if (at < v.out_capacity) v.out_positions[at] = g - bd.start;
+        ++at;
+      }
     }
+    __syncthreads();
   }
 }
 
-// Emit, step 4: offsets[t] = junctions in strings before t.
+// offsets[t] = junctions in strings before t (one block per string); the
+// last entry is the total, checked against the output's capacity.
 __global__ void __launch_bounds__(kBlock) emit_offsets_kernel(RunView v) {
-  const uint64_t t = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
-  if (t > v.n_seqs) return;
+  const uint64_t t = blockIdx.x;
   const uint64_t g = (t == v.n_seqs) ? v.m : __ldg(v.offsets + t);
   const uint64_t w = g >> 5;
   const uint64_t tile = w / kEmitTileWords;
-  uint64_t cnt = v.tile_prefix[tile < v.n_tiles ? tile : v.n_tiles];
-  for (uint64_t x = tile * kEmitTileWords; x < w; ++x) cnt += __popc(v.cfinal[x]);
-  if (g & 31) cnt += __popc(v.cfinal[w] & ((1u << (g & 31)) - 1u));
-  v.out_offsets[t] = cnt;
+  unsigned long long cnt = 0;
+  for (uint64_t x = tile * kEmitTileWords + threadIdx.x; x < w; x += kBlock) cnt += __popc(__ldcg(v.cfinal + x));
+  __shared__ unsigned long long part[kBlock / 32];
+  cnt = warp_sum(cnt);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cnt = 0;
+    for (int i = 0; i < kBlock / 32; ++i) cnt += part[i];
+    if (tile > 0) cnt += __ldcg(reinterpret_cast<const unsigned long long*>(v.tile_prefix) + (tile - 1)) & kValMask;
+    if (g & 31) cnt += __popc(__ldcg(v.cfinal + w) & ((1u << (g & 31)) - 1u));
+    v.out_offsets[t] = cnt;
+    if (t == v.n_seqs && cnt > v.out_capacity) v.hdr->overflow = 1;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -983,18 +1093,13 @@ int done(int n) {
 void count_launches(int n) { g_launches.fetch_add((unsigned long long)n); }
 
 int launch_init(const RunView& v, cudaStream_t s) {
-  {
-    Timed t("init", s);
-    init_kernel<<<1, 32, 0, s>>>(v);
-  }
-  return done(1);
+  return cudaMemsetAsync(v.hdr, 0, sizeof(DevHeader), s) == cudaSuccess ? 0 : -1;
 }
 
 int launch_pack(const RunView& v, cudaStream_t s) {
-  if (v.packed_words == 0) return 0;
   {
     Timed t("pack", s);
-    pack_kernel<<<grid_for(pack_kernel, kBlock, v.packed_words), kBlock, 0, s>>>(v);
+    pack_kernel<<<grid_for(pack_kernel, kBlock, (v.packed_words + 3) / 4), kBlock, 0, s>>>(v);
   }
   return done(1);
 }
@@ -1037,7 +1142,7 @@ int launch_partition(const RunView& v, int rounds, cudaStream_t s) {
   return done(2);
 }
 
-template <int KW, bool RD, int HB>
+template <int KW, bool RD, int HB, int TS>
 int round_impl(const RunView& v, int round, cudaStream_t s) {
   if (cudaMemsetAsync(v.filter, 0, v.filter_words64 * 8, s) != cudaSuccess) return -1;
   if (cudaMemsetAsync(v.lc_bits, 0, (1ull << v.lc_log2) / 8, s) != cudaSuccess) return -1;
@@ -1059,32 +1164,28 @@ int round_impl(const RunView& v, int round, cudaStream_t s) {
     pass1_probe_kernel<KW, RD, HB><<<grid, kBlock, 0, s>>>(pv, round);
   }
   {
-    Timed t("lc_count", s);
-    lc_count_kernel<<<grid_for(lc_count_kernel, kBlock, (1ull << v.lc_log2) / 32), kBlock, 0, s>>>(pv);
-  }
-  {
     Timed t("table_setup", s);
-    table_setup_kernel<<<1, 32, 0, s>>>(pv);
+    table_setup_kernel<<<grid_for(table_setup_kernel, kBlock, (1ull << v.lc_log2) / 32), kBlock, 0, s>>>(pv);
   }
   {
     Timed t("table_clear", s);
-    table_clear_kernel<KW><<<grid_for(table_clear_kernel<KW>, kBlock, v.table_max_slots), kBlock, 0, s>>>(pv);
+    table_clear_kernel<TS><<<grid_for(table_clear_kernel<TS>, kBlock, v.table_max_slots), kBlock, 0, s>>>(pv);
   }
   // pass 2: enough warps per list segment to fill the GPU (a walk of C_temp
   // if a segment overflowed reuses the same grid)
   const uint32_t want_warps = (uint32_t)sm_count() * 64u;
-  pv.seg_warps = (want_warps + pv.n_segments - 1) / pv.n_segments;
+  pv.seg_warps = (want_warps + pv.n_segments - 1) / pv.n_segments;  // per segment
   if (pv.seg_warps < 1) pv.seg_warps = 1;
   const unsigned g2 = (unsigned)(((uint64_t)pv.n_segments * pv.seg_warps * 32 + kBlock - 1) / kBlock);
   {
     Timed t("pass2_insert", s);
-    pass2_insert_kernel<KW><<<g2, kBlock, 0, s>>>(pv);
+    pass2_insert_kernel<KW, TS><<<g2, kBlock, 0, s>>>(pv);
   }
   {
     Timed t("pass2_classify", s);
-    pass2_classify_kernel<KW><<<g2, kBlock, 0, s>>>(pv);
+    pass2_classify_kernel<KW, TS><<<g2, kBlock, 0, s>>>(pv);
   }
-  return done(7);
+  return done(6);
 }
 
 int launch_round(const RunView& v, int round, int rounds, cudaStream_t s) {
@@ -1092,10 +1193,13 @@ int launch_round(const RunView& v, int round, int rounds, cudaStream_t s) {
   int rc = 0;
   with_hashes(v.hashes, [&](auto hb) {
     constexpr int HB = decltype(hb)::value;
-    if (v.k <= 31)
-      rc = rounds > 1 ? round_impl<1, true, HB>(v, round, s) : round_impl<1, false, HB>(v, round, s);
+    const int ts = table_slot_kind(v.k);
+    if (ts == 0)
+      rc = rounds > 1 ? round_impl<1, true, HB, 0>(v, round, s) : round_impl<1, false, HB, 0>(v, round, s);
+    else if (ts == 1)
+      rc = rounds > 1 ? round_impl<1, true, HB, 1>(v, round, s) : round_impl<1, false, HB, 1>(v, round, s);
     else
-      rc = rounds > 1 ? round_impl<2, true, HB>(v, round, s) : round_impl<2, false, HB>(v, round, s);
+      rc = rounds > 1 ? round_impl<2, true, HB, 2>(v, round, s) : round_impl<2, false, HB, 2>(v, round, s);
   });
   return rc;
 }
@@ -1103,23 +1207,14 @@ int launch_round(const RunView& v, int round, int rounds, cudaStream_t s) {
 int launch_emit(const RunView& v, cudaStream_t s) {
   int n = 0;
   if (v.n_tiles) {
-    Timed t("emit_count", s);
-    emit_count_kernel<<<grid_for(emit_count_kernel, kBlock, v.n_tiles * kBlock), kBlock, 0, s>>>(v);
-    n++;
-  }
-  {
-    Timed t("emit_scan", s);
-    emit_scan_kernel<<<1, 1024, 0, s>>>(v);
-    n++;
-  }
-  if (v.n_tiles) {
-    Timed t("emit_write", s);
-    emit_write_kernel<<<grid_for(emit_write_kernel, kBlock, v.n_tiles * kBlock), kBlock, 0, s>>>(v);
+    if (cudaMemsetAsync(v.tile_prefix, 0, v.n_tiles * 8, s) != cudaSuccess) return -1;
+    Timed t("emit", s);
+    emit_kernel<<<grid_for(emit_kernel, kBlock, v.n_tiles * kBlock), kBlock, 0, s>>>(v);
     n++;
   }
   {
     Timed t("emit_offsets", s);
-    emit_offsets_kernel<<<(unsigned)((v.n_seqs + 1 + kBlock - 1) / kBlock), kBlock, 0, s>>>(v);
+    emit_offsets_kernel<<<(unsigned)(v.n_seqs + 1), kBlock, 0, s>>>(v);
     n++;
   }
   return done(n);

@@ -31,6 +31,19 @@ __global__ void __launch_bounds__(256) sector_reads(const ulonglong2* __restrict
   if (acc == 0x1234567ull) sink[0] = acc;  // keeps the loads alive
 }
 
+__global__ void __launch_bounds__(256) word_reads(const unsigned long long* __restrict__ buf,
+                                                 uint64_t word_mask, int iters,
+                                                 unsigned long long* sink) {
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t acc = 0;
+  uint64_t h = mix(tid + 3);
+  for (int it = 0; it < iters; ++it) {
+    h = mix(h + 0x9e3779b97f4a7c15ull);
+    acc ^= __ldcg(buf + (h & word_mask));
+  }
+  if (acc == 0x1234567ull) sink[0] = acc;
+}
+
 __global__ void __launch_bounds__(256) sector_ors(unsigned long long* __restrict__ buf,
                                                  uint64_t block_mask, int iters) {
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -46,7 +59,8 @@ __global__ void __launch_bounds__(256) sector_ors(unsigned long long* __restrict
 
 extern "C" {
 
-// mode 0: random sector reads; mode 1: random 64-bit ORs (one per sector).
+// mode 0: random 32-byte sector reads; mode 1: random 64-bit ORs (one per
+// sector); mode 2: random 8-byte reads.
 // buf_bytes: power of two >= 32. Returns sector operations per second, or a
 // negative value on a CUDA error. Allocates and frees its own buffer.
 double peaks_l2_random_rate(int mode, uint64_t buf_bytes, int iters, int reps) {
@@ -59,7 +73,8 @@ double peaks_l2_random_rate(int mode, uint64_t buf_bytes, int iters, int reps) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (mode == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sector_reads, 256, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sector_ors, 256, 0);
+  else if (mode == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sector_ors, 256, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, word_reads, 256, 0);
   const unsigned grid = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
   const uint64_t mask = buf_bytes / 32 - 1;
   cudaEvent_t a, b;
@@ -69,7 +84,8 @@ double peaks_l2_random_rate(int mode, uint64_t buf_bytes, int iters, int reps) {
   for (int r = 0; r <= reps; ++r) {  // first launch is a warm-up
     cudaEventRecord(a);
     if (mode == 0) sector_reads<<<grid, 256>>>(static_cast<const ulonglong2*>(buf), mask, iters, sink);
-    else sector_ors<<<grid, 256>>>(static_cast<unsigned long long*>(buf), mask, iters);
+    else if (mode == 1) sector_ors<<<grid, 256>>>(static_cast<unsigned long long*>(buf), mask, iters);
+    else word_reads<<<grid, 256>>>(static_cast<const unsigned long long*>(buf), buf_bytes / 8 - 1, iters, sink);
     cudaEventRecord(b);
     cudaEventSynchronize(b);
     float ms = 0.f;

@@ -85,6 +85,13 @@ def _lib() -> ctypes.CDLL:
         L.twopaco_read_state.restype = I
         L.twopaco_kernel_launches.argtypes = []
         L.twopaco_kernel_launches.restype = ctypes.c_ulonglong
+        L.twopaco_context_create.argtypes = [ctypes.POINTER(ctypes.c_void_p)]
+        L.twopaco_context_create.restype = I
+        L.twopaco_context_destroy.argtypes = [P]
+        L.twopaco_context_destroy.restype = None
+        L.twopaco_build_ctx.argtypes = [P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(U64), U64,
+                                        I, U64, I, ctypes.POINTER(_Options), ctypes.POINTER(_Result)]
+        L.twopaco_build_ctx.restype = I
         L.twopaco_profile_enable.argtypes = [I]
         L.twopaco_profile_enable.restype = I
         L.twopaco_profile_kernels.argtypes = [ctypes.POINTER(ctypes.c_char_p),
@@ -175,6 +182,52 @@ def twopaco_build_ex(seqs: Sequence, k: int, filter_bits: int, rounds: int = 1,
     finally:
         L.twopaco_result_free(out)
     return [pos[off[t]:off[t + 1]] for t in range(n)], stats
+
+
+class Context:
+    """A reusable build context (``twopaco_context_create``): device and pinned
+    buffers survive across ``build`` calls, so repeated builds allocate nothing."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        rc = _lib().twopaco_context_create(ctypes.byref(h))
+        if rc != OK:
+            raise TwopacoError(rc, "twopaco_context_create")
+        self._h = h
+
+    def close(self) -> None:
+        if self._h:
+            _lib().twopaco_context_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build(self, seqs: Sequence, k: int, filter_bits: int, rounds: int = 1,
+              options: Optional[Options] = None, copy: bool = True):
+        """twopaco_build_ctx: (list of junction-position arrays, stats). With
+        copy=False the arrays are views of the context's pinned buffers, valid
+        until the next call."""
+        arrs = [_as_bytes(s) for s in seqs]
+        n = len(arrs)
+        ptrs = (ctypes.c_void_p * max(n, 1))(*[a.ctypes.data if a.size else None for a in arrs])
+        lens = (ctypes.c_uint64 * max(n, 1))(*[a.size for a in arrs])
+        res = _Result()
+        opt = (options or Options())._c()
+        rc = _lib().twopaco_build_ctx(self._h, ptrs, lens, n, int(k), int(filter_bits), int(rounds),
+                                      ctypes.byref(opt), ctypes.byref(res))
+        if rc != OK:
+            raise TwopacoError(rc, "twopaco_build_ctx")
+        off = np.ctypeslib.as_array(res.offsets, shape=(n + 1,))
+        total = int(off[-1])
+        pos = (np.ctypeslib.as_array(res.positions, shape=(total,)) if total
+               else np.zeros(0, np.uint64))
+        if copy:
+            off, pos = off.copy(), pos.copy()
+        return [pos[off[t]:off[t + 1]] for t in range(n)], _stats_dict(res.stats)
 
 
 def twopaco_build(seqs: Sequence, k: int, filter_bits: int, rounds: int = 1):

@@ -282,3 +282,25 @@ def test_candidate_list_overflow_falls_back_to_bitmap_walk():
     got, _ = T().twopaco_build_ex(seqs, 25, 1 << 18, 2,
                                   T().Options(hashes=3, candidate_records=500, partition_bins=64))
     _eq(got, want)
+
+
+def test_context_reuse_across_sizes_and_k():
+    """One context, builds of growing and shrinking inputs: every result exact."""
+    ctx = T().Context()
+    cases = [("plain_single", 0.02, 25), ("plain_single", 0.25, 25), ("batched_set", 0.01, 31),
+             ("plain_single", 0.02, 63), ("plain_single", 0.05, 17)]
+    for name, scale, k in cases:
+        seqs = _named(name, scale)
+        got, st = ctx.build(seqs, k, 1 << 20, 1, T().Options(hashes=4))
+        _eq(got, O.junctions(G.concat(seqs), k))
+        assert st["pass2_marks"] == sum(g.size for g in got)
+    # views into the context's buffers: valid until the next call
+    seqs = _named("plain_single", 0.02)
+    view, _ = ctx.build(seqs, 25, 1 << 20, 1, copy=False)
+    _eq(view, O.junctions(G.concat(seqs), 25))
+    with pytest.raises(T().TwopacoError) as e:
+        ctx.build(["ACGTNNACGT"], 3, 1 << 12, 1)
+    assert e.value.code == T().EBADBASE
+    got, _ = ctx.build(seqs, 25, 1 << 20, 2, T().Options(partition_bins=256))
+    _eq(got, O.junctions(G.concat(seqs), 25))
+    ctx.close()
