@@ -48,6 +48,7 @@ extern "C" {
 #define TWOPACO_ETIMEOUT (-4)  /* a bounded device wait gave up */
 #define TWOPACO_ECUDA (-5)     /* a CUDA runtime call failed */
 #define TWOPACO_EOVERFLOW (-6) /* the pass-2 table or the output buffer is too small */
+#define TWOPACO_ESCRATCH (-7)  /* the run needs more than the no-alloc scratch buffer holds */
 
 typedef struct twopaco_options {
   int hashes;              /* bits per filter item, 1..8 (paper default 4) */
@@ -169,6 +170,37 @@ void twopaco_context_destroy(twopaco_context* ctx);
 int twopaco_build_ctx(twopaco_context* ctx, const char* const* seqs, const uint64_t* lengths,
                       uint64_t n_seqs, int k, uint64_t filter_bits, int rounds,
                       const twopaco_options* opt, twopaco_result* out);
+
+/*
+ * Device-resident run that allocates nothing. The paper has no counterpart:
+ * this is an interface for callers that are not allowed to allocate device
+ * memory -- code running inside a host framework whose pool owns all device
+ * memory (a raw cudaMalloc there is forbidden or fragments the pool), or
+ * latency-critical callers that cannot afford cudaMalloc's device-wide
+ * synchronisation. Instead of a caller workspace it uses one scratch buffer of
+ * TWOPACO_NOALLOC_SCRATCH_BYTES (32 MiB) in static device memory, which every
+ * GPU that loads the library holds until the process exits.
+ *   Arguments and results are those of twopaco_run_device without the
+ *   workspace: the caller still passes the input (d_bases, d_offsets) and the
+ *   output (d_out_offsets, d_out_positions) in device memory. The call waits
+ *   for the run to finish on options->cuda_stream and fills *stats (may be
+ *   NULL), returning TWOPACO_EBADBASE / TWOPACO_EOVERFLOW / TWOPACO_ETIMEOUT as
+ *   twopaco_read_stats does.
+ *   A run whose workspace (twopaco_workspace_size) exceeds the buffer is
+ *   rejected with TWOPACO_ESCRATCH before anything is launched; a small
+ *   options->table_slots and candidate_records shrink the workspace.
+ *   The first call on a device looks up the buffer's device address on that
+ *   device; make that first call before any stream capture.
+ *   Every call on a device shares the one buffer and the run clears what it
+ *   needs; calls whose work overlaps on the GPU (other host threads, other
+ *   streams) race on it and must be serialised by the caller.
+ */
+#define TWOPACO_NOALLOC_SCRATCH_BYTES (32ull << 20)
+int twopaco_run_device_noalloc(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_seqs,
+                               uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
+                               const twopaco_options* opt, uint64_t* d_out_offsets,
+                               uint64_t* d_out_positions, uint64_t out_capacity,
+                               twopaco_stats* stats);
 
 /* Which internal state twopaco_read_state copies out. */
 #define TWOPACO_STATE_CANDIDATES 0 /* C_temp of the last round: ceil(total_bases/32) uint32 words */

@@ -187,6 +187,7 @@ const char* twopaco_strerror(int code) {
     case TWOPACO_ETIMEOUT: return "a bounded device wait gave up";
     case TWOPACO_ECUDA: return "CUDA error";
     case TWOPACO_EOVERFLOW: return "pass-2 table or output buffer too small";
+    case TWOPACO_ESCRATCH: return "run needs more than the no-alloc scratch buffer holds";
     default: return "unknown error";
   }
 }

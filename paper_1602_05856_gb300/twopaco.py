@@ -20,7 +20,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtwopaco.so")
 
-OK, EINVAL, EBADBASE, ENOMEM, ETIMEOUT, ECUDA, EOVERFLOW = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, EBADBASE, ENOMEM, ETIMEOUT, ECUDA, EOVERFLOW, ESCRATCH = 0, -1, -2, -3, -4, -5, -6, -7
+NOALLOC_SCRATCH_BYTES = 32 << 20
 STATE_CANDIDATES, STATE_JUNCTIONS, STATE_BINS, STATE_CUTS = 0, 1, 2, 3
 
 
@@ -79,6 +80,9 @@ def _lib() -> ctypes.CDLL:
         L.twopaco_run_device.argtypes = [P, P, U64, U64, I, U64, I, ctypes.POINTER(_Options), P, U64,
                                          P, P, U64]
         L.twopaco_run_device.restype = I
+        L.twopaco_run_device_noalloc.argtypes = [P, P, U64, U64, I, U64, I, ctypes.POINTER(_Options),
+                                                 P, P, U64, ctypes.POINTER(_Stats)]
+        L.twopaco_run_device_noalloc.restype = I
         L.twopaco_read_stats.argtypes = [P, P, ctypes.POINTER(_Stats)]
         L.twopaco_read_stats.restype = I
         L.twopaco_read_state.argtypes = [P, I, P, U64, P]
@@ -256,6 +260,26 @@ def twopaco_run_device(d_bases: int, d_offsets: int, n_seqs: int, total_bases: i
                                    d_out_positions or None, int(out_capacity))
     if rc != OK:
         raise TwopacoError(rc, "twopaco_run_device")
+
+
+def twopaco_run_device_noalloc(d_bases: int, d_offsets: int, n_seqs: int, total_bases: int, k: int,
+                               filter_bits: int, rounds: int, options: Optional[Options],
+                               d_out_offsets: int, d_out_positions: int, out_capacity: int,
+                               check: bool = True) -> Dict[str, int]:
+    """The run that allocates nothing (its workspace is the library's static
+    scratch buffer); waits for the run and returns its stats."""
+    opt = (options or Options())._c()
+    st = _Stats()
+    rc = _lib().twopaco_run_device_noalloc(d_bases or None, d_offsets or None, int(n_seqs),
+                                           int(total_bases), int(k), int(filter_bits), int(rounds),
+                                           ctypes.byref(opt), d_out_offsets or None,
+                                           d_out_positions or None, int(out_capacity),
+                                           ctypes.byref(st))
+    if check and rc != OK:
+        raise TwopacoError(rc, "twopaco_run_device_noalloc")
+    d = _stats_dict(st)
+    d["rc"] = int(rc)
+    return d
 
 
 def twopaco_read_stats(d_workspace: int, cuda_stream: int = 0, check: bool = True) -> Dict[str, int]:
