@@ -258,6 +258,14 @@ __device__ __forceinline__ bool read_occurrence(const RunView& v, uint64_t g, Oc
   return true;
 }
 
+// Distance from p0 to x, clamped to [-2^30, 2^30] (positions within one
+// thread's chunk are compared in 32 bits).
+__device__ __forceinline__ int32_t rel(uint64_t x, uint64_t p0) {
+  constexpr int64_t kClamp = 1ll << 30;
+  const int64_t d = (int64_t)(x - p0);
+  return (int32_t)(d > kClamp ? kClamp : (d < -kClamp ? -kClamp : d));
+}
+
 // Visit the kR consecutive positions p0 .. p0 + kR - 1 (p0 < m), rolling the
 // k-mer from each position to the next within a string and reading it from
 // scratch after a string boundary. fn(i, p, valid, occ) runs for every i,
@@ -266,6 +274,8 @@ template <int KW, typename F>
 __device__ __forceinline__ void walk(const RunView& v, uint64_t p0, F&& fn) {
   const int k = v.k;
   Bounds b = seq_bounds(v, p0);
+  int32_t s_rel = rel(b.start, p0), e_rel = rel(b.end, p0);  // string bounds relative to p0
+  const int32_t m_rel = rel(v.m, p0);
   // bases p0 + k .. p0 + k + kR - 1: the successor of each position, which is
   // also the base that enters the k-mer when it slides to the next position
   const uint32_t next = (uint32_t)(bases32(v.packed, p0 + (uint64_t)k) >> 32);
@@ -276,18 +286,20 @@ __device__ __forceinline__ void walk(const RunView& v, uint64_t p0, F&& fn) {
     const uint64_t p = p0 + i;
     Occ oc;
     bool valid = false;
-    if (p < v.m) {
-      if (p >= b.end) {
+    if (i < m_rel) {
+      if (i >= e_rel) {  // p starts a later string
         b = seq_bounds(v, p);
+        s_rel = rel(b.start, p0);
+        e_rel = rel(b.end, p0);
         fresh = true;
       }
-      if (p + (uint64_t)k <= b.end) {
+      if (i + k <= e_rel) {
         valid = true;
         uint32_t pred;
         if (fresh) {
           f = load_kmer<KW>(v.packed, p, k);
           if (v.both) r = revcomp<KW>(f, k);
-          pred = p > b.start ? base_at(v.packed, p - 1) : 0u;
+          pred = i > s_rel ? base_at(v.packed, p - 1) : 0u;
           fresh = false;
         } else {
           // the first base of the previous k-mer
@@ -296,7 +308,7 @@ __device__ __forceinline__ void walk(const RunView& v, uint64_t p0, F&& fn) {
           roll<KW>(f, r, i > 0 ? (next >> (32 - 2 * i)) & 3u : 0u, k);
         }
         const uint32_t succ = (next >> (30 - 2 * i)) & 3u;
-        const bool sentinel = p == b.start || p + (uint64_t)k == b.end;
+        const bool sentinel = i == s_rel || i + k == e_rel;
         make_occ<KW>(v, f, v.both ? r : f, pred, succ, sentinel, &oc);
       } else {
         fresh = true;
@@ -321,8 +333,9 @@ __device__ __forceinline__ bool in_round(const RunView& v, uint64_t H, int round
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ unsigned long long* filter_word(const RunView& v, uint64_t H, uint64_t G) {
-  const uint64_t block = v.lg_blocks ? (H >> (64 - v.lg_blocks)) : 0ull;
-  return v.filter + block * 4 + (G >> 62);
+  // b <= 2^40 bits: the block index has at most 32 bits
+  const uint32_t block = v.lg_blocks ? (uint32_t)(H >> (64 - v.lg_blocks)) : 0u;
+  return v.filter + ((uint64_t)block * 4u + (uint32_t)(G >> 62));
 }
 
 __device__ __forceinline__ uint32_t bit_base(uint64_t G, int u) {
@@ -331,15 +344,30 @@ __device__ __forceinline__ uint32_t bit_base(uint64_t G, int u) {
   return (uint32_t)(G >> sh) & 31u;
 }
 
+// The bits of item 0 in each half of the word; item j is both halves
+// rotated left by j (bit (base_u + j) mod 32).
+struct ItemPattern {
+  uint32_t lo, hi;
+};
+
 template <int HB>
-__device__ __forceinline__ uint64_t item_bits(uint64_t G, uint32_t j) {
-  uint32_t lo = 0, hi = 0;
+__device__ __forceinline__ ItemPattern item_pattern(uint64_t G) {
+  ItemPattern p{0u, 0u};
 #pragma unroll
   for (int u = 0; u < HB; ++u) {
-    const uint32_t b = 1u << ((bit_base(G, u) + j) & 31u);
-    if (u & 1) hi |= b; else lo |= b;
+    const uint32_t b = 1u << bit_base(G, u);
+    if (u & 1) p.hi |= b; else p.lo |= b;
   }
-  return ((uint64_t)hi << 32) | lo;
+  return p;
+}
+
+__device__ __forceinline__ uint64_t item_bits(const ItemPattern& p, uint32_t j) {
+  return ((uint64_t)__funnelshift_l(p.hi, p.hi, j) << 32) | __funnelshift_l(p.lo, p.lo, j);
+}
+
+template <int HB>
+__device__ __forceinline__ uint64_t item_bits(uint64_t G, uint32_t j) {
+  return item_bits(item_pattern<HB>(G), j);
 }
 
 // Bit j of the result: item j is present (all of its HB bits are set).
@@ -606,9 +634,10 @@ __global__ void __launch_bounds__(kBlock) pass1_insert_kernel(RunView v, int rou
     walk<KW>(v, p0, [&](int, uint64_t, bool valid, const Occ& oc) {
       if (!valid || (ROUNDS && !in_round(v, oc.H, round))) return;
       const uint64_t G = second_hash(oc.H);
+      const ItemPattern pat = item_pattern<HB>(G);
       const uint32_t j1 = __ffs(oc.items) - 1, j2 = 31 - __clz(oc.items);
-      uint64_t m = item_bits<HB>(G, j1);
-      if (j2 != j1) m |= item_bits<HB>(G, j2);
+      uint64_t m = item_bits(pat, j1);
+      if (j2 != j1) m |= item_bits(pat, j2);  // a palindrome's two orientations
       atomicOr(filter_word(v, oc.H, G), (unsigned long long)m);
     });
   }
