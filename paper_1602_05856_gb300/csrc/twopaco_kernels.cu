@@ -731,6 +731,8 @@ __global__ void __launch_bounds__(kBlock, 3) pass1_probe_kernel(RunView v, int r
   if (round == 0) block_add(valid_n, &v.hdr->positions);
 }
 
+constexpr double kTableLoad = 2.0;  // table slots per estimated distinct candidate
+
 // Size the pass-2 table of this round: twice the number of distinct
 // candidate k-mers, estimated by linear counting (Whang, Vander-Zanden &
 // Taylor 1990) from the bits the probe set, rounded up to a power of two (at
@@ -763,7 +765,7 @@ __global__ void __launch_bounds__(kBlock) table_setup_kernel(RunView v) {
     const unsigned long long e = (unsigned long long)(est * 1.1) + 64ull;
     if (e < distinct) distinct = e;
   }
-  unsigned long long want = 2ull * distinct;
+  unsigned long long want = (unsigned long long)(kTableLoad * (double)distinct);
   if (want < 1024ull) want = 1024ull;
   unsigned long long cap = 1ull;
   while (cap < want) cap <<= 1;
