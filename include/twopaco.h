@@ -146,6 +146,45 @@ int twopaco_run_device(const uint8_t* d_bases, const uint64_t* d_offsets, uint64
 int twopaco_read_stats(const void* d_workspace, void* cuda_stream, twopaco_stats* stats);
 
 /*
+ * One edge of the compacted de Bruijn graph: two consecutive junction
+ * positions p < q of one string (section "Reduction to the Problem of Finding
+ * Junction Positions"; Observation 1 makes these exactly the maximal
+ * non-branching paths). The edge spells s[p .. q + k - 1].
+ */
+typedef struct twopaco_edge {
+  uint64_t from_hi, from_lo; /* normalized k-mer at p (value hi * 2^64 + lo, first base most significant) */
+  uint64_t to_hi, to_lo;     /* normalized k-mer at q */
+  uint64_t start;            /* p, within its string */
+  uint64_t length;           /* q - p */
+  uint32_t from_rc, to_rc;   /* 1: the string reads the reverse complement of the stored k-mer */
+} twopaco_edge;
+
+/*
+ * Edges of the last run on a workspace, computed on the device.
+ *   d_workspace      the workspace of a finished twopaco_run_device call (it
+ *                    still holds that run's packed input)
+ *   d_offsets, n_seqs, d_out_offsets, d_out_positions   that call's input
+ *                    offsets and output
+ *   d_edge_offsets   n_seqs + 1 uint64, written: the edges of string t are
+ *                    d_edges[d_edge_offsets[t] .. d_edge_offsets[t+1]), in
+ *                    position order
+ *   d_edges, edge_capacity   room for the edges (at most one per junction)
+ * Launches on cuda_stream without synchronising; more edges than
+ * edge_capacity set the overflow flag (twopaco_read_stats).
+ */
+int twopaco_edges_device(const void* d_workspace, const uint64_t* d_offsets, uint64_t n_seqs,
+                         const uint64_t* d_out_offsets, const uint64_t* d_out_positions,
+                         uint64_t* d_edge_offsets, twopaco_edge* d_edges, uint64_t edge_capacity,
+                         void* cuda_stream);
+
+/* Edges returned by twopaco_edges_ctx (borrowed from the context). */
+typedef struct twopaco_edge_list {
+  uint64_t n_seqs;
+  uint64_t* offsets;   /* n_seqs + 1 entries */
+  twopaco_edge* edges; /* offsets[n_seqs] edges */
+} twopaco_edge_list;
+
+/*
  * Reusable build context. It keeps device buffers (input, workspace, output)
  * and pinned host buffers for the result across calls, growing them only
  * when an input needs more, so repeated builds do no allocation. One context
@@ -201,6 +240,13 @@ int twopaco_run_device_noalloc(const uint8_t* d_bases, const uint64_t* d_offsets
                                const twopaco_options* opt, uint64_t* d_out_offsets,
                                uint64_t* d_out_positions, uint64_t out_capacity,
                                twopaco_stats* stats);
+
+/*
+ * Edges of the last twopaco_build_ctx on this context. out->offsets and
+ * out->edges point into the context's pinned buffers, valid until the next
+ * call on the context.
+ */
+int twopaco_edges_ctx(twopaco_context* ctx, twopaco_edge_list* out);
 
 /* Which internal state twopaco_read_state copies out. */
 #define TWOPACO_STATE_CANDIDATES 0 /* C_temp of the last round: ceil(total_bases/32) uint32 words */

@@ -30,6 +30,8 @@ def lib() -> ctypes.CDLL:
         L.oracle_alg1_exact.argtypes = [P, P, U64, I, I, P]
         L.oracle_pass1.argtypes = [P, P, U64, I, I, U64, I, U64, U64, U64, P, P]
         L.oracle_partition_cuts.argtypes = [P, U64, I, P]
+        L.oracle_edges.argtypes = [P, P, U64, I, I, P, P, P, P, P, P, P, P, P, P]
+        L.oracle_edges.restype = ctypes.c_longlong
         for f in (L.oracle_junctions, L.oracle_alg1_exact, L.oracle_pass1,
                   L.oracle_partition_cuts):
             f.restype = I
@@ -126,3 +128,30 @@ def partition_cuts(counts: Sequence[int], rounds: int) -> np.ndarray:
     cuts = np.zeros(rounds + 1, np.uint64)
     _check(lib().oracle_partition_cuts(c.ctypes.data, c.size, rounds, cuts.ctypes.data))
     return cuts
+
+
+def edges(seqs, k: int, both_strands: bool = True):
+    """Compacted-graph edges by consecutive junction positions, as a dict of arrays.
+
+    Keys: from_hi, from_lo, to_hi, to_lo (normalized k-mers), from_rc, to_rc,
+    start, length (per edge, string order then position order) and
+    per_string (edge count of every string).
+    """
+    flags, off, _ = junction_flags(seqs, k, both_strands)
+    buf, off = _prep(seqs)
+    nj = max(int(flags.sum()), 1)
+    out = {name: np.zeros(nj, np.uint64) for name in ("from_hi", "from_lo", "to_hi", "to_lo",
+                                                         "start", "length")}
+    out["from_rc"] = np.zeros(nj, np.uint8)
+    out["to_rc"] = np.zeros(nj, np.uint8)
+    per = np.zeros(max(off.size - 1, 1), np.uint64)
+    fl = np.ascontiguousarray(flags if flags.size else np.zeros(1, np.uint8))
+    e = lib().oracle_edges(buf.ctypes.data, off.ctypes.data, off.size - 1, k, int(both_strands),
+                           fl.ctypes.data, out["from_hi"].ctypes.data, out["from_lo"].ctypes.data,
+                           out["to_hi"].ctypes.data, out["to_lo"].ctypes.data,
+                           out["from_rc"].ctypes.data, out["to_rc"].ctypes.data,
+                           out["start"].ctypes.data, out["length"].ctypes.data, per.ctypes.data)
+    _check(0 if e >= 0 else int(e))
+    res = {name: a[:e] for name, a in out.items()}
+    res["per_string"] = per[:off.size - 1]
+    return res

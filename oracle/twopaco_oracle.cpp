@@ -30,6 +30,12 @@
  *                      Algorithm"). PINNED by equality with the definition
  *                      and by the brute-force compactor.
  *
+ *   oracle_edges       Compacted-graph edges: one per pair of consecutive
+ *                      junction positions of a string (section "Reduction to
+ *                      the Problem of Finding Junction Positions").
+ *                      PINNED by Observation 1 against the brute-force
+ *                      maximal non-branching paths.
+ *
  *   oracle_pass1       The first pass of Algorithm 2 with the vertex-keyed
  *                      split-block Bloom filter that the CUDA library uses as
  *                      E, restated here from its written specification (see
@@ -361,6 +367,54 @@ int oracle_pass1(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
     counters[1] = kept;
   }
   return ORACLE_OK;
+}
+
+/*
+ * Compacted-graph edges (section "Reduction to the Problem of Finding
+ * Junction Positions"): for every two consecutive junction positions p < q of
+ * a string, one edge from the k-mer at p to the k-mer at q. flags (m bytes)
+ * is the output of oracle_junctions. Edges are written in string order, then
+ * position order; for each: the normalized start and end k-mers (hi, lo
+ * words), whether the string reads the reverse complement of each (0/1), the
+ * start position p and the length q - p. Returns the number of edges, or a
+ * negative error. The arrays hold at least (number of junctions) entries.
+ */
+long long oracle_edges(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
+                       int both_strands, const uint8_t* flags, uint64_t* from_hi, uint64_t* from_lo,
+                       uint64_t* to_hi, uint64_t* to_lo, uint8_t* from_rc, uint8_t* to_rc,
+                       uint64_t* start, uint64_t* length, uint64_t* edges_per_string) {
+  if (k < 1 || k > 63) return ORACLE_EINVAL;
+  const uint64_t m = offsets[n];
+  std::vector<uint8_t> codes;
+  int rc = encode_all(seq, m, &codes);
+  if (rc) return rc;
+  long long e = 0;
+  for (uint64_t t = 0; t < n; ++t) {
+    const uint64_t s0 = offsets[t], len = offsets[t + 1] - offsets[t];
+    long long before = e;
+    bool have_prev = false;
+    uint64_t prev = 0;
+    for (uint64_t i = 0; i + k <= len && len >= (uint64_t)k; ++i) {
+      if (!flags[s0 + i]) continue;
+      if (have_prev) {
+        u128 a = word_at(codes, s0 + prev, k), b = word_at(codes, s0 + i, k);
+        u128 na = normalized(a, k, both_strands), nb = normalized(b, k, both_strands);
+        from_hi[e] = (uint64_t)(na >> 64);
+        from_lo[e] = (uint64_t)na;
+        to_hi[e] = (uint64_t)(nb >> 64);
+        to_lo[e] = (uint64_t)nb;
+        from_rc[e] = (na != a) ? 1 : 0;
+        to_rc[e] = (nb != b) ? 1 : 0;
+        start[e] = prev;
+        length[e] = i - prev;
+        ++e;
+      }
+      have_prev = true;
+      prev = i;
+    }
+    if (edges_per_string) edges_per_string[t] = (uint64_t)(e - before);
+  }
+  return e;
 }
 
 /*

@@ -228,6 +228,21 @@ int twopaco_run_device(const uint8_t* d_bases, const uint64_t* d_offsets, uint64
   return TWOPACO_OK;
 }
 
+int twopaco_edges_device(const void* d_workspace, const uint64_t* d_offsets, uint64_t n_seqs,
+                         const uint64_t* d_out_offsets, const uint64_t* d_out_positions,
+                         uint64_t* d_edge_offsets, twopaco_edge* d_edges, uint64_t edge_capacity,
+                         void* cuda_stream) {
+  static_assert(sizeof(twopaco_edge) == 56, "twopaco_edge layout");
+  if (!d_workspace || !d_out_offsets || !d_edge_offsets || (n_seqs && !d_offsets)) return TWOPACO_EINVAL;
+  if (edge_capacity && !d_edges) return TWOPACO_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_workspace) % kAlign)) return TWOPACO_EINVAL;
+  if (n_seqs >= (1ull << 32)) return TWOPACO_EINVAL;
+  const int rc = launch_edges(static_cast<const DevHeader*>(d_workspace), d_offsets, n_seqs, d_out_offsets,
+                              d_out_positions, d_edge_offsets, d_edges, edge_capacity,
+                              static_cast<cudaStream_t>(cuda_stream));
+  return rc < 0 ? TWOPACO_ECUDA : TWOPACO_OK;
+}
+
 int twopaco_read_stats(const void* d_workspace, void* cuda_stream, twopaco_stats* stats) {
   if (!d_workspace || !stats) return TWOPACO_EINVAL;
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
@@ -393,6 +408,17 @@ struct twopaco_context {
   uint64_t cap_h_out_off = 0;
   uint64_t* h_pos = nullptr;      // pinned: result positions
   uint64_t cap_hpos = 0;
+  // the last build, for twopaco_edges_ctx
+  uint64_t last_n = 0, last_junctions = 0;
+  bool have_last = false;
+  uint64_t* d_edge_off = nullptr;
+  uint64_t cap_d_edge_off = 0;
+  twopaco_edge* d_edges = nullptr;
+  uint64_t cap_d_edges = 0;
+  uint64_t* h_edge_off = nullptr;
+  uint64_t cap_h_edge_off = 0;
+  twopaco_edge* h_edges = nullptr;
+  uint64_t cap_h_edges = 0;
 };
 
 namespace {
@@ -453,6 +479,10 @@ void twopaco_context_destroy(twopaco_context* c) {
   cudaFreeHost(c->h_off);
   cudaFreeHost(c->h_out_off);
   cudaFreeHost(c->h_pos);
+  cudaFree(c->d_edge_off);
+  cudaFree(c->d_edges);
+  cudaFreeHost(c->h_edge_off);
+  cudaFreeHost(c->h_edges);
   cudaStreamDestroy(c->stream);
   cudaSetDevice(prev);
   delete c;
@@ -528,6 +558,44 @@ int twopaco_build_ctx(twopaco_context* c, const char* const* seqs, const uint64_
   out->offsets = c->h_out_off;
   out->positions = c->h_pos;
   out->stats = st;
+  c->last_n = n_seqs;
+  c->last_junctions = total;
+  c->have_last = true;
+  return finish(TWOPACO_OK);
+}
+
+int twopaco_edges_ctx(twopaco_context* c, twopaco_edge_list* out) {
+  if (!c || !out || !c->have_last) return TWOPACO_EINVAL;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != c->device) cudaSetDevice(c->device);
+  auto finish = [&](int code) {
+    if (prev != c->device) cudaSetDevice(prev);
+    return code;
+  };
+  const uint64_t n = c->last_n, cap = c->last_junctions ? c->last_junctions : 1;
+  cudaError_t e;
+  if ((e = grow_device(&c->d_edge_off, &c->cap_d_edge_off, (n + 1) * 8)) != cudaSuccess ||
+      (e = grow_device(&c->d_edges, &c->cap_d_edges, cap * sizeof(twopaco_edge))) != cudaSuccess ||
+      (e = grow_pinned(&c->h_edge_off, &c->cap_h_edge_off, (n + 1) * 8)) != cudaSuccess ||
+      (e = grow_pinned(&c->h_edges, &c->cap_h_edges, cap * sizeof(twopaco_edge))) != cudaSuccess)
+    return finish(cuda_code(e));
+  int rc = twopaco_edges_device(c->d_ws, c->d_off, n, c->d_out_off, c->d_pos, c->d_edge_off, c->d_edges,
+                                cap, c->stream);
+  if (rc) return finish(rc);
+  e = cudaMemcpyAsync(c->h_edge_off, c->d_edge_off, (n + 1) * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return finish(cuda_code(e));
+  const uint64_t ne = c->h_edge_off[n];
+  if (ne > cap) return finish(TWOPACO_EOVERFLOW);
+  if (ne) {
+    e = cudaMemcpyAsync(c->h_edges, c->d_edges, ne * sizeof(twopaco_edge), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return finish(cuda_code(e));
+  }
+  out->n_seqs = n;
+  out->offsets = c->h_edge_off;
+  out->edges = c->h_edges;
   return finish(TWOPACO_OK);
 }
 

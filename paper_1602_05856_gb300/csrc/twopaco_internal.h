@@ -32,6 +32,11 @@ struct DevHeader {
   unsigned long long bitmap_words;
   unsigned long long q;
   unsigned long long rounds;
+  // what a later edge computation needs from the run
+  const uint32_t* packed;
+  unsigned long long m;
+  int k;
+  int both;
 };
 
 // Device view of one run: every buffer lives inside the workspace except the
@@ -89,6 +94,9 @@ int launch_pack(const RunView& v, cudaStream_t s);
 int launch_partition(const RunView& v, int rounds, cudaStream_t s);
 int launch_round(const RunView& v, int round, int rounds, cudaStream_t s);
 int launch_emit(const RunView& v, cudaStream_t s);
+int launch_edges(const DevHeader* hdr_dev, const uint64_t* d_offsets, uint64_t n_seqs,
+                 const uint64_t* d_out_offsets, const uint64_t* d_out_positions,
+                 uint64_t* d_edge_offsets, void* d_edges, uint64_t edge_capacity, cudaStream_t s);
 
 // Pass-2 slot layout for this k: 0 = one 64-bit word (key << 9 | mask, k <= 27),
 // 1 = 16 bytes (k <= 31), 2 = 32 bytes (128-bit key).

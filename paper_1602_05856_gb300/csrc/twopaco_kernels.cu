@@ -600,6 +600,10 @@ __global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
     h->bitmap_words = v.bitmap_words;
     h->q = (unsigned long long)v.qmask + 1ull;
     h->rounds = (unsigned long long)v.rounds;
+    h->packed = v.packed;
+    h->m = v.m;
+    h->k = v.k;
+    h->both = v.both;
   }
   const bool vec = (reinterpret_cast<uintptr_t>(v.bases) & 15) == 0;
   const uint64_t stride = (uint64_t)gridDim.x * kBlock * 4;
@@ -1092,6 +1096,104 @@ __global__ void __launch_bounds__(kBlock) emit_offsets_kernel(RunView v) {
 }
 
 // ---------------------------------------------------------------------------
+// Compacted-graph edges (section "Reduction to the Problem of Finding
+// Junction Positions"): consecutive junction positions of a string.
+// ---------------------------------------------------------------------------
+
+struct EdgeOut {  // layout of twopaco_edge
+  unsigned long long from_hi, from_lo, to_hi, to_lo, start, length;
+  unsigned int from_rc, to_rc;
+};
+
+// edge_offsets[t] = sum over strings before t of max(junctions - 1, 0).
+__global__ void __launch_bounds__(1024) edge_offsets_kernel(const DevHeader* hdr, const uint64_t* out_off,
+                                                            uint64_t n_seqs, uint64_t* edge_off,
+                                                            uint64_t capacity) {
+  __shared__ unsigned long long wsum[32];
+  __shared__ unsigned long long carry_s;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (uint64_t base = 0; base < n_seqs; base += 1024) {
+    const uint64_t t = base + threadIdx.x;
+    unsigned long long x = 0;
+    if (t < n_seqs) {
+      const unsigned long long j = out_off[t + 1] - out_off[t];
+      x = j ? j - 1 : 0;
+    }
+    unsigned long long inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    unsigned long long before = 0, all = 0;
+    for (int w = 0; w < 32; ++w) {
+      before += (w < wid) ? wsum[w] : 0ull;
+      all += wsum[w];
+    }
+    const unsigned long long c0 = carry_s;
+    if (t < n_seqs) edge_off[t] = c0 + before + inc - x;
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s = c0 + all;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    edge_off[n_seqs] = carry_s;
+    if (carry_s > capacity) const_cast<DevHeader*>(hdr)->overflow = 1;
+  }
+}
+
+template <int KW>
+__device__ __forceinline__ void edge_vertex(const uint32_t* packed, uint64_t g, int k, int both,
+                                            unsigned long long* hi, unsigned long long* lo,
+                                            unsigned int* rc) {
+  const Key f = load_kmer<KW>(packed, g, k);
+  const Key r = both ? revcomp<KW>(f, k) : f;
+  const bool use_r = both && key_less(r, f);
+  *hi = use_r ? r.hi : f.hi;
+  *lo = use_r ? r.lo : f.lo;
+  *rc = use_r ? 1u : 0u;
+}
+
+// One thread per junction: the edge from it to the next junction of its string.
+__global__ void __launch_bounds__(kBlock) edges_kernel(const DevHeader* hdr, const uint64_t* offsets,
+                                                      uint64_t n_seqs, const uint64_t* out_off,
+                                                      const uint64_t* out_pos, const uint64_t* edge_off,
+                                                      EdgeOut* edges, uint64_t capacity) {
+  const uint32_t* packed = hdr->packed;
+  const int k = hdr->k, both = hdr->both;
+  const uint64_t total = out_off[n_seqs];
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+  for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < total; i += stride) {
+    uint64_t lo = 0, hi = n_seqs;  // largest t with out_off[t] <= i
+    while (hi - lo > 1) {
+      const uint64_t mid = (lo + hi) >> 1;
+      if (__ldg(out_off + mid) <= i) lo = mid; else hi = mid;
+    }
+    const uint64_t t = lo;
+    const uint64_t a = i - out_off[t];
+    if (a + 1 >= out_off[t + 1] - out_off[t]) continue;  // the string's last junction
+    const uint64_t e = edge_off[t] + a;
+    if (e >= capacity) continue;
+    const uint64_t p = out_pos[i], q = out_pos[i + 1], g0 = offsets[t];
+    EdgeOut o;
+    if (k <= 31) {
+      edge_vertex<1>(packed, g0 + p, k, both, &o.from_hi, &o.from_lo, &o.from_rc);
+      edge_vertex<1>(packed, g0 + q, k, both, &o.to_hi, &o.to_lo, &o.to_rc);
+    } else {
+      edge_vertex<2>(packed, g0 + p, k, both, &o.from_hi, &o.from_lo, &o.from_rc);
+      edge_vertex<2>(packed, g0 + q, k, both, &o.to_hi, &o.to_lo, &o.to_rc);
+    }
+    o.start = p;
+    o.length = q - p;
+    edges[e] = o;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Launch helpers
 // ---------------------------------------------------------------------------
 
@@ -1249,6 +1351,22 @@ int launch_emit(const RunView& v, cudaStream_t s) {
     n++;
   }
   return done(n);
+}
+
+int launch_edges(const DevHeader* hdr_dev, const uint64_t* d_offsets, uint64_t n_seqs,
+                 const uint64_t* d_out_offsets, const uint64_t* d_out_positions,
+                 uint64_t* d_edge_offsets, void* d_edges, uint64_t edge_capacity, cudaStream_t s) {
+  {
+    Timed t("edge_offsets", s);
+    edge_offsets_kernel<<<1, 1024, 0, s>>>(hdr_dev, d_out_offsets, n_seqs, d_edge_offsets, edge_capacity);
+  }
+  {
+    Timed t("edges", s);
+    edges_kernel<<<grid_for(edges_kernel, kBlock, 1ull << 30), kBlock, 0, s>>>(
+        hdr_dev, d_offsets, n_seqs, d_out_offsets, d_out_positions, d_edge_offsets,
+        static_cast<EdgeOut*>(d_edges), edge_capacity);
+  }
+  return done(2);
 }
 
 }  // namespace twopaco

@@ -45,6 +45,22 @@ class _Stats(ctypes.Structure):
                 ("timeout", ctypes.c_uint32)]
 
 
+class _Edge(ctypes.Structure):
+    _fields_ = [("from_hi", ctypes.c_uint64), ("from_lo", ctypes.c_uint64), ("to_hi", ctypes.c_uint64),
+                ("to_lo", ctypes.c_uint64), ("start", ctypes.c_uint64), ("length", ctypes.c_uint64),
+                ("from_rc", ctypes.c_uint32), ("to_rc", ctypes.c_uint32)]
+
+
+EDGE_DTYPE = np.dtype([("from_hi", np.uint64), ("from_lo", np.uint64), ("to_hi", np.uint64),
+                       ("to_lo", np.uint64), ("start", np.uint64), ("length", np.uint64),
+                       ("from_rc", np.uint32), ("to_rc", np.uint32)])
+
+
+class _EdgeList(ctypes.Structure):
+    _fields_ = [("n_seqs", ctypes.c_uint64), ("offsets", ctypes.POINTER(ctypes.c_uint64)),
+                ("edges", ctypes.POINTER(_Edge))]
+
+
 class _Result(ctypes.Structure):
     _fields_ = [("n_seqs", ctypes.c_uint64), ("offsets", ctypes.POINTER(ctypes.c_uint64)),
                 ("positions", ctypes.POINTER(ctypes.c_uint64)), ("stats", _Stats)]
@@ -96,6 +112,10 @@ def _lib() -> ctypes.CDLL:
         L.twopaco_build_ctx.argtypes = [P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(U64), U64,
                                         I, U64, I, ctypes.POINTER(_Options), ctypes.POINTER(_Result)]
         L.twopaco_build_ctx.restype = I
+        L.twopaco_edges_ctx.argtypes = [P, ctypes.POINTER(_EdgeList)]
+        L.twopaco_edges_ctx.restype = I
+        L.twopaco_edges_device.argtypes = [P, P, U64, P, P, P, P, U64, P]
+        L.twopaco_edges_device.restype = I
         L.twopaco_profile_enable.argtypes = [I]
         L.twopaco_profile_enable.restype = I
         L.twopaco_profile_kernels.argtypes = [ctypes.POINTER(ctypes.c_char_p),
@@ -233,6 +253,22 @@ class Context:
             off, pos = off.copy(), pos.copy()
         return [pos[off[t]:off[t + 1]] for t in range(n)], _stats_dict(res.stats)
 
+    def edges(self):
+        """twopaco_edges_ctx: (edge offsets per string, structured array of EDGE_DTYPE)."""
+        lst = _EdgeList()
+        rc = _lib().twopaco_edges_ctx(self._h, ctypes.byref(lst))
+        if rc != OK:
+            raise TwopacoError(rc, "twopaco_edges_ctx")
+        n = int(lst.n_seqs)
+        off = np.ctypeslib.as_array(lst.offsets, shape=(n + 1,)).copy()
+        ne = int(off[-1])
+        if ne:
+            raw = ctypes.cast(lst.edges, ctypes.POINTER(ctypes.c_uint8 * (ne * EDGE_DTYPE.itemsize))).contents
+            arr = np.frombuffer(bytes(raw), dtype=EDGE_DTYPE).copy()
+        else:
+            arr = np.zeros(0, EDGE_DTYPE)
+        return off, arr
+
 
 def twopaco_build(seqs: Sequence, k: int, filter_bits: int, rounds: int = 1):
     return twopaco_build_ex(seqs, k, filter_bits, rounds, None)
@@ -280,6 +316,17 @@ def twopaco_run_device_noalloc(d_bases: int, d_offsets: int, n_seqs: int, total_
     d = _stats_dict(st)
     d["rc"] = int(rc)
     return d
+
+
+def twopaco_edges_device(d_workspace: int, d_offsets: int, n_seqs: int, d_out_offsets: int,
+                         d_out_positions: int, d_edge_offsets: int, d_edges: int, edge_capacity: int,
+                         cuda_stream: int = 0) -> None:
+    rc = _lib().twopaco_edges_device(d_workspace or None, d_offsets or None, int(n_seqs),
+                                     d_out_offsets or None, d_out_positions or None,
+                                     d_edge_offsets or None, d_edges or None, int(edge_capacity),
+                                     cuda_stream or None)
+    if rc != OK:
+        raise TwopacoError(rc, "twopaco_edges_device")
 
 
 def twopaco_read_stats(d_workspace: int, cuda_stream: int = 0, check: bool = True) -> Dict[str, int]:

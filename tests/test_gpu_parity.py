@@ -304,3 +304,29 @@ def test_context_reuse_across_sizes_and_k():
     got, _ = ctx.build(seqs, 25, 1 << 20, 2, T().Options(partition_bins=256))
     _eq(got, O.junctions(G.concat(seqs), 25))
     ctx.close()
+
+
+@pytest.mark.parametrize("name,scale,k,both", [("plain_single", 0.05, 25, True),
+                                                ("batched_set", 0.01, 31, True),
+                                                ("plain_single", 0.02, 63, True),
+                                                ("plain_single", 0.02, 21, False)])
+def test_edges_match_oracle(name, scale, k, both):
+    """Compacted-graph edges (consecutive junction pairs) against the oracle, field by field."""
+    seqs = _named(name, scale)
+    ctx = T().Context()
+    ctx.build(seqs, k, 1 << 20, 1, T().Options(hashes=4, both_strands=both))
+    off, got = ctx.edges()
+    want = O.edges(G.concat(seqs), k, both_strands=both)
+    assert np.array_equal(np.diff(off), want["per_string"])
+    for f in ("from_hi", "from_lo", "to_hi", "to_lo", "start", "length", "from_rc", "to_rc"):
+        assert np.array_equal(got[f].astype(np.uint64), want[f].astype(np.uint64)), f
+    ctx.close()
+
+
+def test_edges_fig1_and_tiny_strings():
+    ctx = T().Context()
+    ctx.build(["TGGCACGTC", "TGGCACTTC", "A", ""], 2, 1 << 12, 1, T().Options(both_strands=False))
+    off, e = ctx.edges()
+    assert list(np.diff(off)) == [2, 2, 0, 0]
+    assert list(e["length"]) == [4, 3, 4, 3]
+    ctx.close()

@@ -248,3 +248,46 @@ def test_partition_cuts_greedy_property(seed):
                 assert s * ell <= total
             if hi < q - (ell - 1 - r):
                 assert (s + int(counts[hi])) * ell > total or hi - lo == 0
+
+
+# --- compacted-graph edges -----------------------------------------------------------
+
+def _kmer_str(hi, lo, k):
+    v = (int(hi) << 64) | int(lo)
+    return "".join("ACGT"[(v >> (2 * (k - 1 - i))) & 3] for i in range(k))
+
+
+@pytest.mark.parametrize("k,both", [(2, False), (3, True), (4, True), (5, False), (7, True)])
+def test_edges_are_the_maximal_nonbranching_paths(k, both):
+    """Observation 1: junction-to-junction edges = the compacted graph's edges."""
+    seqs = [bytes(s).decode() for s in G.random_strings(300 + k, 4, 20, 80, b"ACG")]
+    seqs.append(seqs[0][3:50] + seqs[1][:25])
+    e = O.edges(seqs, k, both_strands=both)
+    # every edge spells a string segment whose first and last k-mers are its endpoints
+    spelled = set()
+    o = 0
+    for t, s in enumerate(seqs):
+        for _ in range(int(e["per_string"][t])):
+            p, ln = int(e["start"][o]), int(e["length"][o])
+            seg = s[p:p + ln + k]
+            a = _kmer_str(e["from_hi"][o], e["from_lo"][o], k)
+            b = _kmer_str(e["to_hi"][o], e["to_lo"][o], k)
+            assert (brute.revcomp(a) if e["from_rc"][o] else a) == seg[:k]
+            assert (brute.revcomp(b) if e["to_rc"][o] else b) == seg[-k:]
+            path = tuple(seg[i:i + k] for i in range(ln + 1))
+            spelled.add(path)
+            if both:
+                r = brute.revcomp(seg)
+                spelled.add(tuple(r[i:i + k] for i in range(ln + 1)))
+            o += 1
+    assert o == e["start"].size
+    assert spelled == brute.compacted_paths(seqs, k, both)
+
+
+def test_edges_fig1():
+    e = O.edges(["TGGCACGTC", "TGGCACTTC"], 2, both_strands=False)
+    # TG -> AC (TGGCAC), AC -> TC (ACGTC / ACTTC): Fig. 1b/1c
+    assert list(e["per_string"]) == [2, 2]
+    assert [_kmer_str(0, x, 2) for x in e["from_lo"]] == ["TG", "AC", "TG", "AC"]
+    assert [_kmer_str(0, x, 2) for x in e["to_lo"]] == ["AC", "TC", "AC", "TC"]
+    assert list(e["length"]) == [4, 3, 4, 3]
