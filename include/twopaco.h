@@ -55,9 +55,11 @@ typedef struct twopaco_options {
   int both_strands;        /* 1: comprehensive graph (default); 0: single strand */
   uint32_t partition_bins; /* q of the rounds heuristic, power of two (65536) */
   uint64_t table_slots;    /* pass-2 table capacity in slots; 0 = automatic */
-  uint64_t candidate_records; /* pass-2 candidate list capacity; 0 = automatic
-                                 (a quarter of a round's positions). A round with
-                                 more candidates stays correct but slower. */
+  uint64_t candidate_records; /* pass-2 candidate list size in 8-byte units; 0 =
+                                 automatic (a quarter of a round's positions). It
+                                 holds twice as many candidates when the input has
+                                 at most 2^32 bases. A round with more candidates
+                                 stays correct but slower. */
   void* cuda_stream;       /* cudaStream_t to launch on, borrowed; NULL = default */
 } twopaco_options;
 

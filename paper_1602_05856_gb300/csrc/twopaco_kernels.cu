@@ -1291,7 +1291,8 @@ int round_impl(const RunView& v, int round, cudaStream_t s) {
   unsigned grid = grid_for(pass1_probe_kernel<KW, RD, HB>, kBlock, threads);
   if (grid * (kBlock / 32) > kMaxSegments) grid = kMaxSegments / (kBlock / 32);
   pv.n_segments = grid * (kBlock / 32);
-  pv.seg_cap = v.cand_cap / pv.n_segments;
+  // the list region holds cand_cap 8-byte records, or twice as many 32-bit ones
+  pv.seg_cap = (v.narrow ? 2 * v.cand_cap : v.cand_cap) / pv.n_segments;
   {
     Timed t("pass1_probe", s);
     pass1_probe_kernel<KW, RD, HB><<<grid, kBlock, 0, s>>>(pv, round);

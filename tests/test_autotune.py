@@ -1,0 +1,38 @@
+"""The autotuner: host-side helpers (CPU) and a tuned run's parity (GPU)."""
+import numpy as np
+import pytest
+
+from paper_1602_05856_gb300 import autotune, genomes
+
+
+def test_prefix_sample_takes_the_same_prefix_of_every_string():
+    seqs = [np.frombuffer(b"A" * n, np.uint8) for n in (1000, 3000, 50)]
+    s = autotune.prefix_sample(seqs, 0.1, k=25)
+    assert [x.size for x in s] == [135, 135, 50]  # 10% of 4050 bases, over 3 strings
+    assert autotune._pow2_at_least(1) == 1 and autotune._pow2_at_least(1025) == 2048
+
+
+@pytest.mark.gpu
+def test_tuned_configuration_is_exact_and_fits_the_budget():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle as O
+    from paper_1602_05856_gb300 import build, twopaco as T
+    build.build()
+    seqs = genomes.named_set("plain_single", 0.1)
+    k = 25
+    choice = autotune.tune(seqs, k, bits_per_base=(4, 16), hashes=(3, 6), rounds=(1, 2),
+                           sample_fraction=0.25, repeats=2)
+    assert choice.rounds == 1 and len(choice.trials) == 4
+    got, _ = T.twopaco_build_ex(seqs, k, choice.bits, choice.rounds, choice.options())
+    want = O.junctions(genomes.concat(seqs), k)
+    assert all(np.array_equal(g, w) for g, w in zip(got, want))
+    # a budget one round cannot meet pushes the tuner to more rounds
+    one_round = min(t.workspace for t in choice.trials if t.rounds == 1)
+    tight = autotune.tune(seqs, k, budget_bytes=one_round - 1, bits_per_base=(4,), hashes=(4,),
+                          rounds=(1, 4), sample_fraction=0.25, repeats=1)
+    assert tight.rounds == 4 and tight.workspace < one_round
+    with pytest.raises(ValueError):
+        autotune.tune(seqs, k, budget_bytes=1024, bits_per_base=(4,), hashes=(4,), rounds=(1,),
+                      sample_fraction=0.25, repeats=1)
