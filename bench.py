@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=60,
+                   help="requests of the served leg (Poisson, 20/s); 0 skips it")
     p.add_argument("--workload", default=WORKLOAD, choices=["bacterial_set", "plain_single"],
                    help="plain_single: the 4 x 1 Mbp set (k=25, 2^24 bits, 3 hashes) for small captures")
     return p.parse_args()
@@ -264,6 +266,23 @@ def run_ours(args, world, rank, local):
         assert sum(g.size for g in got) == junctions, "host API and device run disagree"
     ctx.close()
     e2e_s = max_over_ranks(statistics.mean(e2e_t), world) if e2e_t else None
+    # served leg: a Poisson stream of build requests through the continuous-batching loop
+    served = None
+    if args.serve_requests > 0:
+        from paper_1602_05856_gb300 import serve
+        reqs = serve.served_requests(seqs, args.serve_requests, 20.0, seed=1606)
+        slots = [serve.GpuSlot(device=f"cuda:{local}") for _ in range(4)]
+        serve.Scheduler(slots, 120 << 30).run(serve.served_requests(seqs, 4, 1000.0, seed=7))
+        mix = serve.Scheduler(slots, 120 << 30).run(reqs).summary()
+        alone_reqs = serve.served_requests(seqs, args.serve_requests, 20.0, seed=1606)
+        alone = serve.run_alone(slots[0], alone_reqs).summary()
+        served = {"requests": args.serve_requests, "rate_per_s": 20.0, "slots": 4,
+                  "budget_gb": 120,
+                  "mix": {k: mix[k] for k in ("p50_ms", "p99_ms", "throughput_gbps", "wall_s")},
+                  "alone": {k: alone[k] for k in ("p50_ms", "p99_ms", "throughput_gbps", "wall_s")},
+                  "request_recipe": "2-7 prefixes of the 7 genomes, log-uniform 0.1-5 Mbp, k 25/31, "
+                                    "~8 filter bits per base, 4 hashes"}
+
     # roofline of the dominant kernel
     table_bytes = st["table_slots"] * (16 if K <= 31 else 32)
     top = max(prof.items(), key=lambda kv: kv[1]["ms"])
@@ -314,6 +333,7 @@ def run_ours(args, world, rank, local):
         "gpu_launches": launches,
         "roofline": roof,
         "cpu_baseline": cpu,
+        "served": served,
         "clocks": clocks,
         "stats": {k: st[k] for k in ("positions", "pass1_marks", "pass2_marks", "table_slots")},
         "kernels": kernels,

@@ -1,0 +1,271 @@
+"""Request loop for junction-detection builds: continuous batching on one GPU.
+
+Requests (sets of strings to build, each with its own k, filter size and
+rounds) arrive over time. A request is admitted as soon as an execution slot
+is free and the device memory it needs -- its input, its workspace (filter,
+pass-2 table, bitmaps) and its output -- fits the remaining budget; requests
+that arrive while others run are admitted as slots and memory free up, and
+the work of admitted requests overlaps on the device (one CUDA stream per
+slot). A slot keeps its buffers between requests and only grows them. The
+loop records each request's latency (completion minus arrival) and reports
+p50/p99 and throughput.
+
+The scheduler (``Scheduler``) holds no GPU code; ``GpuSlot`` runs a request
+through the C ABI (``twopaco_run_device``) on the slot's stream; tests drive
+the scheduler with a fake slot on the CPU.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+from typing import Callable, Deque, Dict, List, Optional, Sequence
+
+import numpy as np
+
+from . import twopaco
+
+
+@dataclass
+class Request:
+    rid: int
+    seqs: Sequence[np.ndarray]
+    k: int
+    filter_bits: int
+    rounds: int = 1
+    hashes: int = 4
+    arrival: float = 0.0          # seconds, on the loop's clock
+    # filled by the loop
+    admitted: Optional[float] = None
+    done: Optional[float] = None
+    result: Optional[List[np.ndarray]] = None
+    stats: Optional[Dict[str, int]] = None
+
+    @property
+    def bases(self) -> int:
+        return int(sum(int(s.size) for s in self.seqs))
+
+    def positions_upper(self) -> int:
+        return int(sum(max(0, int(s.size) - self.k + 1) for s in self.seqs))
+
+    def options(self, stream: int = 0) -> twopaco.Options:
+        return twopaco.Options(hashes=self.hashes, cuda_stream=stream)
+
+    def device_bytes(self) -> int:
+        """Device memory of one run: input, offsets, workspace, outputs."""
+        n = len(self.seqs)
+        ws = twopaco.twopaco_workspace_size(self.bases, n, self.k, self.filter_bits, self.rounds,
+                                            self.options())
+        return self.bases + 8 * (n + 1) + ws + 256 + 8 * (n + 1) + 8 * max(self.positions_upper(), 1)
+
+
+class Slot:
+    """Interface of an execution slot (one request at a time)."""
+
+    def start(self, req: Request) -> None:
+        raise NotImplementedError
+
+    def poll(self) -> bool:
+        """True once the running request has finished (its result is filled)."""
+        raise NotImplementedError
+
+    def held_bytes(self) -> int:
+        """Device memory the slot keeps (its buffers survive between requests)."""
+        raise NotImplementedError
+
+
+class GpuSlot(Slot):
+    """Runs requests on its own CUDA stream with buffers kept between requests."""
+
+    def __init__(self, device: str = "cuda"):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = torch.cuda.Stream(device=self.device)
+        self.buf: Dict[str, "torch.Tensor"] = {}
+        self.pinned: Dict[str, "torch.Tensor"] = {}
+        self.req: Optional[Request] = None
+        self.event = None
+
+    def _grow(self, name: str, nbytes: int):
+        t = self.buf.get(name)
+        if t is None or t.numel() < nbytes:
+            t = self.torch.empty(max(nbytes, 1), dtype=self.torch.uint8, device=self.device)
+            self.buf[name] = t
+        return t
+
+    def _grow_pinned(self, name: str, nbytes: int):
+        t = self.pinned.get(name)
+        if t is None or t.numel() < nbytes:
+            t = self.torch.empty(max(nbytes, 1), dtype=self.torch.uint8, pin_memory=True)
+            self.pinned[name] = t
+        return t
+
+    def held_bytes(self) -> int:
+        return int(sum(t.numel() for t in self.buf.values()))
+
+    def start(self, req: Request) -> None:
+        torch = self.torch
+        n = len(req.seqs)
+        lens = np.array([s.size for s in req.seqs], dtype=np.uint64)
+        off = np.zeros(n + 1, dtype=np.uint64)
+        np.cumsum(lens, out=off[1:])
+        m = int(off[-1])
+        cap = max(req.positions_upper(), 1)
+        ws_bytes = twopaco.twopaco_workspace_size(m, n, req.k, req.filter_bits, req.rounds,
+                                                  req.options())
+        # pinned staging of the request's input, copied on the slot's stream
+        host = self._grow_pinned("input", m + 8 * (n + 1))
+        hv = host.numpy()
+        if m:
+            hv[:m] = np.concatenate([np.asarray(s, dtype=np.uint8) for s in req.seqs])
+        hv[m:m + 8 * (n + 1)] = off.view(np.uint8)
+        d_in = self._grow("input", m + 8 * (n + 1) + 16)
+        ws = self._grow("workspace", ws_bytes + 256)
+        d_out_off = self._grow("out_offsets", 8 * (n + 1))
+        d_out_pos = self._grow("out_positions", 8 * cap)
+        off_at = (m + 15) // 16 * 16
+        with torch.cuda.stream(self.stream):
+            d_in[:m].copy_(host[:m], non_blocking=True)
+            d_in[off_at:off_at + 8 * (n + 1)].copy_(host[m:m + 8 * (n + 1)], non_blocking=True)
+        ws_ptr = (ws.data_ptr() + 255) // 256 * 256
+        opts = req.options(int(self.stream.cuda_stream))
+        twopaco.twopaco_run_device(d_in.data_ptr() if m else 0, d_in.data_ptr() + off_at, n, m,
+                                   req.k, req.filter_bits, req.rounds, opts, ws_ptr, ws_bytes,
+                                   d_out_off.data_ptr(), d_out_pos.data_ptr(), cap)
+        self.h_off = self._grow_pinned("out_offsets", 8 * (n + 1))[:8 * (n + 1)]
+        self.h_pos = self._grow_pinned("out_positions", 8 * cap)[:8 * cap]
+        with torch.cuda.stream(self.stream):
+            self.h_off.copy_(d_out_off[:8 * (n + 1)], non_blocking=True)
+            self.h_pos.copy_(d_out_pos[:8 * cap], non_blocking=True)
+            self.event = torch.cuda.Event()
+            self.event.record(self.stream)
+        self.ws_ptr, self.n, self.req = ws_ptr, n, req
+
+    def poll(self) -> bool:
+        if self.req is None or not self.event.query():
+            return False
+        req = self.req
+        req.stats = twopaco.twopaco_read_stats(self.ws_ptr, int(self.stream.cuda_stream))
+        off = self.h_off.numpy().view(np.uint64)
+        pos = self.h_pos.numpy().view(np.uint64)[: int(off[-1])]
+        req.result = [pos[off[t]:off[t + 1]].copy() for t in range(self.n)]
+        self.req = None
+        return True
+
+
+@dataclass
+class ServeReport:
+    requests: List[Request] = field(default_factory=list)
+    wall_s: float = 0.0
+
+    def latencies(self) -> np.ndarray:
+        return np.array([r.done - r.arrival for r in self.requests], dtype=np.float64)
+
+    def summary(self) -> Dict[str, float]:
+        lat = self.latencies()
+        bases = sum(r.bases for r in self.requests)
+        return {"requests": len(self.requests),
+                "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else 0.0,
+                "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else 0.0,
+                "mean_ms": float(lat.mean() * 1e3) if lat.size else 0.0,
+                "throughput_gbps": bases / self.wall_s / 1e9 if self.wall_s > 0 else 0.0,
+                "wall_s": self.wall_s}
+
+
+class Scheduler:
+    """Admit requests in arrival order as slots and the memory budget allow."""
+
+    def __init__(self, slots: Sequence[Slot], budget_bytes: int,
+                 clock: Callable[[], float] = time.perf_counter):
+        self.slots = list(slots)
+        self.budget = int(budget_bytes)
+        self.clock = clock
+        self.busy: Dict[int, Request] = {}   # slot index -> request
+        self.reserved: Dict[int, int] = {}   # slot index -> bytes reserved
+
+    def free_bytes(self) -> int:
+        return self.budget - sum(self.reserved.values())
+
+    def run(self, requests: Sequence[Request], sleep: Callable[[float], None] = time.sleep,
+            poll_interval: float = 50e-6) -> ServeReport:
+        pending: Deque[Request] = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        for r in pending:
+            if r.device_bytes() > self.budget:
+                raise ValueError(f"request {r.rid} needs more than the whole budget")
+        finished: List[Request] = []
+        t0 = self.clock()
+        while pending or self.busy:
+            now = self.clock() - t0
+            for i, slot in enumerate(self.slots):
+                if i in self.busy and slot.poll():
+                    req = self.busy.pop(i)
+                    req.done = self.clock() - t0
+                    self.reserved.pop(i, None)
+                    finished.append(req)
+            # admit in arrival order (no overtaking): continuous batching
+            while pending and pending[0].arrival <= now:
+                free = [i for i in range(len(self.slots)) if i not in self.busy]
+                need = pending[0].device_bytes()
+                if not free or need > self.free_bytes():
+                    break
+                i = free[0]
+                req = pending.popleft()
+                req.admitted = self.clock() - t0
+                self.reserved[i] = need
+                self.busy[i] = req
+                self.slots[i].start(req)
+            if not self.busy and pending and pending[0].arrival > now:
+                sleep(min(pending[0].arrival - now, 1e-3))
+            elif self.busy:
+                sleep(poll_interval)
+        return ServeReport(finished, self.clock() - t0)
+
+
+def poisson_arrivals(n: int, rate_per_s: float, seed: int) -> np.ndarray:
+    """Arrival times (seconds) of a seeded Poisson stream."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
+
+
+def served_requests(pool: Sequence[np.ndarray], n: int, rate_per_s: float, seed: int,
+                    genomes_range=(2, 7), mbp_range=(0.1, 5.0), ks=(25, 31),
+                    bits_per_base: float = 8.0, hashes: int = 4) -> List[Request]:
+    """A seeded stream of build requests over a pool of related genomes.
+
+    Each request takes 2-7 strings: prefixes of pool genomes whose lengths are
+    log-uniform in ``mbp_range`` (Mbp); k alternates over ``ks``; the filter has
+    about ``bits_per_base`` bits per base (a power of two); arrivals are Poisson.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    arrivals = poisson_arrivals(n, rate_per_s, seed + 1)
+    out = []
+    lo, hi = np.log(mbp_range[0] * 1e6), np.log(mbp_range[1] * 1e6)
+    for i in range(n):
+        g = int(rng.integers(genomes_range[0], genomes_range[1] + 1))
+        seqs = []
+        for _ in range(g):
+            src = pool[int(rng.integers(0, len(pool)))]
+            ln = int(min(src.size, np.exp(rng.uniform(lo, hi))))
+            start = int(rng.integers(0, src.size - ln + 1))
+            seqs.append(np.ascontiguousarray(src[start:start + ln]))
+        bases = sum(s.size for s in seqs)
+        bits = 1 << max(8, int(np.ceil(np.log2(bits_per_base * bases))))
+        out.append(Request(i, seqs, int(ks[i % len(ks)]), bits, hashes=hashes,
+                           arrival=float(arrivals[i])))
+    return out
+
+
+def run_alone(slot: Slot, requests: Sequence[Request],
+              clock: Callable[[], float] = time.perf_counter) -> ServeReport:
+    """Each request by itself on one slot, back to back (latency = its own run)."""
+    done = []
+    t0 = clock()
+    for r in requests:
+        a = clock()
+        slot.start(r)
+        while not slot.poll():
+            pass
+        r.arrival, r.admitted, r.done = a - t0, a - t0, clock() - t0
+        done.append(r)
+    return ServeReport(done, clock() - t0)
