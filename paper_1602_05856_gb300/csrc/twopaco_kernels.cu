@@ -72,7 +72,11 @@ struct Timed {
   }
 };
 
-constexpr int kR = 8;  // consecutive positions per thread in the first pass
+// Consecutive positions per thread (at most 16: one 32-bit word of successor
+// bases) in the first-pass kernels and the partition pre-pass.
+constexpr int kInsertR = 16;
+constexpr int kProbeR = 8;
+constexpr int kR = 8;  // partition pre-pass
 
 // ---------------------------------------------------------------------------
 // k-mer words
@@ -266,23 +270,24 @@ __device__ __forceinline__ int32_t rel(uint64_t x, uint64_t p0) {
   return (int32_t)(d > kClamp ? kClamp : (d < -kClamp ? -kClamp : d));
 }
 
-// Visit the kR consecutive positions p0 .. p0 + kR - 1 (p0 < m), rolling the
+// Visit the R consecutive positions p0 .. p0 + R - 1 (p0 < m), rolling the
 // k-mer from each position to the next within a string and reading it from
 // scratch after a string boundary. fn(i, p, valid, occ) runs for every i,
 // with i a compile-time constant once unrolled.
-template <int KW, typename F>
+template <int KW, int R, typename F>
 __device__ __forceinline__ void walk(const RunView& v, uint64_t p0, F&& fn) {
+  static_assert(R >= 1 && R <= 16, "successor bases come from one 32-bit word");
   const int k = v.k;
   Bounds b = seq_bounds(v, p0);
   int32_t s_rel = rel(b.start, p0), e_rel = rel(b.end, p0);  // string bounds relative to p0
   const int32_t m_rel = rel(v.m, p0);
-  // bases p0 + k .. p0 + k + kR - 1: the successor of each position, which is
+  // bases p0 + k .. p0 + k + R - 1: the successor of each position, which is
   // also the base that enters the k-mer when it slides to the next position
   const uint32_t next = (uint32_t)(bases32(v.packed, p0 + (uint64_t)k) >> 32);
   Key f{0, 0}, r{0, 0};
   bool fresh = true;
 #pragma unroll
-  for (int i = 0; i < kR; ++i) {
+  for (int i = 0; i < R; ++i) {
     const uint64_t p = p0 + i;
     Occ oc;
     bool valid = false;
@@ -633,9 +638,9 @@ __global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
 // item(s) in its k-mer's filter word with one atomic OR.
 template <int KW, bool ROUNDS, int HB>
 __global__ void __launch_bounds__(kBlock) pass1_insert_kernel(RunView v, int round) {
-  const uint64_t stride = (uint64_t)gridDim.x * kBlock * kR;
-  for (uint64_t p0 = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) * kR; p0 < v.m; p0 += stride) {
-    walk<KW>(v, p0, [&](int, uint64_t, bool valid, const Occ& oc) {
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock * kInsertR;
+  for (uint64_t p0 = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) * kInsertR; p0 < v.m; p0 += stride) {
+    walk<KW, kInsertR>(v, p0, [&](int, uint64_t, bool valid, const Occ& oc) {
       if (!valid || (ROUNDS && !in_round(v, oc.H, round))) return;
       const uint64_t G = second_hash(oc.H);
       const ItemPattern pat = item_pattern<HB>(G);
@@ -657,6 +662,7 @@ __global__ void __launch_bounds__(kBlock) pass1_insert_kernel(RunView v, int rou
 template <int KW, bool ROUNDS, int HB>
 __global__ void __launch_bounds__(kBlock, 3) pass1_probe_kernel(RunView v, int round) {
   const int lane = threadIdx.x & 31;
+  constexpr int kR = kProbeR;
   const uint64_t stride = (uint64_t)gridDim.x * kBlock * kR;
   constexpr int kLanesPerWord = 32 / kR;
   unsigned long long kept = 0, valid_n = 0;
@@ -670,7 +676,7 @@ __global__ void __launch_bounds__(kBlock, 3) pass1_probe_kernel(RunView v, int r
     uint64_t word[kR], G[kR];
     uint32_t probe_bits = 0, sent_bits = 0, valid_bits = 0;
     if (p0 < v.m) {
-      walk<KW>(v, p0, [&](int i, uint64_t, bool valid, const Occ& oc) {
+      walk<KW, kR>(v, p0, [&](int i, uint64_t, bool valid, const Occ& oc) {
         if (!valid) return;
         valid_bits |= 1u << i;
         if (ROUNDS && !in_round(v, oc.H, round)) return;
@@ -916,7 +922,7 @@ template <int KW, int HB>
 __global__ void __launch_bounds__(kBlock) partition_count_kernel(RunView v) {
   const uint64_t stride = (uint64_t)gridDim.x * kBlock * kR;
   for (uint64_t p0 = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) * kR; p0 < v.m; p0 += stride) {
-    walk<KW>(v, p0, [&](int, uint64_t, bool valid, const Occ& oc) {
+    walk<KW, kR>(v, p0, [&](int, uint64_t, bool valid, const Occ& oc) {
       if (!valid) return;
       const uint64_t G = second_hash(oc.H);
       const uint64_t m = item_bits<HB>(G, 17u);
@@ -1280,12 +1286,13 @@ int round_impl(const RunView& v, int round, cudaStream_t s) {
   if (cudaMemsetAsync(v.filter, 0, v.filter_words64 * 8, s) != cudaSuccess) return -1;
   if (cudaMemsetAsync(v.lc_bits, 0, (1ull << v.lc_log2) / 8, s) != cudaSuccess) return -1;
   if (round == 0 && cudaMemsetAsync(v.cfinal, 0, v.bitmap_words * 4, s) != cudaSuccess) return -1;
-  const uint64_t threads = (v.m + kR - 1) / kR;
   {
     Timed t("pass1_insert", s);
-    pass1_insert_kernel<KW, RD, HB>
-        <<<grid_for(pass1_insert_kernel<KW, RD, HB>, kBlock, threads), kBlock, 0, s>>>(v, round);
+    pass1_insert_kernel<KW, RD, HB><<<grid_for(pass1_insert_kernel<KW, RD, HB>, kBlock,
+                                               (v.m + kInsertR - 1) / kInsertR),
+                                      kBlock, 0, s>>>(v, round);
   }
+  const uint64_t threads = (v.m + kProbeR - 1) / kProbeR;
   // one candidate-list segment per probe warp
   RunView pv = v;
   unsigned grid = grid_for(pass1_probe_kernel<KW, RD, HB>, kBlock, threads);
