@@ -139,7 +139,7 @@ RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_
   v.table = base + L.table;
   v.table_max_slots = L.table_slots;
   v.cands = reinterpret_cast<uint64_t*>(base + L.cands);
-  v.narrow = m <= (1ull << 32) ? 1 : 0;
+  v.narrow = m < (1ull << 31) ? 1 : 0;  // 31-bit positions + a sentinel flag
   v.cand_cap = L.cand_cap;
   v.lc_bits = reinterpret_cast<uint32_t*>(base + L.lc);
   v.lc_log2 = L.lc_log2;

@@ -63,7 +63,7 @@ struct RunView {
   void* table;              // pass-2 slots
   uint64_t table_max_slots;
   uint64_t* cands;          // positions of the pass-1 survivors, for pass 2
-  int narrow;               // m <= 2^32: the list holds 32-bit positions
+  int narrow;               // m < 2^31: the list holds 32-bit records
   uint64_t cand_cap;        // records the list can hold
   uint32_t* seg_count;      // candidates per list segment (one segment per probe warp)
   uint32_t n_segments;      // warps of the probe grid (set per launch)

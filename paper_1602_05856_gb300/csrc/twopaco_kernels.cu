@@ -270,6 +270,18 @@ __device__ __forceinline__ int32_t rel(uint64_t x, uint64_t p0) {
   return (int32_t)(d > kClamp ? kClamp : (d < -kClamp ? -kClamp : d));
 }
 
+// The occurrence of a listed candidate: its string bounds are not needed,
+// because the list marks candidates at a string end (sentinel positions)
+// and every other candidate has a predecessor and a successor.
+template <int KW>
+__device__ __forceinline__ void read_listed(const RunView& v, uint64_t g, bool sentinel, Occ* oc) {
+  const Key f = load_kmer<KW>(v.packed, g, v.k);
+  const Key r = v.both ? revcomp<KW>(f, v.k) : f;
+  const uint32_t pred = sentinel ? 0u : base_at(v.packed, g - 1);
+  const uint32_t succ = sentinel ? 0u : base_at(v.packed, g + v.k);
+  make_occ<KW>(v, f, r, pred, succ, sentinel, oc);
+}
+
 // Visit the R consecutive positions p0 .. p0 + R - 1 (p0 < m), rolling the
 // k-mer from each position to the next within a string and reading it from
 // scratch after a string boundary. fn(i, p, valid, occ) runs for every i,
@@ -723,8 +735,9 @@ __global__ void __launch_bounds__(kBlock, 3) pass1_probe_kernel(RunView v, int r
       const int i = __ffs(bits) - 1;
       bits &= bits - 1;
       if (at < v.seg_cap) {
-        if (v.narrow) seg32[at] = (uint32_t)(p0 + (uint64_t)i);
-        else seg[at] = p0 + (uint64_t)i;
+        const uint64_t sent = (sent_bits >> i) & 1u;  // a string's first or last k-mer
+        if (v.narrow) seg32[at] = (uint32_t)(p0 + (uint64_t)i) | ((uint32_t)sent << 31);
+        else seg[at] = (p0 + (uint64_t)i) | (sent << 63);
       }
       ++at;
     }
@@ -807,9 +820,18 @@ __global__ void __launch_bounds__(kBlock) table_clear_kernel(RunView v) {
   }
 }
 
-// Candidate i of the list (32-bit records when the input has at most 2^32 bases).
-__device__ __forceinline__ uint64_t list_at(const RunView& v, uint64_t i) {
-  return v.narrow ? (uint64_t)__ldcs(reinterpret_cast<const uint32_t*>(v.cands) + i) : __ldcs(v.cands + i);
+// Candidate i of the list: its position, and whether it is a sentinel
+// position (the record's top bit; 32-bit records when the input has fewer
+// than 2^31 bases).
+__device__ __forceinline__ uint64_t list_at(const RunView& v, uint64_t i, bool* sentinel) {
+  if (v.narrow) {
+    const uint32_t r = __ldcs(reinterpret_cast<const uint32_t*>(v.cands) + i);
+    *sentinel = r >> 31;
+    return r & 0x7FFFFFFFu;
+  }
+  const uint64_t r = __ldcs(v.cands + i);
+  *sentinel = r >> 63;
+  return r & ~(1ull << 63);
 }
 
 // Algorithm 1, insert loop, second pass: every candidate ORs its in/out bases
@@ -851,7 +873,12 @@ __global__ void __launch_bounds__(kBlock) pass2_insert_kernel(RunView v) {
 #pragma unroll
       for (int u = 0; u < kP2; ++u) {
         const uint32_t jj = j + 32 * u;
-        ok[u] = jj < ls.n && read_occurrence<KW>(v, list_at(v, ls.first + jj), &oc[u]);
+        ok[u] = jj < ls.n;
+        if (ok[u]) {
+          bool sent;
+          const uint64_t g = list_at(v, ls.first + jj, &sent);
+          read_listed<KW>(v, g, sent, &oc[u]);
+        }
       }
 #pragma unroll
       for (int u = 0; u < kP2; ++u)
@@ -893,8 +920,12 @@ __global__ void __launch_bounds__(kBlock) pass2_classify_kernel(RunView v) {
 #pragma unroll
         for (int u = 0; u < kP2; ++u) {
           const uint32_t jj = j + 32 * u;
-          g[u] = jj < ls.n ? list_at(v, ls.first + jj) : 0;
-          ok[u] = jj < ls.n && read_occurrence<KW>(v, g[u], &oc[u]);
+          ok[u] = jj < ls.n;
+          if (ok[u]) {
+            bool sent;
+            g[u] = list_at(v, ls.first + jj, &sent);
+            read_listed<KW>(v, g[u], sent, &oc[u]);
+          }
         }
         int mk[kP2];
 #pragma unroll
