@@ -140,6 +140,27 @@ int twopaco_run_device(const uint8_t* d_bases, const uint64_t* d_offsets, uint64
                        uint64_t* d_out_offsets, uint64_t* d_out_positions, uint64_t out_capacity);
 
 /*
+ * A device-resident run captured as a CUDA graph. twopaco_plan_create takes
+ * the arguments of twopaco_run_device (options->cuda_stream is ignored),
+ * records that run's whole launch sequence -- pack, every round's two
+ * passes, emit -- into a graph without executing it, and instantiates it.
+ * twopaco_plan_launch replays it on cuda_stream with one launch; every
+ * replay is a complete run on the same buffers, so the caller may rewrite the
+ * input in place between replays (same sizes). Read the outcome with
+ * twopaco_read_stats as after twopaco_run_device. Kernels launched by a
+ * replay are counted by twopaco_kernel_launches; when profiling is enabled at
+ * creation, every replay re-records the per-kernel events.
+ */
+typedef struct twopaco_plan twopaco_plan;
+int twopaco_plan_create(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_seqs,
+                        uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
+                        const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
+                        uint64_t* d_out_offsets, uint64_t* d_out_positions, uint64_t out_capacity,
+                        twopaco_plan** plan);
+int twopaco_plan_launch(twopaco_plan* plan, void* cuda_stream);
+void twopaco_plan_destroy(twopaco_plan* plan);
+
+/*
  * Copy the counters of the last run on this workspace into *stats,
  * synchronising `cuda_stream` (NULL = default stream) first. Returns
  * TWOPACO_EBADBASE / TWOPACO_EOVERFLOW / TWOPACO_ETIMEOUT when the run

@@ -386,6 +386,79 @@ int twopaco_build_ex(const char* const* seqs, const uint64_t* lengths, uint64_t 
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Captured runs
+// ---------------------------------------------------------------------------
+
+struct twopaco_plan {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long kernels = 0;  // library kernels in one replay
+};
+
+extern "C" {
+
+int twopaco_plan_create(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_seqs,
+                        uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
+                        const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
+                        uint64_t* d_out_offsets, uint64_t* d_out_positions, uint64_t out_capacity,
+                        twopaco_plan** plan) {
+  if (!plan) return TWOPACO_EINVAL;
+  *plan = nullptr;
+  twopaco_options o = resolve(opt);
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_code(e);
+  o.cuda_stream = cs;
+  twopaco_plan* p = new (std::nothrow) twopaco_plan();
+  if (!p) {
+    cudaStreamDestroy(cs);
+    return TWOPACO_ENOMEM;
+  }
+  const unsigned long long before = launches_so_far();
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  int rc = e == cudaSuccess ? TWOPACO_OK : cuda_code(e);
+  if (rc == TWOPACO_OK) {
+    rc = twopaco_run_device(d_bases, d_offsets, n_seqs, total_bases, k, filter_bits, rounds, &o,
+                            d_workspace, workspace_bytes, d_out_offsets, d_out_positions, out_capacity);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);  // always end the capture, even after an error
+    if (rc == TWOPACO_OK && e != cudaSuccess) rc = cuda_code(e);
+    p->graph = g;
+  }
+  // the captured launches did not run: take them back out of the count
+  p->kernels = launches_so_far() - before;
+  count_launches(-(int)p->kernels);
+  if (rc == TWOPACO_OK) {
+    e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    if (e != cudaSuccess) rc = cuda_code(e);
+  }
+  cudaStreamDestroy(cs);
+  if (rc != TWOPACO_OK) {
+    twopaco_plan_destroy(p);
+    return rc;
+  }
+  *plan = p;
+  return TWOPACO_OK;
+}
+
+int twopaco_plan_launch(twopaco_plan* p, void* cuda_stream) {
+  if (!p || !p->exec) return TWOPACO_EINVAL;
+  cudaError_t e = cudaGraphLaunch(p->exec, static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_code(e);
+  count_launches((int)p->kernels);
+  return TWOPACO_OK;
+}
+
+void twopaco_plan_destroy(twopaco_plan* p) {
+  if (!p) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  delete p;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
 // Reusable context
 // ---------------------------------------------------------------------------
 

@@ -108,5 +108,6 @@ inline uint64_t cand_record_bytes(int) { return 8; }
 
 // Process-wide count of kernels launched by the library.
 void count_launches(int n);
+unsigned long long launches_so_far();
 
 }  // namespace twopaco

@@ -56,17 +56,22 @@ cudaEvent_t take_event() {
 struct Timed {
   ProfRecord rec{nullptr, nullptr, nullptr};
   cudaStream_t s;
+  unsigned flags = cudaEventRecordDefault;
   Timed(const char* name, cudaStream_t st) : s(st) {
     std::lock_guard<std::mutex> g(g_prof_mu);
     if (!g_prof_on) return;
     rec.name = name;
     rec.start = take_event();
     rec.stop = take_event();
-    cudaEventRecord(rec.start, s);
+    // inside a stream capture the events must become graph nodes of their own
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+      flags = cudaEventRecordExternal;
+    cudaEventRecordWithFlags(rec.start, s, flags);
   }
   ~Timed() {
     if (!rec.name) return;
-    cudaEventRecord(rec.stop, s);
+    cudaEventRecordWithFlags(rec.stop, s, flags);
     std::lock_guard<std::mutex> g(g_prof_mu);
     g_prof.push_back(rec);
   }
@@ -606,7 +611,9 @@ __device__ __forceinline__ uint32_t pack16(const RunView& v, uint64_t g, uint4 q
 }
 
 // ASCII -> 2-bit words: 64 bytes (four 128-bit loads in flight) per thread.
-// Block 0 also records where this run keeps its bitmaps (for inspection).
+// Block 0 also records where this run keeps its bitmaps (for inspection), and
+// the grid clears the filter, the linear-counting bitmap, C_final and the
+// emit's tile status for the first round.
 __global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     DevHeader* h = v.hdr;
@@ -644,6 +651,16 @@ __global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
     }
   }
   if (bad_at != ~0ull) atomicMax(&v.hdr->bad_inv, ~(unsigned long long)bad_at);
+  // clear what the first round and the emit need to start at zero
+  const uint64_t tid = (uint64_t)blockIdx.x * kBlock + threadIdx.x, nthreads = (uint64_t)gridDim.x * kBlock;
+  auto zero = [&](void* p, uint64_t bytes) {  // 16-byte multiples at 16-byte aligned addresses
+    uint4* q = static_cast<uint4*>(p);
+    for (uint64_t i = tid; i < bytes / 16; i += nthreads) q[i] = make_uint4(0u, 0u, 0u, 0u);
+  };
+  zero(v.filter, v.filter_words64 * 8);
+  zero(v.lc_bits, (1ull << v.lc_log2) / 8);
+  zero(v.cfinal, (v.bitmap_words + 3) / 4 * 16);
+  zero(v.tile_prefix, (v.n_tiles + 1) / 2 * 16);
 }
 
 // Algorithm 1, insert loop, first pass: every active position records its
@@ -1261,6 +1278,7 @@ int done(int n) {
 }  // namespace
 
 void count_launches(int n) { g_launches.fetch_add((unsigned long long)n); }
+unsigned long long launches_so_far() { return g_launches.load(); }
 
 int launch_init(const RunView& v, cudaStream_t s) {
   return cudaMemsetAsync(v.hdr, 0, sizeof(DevHeader), s) == cudaSuccess ? 0 : -1;
@@ -1291,7 +1309,7 @@ void with_hashes(int h, F&& f) {
 
 int launch_partition(const RunView& v, int rounds, cudaStream_t s) {
   if (v.m == 0) return 0;
-  if (cudaMemsetAsync(v.filter, 0, v.filter_words64 * 8, s) != cudaSuccess) return -1;
+  // the filter is clear (pack kernel); the pre-pass uses it, round 0 clears it again
   if (cudaMemsetAsync(v.bins, 0, (uint64_t)(v.qmask + 1u) * 4, s) != cudaSuccess) return -1;
   const uint64_t threads = (v.m + kR - 1) / kR;
   {
@@ -1314,9 +1332,10 @@ int launch_partition(const RunView& v, int rounds, cudaStream_t s) {
 
 template <int KW, bool RD, int HB, int TS>
 int round_impl(const RunView& v, int round, cudaStream_t s) {
-  if (cudaMemsetAsync(v.filter, 0, v.filter_words64 * 8, s) != cudaSuccess) return -1;
-  if (cudaMemsetAsync(v.lc_bits, 0, (1ull << v.lc_log2) / 8, s) != cudaSuccess) return -1;
-  if (round == 0 && cudaMemsetAsync(v.cfinal, 0, v.bitmap_words * 4, s) != cudaSuccess) return -1;
+  // the pack kernel cleared the filter and the LC bitmap for round 0; the
+  // partition pre-pass (rounds > 1) uses the filter before round 0
+  if (RD && cudaMemsetAsync(v.filter, 0, v.filter_words64 * 8, s) != cudaSuccess) return -1;
+  if (round > 0 && cudaMemsetAsync(v.lc_bits, 0, (1ull << v.lc_log2) / 8, s) != cudaSuccess) return -1;
   {
     Timed t("pass1_insert", s);
     pass1_insert_kernel<KW, RD, HB><<<grid_for(pass1_insert_kernel<KW, RD, HB>, kBlock,
@@ -1378,8 +1397,7 @@ int launch_round(const RunView& v, int round, int rounds, cudaStream_t s) {
 
 int launch_emit(const RunView& v, cudaStream_t s) {
   int n = 0;
-  if (v.n_tiles) {
-    if (cudaMemsetAsync(v.tile_prefix, 0, v.n_tiles * 8, s) != cudaSuccess) return -1;
+  if (v.n_tiles) {  // tile status cleared by the pack kernel
     Timed t("emit", s);
     emit_kernel<<<grid_for(emit_kernel, kBlock, v.n_tiles * kBlock), kBlock, 0, s>>>(v);
     n++;

@@ -116,6 +116,13 @@ def _lib() -> ctypes.CDLL:
         L.twopaco_edges_ctx.restype = I
         L.twopaco_edges_device.argtypes = [P, P, U64, P, P, P, P, U64, P]
         L.twopaco_edges_device.restype = I
+        L.twopaco_plan_create.argtypes = [P, P, U64, U64, I, U64, I, ctypes.POINTER(_Options), P, U64,
+                                          P, P, U64, ctypes.POINTER(ctypes.c_void_p)]
+        L.twopaco_plan_create.restype = I
+        L.twopaco_plan_launch.argtypes = [P, P]
+        L.twopaco_plan_launch.restype = I
+        L.twopaco_plan_destroy.argtypes = [P]
+        L.twopaco_plan_destroy.restype = None
         L.twopaco_profile_enable.argtypes = [I]
         L.twopaco_profile_enable.restype = I
         L.twopaco_profile_kernels.argtypes = [ctypes.POINTER(ctypes.c_char_p),
@@ -387,12 +394,36 @@ class DeviceBuild:
         return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
 
     def run(self, stream=None) -> None:
+        if getattr(self, "_plan", None):
+            rc = _lib().twopaco_plan_launch(self._plan, self._stream(stream) or None)
+            if rc != OK:
+                raise TwopacoError(rc, "twopaco_plan_launch")
+            return
         opt = Options(self.options.hashes, self.options.both_strands, self.options.partition_bins,
                       self.options.table_slots, self._stream(stream), self.options.candidate_records)
         twopaco_run_device(self.bases.data_ptr() if self.total_bases else 0, self.offsets.data_ptr(),
                            self.n_seqs, self.total_bases, self.k, self.filter_bits, self.rounds, opt,
                            self.ws_ptr, self.ws_bytes, self.out_offsets.data_ptr(),
                            self.out_positions.data_ptr(), self.capacity)
+
+    def capture(self) -> None:
+        """Capture this run as a CUDA graph (twopaco_plan_create); run() then replays it."""
+        self.release_plan()
+        h = ctypes.c_void_p()
+        opt = self.options._c()
+        rc = _lib().twopaco_plan_create(self.bases.data_ptr() if self.total_bases else None,
+                                        self.offsets.data_ptr(), self.n_seqs, self.total_bases,
+                                        self.k, self.filter_bits, self.rounds, ctypes.byref(opt),
+                                        self.ws_ptr, self.ws_bytes, self.out_offsets.data_ptr(),
+                                        self.out_positions.data_ptr(), self.capacity, ctypes.byref(h))
+        if rc != OK:
+            raise TwopacoError(rc, "twopaco_plan_create")
+        self._plan = h
+
+    def release_plan(self) -> None:
+        if getattr(self, "_plan", None):
+            _lib().twopaco_plan_destroy(self._plan)
+            self._plan = None
 
     def stats(self, stream=None, check: bool = True) -> Dict[str, int]:
         return twopaco_read_stats(self.ws_ptr, self._stream(stream), check)

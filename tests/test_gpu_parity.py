@@ -330,3 +330,46 @@ def test_edges_fig1_and_tiny_strings():
     assert list(np.diff(off)) == [2, 2, 0, 0]
     assert list(e["length"]) == [4, 3, 4, 3]
     ctx.close()
+
+
+def test_captured_run_replays_exactly():
+    """A run captured as a CUDA graph: replays, and replays after rewriting the input in place."""
+    import torch
+    seqs_a = _named("plain_single", 0.05)
+    bases_a, off = G.concat(seqs_a)
+    # a second input of identical string lengths: the same strings, reverse-complemented
+    comp = np.frombuffer(b"TGCA", np.uint8)
+    code = {65: 0, 67: 1, 71: 2, 84: 3}
+    seqs_b = [comp[np.array([code[int(c)] for c in s[::-1]])] for s in seqs_a]
+    bases_b, off_b = G.concat(seqs_b)
+    assert np.array_equal(off, off_b)
+    run = T().DeviceBuild(bases_a, off, 25, 1 << 20, 2, T().Options(hashes=4, partition_bins=256))
+    before = T().twopaco_kernel_launches()
+    run.capture()
+    assert T().twopaco_kernel_launches() == before, "capturing launches nothing"
+    for _ in range(3):
+        run.run()
+    per_replay = (T().twopaco_kernel_launches() - before) // 3
+    assert per_replay > 0
+    _eq(run.result(), O.junctions((bases_a, off), 25))
+    run.bases.copy_(torch.from_numpy(bases_b).cuda())  # same buffer, new content
+    run.run()
+    _eq(run.result(), O.junctions((bases_b, off), 25))
+    run.release_plan()
+
+
+def test_captured_run_profiles_every_replay():
+    seqs = _named("plain_single", 0.02)
+    bases, off = G.concat(seqs)
+    run = T().DeviceBuild(bases, off, 25, 1 << 20, 1, T().Options(hashes=4))
+    T().twopaco_profile_enable(True)
+    try:
+        run.capture()
+        for _ in range(2):
+            run.run()
+            prof = T().twopaco_profile_kernels()
+            assert prof["pass1_probe"]["ms"] > 0 and prof["pass1_insert"]["launches"] == 1
+    finally:
+        T().twopaco_profile_enable(False)
+        run.release_plan()
+    _eq(run.result(), O.junctions((bases, off), 25))
