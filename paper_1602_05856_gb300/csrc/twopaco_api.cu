@@ -54,7 +54,8 @@ int validate_size(uint64_t total_bases) {
 
 struct Layout {
   uint64_t header, packed, filter, ctemp, cfinal, tile_count, tile_prefix, bins, cuts, table;
-  uint64_t cands, lc, segs;
+  uint64_t cands, lc, segs, desc;
+  int use_desc;
   uint64_t total;
   uint64_t packed_words, bitmap_words, n_tiles, table_slots, cand_cap;
   int lc_log2;
@@ -108,6 +109,11 @@ Layout layout(uint64_t m, int k, uint64_t filter_bits, int rounds, const twopaco
   at += align_up((1ull << L.lc_log2) / 8);
   L.segs = at;
   at += align_up((uint64_t)kMaxSegments * 4);
+  // probe descriptors: one 64-bit word per position (filter word index, 30 bits
+  // of bit bases, flags) when they fit -- under 2^31 bases, h <= 6, b <= 2^37
+  L.use_desc = (m < (1ull << 31) && o.hashes <= 6 && filter_bits <= (1ull << 37)) ? 1 : 0;
+  L.desc = at;
+  if (L.use_desc) at += align_up((m + 16) * 8);
   L.total = at;
   return L;
 }
@@ -140,6 +146,8 @@ RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_
   v.table_max_slots = L.table_slots;
   v.cands = reinterpret_cast<uint64_t*>(base + L.cands);
   v.narrow = m < (1ull << 31) ? 1 : 0;  // 31-bit positions + a sentinel flag
+  v.use_desc = L.use_desc;
+  v.desc = reinterpret_cast<uint64_t*>(base + L.desc);
   v.cand_cap = L.cand_cap;
   v.lc_bits = reinterpret_cast<uint32_t*>(base + L.lc);
   v.lc_log2 = L.lc_log2;

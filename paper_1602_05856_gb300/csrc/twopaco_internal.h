@@ -64,6 +64,8 @@ struct RunView {
   uint64_t table_max_slots;
   uint64_t* cands;          // positions of the pass-1 survivors, for pass 2
   int narrow;               // m < 2^31: the list holds 32-bit records
+  uint64_t* desc;           // per-position probe descriptors (use_desc), m + 16 entries
+  int use_desc;             // the insert leaves descriptors and the probe reads them
   uint64_t cand_cap;        // records the list can hold
   uint32_t* seg_count;      // candidates per list segment (one segment per probe warp)
   uint32_t n_segments;      // warps of the probe grid (set per launch)

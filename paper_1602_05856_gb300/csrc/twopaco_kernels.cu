@@ -663,21 +663,69 @@ __global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
   zero(v.tile_prefix, (v.n_tiles + 1) / 2 * 16);
 }
 
+// Probe descriptor of a position (64 bits): bit 63 active (probe it), bit 62
+// sentinel position, bits 32-61 the bit bases of its k-mer (G >> 32, bases
+// of u < 6), bits 0-31 its filter word index. 1 marks a position whose
+// k-mer is in another round's class, 0 a position without a k-mer.
+constexpr uint64_t kDescActive = 1ull << 63, kDescSentinel = 1ull << 62;
+
+__device__ __forceinline__ uint64_t make_desc(const RunView& v, uint64_t H, uint64_t G, bool sentinel) {
+  const uint64_t block = v.lg_blocks ? (H >> (64 - v.lg_blocks)) : 0ull;
+  const uint64_t index = block * 4 + (G >> 62);  // < 2^32 for b <= 2^37
+  return kDescActive | (sentinel ? kDescSentinel : 0ull) | (((G >> 32) & 0x3FFFFFFFull) << 32) | index;
+}
+
 // Algorithm 1, insert loop, first pass: every active position records its
-// item(s) in its k-mer's filter word with one atomic OR.
-template <int KW, bool ROUNDS, int HB>
+// item(s) in its k-mer's filter word with one atomic OR. With DESC it also
+// leaves the position's probe descriptor for the probe loop: the block's
+// descriptors are staged in shared memory (16-byte pairs, columns swizzled by
+// the owning thread so that neither side conflicts) and written out in
+// order, whole sectors at a time.
+template <int KW, bool ROUNDS, int HB, bool DESC>
 __global__ void __launch_bounds__(kBlock) pass1_insert_kernel(RunView v, int round) {
-  const uint64_t stride = (uint64_t)gridDim.x * kBlock * kInsertR;
-  for (uint64_t p0 = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) * kInsertR; p0 < v.m; p0 += stride) {
-    walk<KW, kInsertR>(v, p0, [&](int, uint64_t, bool valid, const Occ& oc) {
-      if (!valid || (ROUNDS && !in_round(v, oc.H, round))) return;
-      const uint64_t G = second_hash(oc.H);
-      const ItemPattern pat = item_pattern<HB>(G);
-      const uint32_t j1 = __ffs(oc.items) - 1, j2 = 31 - __clz(oc.items);
-      uint64_t m = item_bits(pat, j1);
-      if (j2 != j1) m |= item_bits(pat, j2);  // a palindrome's two orientations
-      atomicOr(filter_word(v, oc.H, G), (unsigned long long)m);
-    });
+  constexpr int kTile = kBlock * kInsertR;  // positions per block per pass
+  constexpr int kPairs = kInsertR / 2;      // 16-byte descriptor pairs per thread
+  __shared__ ulonglong2 stage[DESC ? kTile / 2 : 1];
+  const uint64_t stride = (uint64_t)gridDim.x * kTile;
+  const int t = threadIdx.x;
+  for (uint64_t base = (uint64_t)blockIdx.x * kTile; base < v.m; base += stride) {
+    const uint64_t p0 = base + (uint64_t)t * kInsertR;
+    if (p0 < v.m) {
+      uint64_t prev = 0;
+      walk<KW, kInsertR>(v, p0, [&](int i, uint64_t, bool valid, const Occ& oc) {
+        uint64_t d = 0;
+        if (valid) {
+          if (ROUNDS && !in_round(v, oc.H, round)) {
+            d = 1;
+          } else {
+            const uint64_t G = second_hash(oc.H);
+            const ItemPattern pat = item_pattern<HB>(G);
+            const uint32_t j1 = __ffs(oc.items) - 1, j2 = 31 - __clz(oc.items);
+            uint64_t m = item_bits(pat, j1);
+            if (j2 != j1) m |= item_bits(pat, j2);  // a palindrome's two orientations
+            atomicOr(filter_word(v, oc.H, G), (unsigned long long)m);
+            if (DESC) d = make_desc(v, oc.H, G, oc.sentinel);
+          }
+        }
+        if (DESC) {
+          if (i & 1) stage[t * kPairs + ((i >> 1) ^ (t % kPairs))] = make_ulonglong2(prev, d);
+          else prev = d;
+        }
+      });
+    }
+    if (DESC) {
+      __syncthreads();
+      // pair j covers positions base + 2j, base + 2j + 1; its owner is thread
+      // j / kPairs (which wrote 0 for any of them past m). The region holds
+      // m + 16 descriptors, so a pair that starts before m fits.
+      for (int j = t; j < kTile / 2; j += kBlock) {
+        const uint64_t p = base + 2 * (uint64_t)j;
+        if (p >= v.m) break;
+        const int owner = j / kPairs, c = j % kPairs;
+        __stcs(reinterpret_cast<ulonglong2*>(v.desc + p), stage[owner * kPairs + (c ^ (owner % kPairs))]);
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -761,6 +809,80 @@ __global__ void __launch_bounds__(kBlock, 3) pass1_probe_kernel(RunView v, int r
     seg_used += __shfl_sync(0xffffffffu, inc, 31);
     kept += c;
     valid_n += __popc(valid_bits);
+  }
+  if (lane == 0) {
+    v.seg_count[warp_id] = (uint32_t)(seg_used < v.seg_cap ? seg_used : v.seg_cap);
+    if (seg_used > v.seg_cap) v.hdr->cand_overflow = 1;
+  }
+  block_add(kept, &v.hdr->pass1_kept);
+  block_add(kept, &v.hdr->round_kept);
+  if (round == 0) block_add(valid_n, &v.hdr->positions);
+}
+
+// The probe loop from descriptors (same decisions and outputs as
+// pass1_probe_kernel). A warp takes kProbeR rows of 32 consecutive
+// positions; lane l reads the descriptor of position row + l (one coalesced
+// 256-byte load per row), loads the filter words of its active non-sentinel
+// positions, then decides. A row's ballot is its C_temp word, and its kept
+// positions go to the warp's list segment in order.
+template <int HB>
+__global__ void __launch_bounds__(kBlock) pass1_probe_desc_kernel(RunView v, int round) {
+  static_assert(HB <= 6, "descriptors carry the bases of six bits");
+  constexpr int kRows = kProbeR;
+  static_assert(kRows <= 32, "one C_temp word per lane");
+  const int lane = threadIdx.x & 31;
+  const uint32_t below = (1u << lane) - 1u;
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock * kRows;
+  unsigned long long kept = 0, valid_n = 0;
+  const uint32_t warp_id = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  uint64_t* seg = v.cands + (uint64_t)warp_id * v.seg_cap;
+  uint32_t* seg32 = reinterpret_cast<uint32_t*>(v.cands) + (uint64_t)warp_id * v.seg_cap;
+  uint64_t seg_used = 0;
+  for (uint64_t wbase = ((uint64_t)blockIdx.x * kBlock + (threadIdx.x & ~31u)) * kRows; wbase < v.m;
+       wbase += stride) {
+    uint64_t d[kRows], word[kRows];
+#pragma unroll
+    for (int q = 0; q < kRows; ++q) {
+      const uint64_t p = wbase + 32 * q + lane;
+      d[q] = p < v.m ? __ldcs(v.desc + p) : 0ull;
+    }
+#pragma unroll
+    for (int q = 0; q < kRows; ++q)
+      if ((d[q] & (kDescActive | kDescSentinel)) == kDescActive) word[q] = __ldcg(v.filter + (uint32_t)d[q]);
+    uint32_t my_word = 0;
+#pragma unroll
+    for (int q = 0; q < kRows; ++q) {
+      bool keep = false;
+      if (d[q] & kDescActive) {
+        if (d[q] & kDescSentinel) {
+          keep = true;
+        } else {
+          // descriptor bits 32-61 are G's, the only bits bit_base reads for u < 6
+          const uint32_t pres = present_items<HB>(d[q], word[q]);
+          keep = (pres >> 16) || __popc(pres & 0xFFFFu) >= 2;
+        }
+      }
+      valid_n += d[q] != 0;
+      const uint32_t row = __ballot_sync(0xffffffffu, keep);
+      if (lane == q) my_word = row;
+      if (keep) {
+        const uint64_t idx = ((d[q] & ~(kDescActive | kDescSentinel)) * 0xff51afd7ed558ccdull) >> (64 - v.lc_log2);
+        atomicOr(v.lc_bits + (idx >> 5), 1u << (idx & 31));
+        const uint64_t at = seg_used + __popc(row & below);
+        if (at < v.seg_cap) {
+          const uint64_t p = wbase + 32 * q + lane;
+          const uint64_t sent = (d[q] >> 62) & 1u;
+          if (v.narrow) seg32[at] = (uint32_t)p | ((uint32_t)sent << 31);
+          else seg[at] = p | (sent << 63);
+        }
+        ++kept;
+      }
+      seg_used += __popc(row);
+    }
+    if (lane < kRows) {
+      const uint64_t w = (wbase >> 5) + lane;
+      if (w < v.bitmap_words) v.ctemp[w] = my_word;
+    }
   }
   if (lane == 0) {
     v.seg_count[warp_id] = (uint32_t)(seg_used < v.seg_cap ? seg_used : v.seg_cap);
@@ -1336,23 +1458,31 @@ int round_impl(const RunView& v, int round, cudaStream_t s) {
   // partition pre-pass (rounds > 1) uses the filter before round 0
   if (RD && cudaMemsetAsync(v.filter, 0, v.filter_words64 * 8, s) != cudaSuccess) return -1;
   if (round > 0 && cudaMemsetAsync(v.lc_bits, 0, (1ull << v.lc_log2) / 8, s) != cudaSuccess) return -1;
+  constexpr bool kDescOk = HB <= 6;
+  const bool desc = kDescOk && v.use_desc;
   {
     Timed t("pass1_insert", s);
-    pass1_insert_kernel<KW, RD, HB><<<grid_for(pass1_insert_kernel<KW, RD, HB>, kBlock,
-                                               (v.m + kInsertR - 1) / kInsertR),
-                                      kBlock, 0, s>>>(v, round);
+    const uint64_t threads = (v.m + kInsertR - 1) / kInsertR;
+    if (desc)
+      pass1_insert_kernel<KW, RD, HB, kDescOk><<<grid_for(pass1_insert_kernel<KW, RD, HB, kDescOk>, kBlock, threads),
+                                                 kBlock, 0, s>>>(v, round);
+    else
+      pass1_insert_kernel<KW, RD, HB, false><<<grid_for(pass1_insert_kernel<KW, RD, HB, false>, kBlock, threads),
+                                               kBlock, 0, s>>>(v, round);
   }
   const uint64_t threads = (v.m + kProbeR - 1) / kProbeR;
   // one candidate-list segment per probe warp
   RunView pv = v;
-  unsigned grid = grid_for(pass1_probe_kernel<KW, RD, HB>, kBlock, threads);
+  unsigned grid = desc ? grid_for(pass1_probe_desc_kernel<kDescOk ? HB : 1>, kBlock, threads)
+                       : grid_for(pass1_probe_kernel<KW, RD, HB>, kBlock, threads);
   if (grid * (kBlock / 32) > kMaxSegments) grid = kMaxSegments / (kBlock / 32);
   pv.n_segments = grid * (kBlock / 32);
   // the list region holds cand_cap 8-byte records, or twice as many 32-bit ones
   pv.seg_cap = (v.narrow ? 2 * v.cand_cap : v.cand_cap) / pv.n_segments;
   {
     Timed t("pass1_probe", s);
-    pass1_probe_kernel<KW, RD, HB><<<grid, kBlock, 0, s>>>(pv, round);
+    if (desc) pass1_probe_desc_kernel<kDescOk ? HB : 1><<<grid, kBlock, 0, s>>>(pv, round);
+    else pass1_probe_kernel<KW, RD, HB><<<grid, kBlock, 0, s>>>(pv, round);
   }
   {
     Timed t("table_setup", s);
