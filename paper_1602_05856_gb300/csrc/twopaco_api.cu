@@ -54,8 +54,8 @@ int validate_size(uint64_t total_bases) {
 
 struct Layout {
   uint64_t header, packed, filter, ctemp, cfinal, tile_count, tile_prefix, bins, cuts, table;
-  uint64_t cands, lc, segs, desc;
-  int use_desc;
+  uint64_t cands, lc, segs, desc, cslot;
+  int use_desc, use_slot;
   uint64_t total;
   uint64_t packed_words, bitmap_words, n_tiles, table_slots, cand_cap;
   int lc_log2;
@@ -102,6 +102,12 @@ Layout layout(uint64_t m, int k, uint64_t filter_bits, int rounds, const twopaco
                                    : (per_round / 4 > (1u << 16) ? per_round / 4 : (1u << 16));
   L.cands = at;
   at += align_up(L.cand_cap * cand_record_bytes(k));
+  // the table slot of every listed candidate (32-bit slot indices), kept by
+  // the second-pass insert for its probe loop; one per record of the list
+  // (twice as many 32-bit records under 2^31 bases)
+  L.use_slot = L.table_slots <= (1ull << 32) ? 1 : 0;
+  L.cslot = at;
+  if (L.use_slot) at += align_up(L.cand_cap * (m < (1ull << 31) ? 2 : 1) * 4);
   // linear-counting bitmap: 2^lc_log2 >= the list's capacity (at least 2^16 bits)
   L.lc_log2 = 16;
   while ((1ull << L.lc_log2) < L.cand_cap && L.lc_log2 < 36) ++L.lc_log2;
@@ -147,6 +153,7 @@ RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_
   v.cands = reinterpret_cast<uint64_t*>(base + L.cands);
   v.narrow = m < (1ull << 31) ? 1 : 0;  // 31-bit positions + a sentinel flag
   v.use_desc = L.use_desc;
+  v.cand_slot = L.use_slot ? reinterpret_cast<uint32_t*>(base + L.cslot) : nullptr;
   v.desc = reinterpret_cast<uint64_t*>(base + L.desc);
   v.cand_cap = L.cand_cap;
   v.lc_bits = reinterpret_cast<uint32_t*>(base + L.lc);

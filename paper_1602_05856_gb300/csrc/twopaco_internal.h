@@ -20,7 +20,7 @@ struct DevHeader {
   unsigned int cand_overflow;      // a warp's list segment ran out of room this round
   unsigned int round_listed;       // pass 2 of this round reads the list (else C_temp)
   unsigned int lc_blocks_done;     // blocks of lc_count finished this round
-  unsigned int pad0;
+  unsigned int list_parts;         // pass-2 parts per list segment this round
   unsigned long long emit_ticket;  // next emit tile to claim
   unsigned int overflow;           // table or output out of room
   unsigned int timeout;            // a bounded wait gave up
@@ -64,13 +64,13 @@ struct RunView {
   uint64_t table_max_slots;
   uint64_t* cands;          // positions of the pass-1 survivors, for pass 2
   int narrow;               // m < 2^31: the list holds 32-bit records
+  uint32_t* cand_slot;      // table slot of every listed candidate (null: look it up)
   uint64_t* desc;           // per-position probe descriptors (use_desc), m + 16 entries
   int use_desc;             // the insert leaves descriptors and the probe reads them
   uint64_t cand_cap;        // records the list can hold
   uint32_t* seg_count;      // candidates per list segment (one segment per probe warp)
   uint32_t n_segments;      // warps of the probe grid (set per launch)
   uint64_t seg_cap;         // records per segment (set per launch)
-  uint32_t seg_warps;       // pass-2 warps per segment (set per launch)
   uint32_t* lc_bits;        // linear-counting bitmap, 2^lc_log2 bits
   int lc_log2;
   uint32_t* bins;           // partition counters (q), rounds > 1

@@ -444,11 +444,13 @@ __device__ __forceinline__ void cas128(unsigned long long* addr, uint64_t cmp_lo
   *old_hi = oh;
 }
 
-// Insert (key, bits) into a table of TS-kind slots (table_slot_kind); false
-// if every slot was tried (the table is full). Bits already present are not
-// written again.
+constexpr uint64_t kNoSlot = ~0ull;
+
+// Insert (key, bits) into a table of TS-kind slots (table_slot_kind); the
+// key's slot, or kNoSlot if every slot was tried (the table is full). Bits
+// already present are not written again.
 template <int TS>
-__device__ __forceinline__ bool table_insert(const RunView& v, uint64_t cap, const Key& key,
+__device__ __forceinline__ uint64_t table_insert(const RunView& v, uint64_t cap, const Key& key,
                                              uint64_t start, uint32_t bits) {
   const uint64_t mask = cap - 1;
   uint64_t i = start & mask;
@@ -459,11 +461,11 @@ __device__ __forceinline__ bool table_insert(const RunView& v, uint64_t cap, con
       unsigned long long cur = __ldcg(s);
       if (cur == kEmpty) {
         cur = atomicCAS(s, kEmpty, (key.lo << kMaskBits) | bits);
-        if (cur == kEmpty) return true;
+        if (cur == kEmpty) return i;
       }
       if ((cur >> kMaskBits) != key.lo) continue;
       if ((cur & bits) != bits) atomicOr(s, (unsigned long long)bits);
-      return true;
+      return i;
     } else if (TS == 1) {
       Slot1* s = static_cast<Slot1*>(v.table) + i;
       const ulonglong2 w = __ldcg(reinterpret_cast<const ulonglong2*>(s));
@@ -476,7 +478,7 @@ __device__ __forceinline__ bool table_insert(const RunView& v, uint64_t cap, con
       }
       if (cur != key.lo) continue;
       if ((have & bits) != bits) atomicOr(&s->mask, bits);
-      return true;
+      return i;
     } else {
       Slot2* s = static_cast<Slot2*>(v.table) + i;
       uint64_t ol, oh;
@@ -484,10 +486,10 @@ __device__ __forceinline__ bool table_insert(const RunView& v, uint64_t cap, con
       const bool mine = (ol == kEmpty && oh == kEmpty) || (ol == key.lo && oh == key.hi);
       if (!mine) continue;
       if ((__ldcg(&s->mask) & bits) != bits) atomicOr(&s->mask, bits);
-      return true;
+      return i;
     }
   }
-  return false;
+  return kNoSlot;
 }
 
 // Mask of key, or -1 if absent.
@@ -513,6 +515,14 @@ __device__ __forceinline__ int table_find(const RunView& v, uint64_t cap, const 
     }
   }
   return -1;
+}
+
+// Mask held by slot i (a slot that table_insert returned).
+template <int TS>
+__device__ __forceinline__ int table_mask(const RunView& v, uint64_t i) {
+  if (TS == 0) return (int)(__ldcg(static_cast<const unsigned long long*>(v.table) + i) & ((1u << kMaskBits) - 1u));
+  if (TS == 1) return (int)__ldcg(&(static_cast<const Slot1*>(v.table) + i)->mask);
+  return (int)__ldcg(&(static_cast<const Slot2*>(v.table) + i)->mask);
 }
 
 __device__ __forceinline__ bool is_junction_mask(int mk) {
@@ -893,7 +903,9 @@ __global__ void __launch_bounds__(kBlock) pass1_probe_desc_kernel(RunView v, int
   if (round == 0) block_add(valid_n, &v.hdr->positions);
 }
 
-constexpr double kTableLoad = 2.0;  // table slots per estimated distinct candidate
+constexpr double kTableLoad = 2.0;
+// pass-2 list work: parts of about this many records, at most kMaxParts per segment
+constexpr unsigned long long kPartRecords = 32, kMaxParts = 4096;  // table slots per estimated distinct candidate
 
 // Size the pass-2 table of this round: twice the number of distinct
 // candidate k-mers, estimated by linear counting (Whang, Vander-Zanden &
@@ -935,6 +947,9 @@ __global__ void __launch_bounds__(kBlock) table_setup_kernel(RunView v) {
   v.hdr->table_slots = cap;
   if (cap > v.hdr->table_max) v.hdr->table_max = cap;
   v.hdr->round_listed = *(volatile unsigned int*)&v.hdr->cand_overflow ? 0u : 1u;
+  // pass 2 cuts every list segment into parts of about kPartRecords records
+  unsigned long long parts = (kept / v.n_segments + kPartRecords) / kPartRecords;
+  v.hdr->list_parts = (unsigned int)(parts < kMaxParts ? parts : kMaxParts);
   v.hdr->cand_overflow = 0;
   v.hdr->round_kept = 0;
   v.hdr->lc_set = 0;
@@ -962,68 +977,53 @@ __global__ void __launch_bounds__(kBlock) table_clear_kernel(RunView v) {
 // Candidate i of the list: its position, and whether it is a sentinel
 // position (the record's top bit; 32-bit records when the input has fewer
 // than 2^31 bases).
-__device__ __forceinline__ uint64_t list_at(const RunView& v, uint64_t i, bool* sentinel) {
+__device__ __forceinline__ uint64_t list_at(const RunView& v, uint64_t i, bool* sentinel, bool last_use) {
   if (v.narrow) {
-    const uint32_t r = __ldcs(reinterpret_cast<const uint32_t*>(v.cands) + i);
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(v.cands) + i;
+    const uint32_t r = last_use ? __ldcs(p) : __ldcg(p);
     *sentinel = r >> 31;
     return r & 0x7FFFFFFFu;
   }
-  const uint64_t r = __ldcs(v.cands + i);
+  const uint64_t r = last_use ? __ldcs(v.cands + i) : __ldcg(v.cands + i);
   *sentinel = r >> 63;
   return r & ~(1ull << 63);
 }
 
-// Algorithm 1, insert loop, second pass: every candidate ORs its in/out bases
-// (or the sentinel bit) into the exact table entry of its k-mer. Reads the
-// candidate list; if the list overflowed, walks C_temp instead.
-constexpr int kP2 = 1;  // candidates per thread and step in pass 2 (1 measured fastest)
-
-// The list segment and the slice of it that this thread visits: candidate
-// indices first + j for j = j0, j0 + jstep, ... < n.
-struct ListSlice {
-  uint64_t first;
-  uint32_t j0, jstep, n;
-};
-
-__device__ __forceinline__ bool list_slice(const RunView& v, ListSlice* ls) {
-  const uint32_t gw = (blockIdx.x * kBlock + threadIdx.x) >> 5;
-  const uint32_t sgm = gw / v.seg_warps;
-  if (sgm >= v.n_segments) return false;
-  ls->first = (uint64_t)sgm * v.seg_cap;
-  ls->n = v.seg_count[sgm];
-  ls->j0 = (gw % v.seg_warps) * 32 * kP2 + (threadIdx.x & 31);
-  ls->jstep = 32 * kP2 * v.seg_warps;
-  return true;
+// Pass-2 work over the candidate list. Every list segment is cut into
+// list_parts parts (interleaved 32-record rows), and the launched warps take
+// the (segment, part) pairs in turn, so that the work spreads evenly over a
+// grid that is resident all at once. fn(i) runs for list index i.
+template <typename F>
+__device__ __forceinline__ void for_listed(const RunView& v, F&& fn) {
+  const uint32_t parts = *(volatile unsigned int*)&v.hdr->list_parts;
+  const uint64_t pairs = (uint64_t)v.n_segments * parts;
+  const uint64_t warps = (uint64_t)gridDim.x * (kBlock / 32);
+  const uint32_t lane = threadIdx.x & 31;
+  for (uint64_t w = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) >> 5; w < pairs; w += warps) {
+    const uint32_t sgm = (uint32_t)(w / parts), part = (uint32_t)(w % parts);
+    const uint32_t n = __ldcg(v.seg_count + sgm);
+    const uint64_t first = (uint64_t)sgm * v.seg_cap;
+    for (uint32_t j = part * 32 + lane; j < n; j += 32 * parts) fn(first + j);
+  }
 }
 
 // Algorithm 1, insert loop, second pass: every candidate ORs its in/out bases
 // (or the sentinel bit) into the exact table entry of its k-mer. Reads the
-// candidate list (kP2 candidates per thread at a time, so that their loads
-// overlap); if the list overflowed, walks C_temp instead.
+// candidate list and keeps the slot of each listed candidate for the probe
+// loop; if the list overflowed, walks C_temp instead.
 template <int KW, int TS>
 __global__ void __launch_bounds__(kBlock) pass2_insert_kernel(RunView v) {
   const uint64_t cap = *(volatile unsigned long long*)&v.hdr->table_slots;
   if (*(volatile unsigned int*)&v.hdr->round_listed) {
-    ListSlice ls;
-    if (!list_slice(v, &ls)) return;
-    for (uint32_t j = ls.j0; j < ls.n; j += ls.jstep) {
-      Occ oc[kP2];
-      bool ok[kP2];
-#pragma unroll
-      for (int u = 0; u < kP2; ++u) {
-        const uint32_t jj = j + 32 * u;
-        ok[u] = jj < ls.n;
-        if (ok[u]) {
-          bool sent;
-          const uint64_t g = list_at(v, ls.first + jj, &sent);
-          read_listed<KW>(v, g, sent, &oc[u]);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kP2; ++u)
-        if (ok[u] && !table_insert<TS>(v, cap, oc[u].key, slot_hash(oc[u].H), oc[u].tbits))
-          v.hdr->overflow = 1;
-    }
+    for_listed(v, [&](uint64_t i) {
+      bool sent;
+      const uint64_t g = list_at(v, i, &sent, false);
+      Occ oc;
+      read_listed<KW>(v, g, sent, &oc);
+      const uint64_t slot = table_insert<TS>(v, cap, oc.key, slot_hash(oc.H), oc.tbits);
+      if (slot == kNoSlot) v.hdr->overflow = 1;
+      if (v.cand_slot) v.cand_slot[i] = slot == kNoSlot ? 0xFFFFFFFFu : (uint32_t)slot;
+    });
     return;
   }
   const uint64_t stride = (uint64_t)gridDim.x * kBlock;
@@ -1031,13 +1031,15 @@ __global__ void __launch_bounds__(kBlock) pass2_insert_kernel(RunView v) {
     if (!((__ldg(v.ctemp + (g >> 5)) >> (g & 31)) & 1u)) continue;
     Occ oc;
     if (!read_occurrence<KW>(v, g, &oc)) continue;
-    if (!table_insert<TS>(v, cap, oc.key, slot_hash(oc.H), oc.tbits)) v.hdr->overflow = 1;
+    if (table_insert<TS>(v, cap, oc.key, slot_hash(oc.H), oc.tbits) == kNoSlot) v.hdr->overflow = 1;
   }
 }
 
 // Algorithm 1, probe loop, second pass: a candidate is a junction iff its
 // k-mer is a sentinel or has more than one distinct in- or out-base. Sets
-// the junction's bit of C_final (cleared before the first round).
+// the junction's bit of C_final (cleared before the first round). A listed
+// candidate reads its mask from the slot the insert loop kept (or looks its
+// k-mer up when no slots were kept).
 template <int KW, int TS>
 __global__ void __launch_bounds__(kBlock) pass2_classify_kernel(RunView v) {
   const uint64_t cap = *(volatile unsigned long long*)&v.hdr->table_slots;
@@ -1050,30 +1052,18 @@ __global__ void __launch_bounds__(kBlock) pass2_classify_kernel(RunView v) {
     }
   };
   if (*(volatile unsigned int*)&v.hdr->round_listed) {
-    ListSlice ls;
-    if (list_slice(v, &ls)) {
-      for (uint32_t j = ls.j0; j < ls.n; j += ls.jstep) {
-        Occ oc[kP2];
-        uint64_t g[kP2];
-        bool ok[kP2];
-#pragma unroll
-        for (int u = 0; u < kP2; ++u) {
-          const uint32_t jj = j + 32 * u;
-          ok[u] = jj < ls.n;
-          if (ok[u]) {
-            bool sent;
-            g[u] = list_at(v, ls.first + jj, &sent);
-            read_listed<KW>(v, g[u], sent, &oc[u]);
-          }
-        }
-        int mk[kP2];
-#pragma unroll
-        for (int u = 0; u < kP2; ++u) mk[u] = ok[u] ? table_find<TS>(v, cap, oc[u].key, slot_hash(oc[u].H)) : 0;
-#pragma unroll
-        for (int u = 0; u < kP2; ++u)
-          if (ok[u]) mark(g[u], mk[u]);
+    for_listed(v, [&](uint64_t i) {
+      bool sent;
+      const uint64_t g = list_at(v, i, &sent, true);
+      if (v.cand_slot) {
+        const uint32_t slot = __ldcs(v.cand_slot + i);
+        mark(g, slot == 0xFFFFFFFFu ? -1 : table_mask<TS>(v, slot));
+      } else {
+        Occ oc;
+        read_listed<KW>(v, g, sent, &oc);
+        mark(g, table_find<TS>(v, cap, oc.key, slot_hash(oc.H)));
       }
-    }
+    });
   } else {
     const uint64_t stride = (uint64_t)gridDim.x * kBlock;
     for (uint64_t g = (uint64_t)blockIdx.x * kBlock + threadIdx.x; g < v.m; g += stride) {
@@ -1492,19 +1482,16 @@ int round_impl(const RunView& v, int round, cudaStream_t s) {
     Timed t("table_clear", s);
     table_clear_kernel<TS><<<grid_for(table_clear_kernel<TS>, kBlock, v.table_max_slots), kBlock, 0, s>>>(pv);
   }
-  // pass 2: enough warps per list segment to fill the GPU (a walk of C_temp
-  // if a segment overflowed reuses the same grid)
-  const uint32_t want_warps = (uint32_t)sm_count() * 64u;
-  pv.seg_warps = (want_warps + pv.n_segments - 1) / pv.n_segments;  // per segment
-  if (pv.seg_warps < 1) pv.seg_warps = 1;
-  const unsigned g2 = (unsigned)(((uint64_t)pv.n_segments * pv.seg_warps * 32 + kBlock - 1) / kBlock);
+  // pass 2: one resident wave; the warps share out the list's segment parts
+  const unsigned g2 = grid_for(pass2_insert_kernel<KW, TS>, kBlock, ~0ull >> 1);
+  const unsigned g3 = grid_for(pass2_classify_kernel<KW, TS>, kBlock, ~0ull >> 1);
   {
     Timed t("pass2_insert", s);
     pass2_insert_kernel<KW, TS><<<g2, kBlock, 0, s>>>(pv);
   }
   {
     Timed t("pass2_classify", s);
-    pass2_classify_kernel<KW, TS><<<g2, kBlock, 0, s>>>(pv);
+    pass2_classify_kernel<KW, TS><<<g3, kBlock, 0, s>>>(pv);
   }
   return done(6);
 }
