@@ -187,6 +187,26 @@ def kernel_work(name, st, m, n_seqs, table_bytes):
     return None, None
 
 
+def ncu_traffic(workload, kernel):
+    """DRAM bytes per launch of `kernel` on `workload`, from a committed ncu summary.
+
+    profiles/dram_traffic_*.md carry lines ``dram-traffic <workload> <kernel> <bytes>
+    sha256:<digest of csrc/twopaco_kernels.cu when captured>``; a figure taken from an
+    older kernel source does not count (None).
+    """
+    import hashlib
+    import glob
+    import re
+    src = os.path.join(ROOT, "paper_1602_05856_gb300", "csrc", "twopaco_kernels.cu")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "dram_traffic_*.md"))):
+        for line in open(path):
+            m = re.match(r"dram-traffic (\S+) (\S+) (\d+) sha256:([0-9a-f]{64})\s*$", line.strip())
+            if m and m.group(1) == workload and m.group(2) == kernel and m.group(4) == digest:
+                return int(m.group(3))
+    return None
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_1602_05856_gb300 import build, genomes, twopaco as T
@@ -293,7 +313,7 @@ def run_ours(args, world, rank, local):
                                     "~8 filter bits per base, 4 hashes"}
 
     # roofline of the dominant kernel
-    table_bytes = st["table_slots"] * (16 if K <= 31 else 32)
+    table_bytes = st["table_slots"] * (8 if K <= 27 else 16 if K <= 31 else 32)
     top = max(prof.items(), key=lambda kv: kv[1]["ms"])
     name, rec = top
     per_launch_ms = rec["ms"] / rec["launches"]
@@ -316,6 +336,8 @@ def run_ours(args, world, rank, local):
                                 + f" over a {FILTER_BITS // 8 >> 20} MiB buffer (the filter's size), "
                                 "all SMs, best of 5")}
     roof["kernel"] = name
+    roof["traffic"] = ncu_traffic(WORKLOAD, name)
+    roof["traffic_unit"] = "DRAM bytes per launch (ncu, cold cache)"
     roof["kernel_ms"] = per_launch_ms
 
     kernels = {k: {"launches": v["launches"], "ms_per_launch": v["ms"] / v["launches"],
