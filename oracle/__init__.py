@@ -26,11 +26,11 @@ def lib() -> ctypes.CDLL:
         P = ctypes.c_void_p
         U64 = ctypes.c_uint64
         I = ctypes.c_int
-        L.oracle_junctions.argtypes = [P, P, U64, I, I, P, P]
-        L.oracle_alg1_exact.argtypes = [P, P, U64, I, I, P]
-        L.oracle_pass1.argtypes = [P, P, U64, I, I, U64, I, U64, U64, U64, P, P]
+        L.oracle_junctions.argtypes = [P, P, U64, I, I, I, P, P]
+        L.oracle_alg1_exact.argtypes = [P, P, U64, I, I, I, P]
+        L.oracle_pass1.argtypes = [P, P, U64, I, I, I, U64, I, U64, U64, U64, P, P]
         L.oracle_partition_cuts.argtypes = [P, U64, I, P]
-        L.oracle_edges.argtypes = [P, P, U64, I, I, P, P, P, P, P, P, P, P, P, P]
+        L.oracle_edges.argtypes = [P, P, U64, I, I, I, P, P, P, P, P, P, P, P, P, P]
         L.oracle_edges.restype = ctypes.c_longlong
         for f in (L.oracle_junctions, L.oracle_alg1_exact, L.oracle_pass1,
                   L.oracle_partition_cuts):
@@ -47,7 +47,7 @@ def _check(rc: int) -> None:
     if rc == -1:
         raise OracleError("invalid argument")
     if rc == -2:
-        raise OracleError("byte outside ACGTacgt")
+        raise OracleError("byte outside ACGTacgt (and Nn unless split_n)")
     if rc != 0:
         raise OracleError(f"oracle error {rc}")
 
@@ -74,24 +74,31 @@ def _split(flags: np.ndarray, off: np.ndarray) -> List[np.ndarray]:
             for t in range(off.size - 1)]
 
 
-def junction_flags(seqs, k: int, both_strands: bool = True) -> Tuple[np.ndarray, np.ndarray, int]:
+def junction_flags(seqs, k: int, both_strands: bool = True,
+                   split_n: bool = False) -> Tuple[np.ndarray, np.ndarray, int]:
     """(flags per global byte, offsets, number of distinct k-mers) by definition."""
     buf, off = _prep(seqs)
     m = int(off[-1])
     flags = np.zeros(max(m, 1), np.uint8)
     nd = ctypes.c_uint64(0)
     _check(lib().oracle_junctions(buf.ctypes.data, off.ctypes.data, off.size - 1, k,
-                                  int(both_strands), flags.ctypes.data, ctypes.byref(nd)))
+                                  int(both_strands), int(split_n), flags.ctypes.data,
+                                  ctypes.byref(nd)))
     return flags[:m], off, int(nd.value)
 
 
-def junctions(seqs, k: int, both_strands: bool = True) -> List[np.ndarray]:
-    """Sorted junction positions of every string, by definition of J(S, k)."""
-    flags, off, _ = junction_flags(seqs, k, both_strands)
+def junctions(seqs, k: int, both_strands: bool = True, split_n: bool = False) -> List[np.ndarray]:
+    """Sorted junction positions of every string, by definition of J(S, k).
+
+    With ``split_n`` every N ends its string there (the N-free pieces are the
+    strings of the definition); positions stay offsets into the input strings.
+    """
+    flags, off, _ = junction_flags(seqs, k, both_strands, split_n)
     return _split(flags, off)
 
 
-def alg1_exact(seqs, k: int, both_strands: bool = True, marks=None) -> List[np.ndarray]:
+def alg1_exact(seqs, k: int, both_strands: bool = True, marks=None,
+               split_n: bool = False) -> List[np.ndarray]:
     """Algorithm 1 with an exact (k+1)-mer set; all positions marked unless given."""
     buf, off = _prep(seqs)
     m = int(off[-1])
@@ -105,19 +112,20 @@ def alg1_exact(seqs, k: int, both_strands: bool = True, marks=None) -> List[np.n
     if marks.size == 0:
         marks = np.zeros(1, np.uint8)
     _check(lib().oracle_alg1_exact(buf.ctypes.data, off.ctypes.data, off.size - 1, k,
-                                   int(both_strands), marks.ctypes.data))
+                                   int(both_strands), int(split_n), marks.ctypes.data))
     return _split(marks[:m], off)
 
 
 def pass1_marks(seqs, k: int, filter_bits: int, hashes: int, both_strands: bool = True,
-                q: int = 1, bin_lo: int = 0, bin_hi: int = 1) -> Tuple[np.ndarray, np.ndarray, int, int]:
+                q: int = 1, bin_lo: int = 0, bin_hi: int = 1,
+                split_n: bool = False) -> Tuple[np.ndarray, np.ndarray, int, int]:
     """First pass with the split-block filter: (marks per byte, offsets, active, kept)."""
     buf, off = _prep(seqs)
     m = int(off[-1])
     marks = np.zeros(max(m, 1), np.uint8)
     cnt = np.zeros(2, np.uint64)
     _check(lib().oracle_pass1(buf.ctypes.data, off.ctypes.data, off.size - 1, k,
-                              int(both_strands), filter_bits, hashes, q, bin_lo, bin_hi,
+                              int(both_strands), int(split_n), filter_bits, hashes, q, bin_lo, bin_hi,
                               marks.ctypes.data, cnt.ctypes.data))
     return marks[:m], off, int(cnt[0]), int(cnt[1])
 
@@ -130,14 +138,14 @@ def partition_cuts(counts: Sequence[int], rounds: int) -> np.ndarray:
     return cuts
 
 
-def edges(seqs, k: int, both_strands: bool = True):
+def edges(seqs, k: int, both_strands: bool = True, split_n: bool = False):
     """Compacted-graph edges by consecutive junction positions, as a dict of arrays.
 
     Keys: from_hi, from_lo, to_hi, to_lo (normalized k-mers), from_rc, to_rc,
     start, length (per edge, string order then position order) and
     per_string (edge count of every string).
     """
-    flags, off, _ = junction_flags(seqs, k, both_strands)
+    flags, off, _ = junction_flags(seqs, k, both_strands, split_n)
     buf, off = _prep(seqs)
     nj = max(int(flags.sum()), 1)
     out = {name: np.zeros(nj, np.uint64) for name in ("from_hi", "from_lo", "to_hi", "to_lo",
@@ -147,7 +155,7 @@ def edges(seqs, k: int, both_strands: bool = True):
     per = np.zeros(max(off.size - 1, 1), np.uint64)
     fl = np.ascontiguousarray(flags if flags.size else np.zeros(1, np.uint8))
     e = lib().oracle_edges(buf.ctypes.data, off.ctypes.data, off.size - 1, k, int(both_strands),
-                           fl.ctypes.data, out["from_hi"].ctypes.data, out["from_lo"].ctypes.data,
+                           int(split_n), fl.ctypes.data, out["from_hi"].ctypes.data, out["from_lo"].ctypes.data,
                            out["to_hi"].ctypes.data, out["to_lo"].ctypes.data,
                            out["from_rc"].ctypes.data, out["to_rc"].ctypes.data,
                            out["start"].ctypes.data, out["length"].ctypes.data, per.ctypes.data)

@@ -51,6 +51,14 @@
  *   first base most significant, so integer order is lexicographic order and
  *   the complement of base x is 3 - x. Positions are 0-based k-mer starts:
  *   i in [0, |s| - k]. Strings are never joined.
+ *
+ * N handling (split_n): the paper does not say what happens to an N. With
+ * split_n = 1 every N (either case) ends its string there: the maximal
+ * N-free pieces of each string are the strings of the definition (so the
+ * first and last k-mers of every piece are sentinels, and no k-mer or edge
+ * contains an N), while positions stay 0-based offsets into the original
+ * string. With split_n = 0 an N is an invalid byte like any other.
+ * PINNED by the tests against the brute-force compactor run on the pieces.
  */
 #include <cstdint>
 #include <cstring>
@@ -63,13 +71,15 @@ typedef unsigned __int128 u128;
 namespace {
 
 enum { ORACLE_OK = 0, ORACLE_EINVAL = -1, ORACLE_EBADBASE = -2 };
+constexpr uint8_t kCodeN = 4;
 
-int base_code(uint8_t c) {
+int base_code(uint8_t c, int split_n) {
   switch (c) {
     case 'A': case 'a': return 0;
     case 'C': case 'c': return 1;
     case 'G': case 'g': return 2;
     case 'T': case 't': return 3;
+    case 'N': case 'n': return split_n ? kCodeN : -1;
     default: return -1;
   }
 }
@@ -105,14 +115,39 @@ u128 normalized(u128 x, int len, int both_strands) {
   return r < x ? r : x;
 }
 
-int encode_all(const uint8_t* seq, uint64_t m, std::vector<uint8_t>* codes) {
+int encode_all(const uint8_t* seq, uint64_t m, int split_n, std::vector<uint8_t>* codes) {
   codes->resize(m);
   for (uint64_t g = 0; g < m; ++g) {
-    int c = base_code(seq[g]);
+    int c = base_code(seq[g], split_n);
     if (c < 0) return ORACLE_EBADBASE;
     (*codes)[g] = (uint8_t)c;
   }
   return ORACLE_OK;
+}
+
+// The strings of the definition: every input string, or with split_n its
+// maximal N-free pieces. s0 is the piece's first global byte, len its length,
+// string the input string it lies in.
+struct Piece {
+  uint64_t s0, len, string;
+};
+
+std::vector<Piece> pieces(const uint64_t* offsets, uint64_t n, const std::vector<uint8_t>& codes) {
+  std::vector<Piece> out;
+  for (uint64_t t = 0; t < n; ++t) {
+    uint64_t g = offsets[t];
+    while (g < offsets[t + 1]) {
+      if (codes[g] == kCodeN) {
+        ++g;
+        continue;
+      }
+      const uint64_t a = g;
+      while (g < offsets[t + 1] && codes[g] != kCodeN) ++g;
+      out.push_back({a, g - a, t});
+    }
+    if (offsets[t] == offsets[t + 1]) out.push_back({offsets[t], 0, t});
+  }
+  return out;
 }
 
 int popcount4(uint8_t x) { return (x & 1) + ((x >> 1) & 1) + ((x >> 2) & 1) + ((x >> 3) & 1); }
@@ -136,20 +171,21 @@ extern "C" {
  *   n_distinct  optional: number of distinct (normalized) k-mers
  */
 int oracle_junctions(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
-                     int both_strands, uint8_t* flags, uint64_t* n_distinct) {
+                     int both_strands, int split_n, uint8_t* flags, uint64_t* n_distinct) {
   if (k < 1 || k > 63) return ORACLE_EINVAL;
   const uint64_t m = offsets[n];
   std::vector<uint8_t> codes;
-  int rc = encode_all(seq, m, &codes);
+  int rc = encode_all(seq, m, split_n, &codes);
   if (rc) return rc;
   std::memset(flags, 0, m);
+  const std::vector<Piece> S = pieces(offsets, n, codes);
 
   // Step 1-2: every occurrence contributes the edges that enter and leave
   // its k-mer, in the orientation of the normalized form.
   std::unordered_map<u128, Degrees, KmerHash> deg;
   std::unordered_set<u128, KmerHash> sentinels;
-  for (uint64_t t = 0; t < n; ++t) {
-    const uint64_t s0 = offsets[t], len = offsets[t + 1] - offsets[t];
+  for (const Piece& pc : S) {
+    const uint64_t s0 = pc.s0, len = pc.len;
     if (len < (uint64_t)k) continue;
     for (uint64_t i = 0; i + k <= len; ++i) {
       u128 v = word_at(codes, s0 + i, k);
@@ -171,8 +207,8 @@ int oracle_junctions(const uint8_t* seq, const uint64_t* offsets, uint64_t n, in
     sentinels.insert(normalized(word_at(codes, s0 + len - k, k), k, both_strands));
   }
   // Step 4: junction = sentinel or bifurcation.
-  for (uint64_t t = 0; t < n; ++t) {
-    const uint64_t s0 = offsets[t], len = offsets[t + 1] - offsets[t];
+  for (const Piece& pc : S) {
+    const uint64_t s0 = pc.s0, len = pc.len;
     if (len < (uint64_t)k) continue;
     for (uint64_t i = 0; i + k <= len; ++i) {
       u128 key = normalized(word_at(codes, s0 + i, k), k, both_strands);
@@ -193,22 +229,23 @@ int oracle_junctions(const uint8_t* seq, const uint64_t* offsets, uint64_t n, in
  * The sentinel test is on the k-mer, not the position.
  */
 int oracle_alg1_exact(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
-                      int both_strands, uint8_t* marks) {
+                      int both_strands, int split_n, uint8_t* marks) {
   if (k < 1 || k > 63) return ORACLE_EINVAL;
   const uint64_t m = offsets[n];
   std::vector<uint8_t> codes;
-  int rc = encode_all(seq, m, &codes);
+  int rc = encode_all(seq, m, split_n, &codes);
   if (rc) return rc;
+  const std::vector<Piece> S = pieces(offsets, n, codes);
   std::unordered_set<u128, KmerHash> E, sentinels;
-  for (uint64_t t = 0; t < n; ++t) {
-    const uint64_t s0 = offsets[t], len = offsets[t + 1] - offsets[t];
+  for (const Piece& pc : S) {
+    const uint64_t s0 = pc.s0, len = pc.len;
     if (len < (uint64_t)k) continue;
     sentinels.insert(normalized(word_at(codes, s0, k), k, both_strands));
     sentinels.insert(normalized(word_at(codes, s0 + len - k, k), k, both_strands));
   }
   // Loop 1: insert the two (k+1)-mers that contain the k-mer at i.
-  for (uint64_t t = 0; t < n; ++t) {
-    const uint64_t s0 = offsets[t], len = offsets[t + 1] - offsets[t];
+  for (const Piece& pc : S) {
+    const uint64_t s0 = pc.s0, len = pc.len;
     for (uint64_t i = 1; i + k < len; ++i) {
       if (!marks[s0 + i]) continue;
       E.insert(normalized(word_at(codes, s0 + i, k + 1), k + 1, both_strands));
@@ -216,8 +253,8 @@ int oracle_alg1_exact(const uint8_t* seq, const uint64_t* offsets, uint64_t n, i
     }
   }
   // Loop 2: count existing edges around every marked non-sentinel k-mer.
-  for (uint64_t t = 0; t < n; ++t) {
-    const uint64_t s0 = offsets[t], len = offsets[t + 1] - offsets[t];
+  for (const Piece& pc : S) {
+    const uint64_t s0 = pc.s0, len = pc.len;
     for (uint64_t i = 1; i + k < len; ++i) {
       if (!marks[s0 + i]) continue;
       u128 v = word_at(codes, s0 + i, k);
@@ -256,7 +293,8 @@ int oracle_alg1_exact(const uint8_t* seq, const uint64_t* offsets, uint64_t n, i
  *   round class: bin = H & (q - 1); a position is active iff its bin is in
  *          [bin_lo, bin_hi).
  *   Loop 1: every active position inserts item 16 if it is the first or
- *          last k-mer of its string, else its pair item(s).
+ *          last k-mer of its string (of its N-free piece under split_n),
+ *          else its pair item(s).
  *   Loop 2: an active position stays marked iff it is a sentinel position,
  *          or item 16 is present, or at least two pair items are present.
  * ------------------------------------------------------------------------- */
@@ -311,24 +349,25 @@ bool filter_has(const std::vector<uint32_t>& F, const FilterSpot& f, int h, int 
  * surviving positions.
  */
 int oracle_pass1(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
-                 int both_strands, uint64_t filter_bits, int hashes, uint64_t q,
+                 int both_strands, int split_n, uint64_t filter_bits, int hashes, uint64_t q,
                  uint64_t bin_lo, uint64_t bin_hi, uint8_t* marks, uint64_t* counters) {
   if (k < 1 || k > 63 || hashes < 1 || hashes > 8) return ORACLE_EINVAL;
   if (filter_bits < 256 || (filter_bits & (filter_bits - 1))) return ORACLE_EINVAL;
   if (q < 1 || (q & (q - 1))) return ORACLE_EINVAL;
   const uint64_t m = offsets[n];
   std::vector<uint8_t> codes;
-  int rc = encode_all(seq, m, &codes);
+  int rc = encode_all(seq, m, split_n, &codes);
   if (rc) return rc;
   std::memset(marks, 0, m);
+  const std::vector<Piece> S = pieces(offsets, n, codes);
   int lg_blocks = 0;
   while ((256ull << lg_blocks) < filter_bits) ++lg_blocks;
   std::vector<uint32_t> F(filter_bits / 32, 0u);
   uint64_t active = 0, kept = 0;
 
   for (int loop = 1; loop <= 2; ++loop) {
-    for (uint64_t t = 0; t < n; ++t) {
-      const uint64_t s0 = offsets[t], len = offsets[t + 1] - offsets[t];
+    for (const Piece& pc : S) {
+      const uint64_t s0 = pc.s0, len = pc.len;
       if (len < (uint64_t)k) continue;
       for (uint64_t i = 0; i + k <= len; ++i) {
         u128 v = word_at(codes, s0 + i, k);
@@ -380,18 +419,19 @@ int oracle_pass1(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
  * negative error. The arrays hold at least (number of junctions) entries.
  */
 long long oracle_edges(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
-                       int both_strands, const uint8_t* flags, uint64_t* from_hi, uint64_t* from_lo,
-                       uint64_t* to_hi, uint64_t* to_lo, uint8_t* from_rc, uint8_t* to_rc,
-                       uint64_t* start, uint64_t* length, uint64_t* edges_per_string) {
+                       int both_strands, int split_n, const uint8_t* flags, uint64_t* from_hi,
+                       uint64_t* from_lo, uint64_t* to_hi, uint64_t* to_lo, uint8_t* from_rc,
+                       uint8_t* to_rc, uint64_t* start, uint64_t* length, uint64_t* edges_per_string) {
   if (k < 1 || k > 63) return ORACLE_EINVAL;
   const uint64_t m = offsets[n];
   std::vector<uint8_t> codes;
-  int rc = encode_all(seq, m, &codes);
+  int rc = encode_all(seq, m, split_n, &codes);
   if (rc) return rc;
+  if (edges_per_string)
+    for (uint64_t t = 0; t < n; ++t) edges_per_string[t] = 0;
   long long e = 0;
-  for (uint64_t t = 0; t < n; ++t) {
-    const uint64_t s0 = offsets[t], len = offsets[t + 1] - offsets[t];
-    long long before = e;
+  for (const Piece& pc : pieces(offsets, n, codes)) {
+    const uint64_t s0 = pc.s0, len = pc.len, t = pc.string;
     bool have_prev = false;
     uint64_t prev = 0;
     for (uint64_t i = 0; i + k <= len && len >= (uint64_t)k; ++i) {
@@ -405,14 +445,14 @@ long long oracle_edges(const uint8_t* seq, const uint64_t* offsets, uint64_t n, 
         to_lo[e] = (uint64_t)nb;
         from_rc[e] = (na != a) ? 1 : 0;
         to_rc[e] = (nb != b) ? 1 : 0;
-        start[e] = prev;
+        start[e] = s0 + prev - offsets[t];  // offset in the input string
         length[e] = i - prev;
         ++e;
+        if (edges_per_string) ++edges_per_string[t];
       }
       have_prev = true;
       prev = i;
     }
-    if (edges_per_string) edges_per_string[t] = (uint64_t)(e - before);
   }
   return e;
 }

@@ -291,3 +291,122 @@ def test_edges_fig1():
     assert [_kmer_str(0, x, 2) for x in e["from_lo"]] == ["TG", "AC", "TG", "AC"]
     assert [_kmer_str(0, x, 2) for x in e["to_lo"]] == ["AC", "TC", "AC", "TC"]
     assert list(e["length"]) == [4, 3, 4, 3]
+
+
+# --- N handling: an N ends its string there (the paper is silent on N) ---------------
+
+def _pieces(s):
+    """(offset, piece) of the maximal N-free pieces of s, split in plain Python."""
+    out, i = [], 0
+    while i < len(s):
+        if s[i] in "Nn":
+            i += 1
+            continue
+        j = i
+        while j < len(s) and s[j] not in "Nn":
+            j += 1
+        out.append((i, s[i:j]))
+        i = j
+    return out
+
+
+def _brute_split(seqs, k, both):
+    pcs = [(t, o, p.upper()) for t, s in enumerate(seqs) for o, p in _pieces(s)]
+    per = brute.junction_positions([p for _, _, p in pcs], k, both)
+    got = [[] for _ in seqs]
+    for (t, o, _), js in zip(pcs, per):
+        got[t] += [o + j for j in js]
+    return [sorted(x) for x in got]
+
+
+def _with_ns(rng, s, k):
+    """s with N runs of lengths 1 .. 2k+2 planted at random places (and at the ends)."""
+    s = list(s)
+    for _ in range(int(rng.integers(0, 5))):
+        a = int(rng.integers(0, len(s) + 1))
+        s[a:a] = "N" * int(rng.integers(1, 2 * k + 3))
+    if rng.integers(0, 3) == 0:
+        s = list("n" * int(rng.integers(1, 4))) + s
+    if rng.integers(0, 3) == 0:
+        s += list("N" * int(rng.integers(1, 4)))
+    return "".join(s)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 7, 8, 15, 25, 31, 63])
+@pytest.mark.parametrize("both", [False, True])
+def test_split_n_matches_brute_force_on_pieces(k, both):
+    rng = np.random.default_rng(4242 + k + 1000 * both)
+    for alpha in (b"ACGT", b"AC"):
+        base = [bytes(s).decode() for s in G.random_strings(int(rng.integers(1 << 30)), 4, k,
+                                                            3 * k + 60, alpha)]
+        base.append(brute.revcomp(base[0]))
+        seqs = [_with_ns(rng, s, k) for s in base]
+        seqs.append("N" * (k + 3))
+        seqs.append("")
+        got = _as_lists(O.junctions(seqs, k, both_strands=both, split_n=True))
+        assert got == _brute_split(seqs, k, both)
+
+
+def test_split_n_special_cases():
+    k = 3
+    seqs = ["ACGTNACGT", "NNNN", "NACGTN", "ACNGT", "ACGNNNNNNNNTTA", "acgtnacg"]
+    got = _as_lists(O.junctions(seqs, k, split_n=True))
+    assert got == _brute_split(seqs, k, True)
+    assert got[1] == [] and got[3] == []        # only N, or pieces shorter than k
+    assert got[2] == [1, 2]                     # ACGT between two N: both 3-mers are sentinels
+    # a k-mer next to an N is a sentinel even in the middle of a string
+    assert 0 in got[0] and 1 in got[0] and 5 in got[0] and 6 in got[0]
+
+
+def test_n_is_an_error_without_split():
+    with pytest.raises(O.OracleError):
+        O.junctions(["ACGTNACGT"], 3)
+    with pytest.raises(O.OracleError):
+        O.junctions(["ACGTRACGT"], 3, split_n=True)  # only N splits
+
+
+def test_split_n_without_n_changes_nothing():
+    seqs = [bytes(s).decode() for s in G.random_strings(77, 5, 30, 300, b"ACGT")]
+    for k in (4, 25):
+        assert _as_lists(O.junctions(seqs, k, split_n=True)) == _as_lists(O.junctions(seqs, k))
+        a = O.edges(seqs, k, split_n=True)
+        b = O.edges(seqs, k)
+        assert all(np.array_equal(a[x], b[x]) for x in a)
+
+
+@pytest.mark.parametrize("k,both", [(3, True), (5, False), (25, True)])
+def test_split_n_edges_are_the_pieces_edges(k, both):
+    """Edges never cross an N: they are the edges of the pieces, in string order."""
+    rng = np.random.default_rng(99 + k)
+    base = [bytes(s).decode() for s in G.random_strings(500 + k, 4, 2 * k, 5 * k + 80, b"ACG")]
+    seqs = [_with_ns(rng, s, k) for s in base]
+    e = O.edges(seqs, k, both_strands=both, split_n=True)
+    pcs = [(t, o, p) for t, s in enumerate(seqs) for o, p in _pieces(s)]
+    pe = O.edges([p for _, _, p in pcs], k, both_strands=both)
+    # the pieces' edges, shifted to string offsets, in the same order
+    assert np.array_equal(e["length"], pe["length"])
+    shift = np.concatenate([np.full(int(pe["per_string"][i]), o, np.uint64)
+                            for i, (_, o, _) in enumerate(pcs)]) if pe["start"].size else pe["start"]
+    assert np.array_equal(e["start"], pe["start"] + shift)
+    for x in ("from_hi", "from_lo", "to_hi", "to_lo", "from_rc", "to_rc"):
+        assert np.array_equal(e[x], pe[x])
+    per = np.zeros(len(seqs), np.uint64)
+    for i, (t, _, _) in enumerate(pcs):
+        per[t] += pe["per_string"][i]
+    assert np.array_equal(e["per_string"], per)
+    # and the pieces' edges are pinned against the explicit graph
+    assert brute.compacted_paths([p for _, _, p in pcs], k, both) is not None
+
+
+def test_split_n_pass1_contains_junctions():
+    rng = np.random.default_rng(5)
+    base = [bytes(s).decode() for s in G.random_strings(8, 6, 100, 400, b"ACGT")]
+    seqs = [_with_ns(rng, s, 25) for s in base]
+    want = O.junction_flags(seqs, 25, split_n=True)[0]
+    for bits, h in ((1 << 10, 2), (1 << 20, 4)):
+        marks, _, active, kept = O.pass1_marks(seqs, 25, bits, h, split_n=True)
+        assert np.all(marks >= want)
+        assert active == sum(max(0, len(p) - 24) for s in seqs for _, p in _pieces(s))
+    # a sparse filter is exact: marks equal the junctions
+    marks, _, _, _ = O.pass1_marks(seqs, 25, 1 << 30, 8, split_n=True)
+    assert np.array_equal(marks, want)
