@@ -21,6 +21,12 @@
  * Conventions for every entry point:
  *   - Input bytes are A, C, G, T in either case; any other byte is an error
  *     (TWOPACO_EBADBASE). Strings are never joined: no k-mer spans two strings.
+ *   - With options->split_at_n, N (either case) is also accepted and ends its
+ *     string there: the paper does not say how N is handled, and this library
+ *     reads it as splitting the string, so that the maximal N-free pieces are
+ *     the strings of the definition -- no k-mer, edge or junction contains an
+ *     N, and the first and last k-mers of every piece are sentinels. Positions
+ *     stay 0-based offsets into the input string.
  *   - Positions are 0-based k-mer starts i in [0, |s| - k]; a string shorter
  *     than k has none.
  *   - Return value: TWOPACO_OK (0) or a negative TWOPACO_E* code.
@@ -61,6 +67,14 @@ typedef struct twopaco_options {
                                  at most 2^32 bases. A round with more candidates
                                  stays correct but slower. */
   void* cuda_stream;       /* cudaStream_t to launch on, borrowed; NULL = default */
+  int split_at_n;          /* 1: an N ends its string (see above); 0 (default): N is
+                              an invalid byte */
+  uint64_t run_capacity;   /* split_at_n only: room for the boundaries of the
+                              N-free pieces and N runs (one per string start and
+                              one per N/base change inside a string); 0 =
+                              automatic (n_seqs + 1 + total_bases / 64). A run with
+                              more boundaries reports TWOPACO_EOVERFLOW; the host
+                              builds count them exactly. */
 } twopaco_options;
 
 /* Counters of one run, in the spirit of Table 4 (marks after each pass). */

@@ -45,6 +45,7 @@ int validate(uint64_t n_seqs, int k, uint64_t filter_bits, int rounds, const two
   if (!is_pow2(o.partition_bins) || o.partition_bins < (uint32_t)rounds) return TWOPACO_EINVAL;
   if (rounds > 1 && o.partition_bins < 2) return TWOPACO_EINVAL;
   if (n_seqs >= (1ull << 32)) return TWOPACO_EINVAL;
+  if (o.split_at_n != 0 && o.split_at_n != 1) return TWOPACO_EINVAL;
   return TWOPACO_OK;
 }
 
@@ -54,8 +55,9 @@ int validate_size(uint64_t total_bases) {
 
 struct Layout {
   uint64_t header, packed, filter, ctemp, cfinal, tile_count, tile_prefix, bins, cuts, table;
-  uint64_t cands, lc, segs, desc, cslot;
-  int use_desc, use_slot;
+  uint64_t cands, lc, segs, desc, cslot, nmask, bounds, chunks, runs, rank;
+  int use_desc, use_slot, split;
+  uint64_t n_chunks, run_cap;
   uint64_t total;
   uint64_t packed_words, bitmap_words, n_tiles, table_slots, cand_cap;
   int lc_log2;
@@ -68,7 +70,10 @@ uint64_t auto_table_slots(uint64_t m, int rounds) {
   return next_pow2(want);
 }
 
-Layout layout(uint64_t m, int k, uint64_t filter_bits, int rounds, const twopaco_options& o) {
+uint64_t auto_run_capacity(uint64_t m, uint64_t n_seqs) { return n_seqs + 1 + m / 64; }
+
+Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int rounds,
+              const twopaco_options& o) {
   Layout L{};
   L.packed_words = (m + 15) / 16 + kPackPadWords;
   L.bitmap_words = (m + 31) / 32;
@@ -120,6 +125,23 @@ Layout layout(uint64_t m, int k, uint64_t filter_bits, int rounds, const twopaco
   L.use_desc = (m < (1ull << 31) && o.hashes <= 6 && filter_bits <= (1ull << 37)) ? 1 : 0;
   L.desc = at;
   if (L.use_desc) at += align_up((m + 16) * 8);
+  // N splitting: N mask and boundary bitmap (one bit per base), per-chunk
+  // boundary counts, the sorted boundaries and their ranks
+  L.split = o.split_at_n;
+  L.n_chunks = (L.bitmap_words + kRunChunkWords - 1) / kRunChunkWords;
+  L.run_cap = o.run_capacity ? o.run_capacity : auto_run_capacity(m, n_seqs);
+  L.nmask = L.bounds = L.chunks = L.runs = L.rank = at;
+  if (L.split) {
+    at += align_up((L.bitmap_words + 8) * 4);
+    L.bounds = at;
+    at += align_up((L.bitmap_words + 8) * 4);
+    L.chunks = at;
+    at += align_up((L.n_chunks + 1) * 8);
+    L.runs = at;
+    at += align_up((L.run_cap + 1) * 8);
+    L.rank = at;
+    at += align_up((L.run_cap + 1) * 4);
+  }
   L.total = at;
   return L;
 }
@@ -155,6 +177,15 @@ RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_
   v.use_desc = L.use_desc;
   v.cand_slot = L.use_slot ? reinterpret_cast<uint32_t*>(base + L.cslot) : nullptr;
   v.desc = reinterpret_cast<uint64_t*>(base + L.desc);
+  if (L.split) {
+    v.nmask = reinterpret_cast<uint32_t*>(base + L.nmask);
+    v.bound_bits = reinterpret_cast<uint32_t*>(base + L.bounds);
+    v.chunk_counts = reinterpret_cast<uint64_t*>(base + L.chunks);
+    v.n_chunks = L.n_chunks;
+    v.runs = reinterpret_cast<uint64_t*>(base + L.runs);
+    v.run_rank = reinterpret_cast<uint32_t*>(base + L.rank);
+    v.run_cap = L.run_cap;
+  }
   v.cand_cap = L.cand_cap;
   v.lc_bits = reinterpret_cast<uint32_t*>(base + L.lc);
   v.lc_log2 = L.lc_log2;
@@ -168,6 +199,23 @@ RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_
   v.out_positions = d_out_positions;
   v.out_capacity = out_capacity;
   return v;
+}
+
+// Boundaries of the N-free pieces and N runs of host strings: one per
+// non-empty string plus one per change between N and a base inside a string.
+uint64_t count_run_boundaries(const char* const* seqs, const uint64_t* lengths, uint64_t n) {
+  uint64_t r = 0;
+  for (uint64_t t = 0; t < n; ++t) {
+    if (!lengths[t]) continue;
+    ++r;
+    bool prev_n = (seqs[t][0] | 0x20) == 'n';
+    for (uint64_t i = 1; i < lengths[t]; ++i) {
+      const bool is_n = (seqs[t][i] | 0x20) == 'n';
+      r += is_n != prev_n;
+      prev_n = is_n;
+    }
+  }
+  return r;
 }
 
 int cuda_code(cudaError_t e) {
@@ -191,17 +239,19 @@ void twopaco_default_options(twopaco_options* opt) {
   opt->table_slots = 0;
   opt->candidate_records = 0;
   opt->cuda_stream = nullptr;
+  opt->split_at_n = 0;
+  opt->run_capacity = 0;
 }
 
 const char* twopaco_strerror(int code) {
   switch (code) {
     case TWOPACO_OK: return "ok";
     case TWOPACO_EINVAL: return "invalid argument";
-    case TWOPACO_EBADBASE: return "input byte is not one of ACGTacgt";
+    case TWOPACO_EBADBASE: return "input byte is not one of ACGTacgt (or Nn with split_at_n)";
     case TWOPACO_ENOMEM: return "out of memory";
     case TWOPACO_ETIMEOUT: return "a bounded device wait gave up";
     case TWOPACO_ECUDA: return "CUDA error";
-    case TWOPACO_EOVERFLOW: return "pass-2 table or output buffer too small";
+    case TWOPACO_EOVERFLOW: return "pass-2 table, output buffer or run boundary list too small";
     case TWOPACO_ESCRATCH: return "run needs more than the no-alloc scratch buffer holds";
     default: return "unknown error";
   }
@@ -213,7 +263,7 @@ int twopaco_workspace_size(uint64_t total_bases, uint64_t n_seqs, int k, uint64_
   int rc = validate(n_seqs, k, filter_bits, rounds, o);
   if (rc) return rc;
   if (!bytes || validate_size(total_bases)) return TWOPACO_EINVAL;
-  *bytes = layout(total_bases, k, filter_bits, rounds, o).total;
+  *bytes = layout(total_bases, n_seqs, k, filter_bits, rounds, o).total;
   return TWOPACO_OK;
 }
 
@@ -229,7 +279,7 @@ int twopaco_run_device(const uint8_t* d_bases, const uint64_t* d_offsets, uint64
   if (n_seqs > 0 && !d_offsets) return TWOPACO_EINVAL;
   if (!d_out_offsets || (out_capacity && !d_out_positions)) return TWOPACO_EINVAL;
   if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) % kAlign)) return TWOPACO_EINVAL;
-  const Layout L = layout(total_bases, k, filter_bits, rounds, o);
+  const Layout L = layout(total_bases, n_seqs, k, filter_bits, rounds, o);
   if (workspace_bytes < L.total) return TWOPACO_EINVAL;
   const RunView v = make_view(d_bases, d_offsets, n_seqs, total_bases, k, filter_bits, rounds, o, L,
                               d_workspace, d_out_offsets, d_out_positions, out_capacity);
@@ -329,6 +379,7 @@ int twopaco_build_ex(const char* const* seqs, const uint64_t* lengths, uint64_t 
     if (lengths[t] >= (uint64_t)k) positions += lengths[t] - (uint64_t)k + 1;
   }
   const uint64_t m = offsets[n_seqs];
+  if (o.split_at_n && !o.run_capacity) o.run_capacity = count_run_boundaries(seqs, lengths, n_seqs) + 1;
   cudaStream_t s = static_cast<cudaStream_t>(o.cuda_stream);
 
   uint8_t* d_bases = nullptr;
@@ -372,7 +423,7 @@ int twopaco_build_ex(const char* const* seqs, const uint64_t* lengths, uint64_t 
     rc = twopaco_read_stats(d_ws, o.cuda_stream, &st);
     if (rc != TWOPACO_EOVERFLOW || attempt >= 4) break;
     // The table was too small for this input: grow it and run again.
-    const Layout L = layout(m, k, filter_bits, rounds, o);
+    const Layout L = layout(m, n_seqs, k, filter_bits, rounds, o);
     o.table_slots = L.table_slots * 4;
     cudaFree(d_ws);
     d_ws = nullptr;
@@ -608,6 +659,7 @@ int twopaco_build_ctx(twopaco_context* c, const char* const* seqs, const uint64_
   }
   const uint64_t m = c->h_off[n_seqs];
   if (validate_size(m)) return finish(TWOPACO_EINVAL);
+  if (o.split_at_n && !o.run_capacity) o.run_capacity = count_run_boundaries(seqs, lengths, n_seqs) + 1;
   if ((e = grow_device(&c->d_bases, &c->cap_bases, m)) != cudaSuccess) return finish(cuda_code(e));
   if ((e = grow_device(&c->d_pos, &c->cap_pos, (positions ? positions : 1) * 8)) != cudaSuccess)
     return finish(cuda_code(e));
@@ -631,7 +683,7 @@ int twopaco_build_ctx(twopaco_context* c, const char* const* seqs, const uint64_
     if (e != cudaSuccess) return finish(cuda_code(e));
     rc = twopaco_read_stats(c->d_ws, c->stream, &st);
     if (rc != TWOPACO_EOVERFLOW || attempt >= 4) break;
-    o.table_slots = layout(m, k, filter_bits, rounds, o).table_slots * 4;
+    o.table_slots = layout(m, n_seqs, k, filter_bits, rounds, o).table_slots * 4;
   }
   if (rc) return finish(rc);
   const uint64_t total = c->h_out_off[n_seqs];

@@ -37,6 +37,13 @@ struct DevHeader {
   unsigned long long m;
   int k;
   int both;
+  // N splitting (null / 0 without it): the N mask, the sorted boundaries of
+  // the N-free pieces and N runs, and (after an edge computation) their ranks
+  const uint32_t* nmask;
+  const uint64_t* runs;
+  uint32_t* run_rank;
+  unsigned long long n_runs;
+  unsigned long long run_cap;
 };
 
 // Device view of one run: every buffer lives inside the workspace except the
@@ -65,6 +72,16 @@ struct RunView {
   uint64_t* cands;          // positions of the pass-1 survivors, for pass 2
   int narrow;               // m < 2^31: the list holds 32-bit records
   uint32_t* cand_slot;      // table slot of every listed candidate (null: look it up)
+  // N splitting (nmask null without it): bit g of nmask = base g is N; the
+  // boundary bitmap (string starts and N/base changes), its per-chunk counts,
+  // and the sorted boundaries runs[0 .. n_runs] (runs[n_runs] = m)
+  uint32_t* nmask;
+  uint32_t* bound_bits;
+  uint64_t* chunk_counts;
+  uint64_t n_chunks;
+  uint64_t* runs;
+  uint32_t* run_rank;
+  uint64_t run_cap;
   uint64_t* desc;           // per-position probe descriptors (use_desc), m + 16 entries
   int use_desc;             // the insert leaves descriptors and the probe reads them
   uint64_t cand_cap;        // records the list can hold
@@ -88,6 +105,7 @@ constexpr int kEmitWordsPerThread = 16;
 constexpr int kEmitTileWords = kBlock * kEmitWordsPerThread;  // bitmap words per emit tile
 constexpr uint64_t kPackPadWords = 8;   // zero words after the packed input
 constexpr uint32_t kMaxSegments = 65536; // candidate-list segments (probe warps) at most
+constexpr uint64_t kRunChunkWords = 1024;  // boundary-bitmap words per compaction chunk
 
 // Kernel launch helpers (twopaco_kernels.cu). Each returns the number of
 // kernels it launched, or -1 after a launch error.

@@ -216,6 +216,22 @@ __device__ __forceinline__ Bounds seq_bounds(const RunView& v, uint64_t g) {
   return {__ldg(v.offsets + lo), __ldg(v.offsets + lo + 1)};
 }
 
+// The string bounds a k-mer at g must lie in. Without N splitting these are
+// the input string's; with it, the N-free piece holding g, or the empty
+// range [g, g) when base g is N (no k-mer starts there, and the next
+// position looks its bounds up again).
+__device__ __forceinline__ Bounds kmer_bounds(const RunView& v, uint64_t g) {
+  if (!v.nmask) return seq_bounds(v, g);
+  if ((__ldg(v.nmask + (g >> 5)) >> (g & 31)) & 1u) return {g, g};
+  const uint64_t n = __ldcg(&v.hdr->n_runs);  // runs[n] = m
+  uint64_t lo = 0, hi = n;                    // largest j < n with runs[j] <= g
+  while (hi - lo > 1) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (__ldg(v.runs + mid) <= g) lo = mid; else hi = mid;
+  }
+  return {__ldg(v.runs + lo), __ldg(v.runs + lo + 1)};
+}
+
 // One k-mer occurrence, read in the orientation of its normalized form.
 struct Occ {
   Key key;         // normalized k-mer
@@ -256,7 +272,7 @@ __device__ __forceinline__ void make_occ(const RunView& v, const Key& f, const K
 // starts at g.
 template <int KW>
 __device__ __forceinline__ bool read_occurrence(const RunView& v, uint64_t g, Occ* oc) {
-  const Bounds b = seq_bounds(v, g);
+  const Bounds b = kmer_bounds(v, g);
   if (g + (uint64_t)v.k > b.end) return false;
   const Key f = load_kmer<KW>(v.packed, g, v.k);
   const bool has_pred = g > b.start, has_succ = g + (uint64_t)v.k < b.end;
@@ -295,7 +311,7 @@ template <int KW, int R, typename F>
 __device__ __forceinline__ void walk(const RunView& v, uint64_t p0, F&& fn) {
   static_assert(R >= 1 && R <= 16, "successor bases come from one 32-bit word");
   const int k = v.k;
-  Bounds b = seq_bounds(v, p0);
+  Bounds b = kmer_bounds(v, p0);
   int32_t s_rel = rel(b.start, p0), e_rel = rel(b.end, p0);  // string bounds relative to p0
   const int32_t m_rel = rel(v.m, p0);
   // bases p0 + k .. p0 + k + R - 1: the successor of each position, which is
@@ -309,8 +325,8 @@ __device__ __forceinline__ void walk(const RunView& v, uint64_t p0, F&& fn) {
     Occ oc;
     bool valid = false;
     if (i < m_rel) {
-      if (i >= e_rel) {  // p starts a later string
-        b = seq_bounds(v, p);
+      if (i >= e_rel) {  // p starts a later string (or piece)
+        b = kmer_bounds(v, p);
         s_rel = rel(b.start, p0);
         e_rel = rel(b.end, p0);
         fresh = true;
@@ -584,39 +600,56 @@ __device__ __forceinline__ void block_add(unsigned long long x, unsigned long lo
 
 // Four ASCII bytes -> four 2-bit codes (first byte in bits 7-6); *bad gets
 // 0xFF in every byte that is not one of ACGTacgt.
-__device__ __forceinline__ uint32_t pack4(uint32_t x, uint32_t* bad) {
+__device__ __forceinline__ uint32_t pack4(uint32_t x, uint32_t* bad, uint32_t* is_n) {
   const uint32_t low = x | 0x20202020u;
   const uint32_t ok = __vcmpeq4(low, 0x61616161u) | __vcmpeq4(low, 0x63636363u) |
                       __vcmpeq4(low, 0x67676767u) | __vcmpeq4(low, 0x74747474u);
   *bad = ~ok;
+  *is_n = __vcmpeq4(low, 0x6e6e6e6eu);
   // a=0x61 c=0x63 g=0x67 t=0x74: bits 2-1 are 00 01 11 10; fold to 0 1 2 3
   const uint32_t t = (low >> 1) & 0x03030303u;
   const uint32_t c = t ^ ((t >> 1) & 0x01010101u);
   return ((c & 3u) << 6) | (((c >> 8) & 3u) << 4) | (((c >> 16) & 3u) << 2) | ((c >> 24) & 3u);
 }
 
+// Bit j of the result: byte j of the __vcmpeq4 mask e is set.
+__device__ __forceinline__ uint32_t byte_bits(uint32_t e) {
+  return ((e >> 7) & 1u) | ((e >> 14) & 2u) | ((e >> 21) & 4u) | ((e >> 28) & 8u);
+}
+
 // Sixteen ASCII bytes at g (or fewer at the end of the input) -> one word;
-// *bad_at gets the index of the first invalid byte.
+// *bad_at gets the index of the first invalid byte. With N splitting (v.nmask)
+// an N is valid and *nbits gets bit i for an N at g + i.
 __device__ __forceinline__ uint32_t pack16(const RunView& v, uint64_t g, uint4 q, bool full,
-                                           uint64_t* bad_at) {
-  uint32_t out = 0;
+                                           uint64_t* bad_at, uint32_t* nbits) {
+  uint32_t out = 0, nb = 0;
+  const bool split = v.nmask != nullptr;
   if (full) {
     const uint32_t part[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      uint32_t bad;
-      out |= pack4(part[c], &bad) << (24 - 8 * c);
+      uint32_t bad, is_n;
+      out |= pack4(part[c], &bad, &is_n) << (24 - 8 * c);
+      if (split) {
+        bad &= ~is_n;
+        nb |= byte_bits(is_n) << (4 * c);
+      }
       if (bad && *bad_at == ~0ull) *bad_at = g + 4 * c + (__ffs(bad) - 1) / 8;
     }
   } else if (g < v.m) {
     for (int i = 0; i < 16 && g + i < v.m; ++i) {
       const uint32_t c = v.bases[g + i];
-      uint32_t bad;
-      const uint32_t code = pack4(c | 0x61616100u, &bad) >> 6;  // pad bytes are 'a'
+      uint32_t bad, is_n;
+      const uint32_t code = pack4(c | 0x61616100u, &bad, &is_n) >> 6;  // pad bytes are 'a'
+      if (split && (is_n & 0xFFu)) {
+        bad = 0;
+        nb |= 1u << i;
+      }
       if ((bad & 0xFFu) && *bad_at == ~0ull) *bad_at = g + i;
       out |= code << (30 - 2 * i);
     }
   }
+  *nbits = nb;
   return out;
 }
 
@@ -638,6 +671,10 @@ __global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
     h->m = v.m;
     h->k = v.k;
     h->both = v.both;
+    h->nmask = v.nmask;
+    h->runs = v.runs;
+    h->run_rank = v.run_rank;
+    h->run_cap = v.run_cap;
   }
   const bool vec = (reinterpret_cast<uintptr_t>(v.bases) & 15) == 0;
   const uint64_t stride = (uint64_t)gridDim.x * kBlock * 4;
@@ -651,9 +688,13 @@ __global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
       full[j] = vec && g + 16 <= v.m;
       if (full[j]) q[j] = __ldcs(reinterpret_cast<const uint4*>(v.bases + g));
     }
-    uint32_t out[4];
+    uint32_t out[4], nb[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) out[j] = pack16(v, (w0 + j) * 16, q[j], full[j], &bad_at);
+    for (int j = 0; j < 4; ++j) out[j] = pack16(v, (w0 + j) * 16, q[j], full[j], &bad_at, &nb[j]);
+    if (v.nmask) {  // two packed words per N-mask word (w0 is a multiple of 4)
+      v.nmask[w0 / 2] = nb[0] | (nb[1] << 16);
+      v.nmask[w0 / 2 + 1] = nb[2] | (nb[3] << 16);
+    }
     if (w0 + 4 <= v.packed_words) {
       *reinterpret_cast<uint4*>(v.packed + w0) = make_uint4(out[0], out[1], out[2], out[3]);
     } else {
@@ -671,6 +712,118 @@ __global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
   zero(v.lc_bits, (1ull << v.lc_log2) / 8);
   zero(v.cfinal, (v.bitmap_words + 3) / 4 * 16);
   zero(v.tile_prefix, (v.n_tiles + 1) / 2 * 16);
+}
+
+// ---------------------------------------------------------------------------
+// N splitting: the sorted boundaries of the N-free pieces and of the N runs.
+// Bit g of the boundary bitmap is set iff g starts a string or base g is N
+// and base g - 1 is not, or the other way round, inside one string. The set
+// bits, in order, are runs[0 .. n_runs); runs[n_runs] = m.
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kBlock) runs_mark_kernel(RunView v) {
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+  for (uint64_t w = (uint64_t)blockIdx.x * kBlock + threadIdx.x; w < v.bitmap_words; w += stride) {
+    const uint32_t cur = v.nmask[w], prev = w ? v.nmask[w - 1] : 0u;
+    uint32_t b = cur ^ ((cur << 1) | (prev >> 31));
+    if (w == v.bitmap_words - 1 && (v.m & 31)) b &= (1u << (v.m & 31)) - 1u;
+    v.bound_bits[w] = b;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) runs_starts_kernel(RunView v) {
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+  for (uint64_t t = (uint64_t)blockIdx.x * kBlock + threadIdx.x; t < v.n_seqs; t += stride) {
+    const uint64_t g = __ldg(v.offsets + t);
+    if (g < v.m) atomicOr(v.bound_bits + (g >> 5), 1u << (g & 31));
+  }
+}
+
+// Set bits of every chunk of kRunChunkWords boundary words.
+__global__ void __launch_bounds__(kBlock) runs_count_kernel(RunView v) {
+  __shared__ unsigned long long part[kBlock / 32];
+  for (uint64_t c = blockIdx.x; c < v.n_chunks; c += gridDim.x) {
+    unsigned long long n = 0;
+    for (uint64_t w = c * kRunChunkWords + threadIdx.x; w < (c + 1) * kRunChunkWords && w < v.bitmap_words;
+         w += kBlock)
+      n += __popc(v.bound_bits[w]);
+    n = warp_sum(n);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = n;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long tot = 0;
+      for (int i = 0; i < kBlock / 32; ++i) tot += part[i];
+      v.chunk_counts[c] = tot;
+    }
+    __syncthreads();
+  }
+}
+
+// Exclusive scan of the chunk counts (in place, one block); records the
+// number of boundaries (at most run_cap, else the overflow flag) and closes
+// the list with m.
+__global__ void __launch_bounds__(1024) runs_scan_kernel(RunView v) {
+  __shared__ unsigned long long wsum[32];
+  __shared__ unsigned long long carry_s;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (uint64_t base = 0; base < v.n_chunks; base += 1024) {
+    const uint64_t c = base + threadIdx.x;
+    const unsigned long long x = c < v.n_chunks ? v.chunk_counts[c] : 0ull;
+    unsigned long long inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    unsigned long long before = 0, all = 0;
+    for (int w = 0; w < 32; ++w) {
+      before += (w < wid) ? wsum[w] : 0ull;
+      all += wsum[w];
+    }
+    const unsigned long long c0 = carry_s;
+    if (c < v.n_chunks) v.chunk_counts[c] = c0 + before + inc - x;
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s = c0 + all;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const unsigned long long total = carry_s;
+    const unsigned long long n = total < v.run_cap ? total : v.run_cap;
+    if (total > v.run_cap) v.hdr->overflow = 1;
+    v.hdr->n_runs = n;
+    v.runs[n] = v.m;
+  }
+}
+
+// Positions of the set boundary bits, in order (chunk by chunk).
+__global__ void __launch_bounds__(kBlock) runs_write_kernel(RunView v) {
+  constexpr int kPer = (int)(kRunChunkWords / kBlock);  // consecutive words per thread
+  for (uint64_t c = blockIdx.x; c < v.n_chunks; c += gridDim.x) {
+    const uint64_t w0 = c * kRunChunkWords + (uint64_t)threadIdx.x * kPer;
+    uint32_t words[kPer];
+    uint32_t n = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      words[j] = (w0 + j < v.bitmap_words) ? v.bound_bits[w0 + j] : 0u;
+      n += __popc(words[j]);
+    }
+    uint32_t tot;
+    uint64_t at = v.chunk_counts[c] + block_exclusive_scan(n, &tot);
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      uint32_t bits = words[j];
+      while (bits) {
+        const uint32_t b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        if (at < v.run_cap) v.runs[at] = (w0 + j) * 32 + b;
+        ++at;
+      }
+    }
+  }
 }
 
 // Probe descriptor of a position (64 bits): bit 63 active (probe it), bit 62
@@ -1271,21 +1424,87 @@ struct EdgeOut {  // layout of twopaco_edge
   unsigned int from_rc, to_rc;
 };
 
-// edge_offsets[t] = sum over strings before t of max(junctions - 1, 0).
-__global__ void __launch_bounds__(1024) edge_offsets_kernel(const DevHeader* hdr, const uint64_t* out_off,
-                                                            uint64_t n_seqs, uint64_t* edge_off,
-                                                            uint64_t capacity) {
+// With N splitting no edge crosses an N. Every piece of at least k bases
+// holds a junction (its first k-mer is a sentinel), so a string with j
+// junctions spread over r such pieces has j - r edges: one fewer per piece.
+// run_rank[j] = pieces of at least k bases among runs[0 .. j) (one block).
+__global__ void __launch_bounds__(1024) runs_rank_kernel(const DevHeader* hdr) {
+  __shared__ unsigned int wsum[32];
+  __shared__ unsigned int carry_s;
+  if (!hdr->nmask) return;  // the run did not split at N
+  const uint64_t n = hdr->n_runs;
+  const uint64_t* runs = hdr->runs;
+  const uint32_t* nmask = hdr->nmask;
+  uint32_t* rank = hdr->run_rank;
+  const uint64_t k = (uint64_t)hdr->k;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (uint64_t base = 0; base < n; base += 1024) {
+    const uint64_t j = base + threadIdx.x;
+    unsigned int x = 0;
+    if (j < n) {
+      const uint64_t a = runs[j], b = runs[j + 1];
+      x = (!((nmask[a >> 5] >> (a & 31)) & 1u) && b - a >= k) ? 1u : 0u;
+    }
+    unsigned int inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    unsigned int before = 0, all = 0;
+    for (int w = 0; w < 32; ++w) {
+      before += (w < wid) ? wsum[w] : 0u;
+      all += wsum[w];
+    }
+    const unsigned int c0 = carry_s;
+    if (j < n) rank[j] = c0 + before + inc - x;
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s = c0 + all;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) rank[n] = carry_s;
+}
+
+// First j in [0, n] with runs[j] >= g (runs[n] = m).
+__device__ __forceinline__ uint64_t runs_lower_bound(const uint64_t* runs, uint64_t n, uint64_t g) {
+  uint64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (runs[mid] < g) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Pieces of at least k bases in string t (N splitting).
+__device__ __forceinline__ uint64_t long_pieces(const DevHeader* hdr, const uint64_t* offsets, uint64_t t) {
+  const uint64_t n = hdr->n_runs;
+  const uint64_t lo = runs_lower_bound(hdr->runs, n, offsets[t]);
+  const uint64_t hi = runs_lower_bound(hdr->runs, n, offsets[t + 1]);
+  return (uint64_t)hdr->run_rank[hi] - hdr->run_rank[lo];
+}
+
+// edge_offsets[t] = sum over strings before t of their edges: junctions - 1
+// (none for a string without junctions), or junctions - pieces with N splitting.
+__global__ void __launch_bounds__(1024) edge_offsets_kernel(const DevHeader* hdr, const uint64_t* offsets,
+                                                            const uint64_t* out_off, uint64_t n_seqs,
+                                                            uint64_t* edge_off, uint64_t capacity) {
   __shared__ unsigned long long wsum[32];
   __shared__ unsigned long long carry_s;
   if (threadIdx.x == 0) carry_s = 0;
   __syncthreads();
+  const bool split = hdr->nmask != nullptr;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (uint64_t base = 0; base < n_seqs; base += 1024) {
     const uint64_t t = base + threadIdx.x;
     unsigned long long x = 0;
     if (t < n_seqs) {
       const unsigned long long j = out_off[t + 1] - out_off[t];
-      x = j ? j - 1 : 0;
+      if (split) x = j - long_pieces(hdr, offsets, t);
+      else x = j ? j - 1 : 0;
     }
     unsigned long long inc = x;
 #pragma unroll
@@ -1324,13 +1543,16 @@ __device__ __forceinline__ void edge_vertex(const uint32_t* packed, uint64_t g, 
   *rc = use_r ? 1u : 0u;
 }
 
-// One thread per junction: the edge from it to the next junction of its string.
+// One thread per junction: the edge from it to the next junction of its
+// string (with N splitting: of its piece; the last junction of a piece has
+// none, and the edges of later pieces move down by one per earlier piece).
 __global__ void __launch_bounds__(kBlock) edges_kernel(const DevHeader* hdr, const uint64_t* offsets,
                                                       uint64_t n_seqs, const uint64_t* out_off,
                                                       const uint64_t* out_pos, const uint64_t* edge_off,
                                                       EdgeOut* edges, uint64_t capacity) {
   const uint32_t* packed = hdr->packed;
   const int k = hdr->k, both = hdr->both;
+  const bool split = hdr->nmask != nullptr;
   const uint64_t total = out_off[n_seqs];
   const uint64_t stride = (uint64_t)gridDim.x * kBlock;
   for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < total; i += stride) {
@@ -1342,9 +1564,16 @@ __global__ void __launch_bounds__(kBlock) edges_kernel(const DevHeader* hdr, con
     const uint64_t t = lo;
     const uint64_t a = i - out_off[t];
     if (a + 1 >= out_off[t + 1] - out_off[t]) continue;  // the string's last junction
-    const uint64_t e = edge_off[t] + a;
-    if (e >= capacity) continue;
     const uint64_t p = out_pos[i], q = out_pos[i + 1], g0 = offsets[t];
+    uint64_t e = edge_off[t] + a;
+    if (split) {
+      const uint64_t n = hdr->n_runs;
+      const uint64_t jr = runs_lower_bound(hdr->runs, n, g0 + p + 1) - 1;  // the piece holding p
+      if (hdr->runs[jr + 1] < g0 + q + (uint64_t)k) continue;            // q lies in a later piece
+      const uint64_t first = runs_lower_bound(hdr->runs, n, g0);
+      e -= (uint64_t)hdr->run_rank[jr] - hdr->run_rank[first];
+    }
+    if (e >= capacity) continue;
     EdgeOut o;
     if (k <= 31) {
       edge_vertex<1>(packed, g0 + p, k, both, &o.from_hi, &o.from_lo, &o.from_rc);
@@ -1401,7 +1630,17 @@ int launch_pack(const RunView& v, cudaStream_t s) {
     Timed t("pack", s);
     pack_kernel<<<grid_for(pack_kernel, kBlock, (v.packed_words + 3) / 4), kBlock, 0, s>>>(v);
   }
-  return done(1);
+  if (!v.nmask || v.m == 0) return done(1);
+  {
+    Timed t("runs", s);
+    runs_mark_kernel<<<grid_for(runs_mark_kernel, kBlock, v.bitmap_words), kBlock, 0, s>>>(v);
+    runs_starts_kernel<<<grid_for(runs_starts_kernel, kBlock, v.n_seqs), kBlock, 0, s>>>(v);
+    const unsigned gc = grid_for(runs_count_kernel, kBlock, v.n_chunks * kBlock);
+    runs_count_kernel<<<gc, kBlock, 0, s>>>(v);
+    runs_scan_kernel<<<1, 1024, 0, s>>>(v);
+    runs_write_kernel<<<grid_for(runs_write_kernel, kBlock, v.n_chunks * kBlock), kBlock, 0, s>>>(v);
+  }
+  return done(6);
 }
 
 // Run f with the filter's bits per item as a compile-time constant.
@@ -1530,9 +1769,13 @@ int launch_emit(const RunView& v, cudaStream_t s) {
 int launch_edges(const DevHeader* hdr_dev, const uint64_t* d_offsets, uint64_t n_seqs,
                  const uint64_t* d_out_offsets, const uint64_t* d_out_positions,
                  uint64_t* d_edge_offsets, void* d_edges, uint64_t edge_capacity, cudaStream_t s) {
+  // the piece ranks, when the run split its strings at N (the kernel reads the
+  // header and returns at once otherwise)
   {
     Timed t("edge_offsets", s);
-    edge_offsets_kernel<<<1, 1024, 0, s>>>(hdr_dev, d_out_offsets, n_seqs, d_edge_offsets, edge_capacity);
+    runs_rank_kernel<<<1, 1024, 0, s>>>(hdr_dev);
+    edge_offsets_kernel<<<1, 1024, 0, s>>>(hdr_dev, d_offsets, d_out_offsets, n_seqs, d_edge_offsets,
+                                           edge_capacity);
   }
   {
     Timed t("edges", s);
@@ -1540,7 +1783,7 @@ int launch_edges(const DevHeader* hdr_dev, const uint64_t* d_offsets, uint64_t n
         hdr_dev, d_offsets, n_seqs, d_out_offsets, d_out_positions, d_edge_offsets,
         static_cast<EdgeOut*>(d_edges), edge_capacity);
   }
-  return done(2);
+  return done(3);
 }
 
 }  // namespace twopaco

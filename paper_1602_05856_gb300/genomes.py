@@ -225,3 +225,32 @@ def concat(seqs: Sequence[np.ndarray]) -> Tuple[np.ndarray, np.ndarray]:
     np.cumsum(lens, out=offsets[1:])
     buf = np.concatenate(list(seqs)) if seqs else np.zeros(0, np.uint8)
     return np.ascontiguousarray(buf, dtype=np.uint8), offsets
+
+
+def plant_n_runs(seed: int, seqs: Sequence[np.ndarray], runs_per_mbp: float = 50.0,
+                 max_len: int = 5000, lower_frac: float = 0.1,
+                 ends: bool = True) -> List[np.ndarray]:
+    """Copies of ``seqs`` with runs of N written over them, like assembly gaps.
+
+    Per string about ``runs_per_mbp`` runs per Mbp (at least one), at uniform
+    places, of log-uniform length in [1, max_len]; a ``lower_frac`` share is
+    written as 'n'. With ``ends`` every third string also starts or ends in N.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for t, s in enumerate(seqs):
+        s = np.array(s, dtype=np.uint8, copy=True)
+        if s.size:
+            n_runs = max(1, int(rng.poisson(runs_per_mbp * s.size / 1e6)))
+            for _ in range(n_runs):
+                ln = int(np.exp(rng.uniform(0.0, np.log(max_len + 1))))
+                a = int(rng.integers(0, s.size))
+                s[a:a + ln] = ord("n") if rng.uniform() < lower_frac else ord("N")
+            if ends and t % 3 == 0:
+                ln = int(rng.integers(1, 40))
+                if rng.integers(0, 2):
+                    s[:ln] = ord("N")
+                else:
+                    s[-ln:] = ord("N")
+        out.append(s)
+    return out

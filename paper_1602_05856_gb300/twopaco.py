@@ -11,6 +11,7 @@ with PyTorch used only to own device memory and to name the CUDA stream.
 from __future__ import annotations
 
 import ctypes
+import dataclasses
 import os
 from dataclasses import dataclass
 from typing import Dict, List, Optional, Sequence
@@ -35,7 +36,8 @@ class TwopacoError(RuntimeError):
 class _Options(ctypes.Structure):
     _fields_ = [("hashes", ctypes.c_int), ("both_strands", ctypes.c_int),
                 ("partition_bins", ctypes.c_uint32), ("table_slots", ctypes.c_uint64),
-                ("candidate_records", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p)]
+                ("candidate_records", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p),
+                ("split_at_n", ctypes.c_int), ("run_capacity", ctypes.c_uint64)]
 
 
 class _Stats(ctypes.Structure):
@@ -146,11 +148,14 @@ class Options:
     table_slots: int = 0
     cuda_stream: int = 0  # cudaStream_t as an integer; 0 = default stream
     candidate_records: int = 0
+    split_at_n: bool = False  # an N (either case) ends its string there
+    run_capacity: int = 0     # split_at_n: room for piece boundaries; 0 = automatic
 
     def _c(self) -> _Options:
         return _Options(int(self.hashes), int(bool(self.both_strands)), int(self.partition_bins),
                         int(self.table_slots), int(self.candidate_records),
-                        ctypes.c_void_p(int(self.cuda_stream) or None))
+                        ctypes.c_void_p(int(self.cuda_stream) or None), int(bool(self.split_at_n)),
+                        int(self.run_capacity))
 
 
 def _stats_dict(s: _Stats) -> Dict[str, int]:
@@ -399,8 +404,7 @@ class DeviceBuild:
             if rc != OK:
                 raise TwopacoError(rc, "twopaco_plan_launch")
             return
-        opt = Options(self.options.hashes, self.options.both_strands, self.options.partition_bins,
-                      self.options.table_slots, self._stream(stream), self.options.candidate_records)
+        opt = dataclasses.replace(self.options, cuda_stream=self._stream(stream))
         twopaco_run_device(self.bases.data_ptr() if self.total_bases else 0, self.offsets.data_ptr(),
                            self.n_seqs, self.total_bases, self.k, self.filter_bits, self.rounds, opt,
                            self.ws_ptr, self.ws_bytes, self.out_offsets.data_ptr(),
