@@ -70,6 +70,66 @@ typedef unsigned __int128 u128;
 
 namespace {
 
+// A k-mer of 64 to 128 bases: four 64-bit words, w[0] the most significant,
+// with the same integer encoding as u128 holds for k <= 63 (k-mers of
+// 64 <= k <= 127; the (k+1)-mers of Algorithm 1 fit as well).
+struct U256 {
+  uint64_t w[4] = {0, 0, 0, 0};
+  U256() = default;
+  explicit U256(uint64_t x) { w[3] = x; }
+};
+
+U256 operator<<(const U256& x, int s) {  // 0 <= s < 256
+  U256 y;
+  const int q = s / 64, r = s % 64;
+  for (int i = 0; i < 4; ++i) {
+    const int j = i + q;
+    uint64_t v = j < 4 ? x.w[j] << r : 0;
+    if (r && j + 1 < 4) v |= x.w[j + 1] >> (64 - r);
+    y.w[i] = v;
+  }
+  return y;
+}
+
+U256 operator>>(const U256& x, int s) {  // 0 <= s < 256
+  U256 y;
+  const int q = s / 64, r = s % 64;
+  for (int i = 0; i < 4; ++i) {
+    const int j = i - q;
+    uint64_t v = j >= 0 ? x.w[j] >> r : 0;
+    if (r && j - 1 >= 0) v |= x.w[j - 1] << (64 - r);
+    y.w[i] = v;
+  }
+  return y;
+}
+
+U256 operator|(const U256& a, const U256& b) {
+  U256 y;
+  for (int i = 0; i < 4; ++i) y.w[i] = a.w[i] | b.w[i];
+  return y;
+}
+
+bool operator==(const U256& a, const U256& b) {
+  for (int i = 0; i < 4; ++i)
+    if (a.w[i] != b.w[i]) return false;
+  return true;
+}
+bool operator!=(const U256& a, const U256& b) { return !(a == b); }
+bool operator<(const U256& a, const U256& b) {
+  for (int i = 0; i < 4; ++i)
+    if (a.w[i] != b.w[i]) return a.w[i] < b.w[i];
+  return false;
+}
+
+// Last base (two least significant bits) of a word.
+unsigned last_base(u128 x) { return (unsigned)(x & 3); }
+unsigned last_base(const U256& x) { return (unsigned)(x.w[3] & 3); }
+// The 128 least significant bits, as (high, low) 64-bit halves.
+uint64_t low_hi(u128 x) { return (uint64_t)(x >> 64); }
+uint64_t low_lo(u128 x) { return (uint64_t)x; }
+uint64_t low_hi(const U256& x) { return x.w[2]; }
+uint64_t low_lo(const U256& x) { return x.w[3]; }
+
 enum { ORACLE_OK = 0, ORACLE_EINVAL = -1, ORACLE_EBADBASE = -2 };
 constexpr uint8_t kCodeN = 4;
 
@@ -89,29 +149,37 @@ struct KmerHash {
     uint64_t lo = (uint64_t)x, hi = (uint64_t)(x >> 64);
     return std::hash<uint64_t>()(lo ^ (lo >> 31) ^ (hi * 0x9E3779B97F4A7C15ull));
   }
+  size_t operator()(const U256& x) const {
+    uint64_t h = 0;
+    for (int i = 0; i < 4; ++i) h = (h ^ x.w[i] ^ (x.w[i] >> 31)) * 0x9E3779B97F4A7C15ull;
+    return std::hash<uint64_t>()(h);
+  }
 };
 
 // The string of length len starting at codes[start], as an integer.
-u128 word_at(const std::vector<uint8_t>& codes, uint64_t start, int len) {
-  u128 x = 0;
-  for (int j = 0; j < len; ++j) x = (x << 2) | codes[start + j];
+template <typename W>
+W word_at(const std::vector<uint8_t>& codes, uint64_t start, int len) {
+  W x{};
+  for (int j = 0; j < len; ++j) x = (x << 2) | W(codes[start + j]);
   return x;
 }
 
 // Reverse complement of a len-base word: read backwards, complement each base.
-u128 reverse_complement(u128 x, int len) {
-  u128 y = 0;
+template <typename W>
+W reverse_complement(W x, int len) {
+  W y{};
   for (int j = 0; j < len; ++j) {
-    y = (y << 2) | (u128)(3 - (int)(x & 3));
-    x >>= 2;
+    y = (y << 2) | W(3 - last_base(x));
+    x = x >> 2;
   }
   return y;
 }
 
 // Normalized form (reverse-complement paragraph after Algorithm 2).
-u128 normalized(u128 x, int len, int both_strands) {
+template <typename W>
+W normalized(W x, int len, int both_strands) {
   if (!both_strands) return x;
-  u128 r = reverse_complement(x, len);
+  W r = reverse_complement(x, len);
   return r < x ? r : x;
 }
 
@@ -157,10 +225,6 @@ struct Degrees {
   uint8_t out = 0;  // bit c set: edge v.c exists
 };
 
-}  // namespace
-
-extern "C" {
-
 /*
  * J(S, k) by definition ("Preliminaries"; normalized forms per the
  * reverse-complement paragraph after Algorithm 2).
@@ -170,9 +234,9 @@ extern "C" {
  *            global byte g is a junction (0 where no k-mer starts)
  *   n_distinct  optional: number of distinct (normalized) k-mers
  */
-int oracle_junctions(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
-                     int both_strands, int split_n, uint8_t* flags, uint64_t* n_distinct) {
-  if (k < 1 || k > 63) return ORACLE_EINVAL;
+template <typename W>
+int junctions_impl(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
+                   int both_strands, int split_n, uint8_t* flags, uint64_t* n_distinct) {
   const uint64_t m = offsets[n];
   std::vector<uint8_t> codes;
   int rc = encode_all(seq, m, split_n, &codes);
@@ -182,15 +246,15 @@ int oracle_junctions(const uint8_t* seq, const uint64_t* offsets, uint64_t n, in
 
   // Step 1-2: every occurrence contributes the edges that enter and leave
   // its k-mer, in the orientation of the normalized form.
-  std::unordered_map<u128, Degrees, KmerHash> deg;
-  std::unordered_set<u128, KmerHash> sentinels;
+  std::unordered_map<W, Degrees, KmerHash> deg;
+  std::unordered_set<W, KmerHash> sentinels;
   for (const Piece& pc : S) {
     const uint64_t s0 = pc.s0, len = pc.len;
     if (len < (uint64_t)k) continue;
     for (uint64_t i = 0; i + k <= len; ++i) {
-      u128 v = word_at(codes, s0 + i, k);
-      u128 r = both_strands ? reverse_complement(v, k) : v;
-      u128 key = (both_strands && r < v) ? r : v;
+      W v = word_at<W>(codes, s0 + i, k);
+      W r = both_strands ? reverse_complement(v, k) : v;
+      W key = (both_strands && r < v) ? r : v;
       Degrees& d = deg[key];
       const bool has_pred = i >= 1, has_succ = i + k < len;
       if (key == v) {  // forward occurrence of the normalized k-mer
@@ -203,15 +267,15 @@ int oracle_junctions(const uint8_t* seq, const uint64_t* offsets, uint64_t n, in
       }
     }
     // Step 3: first and last k-mer of the string are sentinels.
-    sentinels.insert(normalized(word_at(codes, s0, k), k, both_strands));
-    sentinels.insert(normalized(word_at(codes, s0 + len - k, k), k, both_strands));
+    sentinels.insert(normalized(word_at<W>(codes, s0, k), k, both_strands));
+    sentinels.insert(normalized(word_at<W>(codes, s0 + len - k, k), k, both_strands));
   }
   // Step 4: junction = sentinel or bifurcation.
   for (const Piece& pc : S) {
     const uint64_t s0 = pc.s0, len = pc.len;
     if (len < (uint64_t)k) continue;
     for (uint64_t i = 0; i + k <= len; ++i) {
-      u128 key = normalized(word_at(codes, s0 + i, k), k, both_strands);
+      W key = normalized(word_at<W>(codes, s0 + i, k), k, both_strands);
       const Degrees& d = deg[key];
       bool junction = sentinels.count(key) || popcount4(d.in) > 1 || popcount4(d.out) > 1;
       flags[s0 + i] = junction ? 1 : 0;
@@ -228,28 +292,28 @@ int oracle_junctions(const uint8_t* seq, const uint64_t* offsets, uint64_t n, in
  * the two sentinel positions 0 and |s| - k untouched (they stay as given).
  * The sentinel test is on the k-mer, not the position.
  */
-int oracle_alg1_exact(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
-                      int both_strands, int split_n, uint8_t* marks) {
-  if (k < 1 || k > 63) return ORACLE_EINVAL;
+template <typename W>
+int alg1_impl(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
+              int both_strands, int split_n, uint8_t* marks) {
   const uint64_t m = offsets[n];
   std::vector<uint8_t> codes;
   int rc = encode_all(seq, m, split_n, &codes);
   if (rc) return rc;
   const std::vector<Piece> S = pieces(offsets, n, codes);
-  std::unordered_set<u128, KmerHash> E, sentinels;
+  std::unordered_set<W, KmerHash> E, sentinels;
   for (const Piece& pc : S) {
     const uint64_t s0 = pc.s0, len = pc.len;
     if (len < (uint64_t)k) continue;
-    sentinels.insert(normalized(word_at(codes, s0, k), k, both_strands));
-    sentinels.insert(normalized(word_at(codes, s0 + len - k, k), k, both_strands));
+    sentinels.insert(normalized(word_at<W>(codes, s0, k), k, both_strands));
+    sentinels.insert(normalized(word_at<W>(codes, s0 + len - k, k), k, both_strands));
   }
   // Loop 1: insert the two (k+1)-mers that contain the k-mer at i.
   for (const Piece& pc : S) {
     const uint64_t s0 = pc.s0, len = pc.len;
     for (uint64_t i = 1; i + k < len; ++i) {
       if (!marks[s0 + i]) continue;
-      E.insert(normalized(word_at(codes, s0 + i, k + 1), k + 1, both_strands));
-      E.insert(normalized(word_at(codes, s0 + i - 1, k + 1), k + 1, both_strands));
+      E.insert(normalized(word_at<W>(codes, s0 + i, k + 1), k + 1, both_strands));
+      E.insert(normalized(word_at<W>(codes, s0 + i - 1, k + 1), k + 1, both_strands));
     }
   }
   // Loop 2: count existing edges around every marked non-sentinel k-mer.
@@ -257,12 +321,12 @@ int oracle_alg1_exact(const uint8_t* seq, const uint64_t* offsets, uint64_t n, i
     const uint64_t s0 = pc.s0, len = pc.len;
     for (uint64_t i = 1; i + k < len; ++i) {
       if (!marks[s0 + i]) continue;
-      u128 v = word_at(codes, s0 + i, k);
+      W v = word_at<W>(codes, s0 + i, k);
       if (sentinels.count(normalized(v, k, both_strands))) continue;
       int in = 0, out = 0;
       for (int c = 0; c < 4; ++c) {
-        u128 vc = (v << 2) | (u128)c;                    // v . c
-        u128 cv = ((u128)c << (2 * k)) | v;              // c . v
+        W vc = (v << 2) | W(c);                    // v . c
+        W cv = (W(c) << (2 * k)) | v;              // c . v
         if (E.count(normalized(vc, k + 1, both_strands))) ++out;
         if (E.count(normalized(cv, k + 1, both_strands))) ++in;
       }
@@ -279,8 +343,11 @@ int oracle_alg1_exact(const uint8_t* seq, const uint64_t* offsets, uint64_t n, i
  *   mix64(z)  = splitmix64 finalizer (Steele, Lea & Flood 2014):
  *               z ^= z >> 30; z *= 0xbf58476d1ce4e5b9;
  *               z ^= z >> 27; z *= 0x94d049bb133111eb; z ^= z >> 31.
- *   V = hi * 2^64 + lo, the normalized k-mer.
- *   H = mix64(lo ^ mix64(hi));  G = H * 0x9e3779b97f4a7c15 (mod 2^64)
+ *   V = hi * 2^64 + lo, the normalized k-mer (k <= 63), or
+ *   V = w0 * 2^192 + w1 * 2^128 + w2 * 2^64 + w3 (64 <= k <= 127).
+ *   H = mix64(lo ^ mix64(hi)), resp. mix64(w3 ^ mix64(w2 ^ mix64(w1 ^ mix64(w0))))
+ *       (the same value when w0 = w1 = 0, as mix64(0) = 0);
+ *   G = H * 0x9e3779b97f4a7c15 (mod 2^64)
  *   The filter has b bits = b/256 blocks of eight 32-bit words; a k-mer
  *   uses one 64-bit half-pair of its block: 32-bit words 2*o and 2*o + 1.
  *   block = H >> (64 - log2(b/256))  (0 when b = 256)
@@ -316,10 +383,15 @@ struct FilterSpot {
   uint32_t base[8];  // bit base for that word
 };
 
-FilterSpot locate(u128 V, int lg_blocks, int h) {
+uint64_t key_hash64(u128 V) { return mix64((uint64_t)V ^ mix64((uint64_t)(V >> 64))); }
+uint64_t key_hash64(const U256& V) {
+  return mix64(V.w[3] ^ mix64(V.w[2] ^ mix64(V.w[1] ^ mix64(V.w[0]))));
+}
+
+template <typename W>
+FilterSpot locate(const W& V, int lg_blocks, int h) {
   FilterSpot f;
-  uint64_t lo = (uint64_t)V, hi = (uint64_t)(V >> 64);
-  f.H = mix64(lo ^ mix64(hi));
+  f.H = key_hash64(V);
   uint64_t G = f.H * 0x9e3779b97f4a7c15ull;
   f.block = lg_blocks ? (f.H >> (64 - lg_blocks)) : 0;
   uint32_t o = (uint32_t)(G >> 62);
@@ -343,15 +415,11 @@ bool filter_has(const std::vector<uint32_t>& F, const FilterSpot& f, int h, int 
 
 }  // namespace
 
-/*
- * marks: m bytes, written: 1 where the position is active and survives the
- * first pass, else 0. counters (optional, 2 entries): active positions,
- * surviving positions.
- */
-int oracle_pass1(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
-                 int both_strands, int split_n, uint64_t filter_bits, int hashes, uint64_t q,
-                 uint64_t bin_lo, uint64_t bin_hi, uint8_t* marks, uint64_t* counters) {
-  if (k < 1 || k > 63 || hashes < 1 || hashes > 8) return ORACLE_EINVAL;
+template <typename W>
+int pass1_impl(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
+               int both_strands, int split_n, uint64_t filter_bits, int hashes, uint64_t q,
+               uint64_t bin_lo, uint64_t bin_hi, uint8_t* marks, uint64_t* counters) {
+  if (hashes < 1 || hashes > 8) return ORACLE_EINVAL;
   if (filter_bits < 256 || (filter_bits & (filter_bits - 1))) return ORACLE_EINVAL;
   if (q < 1 || (q & (q - 1))) return ORACLE_EINVAL;
   const uint64_t m = offsets[n];
@@ -370,9 +438,9 @@ int oracle_pass1(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
       const uint64_t s0 = pc.s0, len = pc.len;
       if (len < (uint64_t)k) continue;
       for (uint64_t i = 0; i + k <= len; ++i) {
-        u128 v = word_at(codes, s0 + i, k);
-        u128 r = both_strands ? reverse_complement(v, k) : v;
-        u128 key = (both_strands && r < v) ? r : v;
+        W v = word_at<W>(codes, s0 + i, k);
+        W r = both_strands ? reverse_complement(v, k) : v;
+        W key = (both_strands && r < v) ? r : v;
         FilterSpot f = locate(key, lg_blocks, hashes);
         uint64_t bin = f.H & (q - 1);
         if (bin < bin_lo || bin >= bin_hi) continue;
@@ -411,18 +479,19 @@ int oracle_pass1(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
 /*
  * Compacted-graph edges (section "Reduction to the Problem of Finding
  * Junction Positions"): for every two consecutive junction positions p < q of
- * a string, one edge from the k-mer at p to the k-mer at q. flags (m bytes)
+ * a string (of a piece under split_n), one edge from the k-mer at p to the
+ * k-mer at q. flags (m bytes)
  * is the output of oracle_junctions. Edges are written in string order, then
  * position order; for each: the normalized start and end k-mers (hi, lo
  * words), whether the string reads the reverse complement of each (0/1), the
  * start position p and the length q - p. Returns the number of edges, or a
  * negative error. The arrays hold at least (number of junctions) entries.
  */
-long long oracle_edges(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
-                       int both_strands, int split_n, const uint8_t* flags, uint64_t* from_hi,
-                       uint64_t* from_lo, uint64_t* to_hi, uint64_t* to_lo, uint8_t* from_rc,
-                       uint8_t* to_rc, uint64_t* start, uint64_t* length, uint64_t* edges_per_string) {
-  if (k < 1 || k > 63) return ORACLE_EINVAL;
+template <typename W>
+long long edges_impl(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
+                     int both_strands, int split_n, const uint8_t* flags, uint64_t* from_hi,
+                     uint64_t* from_lo, uint64_t* to_hi, uint64_t* to_lo, uint8_t* from_rc,
+                     uint8_t* to_rc, uint64_t* start, uint64_t* length, uint64_t* edges_per_string) {
   const uint64_t m = offsets[n];
   std::vector<uint8_t> codes;
   int rc = encode_all(seq, m, split_n, &codes);
@@ -437,12 +506,12 @@ long long oracle_edges(const uint8_t* seq, const uint64_t* offsets, uint64_t n, 
     for (uint64_t i = 0; i + k <= len && len >= (uint64_t)k; ++i) {
       if (!flags[s0 + i]) continue;
       if (have_prev) {
-        u128 a = word_at(codes, s0 + prev, k), b = word_at(codes, s0 + i, k);
-        u128 na = normalized(a, k, both_strands), nb = normalized(b, k, both_strands);
-        from_hi[e] = (uint64_t)(na >> 64);
-        from_lo[e] = (uint64_t)na;
-        to_hi[e] = (uint64_t)(nb >> 64);
-        to_lo[e] = (uint64_t)nb;
+        W a = word_at<W>(codes, s0 + prev, k), b = word_at<W>(codes, s0 + i, k);
+        W na = normalized(a, k, both_strands), nb = normalized(b, k, both_strands);
+        from_hi[e] = low_hi(na);
+        from_lo[e] = low_lo(na);
+        to_hi[e] = low_hi(nb);
+        to_lo[e] = low_lo(nb);
         from_rc[e] = (na != a) ? 1 : 0;
         to_rc[e] = (nb != b) ? 1 : 0;
         start[e] = s0 + prev - offsets[t];  // offset in the input string
@@ -455,6 +524,61 @@ long long oracle_edges(const uint8_t* seq, const uint64_t* offsets, uint64_t n, 
     }
   }
   return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Entry points: k-mers of up to 63 bases are held in 128-bit words, of 64 to
+// 127 bases in 256-bit words (U256); the same code serves both.
+int oracle_junctions(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
+                     int both_strands, int split_n, uint8_t* flags, uint64_t* n_distinct) {
+  if (k >= 1 && k <= 63) return junctions_impl<u128>(seq, offsets, n, k, both_strands, split_n, flags, n_distinct);
+  if (k >= 64 && k <= 127) return junctions_impl<U256>(seq, offsets, n, k, both_strands, split_n, flags, n_distinct);
+  return ORACLE_EINVAL;
+}
+
+int oracle_alg1_exact(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
+                      int both_strands, int split_n, uint8_t* marks) {
+  if (k >= 1 && k <= 63) return alg1_impl<u128>(seq, offsets, n, k, both_strands, split_n, marks);
+  if (k >= 64 && k <= 127) return alg1_impl<U256>(seq, offsets, n, k, both_strands, split_n, marks);
+  return ORACLE_EINVAL;
+}
+
+/*
+ * marks: m bytes, written: 1 where the position is active and survives the
+ * first pass, else 0. counters (optional, 2 entries): active positions,
+ * surviving positions.
+ */
+int oracle_pass1(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
+                 int both_strands, int split_n, uint64_t filter_bits, int hashes, uint64_t q,
+                 uint64_t bin_lo, uint64_t bin_hi, uint8_t* marks, uint64_t* counters) {
+  if (k >= 1 && k <= 63)
+    return pass1_impl<u128>(seq, offsets, n, k, both_strands, split_n, filter_bits, hashes, q, bin_lo,
+                            bin_hi, marks, counters);
+  if (k >= 64 && k <= 127)
+    return pass1_impl<U256>(seq, offsets, n, k, both_strands, split_n, filter_bits, hashes, q, bin_lo,
+                            bin_hi, marks, counters);
+  return ORACLE_EINVAL;
+}
+
+/*
+ * Compacted-graph edges: see edges_impl. For k > 63 the from/to words hold
+ * the 128 least significant bits of the normalized k-mers (their last 64
+ * bases).
+ */
+long long oracle_edges(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
+                       int both_strands, int split_n, const uint8_t* flags, uint64_t* from_hi,
+                       uint64_t* from_lo, uint64_t* to_hi, uint64_t* to_lo, uint8_t* from_rc,
+                       uint8_t* to_rc, uint64_t* start, uint64_t* length, uint64_t* edges_per_string) {
+  if (k >= 1 && k <= 63)
+    return edges_impl<u128>(seq, offsets, n, k, both_strands, split_n, flags, from_hi, from_lo, to_hi,
+                            to_lo, from_rc, to_rc, start, length, edges_per_string);
+  if (k >= 64 && k <= 127)
+    return edges_impl<U256>(seq, offsets, n, k, both_strands, split_n, flags, from_hi, from_lo, to_hi,
+                            to_lo, from_rc, to_rc, start, length, edges_per_string);
+  return ORACLE_EINVAL;
 }
 
 /*

@@ -44,7 +44,7 @@ def test_fig1_false_junction_gc_absent():
 def _random_cases():
     cases = []
     seed = 11
-    for k in list(range(1, 9)) + [15, 25, 31, 63]:
+    for k in list(range(1, 9)) + [15, 25, 31, 63, 64, 65, 96, 100, 127]:
         for both in (False, True):
             for alpha in (b"ACGT", b"AC", b"ACG"):
                 lo = max(1, k - 3)
@@ -77,6 +77,10 @@ SPECIAL = [
     ("exactly_k", ["ACGTA", "CCCCGGGG"], 5),
     ("self_rc_string", ["AAGCTT", "GGATCC" * 3], 6),
     ("k1", ["ACGTTTACG"], 1),
+    ("homopolymer_k100", ["A" * 160, "T" * 101], 100),
+    ("palindromes_k64", ["ACGT" * 40, "AATT" * 16 + "GC" + "AATT" * 20], 64),
+    ("rc_pair_k127", ["ACGGT" * 40, "ACCGT" * 40], 127),
+    ("exactly_k_k100", ["ACGTTGCA" * 12 + "ACGT", "C" * 99], 100),
 ]
 
 
@@ -152,7 +156,7 @@ def test_lowercase_and_bad_bytes():
     with pytest.raises(O.OracleError):
         O.junctions(["ACGT"], 0)
     with pytest.raises(O.OracleError):
-        O.junctions(["ACGT"], 64)
+        O.junctions(["ACGT"], 128)
 
 
 def test_empty_input():
@@ -410,3 +414,58 @@ def test_split_n_pass1_contains_junctions():
     # a sparse filter is exact: marks equal the junctions
     marks, _, _, _ = O.pass1_marks(seqs, 25, 1 << 30, 8, split_n=True)
     assert np.array_equal(marks, want)
+
+
+# --- k > 63: 256-bit k-mer words -----------------------------------------------------
+
+@pytest.mark.parametrize("k,both", [(64, True), (70, False), (100, True), (127, True)])
+def test_edges_long_k(k, both):
+    """Edges for k > 63 carry the last 64 bases of each normalized k-mer."""
+    seqs = [bytes(s).decode() for s in G.random_strings(700 + k, 4, k, 4 * k, b"AC")]
+    seqs.append(seqs[0][5:k + 40] + seqs[1][: k + 10])
+    e = O.edges(seqs, k, both_strands=both)
+    spelled, o = set(), 0
+    for t, s in enumerate(seqs):
+        for _ in range(int(e["per_string"][t])):
+            p, ln = int(e["start"][o]), int(e["length"][o])
+            seg = s[p:p + ln + k]
+            a, b = seg[:k], seg[-k:]
+            na = min(a, brute.revcomp(a)) if both else a
+            nb = min(b, brute.revcomp(b)) if both else b
+            assert _kmer_str(e["from_hi"][o], e["from_lo"][o], 64) == na[-64:]
+            assert _kmer_str(e["to_hi"][o], e["to_lo"][o], 64) == nb[-64:]
+            assert e["from_rc"][o] == (na != a) and e["to_rc"][o] == (nb != b)
+            spelled.add(tuple(seg[i:i + k] for i in range(ln + 1)))
+            if both:
+                r = brute.revcomp(seg)
+                spelled.add(tuple(r[i:i + k] for i in range(ln + 1)))
+            o += 1
+    assert spelled == brute.compacted_paths(seqs, k, both)
+
+
+@pytest.mark.parametrize("k", [64, 100, 127])
+def test_pass1_invariants_long_k(k):
+    seqs = [bytes(s).decode() for s in G.random_strings(40 + k, 5, 2 * k, 900, b"ACGT")]
+    seqs.append(seqs[0][10:600])
+    want = O.junction_flags(seqs, k)[0]
+    for bits, h in ((1 << 10, 2), (1 << 16, 4), (1 << 30, 8)):
+        marks, _, active, kept = O.pass1_marks(seqs, k, bits, h)
+        assert np.all(marks >= want) and active == sum(len(s) - k + 1 for s in seqs)
+    assert np.array_equal(marks, want)  # 2^30 bits: no collisions on this input
+    # the candidate-set property: all occurrences of a k-mer agree
+    marks, _, _, _ = O.pass1_marks(seqs, k, 1 << 12, 3)
+    _, off = O._prep(seqs)
+    groups = {}
+    for t, s in enumerate(seqs):
+        for i in range(len(s) - k + 1):
+            v = s[i:i + k]
+            groups.setdefault(min(v, brute.revcomp(v)), set()).add(int(marks[int(off[t]) + i]))
+    assert all(len(g) == 1 for g in groups.values())
+
+
+def test_split_n_long_k():
+    rng = np.random.default_rng(17)
+    base = [bytes(s).decode() for s in G.random_strings(18, 5, 150, 700, b"ACGT")]
+    seqs = [_with_ns(rng, s, 100) for s in base]
+    got = _as_lists(O.junctions(seqs, 100, split_n=True))
+    assert got == _brute_split(seqs, 100, True)
