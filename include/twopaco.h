@@ -30,7 +30,9 @@
  *   - Positions are 0-based k-mer starts i in [0, |s| - k]; a string shorter
  *     than k has none.
  *   - Return value: TWOPACO_OK (0) or a negative TWOPACO_E* code.
- *   - k in [1, 63]; filter_bits a power of two >= 256; rounds >= 1;
+ *   - k in [1, 127] (k-mers of up to 31 bases are held in one 64-bit word,
+ *     up to 63 in two, up to 127 in four); filter_bits a power of two >= 256;
+ *     rounds >= 1;
  *     total_bases < 2^48;
  *     options->hashes in [1, 8]; options->partition_bins a power of two
  *     >= rounds. Anything else is TWOPACO_EINVAL.
@@ -186,10 +188,13 @@ int twopaco_read_stats(const void* d_workspace, void* cuda_stream, twopaco_stats
  * One edge of the compacted de Bruijn graph: two consecutive junction
  * positions p < q of one string (section "Reduction to the Problem of Finding
  * Junction Positions"; Observation 1 makes these exactly the maximal
- * non-branching paths). The edge spells s[p .. q + k - 1].
+ * non-branching paths). The edge spells s[p .. q + k - 1]. With split_at_n,
+ * p and q lie in one N-free piece (no edge crosses an N).
  */
 typedef struct twopaco_edge {
-  uint64_t from_hi, from_lo; /* normalized k-mer at p (value hi * 2^64 + lo, first base most significant) */
+  uint64_t from_hi, from_lo; /* normalized k-mer at p (value hi * 2^64 + lo, first base most
+                                significant); for k > 63 its 128 least significant bits,
+                                i.e. its last 64 bases */
   uint64_t to_hi, to_lo;     /* normalized k-mer at q */
   uint64_t start;            /* p, within its string */
   uint64_t length;           /* q - p */

@@ -37,7 +37,7 @@ twopaco_options resolve(const twopaco_options* opt) {
 }
 
 int validate(uint64_t n_seqs, int k, uint64_t filter_bits, int rounds, const twopaco_options& o) {
-  if (k < 1 || k > 63) return TWOPACO_EINVAL;
+  if (k < 1 || k > 127) return TWOPACO_EINVAL;
   if (filter_bits < 256 || !is_pow2(filter_bits) || filter_bits > (1ull << 40)) return TWOPACO_EINVAL;
   if (rounds < 1) return TWOPACO_EINVAL;
   if (o.hashes < 1 || o.hashes > 8) return TWOPACO_EINVAL;
@@ -132,7 +132,8 @@ Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int roun
   L.run_cap = o.run_capacity ? o.run_capacity : auto_run_capacity(m, n_seqs);
   L.nmask = L.bounds = L.chunks = L.runs = L.rank = at;
   if (L.split) {
-    at += align_up((L.bitmap_words + 8) * 4);
+    // the pack kernel writes one N-mask word per two packed words, pad included
+    at += align_up((L.packed_words + 3) / 2 * 4);
     L.bounds = at;
     at += align_up((L.bitmap_words + 8) * 4);
     L.chunks = at;

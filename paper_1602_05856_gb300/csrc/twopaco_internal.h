@@ -103,7 +103,7 @@ struct RunView {
 constexpr int kBlock = 256;             // threads per block of the position kernels
 constexpr int kEmitWordsPerThread = 16;
 constexpr int kEmitTileWords = kBlock * kEmitWordsPerThread;  // bitmap words per emit tile
-constexpr uint64_t kPackPadWords = 8;   // zero words after the packed input
+constexpr uint64_t kPackPadWords = 16;  // zero words after the packed input (window reads of k <= 127 stay inside)
 constexpr uint32_t kMaxSegments = 65536; // candidate-list segments (probe warps) at most
 constexpr uint64_t kRunChunkWords = 1024;  // boundary-bitmap words per compaction chunk
 
@@ -120,11 +120,22 @@ int launch_edges(const DevHeader* hdr_dev, const uint64_t* d_offsets, uint64_t n
 
 // Pass-2 slot layout for this k: 0 = one 64-bit word (key << 9 | mask, k <= 27),
 // 1 = 16 bytes (k <= 31), 2 = 32 bytes (128-bit key).
-inline int table_slot_kind(int k) { return k <= 27 ? 0 : (k <= 31 ? 1 : 2); }
-inline uint64_t table_slot_bytes(int k) { return 8ull << table_slot_kind(k); }
+// Pass-2 table slots: 0 = one word (key << 9 | mask, k <= 27); 1 = 16 B key +
+// mask (k <= 31); 2 = 32 B 128-bit key + mask (k <= 63); 3 = 16 B reference
+// to an occurrence + mask (k <= 127).
+inline int table_slot_kind(int k) { return k <= 27 ? 0 : (k <= 31 ? 1 : (k <= 63 ? 2 : 3)); }
+inline uint64_t table_slot_bytes(int k) {
+  const int t = table_slot_kind(k);
+  return t == 3 ? 16ull : (8ull << t);
+}
 
 // Bytes per candidate record (a global position).
 inline uint64_t cand_record_bytes(int) { return 8; }
+
+// The k > 63 halves of launch_round and of the partition pre-pass (compiled
+// in twopaco_kernels_wide.cu).
+int launch_round_wide(const RunView& v, int round, int rounds, cudaStream_t s);
+int launch_partition_count_wide(const RunView& v, cudaStream_t s);
 
 // Process-wide count of kernels launched by the library.
 void count_launches(int n);

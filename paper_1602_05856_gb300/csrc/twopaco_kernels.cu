@@ -24,22 +24,33 @@
 #include <type_traits>
 #include <vector>
 
+// This file is compiled twice: on its own (every kernel but the k > 63
+// ones, and the library's entry points), and with TWOPACO_WIDE_ONLY from
+// twopaco_kernels_wide.cu (only the k > 63 instances, launch_round_wide and
+// launch_partition_count_wide), so that the two halves build in parallel.
+
 namespace twopaco {
 
-namespace {
-
-std::atomic<unsigned long long> g_launches{0};
-
 // Optional per-kernel timing: CUDA events recorded on the launch stream
-// right before and after every kernel.
+// right before and after every kernel (state shared by both halves).
 struct ProfRecord {
   const char* name;
   cudaEvent_t start, stop;
 };
+extern std::atomic<unsigned long long> g_launches;
+extern std::mutex g_prof_mu;
+extern bool g_prof_on;
+extern std::vector<ProfRecord> g_prof;
+extern std::vector<cudaEvent_t> g_event_pool;
+#ifndef TWOPACO_WIDE_ONLY
+std::atomic<unsigned long long> g_launches{0};
 std::mutex g_prof_mu;
 bool g_prof_on = false;
 std::vector<ProfRecord> g_prof;
 std::vector<cudaEvent_t> g_event_pool;
+#endif
+
+namespace {
 
 cudaEvent_t take_event() {
   if (!g_event_pool.empty()) {
@@ -91,8 +102,53 @@ struct Key {
   uint64_t hi, lo;  // value = hi * 2^64 + lo; hi == 0 for k <= 31
 };
 
+// k-mers of 64 to 127 bases: four words, w[0] the most significant.
+struct Key4 {
+  uint64_t w[4];
+};
+
+// The k-mer word of KW = 1 (k <= 31), 2 (k <= 63) or 4 (k <= 127).
+template <int KW>
+struct KeyOf {
+  using T = Key;
+};
+template <>
+struct KeyOf<4> {
+  using T = Key4;
+};
+template <int KW>
+using KeyT = typename KeyOf<KW>::T;
+
 __device__ __forceinline__ bool key_less(const Key& a, const Key& b) {
   return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+
+__device__ __forceinline__ bool key_less(const Key4& a, const Key4& b) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (a.w[i] != b.w[i]) return a.w[i] < b.w[i];
+  return false;
+}
+
+__device__ __forceinline__ bool key_eq(const Key4& a, const Key4& b) {
+  return a.w[0] == b.w[0] && a.w[1] == b.w[1] && a.w[2] == b.w[2] && a.w[3] == b.w[3];
+}
+
+// a0:a1:a2:a3 (a0 most significant) shifted right by s bits, 0 <= s <= 128.
+__device__ __forceinline__ Key4 shr256(uint64_t a0, uint64_t a1, uint64_t a2, uint64_t a3, int s) {
+  if (s >= 64) {
+    a3 = a2; a2 = a1; a1 = a0; a0 = 0; s -= 64;
+  }
+  if (s >= 64) {
+    a3 = a2; a2 = a1; a1 = a0; a0 = 0; s -= 64;
+  }
+  if (s) {
+    a3 = (a3 >> s) | (a2 << (64 - s));
+    a2 = (a2 >> s) | (a1 << (64 - s));
+    a1 = (a1 >> s) | (a0 << (64 - s));
+    a0 >>= s;
+  }
+  return Key4{{a0, a1, a2, a3}};
 }
 
 // splitmix64 output finalizer (Steele, Lea & Flood, OOPSLA 2014).
@@ -105,9 +161,13 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z;
 }
 
+// H of a k-mer: mix64(lo), mix64(lo ^ mix64(hi)), or for four words
+// mix64(w3 ^ mix64(w2 ^ mix64(w1 ^ mix64(w0)))) -- the same value whenever the
+// higher words are zero, as mix64(0) = 0.
 template <int KW>
-__device__ __forceinline__ uint64_t key_hash(const Key& v) {
-  return KW == 1 ? mix64(v.lo) : mix64(v.lo ^ mix64(v.hi));
+__device__ __forceinline__ uint64_t key_hash(const KeyT<KW>& v) {
+  if constexpr (KW == 4) return mix64(v.w[3] ^ mix64(v.w[2] ^ mix64(v.w[1] ^ mix64(v.w[0]))));
+  else return KW == 1 ? mix64(v.lo) : mix64(v.lo ^ mix64(v.hi));
 }
 
 // Second hash word: H times the 64-bit golden ratio; only its high bits are used.
@@ -137,54 +197,86 @@ __device__ __forceinline__ uint64_t bases32(const uint32_t* __restrict__ packed,
 }
 
 // The k-mer starting at base g. KW = 1 for k <= 31 (one 64-bit word), 2 for
-// 32 <= k <= 63.
+// 32 <= k <= 63, 4 for 64 <= k <= 127.
 template <int KW>
-__device__ __forceinline__ Key load_kmer(const uint32_t* __restrict__ packed, uint64_t g, int k) {
-  const uint64_t a = bases32(packed, g);
-  Key v;
-  if (KW == 1) {
-    v.hi = 0;
-    v.lo = a >> (64 - 2 * k);
+__device__ __forceinline__ KeyT<KW> load_kmer(const uint32_t* __restrict__ packed, uint64_t g, int k) {
+  if constexpr (KW == 4) {
+    // 128 bases from g, then the first k of them
+    return shr256(bases32(packed, g), bases32(packed, g + 32), bases32(packed, g + 64),
+                  bases32(packed, g + 96), 256 - 2 * k);
   } else {
-    const uint64_t b = bases32(packed, g + 32);
-    const int sh = 128 - 2 * k;  // 2 .. 64
-    if (sh == 64) {
+    const uint64_t a = bases32(packed, g);
+    Key v;
+    if (KW == 1) {
       v.hi = 0;
-      v.lo = a;
+      v.lo = a >> (64 - 2 * k);
     } else {
-      v.hi = a >> sh;
-      v.lo = (b >> sh) | (a << (64 - sh));
+      const uint64_t b = bases32(packed, g + 32);
+      const int sh = 128 - 2 * k;  // 2 .. 64
+      if (sh == 64) {
+        v.hi = 0;
+        v.lo = a;
+      } else {
+        v.hi = a >> sh;
+        v.lo = (b >> sh) | (a << (64 - sh));
+      }
     }
+    return v;
   }
-  return v;
 }
 
 // Reverse complement of a k-mer.
 template <int KW>
-__device__ __forceinline__ Key revcomp(const Key& v, int k) {
-  Key r;
-  if (KW == 1) {
-    r.hi = 0;
-    r.lo = rev_pairs(~v.lo) >> (64 - 2 * k);
+__device__ __forceinline__ KeyT<KW> revcomp(const KeyT<KW>& v, int k) {
+  if constexpr (KW == 4) {
+    return shr256(rev_pairs(~v.w[3]), rev_pairs(~v.w[2]), rev_pairs(~v.w[1]), rev_pairs(~v.w[0]),
+                  256 - 2 * k);
   } else {
-    const uint64_t nh = rev_pairs(~v.lo), nl = rev_pairs(~v.hi);
-    const int sh = 128 - 2 * k;
-    if (sh == 64) {
+    Key r;
+    if (KW == 1) {
       r.hi = 0;
-      r.lo = nh;
+      r.lo = rev_pairs(~v.lo) >> (64 - 2 * k);
     } else {
-      r.hi = nh >> sh;
-      r.lo = (nl >> sh) | (nh << (64 - sh));
+      const uint64_t nh = rev_pairs(~v.lo), nl = rev_pairs(~v.hi);
+      const int sh = 128 - 2 * k;
+      if (sh == 64) {
+        r.hi = 0;
+        r.lo = nh;
+      } else {
+        r.hi = nh >> sh;
+        r.lo = (nl >> sh) | (nh << (64 - sh));
+      }
     }
+    return r;
   }
-  return r;
 }
 
 // Slide the k-mer one base to the right: f gains base b at its end, r (the
 // reverse complement) gains 3 - b at its start.
 template <int KW>
-__device__ __forceinline__ void roll(Key& f, Key& r, uint32_t b, int k) {
-  if (KW == 1) {
+__device__ __forceinline__ void roll(KeyT<KW>& f, KeyT<KW>& r, uint32_t b, int k) {
+  if constexpr (KW == 4) {
+    f.w[0] = (f.w[0] << 2) | (f.w[1] >> 62);
+    f.w[1] = (f.w[1] << 2) | (f.w[2] >> 62);
+    f.w[2] = (f.w[2] << 2) | (f.w[3] >> 62);
+    f.w[3] = (f.w[3] << 2) | b;
+    const int hb = 2 * k - 128;  // bits above the two low words, 0 .. 126
+    if (hb > 64) {
+      f.w[0] &= (1ull << (hb - 64)) - 1ull;
+    } else {
+      f.w[0] = 0;
+      if (hb < 64) f.w[1] &= (1ull << hb) - 1ull;
+    }
+    r.w[3] = (r.w[3] >> 2) | (r.w[2] << 62);
+    r.w[2] = (r.w[2] >> 2) | (r.w[1] << 62);
+    r.w[1] = (r.w[1] >> 2) | (r.w[0] << 62);
+    r.w[0] >>= 2;
+    const int top = 2 * k - 2;  // bit of the first base, from the least significant
+    const uint64_t c = 3u - b;
+    if (top >= 192) r.w[0] |= c << (top - 192);
+    else if (top >= 128) r.w[1] |= c << (top - 128);
+    else r.w[2] |= c << (top - 64);
+  } else if (KW == 1) {
     f.lo = ((f.lo << 2) | b) & ((1ull << (2 * k)) - 1ull);
     r.lo = (r.lo >> 2) | ((uint64_t)(3u - b) << (2 * k - 2));
   } else {
@@ -195,6 +287,20 @@ __device__ __forceinline__ void roll(Key& f, Key& r, uint32_t b, int k) {
     r.hi >>= 2;
     if (hb >= 2) r.hi |= (uint64_t)(3u - b) << (hb - 2);
     else r.lo |= (uint64_t)(3u - b) << 62;
+  }
+}
+
+// First base of a k-mer.
+template <int KW>
+__device__ __forceinline__ uint32_t first_base(const KeyT<KW>& f, int k) {
+  if constexpr (KW == 4) {
+    const int top = 2 * k - 2;
+    const uint64_t x = top >= 192 ? f.w[0] >> (top - 192) : (top >= 128 ? f.w[1] >> (top - 128) : f.w[2] >> (top - 64));
+    return (uint32_t)x & 3u;
+  } else if (KW == 1) {
+    return (uint32_t)(f.lo >> (2 * k - 2)) & 3u;
+  } else {
+    return (uint32_t)(k == 32 ? f.lo >> 62 : f.hi >> (2 * k - 66)) & 3u;
   }
 }
 
@@ -233,22 +339,25 @@ __device__ __forceinline__ Bounds kmer_bounds(const RunView& v, uint64_t g) {
 }
 
 // One k-mer occurrence, read in the orientation of its normalized form.
-struct Occ {
-  Key key;         // normalized k-mer
+template <int KW>
+struct OccT {
+  KeyT<KW> key;    // normalized k-mer
   uint64_t H;      // key_hash(key)
   uint32_t items;  // filter items this occurrence inserts (bit j = item j)
   uint32_t tbits;  // pass-2 bits: in-bases 0-3, out-bases 4-7, sentinel 8
   bool sentinel;   // first or last k-mer of its string
+  bool rc;         // the string reads the reverse complement of key here
 };
 
 template <int KW>
-__device__ __forceinline__ void make_occ(const RunView& v, const Key& f, const Key& r,
-                                         uint32_t pred, uint32_t succ, bool sentinel, Occ* oc) {
+__device__ __forceinline__ void make_occ(const RunView& v, const KeyT<KW>& f, const KeyT<KW>& r,
+                                         uint32_t pred, uint32_t succ, bool sentinel, OccT<KW>* oc) {
   const bool use_f = !v.both || !key_less(r, f);  // f is the normalized form
   const bool use_r = v.both && !key_less(f, r);   // r is (palindromes: both)
   oc->key = use_f ? f : r;
   oc->H = key_hash<KW>(oc->key);
   oc->sentinel = sentinel;
+  oc->rc = !use_f;
   if (sentinel) {
     oc->items = 1u << 16;
     oc->tbits = 1u << 8;
@@ -271,14 +380,14 @@ __device__ __forceinline__ void make_occ(const RunView& v, const Key& f, const K
 // The occurrence at global position g, read from scratch; false if no k-mer
 // starts at g.
 template <int KW>
-__device__ __forceinline__ bool read_occurrence(const RunView& v, uint64_t g, Occ* oc) {
+__device__ __forceinline__ bool read_occurrence(const RunView& v, uint64_t g, OccT<KW>* oc) {
   const Bounds b = kmer_bounds(v, g);
   if (g + (uint64_t)v.k > b.end) return false;
-  const Key f = load_kmer<KW>(v.packed, g, v.k);
+  const KeyT<KW> f = load_kmer<KW>(v.packed, g, v.k);
   const bool has_pred = g > b.start, has_succ = g + (uint64_t)v.k < b.end;
   const uint32_t pred = has_pred ? base_at(v.packed, g - 1) : 0u;
   const uint32_t succ = has_succ ? base_at(v.packed, g + v.k) : 0u;
-  const Key r = v.both ? revcomp<KW>(f, v.k) : f;
+  const KeyT<KW> r = v.both ? revcomp<KW>(f, v.k) : f;
   make_occ<KW>(v, f, r, pred, succ, !has_pred || !has_succ, oc);
   return true;
 }
@@ -295,9 +404,9 @@ __device__ __forceinline__ int32_t rel(uint64_t x, uint64_t p0) {
 // because the list marks candidates at a string end (sentinel positions)
 // and every other candidate has a predecessor and a successor.
 template <int KW>
-__device__ __forceinline__ void read_listed(const RunView& v, uint64_t g, bool sentinel, Occ* oc) {
-  const Key f = load_kmer<KW>(v.packed, g, v.k);
-  const Key r = v.both ? revcomp<KW>(f, v.k) : f;
+__device__ __forceinline__ void read_listed(const RunView& v, uint64_t g, bool sentinel, OccT<KW>* oc) {
+  const KeyT<KW> f = load_kmer<KW>(v.packed, g, v.k);
+  const KeyT<KW> r = v.both ? revcomp<KW>(f, v.k) : f;
   const uint32_t pred = sentinel ? 0u : base_at(v.packed, g - 1);
   const uint32_t succ = sentinel ? 0u : base_at(v.packed, g + v.k);
   make_occ<KW>(v, f, r, pred, succ, sentinel, oc);
@@ -317,12 +426,12 @@ __device__ __forceinline__ void walk(const RunView& v, uint64_t p0, F&& fn) {
   // bases p0 + k .. p0 + k + R - 1: the successor of each position, which is
   // also the base that enters the k-mer when it slides to the next position
   const uint32_t next = (uint32_t)(bases32(v.packed, p0 + (uint64_t)k) >> 32);
-  Key f{0, 0}, r{0, 0};
+  KeyT<KW> f{}, r{};
   bool fresh = true;
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const uint64_t p = p0 + i;
-    Occ oc;
+    OccT<KW> oc;
     bool valid = false;
     if (i < m_rel) {
       if (i >= e_rel) {  // p starts a later string (or piece)
@@ -340,9 +449,7 @@ __device__ __forceinline__ void walk(const RunView& v, uint64_t p0, F&& fn) {
           pred = i > s_rel ? base_at(v.packed, p - 1) : 0u;
           fresh = false;
         } else {
-          // the first base of the previous k-mer
-          if (KW == 1) pred = (uint32_t)(f.lo >> (2 * k - 2)) & 3u;
-          else pred = (uint32_t)(k == 32 ? f.lo >> 62 : f.hi >> (2 * k - 66)) & 3u;
+          pred = first_base<KW>(f, k);  // the first base of the previous k-mer
           roll<KW>(f, r, i > 0 ? (next >> (32 - 2 * i)) & 3u : 0u, k);
         }
         const uint32_t succ = (next >> (30 - 2 * i)) & 3u;
@@ -388,11 +495,14 @@ struct ItemPattern {
   uint32_t lo, hi;
 };
 
+// HB > 0: that many bits per item, a compile-time constant; HB = 0: hb bits,
+// a run-time value (the k > 63 kernels, to keep their instances few).
 template <int HB>
-__device__ __forceinline__ ItemPattern item_pattern(uint64_t G) {
+__device__ __forceinline__ ItemPattern item_pattern(uint64_t G, int hb) {
   ItemPattern p{0u, 0u};
 #pragma unroll
-  for (int u = 0; u < HB; ++u) {
+  for (int u = 0; u < (HB ? HB : 8); ++u) {
+    if (!HB && u >= hb) break;
     const uint32_t b = 1u << bit_base(G, u);
     if (u & 1) p.hi |= b; else p.lo |= b;
   }
@@ -404,17 +514,18 @@ __device__ __forceinline__ uint64_t item_bits(const ItemPattern& p, uint32_t j) 
 }
 
 template <int HB>
-__device__ __forceinline__ uint64_t item_bits(uint64_t G, uint32_t j) {
-  return item_bits(item_pattern<HB>(G), j);
+__device__ __forceinline__ uint64_t item_bits(uint64_t G, uint32_t j, int hb) {
+  return item_bits(item_pattern<HB>(G, hb), j);
 }
 
-// Bit j of the result: item j is present (all of its HB bits are set).
+// Bit j of the result: item j is present (all of its bits are set).
 template <int HB>
-__device__ __forceinline__ uint32_t present_items(uint64_t G, uint64_t w) {
+__device__ __forceinline__ uint32_t present_items(uint64_t G, uint64_t w, int hb) {
   const uint32_t lo = (uint32_t)w, hi = (uint32_t)(w >> 32);
   uint32_t pres = 0x1FFFFu;
 #pragma unroll
-  for (int u = 0; u < HB; ++u) {
+  for (int u = 0; u < (HB ? HB : 8); ++u) {
+    if (!HB && u >= hb) break;
     const uint32_t x = (u & 1) ? hi : lo;
     pres &= __funnelshift_r(x, x, bit_base(G, u));
   }
@@ -533,11 +644,80 @@ __device__ __forceinline__ int table_find(const RunView& v, uint64_t cap, const 
   return -1;
 }
 
+// Slots of k-mers of 64 to 127 bases (kind 3): instead of the key, a
+// reference to one occurrence of it -- bits 0-47 its position + 1, bit 48
+// whether the string reads the key's reverse complement there, bits 49-63
+// the top 15 bits of H as a tag. 0 is empty. Keys are compared by reading the
+// referenced occurrence back from the packed input, so one 64-bit CAS claims
+// a slot for a key of any length.
+struct alignas(16) Slot3 {
+  unsigned long long ref;
+  unsigned int mask;
+  unsigned int pad;
+};
+
+constexpr uint64_t kRefPos = (1ull << 48) - 1;
+
+__device__ __forceinline__ bool ref_holds(const RunView& v, uint64_t ref, const Key4& key) {
+  Key4 x = load_kmer<4>(v.packed, (ref & kRefPos) - 1, v.k);
+  if ((ref >> 48) & 1u) x = revcomp<4>(x, v.k);
+  return key_eq(x, key);
+}
+
+__device__ __forceinline__ uint64_t table_insert_ref(const RunView& v, uint64_t cap, const Key4& key,
+                                                     uint64_t H, uint32_t bits, uint64_t g, bool rc) {
+  const uint64_t mask = cap - 1, tag = H >> 49;
+  const unsigned long long mine = (tag << 49) | ((uint64_t)rc << 48) | (g + 1);
+  uint64_t i = slot_hash(H) & mask;
+  for (uint64_t probe = 0; probe < cap; ++probe, i = (i + 1) & mask) {
+    Slot3* s = static_cast<Slot3*>(v.table) + i;
+    unsigned long long cur = __ldcg(&s->ref);
+    if (cur == 0) {
+      cur = atomicCAS(&s->ref, 0ull, mine);
+      if (cur == 0) {
+        atomicOr(&s->mask, bits);
+        return i;
+      }
+    }
+    if ((cur >> 49) != tag || !ref_holds(v, cur, key)) continue;
+    if ((__ldcg(&s->mask) & bits) != bits) atomicOr(&s->mask, bits);
+    return i;
+  }
+  return kNoSlot;
+}
+
+__device__ __forceinline__ int table_find_ref(const RunView& v, uint64_t cap, const Key4& key, uint64_t H) {
+  const uint64_t mask = cap - 1, tag = H >> 49;
+  uint64_t i = slot_hash(H) & mask;
+  for (uint64_t probe = 0; probe < cap; ++probe, i = (i + 1) & mask) {
+    const Slot3* s = static_cast<const Slot3*>(v.table) + i;
+    const unsigned long long cur = __ldcg(&s->ref);
+    if (cur == 0) return -1;
+    if ((cur >> 49) == tag && ref_holds(v, cur, key)) return (int)__ldcg(&s->mask);
+  }
+  return -1;
+}
+
+// The table slot of an occurrence at g (inserted), or its mask (found).
+template <int KW, int TS>
+__device__ __forceinline__ uint64_t insert_occurrence(const RunView& v, uint64_t cap, const OccT<KW>& oc,
+                                                      uint64_t g) {
+  if constexpr (TS == 3) return table_insert_ref(v, cap, oc.key, oc.H, oc.tbits, g, oc.rc);
+  else return table_insert<TS>(v, cap, oc.key, slot_hash(oc.H), oc.tbits);
+}
+
+template <int KW, int TS>
+__device__ __forceinline__ int find_occurrence(const RunView& v, uint64_t cap, const OccT<KW>& oc) {
+  if constexpr (TS == 3) return table_find_ref(v, cap, oc.key, oc.H);
+  else return table_find<TS>(v, cap, oc.key, slot_hash(oc.H));
+}
+
 // Mask held by slot i (a slot that table_insert returned).
 template <int TS>
 __device__ __forceinline__ int table_mask(const RunView& v, uint64_t i) {
   if (TS == 0) return (int)(__ldcg(static_cast<const unsigned long long*>(v.table) + i) & ((1u << kMaskBits) - 1u));
   if (TS == 1) return (int)__ldcg(&(static_cast<const Slot1*>(v.table) + i)->mask);
+  if (TS == 3) return (int)__ldcg(&(static_cast<const Slot3*>(v.table) + i)->mask);
   return (int)__ldcg(&(static_cast<const Slot2*>(v.table) + i)->mask);
 }
 
@@ -855,14 +1035,14 @@ __global__ void __launch_bounds__(kBlock) pass1_insert_kernel(RunView v, int rou
     const uint64_t p0 = base + (uint64_t)t * kInsertR;
     if (p0 < v.m) {
       uint64_t prev = 0;
-      walk<KW, kInsertR>(v, p0, [&](int i, uint64_t, bool valid, const Occ& oc) {
+      walk<KW, kInsertR>(v, p0, [&](int i, uint64_t, bool valid, const auto& oc) {
         uint64_t d = 0;
         if (valid) {
           if (ROUNDS && !in_round(v, oc.H, round)) {
             d = 1;
           } else {
             const uint64_t G = second_hash(oc.H);
-            const ItemPattern pat = item_pattern<HB>(G);
+            const ItemPattern pat = item_pattern<HB>(G, v.hashes);
             const uint32_t j1 = __ffs(oc.items) - 1, j2 = 31 - __clz(oc.items);
             uint64_t m = item_bits(pat, j1);
             if (j2 != j1) m |= item_bits(pat, j2);  // a palindrome's two orientations
@@ -916,7 +1096,7 @@ __global__ void __launch_bounds__(kBlock, 3) pass1_probe_kernel(RunView v, int r
     uint64_t word[kR], G[kR];
     uint32_t probe_bits = 0, sent_bits = 0, valid_bits = 0;
     if (p0 < v.m) {
-      walk<KW, kR>(v, p0, [&](int i, uint64_t, bool valid, const Occ& oc) {
+      walk<KW, kR>(v, p0, [&](int i, uint64_t, bool valid, const auto& oc) {
         if (!valid) return;
         valid_bits |= 1u << i;
         if (ROUNDS && !in_round(v, oc.H, round)) return;
@@ -933,7 +1113,7 @@ __global__ void __launch_bounds__(kBlock, 3) pass1_probe_kernel(RunView v, int r
 #pragma unroll
     for (int i = 0; i < kR; ++i) {
       if ((probe_bits >> i) & 1u) {
-        const uint32_t pres = present_items<HB>(G[i], word[i]);
+        const uint32_t pres = present_items<HB>(G[i], word[i], v.hashes);
         if ((pres >> 16) || __popc(pres & 0xFFFFu) >= 2) keep_bits |= 1u << i;
       }
       if ((keep_bits >> i) & 1u) {
@@ -1021,7 +1201,7 @@ __global__ void __launch_bounds__(kBlock) pass1_probe_desc_kernel(RunView v, int
           keep = true;
         } else {
           // descriptor bits 32-61 are G's, the only bits bit_base reads for u < 6
-          const uint32_t pres = present_items<HB>(d[q], word[q]);
+          const uint32_t pres = present_items<HB>(d[q], word[q], v.hashes);
           keep = (pres >> 16) || __popc(pres & 0xFFFFu) >= 2;
         }
       }
@@ -1119,6 +1299,8 @@ __global__ void __launch_bounds__(kBlock) table_clear_kernel(RunView v) {
     } else if (TS == 1) {
       Slot1* s = static_cast<Slot1*>(v.table) + i;
       *reinterpret_cast<ulonglong2*>(s) = make_ulonglong2(kEmpty, 0ull);
+    } else if (TS == 3) {
+      reinterpret_cast<ulonglong2*>(v.table)[i] = make_ulonglong2(0ull, 0ull);
     } else {
       Slot2* s = static_cast<Slot2*>(v.table) + i;
       reinterpret_cast<ulonglong2*>(s)[0] = make_ulonglong2(kEmpty, kEmpty);
@@ -1171,9 +1353,9 @@ __global__ void __launch_bounds__(kBlock) pass2_insert_kernel(RunView v) {
     for_listed(v, [&](uint64_t i) {
       bool sent;
       const uint64_t g = list_at(v, i, &sent, false);
-      Occ oc;
+      OccT<KW> oc;
       read_listed<KW>(v, g, sent, &oc);
-      const uint64_t slot = table_insert<TS>(v, cap, oc.key, slot_hash(oc.H), oc.tbits);
+      const uint64_t slot = insert_occurrence<KW, TS>(v, cap, oc, g);
       if (slot == kNoSlot) v.hdr->overflow = 1;
       if (v.cand_slot) v.cand_slot[i] = slot == kNoSlot ? 0xFFFFFFFFu : (uint32_t)slot;
     });
@@ -1182,9 +1364,9 @@ __global__ void __launch_bounds__(kBlock) pass2_insert_kernel(RunView v) {
   const uint64_t stride = (uint64_t)gridDim.x * kBlock;
   for (uint64_t g = (uint64_t)blockIdx.x * kBlock + threadIdx.x; g < v.m; g += stride) {
     if (!((__ldg(v.ctemp + (g >> 5)) >> (g & 31)) & 1u)) continue;
-    Occ oc;
+    OccT<KW> oc;
     if (!read_occurrence<KW>(v, g, &oc)) continue;
-    if (table_insert<TS>(v, cap, oc.key, slot_hash(oc.H), oc.tbits) == kNoSlot) v.hdr->overflow = 1;
+    if (insert_occurrence<KW, TS>(v, cap, oc, g) == kNoSlot) v.hdr->overflow = 1;
   }
 }
 
@@ -1212,18 +1394,18 @@ __global__ void __launch_bounds__(kBlock) pass2_classify_kernel(RunView v) {
         const uint32_t slot = __ldcs(v.cand_slot + i);
         mark(g, slot == 0xFFFFFFFFu ? -1 : table_mask<TS>(v, slot));
       } else {
-        Occ oc;
+        OccT<KW> oc;
         read_listed<KW>(v, g, sent, &oc);
-        mark(g, table_find<TS>(v, cap, oc.key, slot_hash(oc.H)));
+        mark(g, find_occurrence<KW, TS>(v, cap, oc));
       }
     });
   } else {
     const uint64_t stride = (uint64_t)gridDim.x * kBlock;
     for (uint64_t g = (uint64_t)blockIdx.x * kBlock + threadIdx.x; g < v.m; g += stride) {
       if (!((__ldg(v.ctemp + (g >> 5)) >> (g & 31)) & 1u)) continue;
-      Occ oc;
+      OccT<KW> oc;
       if (!read_occurrence<KW>(v, g, &oc)) continue;
-      mark(g, table_find<TS>(v, cap, oc.key, slot_hash(oc.H)));
+      mark(g, find_occurrence<KW, TS>(v, cap, oc));
     }
   }
   block_add(found, &v.hdr->pass2_kept);
@@ -1235,10 +1417,10 @@ template <int KW, int HB>
 __global__ void __launch_bounds__(kBlock) partition_count_kernel(RunView v) {
   const uint64_t stride = (uint64_t)gridDim.x * kBlock * kR;
   for (uint64_t p0 = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) * kR; p0 < v.m; p0 += stride) {
-    walk<KW, kR>(v, p0, [&](int, uint64_t, bool valid, const Occ& oc) {
+    walk<KW, kR>(v, p0, [&](int, uint64_t, bool valid, const auto& oc) {
       if (!valid) return;
       const uint64_t G = second_hash(oc.H);
-      const uint64_t m = item_bits<HB>(G, 17u);
+      const uint64_t m = item_bits<HB>(G, 17u, v.hashes);
       unsigned long long* w = filter_word(v, oc.H, G);
       if ((__ldcg(w) & m) == m) return;
       const unsigned long long old = atomicOr(w, (unsigned long long)m);
@@ -1531,15 +1713,23 @@ __global__ void __launch_bounds__(1024) edge_offsets_kernel(const DevHeader* hdr
   }
 }
 
+// The normalized k-mer at g (for k > 63 its 128 least significant bits, the
+// last 64 bases) and whether the string reads its reverse complement.
 template <int KW>
 __device__ __forceinline__ void edge_vertex(const uint32_t* packed, uint64_t g, int k, int both,
                                             unsigned long long* hi, unsigned long long* lo,
                                             unsigned int* rc) {
-  const Key f = load_kmer<KW>(packed, g, k);
-  const Key r = both ? revcomp<KW>(f, k) : f;
+  const KeyT<KW> f = load_kmer<KW>(packed, g, k);
+  const KeyT<KW> r = both ? revcomp<KW>(f, k) : f;
   const bool use_r = both && key_less(r, f);
-  *hi = use_r ? r.hi : f.hi;
-  *lo = use_r ? r.lo : f.lo;
+  const KeyT<KW>& x = use_r ? r : f;
+  if constexpr (KW == 4) {
+    *hi = x.w[2];
+    *lo = x.w[3];
+  } else {
+    *hi = x.hi;
+    *lo = x.lo;
+  }
   *rc = use_r ? 1u : 0u;
 }
 
@@ -1578,9 +1768,12 @@ __global__ void __launch_bounds__(kBlock) edges_kernel(const DevHeader* hdr, con
     if (k <= 31) {
       edge_vertex<1>(packed, g0 + p, k, both, &o.from_hi, &o.from_lo, &o.from_rc);
       edge_vertex<1>(packed, g0 + q, k, both, &o.to_hi, &o.to_lo, &o.to_rc);
-    } else {
+    } else if (k <= 63) {
       edge_vertex<2>(packed, g0 + p, k, both, &o.from_hi, &o.from_lo, &o.from_rc);
       edge_vertex<2>(packed, g0 + q, k, both, &o.to_hi, &o.to_lo, &o.to_rc);
+    } else {
+      edge_vertex<4>(packed, g0 + p, k, both, &o.from_hi, &o.from_lo, &o.from_rc);
+      edge_vertex<4>(packed, g0 + q, k, both, &o.to_hi, &o.to_lo, &o.to_rc);
     }
     o.start = p;
     o.length = q - p;
@@ -1618,6 +1811,7 @@ int done(int n) {
 
 }  // namespace
 
+#ifndef TWOPACO_WIDE_ONLY
 void count_launches(int n) { g_launches.fetch_add((unsigned long long)n); }
 unsigned long long launches_so_far() { return g_launches.load(); }
 
@@ -1643,6 +1837,8 @@ int launch_pack(const RunView& v, cudaStream_t s) {
   return done(6);
 }
 
+#endif  // TWOPACO_WIDE_ONLY
+
 // Run f with the filter's bits per item as a compile-time constant.
 template <typename F>
 void with_hashes(int h, F&& f) {
@@ -1658,6 +1854,7 @@ void with_hashes(int h, F&& f) {
   }
 }
 
+#ifndef TWOPACO_WIDE_ONLY
 int launch_partition(const RunView& v, int rounds, cudaStream_t s) {
   if (v.m == 0) return 0;
   // the filter is clear (pack kernel); the pre-pass uses it, round 0 clears it again
@@ -1665,13 +1862,17 @@ int launch_partition(const RunView& v, int rounds, cudaStream_t s) {
   const uint64_t threads = (v.m + kR - 1) / kR;
   {
     Timed t("partition_count", s);
-    with_hashes(v.hashes, [&](auto hb) {
-      constexpr int HB = decltype(hb)::value;
-      if (v.k <= 31)
-        partition_count_kernel<1, HB><<<grid_for(partition_count_kernel<1, HB>, kBlock, threads), kBlock, 0, s>>>(v);
-      else
-        partition_count_kernel<2, HB><<<grid_for(partition_count_kernel<2, HB>, kBlock, threads), kBlock, 0, s>>>(v);
-    });
+    if (v.k > 63) {
+      if (launch_partition_count_wide(v, s) < 0) return -1;
+    } else {
+      with_hashes(v.hashes, [&](auto hb) {
+        constexpr int HB = decltype(hb)::value;
+        if (v.k <= 31)
+          partition_count_kernel<1, HB><<<grid_for(partition_count_kernel<1, HB>, kBlock, threads), kBlock, 0, s>>>(v);
+        else
+          partition_count_kernel<2, HB><<<grid_for(partition_count_kernel<2, HB>, kBlock, threads), kBlock, 0, s>>>(v);
+      });
+    }
   }
   uint64_t* prefix = reinterpret_cast<uint64_t*>(v.bins + (v.qmask + 1u));
   {
@@ -1680,6 +1881,7 @@ int launch_partition(const RunView& v, int rounds, cudaStream_t s) {
   }
   return done(2);
 }
+#endif  // TWOPACO_WIDE_ONLY
 
 template <int KW, bool RD, int HB, int TS>
 int round_impl(const RunView& v, int round, cudaStream_t s) {
@@ -1735,8 +1937,10 @@ int round_impl(const RunView& v, int round, cudaStream_t s) {
   return done(6);
 }
 
+#ifndef TWOPACO_WIDE_ONLY
 int launch_round(const RunView& v, int round, int rounds, cudaStream_t s) {
   if (v.m == 0) return 0;
+  if (v.k > 63) return launch_round_wide(v, round, rounds, s);
   int rc = 0;
   with_hashes(v.hashes, [&](auto hb) {
     constexpr int HB = decltype(hb)::value;
@@ -1786,7 +1990,22 @@ int launch_edges(const DevHeader* hdr_dev, const uint64_t* d_offsets, uint64_t n
   return done(3);
 }
 
+#else
+// k > 63: four-word k-mers, reference slots, the bits per item a run-time value.
+int launch_round_wide(const RunView& v, int round, int rounds, cudaStream_t s) {
+  return rounds > 1 ? round_impl<4, true, 0, 3>(v, round, s) : round_impl<4, false, 0, 3>(v, round, s);
+}
+
+int launch_partition_count_wide(const RunView& v, cudaStream_t s) {
+  const uint64_t threads = (v.m + kR - 1) / kR;
+  partition_count_kernel<4, 0><<<grid_for(partition_count_kernel<4, 0>, kBlock, threads), kBlock, 0, s>>>(v);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+#endif  // TWOPACO_WIDE_ONLY
+
 }  // namespace twopaco
+
+#ifndef TWOPACO_WIDE_ONLY
 
 extern "C" unsigned long long twopaco_kernel_launches(void) {
   return twopaco::g_launches.load();
@@ -1835,3 +2054,5 @@ extern "C" int twopaco_profile_kernels(const char** names, unsigned long long* l
   }
   return n;
 }
+
+#endif  // TWOPACO_WIDE_ONLY

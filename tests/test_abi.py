@@ -35,7 +35,7 @@ def test_host_side_argument_checks():
     assert T.twopaco_strerror(T.EINVAL) == "invalid argument"
     ok = T.twopaco_workspace_size(1000, 2, 25, 1 << 20, 1)
     assert ok > (1 << 20) // 8
-    bad = [dict(k=0), dict(k=64), dict(filter_bits=100), dict(filter_bits=3 << 10), dict(rounds=0),
+    bad = [dict(k=0), dict(k=128), dict(filter_bits=100), dict(filter_bits=3 << 10), dict(rounds=0),
            dict(options=T.Options(hashes=0)), dict(options=T.Options(hashes=9)),
            dict(options=T.Options(partition_bins=1000)), dict(rounds=8, options=T.Options(partition_bins=4))]
     for b in bad:
@@ -58,3 +58,15 @@ def test_workspace_grows_with_input_and_filter():
     c = T.twopaco_workspace_size(10**6, 4, 25, 1 << 26, 1)
     d = T.twopaco_workspace_size(10**6, 4, 63, 1 << 20, 1)
     assert b > a and c - a >= ((1 << 26) - (1 << 20)) // 8 and d > a
+
+
+def test_split_and_long_k_workspace():
+    from paper_1602_05856_gb300 import build, twopaco as T
+    build.build()
+    plain = T.twopaco_workspace_size(1 << 20, 4, 25, 1 << 20, 1)
+    split = T.twopaco_workspace_size(1 << 20, 4, 25, 1 << 20, 1, T.Options(split_at_n=True))
+    assert split > plain + 2 * ((1 << 20) // 8)  # N mask and boundary bitmap
+    small = T.twopaco_workspace_size(1 << 20, 4, 25, 1 << 20, 1, T.Options(split_at_n=True, run_capacity=16))
+    assert plain < small < split
+    assert T.twopaco_workspace_size(1 << 20, 4, 100, 1 << 20, 1) > 0
+    assert T.twopaco_workspace_size(1 << 20, 4, 127, 1 << 20, 1) > 0
