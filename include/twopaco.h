@@ -156,6 +156,58 @@ int twopaco_run_device(const uint8_t* d_bases, const uint64_t* d_offsets, uint64
                        uint64_t* d_out_offsets, uint64_t* d_out_positions, uint64_t out_capacity);
 
 /*
+ * The rounds [round_begin, round_end) of a device-resident run (Algorithm 3
+ * runs its rounds one after the other, each adding its junctions to
+ * C_final), with the arguments of twopaco_run_device; 0 <= round_begin <
+ * round_end <= rounds, or round_begin == round_end == rounds (only write the
+ * output of a finished run, e.g. one restored from its last checkpoint),
+ * else TWOPACO_EINVAL. round_begin == 0 starts the run
+ * (packs the input and, for rounds > 1, cuts the k-mer classes); a later
+ * round_begin continues the run the workspace holds -- from an earlier call
+ * on the same workspace, or restored by twopaco_checkpoint_load. The call
+ * with round_end == rounds also writes the output. twopaco_run_device is
+ * twopaco_run_rounds(..., 0, rounds, ...). Launches without synchronising.
+ */
+int twopaco_run_rounds(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_seqs,
+                       uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
+                       const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
+                       int round_begin, int round_end, uint64_t* d_out_offsets,
+                       uint64_t* d_out_positions, uint64_t out_capacity);
+
+/*
+ * Checkpoints between rounds (the paper has no counterpart; for runs long
+ * enough that a failure should not restart every round). A checkpoint
+ * holds what the finished rounds left: C_final (one bit per base), the class
+ * cut and partition counters, the Table-4 counters, the run's parameters and
+ * a digest of the packed input; host memory, owned by the caller, a plain
+ * byte string that may be written to a file.
+ *
+ * twopaco_checkpoint_bytes: the size of a checkpoint of such a run.
+ *
+ * twopaco_checkpoint_save: after twopaco_run_rounds(..., round_end = r, ...)
+ *   with 1 <= r <= rounds, copy the workspace's state into host_dst (bytes >=
+ *   twopaco_checkpoint_bytes) with next_round = r; synchronises cuda_stream.
+ *   Returns the run's failure (TWOPACO_EBADBASE / EOVERFLOW / ETIMEOUT) instead
+ *   of saving a failed state.
+ *
+ * twopaco_checkpoint_load: restore a checkpoint into a workspace (which may
+ *   be a fresh one in another process), given the same input and
+ *   parameters as the run it was taken from: the input is packed again and
+ *   its digest compared. A checkpoint of another input, parameter set or
+ *   format is TWOPACO_EINVAL. Synchronises options->cuda_stream; *next_round
+ *   gets the round to continue with (twopaco_run_rounds(..., *next_round,
+ *   rounds, ...)).
+ */
+int twopaco_checkpoint_bytes(uint64_t total_bases, uint64_t n_seqs, int k, uint64_t filter_bits,
+                             int rounds, const twopaco_options* opt, uint64_t* bytes);
+int twopaco_checkpoint_save(void* d_workspace, int next_round, void* host_dst, uint64_t bytes,
+                            void* cuda_stream);
+int twopaco_checkpoint_load(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_seqs,
+                            uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
+                            const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
+                            const void* host_src, uint64_t bytes, int* next_round);
+
+/*
  * A device-resident run captured as a CUDA graph. twopaco_plan_create takes
  * the arguments of twopaco_run_device (options->cuda_stream is ignored),
  * records that run's whole launch sequence -- pack, every round's two

@@ -1,5 +1,6 @@
 // C-ABI layer of the junction-detection library: argument checks, workspace
 // layout, the launch sequence of one run, and the host-to-host build.
+#include <cstddef>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -268,14 +269,17 @@ int twopaco_workspace_size(uint64_t total_bases, uint64_t n_seqs, int k, uint64_
   return TWOPACO_OK;
 }
 
-int twopaco_run_device(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_seqs,
+int twopaco_run_rounds(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_seqs,
                        uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
                        const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
-                       uint64_t* d_out_offsets, uint64_t* d_out_positions, uint64_t out_capacity) {
+                       int round_begin, int round_end, uint64_t* d_out_offsets,
+                       uint64_t* d_out_positions, uint64_t out_capacity) {
   const twopaco_options o = resolve(opt);
   int rc = validate(n_seqs, k, filter_bits, rounds, o);
   if (rc) return rc;
   if (validate_size(total_bases)) return TWOPACO_EINVAL;
+  if (round_begin < 0 || round_end > rounds || round_begin > round_end) return TWOPACO_EINVAL;
+  if (round_begin == round_end && round_end != rounds) return TWOPACO_EINVAL;
   if (total_bases > 0 && (n_seqs == 0 || !d_bases || !d_offsets)) return TWOPACO_EINVAL;
   if (n_seqs > 0 && !d_offsets) return TWOPACO_EINVAL;
   if (!d_out_offsets || (out_capacity && !d_out_positions)) return TWOPACO_EINVAL;
@@ -285,13 +289,24 @@ int twopaco_run_device(const uint8_t* d_bases, const uint64_t* d_offsets, uint64
   const RunView v = make_view(d_bases, d_offsets, n_seqs, total_bases, k, filter_bits, rounds, o, L,
                               d_workspace, d_out_offsets, d_out_positions, out_capacity);
   cudaStream_t s = static_cast<cudaStream_t>(o.cuda_stream);
-  if (launch_init(v, s) < 0) return TWOPACO_ECUDA;
-  if (launch_pack(v, s) < 0) return TWOPACO_ECUDA;
-  if (rounds > 1 && launch_partition(v, rounds, s) < 0) return TWOPACO_ECUDA;
-  for (int r = 0; r < rounds; ++r)
+  if (round_begin == 0) {  // a new run: pack, and the class cut of Algorithm 3
+    if (launch_init(v, s) < 0) return TWOPACO_ECUDA;
+    if (launch_pack(v, s) < 0) return TWOPACO_ECUDA;
+    if (rounds > 1 && launch_partition(v, rounds, s) < 0) return TWOPACO_ECUDA;
+  }
+  for (int r = round_begin; r < round_end; ++r)
     if (launch_round(v, r, rounds, s) < 0) return TWOPACO_ECUDA;
-  if (launch_emit(v, s) < 0) return TWOPACO_ECUDA;
+  if (round_end == rounds && launch_emit(v, s) < 0) return TWOPACO_ECUDA;
   return TWOPACO_OK;
+}
+
+int twopaco_run_device(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_seqs,
+                       uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
+                       const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
+                       uint64_t* d_out_offsets, uint64_t* d_out_positions, uint64_t out_capacity) {
+  return twopaco_run_rounds(d_bases, d_offsets, n_seqs, total_bases, k, filter_bits, rounds, opt,
+                            d_workspace, workspace_bytes, 0, rounds < 1 ? 1 : rounds, d_out_offsets,
+                            d_out_positions, out_capacity);
 }
 
 int twopaco_edges_device(const void* d_workspace, const uint64_t* d_offsets, uint64_t n_seqs,
@@ -349,6 +364,158 @@ int twopaco_read_state(const void* d_workspace, int which, void* host_dst, uint6
   if (bytes > avail) return TWOPACO_EINVAL;
   if (!bytes) return TWOPACO_OK;
   return cuda_code(cudaMemcpy(host_dst, src, bytes, cudaMemcpyDeviceToHost));
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoints: the state between rounds (C_final, the class cut, counters)
+// ---------------------------------------------------------------------------
+
+}  // extern "C"
+
+namespace twopaco {
+namespace {
+
+static_assert(offsetof(DevHeader, pass2_kept) == offsetof(DevHeader, positions) + 16,
+              "positions, pass1_kept, pass2_kept are restored as one block");
+
+struct CheckpointHead {
+  char magic[8];  // "TPCKPT01"
+  uint32_t version;
+  int32_t k, rounds, hashes, both, split, next_round, lg_blocks;
+  uint64_t m, n_seqs, q, bitmap_words, input_digest;
+  uint64_t positions, pass1_kept, pass2_kept, table_max;
+};
+constexpr char kCheckpointMagic[8] = {'T', 'P', 'C', 'K', 'P', 'T', '0', '1'};
+
+uint64_t checkpoint_bytes(uint64_t m, int rounds, uint64_t q) {
+  const uint64_t words = (m + 31) / 32;
+  return sizeof(CheckpointHead) + 4 * ((uint64_t)rounds + 1) + (rounds > 1 ? 4 * q : 0) + 4 * words;
+}
+
+}  // namespace
+}  // namespace twopaco
+
+extern "C" {
+
+int twopaco_checkpoint_bytes(uint64_t total_bases, uint64_t n_seqs, int k, uint64_t filter_bits,
+                             int rounds, const twopaco_options* opt, uint64_t* bytes) {
+  const twopaco_options o = resolve(opt);
+  int rc = validate(n_seqs, k, filter_bits, rounds, o);
+  if (rc) return rc;
+  if (!bytes || validate_size(total_bases)) return TWOPACO_EINVAL;
+  *bytes = checkpoint_bytes(total_bases, rounds, o.partition_bins);
+  return TWOPACO_OK;
+}
+
+int twopaco_checkpoint_save(void* d_workspace, int next_round, void* host_dst, uint64_t bytes,
+                            void* cuda_stream) {
+  if (!d_workspace || !host_dst || (reinterpret_cast<uintptr_t>(d_workspace) % kAlign)) return TWOPACO_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_code(e);
+  DevHeader* hd = static_cast<DevHeader*>(d_workspace);
+  DevHeader h;
+  if ((e = cudaMemcpy(&h, hd, sizeof(h), cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_code(e);
+  if (h.bad_inv) return TWOPACO_EBADBASE;
+  if (h.timeout) return TWOPACO_ETIMEOUT;
+  if (h.overflow) return TWOPACO_EOVERFLOW;
+  if (!h.packed || next_round < 1 || (uint64_t)next_round > h.rounds) return TWOPACO_EINVAL;
+  const int rounds = (int)h.rounds;
+  if (bytes < checkpoint_bytes(h.m, rounds, h.q)) return TWOPACO_EINVAL;
+  if (launch_digest(hd, h.packed, h.packed_words, s) < 0) return TWOPACO_ECUDA;
+  unsigned long long digest = 0;
+  if ((e = cudaMemcpyAsync(&digest, &hd->input_digest, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_code(e);
+  CheckpointHead c{};
+  std::memcpy(c.magic, kCheckpointMagic, 8);
+  c.version = 1;
+  c.k = h.k;
+  c.rounds = rounds;
+  c.hashes = h.hashes;
+  c.both = h.both;
+  c.split = h.nmask ? 1 : 0;
+  c.next_round = next_round;
+  c.lg_blocks = h.lg_blocks;
+  c.m = h.m;
+  c.n_seqs = h.n_seqs;
+  c.q = h.q;
+  c.bitmap_words = h.bitmap_words;
+  c.input_digest = digest;
+  c.positions = h.positions;
+  c.pass1_kept = h.pass1_kept;
+  c.pass2_kept = h.pass2_kept;
+  c.table_max = h.table_max;
+  char* out = static_cast<char*>(host_dst);
+  std::memcpy(out, &c, sizeof(c));
+  out += sizeof(c);
+  if ((e = cudaMemcpy(out, h.cuts, 4 * ((uint64_t)rounds + 1), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_code(e);
+  out += 4 * ((uint64_t)rounds + 1);
+  if (rounds > 1) {
+    if ((e = cudaMemcpy(out, h.bins, 4 * h.q, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_code(e);
+    out += 4 * h.q;
+  }
+  if (h.bitmap_words && (e = cudaMemcpy(out, h.cfinal, 4 * h.bitmap_words, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_code(e);
+  return TWOPACO_OK;
+}
+
+int twopaco_checkpoint_load(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_seqs,
+                            uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
+                            const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
+                            const void* host_src, uint64_t bytes, int* next_round) {
+  const twopaco_options o = resolve(opt);
+  int rc = validate(n_seqs, k, filter_bits, rounds, o);
+  if (rc) return rc;
+  if (validate_size(total_bases) || !host_src || !next_round) return TWOPACO_EINVAL;
+  if (total_bases > 0 && (n_seqs == 0 || !d_bases || !d_offsets)) return TWOPACO_EINVAL;
+  if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) % kAlign)) return TWOPACO_EINVAL;
+  const Layout L = layout(total_bases, n_seqs, k, filter_bits, rounds, o);
+  if (workspace_bytes < L.total) return TWOPACO_EINVAL;
+  if (bytes < sizeof(CheckpointHead)) return TWOPACO_EINVAL;
+  CheckpointHead c;
+  std::memcpy(&c, host_src, sizeof(c));
+  const uint64_t q = o.partition_bins;
+  if (std::memcmp(c.magic, kCheckpointMagic, 8) || c.version != 1 || c.k != k || c.rounds != rounds ||
+      c.hashes != o.hashes || c.both != o.both_strands || c.split != o.split_at_n ||
+      c.lg_blocks != log2_exact(filter_bits / 256) || c.m != total_bases || c.n_seqs != n_seqs ||
+      c.q != q || c.bitmap_words != L.bitmap_words || c.next_round < 1 || c.next_round > rounds ||
+      bytes < checkpoint_bytes(total_bases, rounds, q))
+    return TWOPACO_EINVAL;
+  // the input, packed again, must be the one the checkpoint was taken on
+  const RunView v = make_view(d_bases, d_offsets, n_seqs, total_bases, k, filter_bits, rounds, o, L,
+                              d_workspace, nullptr, nullptr, 0);
+  cudaStream_t s = static_cast<cudaStream_t>(o.cuda_stream);
+  DevHeader* hd = v.hdr;
+  if (launch_init(v, s) < 0 || launch_pack(v, s) < 0) return TWOPACO_ECUDA;
+  if (launch_digest(hd, v.packed, v.packed_words, s) < 0) return TWOPACO_ECUDA;
+  unsigned long long digest = 0, bad = 0;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(&digest, &hd->input_digest, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&bad, &hd->bad_inv, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_code(e);
+  if (bad) return TWOPACO_EBADBASE;
+  if (digest != c.input_digest) return TWOPACO_EINVAL;
+  const char* in = static_cast<const char*>(host_src) + sizeof(c);
+  if ((e = cudaMemcpyAsync(v.cuts, in, 4 * ((uint64_t)rounds + 1), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_code(e);
+  in += 4 * ((uint64_t)rounds + 1);
+  if (rounds > 1) {
+    if ((e = cudaMemcpyAsync(v.bins, in, 4 * q, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_code(e);
+    in += 4 * q;
+  }
+  if (v.bitmap_words &&
+      (e = cudaMemcpyAsync(v.cfinal, in, 4 * v.bitmap_words, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_code(e);
+  const unsigned long long counters[3] = {c.positions, c.pass1_kept, c.pass2_kept};
+  if ((e = cudaMemcpyAsync(&hd->positions, counters, sizeof(counters), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&hd->table_max, &c.table_max, 8, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_code(e);
+  *next_round = c.next_round;
+  return TWOPACO_OK;
 }
 
 void twopaco_result_free(twopaco_result* res) {

@@ -44,6 +44,12 @@ struct DevHeader {
   uint32_t* run_rank;
   unsigned long long n_runs;
   unsigned long long run_cap;
+  // what a checkpoint records about the run
+  unsigned long long n_seqs;
+  int hashes;
+  int lg_blocks;
+  unsigned long long packed_words;
+  unsigned long long input_digest;  // written by launch_digest
 };
 
 // Device view of one run: every buffer lives inside the workspace except the
@@ -136,6 +142,10 @@ inline uint64_t cand_record_bytes(int) { return 8; }
 // in twopaco_kernels_wide.cu).
 int launch_round_wide(const RunView& v, int round, int rounds, cudaStream_t s);
 int launch_partition_count_wide(const RunView& v, cudaStream_t s);
+
+// Sum over the packed input words w of mix64(index << 32 ^ w), into
+// hdr->input_digest (order-free, so the same input always gives the same value).
+int launch_digest(DevHeader* hdr_dev, const uint32_t* packed, uint64_t words, cudaStream_t s);
 
 // Process-wide count of kernels launched by the library.
 void count_launches(int n);

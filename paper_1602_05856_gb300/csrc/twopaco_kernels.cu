@@ -855,6 +855,10 @@ __global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
     h->runs = v.runs;
     h->run_rank = v.run_rank;
     h->run_cap = v.run_cap;
+    h->n_seqs = v.n_seqs;
+    h->hashes = v.hashes;
+    h->lg_blocks = v.lg_blocks;
+    h->packed_words = v.packed_words;
   }
   const bool vec = (reinterpret_cast<uintptr_t>(v.bases) & 15) == 0;
   const uint64_t stride = (uint64_t)gridDim.x * kBlock * 4;
@@ -892,6 +896,15 @@ __global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
   zero(v.lc_bits, (1ull << v.lc_log2) / 8);
   zero(v.cfinal, (v.bitmap_words + 3) / 4 * 16);
   zero(v.tile_prefix, (v.n_tiles + 1) / 2 * 16);
+}
+
+// Digest of the packed input (checkpoints record it and check it on resume).
+__global__ void __launch_bounds__(kBlock) digest_kernel(DevHeader* hdr, const uint32_t* packed, uint64_t words) {
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+  unsigned long long d = 0;
+  for (uint64_t w = (uint64_t)blockIdx.x * kBlock + threadIdx.x; w < words; w += stride)
+    d += mix64((w << 32) ^ packed[w]);
+  block_add(d, &hdr->input_digest);
 }
 
 // ---------------------------------------------------------------------------
@@ -1817,6 +1830,12 @@ unsigned long long launches_so_far() { return g_launches.load(); }
 
 int launch_init(const RunView& v, cudaStream_t s) {
   return cudaMemsetAsync(v.hdr, 0, sizeof(DevHeader), s) == cudaSuccess ? 0 : -1;
+}
+
+int launch_digest(DevHeader* hdr_dev, const uint32_t* packed, uint64_t words, cudaStream_t s) {
+  if (cudaMemsetAsync(&hdr_dev->input_digest, 0, sizeof(unsigned long long), s) != cudaSuccess) return -1;
+  digest_kernel<<<grid_for(digest_kernel, kBlock, words), kBlock, 0, s>>>(hdr_dev, packed, words);
+  return done(1);
 }
 
 int launch_pack(const RunView& v, cudaStream_t s) {

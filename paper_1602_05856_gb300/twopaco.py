@@ -98,6 +98,17 @@ def _lib() -> ctypes.CDLL:
         L.twopaco_run_device.argtypes = [P, P, U64, U64, I, U64, I, ctypes.POINTER(_Options), P, U64,
                                          P, P, U64]
         L.twopaco_run_device.restype = I
+        L.twopaco_run_rounds.argtypes = [P, P, U64, U64, I, U64, I, ctypes.POINTER(_Options), P, U64,
+                                         I, I, P, P, U64]
+        L.twopaco_run_rounds.restype = I
+        L.twopaco_checkpoint_bytes.argtypes = [U64, U64, I, U64, I, ctypes.POINTER(_Options),
+                                               ctypes.POINTER(U64)]
+        L.twopaco_checkpoint_bytes.restype = I
+        L.twopaco_checkpoint_save.argtypes = [P, I, P, U64, P]
+        L.twopaco_checkpoint_save.restype = I
+        L.twopaco_checkpoint_load.argtypes = [P, P, U64, U64, I, U64, I, ctypes.POINTER(_Options), P,
+                                              U64, P, U64, ctypes.POINTER(I)]
+        L.twopaco_checkpoint_load.restype = I
         L.twopaco_run_device_noalloc.argtypes = [P, P, U64, U64, I, U64, I, ctypes.POINTER(_Options),
                                                  P, P, U64, ctypes.POINTER(_Stats)]
         L.twopaco_run_device_noalloc.restype = I
@@ -310,6 +321,55 @@ def twopaco_run_device(d_bases: int, d_offsets: int, n_seqs: int, total_bases: i
         raise TwopacoError(rc, "twopaco_run_device")
 
 
+def twopaco_run_rounds(d_bases: int, d_offsets: int, n_seqs: int, total_bases: int, k: int,
+                       filter_bits: int, rounds: int, options: Optional[Options], d_workspace: int,
+                       workspace_bytes: int, round_begin: int, round_end: int, d_out_offsets: int,
+                       d_out_positions: int, out_capacity: int) -> None:
+    opt = (options or Options())._c()
+    rc = _lib().twopaco_run_rounds(d_bases or None, d_offsets or None, int(n_seqs), int(total_bases),
+                                   int(k), int(filter_bits), int(rounds), ctypes.byref(opt),
+                                   d_workspace or None, int(workspace_bytes), int(round_begin),
+                                   int(round_end), d_out_offsets or None, d_out_positions or None,
+                                   int(out_capacity))
+    if rc != OK:
+        raise TwopacoError(rc, "twopaco_run_rounds")
+
+
+def twopaco_checkpoint_bytes(total_bases: int, n_seqs: int, k: int, filter_bits: int, rounds: int,
+                             options: Optional[Options] = None) -> int:
+    out = ctypes.c_uint64(0)
+    opt = (options or Options())._c()
+    rc = _lib().twopaco_checkpoint_bytes(int(total_bases), int(n_seqs), int(k), int(filter_bits),
+                                         int(rounds), ctypes.byref(opt), ctypes.byref(out))
+    if rc != OK:
+        raise TwopacoError(rc, "twopaco_checkpoint_bytes")
+    return int(out.value)
+
+
+def twopaco_checkpoint_save(d_workspace: int, next_round: int, nbytes: int,
+                            cuda_stream: int = 0) -> bytes:
+    buf = ctypes.create_string_buffer(max(int(nbytes), 1))
+    rc = _lib().twopaco_checkpoint_save(d_workspace or None, int(next_round), buf, int(nbytes),
+                                        cuda_stream or None)
+    if rc != OK:
+        raise TwopacoError(rc, "twopaco_checkpoint_save")
+    return buf.raw[:int(nbytes)]
+
+
+def twopaco_checkpoint_load(d_bases: int, d_offsets: int, n_seqs: int, total_bases: int, k: int,
+                            filter_bits: int, rounds: int, options: Optional[Options],
+                            d_workspace: int, workspace_bytes: int, blob: bytes) -> int:
+    opt = (options or Options())._c()
+    nxt = ctypes.c_int(0)
+    rc = _lib().twopaco_checkpoint_load(d_bases or None, d_offsets or None, int(n_seqs),
+                                        int(total_bases), int(k), int(filter_bits), int(rounds),
+                                        ctypes.byref(opt), d_workspace or None, int(workspace_bytes),
+                                        blob, len(blob), ctypes.byref(nxt))
+    if rc != OK:
+        raise TwopacoError(rc, "twopaco_checkpoint_load")
+    return int(nxt.value)
+
+
 def twopaco_run_device_noalloc(d_bases: int, d_offsets: int, n_seqs: int, total_bases: int, k: int,
                                filter_bits: int, rounds: int, options: Optional[Options],
                                d_out_offsets: int, d_out_positions: int, out_capacity: int,
@@ -409,6 +469,28 @@ class DeviceBuild:
                            self.n_seqs, self.total_bases, self.k, self.filter_bits, self.rounds, opt,
                            self.ws_ptr, self.ws_bytes, self.out_offsets.data_ptr(),
                            self.out_positions.data_ptr(), self.capacity)
+
+    def run_rounds(self, round_begin: int, round_end: int, stream=None) -> None:
+        """Rounds [round_begin, round_end) of the run (twopaco_run_rounds)."""
+        opt = dataclasses.replace(self.options, cuda_stream=self._stream(stream))
+        twopaco_run_rounds(self.bases.data_ptr() if self.total_bases else 0, self.offsets.data_ptr(),
+                           self.n_seqs, self.total_bases, self.k, self.filter_bits, self.rounds, opt,
+                           self.ws_ptr, self.ws_bytes, round_begin, round_end,
+                           self.out_offsets.data_ptr(), self.out_positions.data_ptr(), self.capacity)
+
+    def checkpoint(self, next_round: int, stream=None) -> bytes:
+        """The state after the rounds before next_round, as bytes (twopaco_checkpoint_save)."""
+        n = twopaco_checkpoint_bytes(self.total_bases, self.n_seqs, self.k, self.filter_bits,
+                                     self.rounds, self.options)
+        return twopaco_checkpoint_save(self.ws_ptr, next_round, n, self._stream(stream))
+
+    def restore(self, blob: bytes, stream=None) -> int:
+        """Load a checkpoint of this input into this workspace; returns the round to continue with."""
+        opt = dataclasses.replace(self.options, cuda_stream=self._stream(stream))
+        return twopaco_checkpoint_load(self.bases.data_ptr() if self.total_bases else 0,
+                                       self.offsets.data_ptr(), self.n_seqs, self.total_bases, self.k,
+                                       self.filter_bits, self.rounds, opt, self.ws_ptr, self.ws_bytes,
+                                       blob)
 
     def capture(self) -> None:
         """Capture this run as a CUDA graph (twopaco_plan_create); run() then replays it."""

@@ -70,3 +70,17 @@ def test_split_and_long_k_workspace():
     assert plain < small < split
     assert T.twopaco_workspace_size(1 << 20, 4, 100, 1 << 20, 1) > 0
     assert T.twopaco_workspace_size(1 << 20, 4, 127, 1 << 20, 1) > 0
+
+
+def test_checkpoint_sizes_and_round_range_checks():
+    from paper_1602_05856_gb300 import build, twopaco as T
+    build.build()
+    m = 1 << 20
+    one = T.twopaco_checkpoint_bytes(m, 3, 25, 1 << 20, 1)
+    four = T.twopaco_checkpoint_bytes(m, 3, 25, 1 << 20, 4, T.Options(partition_bins=1024))
+    assert one >= m // 8 and four == one + 3 * 4 + 1024 * 4
+    for b, e in ((-1, 1), (0, 0), (2, 1), (0, 5)):  # rounds = 4
+        with pytest.raises(T.TwopacoError) as err:
+            T.twopaco_run_rounds(0, 0, 0, 0, 25, 1 << 20, 4, T.Options(partition_bins=64), 0, 0,
+                                 b, e, 0, 0, 0)
+        assert err.value.code == T.EINVAL
