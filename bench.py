@@ -314,10 +314,14 @@ def run_ours(args, world, rank, local):
 
     # roofline of the dominant kernel
     table_bytes = st["table_slots"] * (8 if K <= 27 else 16 if K <= 31 else 32)
-    top = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    # the kernel with the largest share among those with a work model
+    modelled = [kv for kv in prof.items() if kernel_work(kv[0], st, m, n, table_bytes)[0] is not None]
+    top = max(modelled or prof.items(), key=lambda kv: kv[1]["ms"])
     name, rec = top
     per_launch_ms = rec["ms"] / rec["launches"]
     amount, kind = kernel_work(name, st, m, n, table_bytes)
+    if amount is None:
+        amount, kind = 0.0, "hbm"
     peaks_json = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = float(peaks_json.get("hbm_gbs", 6800.0))

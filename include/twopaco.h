@@ -64,7 +64,7 @@ typedef struct twopaco_options {
   uint32_t partition_bins; /* q of the rounds heuristic, power of two (65536) */
   uint64_t table_slots;    /* pass-2 table capacity in slots; 0 = automatic */
   uint64_t candidate_records; /* pass-2 candidate list size in 8-byte units; 0 =
-                                 automatic (a quarter of a round's positions). It
+                                 automatic (half a round's positions). It
                                  holds twice as many candidates when the input has
                                  at most 2^32 bases. A round with more candidates
                                  stays correct but slower. */

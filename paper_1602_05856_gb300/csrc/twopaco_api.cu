@@ -101,11 +101,12 @@ Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int roun
   at += align_up(((uint64_t)rounds + 1) * 4);
   L.table = at;
   at += align_up(L.table_slots * table_slot_bytes(k));
-  // candidate list: a quarter of the positions of a round by default; a
+  // candidate list: half the positions of a round in 8-byte units by default
+  // (every position of the round, as 32-bit records, under 2^31 bases); a
   // longer round falls back to walking C_temp
   const uint64_t per_round = (m + (uint64_t)rounds - 1) / (uint64_t)rounds;
   L.cand_cap = o.candidate_records ? o.candidate_records
-                                   : (per_round / 4 > (1u << 16) ? per_round / 4 : (1u << 16));
+                                   : (per_round / 2 > (1u << 16) ? per_round / 2 : (1u << 16));
   L.cands = at;
   at += align_up(L.cand_cap * cand_record_bytes(k));
   // the table slot of every listed candidate (32-bit slot indices), kept by

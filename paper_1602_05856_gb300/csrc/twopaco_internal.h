@@ -107,7 +107,7 @@ struct RunView {
 };
 
 constexpr int kBlock = 256;             // threads per block of the position kernels
-constexpr int kEmitWordsPerThread = 16;
+constexpr int kEmitWordsPerThread = 8;
 constexpr int kEmitTileWords = kBlock * kEmitWordsPerThread;  // bitmap words per emit tile
 constexpr uint64_t kPackPadWords = 16;  // zero words after the packed input (window reads of k <= 127 stay inside)
 constexpr uint32_t kMaxSegments = 65536; // candidate-list segments (probe warps) at most

@@ -1184,7 +1184,7 @@ __global__ void __launch_bounds__(kBlock, 3) pass1_probe_kernel(RunView v, int r
 template <int HB>
 __global__ void __launch_bounds__(kBlock) pass1_probe_desc_kernel(RunView v, int round) {
   static_assert(HB <= 6, "descriptors carry the bases of six bits");
-  constexpr int kRows = kProbeR;
+  constexpr int kRows = 4;  // rows of 32 positions per warp and step (4 measured faster than 8 or 16)
   static_assert(kRows <= 32, "one C_temp word per lane");
   const int lane = threadIdx.x & 31;
   const uint32_t below = (1u << lane) - 1u;
@@ -1249,9 +1249,9 @@ __global__ void __launch_bounds__(kBlock) pass1_probe_desc_kernel(RunView v, int
   if (round == 0) block_add(valid_n, &v.hdr->positions);
 }
 
-constexpr double kTableLoad = 2.0;
+constexpr double kTableLoad = 2.0;  // table slots per estimated distinct candidate
 // pass-2 list work: parts of about this many records, at most kMaxParts per segment
-constexpr unsigned long long kPartRecords = 32, kMaxParts = 4096;  // table slots per estimated distinct candidate
+constexpr unsigned long long kPartRecords = 128, kMaxParts = 4096;
 
 // Size the pass-2 table of this round: twice the number of distinct
 // candidate k-mers, estimated by linear counting (Whang, Vander-Zanden &
@@ -1343,12 +1343,13 @@ __device__ __forceinline__ uint64_t list_at(const RunView& v, uint64_t i, bool* 
 // grid that is resident all at once. fn(i) runs for list index i.
 template <typename F>
 __device__ __forceinline__ void for_listed(const RunView& v, F&& fn) {
+  // 32-bit arithmetic: at most kMaxSegments segments of at most kMaxParts parts
   const uint32_t parts = *(volatile unsigned int*)&v.hdr->list_parts;
-  const uint64_t pairs = (uint64_t)v.n_segments * parts;
-  const uint64_t warps = (uint64_t)gridDim.x * (kBlock / 32);
+  const uint32_t pairs = v.n_segments * parts;
+  const uint32_t warps = gridDim.x * (kBlock / 32);
   const uint32_t lane = threadIdx.x & 31;
-  for (uint64_t w = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) >> 5; w < pairs; w += warps) {
-    const uint32_t sgm = (uint32_t)(w / parts), part = (uint32_t)(w % parts);
+  for (uint32_t w = (blockIdx.x * kBlock + threadIdx.x) >> 5; w < pairs; w += warps) {
+    const uint32_t sgm = w / parts, part = w - sgm * parts;
     const uint32_t n = __ldcg(v.seg_count + sgm);
     const uint64_t first = (uint64_t)sgm * v.seg_cap;
     for (uint32_t j = part * 32 + lane; j < n; j += 32 * parts) fn(first + j);
