@@ -92,6 +92,11 @@ struct Timed {
 // bases) in the first-pass kernels and the partition pre-pass.
 constexpr int kInsertR = 16;
 constexpr int kProbeR = 8;
+// Loads issued one step ahead (measured: the probe's descriptors and the
+// classify's records gain; the second-pass insert's records lose).
+constexpr bool kProbePrefetch = true;
+constexpr bool kInsertPrefetch = false;
+constexpr bool kClassifyPrefetch = true;
 constexpr int kR = 8;  // partition pre-pass
 
 // ---------------------------------------------------------------------------
@@ -1194,17 +1199,35 @@ __global__ void __launch_bounds__(kBlock) pass1_probe_desc_kernel(RunView v, int
   uint64_t* seg = v.cands + (uint64_t)warp_id * v.seg_cap;
   uint32_t* seg32 = reinterpret_cast<uint32_t*>(v.cands) + (uint64_t)warp_id * v.seg_cap;
   uint64_t seg_used = 0;
-  for (uint64_t wbase = ((uint64_t)blockIdx.x * kBlock + (threadIdx.x & ~31u)) * kRows; wbase < v.m;
-       wbase += stride) {
+  // the descriptors of a step are loaded one step ahead (kProbePrefetch), so
+  // that their stream overlaps the previous step's filter loads
+  uint64_t dn[kRows];
+  const uint64_t wfirst = ((uint64_t)blockIdx.x * kBlock + (threadIdx.x & ~31u)) * kRows;
+  if (kProbePrefetch) {
+#pragma unroll
+    for (int q = 0; q < kRows; ++q) {
+      const uint64_t p = wfirst + 32 * q + lane;
+      dn[q] = p < v.m ? __ldcs(v.desc + p) : 0ull;
+    }
+  }
+  for (uint64_t wbase = wfirst; wbase < v.m; wbase += stride) {
     uint64_t d[kRows], word[kRows];
 #pragma unroll
     for (int q = 0; q < kRows; ++q) {
       const uint64_t p = wbase + 32 * q + lane;
-      d[q] = p < v.m ? __ldcs(v.desc + p) : 0ull;
+      if (kProbePrefetch) d[q] = dn[q];
+      else d[q] = p < v.m ? __ldcs(v.desc + p) : 0ull;
     }
 #pragma unroll
     for (int q = 0; q < kRows; ++q)
       if ((d[q] & (kDescActive | kDescSentinel)) == kDescActive) word[q] = __ldcg(v.filter + (uint32_t)d[q]);
+    if (kProbePrefetch) {
+#pragma unroll
+      for (int q = 0; q < kRows; ++q) {
+        const uint64_t p = wbase + stride + 32 * q + lane;
+        dn[q] = p < v.m ? __ldcs(v.desc + p) : 0ull;
+      }
+    }
     uint32_t my_word = 0;
 #pragma unroll
     for (int q = 0; q < kRows; ++q) {
@@ -1356,6 +1379,38 @@ __device__ __forceinline__ void for_listed(const RunView& v, F&& fn) {
   }
 }
 
+// for_listed that reads each record one ahead: fn(i, g, sentinel, slot)
+// gets list index i with its position (and with SLOT its kept table slot)
+// already loaded, while the lane's next record is in flight.
+template <bool SLOT, typename F>
+__device__ __forceinline__ void for_listed_ahead(const RunView& v, bool last_use, F&& fn) {
+  const uint32_t parts = *(volatile unsigned int*)&v.hdr->list_parts;
+  const uint32_t pairs = v.n_segments * parts;
+  const uint32_t warps = gridDim.x * (kBlock / 32);
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t row = 32 * parts;
+  for (uint32_t w = (blockIdx.x * kBlock + threadIdx.x) >> 5; w < pairs; w += warps) {
+    const uint32_t sgm = w / parts, part = w - sgm * parts;
+    const uint32_t n = __ldcg(v.seg_count + sgm);
+    const uint64_t first = (uint64_t)sgm * v.seg_cap;
+    uint32_t j = part * 32 + lane;
+    bool sent = false;
+    uint64_t g = j < n ? list_at(v, first + j, &sent, last_use) : 0;
+    uint32_t slot = (SLOT && j < n) ? __ldcs(v.cand_slot + first + j) : 0u;
+    while (j < n) {
+      const uint32_t jn = j + row;
+      bool sent_n = false;
+      const uint64_t gn = jn < n ? list_at(v, first + jn, &sent_n, last_use) : 0;
+      const uint32_t slot_n = (SLOT && jn < n) ? __ldcs(v.cand_slot + first + jn) : 0u;
+      fn(first + j, g, sent, slot);
+      j = jn;
+      g = gn;
+      sent = sent_n;
+      slot = slot_n;
+    }
+  }
+}
+
 // Algorithm 1, insert loop, second pass: every candidate ORs its in/out bases
 // (or the sentinel bit) into the exact table entry of its k-mer. Reads the
 // candidate list and keeps the slot of each listed candidate for the probe
@@ -1364,15 +1419,22 @@ template <int KW, int TS>
 __global__ void __launch_bounds__(kBlock) pass2_insert_kernel(RunView v) {
   const uint64_t cap = *(volatile unsigned long long*)&v.hdr->table_slots;
   if (*(volatile unsigned int*)&v.hdr->round_listed) {
-    for_listed(v, [&](uint64_t i) {
-      bool sent;
-      const uint64_t g = list_at(v, i, &sent, false);
+    auto insert_one = [&](uint64_t i, uint64_t g, bool sent, uint32_t) {
       OccT<KW> oc;
       read_listed<KW>(v, g, sent, &oc);
       const uint64_t slot = insert_occurrence<KW, TS>(v, cap, oc, g);
       if (slot == kNoSlot) v.hdr->overflow = 1;
       if (v.cand_slot) v.cand_slot[i] = slot == kNoSlot ? 0xFFFFFFFFu : (uint32_t)slot;
-    });
+    };
+    if (kInsertPrefetch) {
+      for_listed_ahead<false>(v, false, insert_one);
+    } else {
+      for_listed(v, [&](uint64_t i) {
+        bool sent;
+        const uint64_t g = list_at(v, i, &sent, false);
+        insert_one(i, g, sent, 0u);
+      });
+    }
     return;
   }
   const uint64_t stride = (uint64_t)gridDim.x * kBlock;
@@ -1401,18 +1463,26 @@ __global__ void __launch_bounds__(kBlock) pass2_classify_kernel(RunView v) {
     }
   };
   if (*(volatile unsigned int*)&v.hdr->round_listed) {
-    for_listed(v, [&](uint64_t i) {
-      bool sent;
-      const uint64_t g = list_at(v, i, &sent, true);
+    auto classify_one = [&](uint64_t i, uint64_t g, bool sent, uint32_t slot) {
       if (v.cand_slot) {
-        const uint32_t slot = __ldcs(v.cand_slot + i);
         mark(g, slot == 0xFFFFFFFFu ? -1 : table_mask<TS>(v, slot));
       } else {
         OccT<KW> oc;
         read_listed<KW>(v, g, sent, &oc);
         mark(g, find_occurrence<KW, TS>(v, cap, oc));
       }
-    });
+    };
+    if (kClassifyPrefetch && v.cand_slot) {
+      for_listed_ahead<true>(v, true, classify_one);
+    } else if (kClassifyPrefetch) {
+      for_listed_ahead<false>(v, true, classify_one);
+    } else {
+      for_listed(v, [&](uint64_t i) {
+        bool sent;
+        const uint64_t g = list_at(v, i, &sent, true);
+        classify_one(i, g, sent, v.cand_slot ? __ldcs(v.cand_slot + i) : 0u);
+      });
+    }
   } else {
     const uint64_t stride = (uint64_t)gridDim.x * kBlock;
     for (uint64_t g = (uint64_t)blockIdx.x * kBlock + threadIdx.x; g < v.m; g += stride) {
