@@ -325,13 +325,13 @@ int twopaco_edges_device(const void* d_workspace, const uint64_t* d_offsets, uin
   return rc < 0 ? TWOPACO_ECUDA : TWOPACO_OK;
 }
 
-int twopaco_read_stats(const void* d_workspace, void* cuda_stream, twopaco_stats* stats) {
-  if (!d_workspace || !stats) return TWOPACO_EINVAL;
-  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
-  if (e != cudaSuccess) return cuda_code(e);
-  DevHeader h;
-  e = cudaMemcpy(&h, d_workspace, sizeof(h), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_code(e);
+}  // extern "C"
+
+namespace twopaco {
+namespace {
+
+// The counters and failure flags of a run, from a copy of its header.
+int stats_from_header(const DevHeader& h, twopaco_stats* stats) {
   stats->positions = h.positions;
   stats->pass1_marks = h.pass1_kept;
   stats->pass2_marks = h.pass2_kept;
@@ -343,6 +343,21 @@ int twopaco_read_stats(const void* d_workspace, void* cuda_stream, twopaco_stats
   if (h.timeout) return TWOPACO_ETIMEOUT;
   if (h.overflow) return TWOPACO_EOVERFLOW;
   return TWOPACO_OK;
+}
+
+}  // namespace
+}  // namespace twopaco
+
+extern "C" {
+
+int twopaco_read_stats(const void* d_workspace, void* cuda_stream, twopaco_stats* stats) {
+  if (!d_workspace || !stats) return TWOPACO_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_code(e);
+  DevHeader h;
+  e = cudaMemcpy(&h, d_workspace, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_code(e);
+  return stats_from_header(h, stats);
 }
 
 int twopaco_read_state(const void* d_workspace, int which, void* host_dst, uint64_t bytes,
@@ -699,7 +714,9 @@ void twopaco_plan_destroy(twopaco_plan* p) {
 
 struct twopaco_context {
   int device = 0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;  // copies and kernels (spreading the copies over more streams
+                                  // measured slower: one already fills the host link)
+  twopaco::DevHeader* h_hdr = nullptr;  // pinned: the last run's header
   uint8_t* d_bases = nullptr;
   uint64_t cap_bases = 0;
   uint64_t* d_off = nullptr;
@@ -765,8 +782,9 @@ int twopaco_context_create(twopaco_context** ctx) {
   if (!c) return TWOPACO_ENOMEM;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_hdr, sizeof(twopaco::DevHeader));
   if (e != cudaSuccess) {
-    delete c;
+    twopaco_context_destroy(c);
     return cuda_code(e);
   }
   *ctx = c;
@@ -791,7 +809,8 @@ void twopaco_context_destroy(twopaco_context* c) {
   cudaFree(c->d_edges);
   cudaFreeHost(c->h_edge_off);
   cudaFreeHost(c->h_edges);
-  cudaStreamDestroy(c->stream);
+  cudaFreeHost(c->h_hdr);
+  if (c->stream) cudaStreamDestroy(c->stream);
   cudaSetDevice(prev);
   delete c;
 }
@@ -849,8 +868,11 @@ int twopaco_build_ctx(twopaco_context* c, const char* const* seqs, const uint64_
                             c->d_out_off, c->d_pos, positions);
     if (rc) return finish(rc);
     e = cudaMemcpyAsync(c->h_out_off, c->d_out_off, (n_seqs + 1) * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->h_hdr, c->d_ws, sizeof(DevHeader), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return finish(cuda_code(e));
-    rc = twopaco_read_stats(c->d_ws, c->stream, &st);
+    rc = stats_from_header(*c->h_hdr, &st);
     if (rc != TWOPACO_EOVERFLOW || attempt >= 4) break;
     o.table_slots = layout(m, n_seqs, k, filter_bits, rounds, o).table_slots * 4;
   }
