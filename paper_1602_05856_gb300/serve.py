@@ -104,21 +104,38 @@ class GpuSlot(Slot):
     def held_bytes(self) -> int:
         return int(sum(t.numel() for t in self.buf.values()))
 
+    @staticmethod
+    def _sizes(req: Request) -> Dict[str, int]:
+        n, m = len(req.seqs), req.bases
+        return {"n": n, "m": m, "cap": max(req.positions_upper(), 1),
+                "ws": twopaco.twopaco_workspace_size(m, n, req.k, req.filter_bits, req.rounds,
+                                                     req.options())}
+
+    def reserve(self, reqs: Sequence[Request]) -> None:
+        """Grow the slot's device and pinned buffers for the largest of reqs up
+        front, so that serving them allocates nothing (buffers stay resident)."""
+        for r in reqs:
+            z = self._sizes(r)
+            n, m = z["n"], z["m"]
+            self._grow_pinned("input", m + 8 * (n + 1))
+            self._grow_pinned("out_offsets", 8 * (n + 1))
+            self._grow_pinned("out_positions", 8 * z["cap"])
+            self._grow("input", m + 8 * (n + 1) + 16)
+            self._grow("workspace", z["ws"] + 256)
+            self._grow("out_offsets", 8 * (n + 1))
+            self._grow("out_positions", 8 * z["cap"])
+
     def start(self, req: Request) -> None:
         torch = self.torch
-        n = len(req.seqs)
-        lens = np.array([s.size for s in req.seqs], dtype=np.uint64)
+        z = self._sizes(req)
+        n, m, cap, ws_bytes = z["n"], z["m"], z["cap"], z["ws"]
         off = np.zeros(n + 1, dtype=np.uint64)
-        np.cumsum(lens, out=off[1:])
-        m = int(off[-1])
-        cap = max(req.positions_upper(), 1)
-        ws_bytes = twopaco.twopaco_workspace_size(m, n, req.k, req.filter_bits, req.rounds,
-                                                  req.options())
+        np.cumsum(np.array([s.size for s in req.seqs], dtype=np.uint64), out=off[1:])
         # pinned staging of the request's input, copied on the slot's stream
         host = self._grow_pinned("input", m + 8 * (n + 1))
         hv = host.numpy()
         if m:
-            hv[:m] = np.concatenate([np.asarray(s, dtype=np.uint8) for s in req.seqs])
+            np.concatenate([np.asarray(s, dtype=np.uint8) for s in req.seqs], out=hv[:m])
         hv[m:m + 8 * (n + 1)] = off.view(np.uint8)
         d_in = self._grow("input", m + 8 * (n + 1) + 16)
         ws = self._grow("workspace", ws_bytes + 256)
