@@ -27,6 +27,8 @@ def lib() -> ctypes.CDLL:
         U64 = ctypes.c_uint64
         I = ctypes.c_int
         L.oracle_junctions.argtypes = [P, P, U64, I, I, I, P, P]
+        L.oracle_junctions_parallel.argtypes = [P, P, U64, I, I, I, I, P]
+        L.oracle_junctions_parallel.restype = I
         L.oracle_alg1_exact.argtypes = [P, P, U64, I, I, I, P]
         L.oracle_pass1.argtypes = [P, P, U64, I, I, I, U64, I, U64, U64, U64, P, P]
         L.oracle_partition_cuts.argtypes = [P, U64, I, P]
@@ -87,14 +89,25 @@ def junction_flags(seqs, k: int, both_strands: bool = True,
     return flags[:m], off, int(nd.value)
 
 
-def junctions(seqs, k: int, both_strands: bool = True, split_n: bool = False) -> List[np.ndarray]:
+def junctions(seqs, k: int, both_strands: bool = True, split_n: bool = False,
+              threads: int = 1) -> List[np.ndarray]:
     """Sorted junction positions of every string, by definition of J(S, k).
 
     With ``split_n`` every N ends its string there (the N-free pieces are the
     strings of the definition); positions stay offsets into the input strings.
+    With ``threads`` > 1 the definition runs split over that many threads
+    (each owns the k-mers of one hash class and scans all input).
     """
-    flags, off, _ = junction_flags(seqs, k, both_strands, split_n)
-    return _split(flags, off)
+    if threads <= 1:
+        flags, off, _ = junction_flags(seqs, k, both_strands, split_n)
+        return _split(flags, off)
+    buf, off = _prep(seqs)
+    m = int(off[-1])
+    flags = np.zeros(max(m, 1), np.uint8)
+    _check(lib().oracle_junctions_parallel(buf.ctypes.data, off.ctypes.data, off.size - 1, k,
+                                           int(both_strands), int(split_n), int(threads),
+                                           flags.ctypes.data))
+    return _split(flags[:m], off)
 
 
 def alg1_exact(seqs, k: int, both_strands: bool = True, marks=None,

@@ -16,7 +16,7 @@ LIB = os.path.join(HERE, "liboracle.so")
 def build(force: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
-    cmd = [os.environ.get("CXX", "g++"), "-std=c++17", "-O2", "-shared", "-fPIC",
+    cmd = [os.environ.get("CXX", "g++"), "-std=c++17", "-O2", "-shared", "-fPIC", "-pthread",
            "-o", LIB + ".tmp", SRC]
     subprocess.run(cmd, check=True)
     os.replace(LIB + ".tmp", LIB)

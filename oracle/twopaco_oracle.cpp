@@ -24,6 +24,13 @@
  *                      PINNED by the tests against the Fig. 1 example, a
  *                      brute-force explicit-graph compactor and invariants.
  *
+ *   oracle_junctions_parallel  The same definition split over P threads:
+ *                      thread p owns the normalized k-mers whose hash is p
+ *                      mod P, scans all input, and decides the positions of
+ *                      its own k-mers (the partition-parallel CPU timing the
+ *                      benchmark reports). PINNED by equality with
+ *                      oracle_junctions for several P.
+ *
  *   oracle_alg1_exact  Algorithm 1 (Filter-Junctions) run naively: E is an
  *                      exact set of normalized (k+1)-mers. With every position
  *                      marked it must return J(S, k) (section "Single Round
@@ -62,6 +69,7 @@
  */
 #include <cstdint>
 #include <cstring>
+#include <thread>
 #include <unordered_map>
 #include <unordered_set>
 #include <vector>
@@ -292,6 +300,68 @@ int junctions_impl(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int 
  * the two sentinel positions 0 and |s| - k untouched (they stay as given).
  * The sentinel test is on the k-mer, not the position.
  */
+// The definition, for the normalized k-mers K with KmerHash(K) % threads ==
+// part only: their degrees, their sentinel status, and the flags of the
+// positions where they occur (no other thread writes those flags).
+template <typename W>
+void junctions_part(const std::vector<uint8_t>& codes, const std::vector<Piece>& S, int k,
+                    int both_strands, int threads, int part, uint8_t* flags) {
+  KmerHash hash;
+  auto mine = [&](const W& key) { return (int)(hash(key) % (size_t)threads) == part; };
+  std::unordered_map<W, Degrees, KmerHash> deg;
+  std::unordered_set<W, KmerHash> sentinels;
+  for (const Piece& pc : S) {
+    const uint64_t s0 = pc.s0, len = pc.len;
+    if (len < (uint64_t)k) continue;
+    for (uint64_t i = 0; i + k <= len; ++i) {
+      W v = word_at<W>(codes, s0 + i, k);
+      W r = both_strands ? reverse_complement(v, k) : v;
+      W key = (both_strands && r < v) ? r : v;
+      if (!mine(key)) continue;
+      Degrees& d = deg[key];
+      const bool has_pred = i >= 1, has_succ = i + k < len;
+      if (key == v) {
+        if (has_pred) d.in |= (uint8_t)(1u << codes[s0 + i - 1]);
+        if (has_succ) d.out |= (uint8_t)(1u << codes[s0 + i + k]);
+      }
+      if (both_strands && key == r) {
+        if (has_succ) d.in |= (uint8_t)(1u << (3 - codes[s0 + i + k]));
+        if (has_pred) d.out |= (uint8_t)(1u << (3 - codes[s0 + i - 1]));
+      }
+    }
+    const W first = normalized(word_at<W>(codes, s0, k), k, both_strands);
+    const W last = normalized(word_at<W>(codes, s0 + len - k, k), k, both_strands);
+    if (mine(first)) sentinels.insert(first);
+    if (mine(last)) sentinels.insert(last);
+  }
+  for (const Piece& pc : S) {
+    const uint64_t s0 = pc.s0, len = pc.len;
+    if (len < (uint64_t)k) continue;
+    for (uint64_t i = 0; i + k <= len; ++i) {
+      W key = normalized(word_at<W>(codes, s0 + i, k), k, both_strands);
+      if (!mine(key)) continue;
+      const Degrees& d = deg[key];
+      flags[s0 + i] = (sentinels.count(key) || popcount4(d.in) > 1 || popcount4(d.out) > 1) ? 1 : 0;
+    }
+  }
+}
+
+template <typename W>
+int junctions_parallel_impl(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
+                            int both_strands, int split_n, int threads, uint8_t* flags) {
+  const uint64_t m = offsets[n];
+  std::vector<uint8_t> codes;
+  int rc = encode_all(seq, m, split_n, &codes);
+  if (rc) return rc;
+  std::memset(flags, 0, m);
+  const std::vector<Piece> S = pieces(offsets, n, codes);
+  std::vector<std::thread> pool;
+  for (int p = 0; p < threads; ++p)
+    pool.emplace_back([&, p] { junctions_part<W>(codes, S, k, both_strands, threads, p, flags); });
+  for (std::thread& t : pool) t.join();
+  return ORACLE_OK;
+}
+
 template <typename W>
 int alg1_impl(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
               int both_strands, int split_n, uint8_t* marks) {
@@ -536,6 +606,16 @@ int oracle_junctions(const uint8_t* seq, const uint64_t* offsets, uint64_t n, in
                      int both_strands, int split_n, uint8_t* flags, uint64_t* n_distinct) {
   if (k >= 1 && k <= 63) return junctions_impl<u128>(seq, offsets, n, k, both_strands, split_n, flags, n_distinct);
   if (k >= 64 && k <= 127) return junctions_impl<U256>(seq, offsets, n, k, both_strands, split_n, flags, n_distinct);
+  return ORACLE_EINVAL;
+}
+
+int oracle_junctions_parallel(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
+                              int both_strands, int split_n, int threads, uint8_t* flags) {
+  if (threads < 1 || threads > 1024) return ORACLE_EINVAL;
+  if (k >= 1 && k <= 63)
+    return junctions_parallel_impl<u128>(seq, offsets, n, k, both_strands, split_n, threads, flags);
+  if (k >= 64 && k <= 127)
+    return junctions_parallel_impl<U256>(seq, offsets, n, k, both_strands, split_n, threads, flags);
   return ORACLE_EINVAL;
 }
 

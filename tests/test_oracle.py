@@ -469,3 +469,18 @@ def test_split_n_long_k():
     seqs = [_with_ns(rng, s, 100) for s in base]
     got = _as_lists(O.junctions(seqs, 100, split_n=True))
     assert got == _brute_split(seqs, 100, True)
+
+
+# --- the partition-parallel form of the definition ---------------------------------
+
+@pytest.mark.parametrize("k,both,split", [(5, True, False), (25, True, True), (31, False, False),
+                                          (63, True, False), (100, True, True)])
+def test_parallel_definition_equals_single_thread(k, both, split):
+    rng = np.random.default_rng(k + 7 * both)
+    seqs = [bytes(s).decode() for s in G.random_strings(900 + k, 6, k, 20 * k + 400, b"ACGT")]
+    seqs += [bytes(s).decode() for s in G.random_strings(901 + k, 3, 50, 600, b"AC")]
+    if split:
+        seqs = [_with_ns(rng, s, k) for s in seqs]
+    want = _as_lists(O.junctions(seqs, k, both_strands=both, split_n=split))
+    for threads in (2, 3, 8):
+        assert _as_lists(O.junctions(seqs, k, both_strands=both, split_n=split, threads=threads)) == want
