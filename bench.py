@@ -65,6 +65,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--batched", type=int, default=1,
+                   help="1: add the batched leg (62 genomes in one tuned build vs one build per genome)")
     p.add_argument("--serve-requests", type=int, default=60,
                    help="requests of the served leg (Poisson, 20/s); 0 skips it")
     p.add_argument("--workload", default=WORKLOAD, choices=["bacterial_set", "plain_single"],
@@ -213,6 +215,75 @@ def ncu_traffic(workload, kernel):
     return None
 
 
+def batched_leg(T, genomes, dev):
+    """The 62-genome set (310 Mbp) as one build with the autotuner's (b, h), against the
+    same genomes built one at a time (the single-instance path) at the same filter bits per
+    base, both device-resident and timed with CUDA events. The two compute different graphs
+    (one joint graph vs 62 separate ones): this compares throughput, not output."""
+    import torch
+    from paper_1602_05856_gb300 import autotune
+    seqs = genomes.named_set("batched_set")
+    bases, off = genomes.concat(seqs)
+    m = int(off[-1])
+    choice = autotune.tune(seqs, K, budget_bytes=120 << 30, bits_per_base=(4, 8, 16, 32),
+                           hashes=(3, 4, 6), rounds=(1,), sample_fraction=0.1, repeats=2)
+    bpb = choice.bits / m
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        fn()
+        a = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+        b = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+        for i in range(reps):
+            a[i].record(stream)
+            fn()
+            b[i].record(stream)
+        torch.cuda.synchronize()
+        return statistics.mean(x.elapsed_time(y) for x, y in zip(a, b))
+
+    def joint(bits, hashes):
+        run = T.DeviceBuild(bases, off, K, bits, 1, T.Options(hashes=hashes), device=dev)
+        run.capture()
+        ms = timed(run.run, 5)
+        st = run.stats()
+        run.release_plan()
+        return ms, st
+
+    batched_ms, st = joint(choice.bits, choice.hashes)
+    plain_ms, _ = joint(1 << 30, 4)  # the paper's filter size for inputs of this scale, 4 hashes
+    # one genome at a time through twopaco_run_device, on one workspace and one output buffer
+    d_bases = torch.from_numpy(bases).to(dev)
+    lens = [int(off[t + 1] - off[t]) for t in range(len(seqs))]
+    bits_of = [1 << max(8, int(np.ceil(np.log2(max(bpb * ln, 1.0))))) for ln in lens]
+    opts = T.Options(hashes=choice.hashes, cuda_stream=int(stream.cuda_stream))
+    ws_bytes = max(T.twopaco_workspace_size(ln, 1, K, bt, 1, opts) for ln, bt in zip(lens, bits_of))
+    ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
+    ws_ptr = (ws.data_ptr() + 255) // 256 * 256
+    offs = torch.zeros((len(seqs), 2), dtype=torch.int64, device=dev)
+    offs[:, 1] = torch.tensor(lens, dtype=torch.int64)
+    out_off = torch.zeros(2, dtype=torch.int64, device=dev)
+    out_pos = torch.empty(max(lens), dtype=torch.int64, device=dev)
+
+    def per_genome():
+        for t, (ln, bt) in enumerate(zip(lens, bits_of)):
+            T.twopaco_run_device(d_bases.data_ptr() + int(off[t]), offs[t].data_ptr(), 1, ln, K, bt, 1,
+                                 opts, ws_ptr, ws_bytes, out_off.data_ptr(), out_pos.data_ptr(),
+                                 int(out_pos.numel()))
+
+    single_ms = timed(per_genome, 3)
+    return {"genomes": len(seqs), "bases": m, "k": K,
+            "tuned": {"filter_bits": choice.bits, "hashes": choice.hashes, "rounds": choice.rounds,
+                      "trials": len(choice.trials)},
+            "batched_gbps": m / (batched_ms * 1e-3) / 1e9, "batched_ms": batched_ms,
+            "untuned_gbps": m / (plain_ms * 1e-3) / 1e9, "untuned": {"filter_bits": 1 << 30, "hashes": 4},
+            "single_instance_gbps": m / (single_ms * 1e-3) / 1e9, "single_instance_ms": single_ms,
+            "pass1_survivors": st["pass1_marks"] / max(1, st["positions"]),
+            "note": "batched: one joint build of all genomes (one launch per kernel, graph replay) "
+                    "with the tuned (b, h), and untuned with b = 2^30, h = 4; single instance: each "
+                    "genome built alone, back to back (62 separate, far less branched graphs, so "
+                    "throughput only)"}
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_1602_05856_gb300 import build, genomes, twopaco as T
@@ -320,6 +391,8 @@ def run_ours(args, world, rank, local):
                   "request_recipe": "2-7 prefixes of the 7 genomes, log-uniform 0.1-5 Mbp, k 25/31, "
                                     "~8 filter bits per base, 4 hashes"}
 
+    batched = batched_leg(T, genomes, dev) if args.batched and rank == 0 else None
+
     # roofline of the dominant kernel
     table_bytes = st["table_slots"] * (8 if K <= 27 else 16 if K <= 31 else 32)
     # the kernel with the largest share among those with a work model
@@ -381,6 +454,7 @@ def run_ours(args, world, rank, local):
         "roofline": roof,
         "cpu_baseline": cpu,
         "served": served,
+        "batched": batched,
         "clocks": clocks,
         "stats": {k: st[k] for k in ("positions", "pass1_marks", "pass2_marks", "table_slots")},
         "kernels": kernels,
