@@ -225,7 +225,7 @@ def batched_leg(T, genomes, dev):
     seqs = genomes.named_set("batched_set")
     bases, off = genomes.concat(seqs)
     m = int(off[-1])
-    choice = autotune.tune(seqs, K, budget_bytes=120 << 30, bits_per_base=(4, 8, 16, 32),
+    choice = autotune.tune(seqs, K, budget_bytes=120 << 30, bits_per_base=(2, 4, 8, 16),
                            hashes=(3, 4, 6), rounds=(1,), sample_fraction=0.1, repeats=2)
     bpb = choice.bits / m
     stream = torch.cuda.current_stream()

@@ -11,8 +11,9 @@ candidate (b, h), with b scaled so that the filter has the same bits per base
 as it would on the whole input, and keeps the fastest configuration whose
 full-size workspace fits the memory budget, raising the round count only when
 one round does not fit. A scaled-down filter can sit in L2 where the full one
-does not, so the sample misranks large filters: the best few candidates
-(``refine``) are timed again on the whole input before the choice.
+does not, so the sample misranks filters of different sizes: the fastest
+candidate of each filter size (up to ``refine`` sizes) is timed again on the
+whole input before the choice.
 
 Every run goes through the C ABI (``twopaco.DeviceBuild``); nothing here
 computes junctions.
@@ -92,7 +93,7 @@ def tune(seqs: Sequence[np.ndarray], k: int, budget_bytes: Optional[int] = None,
          bits_per_base: Sequence[float] = (4, 8, 16, 32), hashes: Sequence[int] = (3, 4, 6, 8),
          rounds: Sequence[int] = (1, 2, 4, 8, 16), sample_fraction: float = 0.1,
          repeats: int = 3, both_strands: bool = True, device: str = "cuda",
-         refine: int = 3) -> Choice:
+         refine: int = 4) -> Choice:
     """Measure candidate configurations on a sample; return the fastest that fits."""
     seqs = [np.ascontiguousarray(s, dtype=np.uint8) for s in seqs]
     total = sum(int(s.size) for s in seqs)
@@ -123,15 +124,22 @@ def tune(seqs: Sequence[np.ndarray], k: int, budget_bytes: Optional[int] = None,
         if fitting:
             ranked = sorted(fitting, key=lambda t: (t.est_full_ms, t.workspace))
             if refine > 0 and len(ranked) > 1:
+                # the sample's best (h, rounds) for every filter size, fastest sizes first
+                per_size, seen = [], set()
+                for t in ranked:
+                    if t.bits not in seen:
+                        seen.add(t.bits)
+                        per_size.append(t)
+                ranked = per_size[:refine]
                 bases, off = genomes.concat(seqs)
-                for t in ranked[:refine]:  # the sample's estimate, replaced by a full-size time
+                for t in ranked:  # the sample's estimate, replaced by a full-size time
                     run = twopaco.DeviceBuild(bases, off, k, t.bits, t.rounds,
                                               twopaco.Options(hashes=t.hashes,
                                                               both_strands=both_strands),
                                               device=device)
                     t.est_full_ms, _ = _time_run(run, max(1, repeats - 1))
                     del run
-                ranked = sorted(ranked[:refine], key=lambda t: (t.est_full_ms, t.workspace))
+                ranked = sorted(ranked, key=lambda t: (t.est_full_ms, t.workspace))
             best = ranked[0]
             return Choice(best.bits, best.hashes, best.rounds, best.workspace, best.est_full_ms,
                           trials)
