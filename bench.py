@@ -195,18 +195,27 @@ def kernel_work(name, st, m, n_seqs, table_bytes):
     return None, None
 
 
+def kernel_code_digest() -> str:
+    """sha256 of csrc/twopaco_kernels.cu without comments, blank lines and edge whitespace."""
+    import hashlib
+    import re
+    src = open(os.path.join(ROOT, "paper_1602_05856_gb300", "csrc", "twopaco_kernels.cu")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    lines = [re.sub(r"//.*$", "", l).strip() for l in src.splitlines()]
+    return hashlib.sha256("\n".join(l for l in lines if l).encode()).hexdigest()
+
+
 def ncu_traffic(workload, kernel):
     """DRAM bytes per launch of `kernel` on `workload`, from a committed ncu summary.
 
     profiles/dram_traffic_*.md carry lines ``dram-traffic <workload> <kernel> <bytes>
-    sha256:<digest of csrc/twopaco_kernels.cu when captured>``; a figure taken from an
-    older kernel source does not count (None).
+    sha256:<digest of the code of csrc/twopaco_kernels.cu when captured>`` (the digest
+    of the source with its comments and blank lines removed, see kernel_code_digest); a
+    figure taken from older kernel code does not count (None).
     """
-    import hashlib
     import glob
     import re
-    src = os.path.join(ROOT, "paper_1602_05856_gb300", "csrc", "twopaco_kernels.cu")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    digest = kernel_code_digest()
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "dram_traffic_*.md"))):
         for line in open(path):
             m = re.match(r"dram-traffic (\S+) (\S+) (\d+) sha256:([0-9a-f]{64})\s*$", line.strip())

@@ -6,11 +6,12 @@
 // loop, separated by a kernel boundary (the barrier of section
 // "Parallelization Scheme"); then one emit of the junction positions.
 //
-// The first pass visits every position. A thread takes kR consecutive
-// positions and rolls the forward and reverse-complement k-mer words from
-// one to the next, so a warp covers 32 * kR consecutive positions. The
-// second pass visits only the candidates the first pass left, from a compact
-// list.
+// The first pass visits every position. An insert thread takes kInsertR
+// consecutive positions and rolls the forward and reverse-complement k-mer
+// words from one to the next; besides its filter OR it leaves an 8-byte
+// descriptor per position, which the probe streams (4 rows of 32 positions
+// per warp and step) instead of walking again. The second pass visits only
+// the candidates the first pass left, from a compact list.
 //
 // Encoding: A,C,G,T = 0,1,2,3, 16 bases per 32-bit word, first base in the
 // two most significant bits. A k-mer is the integer with its first base most
