@@ -254,3 +254,46 @@ def plant_n_runs(seed: int, seqs: Sequence[np.ndarray], runs_per_mbp: float = 50
                     s[-ln:] = ord("N")
         out.append(s)
     return out
+
+
+def mammal_slice(seed: int = 1605, genome_len: int = 1_000_000, leaves: int = 8,
+                 repeat_share: float = 0.45) -> List[np.ndarray]:
+    """A slice of the mammal-scale configuration: ``leaves`` genomes of about
+    ``genome_len`` bases at the leaves of a seeded random binary tree.
+
+    The ancestor is ``repeat_share`` repeats: copies of a 300 bp family at
+    10-15% divergence each and of a 6 kbp family, 20 copies of the short one
+    per copy of the long one, the counts scaled to reach the share (the
+    configuration's literal counts give 20%, its stated share 45%). Every tree
+    edge mutates with SNPs and 1-10 bp indels at 10:1 and a few inversions or
+    transpositions, at per-edge rates drawn so that two leaves differ by about
+    1-8%. Full size would be 8 x 3 Gbp; the slice keeps the structure.
+    """
+    ss = np.random.SeedSequence(seed)
+    anc_ss, tree_ss = ss.spawn(2)
+    rng = np.random.Generator(np.random.PCG64(anc_ss))
+    anc = random_bases(rng, genome_len, 0.41)
+    unit = int(round(repeat_share * genome_len / (20 * 300 + 6_000)))  # copies of the 6 kbp family
+    long_cons, short_cons = random_bases(rng, 6_000), random_bases(rng, 300)
+    for cons, copies in ((long_cons, unit), (short_cons, 20 * unit)):
+        for _ in range(copies):  # written over the ancestor: its length stays genome_len
+            c = substitute(rng, cons, float(rng.uniform(0.10, 0.15)))
+            at = int(rng.integers(0, max(1, anc.size - c.size)))
+            anc[at:at + c.size] = c[: anc.size - at]
+    # a random binary tree with `leaves` leaves: split the leaf set at random, recursively
+    r = np.random.Generator(np.random.PCG64(tree_ss))
+
+    def evolve(seq: np.ndarray, n: int) -> List[np.ndarray]:
+        if n == 1:
+            return [np.ascontiguousarray(seq, dtype=np.uint8)]
+        left = int(r.integers(1, n))
+        out = []
+        for part in (left, n - left):
+            rate = float(r.uniform(0.002, 0.012))  # per-edge divergence
+            child = substitute(r, seq, rate * 10 / 11)
+            child = indels(r, child, rate / 11, 10)
+            child = structural_variants(r, child, int(r.integers(0, 3)), 1_000, 20_000)
+            out += evolve(child, part)
+        return out
+
+    return evolve(anc, leaves)
