@@ -1,5 +1,6 @@
 // C-ABI layer of the junction-detection library: argument checks, workspace
 // layout, the launch sequence of one run, and the host-to-host build.
+#include <algorithm>
 #include <cstddef>
 #include <cstdlib>
 #include <cstring>
@@ -297,7 +298,7 @@ int twopaco_run_rounds(const uint8_t* d_bases, const uint64_t* d_offsets, uint64
   }
   for (int r = round_begin; r < round_end; ++r)
     if (launch_round(v, r, rounds, s) < 0) return TWOPACO_ECUDA;
-  if (round_end == rounds && launch_emit(v, s) < 0) return TWOPACO_ECUDA;
+  if (round_end == rounds && launch_emit(v, s, round_begin == rounds) < 0) return TWOPACO_ECUDA;
   return TWOPACO_OK;
 }
 
@@ -337,12 +338,22 @@ int stats_from_header(const DevHeader& h, twopaco_stats* stats) {
   stats->pass2_marks = h.pass2_kept;
   stats->table_slots = h.table_max;
   stats->bad_base_index = h.bad_inv ? ~h.bad_inv : ~0ull;
-  stats->overflow = h.overflow;
+  stats->overflow = h.overflow | h.out_overflow;
   stats->timeout = h.timeout;
   if (h.bad_inv) return TWOPACO_EBADBASE;
   if (h.timeout) return TWOPACO_ETIMEOUT;
-  if (h.overflow) return TWOPACO_EOVERFLOW;
+  if (h.overflow || h.out_overflow) return TWOPACO_EOVERFLOW;
   return TWOPACO_OK;
+}
+
+// Output room a host build starts with: every k-mer position up to 2^27 of
+// them (1 GiB), else an eighth of them; a run whose junctions do not fit
+// writes its exact count, and the output is then written again into a buffer
+// of that size (twopaco_run_rounds(..., rounds, rounds, ...)).
+uint64_t first_output_capacity(uint64_t positions) {
+  constexpr uint64_t kAll = 1ull << 27;
+  const uint64_t c = positions <= kAll ? positions : std::max(kAll, positions / 8);
+  return c ? c : 1;
 }
 
 }  // namespace
@@ -587,7 +598,8 @@ int twopaco_build_ex(const char* const* seqs, const uint64_t* lengths, uint64_t 
   if ((e = cudaMalloc(&d_bases, m ? m : 1)) != cudaSuccess) return fail(cuda_code(e));
   if ((e = cudaMalloc(&d_off, (n_seqs + 1) * 8)) != cudaSuccess) return fail(cuda_code(e));
   if ((e = cudaMalloc(&d_out_off, (n_seqs + 1) * 8)) != cudaSuccess) return fail(cuda_code(e));
-  if ((e = cudaMalloc(&d_pos, (positions ? positions : 1) * 8)) != cudaSuccess) return fail(cuda_code(e));
+  uint64_t out_cap = first_output_capacity(positions);
+  if ((e = cudaMalloc(&d_pos, out_cap * 8)) != cudaSuccess) return fail(cuda_code(e));
   for (uint64_t t = 0; t < n_seqs; ++t) {
     if (!lengths[t]) continue;
     e = cudaMemcpyAsync(d_bases + offsets[t], seqs[t], lengths[t], cudaMemcpyHostToDevice, s);
@@ -602,9 +614,27 @@ int twopaco_build_ex(const char* const* seqs, const uint64_t* lengths, uint64_t 
     if ((rc = twopaco_workspace_size(m, n_seqs, k, filter_bits, rounds, &o, &ws))) return fail(rc);
     if ((e = cudaMalloc(&d_ws, ws)) != cudaSuccess) return fail(cuda_code(e));
     rc = twopaco_run_device(d_bases, d_off, n_seqs, m, k, filter_bits, rounds, &o, d_ws, ws,
-                            d_out_off, d_pos, positions);
+                            d_out_off, d_pos, out_cap);
     if (rc) return fail(rc);
     rc = twopaco_read_stats(d_ws, o.cuda_stream, &st);
+    if (rc == TWOPACO_EOVERFLOW) {
+      DevHeader h;
+      if ((e = cudaMemcpy(&h, d_ws, sizeof(h), cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(cuda_code(e));
+      if (!h.overflow && h.out_overflow) {
+        // only the output was too small: it holds the exact count; write it again
+        uint64_t total = 0;
+        if ((e = cudaMemcpy(&total, d_out_off + n_seqs, 8, cudaMemcpyDeviceToHost)) != cudaSuccess)
+          return fail(cuda_code(e));
+        cudaFree(d_pos);
+        d_pos = nullptr;
+        out_cap = total ? total : 1;
+        if ((e = cudaMalloc(&d_pos, out_cap * 8)) != cudaSuccess) return fail(cuda_code(e));
+        rc = twopaco_run_rounds(d_bases, d_off, n_seqs, m, k, filter_bits, rounds, &o, d_ws, ws, rounds,
+                                rounds, d_out_off, d_pos, out_cap);
+        if (rc) return fail(rc);
+        rc = twopaco_read_stats(d_ws, o.cuda_stream, &st);
+      }
+    }
     if (rc != TWOPACO_EOVERFLOW || attempt >= 4) break;
     // The table was too small for this input: grow it and run again.
     const Layout L = layout(m, n_seqs, k, filter_bits, rounds, o);
@@ -849,7 +879,7 @@ int twopaco_build_ctx(twopaco_context* c, const char* const* seqs, const uint64_
   if (validate_size(m)) return finish(TWOPACO_EINVAL);
   if (o.split_at_n && !o.run_capacity) o.run_capacity = count_run_boundaries(seqs, lengths, n_seqs) + 1;
   if ((e = grow_device(&c->d_bases, &c->cap_bases, m)) != cudaSuccess) return finish(cuda_code(e));
-  if ((e = grow_device(&c->d_pos, &c->cap_pos, (positions ? positions : 1) * 8)) != cudaSuccess)
+  if ((e = grow_device(&c->d_pos, &c->cap_pos, first_output_capacity(positions) * 8)) != cudaSuccess)
     return finish(cuda_code(e));
   for (uint64_t t = 0; t < n_seqs; ++t) {
     if (!lengths[t]) continue;
@@ -865,7 +895,7 @@ int twopaco_build_ctx(twopaco_context* c, const char* const* seqs, const uint64_
     if ((e = grow_device(reinterpret_cast<char**>(&c->d_ws), &c->cap_ws, ws)) != cudaSuccess)
       return finish(cuda_code(e));
     rc = twopaco_run_device(c->d_bases, c->d_off, n_seqs, m, k, filter_bits, rounds, &o, c->d_ws, ws,
-                            c->d_out_off, c->d_pos, positions);
+                            c->d_out_off, c->d_pos, c->cap_pos / 8);
     if (rc) return finish(rc);
     e = cudaMemcpyAsync(c->h_out_off, c->d_out_off, (n_seqs + 1) * 8, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess)
@@ -873,6 +903,19 @@ int twopaco_build_ctx(twopaco_context* c, const char* const* seqs, const uint64_
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return finish(cuda_code(e));
     rc = stats_from_header(*c->h_hdr, &st);
+    if (rc == TWOPACO_EOVERFLOW && !c->h_hdr->overflow && c->h_hdr->out_overflow) {
+      // only the output was too small: it holds the exact count; write it again
+      const uint64_t total = c->h_out_off[n_seqs];
+      if ((e = grow_device(&c->d_pos, &c->cap_pos, (total ? total : 1) * 8)) != cudaSuccess)
+        return finish(cuda_code(e));
+      rc = twopaco_run_rounds(c->d_bases, c->d_off, n_seqs, m, k, filter_bits, rounds, &o, c->d_ws, ws,
+                              rounds, rounds, c->d_out_off, c->d_pos, c->cap_pos / 8);
+      if (rc) return finish(rc);
+      e = cudaMemcpyAsync(c->h_hdr, c->d_ws, sizeof(DevHeader), cudaMemcpyDeviceToHost, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      if (e != cudaSuccess) return finish(cuda_code(e));
+      rc = stats_from_header(*c->h_hdr, &st);
+    }
     if (rc != TWOPACO_EOVERFLOW || attempt >= 4) break;
     o.table_slots = layout(m, n_seqs, k, filter_bits, rounds, o).table_slots * 4;
   }

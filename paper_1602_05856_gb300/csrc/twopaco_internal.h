@@ -22,7 +22,7 @@ struct DevHeader {
   unsigned int lc_blocks_done;     // blocks of lc_count finished this round
   unsigned int list_parts;         // pass-2 parts per list segment this round
   unsigned long long emit_ticket;  // next emit tile to claim
-  unsigned int overflow;           // table or output out of room
+  unsigned int overflow;           // the pass-2 table or a boundary list out of room
   unsigned int timeout;            // a bounded wait gave up
   // where the last run left its bitmaps and partition state (for inspection)
   uint32_t* ctemp;
@@ -50,6 +50,8 @@ struct DevHeader {
   int lg_blocks;
   unsigned long long packed_words;
   unsigned long long input_digest;  // written by launch_digest
+  unsigned int out_overflow;        // the output positions did not fit (the offsets are exact)
+  unsigned int pad1;
 };
 
 // Device view of one run: every buffer lives inside the workspace except the
@@ -119,7 +121,7 @@ int launch_init(const RunView& v, cudaStream_t s);  // clears the header
 int launch_pack(const RunView& v, cudaStream_t s);
 int launch_partition(const RunView& v, int rounds, cudaStream_t s);
 int launch_round(const RunView& v, int round, int rounds, cudaStream_t s);
-int launch_emit(const RunView& v, cudaStream_t s);
+int launch_emit(const RunView& v, cudaStream_t s, bool again = false);
 int launch_edges(const DevHeader* hdr_dev, const uint64_t* d_offsets, uint64_t n_seqs,
                  const uint64_t* d_out_offsets, const uint64_t* d_out_positions,
                  uint64_t* d_edge_offsets, void* d_edges, uint64_t edge_capacity, cudaStream_t s);

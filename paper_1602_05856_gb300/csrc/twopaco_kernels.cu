@@ -1681,7 +1681,7 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(RunView v) {
       unsigned long long cnt = prefix_s + (j < (uint64_t)kEmitTileWords ? before_s[j] : total_s);
       if ((g & 31) && w < v.bitmap_words) cnt += __popc(__ldcg(v.cfinal + w) & ((1u << (g & 31)) - 1u));
       v.out_offsets[t] = cnt;
-      if (t == v.n_seqs && cnt > v.out_capacity) v.hdr->overflow = 1;
+      if (t == v.n_seqs && cnt > v.out_capacity) v.hdr->out_overflow = 1;
     }
     __syncthreads();
   }
@@ -1707,7 +1707,7 @@ __global__ void __launch_bounds__(kBlock) emit_offsets_kernel(RunView v) {
     if (tile > 0) cnt += __ldcg(reinterpret_cast<const unsigned long long*>(v.tile_prefix) + (tile - 1)) & kValMask;
     if (g & 31) cnt += __popc(__ldcg(v.cfinal + w) & ((1u << (g & 31)) - 1u));
     v.out_offsets[t] = cnt;
-    if (t == v.n_seqs && cnt > v.out_capacity) v.hdr->overflow = 1;
+    if (t == v.n_seqs && cnt > v.out_capacity) v.hdr->out_overflow = 1;
   }
 }
 
@@ -2076,7 +2076,13 @@ int launch_round(const RunView& v, int round, int rounds, cudaStream_t s) {
   return rc;
 }
 
-int launch_emit(const RunView& v, cudaStream_t s) {
+int launch_emit(const RunView& v, cudaStream_t s, bool again) {
+  // again: a second emit of the same run (into a larger output): its tile
+  // tickets, tile status and output flag start over
+  if (again && (cudaMemsetAsync(v.tile_prefix, 0, (v.n_tiles + 1) * 8, s) != cudaSuccess ||
+                cudaMemsetAsync(&v.hdr->emit_ticket, 0, sizeof(unsigned long long), s) != cudaSuccess ||
+                cudaMemsetAsync(&v.hdr->out_overflow, 0, sizeof(unsigned int), s) != cudaSuccess))
+    return -1;
   if (v.n_tiles) {  // tile status cleared by the pack kernel; writes the offsets too
     Timed t("emit", s);
     emit_kernel<<<grid_for(emit_kernel, kBlock, v.n_tiles * kBlock), kBlock, 0, s>>>(v);

@@ -144,3 +144,23 @@ def test_finished_run_output_from_its_last_checkpoint():
     assert b.restore(blob) == 2
     b.run_rounds(2, 2)  # only writes the output
     _eq(b.result(), a.result())
+
+
+def test_output_too_small_then_written_again():
+    """A run whose output does not fit reports its exact junction count; after a larger
+    buffer is given, twopaco_run_rounds(rounds, rounds) writes the output again."""
+    import torch
+    bases, off = _input()
+    run = _build(25, 3)
+    small = torch.empty(10, dtype=torch.int64, device="cuda")
+    T().twopaco_run_device(run.bases.data_ptr(), run.offsets.data_ptr(), run.n_seqs, run.total_bases,
+                           25, 1 << 20, 3, T().Options(hashes=4, partition_bins=256), run.ws_ptr,
+                           run.ws_bytes, run.out_offsets.data_ptr(), small.data_ptr(), 10)
+    st = run.stats(check=False)
+    assert st["rc"] == T().EOVERFLOW and st["overflow"]
+    total = int(run.out_offsets.cpu().numpy().view(np.uint64)[-1])
+    want = O.junctions(_input(), 25)
+    assert total == sum(w.size for w in want) > 10
+    run.run_rounds(3, 3)  # into the build's own buffer (room for every position)
+    _eq(run.result(), want)
+    assert run.stats()["rc"] == 0

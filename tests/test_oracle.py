@@ -484,3 +484,13 @@ def test_parallel_definition_equals_single_thread(k, both, split):
     want = _as_lists(O.junctions(seqs, k, both_strands=both, split_n=split))
     for threads in (2, 3, 8):
         assert _as_lists(O.junctions(seqs, k, both_strands=both, split_n=split, threads=threads)) == want
+
+
+def test_mammal_slice_generator_is_seeded_and_shaped():
+    a = G.mammal_slice(genome_len=60_000)
+    b = G.mammal_slice(genome_len=60_000)
+    assert len(a) == 8 and all(np.array_equal(x, y) for x, y in zip(a, b))
+    assert all(55_000 < x.size < 65_000 for x in a)
+    assert not all(np.array_equal(a[0], x) for x in a[1:])  # the leaves differ
+    c = G.mammal_slice(seed=7, genome_len=60_000)
+    assert not np.array_equal(a[0], c[0])
