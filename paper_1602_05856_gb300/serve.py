@@ -184,7 +184,9 @@ class ServeReport:
         bases = sum(r.bases for r in self.requests)
         return {"requests": len(self.requests),
                 "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else 0.0,
+                "p95_ms": float(np.percentile(lat, 95) * 1e3) if lat.size else 0.0,
                 "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else 0.0,
+                "max_ms": float(lat.max() * 1e3) if lat.size else 0.0,
                 "mean_ms": float(lat.mean() * 1e3) if lat.size else 0.0,
                 "throughput_gbps": bases / self.wall_s / 1e9 if self.wall_s > 0 else 0.0,
                 "wall_s": self.wall_s}
