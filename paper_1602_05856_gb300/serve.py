@@ -75,17 +75,26 @@ class Slot:
 
 
 class GpuSlot(Slot):
-    """Runs requests on its own CUDA stream with buffers kept between requests."""
+    """Runs requests on its own CUDA stream with buffers kept between requests.
+
+    A request's host work -- staging its strings in pinned memory, waiting for
+    its counts, reading back exactly its junctions -- runs on the slot's own
+    worker thread, so that the scheduler loop never blocks on one request while
+    others finish (numpy copies release the interpreter lock).
+    """
 
     def __init__(self, device: str = "cuda"):
+        import concurrent.futures
         import torch
         self.torch = torch
         self.device = torch.device(device)
+        if self.device.index is None:  # the worker thread needs an explicit device
+            self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = torch.cuda.Stream(device=self.device)
         self.buf: Dict[str, "torch.Tensor"] = {}
         self.pinned: Dict[str, "torch.Tensor"] = {}
-        self.req: Optional[Request] = None
-        self.event = None
+        self.pool = concurrent.futures.ThreadPoolExecutor(max_workers=1)
+        self.future = None
 
     def _grow(self, name: str, nbytes: int):
         t = self.buf.get(name)
@@ -126,7 +135,11 @@ class GpuSlot(Slot):
             self._grow("out_positions", 8 * z["cap"])
 
     def start(self, req: Request) -> None:
+        self.future = self.pool.submit(self._serve, req)
+
+    def _serve(self, req: Request) -> None:
         torch = self.torch
+        torch.cuda.set_device(self.device)
         z = self._sizes(req)
         n, m, cap, ws_bytes = z["n"], z["m"], z["cap"], z["ws"]
         off = np.zeros(n + 1, dtype=np.uint64)
@@ -146,28 +159,29 @@ class GpuSlot(Slot):
             d_in[:m].copy_(host[:m], non_blocking=True)
             d_in[off_at:off_at + 8 * (n + 1)].copy_(host[m:m + 8 * (n + 1)], non_blocking=True)
         ws_ptr = (ws.data_ptr() + 255) // 256 * 256
-        opts = req.options(int(self.stream.cuda_stream))
+        stream = int(self.stream.cuda_stream)
         twopaco.twopaco_run_device(d_in.data_ptr() if m else 0, d_in.data_ptr() + off_at, n, m,
-                                   req.k, req.filter_bits, req.rounds, opts, ws_ptr, ws_bytes,
-                                   d_out_off.data_ptr(), d_out_pos.data_ptr(), cap)
-        self.h_off = self._grow_pinned("out_offsets", 8 * (n + 1))[:8 * (n + 1)]
-        self.h_pos = self._grow_pinned("out_positions", 8 * cap)[:8 * cap]
+                                   req.k, req.filter_bits, req.rounds, req.options(stream), ws_ptr,
+                                   ws_bytes, d_out_off.data_ptr(), d_out_pos.data_ptr(), cap)
+        h_off = self._grow_pinned("out_offsets", 8 * (n + 1))[:8 * (n + 1)]
         with torch.cuda.stream(self.stream):
-            self.h_off.copy_(d_out_off[:8 * (n + 1)], non_blocking=True)
-            self.h_pos.copy_(d_out_pos[:8 * cap], non_blocking=True)
-            self.event = torch.cuda.Event()
-            self.event.record(self.stream)
-        self.ws_ptr, self.n, self.req = ws_ptr, n, req
+            h_off.copy_(d_out_off[:8 * (n + 1)], non_blocking=True)
+        req.stats = twopaco.twopaco_read_stats(ws_ptr, stream)  # waits for the run and the offsets
+        offs = h_off.numpy().view(np.uint64)
+        total = int(offs[-1])
+        h_pos = self._grow_pinned("out_positions", 8 * max(total, 1))[:8 * total]
+        if total:  # exactly the junctions, not the capacity
+            with torch.cuda.stream(self.stream):
+                h_pos.copy_(d_out_pos[:8 * total], non_blocking=True)
+            self.stream.synchronize()
+        pos = h_pos.numpy().view(np.uint64)
+        req.result = [pos[offs[t]:offs[t + 1]].copy() for t in range(n)]
 
     def poll(self) -> bool:
-        if self.req is None or not self.event.query():
+        if self.future is None or not self.future.done():
             return False
-        req = self.req
-        req.stats = twopaco.twopaco_read_stats(self.ws_ptr, int(self.stream.cuda_stream))
-        off = self.h_off.numpy().view(np.uint64)
-        pos = self.h_pos.numpy().view(np.uint64)[: int(off[-1])]
-        req.result = [pos[off[t]:off[t + 1]].copy() for t in range(self.n)]
-        self.req = None
+        f, self.future = self.future, None
+        f.result()  # a failed request raises here
         return True
 
 
@@ -284,7 +298,7 @@ def run_alone(slot: Slot, requests: Sequence[Request],
         a = clock()
         slot.start(r)
         while not slot.poll():
-            pass
+            time.sleep(20e-6)  # let a slot's worker thread run
         r.arrival, r.admitted, r.done = a - t0, a - t0, clock() - t0
         done.append(r)
     return ServeReport(done, clock() - t0)
