@@ -182,6 +182,17 @@ __device__ __forceinline__ uint64_t second_hash(uint64_t H) { return H * 0x9e377
 // Start slot of a k-mer in the pass-2 table (bits above the partition bins).
 __device__ __forceinline__ uint64_t slot_hash(uint64_t H) { return H >> 16; }
 
+// Start slot of a k-mer in a pass-2 table of cap slots (any capacity): bits
+// 16-47 of H scaled to [0, cap) by a multiply-high (Lemire, "Fast random
+// integer generation in an interval", 2019); larger tables take a remainder.
+__device__ __forceinline__ uint64_t slot_start(uint64_t H, uint64_t cap) {
+  if (cap <= 0xFFFFFFFFull) return __umulhi((uint32_t)(H >> 16), (uint32_t)cap);
+  return slot_hash(H) % cap;
+}
+
+// The slot after i in linear probing, wrapping at cap.
+__device__ __forceinline__ uint64_t next_slot(uint64_t i, uint64_t cap) { return i + 1 == cap ? 0 : i + 1; }
+
 // Reverse the order of the 32 two-bit groups of x.
 __device__ __forceinline__ uint64_t rev_pairs(uint64_t x) {
   const uint64_t b = __brevll(x);
@@ -579,15 +590,14 @@ __device__ __forceinline__ void cas128(unsigned long long* addr, uint64_t cmp_lo
 
 constexpr uint64_t kNoSlot = ~0ull;
 
-// Insert (key, bits) into a table of TS-kind slots (table_slot_kind); the
-// key's slot, or kNoSlot if every slot was tried (the table is full). Bits
-// already present are not written again.
+// Insert (key, bits) into a table of cap TS-kind slots (table_slot_kind),
+// probing from slot start (< cap); the key's slot, or kNoSlot if every slot
+// was tried (the table is full). Bits already present are not written again.
 template <int TS>
 __device__ __forceinline__ uint64_t table_insert(const RunView& v, uint64_t cap, const Key& key,
                                              uint64_t start, uint32_t bits) {
-  const uint64_t mask = cap - 1;
-  uint64_t i = start & mask;
-  for (uint64_t probe = 0; probe < cap; ++probe, i = (i + 1) & mask) {
+  uint64_t i = start;
+  for (uint64_t probe = 0; probe < cap; ++probe, i = next_slot(i, cap)) {
     if (TS == 0) {
       // one word: key << 9 | mask bits; never all ones for a key < 2^54
       unsigned long long* s = static_cast<unsigned long long*>(v.table) + i;
@@ -628,9 +638,8 @@ __device__ __forceinline__ uint64_t table_insert(const RunView& v, uint64_t cap,
 // Mask of key, or -1 if absent.
 template <int TS>
 __device__ __forceinline__ int table_find(const RunView& v, uint64_t cap, const Key& key, uint64_t start) {
-  const uint64_t mask = cap - 1;
-  uint64_t i = start & mask;
-  for (uint64_t probe = 0; probe < cap; ++probe, i = (i + 1) & mask) {
+  uint64_t i = start;
+  for (uint64_t probe = 0; probe < cap; ++probe, i = next_slot(i, cap)) {
     if (TS == 0) {
       const unsigned long long cur = __ldcg(static_cast<const unsigned long long*>(v.table) + i);
       if (cur == kEmpty) return -1;
@@ -672,10 +681,10 @@ __device__ __forceinline__ bool ref_holds(const RunView& v, uint64_t ref, const 
 
 __device__ __forceinline__ uint64_t table_insert_ref(const RunView& v, uint64_t cap, const Key4& key,
                                                      uint64_t H, uint32_t bits, uint64_t g, bool rc) {
-  const uint64_t mask = cap - 1, tag = H >> 49;
+  const uint64_t tag = H >> 49;
   const unsigned long long mine = (tag << 49) | ((uint64_t)rc << 48) | (g + 1);
-  uint64_t i = slot_hash(H) & mask;
-  for (uint64_t probe = 0; probe < cap; ++probe, i = (i + 1) & mask) {
+  uint64_t i = slot_start(H, cap);
+  for (uint64_t probe = 0; probe < cap; ++probe, i = next_slot(i, cap)) {
     Slot3* s = static_cast<Slot3*>(v.table) + i;
     unsigned long long cur = __ldcg(&s->ref);
     if (cur == 0) {
@@ -693,9 +702,9 @@ __device__ __forceinline__ uint64_t table_insert_ref(const RunView& v, uint64_t 
 }
 
 __device__ __forceinline__ int table_find_ref(const RunView& v, uint64_t cap, const Key4& key, uint64_t H) {
-  const uint64_t mask = cap - 1, tag = H >> 49;
-  uint64_t i = slot_hash(H) & mask;
-  for (uint64_t probe = 0; probe < cap; ++probe, i = (i + 1) & mask) {
+  const uint64_t tag = H >> 49;
+  uint64_t i = slot_start(H, cap);
+  for (uint64_t probe = 0; probe < cap; ++probe, i = next_slot(i, cap)) {
     const Slot3* s = static_cast<const Slot3*>(v.table) + i;
     const unsigned long long cur = __ldcg(&s->ref);
     if (cur == 0) return -1;
@@ -709,13 +718,13 @@ template <int KW, int TS>
 __device__ __forceinline__ uint64_t insert_occurrence(const RunView& v, uint64_t cap, const OccT<KW>& oc,
                                                       uint64_t g) {
   if constexpr (TS == 3) return table_insert_ref(v, cap, oc.key, oc.H, oc.tbits, g, oc.rc);
-  else return table_insert<TS>(v, cap, oc.key, slot_hash(oc.H), oc.tbits);
+  else return table_insert<TS>(v, cap, oc.key, slot_start(oc.H, cap), oc.tbits);
 }
 
 template <int KW, int TS>
 __device__ __forceinline__ int find_occurrence(const RunView& v, uint64_t cap, const OccT<KW>& oc) {
   if constexpr (TS == 3) return table_find_ref(v, cap, oc.key, oc.H);
-  else return table_find<TS>(v, cap, oc.key, slot_hash(oc.H));
+  else return table_find<TS>(v, cap, oc.key, slot_start(oc.H, cap));
 }
 
 // Mask held by slot i (a slot that table_insert returned).
@@ -1273,14 +1282,17 @@ __global__ void __launch_bounds__(kBlock) pass1_probe_desc_kernel(RunView v, int
   if (round == 0) block_add(valid_n, &v.hdr->positions);
 }
 
-constexpr double kTableLoad = 2.0;  // table slots per estimated distinct candidate
+// Table slots per estimated distinct candidate: 2.5 for one-word slots
+// (k <= 27), where probe chains cost more than memory, 2 for the wider slots,
+// where a smaller table stays in L2 (measured at k = 25, 31 and 63).
+constexpr double kTableLoadWord = 2.5, kTableLoad = 2.0;
 // pass-2 list work: parts of about this many records, at most kMaxParts per segment
 constexpr unsigned long long kPartRecords = 128, kMaxParts = 4096;
 
-// Size the pass-2 table of this round: twice the number of distinct
+// Size the pass-2 table of this round: 2.5 or 2 times the number of distinct
 // candidate k-mers, estimated by linear counting (Whang, Vander-Zanden &
-// Taylor 1990) from the bits the probe set, rounded up to a power of two (at
-// least 1024) and capped by the workspace. A saturated bitmap falls back to
+// Taylor 1990) from the bits the probe set (at least 1024 slots, a multiple
+// of 32, not rounded to a power of two), capped by the workspace. A saturated bitmap falls back to
 // twice the number of candidate positions. The estimate only sets the table's
 // size; an undersized table is detected and reported, never silently wrong.
 // Every block counts its share of the bitmap; the last block to finish sizes
@@ -1309,10 +1321,10 @@ __global__ void __launch_bounds__(kBlock) table_setup_kernel(RunView v) {
     const unsigned long long e = (unsigned long long)(est * 1.1) + 64ull;
     if (e < distinct) distinct = e;
   }
-  unsigned long long want = (unsigned long long)(kTableLoad * (double)distinct);
-  if (want < 1024ull) want = 1024ull;
-  unsigned long long cap = 1ull;
-  while (cap < want) cap <<= 1;
+  unsigned long long cap =
+      (unsigned long long)((v.k <= 27 ? kTableLoadWord : kTableLoad) * (double)distinct);
+  if (cap < 1024ull) cap = 1024ull;
+  cap = (cap + 31) / 32 * 32;  // any capacity works (slot_start); whole 32-slot groups
   if (cap > v.table_max_slots) cap = v.table_max_slots;
   v.hdr->table_slots = cap;
   if (cap > v.hdr->table_max) v.hdr->table_max = cap;
