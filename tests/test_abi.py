@@ -84,3 +84,22 @@ def test_checkpoint_sizes_and_round_range_checks():
             T.twopaco_run_rounds(0, 0, 0, 0, 25, 1 << 20, 4, T.Options(partition_bins=64), 0, 0,
                                  b, e, 0, 0, 0)
         assert err.value.code == T.EINVAL
+
+
+def test_kernel_code_digest_follows_code_not_comments(tmp_path, monkeypatch):
+    """The ncu traffic figures bench.py reports are keyed to the kernel code only."""
+    import os
+    import shutil
+    import bench
+    src = os.path.join(bench.ROOT, "paper_1602_05856_gb300", "csrc", "twopaco_kernels.cu")
+    d = tmp_path / "paper_1602_05856_gb300" / "csrc"
+    d.mkdir(parents=True)
+    shutil.copy(src, d / "twopaco_kernels.cu")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    base = bench.kernel_code_digest()
+    text = (d / "twopaco_kernels.cu").read_text()
+    (d / "twopaco_kernels.cu").write_text("// a new comment\n\n" + text.replace("{\n", "{  /* note */\n", 1))
+    assert bench.kernel_code_digest() == base
+    (d / "twopaco_kernels.cu").write_text(text.replace("kInsertR = 16", "kInsertR = 8", 1))
+    assert bench.kernel_code_digest() != base
+    assert bench.ncu_traffic("bacterial_set", "pass1_insert") is None  # no profiles under tmp_path
