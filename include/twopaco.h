@@ -123,6 +123,16 @@ int twopaco_build_ex(const char* const* seqs, const uint64_t* lengths, uint64_t 
                      uint64_t filter_bits, int rounds, const twopaco_options* opt,
                      twopaco_result** out);
 
+/*
+ * Diagnostic (no counterpart in the paper): launches one bounded device wait
+ * of the kind the emit uses on a flag that nothing sets, on `cuda_stream`
+ * (NULL = default), and synchronises. The wait gives up after its poll limit
+ * (a fraction of a second) instead of hanging, so the call returns
+ * TWOPACO_ETIMEOUT and the context stays usable; TWOPACO_ECUDA on a CUDA
+ * error. Allocates 16 bytes of device memory for the flag and the status.
+ */
+int twopaco_selftest_bounded_wait(void* cuda_stream);
+
 /* Release a result returned by twopaco_build*. NULL is ignored. */
 void twopaco_result_free(twopaco_result* res);
 

@@ -545,6 +545,24 @@ int twopaco_checkpoint_load(const uint8_t* d_bases, const uint64_t* d_offsets, u
   return TWOPACO_OK;
 }
 
+int twopaco_selftest_bounded_wait(void* cuda_stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  unsigned long long* word = nullptr;
+  unsigned int* status = nullptr;
+  cudaError_t e = cudaMalloc(&word, 16);
+  if (e != cudaSuccess) return cuda_code(e);
+  status = reinterpret_cast<unsigned int*>(word + 1);
+  unsigned int got = 0;
+  if ((e = cudaMemsetAsync(word, 0, 16, s)) == cudaSuccess) {
+    if (launch_bounded_wait(word, status, s) < 0) e = cudaErrorLaunchFailure;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&got, status, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  cudaFree(word);
+  if (e != cudaSuccess) return cuda_code(e);
+  return got == 1 ? TWOPACO_ETIMEOUT : (got == 2 ? TWOPACO_OK : TWOPACO_ECUDA);
+}
+
 void twopaco_result_free(twopaco_result* res) {
   if (!res) return;
   std::free(res->offsets);

@@ -149,6 +149,10 @@ int launch_partition_count_wide(const RunView& v, cudaStream_t s);
 // hdr->input_digest (order-free, so the same input always gives the same value).
 int launch_digest(DevHeader* hdr_dev, const uint32_t* packed, uint64_t words, cudaStream_t s);
 
+// One bounded wait on *word (which the caller leaves 0): *status = 1 when it
+// gives up, 2 if it saw the word set.
+int launch_bounded_wait(unsigned long long* word, unsigned int* status, cudaStream_t s);
+
 // Process-wide count of kernels launched by the library.
 void count_launches(int n);
 unsigned long long launches_so_far();

@@ -101,6 +101,8 @@ def _lib() -> ctypes.CDLL:
         L.twopaco_run_rounds.argtypes = [P, P, U64, U64, I, U64, I, ctypes.POINTER(_Options), P, U64,
                                          I, I, P, P, U64]
         L.twopaco_run_rounds.restype = I
+        L.twopaco_selftest_bounded_wait.argtypes = [P]
+        L.twopaco_selftest_bounded_wait.restype = I
         L.twopaco_checkpoint_bytes.argtypes = [U64, U64, I, U64, I, ctypes.POINTER(_Options),
                                                ctypes.POINTER(U64)]
         L.twopaco_checkpoint_bytes.restype = I
@@ -333,6 +335,12 @@ def twopaco_run_rounds(d_bases: int, d_offsets: int, n_seqs: int, total_bases: i
                                    int(out_capacity))
     if rc != OK:
         raise TwopacoError(rc, "twopaco_run_rounds")
+
+
+def twopaco_selftest_bounded_wait(cuda_stream: int = 0) -> int:
+    """Run one bounded device wait that must give up; returns the library's code
+    (ETIMEOUT expected)."""
+    return int(_lib().twopaco_selftest_bounded_wait(cuda_stream or None))
 
 
 def twopaco_checkpoint_bytes(total_bases: int, n_seqs: int, k: int, filter_bits: int, rounds: int,

@@ -373,3 +373,15 @@ def test_captured_run_profiles_every_replay():
         T().twopaco_profile_enable(False)
         run.release_plan()
     _eq(run.result(), O.junctions((bases, off), 25))
+
+
+def test_bounded_wait_gives_up_and_the_context_survives():
+    """A device wait on a flag that nothing sets ends with ETIMEOUT, not a hang, and the
+    context stays usable: the failure path of the emit's look-back, made to happen."""
+    import time
+    t0 = time.time()
+    assert T().twopaco_selftest_bounded_wait() == T().ETIMEOUT
+    assert time.time() - t0 < 60
+    got, _ = T().twopaco_build_ex(["TGGCACGTC", "TGGCACTTC"], 2, 1 << 12, 1,
+                                  T().Options(both_strands=False))
+    _eq(got, [[0, 4, 7], [0, 4, 7]])
