@@ -1596,24 +1596,6 @@ constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagPrefix = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
 constexpr uint32_t kSpinLimit = 1u << 22;
 
-// The bounded wait of the emit, on a word that nothing ever sets: polls it
-// with back-off like the emit's look-back, gives up after kSpinLimit polls
-// and records that in *status (1 = gave up, 2 = the word was seen set).
-__global__ void bounded_wait_kernel(volatile unsigned long long* word, unsigned int* status) {
-  uint32_t spins = 0;
-  for (;;) {
-    if (*word) {
-      *status = 2;
-      return;
-    }
-    if (++spins > kSpinLimit) {
-      *status = 1;
-      return;
-    }
-    __nanosleep(32);
-  }
-}
-
 __global__ void __launch_bounds__(kBlock) emit_kernel(RunView v) {
   __shared__ unsigned long long tile_s, prefix_s, total_s;
   __shared__ uint32_t before_s[kEmitTileWords];  // junctions of the tile before each of its words
@@ -1962,11 +1944,6 @@ unsigned long long launches_so_far() { return g_launches.load(); }
 
 int launch_init(const RunView& v, cudaStream_t s) {
   return cudaMemsetAsync(v.hdr, 0, sizeof(DevHeader), s) == cudaSuccess ? 0 : -1;
-}
-
-int launch_bounded_wait(unsigned long long* word, unsigned int* status, cudaStream_t s) {
-  bounded_wait_kernel<<<1, 1, 0, s>>>(word, status);
-  return done(1);
 }
 
 int launch_digest(DevHeader* hdr_dev, const uint32_t* packed, uint64_t words, cudaStream_t s) {
