@@ -301,8 +301,11 @@ def run_ours(args, world, rank, local):
     if args.workload == "plain_single":
         WORKLOAD, FILTER_BITS, HASHES = "plain_single", 1 << 24, 3
 
-    build.build()
     torch.cuda.set_device(local)
+    if rank == 0:  # one rank compiles (if anything is out of date); the others wait for it
+        build.build()
+    barrier(world)
+    build.build()  # up to date now: only checks
     dev = torch.device("cuda", local)
     seqs = genomes.named_set(WORKLOAD)
     bases, off = genomes.concat(seqs)
