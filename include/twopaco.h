@@ -86,7 +86,11 @@ typedef struct twopaco_stats {
   uint64_t pass2_marks;    /* junction positions (marks after pass 2) */
   uint64_t table_slots;    /* largest pass-2 table used in any round */
   uint64_t bad_base_index; /* first invalid byte, or UINT64_MAX if none */
-  uint32_t overflow;       /* nonzero: the pass-2 table or output ran out of room */
+  uint32_t overflow;       /* nonzero: the pass-2 table, the output or (split_at_n)
+                              the piece boundary list ran out of room; when only the
+                              output did, d_out_offsets holds the exact counts and
+                              twopaco_run_rounds(..., rounds, rounds, ...) writes the
+                              output again into a larger buffer */
   uint32_t timeout;        /* nonzero: a bounded device wait gave up */
 } twopaco_stats;
 
@@ -113,7 +117,10 @@ const char* twopaco_strerror(int code);
  *                        it with twopaco_result_free. Left NULL on error.
  * Allocates device memory for the input and the workspace, copies the input
  * in, runs, copies the result out and frees everything before returning. If
- * the pass-2 table overflows it is grown and the run repeated.
+ * the pass-2 table overflows it is grown and the run repeated; the output
+ * buffer starts at every k-mer position up to 2^27 of them (else an eighth)
+ * and, if the junctions do not fit, is reallocated at their exact count and
+ * written again.
  */
 int twopaco_build(const char* const* seqs, const uint64_t* lengths, uint64_t n_seqs, int k,
                   uint64_t filter_bits, int rounds, twopaco_result** out);
@@ -140,7 +147,9 @@ void twopaco_result_free(twopaco_result* res);
  * Device workspace size, in bytes, for a device-resident run of
  * `total_bases` bases in `n_seqs` strings. The workspace holds the 2-bit
  * packed input, the filter (filter_bits / 8 bytes), two position bitmaps,
- * the pass-2 table and small counters.
+ * the pass-2 table reserved for the worst case, the candidate list and the
+ * slots it found, one 8-byte probe descriptor per base (under 2^31 bases,
+ * hashes <= 6), the piece boundaries with split_at_n, and small counters.
  */
 int twopaco_workspace_size(uint64_t total_bases, uint64_t n_seqs, int k, uint64_t filter_bits,
                            int rounds, const twopaco_options* opt, uint64_t* bytes);
