@@ -66,7 +66,7 @@ typedef struct twopaco_options {
   uint64_t candidate_records; /* pass-2 candidate list size in 8-byte units; 0 =
                                  automatic (half a round's positions). It
                                  holds twice as many candidates when the input has
-                                 at most 2^32 bases. A round with more candidates
+                                 fewer than 2^31 bases. A round with more candidates
                                  stays correct but slower. */
   void* cuda_stream;       /* cudaStream_t to launch on, borrowed; NULL = default */
   int split_at_n;          /* 1: an N ends its string (see above); 0 (default): N is
@@ -77,6 +77,12 @@ typedef struct twopaco_options {
                               automatic (n_seqs + 1 + total_bases / 64). A run with
                               more boundaries reports TWOPACO_EOVERFLOW; the host
                               builds count them exactly. */
+  int wide_layout;         /* 0 (default): the workspace layout follows the input
+                              size. 1: the layout of inputs of 2^31 bases and more,
+                              at any size: 64-bit candidate records and no probe
+                              descriptors. 2: as 1, and pass 2 also keeps no table
+                              slots (the layout of tables over 2^32 slots). Same
+                              results; for testing those paths on small inputs. */
 } twopaco_options;
 
 /* Counters of one run, in the spirit of Table 4 (marks after each pass). */

@@ -48,6 +48,7 @@ int validate(uint64_t n_seqs, int k, uint64_t filter_bits, int rounds, const two
   if (rounds > 1 && o.partition_bins < 2) return TWOPACO_EINVAL;
   if (n_seqs >= (1ull << 32)) return TWOPACO_EINVAL;
   if (o.split_at_n != 0 && o.split_at_n != 1) return TWOPACO_EINVAL;
+  if (o.wide_layout < 0 || o.wide_layout > 2) return TWOPACO_EINVAL;
   return TWOPACO_OK;
 }
 
@@ -58,7 +59,7 @@ int validate_size(uint64_t total_bases) {
 struct Layout {
   uint64_t header, packed, filter, ctemp, cfinal, tile_count, tile_prefix, bins, cuts, table;
   uint64_t cands, lc, segs, desc, cslot, nmask, bounds, chunks, runs, rank;
-  int use_desc, use_slot, split;
+  int narrow, use_desc, use_slot, split;
   uint64_t n_chunks, run_cap;
   uint64_t total;
   uint64_t packed_words, bitmap_words, n_tiles, table_slots, cand_cap;
@@ -81,6 +82,8 @@ Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int roun
   L.bitmap_words = (m + 31) / 32;
   L.n_tiles = (L.bitmap_words + kEmitTileWords - 1) / kEmitTileWords;
   L.table_slots = o.table_slots ? next_pow2(o.table_slots) : auto_table_slots(m, rounds);
+  // 32-bit candidate records (31-bit positions and a sentinel flag) below 2^31 bases
+  L.narrow = (m < (1ull << 31) && o.wide_layout == 0) ? 1 : 0;
   uint64_t at = 0;
   L.header = at;
   at += align_up(sizeof(DevHeader));
@@ -113,9 +116,9 @@ Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int roun
   // the table slot of every listed candidate (32-bit slot indices), kept by
   // the second-pass insert for its probe loop; one per record of the list
   // (twice as many 32-bit records under 2^31 bases)
-  L.use_slot = L.table_slots <= (1ull << 32) ? 1 : 0;
+  L.use_slot = (L.table_slots <= (1ull << 32) && o.wide_layout < 2) ? 1 : 0;
   L.cslot = at;
-  if (L.use_slot) at += align_up(L.cand_cap * (m < (1ull << 31) ? 2 : 1) * 4);
+  if (L.use_slot) at += align_up(L.cand_cap * (L.narrow ? 2 : 1) * 4);
   // linear-counting bitmap: 2^lc_log2 >= the list's capacity (at least 2^16 bits)
   L.lc_log2 = 16;
   while ((1ull << L.lc_log2) < L.cand_cap && L.lc_log2 < 36) ++L.lc_log2;
@@ -125,7 +128,7 @@ Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int roun
   at += align_up((uint64_t)kMaxSegments * 4);
   // probe descriptors: one 64-bit word per position (filter word index, 30 bits
   // of bit bases, flags) when they fit -- under 2^31 bases, h <= 6, b <= 2^37
-  L.use_desc = (m < (1ull << 31) && o.hashes <= 6 && filter_bits <= (1ull << 37)) ? 1 : 0;
+  L.use_desc = (L.narrow && o.hashes <= 6 && filter_bits <= (1ull << 37)) ? 1 : 0;
   L.desc = at;
   if (L.use_desc) at += align_up((m + 16) * 8);
   // N splitting: N mask and boundary bitmap (one bit per base), per-chunk
@@ -177,7 +180,7 @@ RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_
   v.table = base + L.table;
   v.table_max_slots = L.table_slots;
   v.cands = reinterpret_cast<uint64_t*>(base + L.cands);
-  v.narrow = m < (1ull << 31) ? 1 : 0;  // 31-bit positions + a sentinel flag
+  v.narrow = L.narrow;
   v.use_desc = L.use_desc;
   v.cand_slot = L.use_slot ? reinterpret_cast<uint32_t*>(base + L.cslot) : nullptr;
   v.desc = reinterpret_cast<uint64_t*>(base + L.desc);
@@ -245,6 +248,7 @@ void twopaco_default_options(twopaco_options* opt) {
   opt->cuda_stream = nullptr;
   opt->split_at_n = 0;
   opt->run_capacity = 0;
+  opt->wide_layout = 0;
 }
 
 const char* twopaco_strerror(int code) {

@@ -37,7 +37,8 @@ class _Options(ctypes.Structure):
     _fields_ = [("hashes", ctypes.c_int), ("both_strands", ctypes.c_int),
                 ("partition_bins", ctypes.c_uint32), ("table_slots", ctypes.c_uint64),
                 ("candidate_records", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p),
-                ("split_at_n", ctypes.c_int), ("run_capacity", ctypes.c_uint64)]
+                ("split_at_n", ctypes.c_int), ("run_capacity", ctypes.c_uint64),
+                ("wide_layout", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
@@ -163,12 +164,13 @@ class Options:
     candidate_records: int = 0
     split_at_n: bool = False  # an N (either case) ends its string there
     run_capacity: int = 0     # split_at_n: room for piece boundaries; 0 = automatic
+    wide_layout: int = 0      # 1/2: the large-input workspace layout at any size (testing)
 
     def _c(self) -> _Options:
         return _Options(int(self.hashes), int(bool(self.both_strands)), int(self.partition_bins),
                         int(self.table_slots), int(self.candidate_records),
                         ctypes.c_void_p(int(self.cuda_stream) or None), int(bool(self.split_at_n)),
-                        int(self.run_capacity))
+                        int(self.run_capacity), int(self.wide_layout))
 
 
 def _stats_dict(s: _Stats) -> Dict[str, int]:

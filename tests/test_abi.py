@@ -37,7 +37,8 @@ def test_host_side_argument_checks():
     assert ok > (1 << 20) // 8
     bad = [dict(k=0), dict(k=128), dict(filter_bits=100), dict(filter_bits=3 << 10), dict(rounds=0),
            dict(options=T.Options(hashes=0)), dict(options=T.Options(hashes=9)),
-           dict(options=T.Options(partition_bins=1000)), dict(rounds=8, options=T.Options(partition_bins=4))]
+           dict(options=T.Options(partition_bins=1000)), dict(rounds=8, options=T.Options(partition_bins=4)),
+           dict(options=T.Options(wide_layout=3)), dict(options=T.Options(wide_layout=-1))]
     for b in bad:
         args = dict(total_bases=1000, n_seqs=2, k=25, filter_bits=1 << 20, rounds=1)
         args.update(b)
@@ -70,6 +71,20 @@ def test_split_and_long_k_workspace():
     assert plain < small < split
     assert T.twopaco_workspace_size(1 << 20, 4, 100, 1 << 20, 1) > 0
     assert T.twopaco_workspace_size(1 << 20, 4, 127, 1 << 20, 1) > 0
+
+
+def test_wide_layout_workspace():
+    """64-bit records need no more room than the 32-bit ones (the list holds
+    half as many), and drop the probe descriptors (8 B per base) and, at 2,
+    the kept slots; from 2^31 bases the automatic layout is already wide."""
+    from paper_1602_05856_gb300 import build, twopaco as T
+    build.build()
+    m = 1 << 24
+    w0, w1, w2 = (T.twopaco_workspace_size(m, 10, 25, 1 << 26, 1, T.Options(wide_layout=w)) for w in (0, 1, 2))
+    assert w0 - w1 >= 8 * m and w1 - w2 >= 4 * (m // 2)
+    big = 1 << 31
+    b0, b1 = (T.twopaco_workspace_size(big, 10, 25, 1 << 26, 1, T.Options(wide_layout=w)) for w in (0, 1))
+    assert b0 == b1
 
 
 def test_checkpoint_sizes_and_round_range_checks():
