@@ -74,14 +74,15 @@ typedef struct twopaco_options {
   uint64_t run_capacity;   /* split_at_n only: room for the boundaries of the
                               N-free pieces and N runs (one per string start and
                               one per N/base change inside a string); 0 =
-                              automatic (n_seqs + 1 + total_bases / 64). A run with
-                              more boundaries reports TWOPACO_EOVERFLOW; the host
-                              builds count them exactly. */
+                              automatic (n_seqs + 1 + total_bases / 64, at most
+                              2^32 - 1). A run with more boundaries reports
+                              TWOPACO_EOVERFLOW; the host builds count them exactly.
+                              At most 2^32 - 1, else TWOPACO_EINVAL. */
   int wide_layout;         /* 0 (default): the workspace layout follows the input
                               size. 1: the layout of inputs of 2^31 bases and more,
                               at any size: 64-bit candidate records and no probe
                               descriptors. 2: as 1, and pass 2 also keeps no table
-                              slots (the layout of tables over 2^32 slots). Same
+                              slots (the layout of tables of 2^32 slots and more). Same
                               results; for testing those paths on small inputs. */
 } twopaco_options;
 

@@ -49,6 +49,7 @@ int validate(uint64_t n_seqs, int k, uint64_t filter_bits, int rounds, const two
   if (n_seqs >= (1ull << 32)) return TWOPACO_EINVAL;
   if (o.split_at_n != 0 && o.split_at_n != 1) return TWOPACO_EINVAL;
   if (o.wide_layout < 0 || o.wide_layout > 2) return TWOPACO_EINVAL;
+  if (o.run_capacity >= (1ull << 32)) return TWOPACO_EINVAL;  // piece ranks are 32-bit
   return TWOPACO_OK;
 }
 
@@ -73,7 +74,10 @@ uint64_t auto_table_slots(uint64_t m, int rounds) {
   return next_pow2(want);
 }
 
-uint64_t auto_run_capacity(uint64_t m, uint64_t n_seqs) { return n_seqs + 1 + m / 64; }
+uint64_t auto_run_capacity(uint64_t m, uint64_t n_seqs) {
+  const uint64_t want = n_seqs + 1 + m / 64;
+  return want < (1ull << 32) ? want : (1ull << 32) - 1;  // piece ranks are 32-bit
+}
 
 Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int rounds,
               const twopaco_options& o) {
@@ -116,7 +120,8 @@ Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int roun
   // the table slot of every listed candidate (32-bit slot indices), kept by
   // the second-pass insert for its probe loop; one per record of the list
   // (twice as many 32-bit records under 2^31 bases)
-  L.use_slot = (L.table_slots <= (1ull << 32) && o.wide_layout < 2) ? 1 : 0;
+  // (slot 0xFFFFFFFF stands for "no slot", so the table stays below 2^32 slots)
+  L.use_slot = (L.table_slots < (1ull << 32) && o.wide_layout < 2) ? 1 : 0;
   L.cslot = at;
   if (L.use_slot) at += align_up(L.cand_cap * (L.narrow ? 2 : 1) * 4);
   // linear-counting bitmap: 2^lc_log2 >= the list's capacity (at least 2^16 bits)

@@ -1,7 +1,7 @@
 """The large-input workspace layout on small inputs, against the oracle.
 
 Inputs of 2^31 bases and more keep 64-bit candidate records and no probe
-descriptors, and tables over 2^32 slots keep no slot per candidate; the
+descriptors, and tables of 2^32 slots and more keep no slot per candidate; the
 ``wide_layout`` option selects those layouts at any size, so that the same
 bit-exact checks as elsewhere (junction positions, the pass-1 candidate
 bitmap, edges) cover them.
