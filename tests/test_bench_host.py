@@ -1,0 +1,106 @@
+"""Host-side logic of bench.py on the CPU: the clock sampler against a fake
+nvidia-smi, the per-kernel work model, and the traffic lookup's digest key."""
+import os
+import stat
+import sys
+import textwrap
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+UUID0 = "GPU-00000000-1111-2222-3333-444444444444"
+UUID1 = "GPU-99999999-1111-2222-3333-444444444444"
+
+
+def _fake_smi(tmp_path, rows):
+    """An nvidia-smi that prints `rows` (CSV, no header) every 20 ms until killed."""
+    body = "\n".join(f"echo '{r}'" for r in rows)
+    script = tmp_path / "nvidia-smi"
+    script.write_text(textwrap.dedent("""\
+        #!/bin/bash
+        trap 'exit 0' TERM
+        while true; do
+        {body}
+        sleep 0.02
+        done
+        """).format(body=body))
+    script.chmod(script.stat().st_mode | stat.S_IXUSR)
+    return str(tmp_path)
+
+
+def _sample(tmp_path, monkeypatch, rows, uuid):
+    monkeypatch.setenv("PATH", _fake_smi(tmp_path, rows) + os.pathsep + os.environ["PATH"])
+    s = bench.ClockSampler(uuid)
+    s.start()
+    return s.stop()
+
+
+def test_clock_sampler_reads_its_own_gpu(tmp_path, monkeypatch):
+    rows = [f"0, {UUID0}, 1965, 2070, 900.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            f"1, {UUID1}, 345, 2070, 90.0, 0x0000000000000000, Active, Not Active, Not Active, Not Active"]
+    c = _sample(tmp_path, monkeypatch, rows, UUID0)
+    assert c["sm_mhz"] == 1965.0 and c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap"] and c["samples"] >= 1
+    c = _sample(tmp_path, monkeypatch, rows, UUID1)
+    assert c["sm_mhz"] == 345.0 and c["reasons"] == ["hw_slowdown"]
+
+
+def test_clock_sampler_median_and_bad_fields(tmp_path, monkeypatch):
+    rows = [f"0, {UUID0}, 2000, 2070, 700, 0x0, Not Active, Not Active, Not Active, Not Active",
+            f"0, {UUID0}, 1900, 2070, 700, 0x0, Not Active, Not Active, Active, Not Active",
+            f"0, {UUID0}, [N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]",
+            "garbage line"]
+    c = _sample(tmp_path, monkeypatch, rows, UUID0)
+    assert c["sm_mhz"] in (1900.0, 1950.0, 2000.0)  # median over whole cycles of the four rows
+    assert c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_thermal_slowdown"]
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    s = bench.ClockSampler(UUID0)
+    s.start()
+    c = s.stop()
+    assert c["sm_mhz"] is None and c["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_kernel_work_model():
+    st = {"positions": 1000, "pass1_marks": 80, "pass2_marks": 50}
+    m, n, tb = 1024, 3, 1 << 20
+    assert bench.kernel_work("pass1_insert", st, m, n, tb) == (1000, "l2_or")
+    assert bench.kernel_work("pass1_probe", st, m, n, tb) == (1000, "l2_read")
+    assert bench.kernel_work("pass2_insert", st, m, n, tb) == (80, "l2_or")
+    assert bench.kernel_work("pass2_classify", st, m, n, tb) == (80, "l2_read")
+    assert bench.kernel_work("pack", st, m, n, tb) == (m + m / 4, "hbm")
+    assert bench.kernel_work("table_clear", st, m, n, tb) == (tb, "hbm")
+    assert bench.kernel_work("emit", st, m, n, tb) == (m / 8 + 8 * 50, "hbm")
+    assert bench.kernel_work("table_setup", st, m, n, tb) == (None, None)
+
+
+def test_traffic_lookup_is_keyed_by_workload_kernel_and_code(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    src = tmp_path / "paper_1602_05856_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "twopaco_kernels.cu").write_text("int f() { return 1; }\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    d = bench.kernel_code_digest()
+    (prof / "dram_traffic_x.md").write_text(
+        f"dram-traffic wl pass1_probe 123456 sha256:{d}\n"
+        f"dram-traffic wl pass1_insert 777 sha256:{'0' * 64}\n")
+    assert bench.ncu_traffic("wl", "pass1_probe") == 123456
+    assert bench.ncu_traffic("wl", "pass1_insert") is None  # captured on other code
+    assert bench.ncu_traffic("other", "pass1_probe") is None
+    (src / "twopaco_kernels.cu").write_text("// a comment\nint f() { return 1; }\n\n")
+    assert bench.ncu_traffic("wl", "pass1_probe") == 123456  # comments do not count
+    (src / "twopaco_kernels.cu").write_text("int f() { return 2; }\n")
+    assert bench.ncu_traffic("wl", "pass1_probe") is None
+
+
+def test_workload_config_names_the_workload():
+    c = bench.workload_config(35_000_000)
+    assert c["workload"].startswith("bacterial_set") and c["k"] == 25
+    assert c["filter_bits"] == 1 << 28 and c["rounds"] == 1 and "flushed" in c["l2"]
+    assert "model" not in c
