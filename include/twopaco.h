@@ -31,11 +31,12 @@
  *     than k has none.
  *   - Return value: TWOPACO_OK (0) or a negative TWOPACO_E* code.
  *   - k in [1, 127] (k-mers of up to 31 bases are held in one 64-bit word,
- *     up to 63 in two, up to 127 in four); filter_bits a power of two >= 256;
- *     rounds >= 1;
- *     total_bases < 2^48;
+ *     up to 63 in two, up to 127 in four); filter_bits a power of two in
+ *     [256, 2^40]; rounds >= 1; n_seqs < 2^32; total_bases < 2^48;
  *     options->hashes in [1, 8]; options->partition_bins a power of two
- *     >= rounds. Anything else is TWOPACO_EINVAL.
+ *     >= rounds (and >= 2 when rounds > 1); options->both_strands and
+ *     options->split_at_n 0 or 1; options->wide_layout 0, 1 or 2;
+ *     options->run_capacity < 2^32. Anything else is TWOPACO_EINVAL.
  *   - Calls on different workspaces may run concurrently from different host
  *     threads; calls that share a workspace must be serialised by the caller.
  */
@@ -55,7 +56,8 @@ extern "C" {
 #define TWOPACO_ENOMEM (-3)    /* device or pinned-host allocation failed */
 #define TWOPACO_ETIMEOUT (-4)  /* a bounded device wait gave up */
 #define TWOPACO_ECUDA (-5)     /* a CUDA runtime call failed */
-#define TWOPACO_EOVERFLOW (-6) /* the pass-2 table or the output buffer is too small */
+#define TWOPACO_EOVERFLOW (-6) /* the pass-2 table, the output buffer or the piece
+                                  boundary list (split_at_n) is too small */
 #define TWOPACO_ESCRATCH (-7)  /* the run needs more than the no-alloc scratch buffer holds */
 
 typedef struct twopaco_options {

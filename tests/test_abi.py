@@ -39,7 +39,8 @@ def test_host_side_argument_checks():
            dict(options=T.Options(hashes=0)), dict(options=T.Options(hashes=9)),
            dict(options=T.Options(partition_bins=1000)), dict(rounds=8, options=T.Options(partition_bins=4)),
            dict(options=T.Options(wide_layout=3)), dict(options=T.Options(wide_layout=-1)),
-           dict(options=T.Options(split_at_n=True, run_capacity=1 << 32))]
+           dict(options=T.Options(split_at_n=True, run_capacity=1 << 32)),
+           dict(filter_bits=1 << 41), dict(n_seqs=1 << 32), dict(rounds=2, options=T.Options(partition_bins=1))]
     for b in bad:
         args = dict(total_bases=1000, n_seqs=2, k=25, filter_bits=1 << 20, rounds=1)
         args.update(b)
