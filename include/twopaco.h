@@ -77,9 +77,10 @@ typedef struct twopaco_options {
                               N-free pieces and N runs (one per string start and
                               one per N/base change inside a string); 0 =
                               automatic (n_seqs + 1 + total_bases / 64, at most
-                              2^32 - 1). A run with more boundaries reports
-                              TWOPACO_EOVERFLOW; the host builds count them exactly.
-                              At most 2^32 - 1, else TWOPACO_EINVAL. */
+                              2^32 - 1). A device run with more boundaries
+                              reports TWOPACO_EOVERFLOW; the host builds count them
+                              and raise a smaller capacity to that count. At most
+                              2^32 - 1, else TWOPACO_EINVAL. */
   int wide_layout;         /* 0 (default): the workspace layout follows the input
                               size. 1: the layout of inputs of 2^31 bases and more,
                               at any size: 64-bit candidate records and no probe

@@ -230,6 +230,14 @@ uint64_t count_run_boundaries(const char* const* seqs, const uint64_t* lengths, 
   return r;
 }
 
+// Host builds know their input: with N splitting the boundary list gets at
+// least the exact count, so that only the table or the output can run short.
+void raise_run_capacity(twopaco_options* o, const char* const* seqs, const uint64_t* lengths, uint64_t n) {
+  if (!o->split_at_n) return;
+  const uint64_t need = count_run_boundaries(seqs, lengths, n) + 1;
+  if (o->run_capacity < need) o->run_capacity = need;
+}
+
 int cuda_code(cudaError_t e) {
   if (e == cudaSuccess) return TWOPACO_OK;
   if (e == cudaErrorMemoryAllocation) return TWOPACO_ENOMEM;
@@ -601,7 +609,8 @@ int twopaco_build_ex(const char* const* seqs, const uint64_t* lengths, uint64_t 
     if (lengths[t] >= (uint64_t)k) positions += lengths[t] - (uint64_t)k + 1;
   }
   const uint64_t m = offsets[n_seqs];
-  if (o.split_at_n && !o.run_capacity) o.run_capacity = count_run_boundaries(seqs, lengths, n_seqs) + 1;
+  if (validate_size(m)) return TWOPACO_EINVAL;
+  raise_run_capacity(&o, seqs, lengths, n_seqs);
   cudaStream_t s = static_cast<cudaStream_t>(o.cuda_stream);
 
   uint8_t* d_bases = nullptr;
@@ -904,7 +913,7 @@ int twopaco_build_ctx(twopaco_context* c, const char* const* seqs, const uint64_
   }
   const uint64_t m = c->h_off[n_seqs];
   if (validate_size(m)) return finish(TWOPACO_EINVAL);
-  if (o.split_at_n && !o.run_capacity) o.run_capacity = count_run_boundaries(seqs, lengths, n_seqs) + 1;
+  raise_run_capacity(&o, seqs, lengths, n_seqs);
   if ((e = grow_device(&c->d_bases, &c->cap_bases, m)) != cudaSuccess) return finish(cuda_code(e));
   if ((e = grow_device(&c->d_pos, &c->cap_pos, first_output_capacity(positions) * 8)) != cudaSuccess)
     return finish(cuda_code(e));

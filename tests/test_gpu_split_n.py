@@ -135,9 +135,10 @@ def test_run_capacity_overflow_is_reported():
         run.run()
         run.stats(check=True)
     assert e.value.code == -6
-    # the host build counts the boundaries itself
-    got, _ = T().twopaco_build_ex(seqs, 3, 1 << 12, 1, T().Options(split_at_n=True))
-    _eq(got, O.junctions(seqs, 3, split_n=True))
+    # the host build counts the boundaries itself, and raises a capacity that is too small
+    for cap in (0, 10):
+        got, _ = T().twopaco_build_ex(seqs, 3, 1 << 12, 1, T().Options(split_at_n=True, run_capacity=cap))
+        _eq(got, O.junctions(seqs, 3, split_n=True))
 
 
 @pytest.mark.parametrize("k,both", [(3, True), (25, True), (31, False), (63, True)])
