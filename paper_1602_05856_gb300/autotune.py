@@ -39,6 +39,8 @@ class Trial:
     est_full_ms: float   # sample time scaled to the full input
     workspace: int       # full-size workspace bytes
     candidates: float    # share of positions left after pass 1 (sample)
+    table_slots: int = 0        # full-size table reserve the workspace was sized with
+    candidate_records: int = 0  # full-size candidate list the workspace was sized with
 
 
 @dataclass
@@ -49,9 +51,17 @@ class Choice:
     workspace: int
     est_full_ms: float
     trials: List[Trial] = field(default_factory=list)
+    table_slots: int = 0
+    candidate_records: int = 0
 
     def options(self, **extra) -> twopaco.Options:
-        return twopaco.Options(hashes=self.hashes, **extra)
+        """Options for the chosen configuration, with the table and list sizes its
+        ``workspace`` was computed for (a table that still overflows is grown by the
+        host builds and reported by the device runs)."""
+        kw = dict(hashes=self.hashes, table_slots=self.table_slots,
+                  candidate_records=self.candidate_records)
+        kw.update(extra)
+        return twopaco.Options(**kw)
 
 
 def prefix_sample(seqs: Sequence[np.ndarray], fraction: float, k: int) -> List[np.ndarray]:
@@ -64,8 +74,7 @@ def prefix_sample(seqs: Sequence[np.ndarray], fraction: float, k: int) -> List[n
 def full_workspace(total_bases: int, n_seqs: int, k: int, bits: int, rounds: int, hashes: int,
                    table_slots: int, candidate_records: int) -> int:
     opts = twopaco.Options(hashes=hashes, table_slots=table_slots,
-                           candidate_records=candidate_records,
-                           partition_bins=65536 if rounds > 1 else 65536)
+                           candidate_records=candidate_records, partition_bins=65536)
     return twopaco.twopaco_workspace_size(total_bases, n_seqs, k, bits, rounds, opts)
 
 
@@ -116,7 +125,7 @@ def tune(seqs: Sequence[np.ndarray], k: int, budget_bytes: Optional[int] = None,
                 cand_share = st["pass1_marks"] / max(1, st["positions"])
                 recs = int(cand_share * total / r * 1.25 / 2) + (1 << 16)
                 ws = full_workspace(total, len(seqs), k, bits, r, h, slots, recs)
-                t = Trial(bits, h, r, ms, ms * scale, ws, cand_share)
+                t = Trial(bits, h, r, ms, ms * scale, ws, cand_share, slots, recs)
                 trials.append(t)
                 if budget_bytes is None or ws <= budget_bytes:
                     fitting.append(t)
@@ -142,5 +151,5 @@ def tune(seqs: Sequence[np.ndarray], k: int, budget_bytes: Optional[int] = None,
                 ranked = sorted(ranked, key=lambda t: (t.est_full_ms, t.workspace))
             best = ranked[0]
             return Choice(best.bits, best.hashes, best.rounds, best.workspace, best.est_full_ms,
-                          trials)
+                          trials, best.table_slots, best.candidate_records)
     raise ValueError("no configuration fits the memory budget")

@@ -12,6 +12,19 @@ def test_prefix_sample_takes_the_same_prefix_of_every_string():
     assert autotune._pow2_at_least(1) == 1 and autotune._pow2_at_least(1025) == 2048
 
 
+def test_choice_options_reproduce_the_budgeted_workspace():
+    """A choice's options size the workspace it was budgeted at, below the
+    worst-case table reserve of the default options."""
+    from paper_1602_05856_gb300 import build, twopaco as T
+    build.build()
+    m, n, k, bits, rounds = 10**7, 5, 25, 1 << 26, 2
+    ws = autotune.full_workspace(m, n, k, bits, rounds, 4, 1 << 20, 300000)
+    c = autotune.Choice(bits, 4, rounds, ws, 1.0, [], 1 << 20, 300000)
+    assert T.twopaco_workspace_size(m, n, k, bits, rounds, c.options()) == ws
+    assert ws < T.twopaco_workspace_size(m, n, k, bits, rounds, T.Options(hashes=4))
+    assert c.options(hashes=6).hashes == 6
+
+
 @pytest.mark.gpu
 def test_tuned_configuration_is_exact_and_fits_the_budget():
     import torch
