@@ -123,7 +123,9 @@ def tune(seqs: Sequence[np.ndarray], k: int, budget_bytes: Optional[int] = None,
                 # full-size table and candidate list from the sample's own sizes
                 slots = _pow2_at_least(st["table_slots"] * scale * 1.25)
                 cand_share = st["pass1_marks"] / max(1, st["positions"])
-                recs = int(cand_share * total / r * 1.25 / 2) + (1 << 16)
+                # 8-byte list units hold two 32-bit records below 2^31 bases
+                per_unit = 2 if total < (1 << 31) else 1
+                recs = int(cand_share * total / r * 1.25 / per_unit) + (1 << 16)
                 ws = full_workspace(total, len(seqs), k, bits, r, h, slots, recs)
                 t = Trial(bits, h, r, ms, ms * scale, ws, cand_share, slots, recs)
                 trials.append(t)
