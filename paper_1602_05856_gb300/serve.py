@@ -3,12 +3,15 @@
 Requests (sets of strings to build, each with its own k, filter size and
 rounds) arrive over time. A request is admitted as soon as an execution slot
 is free and the device memory it needs -- its input, its workspace (filter,
-pass-2 table, bitmaps) and its output -- fits the remaining budget; requests
-that arrive while others run are admitted as slots and memory free up, and
-the work of admitted requests overlaps on the device (one CUDA stream per
-slot). A slot keeps its buffers between requests and only grows them. The
-loop records each request's latency (completion minus arrival) and reports
-p50/p99 and throughput.
+pass-2 table, bitmaps) and its output -- fits what the requests in flight
+leave of the budget; requests that arrive while others run are admitted as
+slots and memory free up, and the work of admitted requests overlaps on the
+device (one CUDA stream per slot). A slot keeps its buffers between requests
+and only grows them, so the budget bounds the memory of the requests in
+flight, while the memory held is, per slot, that of the largest request it
+has served (``GpuSlot.reserve`` sizes the slots up front). The loop records
+each request's latency (completion minus arrival) and reports p50/p99 and
+throughput.
 
 The scheduler (``Scheduler``) holds no GPU code; ``GpuSlot`` runs a request
 through the C ABI (``twopaco_run_device``) on the slot's stream; tests drive
