@@ -494,3 +494,27 @@ def test_mammal_slice_generator_is_seeded_and_shaped():
     assert not all(np.array_equal(a[0], x) for x in a[1:])  # the leaves differ
     c = G.mammal_slice(seed=7, genome_len=60_000)
     assert not np.array_equal(a[0], c[0])
+
+
+# --- the ctypes wrappers against the oracle's C entry points ---------------------------
+
+def test_oracle_wrappers_match_the_c_signatures():
+    import ctypes
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(O.__file__), "twopaco_oracle.cpp")).read()
+    defs = re.findall(r"(?m)^(int|long long) (oracle_\w+)\(([^)]*)\)\s*\{", src)
+    assert len(defs) == 6
+    L = O.lib()
+    for ret, name, params in defs:
+        params = [p.strip() for p in params.split(",")]
+        fn = getattr(L, name)
+        assert len(fn.argtypes) == len(params), name
+        for p, t in zip(params, fn.argtypes):
+            if "*" in p:
+                assert t is ctypes.c_void_p, (name, p)
+            elif p.startswith("uint64_t"):
+                assert t is ctypes.c_uint64, (name, p)
+            else:
+                assert p.startswith("int ") and t is ctypes.c_int, (name, p)
+        assert fn.restype is (ctypes.c_int if ret == "int" else ctypes.c_longlong), name
