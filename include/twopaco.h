@@ -223,9 +223,11 @@ int twopaco_run_rounds(const uint8_t* d_bases, const uint64_t* d_offsets, uint64
  *   be a fresh one in another process), given the same input and
  *   parameters as the run it was taken from: the input is packed again and
  *   its digest compared. A checkpoint of another input, parameter set or
- *   format is TWOPACO_EINVAL. Synchronises options->cuda_stream; *next_round
- *   gets the round to continue with (twopaco_run_rounds(..., *next_round,
- *   rounds, ...)).
+ *   format, or one whose contents changed after it was saved (each carries
+ *   a checksum of its payload), is TWOPACO_EINVAL; nothing is launched
+ *   before its head and payload check out. Synchronises
+ *   options->cuda_stream; *next_round gets the round to continue with
+ *   (twopaco_run_rounds(..., *next_round, rounds, ...)).
  */
 int twopaco_checkpoint_bytes(uint64_t total_bases, uint64_t n_seqs, int k, uint64_t filter_bits,
                              int rounds, const twopaco_options* opt, uint64_t* bytes);

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "twopaco.h"
+#include "twopaco_checksum.h"
 #include "twopaco_internal.h"
 
 namespace twopaco {
@@ -428,6 +429,7 @@ struct CheckpointHead {
   int32_t k, rounds, hashes, both, split, next_round, lg_blocks;
   uint64_t m, n_seqs, q, bitmap_words, input_digest;
   uint64_t positions, pass1_kept, pass2_kept, table_max;
+  uint64_t payload_sum;  // payload_checksum of everything after the head
 };
 constexpr char kCheckpointMagic[8] = {'T', 'P', 'C', 'K', 'P', 'T', '0', '1'};
 
@@ -473,7 +475,7 @@ int twopaco_checkpoint_save(void* d_workspace, int next_round, void* host_dst, u
     return cuda_code(e);
   CheckpointHead c{};
   std::memcpy(c.magic, kCheckpointMagic, 8);
-  c.version = 1;
+  c.version = 2;
   c.k = h.k;
   c.rounds = rounds;
   c.hashes = h.hashes;
@@ -491,7 +493,6 @@ int twopaco_checkpoint_save(void* d_workspace, int next_round, void* host_dst, u
   c.pass2_kept = h.pass2_kept;
   c.table_max = h.table_max;
   char* out = static_cast<char*>(host_dst);
-  std::memcpy(out, &c, sizeof(c));
   out += sizeof(c);
   if ((e = cudaMemcpy(out, h.cuts, 4 * ((uint64_t)rounds + 1), cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_code(e);
@@ -502,6 +503,10 @@ int twopaco_checkpoint_save(void* d_workspace, int next_round, void* host_dst, u
   }
   if (h.bitmap_words && (e = cudaMemcpy(out, h.cfinal, 4 * h.bitmap_words, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_code(e);
+  // the head last, with the checksum of the payload just written
+  c.payload_sum = payload_checksum(static_cast<const char*>(host_dst) + sizeof(c),
+                                   checkpoint_bytes(h.m, rounds, h.q) - sizeof(c));
+  std::memcpy(host_dst, &c, sizeof(c));
   return TWOPACO_OK;
 }
 
@@ -521,12 +526,25 @@ int twopaco_checkpoint_load(const uint8_t* d_bases, const uint64_t* d_offsets, u
   CheckpointHead c;
   std::memcpy(&c, host_src, sizeof(c));
   const uint64_t q = o.partition_bins;
-  if (std::memcmp(c.magic, kCheckpointMagic, 8) || c.version != 1 || c.k != k || c.rounds != rounds ||
+  if (std::memcmp(c.magic, kCheckpointMagic, 8) || c.version != 2 || c.k != k || c.rounds != rounds ||
       c.hashes != o.hashes || c.both != o.both_strands || c.split != o.split_at_n ||
       c.lg_blocks != log2_exact(filter_bits / 256) || c.m != total_bases || c.n_seqs != n_seqs ||
       c.q != q || c.bitmap_words != L.bitmap_words || c.next_round < 1 || c.next_round > rounds ||
       bytes < checkpoint_bytes(total_bases, rounds, q))
     return TWOPACO_EINVAL;
+  // a payload changed since it was saved is refused
+  const char* payload = static_cast<const char*>(host_src) + sizeof(c);
+  if (payload_checksum(payload, checkpoint_bytes(total_bases, rounds, q) - sizeof(c)) != c.payload_sum)
+    return TWOPACO_EINVAL;
+  // a class cut must cover the q bins in rounds non-empty, ascending ranges
+  // (written only for rounds > 1 and a non-empty input)
+  if (rounds > 1 && total_bases > 0) {
+    std::vector<uint32_t> cuts((size_t)rounds + 1);
+    std::memcpy(cuts.data(), payload, 4 * cuts.size());
+    if (cuts[0] != 0 || cuts[rounds] != q) return TWOPACO_EINVAL;
+    for (int r = 0; r < rounds; ++r)
+      if (cuts[r] >= cuts[r + 1]) return TWOPACO_EINVAL;
+  }
   // the input, packed again, must be the one the checkpoint was taken on
   const RunView v = make_view(d_bases, d_offsets, n_seqs, total_bases, k, filter_bits, rounds, o, L,
                               d_workspace, nullptr, nullptr, 0);
@@ -542,7 +560,7 @@ int twopaco_checkpoint_load(const uint8_t* d_bases, const uint64_t* d_offsets, u
     return cuda_code(e);
   if (bad) return TWOPACO_EBADBASE;
   if (digest != c.input_digest) return TWOPACO_EINVAL;
-  const char* in = static_cast<const char*>(host_src) + sizeof(c);
+  const char* in = payload;
   if ((e = cudaMemcpyAsync(v.cuts, in, 4 * ((uint64_t)rounds + 1), cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cuda_code(e);
   in += 4 * ((uint64_t)rounds + 1);

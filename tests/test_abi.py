@@ -120,3 +120,42 @@ def test_kernel_code_digest_follows_code_not_comments(tmp_path, monkeypatch):
     (d / "twopaco_kernels.cu").write_text(text.replace("kInsertR = 16", "kInsertR = 8", 1))
     assert bench.kernel_code_digest() != base
     assert bench.ncu_traffic("bacterial_set", "pass1_insert") is None  # no profiles under tmp_path
+
+
+def test_checkpoint_checksum_detects_changes(tmp_path):
+    """The payload checksum of a checkpoint (host code, built here with g++):
+    any flipped bit, two swapped words or another length change it."""
+    import subprocess
+    src = tmp_path / "sum.cpp"
+    src.write_text(r'''
+#include <cstdio>
+#include <vector>
+#include "twopaco_checksum.h"
+int main() {
+  std::vector<unsigned char> b(1003);
+  for (size_t i = 0; i < b.size(); ++i) b[i] = (unsigned char)(i * 131 + 7);
+  const uint64_t base = twopaco::payload_checksum(b.data(), b.size());
+  int bad = 0;
+  for (size_t i = 0; i < b.size(); ++i)
+    for (int bit = 0; bit < 8; ++bit) {
+      b[i] ^= (unsigned char)(1 << bit);
+      bad += twopaco::payload_checksum(b.data(), b.size()) == base;
+      b[i] ^= (unsigned char)(1 << bit);
+    }
+  std::vector<unsigned char> s = b;
+  for (int j = 0; j < 8; ++j) std::swap(s[j], s[8 + j]);
+  bad += twopaco::payload_checksum(s.data(), s.size()) == base;
+  bad += twopaco::payload_checksum(b.data(), b.size() - 1) == base;
+  std::vector<unsigned char> z(b);
+  z.push_back(0);
+  bad += twopaco::payload_checksum(z.data(), z.size()) == base;
+  bad += twopaco::payload_checksum(b.data(), b.size()) != base;
+  std::printf("%d %llu\n", bad, (unsigned long long)twopaco::payload_checksum("", 0));
+  return 0;
+}
+''')
+    csrc = os.path.join(ROOT, "paper_1602_05856_gb300", "csrc")
+    exe = tmp_path / "sum"
+    subprocess.run(["g++", "-std=c++17", "-O2", "-I", csrc, str(src), "-o", str(exe)], check=True)
+    bad, _ = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert bad == "0"

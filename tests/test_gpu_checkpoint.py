@@ -128,6 +128,13 @@ def test_foreign_checkpoints_are_refused():
     bad[0] ^= 1
     with pytest.raises(T().TwopacoError):
         _build(25, 4).restore(bytes(bad))
+    for at in (len(blob) - 1, len(blob) // 2):  # a payload bit changed after saving
+        bad = bytearray(blob)
+        bad[at] ^= 4
+        with pytest.raises(T().TwopacoError) as e:
+            _build(25, 4).restore(bytes(bad))
+        assert e.value.code == T().EINVAL
+    _build(25, 4).restore(blob)  # the undamaged checkpoint still loads
     with pytest.raises(T().TwopacoError):
         _build(25, 4).restore(blob[: len(blob) // 2])
     # the genuine one still works
