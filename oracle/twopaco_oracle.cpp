@@ -53,6 +53,14 @@
  *                      collisions; the exact bit layout is a design choice of
  *                      this project, not the paper's.
  *
+ *   oracle_partition_cuts  The greedy class cut of the multiple-rounds
+ *                      heuristic (section "Multiple Rounds") over given bin
+ *                      counters. PINNED by worked examples and, on random
+ *                      counters, by the greedy property: every class but the
+ *                      last stays within the total / l bound and could not
+ *                      take its next bin without passing it, unless it must
+ *                      leave a bin to each later class.
+ *
  * Conventions shared with the library (stated, not shared as code):
  *   bases A,C,G,T (either case) are 0,1,2,3; a k-mer is the integer with its
  *   first base most significant, so integer order is lexicographic order and
