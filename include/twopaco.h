@@ -216,18 +216,22 @@ int twopaco_run_rounds(const uint8_t* d_bases, const uint64_t* d_offsets, uint64
  * twopaco_checkpoint_save: after twopaco_run_rounds(..., round_end = r, ...)
  *   with 1 <= r <= rounds, copy the workspace's state into host_dst (bytes >=
  *   twopaco_checkpoint_bytes) with next_round = r; synchronises cuda_stream.
- *   Returns the run's failure (TWOPACO_EBADBASE / EOVERFLOW / ETIMEOUT) instead
- *   of saving a failed state.
+ *   The run's d_offsets must still hold the string offsets (they are part of
+ *   the input digest). Returns the run's failure (TWOPACO_EBADBASE /
+ *   EOVERFLOW / ETIMEOUT) instead of saving a failed state.
  *
  * twopaco_checkpoint_load: restore a checkpoint into a workspace (which may
  *   be a fresh one in another process), given the same input and
  *   parameters as the run it was taken from: the input is packed again and
- *   its digest compared. A checkpoint of another input, parameter set or
- *   format, or one whose contents changed after it was saved (each carries
- *   a checksum of its payload), is TWOPACO_EINVAL; nothing is launched
- *   before its head and payload check out. Synchronises
- *   options->cuda_stream; *next_round gets the round to continue with
- *   (twopaco_run_rounds(..., *next_round, rounds, ...)).
+ *   its digest compared. The digest covers the 2-bit packed bases, the
+ *   n_seqs + 1 string offsets (so moved string boundaries differ) and, with
+ *   split_at_n, the N mask (so a G changed to N or back differs: the packed
+ *   code of N is G's). A checkpoint of another input, parameter set or
+ *   format, or one whose head or payload changed after it was saved (each
+ *   carries a checksum of its whole head -- next_round, counters, digest --
+ *   and payload), is TWOPACO_EINVAL; nothing is launched before its head and
+ *   payload check out. Synchronises options->cuda_stream; *next_round gets
+ *   the round to continue with (twopaco_run_rounds(..., *next_round, rounds, ...)).
  */
 int twopaco_checkpoint_bytes(uint64_t total_bases, uint64_t n_seqs, int k, uint64_t filter_bits,
                              int rounds, const twopaco_options* opt, uint64_t* bytes);

@@ -22,23 +22,36 @@ _lib = None
 def lib() -> ctypes.CDLL:
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(_build.build())
-        P = ctypes.c_void_p
-        U64 = ctypes.c_uint64
-        I = ctypes.c_int
-        L.oracle_junctions.argtypes = [P, P, U64, I, I, I, P, P]
-        L.oracle_junctions_parallel.argtypes = [P, P, U64, I, I, I, I, P]
-        L.oracle_junctions_parallel.restype = I
-        L.oracle_alg1_exact.argtypes = [P, P, U64, I, I, I, P]
-        L.oracle_pass1.argtypes = [P, P, U64, I, I, I, U64, I, U64, U64, U64, P, P]
-        L.oracle_partition_cuts.argtypes = [P, U64, I, P]
-        L.oracle_edges.argtypes = [P, P, U64, I, I, I, P, P, P, P, P, P, P, P, P, P]
-        L.oracle_edges.restype = ctypes.c_longlong
-        for f in (L.oracle_junctions, L.oracle_alg1_exact, L.oracle_pass1,
-                  L.oracle_partition_cuts):
-            f.restype = I
-        _lib = L
+        _lib = _load(_build.build())
     return _lib
+
+
+def use_library(path):
+    """Test hook: make the wrappers call another build of the oracle (one with a
+    planted mistake); None goes back to the normal build. Returns the previous one."""
+    global _lib
+    prev = _lib
+    _lib = _load(path) if isinstance(path, str) else path
+    return prev
+
+
+def _load(path: str) -> ctypes.CDLL:
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    U64 = ctypes.c_uint64
+    I = ctypes.c_int
+    L.oracle_junctions.argtypes = [P, P, U64, I, I, I, P, P]
+    L.oracle_junctions_parallel.argtypes = [P, P, U64, I, I, I, I, P]
+    L.oracle_junctions_parallel.restype = I
+    L.oracle_alg1_exact.argtypes = [P, P, U64, I, I, I, P]
+    L.oracle_pass1.argtypes = [P, P, U64, I, I, I, U64, I, U64, U64, U64, P, P]
+    L.oracle_partition_cuts.argtypes = [P, U64, I, P]
+    L.oracle_edges.argtypes = [P, P, U64, I, I, I, P, P, P, P, P, P, P, P, P, P]
+    L.oracle_edges.restype = ctypes.c_longlong
+    for f in (L.oracle_junctions, L.oracle_alg1_exact, L.oracle_pass1,
+              L.oracle_partition_cuts):
+        f.restype = I
+    return L
 
 
 class OracleError(RuntimeError):

@@ -84,6 +84,15 @@
 
 typedef unsigned __int128 u128;
 
+// Test builds define ORACLE_MUTANT = n to plant one known mistake, numbered
+// where it is planted; each such build must fail a named pin of the tests
+// (tests/test_oracle_mutations.py). Otherwise it is 0 and every planted
+// branch compiles away.
+#ifndef ORACLE_MUTANT
+#define ORACLE_MUTANT 0
+#endif
+#define MUTANT(n) (ORACLE_MUTANT == (n))
+
 namespace {
 
 // A k-mer of 64 to 128 bases: four 64-bit words, w[0] the most significant,
@@ -271,18 +280,23 @@ int junctions_impl(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int 
       W v = word_at<W>(codes, s0 + i, k);
       W r = both_strands ? reverse_complement(v, k) : v;
       W key = (both_strands && r < v) ? r : v;
+      if (MUTANT(3)) key = (both_strands && v < r) ? r : v;  // planted 3: stored under the maximum
       Degrees& d = deg[key];
       const bool has_pred = i >= 1, has_succ = i + k < len;
+      const uint64_t succ_at = s0 + i + k - (MUTANT(5) ? 1 : 0);  // planted 5: successor one base early
       if (key == v) {  // forward occurrence of the normalized k-mer
         if (has_pred) d.in |= (uint8_t)(1u << codes[s0 + i - 1]);
-        if (has_succ) d.out |= (uint8_t)(1u << codes[s0 + i + k]);
+        if (has_succ) d.out |= (uint8_t)(1u << codes[succ_at]);
       }
-      if (both_strands && key == r) {  // occurrence on the other strand
-        if (has_succ) d.in |= (uint8_t)(1u << (3 - codes[s0 + i + k]));
+      // planted 7: a palindrome takes only its forward orientation
+      if (both_strands && key == r && !(MUTANT(7) && key == v)) {  // occurrence on the other strand
+        // planted 2: the other strand's predecessor not complemented
+        if (has_succ) d.in |= (uint8_t)(1u << (MUTANT(2) ? codes[s0 + i + k] : 3 - codes[s0 + i + k]));
         if (has_pred) d.out |= (uint8_t)(1u << (3 - codes[s0 + i - 1]));
       }
     }
     // Step 3: first and last k-mer of the string are sentinels.
+    if (MUTANT(1)) continue;  // planted 1: no sentinels
     sentinels.insert(normalized(word_at<W>(codes, s0, k), k, both_strands));
     sentinels.insert(normalized(word_at<W>(codes, s0 + len - k, k), k, both_strands));
   }
@@ -290,10 +304,12 @@ int junctions_impl(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int 
   for (const Piece& pc : S) {
     const uint64_t s0 = pc.s0, len = pc.len;
     if (len < (uint64_t)k) continue;
-    for (uint64_t i = 0; i + k <= len; ++i) {
+    // planted 4: the last k-mer of a string never flagged
+    for (uint64_t i = 0; MUTANT(4) ? i + k < len : i + k <= len; ++i) {
       W key = normalized(word_at<W>(codes, s0 + i, k), k, both_strands);
       const Degrees& d = deg[key];
-      bool junction = sentinels.count(key) || popcount4(d.in) > 1 || popcount4(d.out) > 1;
+      const int branch = MUTANT(6) ? 0 : 1;  // planted 6: one edge already counts as a branch
+      bool junction = sentinels.count(key) || popcount4(d.in) > branch || popcount4(d.out) > branch;
       flags[s0 + i] = junction ? 1 : 0;
     }
   }
@@ -339,6 +355,7 @@ void junctions_part(const std::vector<uint8_t>& codes, const std::vector<Piece>&
     }
     const W first = normalized(word_at<W>(codes, s0, k), k, both_strands);
     const W last = normalized(word_at<W>(codes, s0 + len - k, k), k, both_strands);
+    if (MUTANT(12)) continue;  // planted 12: the split definition forgets the sentinels
     if (mine(first)) sentinels.insert(first);
     if (mine(last)) sentinels.insert(last);
   }
@@ -400,7 +417,8 @@ int alg1_impl(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
     for (uint64_t i = 1; i + k < len; ++i) {
       if (!marks[s0 + i]) continue;
       W v = word_at<W>(codes, s0 + i, k);
-      if (sentinels.count(normalized(v, k, both_strands))) continue;
+      // planted 8: the sentinel test skipped (it is on the k-mer, not the position)
+      if (!MUTANT(8) && sentinels.count(normalized(v, k, both_strands))) continue;
       int in = 0, out = 0;
       for (int c = 0; c < 4; ++c) {
         W vc = (v << 2) | W(c);                    // v . c
@@ -537,7 +555,7 @@ int pass1_impl(const uint8_t* seq, const uint64_t* offsets, uint64_t n, int k,
           if (!keep) {
             int present = 0;
             for (int j = 0; j < 16; ++j) present += filter_has(F, f, hashes, j) ? 1 : 0;
-            keep = present >= 2;
+            keep = present >= (MUTANT(9) ? 1 : 2);  // planted 9: one present item keeps it
           }
           if (keep) {
             marks[s0 + i] = 1;
@@ -593,7 +611,7 @@ long long edges_impl(const uint8_t* seq, const uint64_t* offsets, uint64_t n, in
         from_rc[e] = (na != a) ? 1 : 0;
         to_rc[e] = (nb != b) ? 1 : 0;
         start[e] = s0 + prev - offsets[t];  // offset in the input string
-        length[e] = i - prev;
+        length[e] = i - prev + (MUTANT(11) ? 1 : 0);  // planted 11: length off by one
         ++e;
         if (edges_per_string) ++edges_per_string[t];
       }
@@ -687,7 +705,8 @@ int oracle_partition_cuts(const uint64_t* counts, uint64_t q, int l, uint64_t* c
     u128 sum = 0;
     uint64_t start = j;
     // at least one bin, and leave at least one bin for each later class
-    while (j < q - (uint64_t)(l - 1 - r)) {
+    // planted 10: no bin left over for the later classes
+    while (j < (MUTANT(10) ? q : q - (uint64_t)(l - 1 - r))) {
       if (j > start && (sum + counts[j]) * (u128)l > total) break;
       sum += counts[j];
       ++j;

@@ -429,9 +429,20 @@ struct CheckpointHead {
   int32_t k, rounds, hashes, both, split, next_round, lg_blocks;
   uint64_t m, n_seqs, q, bitmap_words, input_digest;
   uint64_t positions, pass1_kept, pass2_kept, table_max;
-  uint64_t payload_sum;  // payload_checksum of everything after the head
+  uint64_t checksum;  // checkpoint_checksum: this head (with this field 0) and the payload
 };
+static_assert(sizeof(CheckpointHead) == 120, "no padding: every byte of the head is checksummed");
 constexpr char kCheckpointMagic[8] = {'T', 'P', 'C', 'K', 'P', 'T', '0', '1'};
+constexpr uint32_t kCheckpointVersion = 3;
+
+// Checksum of a whole checkpoint: the head with its checksum field zeroed,
+// then the payload, so that a change to any field that steers the resume
+// (next_round, the counters, the digest) is refused like a payload change.
+uint64_t checkpoint_checksum(const CheckpointHead& head, const char* payload, uint64_t n) {
+  CheckpointHead z = head;
+  z.checksum = 0;
+  return checksum_mix(payload_checksum(&z, sizeof(z)) + 0x9e3779b97f4a7c15ull) ^ payload_checksum(payload, n);
+}
 
 uint64_t checkpoint_bytes(uint64_t m, int rounds, uint64_t q) {
   const uint64_t words = (m + 31) / 32;
@@ -468,14 +479,15 @@ int twopaco_checkpoint_save(void* d_workspace, int next_round, void* host_dst, u
   if (!h.packed || next_round < 1 || (uint64_t)next_round > h.rounds) return TWOPACO_EINVAL;
   const int rounds = (int)h.rounds;
   if (bytes < checkpoint_bytes(h.m, rounds, h.q)) return TWOPACO_EINVAL;
-  if (launch_digest(hd, h.packed, h.packed_words, s) < 0) return TWOPACO_ECUDA;
+  if (launch_digest(hd, h.packed, h.packed_words, h.offsets, h.n_seqs, h.nmask, h.bitmap_words, s) < 0)
+    return TWOPACO_ECUDA;
   unsigned long long digest = 0;
   if ((e = cudaMemcpyAsync(&digest, &hd->input_digest, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return cuda_code(e);
   CheckpointHead c{};
   std::memcpy(c.magic, kCheckpointMagic, 8);
-  c.version = 2;
+  c.version = kCheckpointVersion;
   c.k = h.k;
   c.rounds = rounds;
   c.hashes = h.hashes;
@@ -503,8 +515,8 @@ int twopaco_checkpoint_save(void* d_workspace, int next_round, void* host_dst, u
   }
   if (h.bitmap_words && (e = cudaMemcpy(out, h.cfinal, 4 * h.bitmap_words, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_code(e);
-  // the head last, with the checksum of the payload just written
-  c.payload_sum = payload_checksum(static_cast<const char*>(host_dst) + sizeof(c),
+  // the head last, with the checksum of itself and the payload just written
+  c.checksum = checkpoint_checksum(c, static_cast<const char*>(host_dst) + sizeof(c),
                                    checkpoint_bytes(h.m, rounds, h.q) - sizeof(c));
   std::memcpy(host_dst, &c, sizeof(c));
   return TWOPACO_OK;
@@ -526,15 +538,15 @@ int twopaco_checkpoint_load(const uint8_t* d_bases, const uint64_t* d_offsets, u
   CheckpointHead c;
   std::memcpy(&c, host_src, sizeof(c));
   const uint64_t q = o.partition_bins;
-  if (std::memcmp(c.magic, kCheckpointMagic, 8) || c.version != 2 || c.k != k || c.rounds != rounds ||
+  if (std::memcmp(c.magic, kCheckpointMagic, 8) || c.version != kCheckpointVersion || c.k != k || c.rounds != rounds ||
       c.hashes != o.hashes || c.both != o.both_strands || c.split != o.split_at_n ||
       c.lg_blocks != log2_exact(filter_bits / 256) || c.m != total_bases || c.n_seqs != n_seqs ||
       c.q != q || c.bitmap_words != L.bitmap_words || c.next_round < 1 || c.next_round > rounds ||
       bytes < checkpoint_bytes(total_bases, rounds, q))
     return TWOPACO_EINVAL;
-  // a payload changed since it was saved is refused
+  // a head or payload changed since it was saved is refused
   const char* payload = static_cast<const char*>(host_src) + sizeof(c);
-  if (payload_checksum(payload, checkpoint_bytes(total_bases, rounds, q) - sizeof(c)) != c.payload_sum)
+  if (checkpoint_checksum(c, payload, checkpoint_bytes(total_bases, rounds, q) - sizeof(c)) != c.checksum)
     return TWOPACO_EINVAL;
   // a class cut must cover the q bins in rounds non-empty, ascending ranges
   // (written only for rounds > 1 and a non-empty input)
@@ -551,7 +563,8 @@ int twopaco_checkpoint_load(const uint8_t* d_bases, const uint64_t* d_offsets, u
   cudaStream_t s = static_cast<cudaStream_t>(o.cuda_stream);
   DevHeader* hd = v.hdr;
   if (launch_init(v, s) < 0 || launch_pack(v, s) < 0) return TWOPACO_ECUDA;
-  if (launch_digest(hd, v.packed, v.packed_words, s) < 0) return TWOPACO_ECUDA;
+  if (launch_digest(hd, v.packed, v.packed_words, v.offsets, n_seqs, v.nmask, v.bitmap_words, s) < 0)
+    return TWOPACO_ECUDA;
   unsigned long long digest = 0, bad = 0;
   cudaError_t e;
   if ((e = cudaMemcpyAsync(&digest, &hd->input_digest, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||

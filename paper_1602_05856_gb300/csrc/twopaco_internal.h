@@ -44,7 +44,8 @@ struct DevHeader {
   uint32_t* run_rank;
   unsigned long long n_runs;
   unsigned long long run_cap;
-  // what a checkpoint records about the run
+  // what a checkpoint records about the run (and the input it digests)
+  const uint64_t* offsets;
   unsigned long long n_seqs;
   int hashes;
   int lg_blocks;
@@ -145,9 +146,14 @@ inline uint64_t cand_record_bytes(int) { return 8; }
 int launch_round_wide(const RunView& v, int round, int rounds, cudaStream_t s);
 int launch_partition_count_wide(const RunView& v, cudaStream_t s);
 
-// Sum over the packed input words w of mix64(index << 32 ^ w), into
-// hdr->input_digest (order-free, so the same input always gives the same value).
-int launch_digest(DevHeader* hdr_dev, const uint32_t* packed, uint64_t words, cudaStream_t s);
+// Digest of a run's input into hdr->input_digest: an order-free sum over the
+// packed words (the bases), the n_seqs + 1 string offsets (the boundaries,
+// which decide the sentinels and where edges stop) and, with N splitting,
+// the nmask_words words of the N mask (nmask null without it), each term
+// mixed with its index and its kind, so that the same input always gives the
+// same value and a change to any of the three changes it.
+int launch_digest(DevHeader* hdr_dev, const uint32_t* packed, uint64_t words, const uint64_t* offsets,
+                  uint64_t n_seqs, const uint32_t* nmask, uint64_t nmask_words, cudaStream_t s);
 
 // One bounded wait on *word (which the caller leaves 0): *status = 1 when it
 // gives up, 2 if it saw the word set.

@@ -870,6 +870,7 @@ __global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
     h->runs = v.runs;
     h->run_rank = v.run_rank;
     h->run_cap = v.run_cap;
+    h->offsets = v.offsets;
     h->n_seqs = v.n_seqs;
     h->hashes = v.hashes;
     h->lg_blocks = v.lg_blocks;
@@ -913,12 +914,19 @@ __global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
   zero(v.tile_prefix, (v.n_tiles + 1) / 2 * 16);
 }
 
-// Digest of the packed input (checkpoints record it and check it on resume).
-__global__ void __launch_bounds__(kBlock) digest_kernel(DevHeader* hdr, const uint32_t* packed, uint64_t words) {
+// Digest of the input (checkpoints record it and check it on resume): the
+// packed words, the string offsets and the N mask, each term tagged with its
+// kind and index.
+__global__ void __launch_bounds__(kBlock) digest_kernel(DevHeader* hdr, const uint32_t* packed, uint64_t words,
+                                                        const uint64_t* offsets, uint64_t n_off,
+                                                        const uint32_t* nmask, uint64_t nmask_words) {
   const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+  const uint64_t tid = (uint64_t)blockIdx.x * kBlock + threadIdx.x;
   unsigned long long d = 0;
-  for (uint64_t w = (uint64_t)blockIdx.x * kBlock + threadIdx.x; w < words; w += stride)
-    d += mix64((w << 32) ^ packed[w]);
+  for (uint64_t w = tid; w < words; w += stride) d += mix64((w << 32) ^ packed[w]);
+  for (uint64_t t = tid; t < n_off; t += stride) d += mix64(mix64(t ^ 0x6f66667365747321ull) ^ offsets[t]);
+  if (nmask)
+    for (uint64_t w = tid; w < nmask_words; w += stride) d += mix64(mix64(w ^ 0x6e6d61736b212121ull) ^ nmask[w]);
   block_add(d, &hdr->input_digest);
 }
 
@@ -1946,9 +1954,11 @@ int launch_init(const RunView& v, cudaStream_t s) {
   return cudaMemsetAsync(v.hdr, 0, sizeof(DevHeader), s) == cudaSuccess ? 0 : -1;
 }
 
-int launch_digest(DevHeader* hdr_dev, const uint32_t* packed, uint64_t words, cudaStream_t s) {
+int launch_digest(DevHeader* hdr_dev, const uint32_t* packed, uint64_t words, const uint64_t* offsets,
+                  uint64_t n_seqs, const uint32_t* nmask, uint64_t nmask_words, cudaStream_t s) {
   if (cudaMemsetAsync(&hdr_dev->input_digest, 0, sizeof(unsigned long long), s) != cudaSuccess) return -1;
-  digest_kernel<<<grid_for(digest_kernel, kBlock, words), kBlock, 0, s>>>(hdr_dev, packed, words);
+  digest_kernel<<<grid_for(digest_kernel, kBlock, words), kBlock, 0, s>>>(hdr_dev, packed, words, offsets,
+                                                                         n_seqs + 1, nmask, nmask_words);
   return done(1);
 }
 

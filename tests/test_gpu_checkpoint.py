@@ -143,6 +143,71 @@ def test_foreign_checkpoints_are_refused():
     _eq(d.result(), O.junctions(_input(), 25))
 
 
+# Byte offsets of head fields in a checkpoint (the head is 120 bytes: magic,
+# version, seven int32 parameters, then 64-bit fields).
+NEXT_ROUND_AT, POSITIONS_AT, PASS2_AT = 32, 80, 96
+
+
+def test_changed_head_fields_are_refused():
+    """The checksum covers the head: a resume point or counter edited after saving is
+    refused (a next_round moved from 2 to 3 would otherwise skip round 2 silently)."""
+    import struct
+    a = _build(25, 4)
+    a.run_rounds(0, 2)
+    blob = a.checkpoint(2)
+    assert struct.unpack_from("<i", blob, NEXT_ROUND_AT)[0] == 2
+    for at, fmt, value in ((NEXT_ROUND_AT, "<i", 3), (POSITIONS_AT, "<Q", 12345),
+                           (PASS2_AT, "<Q", 1)):
+        bad = bytearray(blob)
+        struct.pack_into(fmt, bad, at, value)
+        with pytest.raises(T().TwopacoError) as e:
+            _build(25, 4).restore(bytes(bad))
+        assert e.value.code == T().EINVAL
+    b = _build(25, 4)
+    b.run_rounds(b.restore(blob), 4)
+    _eq(b.result(), O.junctions(_input(), 25))
+
+
+def test_checkpoint_of_moved_boundaries_is_refused():
+    """Same bases, same number of strings, other string boundaries: other sentinels and
+    other edges, so the digest (which covers the offsets) differs."""
+    bases, off = _input()
+    a = T().DeviceBuild(bases, off, 25, 1 << 20, 3, T().Options(hashes=4, partition_bins=256))
+    a.run_rounds(0, 1)
+    blob = a.checkpoint(1)
+    moved = off.copy()
+    moved[1] += 7
+    b = T().DeviceBuild(bases, moved, 25, 1 << 20, 3, T().Options(hashes=4, partition_bins=256))
+    with pytest.raises(T().TwopacoError) as e:
+        b.restore(blob)
+    assert e.value.code == T().EINVAL
+    c = T().DeviceBuild(bases, off, 25, 1 << 20, 3, T().Options(hashes=4, partition_bins=256))
+    c.run_rounds(c.restore(blob), 3)
+    _eq(c.result(), O.junctions((bases, off), 25))
+
+
+def test_checkpoint_of_g_and_n_swapped_is_refused():
+    """With split_at_n an N packs to G's code; the digest covers the N mask, so an input
+    with one G changed to N (or back) does not pass for the one checkpointed."""
+    bases, off = _input(split=True)
+    opts = T().Options(hashes=4, partition_bins=256, split_at_n=True)
+    a = T().DeviceBuild(bases, off, 25, 1 << 20, 3, opts)
+    a.run_rounds(0, 2)
+    blob = a.checkpoint(2)
+    g_at = int(np.flatnonzero(bases == ord("G"))[100])
+    n_at = int(np.flatnonzero((bases == ord("N")) | (bases == ord("n")))[0])
+    for at, byte in ((g_at, ord("N")), (n_at, ord("G"))):
+        other = bases.copy()
+        other[at] = byte
+        b = T().DeviceBuild(other, off, 25, 1 << 20, 3, opts)
+        with pytest.raises(T().TwopacoError) as e:
+            b.restore(blob)
+        assert e.value.code == T().EINVAL
+    c = T().DeviceBuild(bases, off, 25, 1 << 20, 3, opts)
+    c.run_rounds(c.restore(blob), 3)
+    _eq(c.result(), O.junctions((bases, off), 25, split_n=True))
+
+
 def test_finished_run_output_from_its_last_checkpoint():
     a = _build(25, 2)
     a.run()

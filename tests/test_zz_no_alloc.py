@@ -5,8 +5,9 @@ memory (their host framework's pool owns it all, or cudaMalloc's implicit
 synchronisation is not affordable): its workspace is a fixed static device
 buffer. This test calls it twice in a row through the C ABI and checks both
 results, element by element, against twopaco_run_device with a workspace
-allocated here, and that an input too large for the buffer is rejected.
-Junction positions are integers: the comparison is exact.
+allocated here and against the CPU oracle's junctions, and that an input too
+large for the buffer is rejected. Junction positions are integers: the
+comparison is exact.
 """
 import numpy as np
 import pytest
@@ -67,6 +68,10 @@ def test_noalloc_matches_workspace_run_twice(lib):
     ref_stats = T.twopaco_read_stats(ws_ptr)
     want_off, want_pos = _split(ref_off, ref_pos)
     assert want_pos.size > 0
+    import oracle as O
+    by_definition = O.junctions((bases, off), k)
+    assert np.array_equal(np.diff(want_off.astype(np.int64)), [w.size for w in by_definition])
+    assert np.array_equal(want_pos, np.concatenate(by_definition))
 
     # the entry point that allocates nothing, twice in a row on the same buffer
     for _ in range(2):
