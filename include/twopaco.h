@@ -35,7 +35,7 @@
  *     [256, 2^40]; rounds >= 1; n_seqs < 2^32; total_bases < 2^48;
  *     options->hashes in [1, 8]; options->partition_bins a power of two
  *     >= rounds (and >= 2 when rounds > 1); options->both_strands and
- *     options->split_at_n 0 or 1; options->wide_layout 0, 1 or 2;
+ *     options->split_at_n and options->partial 0 or 1; options->wide_layout 0, 1 or 2;
  *     options->run_capacity < 2^32. Anything else is TWOPACO_EINVAL.
  *   - Calls on different workspaces may run concurrently from different host
  *     threads; calls that share a workspace must be serialised by the caller.
@@ -87,6 +87,15 @@ typedef struct twopaco_options {
                               descriptors. 2: as 1, and pass 2 also keeps no table
                               slots (the layout of tables of 2^32 slots and more). Same
                               results; for testing those paths on small inputs. */
+  int partial;             /* 1: the partially compacted graph (Discussion section:
+                              the second pass of Algorithm 2 is omitted). The output
+                              is every position that survives the first pass -- in
+                              each round, C_temp of that round's class -- a candidate
+                              set that holds every junction plus Bloom-filter false
+                              positives, so that the edges between consecutive
+                              output positions are non-branching paths, though not
+                              all maximal. pass2_marks then counts the output
+                              positions. 0 (default): the exact junctions. */
 } twopaco_options;
 
 /* Counters of one run, in the spirit of Table 4 (marks after each pass). */

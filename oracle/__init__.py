@@ -164,14 +164,18 @@ def partition_cuts(counts: Sequence[int], rounds: int) -> np.ndarray:
     return cuts
 
 
-def edges(seqs, k: int, both_strands: bool = True, split_n: bool = False):
+def edges(seqs, k: int, both_strands: bool = True, split_n: bool = False, flags=None):
     """Compacted-graph edges by consecutive junction positions, as a dict of arrays.
 
     Keys: from_hi, from_lo, to_hi, to_lo (normalized k-mers), from_rc, to_rc,
     start, length (per edge, string order then position order) and
-    per_string (edge count of every string).
+    per_string (edge count of every string). With ``flags`` (one byte per
+    input byte) the edges join consecutive flagged positions instead of
+    consecutive junctions (a partially compacted graph).
     """
-    flags, off, _ = junction_flags(seqs, k, both_strands, split_n)
+    if flags is None:
+        flags, off, _ = junction_flags(seqs, k, both_strands, split_n)
+    flags = np.ascontiguousarray(flags, dtype=np.uint8)
     buf, off = _prep(seqs)
     nj = max(int(flags.sum()), 1)
     out = {name: np.zeros(nj, np.uint64) for name in ("from_hi", "from_lo", "to_hi", "to_lo",

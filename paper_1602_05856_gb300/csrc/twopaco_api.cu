@@ -51,6 +51,7 @@ int validate(uint64_t n_seqs, int k, uint64_t filter_bits, int rounds, const two
   if (o.split_at_n != 0 && o.split_at_n != 1) return TWOPACO_EINVAL;
   if (o.wide_layout < 0 || o.wide_layout > 2) return TWOPACO_EINVAL;
   if (o.run_capacity >= (1ull << 32)) return TWOPACO_EINVAL;  // piece ranks are 32-bit
+  if (o.partial != 0 && o.partial != 1) return TWOPACO_EINVAL;
   return TWOPACO_OK;
 }
 
@@ -87,6 +88,7 @@ Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int roun
   L.bitmap_words = (m + 31) / 32;
   L.n_tiles = (L.bitmap_words + kEmitTileWords - 1) / kEmitTileWords;
   L.table_slots = o.table_slots ? next_pow2(o.table_slots) : auto_table_slots(m, rounds);
+  if (o.partial) L.table_slots = 0;  // no second pass: no table, list or kept slots
   // 32-bit candidate records (31-bit positions and a sentinel flag) below 2^31 bases
   L.narrow = (m < (1ull << 31) && o.wide_layout == 0) ? 1 : 0;
   uint64_t at = 0;
@@ -116,6 +118,7 @@ Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int roun
   const uint64_t per_round = (m + (uint64_t)rounds - 1) / (uint64_t)rounds;
   L.cand_cap = o.candidate_records ? o.candidate_records
                                    : (per_round / 2 > (1u << 16) ? per_round / 2 : (1u << 16));
+  if (o.partial) L.cand_cap = 0;
   L.cands = at;
   at += align_up(L.cand_cap * cand_record_bytes(k));
   // the table slot of every listed candidate (32-bit slot indices), kept by
@@ -173,6 +176,7 @@ RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_
   v.both = o.both_strands;
   v.hashes = o.hashes;
   v.rounds = rounds;
+  v.partial = o.partial;
   v.lg_blocks = log2_exact(filter_bits / 256);
   v.qmask = o.partition_bins - 1u;
   v.hdr = reinterpret_cast<DevHeader*>(base + L.header);
@@ -263,6 +267,7 @@ void twopaco_default_options(twopaco_options* opt) {
   opt->split_at_n = 0;
   opt->run_capacity = 0;
   opt->wide_layout = 0;
+  opt->partial = 0;
 }
 
 const char* twopaco_strerror(int code) {
@@ -426,12 +431,12 @@ static_assert(offsetof(DevHeader, pass2_kept) == offsetof(DevHeader, positions) 
 struct CheckpointHead {
   char magic[8];  // "TPCKPT01"
   uint32_t version;
-  int32_t k, rounds, hashes, both, split, next_round, lg_blocks;
+  int32_t k, rounds, hashes, both, split, next_round, lg_blocks, partial, reserved;
   uint64_t m, n_seqs, q, bitmap_words, input_digest;
   uint64_t positions, pass1_kept, pass2_kept, table_max;
   uint64_t checksum;  // checkpoint_checksum: this head (with this field 0) and the payload
 };
-static_assert(sizeof(CheckpointHead) == 120, "no padding: every byte of the head is checksummed");
+static_assert(sizeof(CheckpointHead) == 128, "no padding: every byte of the head is checksummed");
 constexpr char kCheckpointMagic[8] = {'T', 'P', 'C', 'K', 'P', 'T', '0', '1'};
 constexpr uint32_t kCheckpointVersion = 3;
 
@@ -495,6 +500,7 @@ int twopaco_checkpoint_save(void* d_workspace, int next_round, void* host_dst, u
   c.split = h.nmask ? 1 : 0;
   c.next_round = next_round;
   c.lg_blocks = h.lg_blocks;
+  c.partial = h.partial;
   c.m = h.m;
   c.n_seqs = h.n_seqs;
   c.q = h.q;
@@ -539,7 +545,7 @@ int twopaco_checkpoint_load(const uint8_t* d_bases, const uint64_t* d_offsets, u
   std::memcpy(&c, host_src, sizeof(c));
   const uint64_t q = o.partition_bins;
   if (std::memcmp(c.magic, kCheckpointMagic, 8) || c.version != kCheckpointVersion || c.k != k || c.rounds != rounds ||
-      c.hashes != o.hashes || c.both != o.both_strands || c.split != o.split_at_n ||
+      c.hashes != o.hashes || c.both != o.both_strands || c.split != o.split_at_n || c.partial != o.partial ||
       c.lg_blocks != log2_exact(filter_bits / 256) || c.m != total_bases || c.n_seqs != n_seqs ||
       c.q != q || c.bitmap_words != L.bitmap_words || c.next_round < 1 || c.next_round > rounds ||
       bytes < checkpoint_bytes(total_bases, rounds, q))

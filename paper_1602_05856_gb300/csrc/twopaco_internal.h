@@ -49,6 +49,7 @@ struct DevHeader {
   unsigned long long n_seqs;
   int hashes;
   int lg_blocks;
+  int partial;
   unsigned long long packed_words;
   unsigned long long input_digest;  // written by launch_digest
   unsigned int out_overflow;        // the output positions did not fit (the offsets are exact)
@@ -66,6 +67,7 @@ struct RunView {
   int both;                 // comprehensive graph
   int hashes;               // bits per filter item
   int rounds;               // classes of Algorithm 3
+  int partial;              // omit pass 2: C_final gathers every round's C_temp
   int lg_blocks;            // log2(filter_bits / 256)
   uint32_t qmask;           // partition_bins - 1
   DevHeader* hdr;

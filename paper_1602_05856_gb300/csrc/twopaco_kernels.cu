@@ -874,6 +874,7 @@ __global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
     h->n_seqs = v.n_seqs;
     h->hashes = v.hashes;
     h->lg_blocks = v.lg_blocks;
+    h->partial = v.partial;
     h->packed_words = v.packed_words;
   }
   const bool vec = (reinterpret_cast<uintptr_t>(v.bases) & 15) == 0;
@@ -1152,7 +1153,7 @@ __global__ void __launch_bounds__(kBlock, 3) pass1_probe_kernel(RunView v, int r
         const uint32_t pres = present_items<HB>(G[i], word[i], v.hashes);
         if ((pres >> 16) || __popc(pres & 0xFFFFu) >= 2) keep_bits |= 1u << i;
       }
-      if ((keep_bits >> i) & 1u) {
+      if (((keep_bits >> i) & 1u) && !v.partial) {
         const uint64_t idx = (G[i] * 0xff51afd7ed558ccdull) >> (64 - v.lc_log2);
         atomicOr(v.lc_bits + (idx >> 5), 1u << (idx & 31));
       }
@@ -1163,7 +1164,15 @@ __global__ void __launch_bounds__(kBlock, 3) pass1_probe_kernel(RunView v, int r
     for (int o = 1; o < kLanesPerWord; o <<= 1) wv |= __shfl_xor_sync(0xffffffffu, wv, o);
     if (lane % kLanesPerWord == 0) {
       const uint64_t w = (wbase >> 5) + lane / kLanesPerWord;
-      if (w < v.bitmap_words) v.ctemp[w] = wv;
+      if (w < v.bitmap_words) {
+        v.ctemp[w] = wv;
+        if (v.partial) v.cfinal[w] |= wv;  // rounds own disjoint positions; one writer per word
+      }
+    }
+    if (v.partial) {
+      kept += __popc(keep_bits);
+      valid_n += __popc(valid_bits);
+      continue;
     }
     // candidate list: the warp appends to its own segment, in position order
     const uint32_t c = __popc(keep_bits);
@@ -1194,7 +1203,7 @@ __global__ void __launch_bounds__(kBlock, 3) pass1_probe_kernel(RunView v, int r
     if (seg_used > v.seg_cap) v.hdr->cand_overflow = 1;
   }
   block_add(kept, &v.hdr->pass1_kept);
-  block_add(kept, &v.hdr->round_kept);
+  block_add(kept, v.partial ? &v.hdr->pass2_kept : &v.hdr->round_kept);
   if (round == 0) block_add(valid_n, &v.hdr->positions);
 }
 
@@ -1262,6 +1271,10 @@ __global__ void __launch_bounds__(kBlock) pass1_probe_desc_kernel(RunView v, int
       valid_n += d[q] != 0;
       const uint32_t row = __ballot_sync(0xffffffffu, keep);
       if (lane == q) my_word = row;
+      if (v.partial) {
+        kept += keep;
+        continue;
+      }
       if (keep) {
         const uint64_t idx = ((d[q] & ~(kDescActive | kDescSentinel)) * 0xff51afd7ed558ccdull) >> (64 - v.lc_log2);
         atomicOr(v.lc_bits + (idx >> 5), 1u << (idx & 31));
@@ -1278,7 +1291,10 @@ __global__ void __launch_bounds__(kBlock) pass1_probe_desc_kernel(RunView v, int
     }
     if (lane < kRows) {
       const uint64_t w = (wbase >> 5) + lane;
-      if (w < v.bitmap_words) v.ctemp[w] = my_word;
+      if (w < v.bitmap_words) {
+        v.ctemp[w] = my_word;
+        if (v.partial) v.cfinal[w] |= my_word;  // rounds own disjoint positions; one writer per word
+      }
     }
   }
   if (lane == 0) {
@@ -1286,7 +1302,7 @@ __global__ void __launch_bounds__(kBlock) pass1_probe_desc_kernel(RunView v, int
     if (seg_used > v.seg_cap) v.hdr->cand_overflow = 1;
   }
   block_add(kept, &v.hdr->pass1_kept);
-  block_add(kept, &v.hdr->round_kept);
+  block_add(kept, v.partial ? &v.hdr->pass2_kept : &v.hdr->round_kept);
   if (round == 0) block_add(valid_n, &v.hdr->positions);
 }
 
@@ -2058,6 +2074,7 @@ int round_impl(const RunView& v, int round, cudaStream_t s) {
     if (desc) pass1_probe_desc_kernel<kDescOk ? HB : 1><<<grid, kBlock, 0, s>>>(pv, round);
     else pass1_probe_kernel<KW, RD, HB><<<grid, kBlock, 0, s>>>(pv, round);
   }
+  if (v.partial) return done(2);  // the partially compacted graph: no second pass
   {
     Timed t("table_setup", s);
     table_setup_kernel<<<grid_for(table_setup_kernel, kBlock, (1ull << v.lc_log2) / 32), kBlock, 0, s>>>(pv);

@@ -159,3 +159,21 @@ int main() {
     subprocess.run(["g++", "-std=c++17", "-O2", "-I", csrc, str(src), "-o", str(exe)], check=True)
     bad, _ = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
     assert bad == "0"
+
+
+def test_partial_option_checks_and_smaller_workspace():
+    """partial is 0 or 1; without the second pass the workspace holds no table, list
+    or kept slots."""
+    import ctypes
+    from paper_1602_05856_gb300 import build, twopaco as T
+    build.build()
+    o = T.Options()._c()
+    o.partial = 2
+    b = ctypes.c_uint64(0)
+    rc = T.load().twopaco_workspace_size(1000, 2, 25, 1 << 20, 1, ctypes.byref(o), ctypes.byref(b))
+    assert rc == T.EINVAL
+    m = 10**7
+    full = T.twopaco_workspace_size(m, 4, 25, 1 << 24, 1)
+    part = T.twopaco_workspace_size(m, 4, 25, 1 << 24, 1, T.Options(partial=True))
+    table = 8 * (1 << 25)  # next power of two of 2m one-word slots
+    assert full - part >= table

@@ -143,9 +143,9 @@ def test_foreign_checkpoints_are_refused():
     _eq(d.result(), O.junctions(_input(), 25))
 
 
-# Byte offsets of head fields in a checkpoint (the head is 120 bytes: magic,
-# version, seven int32 parameters, then 64-bit fields).
-NEXT_ROUND_AT, POSITIONS_AT, PASS2_AT = 32, 80, 96
+# Byte offsets of head fields in a checkpoint (the head is 128 bytes: magic,
+# version, nine int32 parameters, then 64-bit fields).
+NEXT_ROUND_AT, POSITIONS_AT, PASS2_AT = 32, 88, 104
 
 
 def test_changed_head_fields_are_refused():

@@ -288,6 +288,33 @@ def test_edges_are_the_maximal_nonbranching_paths(k, both):
     assert spelled == brute.compacted_paths(seqs, k, both)
 
 
+@pytest.mark.parametrize("k,both", [(6, True), (7, False), (9, True)])
+def test_partial_edges_are_nonbranching_paths(k, both):
+    """Edges between consecutive positions of a candidate set (the first pass's survivors,
+    the partially compacted graph of the Discussion section): each spells a path whose
+    inner k-mers are all non-junctions by brute force, every junction is an endpoint, and
+    with the junction set itself they are the maximal non-branching paths."""
+    seqs = [bytes(s).decode() for s in G.random_strings(500 + k, 4, 40, 300, b"ACGT")]
+    seqs.append(seqs[0][10:120] + seqs[1][:90])
+    marks, off, _, kept = O.pass1_marks(seqs, k, 1 << 9, 2, both_strands=both)
+    J = brute.junction_kmers(seqs, k, both)
+    flags, _, _ = O.junction_flags(seqs, k, both_strands=both)
+    assert kept > int(flags.sum()), "the small filter leaves false candidates"
+    e = O.edges(seqs, k, both_strands=both, flags=marks)
+    o = 0
+    for t, s in enumerate(seqs):
+        cand = np.flatnonzero(marks[int(off[t]):int(off[t + 1])])
+        assert int(e["per_string"][t]) == max(0, cand.size - 1)
+        for a, b in zip(cand, cand[1:]):
+            assert int(e["start"][o]) == a and int(e["length"][o]) == b - a
+            assert all(s[i:i + k] not in J for i in range(a + 1, b))
+            o += 1
+        for i in range(len(s) - k + 1):
+            if s[i:i + k] in J:
+                assert i in cand
+    assert o == e["start"].size
+
+
 def test_edges_fig1():
     e = O.edges(["TGGCACGTC", "TGGCACTTC"], 2, both_strands=False)
     # TG -> AC (TGGCAC), AC -> TC (ACGTC / ACTTC): Fig. 1b/1c
