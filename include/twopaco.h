@@ -213,6 +213,59 @@ int twopaco_run_rounds(const uint8_t* d_bases, const uint64_t* d_offsets, uint64
                        uint64_t* d_out_positions, uint64_t out_capacity);
 
 /*
+ * A run split over several devices by k-mer class (section "Multiple
+ * Rounds": every position belongs to exactly one class, each round of
+ * Algorithm 3 decides only the positions of its class, and C_final is the
+ * union of the rounds' C'_i, which are disjoint). Shard `shard` of `n_shards`
+ * (one per device, each with its own copy of the input and its own workspace)
+ * runs the rounds r with r % n_shards == shard over the whole input; the
+ * shards' C_final bitmaps are then merged -- a bitwise OR, which for these
+ * disjoint bitmaps equals an integer sum of their 32-bit words, so one
+ * all-reduce of the words does it -- and one of them writes the output.
+ *
+ * twopaco_shard_begin: pack the input into the workspace and clear C_final;
+ *   with compute_cut = 1 (and rounds > 1) also count the partition bins and
+ *   cut the classes (one shard, the leader, does this; the cut must be the
+ *   same on every shard, and two separate cuts of one input may differ).
+ *   compute_cut is 0 or 1, else TWOPACO_EINVAL. Launches without
+ *   synchronising; no output arguments.
+ *
+ * twopaco_shard_rounds: after twopaco_shard_begin on this workspace, run the
+ *   rounds shard, shard + n_shards, ... (< rounds), adding their junctions to
+ *   the workspace's C_final. d_class_cut: device memory holding the rounds + 1
+ *   uint32 class boundaries to use (the leader's, as read with
+ *   twopaco_state_device / twopaco_read_state), copied into the workspace on
+ *   options->cuda_stream before the first round; NULL keeps the cut the
+ *   workspace holds (the leader's own, or none needed when rounds == 1).
+ *   0 <= shard < n_shards, else TWOPACO_EINVAL. The counters of a shard
+ *   cover its own rounds; positions counts every k-mer position. Launches
+ *   without synchronising.
+ *
+ * After the merge into a workspace's C_final, twopaco_run_rounds(...,
+ * rounds, rounds, ...) on that workspace writes the output.
+ */
+int twopaco_shard_begin(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_seqs,
+                        uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
+                        const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
+                        int compute_cut);
+int twopaco_shard_rounds(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_seqs,
+                         uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
+                         const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
+                         int shard, int n_shards, const uint32_t* d_class_cut);
+
+/*
+ * Device address and size in bytes of one piece of a workspace's state
+ * (which: TWOPACO_STATE_*, laid out as twopaco_read_state describes), for a
+ * run with these parameters, so that a collective can read or write it in
+ * place: C_final for the merge of shards, the class cut for its broadcast.
+ * Host arithmetic only: no synchronisation, nothing launched. BINS of a
+ * one-round run is NULL with size 0.
+ */
+int twopaco_state_device(uint64_t total_bases, uint64_t n_seqs, int k, uint64_t filter_bits, int rounds,
+                         const twopaco_options* opt, void* d_workspace, int which, void** d_ptr,
+                         uint64_t* bytes);
+
+/*
  * Checkpoints between rounds (the paper has no counterpart; for runs long
  * enough that a failure should not restart every round). A checkpoint
  * holds what the finished rounds left: C_final (one bit per base), the class

@@ -294,25 +294,48 @@ int twopaco_workspace_size(uint64_t total_bases, uint64_t n_seqs, int k, uint64_
   return TWOPACO_OK;
 }
 
+}  // extern "C"
+
+namespace twopaco {
+namespace {
+
+// The checks every device-resident call makes before launching anything, and
+// the run's view of the workspace.
+int device_run_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_seqs,
+                    uint64_t total_bases, int k, uint64_t filter_bits, int rounds, const twopaco_options& o,
+                    void* d_workspace, uint64_t workspace_bytes, uint64_t* d_out_offsets,
+                    uint64_t* d_out_positions, uint64_t out_capacity, bool need_output, RunView* v) {
+  int rc = validate(n_seqs, k, filter_bits, rounds, o);
+  if (rc) return rc;
+  if (validate_size(total_bases)) return TWOPACO_EINVAL;
+  if (total_bases > 0 && (n_seqs == 0 || !d_bases || !d_offsets)) return TWOPACO_EINVAL;
+  if (n_seqs > 0 && !d_offsets) return TWOPACO_EINVAL;
+  if (need_output && (!d_out_offsets || (out_capacity && !d_out_positions))) return TWOPACO_EINVAL;
+  if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) % kAlign)) return TWOPACO_EINVAL;
+  const Layout L = layout(total_bases, n_seqs, k, filter_bits, rounds, o);
+  if (workspace_bytes < L.total) return TWOPACO_EINVAL;
+  *v = make_view(d_bases, d_offsets, n_seqs, total_bases, k, filter_bits, rounds, o, L, d_workspace,
+                 d_out_offsets, d_out_positions, out_capacity);
+  return TWOPACO_OK;
+}
+
+}  // namespace
+}  // namespace twopaco
+
+extern "C" {
+
 int twopaco_run_rounds(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_seqs,
                        uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
                        const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
                        int round_begin, int round_end, uint64_t* d_out_offsets,
                        uint64_t* d_out_positions, uint64_t out_capacity) {
   const twopaco_options o = resolve(opt);
-  int rc = validate(n_seqs, k, filter_bits, rounds, o);
+  RunView v;
+  int rc = device_run_view(d_bases, d_offsets, n_seqs, total_bases, k, filter_bits, rounds, o, d_workspace,
+                           workspace_bytes, d_out_offsets, d_out_positions, out_capacity, true, &v);
   if (rc) return rc;
-  if (validate_size(total_bases)) return TWOPACO_EINVAL;
   if (round_begin < 0 || round_end > rounds || round_begin > round_end) return TWOPACO_EINVAL;
   if (round_begin == round_end && round_end != rounds) return TWOPACO_EINVAL;
-  if (total_bases > 0 && (n_seqs == 0 || !d_bases || !d_offsets)) return TWOPACO_EINVAL;
-  if (n_seqs > 0 && !d_offsets) return TWOPACO_EINVAL;
-  if (!d_out_offsets || (out_capacity && !d_out_positions)) return TWOPACO_EINVAL;
-  if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) % kAlign)) return TWOPACO_EINVAL;
-  const Layout L = layout(total_bases, n_seqs, k, filter_bits, rounds, o);
-  if (workspace_bytes < L.total) return TWOPACO_EINVAL;
-  const RunView v = make_view(d_bases, d_offsets, n_seqs, total_bases, k, filter_bits, rounds, o, L,
-                              d_workspace, d_out_offsets, d_out_positions, out_capacity);
   cudaStream_t s = static_cast<cudaStream_t>(o.cuda_stream);
   if (round_begin == 0) {  // a new run: pack, and the class cut of Algorithm 3
     if (launch_init(v, s) < 0) return TWOPACO_ECUDA;
@@ -322,6 +345,64 @@ int twopaco_run_rounds(const uint8_t* d_bases, const uint64_t* d_offsets, uint64
   for (int r = round_begin; r < round_end; ++r)
     if (launch_round(v, r, rounds, s) < 0) return TWOPACO_ECUDA;
   if (round_end == rounds && launch_emit(v, s, round_begin == rounds) < 0) return TWOPACO_ECUDA;
+  return TWOPACO_OK;
+}
+
+int twopaco_shard_begin(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_seqs,
+                        uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
+                        const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
+                        int compute_cut) {
+  const twopaco_options o = resolve(opt);
+  RunView v;
+  int rc = device_run_view(d_bases, d_offsets, n_seqs, total_bases, k, filter_bits, rounds, o, d_workspace,
+                           workspace_bytes, nullptr, nullptr, 0, false, &v);
+  if (rc) return rc;
+  if (compute_cut != 0 && compute_cut != 1) return TWOPACO_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(o.cuda_stream);
+  if (launch_init(v, s) < 0 || launch_pack(v, s) < 0) return TWOPACO_ECUDA;
+  if (compute_cut && rounds > 1 && launch_partition(v, rounds, s) < 0) return TWOPACO_ECUDA;
+  return TWOPACO_OK;
+}
+
+int twopaco_shard_rounds(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_seqs,
+                         uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
+                         const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
+                         int shard, int n_shards, const uint32_t* d_class_cut) {
+  const twopaco_options o = resolve(opt);
+  RunView v;
+  int rc = device_run_view(d_bases, d_offsets, n_seqs, total_bases, k, filter_bits, rounds, o, d_workspace,
+                           workspace_bytes, nullptr, nullptr, 0, false, &v);
+  if (rc) return rc;
+  if (n_shards < 1 || shard < 0 || shard >= n_shards) return TWOPACO_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(o.cuda_stream);
+  if (d_class_cut && rounds > 1 &&
+      cudaMemcpyAsync(v.cuts, d_class_cut, 4 * ((uint64_t)rounds + 1), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return TWOPACO_ECUDA;
+  v.count_round = shard;  // every shard counts the positions in its first round
+  for (int r = shard; r < rounds; r += n_shards)
+    if (launch_round(v, r, rounds, s) < 0) return TWOPACO_ECUDA;
+  return TWOPACO_OK;
+}
+
+int twopaco_state_device(uint64_t total_bases, uint64_t n_seqs, int k, uint64_t filter_bits, int rounds,
+                         const twopaco_options* opt, void* d_workspace, int which, void** d_ptr,
+                         uint64_t* bytes) {
+  const twopaco_options o = resolve(opt);
+  int rc = validate(n_seqs, k, filter_bits, rounds, o);
+  if (rc) return rc;
+  if (validate_size(total_bases) || !d_workspace || !d_ptr || !bytes) return TWOPACO_EINVAL;
+  const Layout L = layout(total_bases, n_seqs, k, filter_bits, rounds, o);
+  char* base = static_cast<char*>(d_workspace);
+  switch (which) {
+    case TWOPACO_STATE_CANDIDATES: *d_ptr = base + L.ctemp; *bytes = L.bitmap_words * 4; break;
+    case TWOPACO_STATE_JUNCTIONS: *d_ptr = base + L.cfinal; *bytes = L.bitmap_words * 4; break;
+    case TWOPACO_STATE_BINS:
+      *d_ptr = rounds > 1 ? base + L.bins : nullptr;
+      *bytes = rounds > 1 ? (uint64_t)o.partition_bins * 4 : 0;
+      break;
+    case TWOPACO_STATE_CUTS: *d_ptr = base + L.cuts; *bytes = ((uint64_t)rounds + 1) * 4; break;
+    default: return TWOPACO_EINVAL;
+  }
   return TWOPACO_OK;
 }
 

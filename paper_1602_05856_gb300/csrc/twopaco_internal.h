@@ -68,6 +68,7 @@ struct RunView {
   int hashes;               // bits per filter item
   int rounds;               // classes of Algorithm 3
   int partial;              // omit pass 2: C_final gathers every round's C_temp
+  int count_round;          // the round whose probe counts the input's k-mer positions
   int lg_blocks;            // log2(filter_bits / 256)
   uint32_t qmask;           // partition_bins - 1
   DevHeader* hdr;

@@ -1204,7 +1204,7 @@ __global__ void __launch_bounds__(kBlock, 3) pass1_probe_kernel(RunView v, int r
   }
   block_add(kept, &v.hdr->pass1_kept);
   block_add(kept, v.partial ? &v.hdr->pass2_kept : &v.hdr->round_kept);
-  if (round == 0) block_add(valid_n, &v.hdr->positions);
+  if (round == v.count_round) block_add(valid_n, &v.hdr->positions);
 }
 
 // The probe loop from descriptors (same decisions and outputs as
@@ -1303,7 +1303,7 @@ __global__ void __launch_bounds__(kBlock) pass1_probe_desc_kernel(RunView v, int
   }
   block_add(kept, &v.hdr->pass1_kept);
   block_add(kept, v.partial ? &v.hdr->pass2_kept : &v.hdr->round_kept);
-  if (round == 0) block_add(valid_n, &v.hdr->positions);
+  if (round == v.count_round) block_add(valid_n, &v.hdr->positions);
 }
 
 // Table slots per estimated distinct candidate: 2.5 for one-word slots

@@ -102,6 +102,14 @@ def _lib() -> ctypes.CDLL:
         L.twopaco_run_rounds.argtypes = [P, P, U64, U64, I, U64, I, ctypes.POINTER(_Options), P, U64,
                                          I, I, P, P, U64]
         L.twopaco_run_rounds.restype = I
+        L.twopaco_shard_begin.argtypes = [P, P, U64, U64, I, U64, I, ctypes.POINTER(_Options), P, U64, I]
+        L.twopaco_shard_begin.restype = I
+        L.twopaco_shard_rounds.argtypes = [P, P, U64, U64, I, U64, I, ctypes.POINTER(_Options), P, U64,
+                                           I, I, P]
+        L.twopaco_shard_rounds.restype = I
+        L.twopaco_state_device.argtypes = [U64, U64, I, U64, I, ctypes.POINTER(_Options), P, I,
+                                           ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(U64)]
+        L.twopaco_state_device.restype = I
         L.twopaco_selftest_bounded_wait.argtypes = [P]
         L.twopaco_selftest_bounded_wait.restype = I
         L.twopaco_checkpoint_bytes.argtypes = [U64, U64, I, U64, I, ctypes.POINTER(_Options),
@@ -340,6 +348,51 @@ def twopaco_run_rounds(d_bases: int, d_offsets: int, n_seqs: int, total_bases: i
         raise TwopacoError(rc, "twopaco_run_rounds")
 
 
+def twopaco_shard_begin(d_bases: int, d_offsets: int, n_seqs: int, total_bases: int, k: int,
+                        filter_bits: int, rounds: int, options: Optional[Options], d_workspace: int,
+                        workspace_bytes: int, compute_cut: bool) -> None:
+    opt = (options or Options())._c()
+    rc = _lib().twopaco_shard_begin(d_bases or None, d_offsets or None, int(n_seqs), int(total_bases),
+                                    int(k), int(filter_bits), int(rounds), ctypes.byref(opt),
+                                    d_workspace or None, int(workspace_bytes), int(bool(compute_cut)))
+    if rc != OK:
+        raise TwopacoError(rc, "twopaco_shard_begin")
+
+
+def twopaco_shard_rounds(d_bases: int, d_offsets: int, n_seqs: int, total_bases: int, k: int,
+                         filter_bits: int, rounds: int, options: Optional[Options], d_workspace: int,
+                         workspace_bytes: int, shard: int, n_shards: int, d_class_cut: int = 0) -> None:
+    opt = (options or Options())._c()
+    rc = _lib().twopaco_shard_rounds(d_bases or None, d_offsets or None, int(n_seqs), int(total_bases),
+                                     int(k), int(filter_bits), int(rounds), ctypes.byref(opt),
+                                     d_workspace or None, int(workspace_bytes), int(shard), int(n_shards),
+                                     d_class_cut or None)
+    if rc != OK:
+        raise TwopacoError(rc, "twopaco_shard_rounds")
+
+
+def twopaco_state_device(total_bases: int, n_seqs: int, k: int, filter_bits: int, rounds: int,
+                         options: Optional[Options], d_workspace: int, which: int):
+    """(device address, bytes) of one piece of a workspace's state."""
+    opt = (options or Options())._c()
+    ptr, nb = ctypes.c_void_p(), ctypes.c_uint64(0)
+    rc = _lib().twopaco_state_device(int(total_bases), int(n_seqs), int(k), int(filter_bits), int(rounds),
+                                     ctypes.byref(opt), d_workspace or None, int(which), ctypes.byref(ptr),
+                                     ctypes.byref(nb))
+    if rc != OK:
+        raise TwopacoError(rc, "twopaco_state_device")
+    return int(ptr.value or 0), int(nb.value)
+
+
+class _DeviceWords:
+    """A device buffer of 32-bit words described by __cuda_array_interface__, so that
+    torch.as_tensor can view it in place (no copy)."""
+
+    def __init__(self, ptr: int, nbytes: int):
+        self.__cuda_array_interface__ = {"shape": (nbytes // 4,), "typestr": "<i4",
+                                         "data": (ptr, False), "version": 3, "strides": None}
+
+
 def twopaco_selftest_bounded_wait(cuda_stream: int = 0) -> int:
     """Run one bounded device wait that must give up; returns the library's code
     (ETIMEOUT expected)."""
@@ -502,6 +555,36 @@ class DeviceBuild:
                                        self.offsets.data_ptr(), self.n_seqs, self.total_bases, self.k,
                                        self.filter_bits, self.rounds, opt, self.ws_ptr, self.ws_bytes,
                                        blob)
+
+    def shard_begin(self, compute_cut: bool, stream=None) -> None:
+        """Pack the input and (compute_cut) cut the classes: twopaco_shard_begin."""
+        opt = dataclasses.replace(self.options, cuda_stream=self._stream(stream))
+        twopaco_shard_begin(self.bases.data_ptr() if self.total_bases else 0, self.offsets.data_ptr(),
+                            self.n_seqs, self.total_bases, self.k, self.filter_bits, self.rounds, opt,
+                            self.ws_ptr, self.ws_bytes, compute_cut)
+
+    def shard_rounds(self, shard: int, n_shards: int, class_cut=None, stream=None) -> None:
+        """This shard's rounds (twopaco_shard_rounds); class_cut: a CUDA tensor of
+        rounds + 1 32-bit words, or None to keep the workspace's cut."""
+        opt = dataclasses.replace(self.options, cuda_stream=self._stream(stream))
+        twopaco_shard_rounds(self.bases.data_ptr() if self.total_bases else 0, self.offsets.data_ptr(),
+                             self.n_seqs, self.total_bases, self.k, self.filter_bits, self.rounds, opt,
+                             self.ws_ptr, self.ws_bytes, shard, n_shards,
+                             class_cut.data_ptr() if class_cut is not None else 0)
+
+    def state_tensor(self, which: int):
+        """An int32 CUDA tensor viewing one piece of the workspace's state in place
+        (twopaco_state_device): writes through it change the workspace."""
+        ptr, nb = twopaco_state_device(self.total_bases, self.n_seqs, self.k, self.filter_bits,
+                                       self.rounds, self.options, self.ws_ptr, which)
+        if nb == 0:
+            return self.torch.zeros(0, dtype=self.torch.int32, device=self.workspace.device)
+        return self.torch.as_tensor(_DeviceWords(ptr, nb), device=self.workspace.device)
+
+    def write_output(self, stream=None) -> None:
+        """Write the output from the C_final the workspace holds
+        (twopaco_run_rounds(..., rounds, rounds, ...))."""
+        self.run_rounds(self.rounds, self.rounds, stream)
 
     def capture(self) -> None:
         """Capture this run as a CUDA graph (twopaco_plan_create); run() then replays it."""
