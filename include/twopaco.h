@@ -194,6 +194,30 @@ int twopaco_run_device(const uint8_t* d_bases, const uint64_t* d_offsets, uint64
                        uint64_t* d_out_offsets, uint64_t* d_out_positions, uint64_t out_capacity);
 
 /*
+ * twopaco_run_device with the input bytes in host memory: they are streamed to
+ * the device in chunks (section "Parallelization Scheme": a reader hands the
+ * input over in pieces, so only a constant amount of it is resident), each
+ * chunk copied into one half of a caller-owned device staging buffer on an
+ * internal stream while the chunk before it is packed on options->cuda_stream;
+ * then the run goes on as twopaco_run_device does from the packed input.
+ *   h_bases        total_bases bytes in host memory, read until the stream has
+ *                  passed the pack; page-locked memory lets the copies overlap
+ *                  the packing (pageable memory works, without overlap)
+ *   d_offsets      n_seqs + 1 uint64 in device memory, as for twopaco_run_device
+ *   d_staging      staging_bytes of device memory, 256-byte aligned, owned by
+ *                  the caller; each half (staging_bytes / 2 rounded down to a
+ *                  multiple of 256) must be at least 64 KiB, else TWOPACO_EINVAL
+ * The other arguments, the workspace (twopaco_workspace_size: the ASCII input
+ * needs no room in it) and the results are those of twopaco_run_device.
+ * Launches without synchronising.
+ */
+int twopaco_run_streamed(const uint8_t* h_bases, const uint64_t* d_offsets, uint64_t n_seqs,
+                         uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
+                         const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
+                         void* d_staging, uint64_t staging_bytes, uint64_t* d_out_offsets,
+                         uint64_t* d_out_positions, uint64_t out_capacity);
+
+/*
  * The rounds [round_begin, round_end) of a device-resident run (Algorithm 3
  * runs its rounds one after the other, each adding its junctions to
  * C_final), with the arguments of twopaco_run_device; 0 <= round_begin <

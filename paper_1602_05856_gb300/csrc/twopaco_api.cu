@@ -15,6 +15,7 @@ namespace twopaco {
 namespace {
 
 constexpr uint64_t kAlign = 256;
+constexpr uint64_t kStreamChunkMin = 64 << 10;  // bytes per staging half, at least
 
 uint64_t align_up(uint64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -61,8 +62,8 @@ int validate_size(uint64_t total_bases) {
 
 struct Layout {
   uint64_t header, packed, filter, ctemp, cfinal, tile_count, tile_prefix, bins, cuts, table;
-  uint64_t cands, lc, segs, desc, cslot, nmask, bounds, chunks, runs, rank;
-  int narrow, use_desc, use_slot, split;
+  uint64_t cands, lc, segs, desc, cslot, nmask, bounds, chunks, runs, rank, cmap;
+  int narrow, use_desc, use_slot, split, use_cmap;
   uint64_t n_chunks, run_cap;
   uint64_t total;
   uint64_t packed_words, bitmap_words, n_tiles, table_slots, cand_cap;
@@ -137,7 +138,12 @@ Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int roun
   at += align_up((uint64_t)kMaxSegments * 4);
   // probe descriptors: one 64-bit word per position (filter word index, 30 bits
   // of bit bases, flags) when they fit -- under 2^31 bases, h <= 6, b <= 2^37
-  L.use_desc = (L.narrow && o.hashes <= 6 && filter_bits <= (1ull << 37)) ? 1 : 0;
+  // class map: one byte per position for 2 .. kMaxMapRounds rounds (then the
+  // rounds need no descriptors: each visits only its class's positions)
+  L.use_cmap = (rounds > 1 && rounds <= kMaxMapRounds) ? 1 : 0;
+  L.cmap = at;
+  if (L.use_cmap) at += align_up(m + 64);
+  L.use_desc = (L.narrow && o.hashes <= 6 && filter_bits <= (1ull << 37) && !L.use_cmap) ? 1 : 0;
   L.desc = at;
   if (L.use_desc) at += align_up((m + 16) * 8);
   // N splitting: N mask and boundary bitmap (one bit per base), per-chunk
@@ -209,6 +215,7 @@ RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_
   v.seg_count = reinterpret_cast<uint32_t*>(base + L.segs);
   v.bins = rounds > 1 ? reinterpret_cast<uint32_t*>(base + L.bins) : nullptr;
   v.cuts = reinterpret_cast<uint32_t*>(base + L.cuts);
+  v.cmap = L.use_cmap ? reinterpret_cast<uint8_t*>(base + L.cmap) : nullptr;
   v.tile_count = reinterpret_cast<uint32_t*>(base + L.tile_count);
   v.tile_prefix = reinterpret_cast<uint64_t*>(base + L.tile_prefix);
   v.n_tiles = L.n_tiles;
@@ -341,11 +348,73 @@ int twopaco_run_rounds(const uint8_t* d_bases, const uint64_t* d_offsets, uint64
     if (launch_init(v, s) < 0) return TWOPACO_ECUDA;
     if (launch_pack(v, s) < 0) return TWOPACO_ECUDA;
     if (rounds > 1 && launch_partition(v, rounds, s) < 0) return TWOPACO_ECUDA;
+    if (launch_class_map(v, s) < 0) return TWOPACO_ECUDA;
   }
   for (int r = round_begin; r < round_end; ++r)
     if (launch_round(v, r, rounds, s) < 0) return TWOPACO_ECUDA;
   if (round_end == rounds && launch_emit(v, s, round_begin == rounds) < 0) return TWOPACO_ECUDA;
   return TWOPACO_OK;
+}
+
+int twopaco_run_streamed(const uint8_t* h_bases, const uint64_t* d_offsets, uint64_t n_seqs,
+                         uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
+                         const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
+                         void* d_staging, uint64_t staging_bytes, uint64_t* d_out_offsets,
+                         uint64_t* d_out_positions, uint64_t out_capacity) {
+  const twopaco_options o = resolve(opt);
+  RunView v;
+  int rc = device_run_view(h_bases, d_offsets, n_seqs, total_bases, k, filter_bits, rounds, o, d_workspace,
+                           workspace_bytes, d_out_offsets, d_out_positions, out_capacity, true, &v);
+  if (rc) return rc;
+  if (!d_staging || (reinterpret_cast<uintptr_t>(d_staging) % kAlign)) return TWOPACO_EINVAL;
+  // two staging halves of a multiple of 256 bytes each (so that every chunk
+  // starts on a packed word that is a multiple of 4, and 16-byte aligned)
+  const uint64_t chunk = staging_bytes / 2 / kAlign * kAlign;
+  if (chunk < kStreamChunkMin) return TWOPACO_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(o.cuda_stream);
+  cudaStream_t cs = nullptr;
+  cudaEvent_t start = nullptr, copied[2] = {nullptr, nullptr}, packed[2] = {nullptr, nullptr};
+  auto finish = [&](int code) {
+    for (cudaEvent_t e : {start, copied[0], copied[1], packed[0], packed[1]})
+      if (e) cudaEventDestroy(e);
+    if (cs) cudaStreamDestroy(cs);  // its work completes first; the release is deferred
+    return code;
+  };
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  for (cudaEvent_t* ev : {&start, &copied[0], &copied[1], &packed[0], &packed[1]})
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return finish(cuda_code(e));
+  // the copies start once earlier work on the stream (which may still read the
+  // staging buffer) is done
+  if ((e = cudaEventRecord(start, s)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, start, 0)) != cudaSuccess)
+    return finish(cuda_code(e));
+  if (launch_init(v, s) < 0) return finish(TWOPACO_ECUDA);
+  char* stage = static_cast<char*>(d_staging);
+  const uint64_t n_chunks = total_bases ? (total_bases + chunk - 1) / chunk : 0;
+  if (n_chunks == 0 && launch_pack_chunk(v, 0, v.packed_words, true, s) < 0) return finish(TWOPACO_ECUDA);
+  for (uint64_t c = 0; c < n_chunks; ++c) {
+    const int b = (int)(c & 1);
+    const uint64_t g0 = c * chunk, len = std::min(chunk, total_bases - g0);
+    char* buf = stage + b * chunk;
+    // reuse a half only after the pack of the chunk it held two chunks ago
+    if (c >= 2 && (e = cudaStreamWaitEvent(cs, packed[b], 0)) != cudaSuccess) return finish(cuda_code(e));
+    if ((e = cudaMemcpyAsync(buf, h_bases + g0, len, cudaMemcpyHostToDevice, cs)) != cudaSuccess ||
+        (e = cudaEventRecord(copied[b], cs)) != cudaSuccess || (e = cudaStreamWaitEvent(s, copied[b], 0)) != cudaSuccess)
+      return finish(cuda_code(e));
+    RunView cv = v;
+    cv.bases = reinterpret_cast<const uint8_t*>(buf) - g0;  // bytes [g0, g0 + len) at buf
+    const uint64_t w_begin = g0 / 16;
+    const uint64_t w_end = c + 1 == n_chunks ? v.packed_words : (g0 + len) / 16;  // the last takes the pad
+    if (launch_pack_chunk(cv, w_begin, w_end, c == 0, s) < 0) return finish(TWOPACO_ECUDA);
+    if ((e = cudaEventRecord(packed[b], s)) != cudaSuccess) return finish(cuda_code(e));
+  }
+  if (launch_pack_finish(v, s) < 0) return finish(TWOPACO_ECUDA);
+  if (rounds > 1 && launch_partition(v, rounds, s) < 0) return finish(TWOPACO_ECUDA);
+  if (launch_class_map(v, s) < 0) return finish(TWOPACO_ECUDA);
+  for (int r = 0; r < rounds; ++r)
+    if (launch_round(v, r, rounds, s) < 0) return finish(TWOPACO_ECUDA);
+  if (launch_emit(v, s) < 0) return finish(TWOPACO_ECUDA);
+  return finish(TWOPACO_OK);
 }
 
 int twopaco_shard_begin(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_seqs,
@@ -379,6 +448,7 @@ int twopaco_shard_rounds(const uint8_t* d_bases, const uint64_t* d_offsets, uint
       cudaMemcpyAsync(v.cuts, d_class_cut, 4 * ((uint64_t)rounds + 1), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return TWOPACO_ECUDA;
   v.count_round = shard;  // every shard counts the positions in its first round
+  if (shard < rounds && launch_class_map(v, s) < 0) return TWOPACO_ECUDA;
   for (int r = shard; r < rounds; r += n_shards)
     if (launch_round(v, r, rounds, s) < 0) return TWOPACO_ECUDA;
   return TWOPACO_OK;
@@ -671,6 +741,7 @@ int twopaco_checkpoint_load(const uint8_t* d_bases, const uint64_t* d_offsets, u
   if (v.bitmap_words &&
       (e = cudaMemcpyAsync(v.cfinal, in, 4 * v.bitmap_words, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cuda_code(e);
+  if (launch_class_map(v, s) < 0) return TWOPACO_ECUDA;  // the remaining rounds' classes, from the restored cut
   const unsigned long long counters[3] = {c.positions, c.pass1_kept, c.pass2_kept};
   if ((e = cudaMemcpyAsync(&hd->positions, counters, sizeof(counters), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(&hd->table_max, &c.table_max, 8, cudaMemcpyHostToDevice, s)) != cudaSuccess ||

@@ -104,6 +104,7 @@ struct RunView {
   int lc_log2;
   uint32_t* bins;           // partition counters (q), rounds > 1
   uint32_t* cuts;           // rounds + 1 class boundaries
+  uint8_t* cmap;            // class map, one byte per position (null: rounds walk every position)
   uint32_t* tile_count;     // emit: junctions per tile
   uint64_t* tile_prefix;    // emit: exclusive prefix per tile
   uint64_t n_tiles;
@@ -118,13 +119,22 @@ constexpr int kEmitTileWords = kBlock * kEmitWordsPerThread;  // bitmap words pe
 constexpr uint64_t kPackPadWords = 16;  // zero words after the packed input (window reads of k <= 127 stay inside)
 constexpr uint32_t kMaxSegments = 65536; // candidate-list segments (probe warps) at most
 constexpr uint64_t kRunChunkWords = 1024;  // boundary-bitmap words per compaction chunk
+constexpr int kMaxMapRounds = 64;          // rounds a class map can tell apart (6 class bits)
 
 // Kernel launch helpers (twopaco_kernels.cu). Each returns the number of
 // kernels it launched, or -1 after a launch error.
 int launch_init(const RunView& v, cudaStream_t s);  // clears the header
 int launch_pack(const RunView& v, cudaStream_t s);
+// The pack in pieces: the packed words [w_begin, w_end) from v.bases (first:
+// also the header and the first round's clears), then, once every word is
+// packed, the piece boundaries of N splitting.
+int launch_pack_chunk(const RunView& v, uint64_t w_begin, uint64_t w_end, bool first, cudaStream_t s);
+int launch_pack_finish(const RunView& v, cudaStream_t s);
 int launch_partition(const RunView& v, int rounds, cudaStream_t s);
 int launch_round(const RunView& v, int round, int rounds, cudaStream_t s);
+// The class map of a run with rounds > 1 (v.cmap), from the class cut in
+// v.cuts; launches nothing without a class map.
+int launch_class_map(const RunView& v, cudaStream_t s);
 int launch_emit(const RunView& v, cudaStream_t s, bool again = false);
 int launch_edges(const DevHeader* hdr_dev, const uint64_t* d_offsets, uint64_t n_seqs,
                  const uint64_t* d_out_offsets, const uint64_t* d_out_positions,
@@ -148,6 +158,7 @@ inline uint64_t cand_record_bytes(int) { return 8; }
 // in twopaco_kernels_wide.cu).
 int launch_round_wide(const RunView& v, int round, int rounds, cudaStream_t s);
 int launch_partition_count_wide(const RunView& v, cudaStream_t s);
+int launch_class_map_wide(const RunView& v, cudaStream_t s);
 
 // Digest of a run's input into hdr->input_digest: an order-free sum over the
 // packed words (the bases), the n_seqs + 1 string offsets (the boundaries,

@@ -848,12 +848,16 @@ __device__ __forceinline__ uint32_t pack16(const RunView& v, uint64_t g, uint4 q
   return out;
 }
 
-// ASCII -> 2-bit words: 64 bytes (four 128-bit loads in flight) per thread.
-// Block 0 also records where this run keeps its bitmaps (for inspection), and
-// the grid clears the filter, the linear-counting bitmap, C_final and the
-// emit's tile status for the first round.
-__global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+// ASCII -> 2-bit words: 64 bytes (four 128-bit loads in flight) per thread,
+// for the packed words [w_begin, w_end) (w_begin a multiple of 4; the input
+// bytes of those words are read at v.bases + 16 * w, so that a chunk of the
+// input staged elsewhere can be packed by passing v.bases offset back by the
+// chunk's start). With `first`, block 0 also records where this run keeps its
+// bitmaps (for inspection), and the grid clears the filter, the
+// linear-counting bitmap, C_final and the emit's tile status for the first
+// round.
+__global__ void __launch_bounds__(kBlock) pack_kernel(RunView v, uint64_t w_begin, uint64_t w_end, int first) {
+  if (first && blockIdx.x == 0 && threadIdx.x == 0) {
     DevHeader* h = v.hdr;
     h->ctemp = v.ctemp;
     h->cfinal = v.cfinal;
@@ -880,7 +884,7 @@ __global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
   const bool vec = (reinterpret_cast<uintptr_t>(v.bases) & 15) == 0;
   const uint64_t stride = (uint64_t)gridDim.x * kBlock * 4;
   uint64_t bad_at = ~0ull;
-  for (uint64_t w0 = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) * 4; w0 < v.packed_words; w0 += stride) {
+  for (uint64_t w0 = w_begin + ((uint64_t)blockIdx.x * kBlock + threadIdx.x) * 4; w0 < w_end; w0 += stride) {
     uint4 q[4];
     bool full[4];
 #pragma unroll
@@ -896,13 +900,14 @@ __global__ void __launch_bounds__(kBlock) pack_kernel(RunView v) {
       v.nmask[w0 / 2] = nb[0] | (nb[1] << 16);
       v.nmask[w0 / 2 + 1] = nb[2] | (nb[3] << 16);
     }
-    if (w0 + 4 <= v.packed_words) {
+    if (w0 + 4 <= w_end) {
       *reinterpret_cast<uint4*>(v.packed + w0) = make_uint4(out[0], out[1], out[2], out[3]);
     } else {
-      for (int j = 0; j < 4 && w0 + j < v.packed_words; ++j) v.packed[w0 + j] = out[j];
+      for (int j = 0; j < 4 && w0 + j < w_end; ++j) v.packed[w0 + j] = out[j];
     }
   }
   if (bad_at != ~0ull) atomicMax(&v.hdr->bad_inv, ~(unsigned long long)bad_at);
+  if (!first) return;
   // clear what the first round and the emit need to start at zero
   const uint64_t tid = (uint64_t)blockIdx.x * kBlock + threadIdx.x, nthreads = (uint64_t)gridDim.x * kBlock;
   auto zero = [&](void* p, uint64_t bytes) {  // 16-byte multiples at 16-byte aligned addresses
@@ -1296,6 +1301,195 @@ __global__ void __launch_bounds__(kBlock) pass1_probe_desc_kernel(RunView v, int
         if (v.partial) v.cfinal[w] |= my_word;  // rounds own disjoint positions; one writer per word
       }
     }
+  }
+  if (lane == 0) {
+    v.seg_count[warp_id] = (uint32_t)(seg_used < v.seg_cap ? seg_used : v.seg_cap);
+    if (seg_used > v.seg_cap) v.hdr->cand_overflow = 1;
+  }
+  block_add(kept, &v.hdr->pass1_kept);
+  block_add(kept, v.partial ? &v.hdr->pass2_kept : &v.hdr->round_kept);
+  if (round == v.count_round) block_add(valid_n, &v.hdr->positions);
+}
+
+// ---------------------------------------------------------------------------
+// Class map (rounds > 1, at most kMaxMapRounds of them): Algorithm 3 marks,
+// in round i, the positions whose k-mer is in class i. Instead of walking and
+// hashing every position again in every round, one pass after the class cut
+// records per position one byte -- bit 7: no k-mer starts here, bit 6: a
+// sentinel position (the first or last k-mer of its string or N-free piece),
+// bits 0-5: the class -- and each round's two first-pass loops then visit only
+// the positions of their class, reading each k-mer from scratch. A warp takes
+// a window of 512 consecutive positions, compacts the indices of the active
+// ones in shared memory and shares them out evenly over its lanes.
+// ---------------------------------------------------------------------------
+
+constexpr uint32_t kCmNone = 0x80u, kCmSentinel = 0x40u, kCmClass = 0x3Fu;
+constexpr int kCmWindow = 32 * 16;  // positions per warp window
+
+// Class of a bin: the r with cuts[r] <= bin < cuts[r + 1] (cuts in shared memory).
+__device__ __forceinline__ uint32_t class_of_bin(const uint32_t* cuts, int rounds, uint32_t bin) {
+  int lo = 0, hi = rounds;  // cuts[lo] <= bin < cuts[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (cuts[mid] <= bin) lo = mid; else hi = mid;
+  }
+  return (uint32_t)lo;
+}
+
+template <int KW>
+__global__ void __launch_bounds__(kBlock) class_map_kernel(RunView v) {
+  __shared__ uint32_t cuts_s[kMaxMapRounds + 1];
+  for (int i = threadIdx.x; i <= v.rounds; i += kBlock) cuts_s[i] = v.cuts[i];
+  __syncthreads();
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock * kInsertR;
+  for (uint64_t p0 = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) * kInsertR; p0 < v.m; p0 += stride) {
+    uint32_t w[4] = {0x80808080u, 0x80808080u, 0x80808080u, 0x80808080u};
+    walk<KW, kInsertR>(v, p0, [&](int i, uint64_t, bool valid, const auto& oc) {
+      if (!valid) return;
+      const uint32_t c = class_of_bin(cuts_s, v.rounds, (uint32_t)oc.H & v.qmask) |
+                         (oc.sentinel ? kCmSentinel : 0u);
+      w[i >> 2] = (w[i >> 2] & ~(0xFFu << (8 * (i & 3)))) | (c << (8 * (i & 3)));
+    });
+    *reinterpret_cast<uint4*>(v.cmap + p0) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// The positions of this round's class in the warp's window [wbase, wbase + 512):
+// their offsets (bits 0-8) with the sentinel flag (bit 9) go to idx[0 .. n), in
+// position order; *valid gets the number of positions with a k-mer.
+__device__ __forceinline__ uint32_t compact_window(const RunView& v, uint64_t wbase, int round, uint16_t* idx,
+                                                   uint32_t* valid) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t p0 = wbase + 16 * (uint64_t)lane;
+  uint4 q = make_uint4(0x80808080u, 0x80808080u, 0x80808080u, 0x80808080u);
+  if (p0 < v.m) q = __ldcs(reinterpret_cast<const uint4*>(v.cmap + p0));
+  const uint32_t part[4] = {q.x, q.y, q.z, q.w};
+  const uint32_t want = (uint32_t)round * 0x01010101u;
+  uint32_t act = 0, sent = 0, val = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    act |= byte_bits(__vcmpeq4(part[c] & 0xBFBFBFBFu, want)) << (4 * c);  // valid and in this class
+    sent |= byte_bits(__vcmpeq4(part[c] & 0x40404040u, 0x40404040u)) << (4 * c);
+    val |= byte_bits(__vcmpeq4(part[c] & 0x80808080u, 0u)) << (4 * c);
+  }
+  const uint32_t n = __popc(act);
+  uint32_t inc = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  uint32_t at = inc - n;
+  while (act) {
+    const uint32_t i = __ffs(act) - 1;
+    act &= act - 1;
+    idx[at++] = (uint16_t)((16 * lane + i) | (((sent >> i) & 1u) << 9));
+  }
+  *valid = __popc(val);
+  __syncwarp();
+  return __shfl_sync(0xffffffffu, inc, 31);
+}
+
+// Algorithm 1, insert loop, first pass, over this round's class only.
+template <int KW, int HB>
+__global__ void __launch_bounds__(kBlock) pass1_insert_cm_kernel(RunView v, int round) {
+  __shared__ uint16_t idx_s[kBlock / 32][kCmWindow];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint16_t* idx = idx_s[wid];
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock * 16;
+  for (uint64_t wbase = ((uint64_t)blockIdx.x * kBlock + (threadIdx.x & ~31u)) * 16; wbase < v.m; wbase += stride) {
+    uint32_t valid;
+    const uint32_t n = compact_window(v, wbase, round, idx, &valid);
+    for (uint32_t j = lane; j < n; j += 32) {
+      const uint32_t e = idx[j];
+      OccT<KW> oc;
+      read_listed<KW>(v, wbase + (e & 511u), (e >> 9) & 1u, &oc);
+      const uint64_t G = second_hash(oc.H);
+      const ItemPattern pat = item_pattern<HB>(G, v.hashes);
+      const uint32_t j1 = __ffs(oc.items) - 1, j2 = 31 - __clz(oc.items);
+      uint64_t m = item_bits(pat, j1);
+      if (j2 != j1) m |= item_bits(pat, j2);  // a palindrome's two orientations
+      atomicOr(filter_word(v, oc.H, G), (unsigned long long)m);
+    }
+    __syncwarp();
+  }
+}
+
+// Algorithm 1, probe loop, first pass, over this round's class only: the same
+// decisions and outputs as pass1_probe_kernel (C_temp words of the window, the
+// candidate list segment of the warp, the linear-counting bits).
+template <int KW, int HB>
+__global__ void __launch_bounds__(kBlock) pass1_probe_cm_kernel(RunView v, int round) {
+  __shared__ uint16_t idx_s[kBlock / 32][kCmWindow];
+  __shared__ uint32_t keep_s[kBlock / 32][kCmWindow / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint16_t* idx = idx_s[wid];
+  uint32_t* keep_w = keep_s[wid];
+  const uint32_t below = (1u << lane) - 1u;
+  unsigned long long kept = 0, valid_n = 0;
+  const uint32_t warp_id = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  uint64_t* seg = v.cands + (uint64_t)warp_id * v.seg_cap;
+  uint32_t* seg32 = reinterpret_cast<uint32_t*>(v.cands) + (uint64_t)warp_id * v.seg_cap;
+  uint64_t seg_used = 0;
+  if (lane < kCmWindow / 32) keep_w[lane] = 0;
+  __syncwarp();
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock * 16;
+  for (uint64_t wbase = ((uint64_t)blockIdx.x * kBlock + (threadIdx.x & ~31u)) * 16; wbase < v.m; wbase += stride) {
+    uint32_t valid;
+    const uint32_t n = compact_window(v, wbase, round, idx, &valid);
+    valid_n += valid;
+    for (uint32_t j0 = 0; j0 < n; j0 += 32) {
+      const uint32_t j = j0 + lane;
+      bool keep = false;
+      uint64_t G = 0, g = 0;
+      uint32_t sentinel = 0;
+      if (j < n) {
+        const uint32_t e = idx[j];
+        g = wbase + (e & 511u);
+        sentinel = (e >> 9) & 1u;
+        if (sentinel) {
+          keep = true;
+          OccT<KW> oc;
+          read_listed<KW>(v, g, true, &oc);
+          G = second_hash(oc.H);
+        } else {
+          OccT<KW> oc;
+          read_listed<KW>(v, g, false, &oc);
+          G = second_hash(oc.H);
+          const uint64_t word = __ldcg(filter_word(v, oc.H, G));
+          const uint32_t pres = present_items<HB>(G, word, v.hashes);
+          keep = (pres >> 16) || __popc(pres & 0xFFFFu) >= 2;
+        }
+        if (keep) atomicOr(keep_w + ((e & 511u) >> 5), 1u << (e & 31u));
+      }
+      if (v.partial) {
+        kept += keep;
+        continue;
+      }
+      const uint32_t row = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        const uint64_t x = (G * 0xff51afd7ed558ccdull) >> (64 - v.lc_log2);
+        atomicOr(v.lc_bits + (x >> 5), 1u << (x & 31));
+        const uint64_t at = seg_used + __popc(row & below);
+        if (at < v.seg_cap) {
+          if (v.narrow) seg32[at] = (uint32_t)g | (sentinel << 31);
+          else seg[at] = g | ((uint64_t)sentinel << 63);
+        }
+        ++kept;
+      }
+      seg_used += __popc(row);
+    }
+    __syncwarp();
+    if (lane < kCmWindow / 32) {
+      const uint64_t w = (wbase >> 5) + lane;
+      const uint32_t word = keep_w[lane];
+      keep_w[lane] = 0;
+      if (w < v.bitmap_words) {
+        v.ctemp[w] = word;
+        if (v.partial) v.cfinal[w] |= word;  // rounds own disjoint positions; one writer per word
+      }
+    }
+    __syncwarp();
   }
   if (lane == 0) {
     v.seg_count[warp_id] = (uint32_t)(seg_used < v.seg_cap ? seg_used : v.seg_cap);
@@ -1979,11 +2173,19 @@ int launch_digest(DevHeader* hdr_dev, const uint32_t* packed, uint64_t words, co
 }
 
 int launch_pack(const RunView& v, cudaStream_t s) {
-  {
-    Timed t("pack", s);
-    pack_kernel<<<grid_for(pack_kernel, kBlock, (v.packed_words + 3) / 4), kBlock, 0, s>>>(v);
-  }
-  if (!v.nmask || v.m == 0) return done(1);
+  if (launch_pack_chunk(v, 0, v.packed_words, true, s) < 0) return -1;
+  return launch_pack_finish(v, s);
+}
+
+int launch_pack_chunk(const RunView& v, uint64_t w_begin, uint64_t w_end, bool first, cudaStream_t s) {
+  Timed t("pack", s);
+  pack_kernel<<<grid_for(pack_kernel, kBlock, (w_end - w_begin + 3) / 4), kBlock, 0, s>>>(v, w_begin, w_end,
+                                                                                          first ? 1 : 0);
+  return done(1);
+}
+
+int launch_pack_finish(const RunView& v, cudaStream_t s) {
+  if (!v.nmask || v.m == 0) return 0;
   {
     Timed t("runs", s);
     runs_mark_kernel<<<grid_for(runs_mark_kernel, kBlock, v.bitmap_words), kBlock, 0, s>>>(v);
@@ -1993,7 +2195,7 @@ int launch_pack(const RunView& v, cudaStream_t s) {
     runs_scan_kernel<<<1, 1024, 0, s>>>(v);
     runs_write_kernel<<<grid_for(runs_write_kernel, kBlock, v.n_chunks * kBlock), kBlock, 0, s>>>(v);
   }
-  return done(6);
+  return done(5);
 }
 
 #endif  // TWOPACO_WIDE_ONLY
@@ -2049,11 +2251,15 @@ int round_impl(const RunView& v, int round, cudaStream_t s) {
   if (RD && cudaMemsetAsync(v.filter, 0, v.filter_words64 * 8, s) != cudaSuccess) return -1;
   if (round > 0 && cudaMemsetAsync(v.lc_bits, 0, (1ull << v.lc_log2) / 8, s) != cudaSuccess) return -1;
   constexpr bool kDescOk = HB <= 6;
-  const bool desc = kDescOk && v.use_desc;
+  const bool cm = RD && v.cmap != nullptr;  // rounds visit only their class's positions
+  const bool desc = !cm && kDescOk && v.use_desc;
   {
     Timed t("pass1_insert", s);
     const uint64_t threads = (v.m + kInsertR - 1) / kInsertR;
-    if (desc)
+    if (cm)
+      pass1_insert_cm_kernel<KW, HB><<<grid_for(pass1_insert_cm_kernel<KW, HB>, kBlock, threads), kBlock, 0, s>>>(
+          v, round);
+    else if (desc)
       pass1_insert_kernel<KW, RD, HB, kDescOk><<<grid_for(pass1_insert_kernel<KW, RD, HB, kDescOk>, kBlock, threads),
                                                  kBlock, 0, s>>>(v, round);
     else
@@ -2063,15 +2269,17 @@ int round_impl(const RunView& v, int round, cudaStream_t s) {
   const uint64_t threads = (v.m + kProbeR - 1) / kProbeR;
   // one candidate-list segment per probe warp
   RunView pv = v;
-  unsigned grid = desc ? grid_for(pass1_probe_desc_kernel<kDescOk ? HB : 1>, kBlock, threads)
-                       : grid_for(pass1_probe_kernel<KW, RD, HB>, kBlock, threads);
+  unsigned grid = cm     ? grid_for(pass1_probe_cm_kernel<KW, HB>, kBlock, (v.m + 15) / 16)
+                  : desc ? grid_for(pass1_probe_desc_kernel<kDescOk ? HB : 1>, kBlock, threads)
+                         : grid_for(pass1_probe_kernel<KW, RD, HB>, kBlock, threads);
   if (grid * (kBlock / 32) > kMaxSegments) grid = kMaxSegments / (kBlock / 32);
   pv.n_segments = grid * (kBlock / 32);
   // the list region holds cand_cap 8-byte records, or twice as many 32-bit ones
   pv.seg_cap = (v.narrow ? 2 * v.cand_cap : v.cand_cap) / pv.n_segments;
   {
     Timed t("pass1_probe", s);
-    if (desc) pass1_probe_desc_kernel<kDescOk ? HB : 1><<<grid, kBlock, 0, s>>>(pv, round);
+    if (cm) pass1_probe_cm_kernel<KW, HB><<<grid, kBlock, 0, s>>>(pv, round);
+    else if (desc) pass1_probe_desc_kernel<kDescOk ? HB : 1><<<grid, kBlock, 0, s>>>(pv, round);
     else pass1_probe_kernel<KW, RD, HB><<<grid, kBlock, 0, s>>>(pv, round);
   }
   if (v.partial) return done(2);  // the partially compacted graph: no second pass
@@ -2113,6 +2321,16 @@ int launch_round(const RunView& v, int round, int rounds, cudaStream_t s) {
       rc = rounds > 1 ? round_impl<2, true, HB, 2>(v, round, s) : round_impl<2, false, HB, 2>(v, round, s);
   });
   return rc;
+}
+
+int launch_class_map(const RunView& v, cudaStream_t s) {
+  if (!v.cmap || v.m == 0) return 0;
+  if (v.k > 63) return launch_class_map_wide(v, s) < 0 ? -1 : done(1);
+  Timed t("class_map", s);
+  const uint64_t threads = (v.m + kInsertR - 1) / kInsertR;
+  if (v.k <= 31) class_map_kernel<1><<<grid_for(class_map_kernel<1>, kBlock, threads), kBlock, 0, s>>>(v);
+  else class_map_kernel<2><<<grid_for(class_map_kernel<2>, kBlock, threads), kBlock, 0, s>>>(v);
+  return done(1);
 }
 
 int launch_emit(const RunView& v, cudaStream_t s, bool again) {
@@ -2161,6 +2379,13 @@ int launch_round_wide(const RunView& v, int round, int rounds, cudaStream_t s) {
 int launch_partition_count_wide(const RunView& v, cudaStream_t s) {
   const uint64_t threads = (v.m + kR - 1) / kR;
   partition_count_kernel<4, 0><<<grid_for(partition_count_kernel<4, 0>, kBlock, threads), kBlock, 0, s>>>(v);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_class_map_wide(const RunView& v, cudaStream_t s) {
+  Timed t("class_map", s);
+  const uint64_t threads = (v.m + kInsertR - 1) / kInsertR;
+  class_map_kernel<4><<<grid_for(class_map_kernel<4>, kBlock, threads), kBlock, 0, s>>>(v);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 #endif  // TWOPACO_WIDE_ONLY

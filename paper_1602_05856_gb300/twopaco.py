@@ -102,6 +102,9 @@ def _lib() -> ctypes.CDLL:
         L.twopaco_run_rounds.argtypes = [P, P, U64, U64, I, U64, I, ctypes.POINTER(_Options), P, U64,
                                          I, I, P, P, U64]
         L.twopaco_run_rounds.restype = I
+        L.twopaco_run_streamed.argtypes = [P, P, U64, U64, I, U64, I, ctypes.POINTER(_Options), P, U64,
+                                           P, U64, P, P, U64]
+        L.twopaco_run_streamed.restype = I
         L.twopaco_shard_begin.argtypes = [P, P, U64, U64, I, U64, I, ctypes.POINTER(_Options), P, U64, I]
         L.twopaco_shard_begin.restype = I
         L.twopaco_shard_rounds.argtypes = [P, P, U64, U64, I, U64, I, ctypes.POINTER(_Options), P, U64,
@@ -348,6 +351,21 @@ def twopaco_run_rounds(d_bases: int, d_offsets: int, n_seqs: int, total_bases: i
         raise TwopacoError(rc, "twopaco_run_rounds")
 
 
+def twopaco_run_streamed(h_bases: int, d_offsets: int, n_seqs: int, total_bases: int, k: int,
+                         filter_bits: int, rounds: int, options: Optional[Options], d_workspace: int,
+                         workspace_bytes: int, d_staging: int, staging_bytes: int, d_out_offsets: int,
+                         d_out_positions: int, out_capacity: int) -> None:
+    """A run whose input bytes (host address h_bases) are streamed in through d_staging."""
+    opt = (options or Options())._c()
+    rc = _lib().twopaco_run_streamed(h_bases or None, d_offsets or None, int(n_seqs), int(total_bases),
+                                     int(k), int(filter_bits), int(rounds), ctypes.byref(opt),
+                                     d_workspace or None, int(workspace_bytes), d_staging or None,
+                                     int(staging_bytes), d_out_offsets or None, d_out_positions or None,
+                                     int(out_capacity))
+    if rc != OK:
+        raise TwopacoError(rc, "twopaco_run_streamed")
+
+
 def twopaco_shard_begin(d_bases: int, d_offsets: int, n_seqs: int, total_bases: int, k: int,
                         filter_bits: int, rounds: int, options: Optional[Options], d_workspace: int,
                         workspace_bytes: int, compute_cut: bool) -> None:
@@ -490,17 +508,24 @@ class DeviceBuild:
     ``bases`` (uint8) and ``offsets`` (n + 1 entries) may be host arrays or
     CUDA tensors; they are made resident once. ``run()`` launches one full
     build on ``stream`` (default: the current stream) without synchronising.
+    With ``resident=False`` the bases stay where they are (host memory) and
+    only ``run_streamed`` runs. ``capacity`` bounds the output positions
+    (default: one per k-mer position, which can never overflow).
     """
 
     def __init__(self, bases, offsets, k: int, filter_bits: int, rounds: int = 1,
-                 options: Optional[Options] = None, device: str = "cuda"):
+                 options: Optional[Options] = None, device: str = "cuda",
+                 capacity: Optional[int] = None, resident: bool = True):
         import torch
         self.torch = torch
         self.k, self.filter_bits, self.rounds = int(k), int(filter_bits), int(rounds)
         self.options = options or Options()
         dev = torch.device(device)
-        self.bases = torch.as_tensor(np.asarray(bases, dtype=np.uint8) if not torch.is_tensor(bases)
-                                     else bases, device=dev).contiguous()
+        if resident:
+            self.bases = torch.as_tensor(np.asarray(bases, dtype=np.uint8) if not torch.is_tensor(bases)
+                                         else bases, device=dev).contiguous()
+        else:
+            self.bases = None
         off = offsets.cpu().numpy() if torch.is_tensor(offsets) else np.asarray(offsets)
         off = off.astype(np.uint64)
         self.n_seqs = off.size - 1
@@ -514,8 +539,20 @@ class DeviceBuild:
         base = self.workspace.data_ptr()
         self.ws_ptr = (base + 255) // 256 * 256
         self.out_offsets = torch.zeros(self.n_seqs + 1, dtype=torch.int64, device=dev)
-        self.capacity = max(self.positions_upper, 1)
+        self.capacity = max(self.positions_upper if capacity is None else int(capacity), 1)
         self.out_positions = torch.empty(self.capacity, dtype=torch.int64, device=dev)
+
+    def _bases_ptr(self, reads: bool = True) -> int:
+        """Device address of the bases. A build that is not resident has none: only
+        calls that do not read the bases (writing the output again) take the host
+        address its last streamed run read; the others raise."""
+        if not self.total_bases:
+            return 0
+        if self.bases is not None:
+            return self.bases.data_ptr()
+        if reads or not getattr(self, "_host_ptr", 0):
+            raise ValueError("the bases of this build are not resident on the device")
+        return self._host_ptr
 
     def _stream(self, stream) -> int:
         if stream is None:
@@ -529,15 +566,30 @@ class DeviceBuild:
                 raise TwopacoError(rc, "twopaco_plan_launch")
             return
         opt = dataclasses.replace(self.options, cuda_stream=self._stream(stream))
-        twopaco_run_device(self.bases.data_ptr() if self.total_bases else 0, self.offsets.data_ptr(),
+        twopaco_run_device(self._bases_ptr(), self.offsets.data_ptr(),
                            self.n_seqs, self.total_bases, self.k, self.filter_bits, self.rounds, opt,
                            self.ws_ptr, self.ws_bytes, self.out_offsets.data_ptr(),
                            self.out_positions.data_ptr(), self.capacity)
 
+    def run_streamed(self, host_bases, staging, stream=None) -> None:
+        """One full build with the bases read from host memory (twopaco_run_streamed):
+        host_bases a page-locked CPU uint8 tensor (or any host array) of total_bases
+        bytes, staging a 256-byte aligned CUDA uint8 tensor split into two halves."""
+        import torch
+        hp = host_bases.data_ptr() if torch.is_tensor(host_bases) else np.asarray(host_bases).ctypes.data
+        self._host_ptr = hp
+        if staging.data_ptr() % 256:
+            raise ValueError("the staging buffer must be 256-byte aligned")
+        opt = dataclasses.replace(self.options, cuda_stream=self._stream(stream))
+        twopaco_run_streamed(hp if self.total_bases else 0, self.offsets.data_ptr(), self.n_seqs,
+                             self.total_bases, self.k, self.filter_bits, self.rounds, opt, self.ws_ptr,
+                             self.ws_bytes, staging.data_ptr(), staging.numel(), self.out_offsets.data_ptr(),
+                             self.out_positions.data_ptr(), self.capacity)
+
     def run_rounds(self, round_begin: int, round_end: int, stream=None) -> None:
         """Rounds [round_begin, round_end) of the run (twopaco_run_rounds)."""
         opt = dataclasses.replace(self.options, cuda_stream=self._stream(stream))
-        twopaco_run_rounds(self.bases.data_ptr() if self.total_bases else 0, self.offsets.data_ptr(),
+        twopaco_run_rounds(self._bases_ptr(reads=round_begin < self.rounds), self.offsets.data_ptr(),
                            self.n_seqs, self.total_bases, self.k, self.filter_bits, self.rounds, opt,
                            self.ws_ptr, self.ws_bytes, round_begin, round_end,
                            self.out_offsets.data_ptr(), self.out_positions.data_ptr(), self.capacity)
@@ -551,7 +603,7 @@ class DeviceBuild:
     def restore(self, blob: bytes, stream=None) -> int:
         """Load a checkpoint of this input into this workspace; returns the round to continue with."""
         opt = dataclasses.replace(self.options, cuda_stream=self._stream(stream))
-        return twopaco_checkpoint_load(self.bases.data_ptr() if self.total_bases else 0,
+        return twopaco_checkpoint_load(self._bases_ptr(),
                                        self.offsets.data_ptr(), self.n_seqs, self.total_bases, self.k,
                                        self.filter_bits, self.rounds, opt, self.ws_ptr, self.ws_bytes,
                                        blob)
@@ -559,7 +611,7 @@ class DeviceBuild:
     def shard_begin(self, compute_cut: bool, stream=None) -> None:
         """Pack the input and (compute_cut) cut the classes: twopaco_shard_begin."""
         opt = dataclasses.replace(self.options, cuda_stream=self._stream(stream))
-        twopaco_shard_begin(self.bases.data_ptr() if self.total_bases else 0, self.offsets.data_ptr(),
+        twopaco_shard_begin(self._bases_ptr(), self.offsets.data_ptr(),
                             self.n_seqs, self.total_bases, self.k, self.filter_bits, self.rounds, opt,
                             self.ws_ptr, self.ws_bytes, compute_cut)
 
@@ -567,7 +619,7 @@ class DeviceBuild:
         """This shard's rounds (twopaco_shard_rounds); class_cut: a CUDA tensor of
         rounds + 1 32-bit words, or None to keep the workspace's cut."""
         opt = dataclasses.replace(self.options, cuda_stream=self._stream(stream))
-        twopaco_shard_rounds(self.bases.data_ptr() if self.total_bases else 0, self.offsets.data_ptr(),
+        twopaco_shard_rounds(self._bases_ptr(), self.offsets.data_ptr(),
                              self.n_seqs, self.total_bases, self.k, self.filter_bits, self.rounds, opt,
                              self.ws_ptr, self.ws_bytes, shard, n_shards,
                              class_cut.data_ptr() if class_cut is not None else 0)
@@ -591,7 +643,7 @@ class DeviceBuild:
         self.release_plan()
         h = ctypes.c_void_p()
         opt = self.options._c()
-        rc = _lib().twopaco_plan_create(self.bases.data_ptr() if self.total_bases else None,
+        rc = _lib().twopaco_plan_create(self._bases_ptr() or None,
                                         self.offsets.data_ptr(), self.n_seqs, self.total_bases,
                                         self.k, self.filter_bits, self.rounds, ctypes.byref(opt),
                                         self.ws_ptr, self.ws_bytes, self.out_offsets.data_ptr(),
