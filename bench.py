@@ -1,19 +1,32 @@
 #!/usr/bin/env python3
 """Throughput of two-pass junction detection (Gbp/s of genome input).
 
-One step = one full build over the bacterial-size genome set (7 related
-genomes of 4.6-5.6 Mbp, k = 25, a 2^28-bit filter with 4 hashes, 1 round):
-pack, pass 1 (filter insert + probe), pass 2 (exact table insert +
-classify) and the emit of sorted junction positions, all from ASCII already
-resident in device memory. The input (35 MB) is smaller than L2, so a
-512 MiB buffer is written between timed steps to flush it.
+One step = one full build: pack, the class cut and class map (rounds > 1),
+every round's two passes (Bloom-filter insert and probe, exact-table insert
+and classify) and the emit of the sorted junction positions of every genome.
+
+The headline workload is the mammal-scale configuration, the largest that
+one GPU holds: 8 genomes of about 3 Gbp (24 Gbp) at the leaves of a seeded
+random tree (45% repeats, 1-8% between leaves), drawn on the GPU, k = 25, a
+2^36-bit filter with 4 hashes, 4 rounds (one round does not fit one GPU: its
+candidate list, table and output would need more than its memory). ``value``
+is measured with the ASCII resident in device memory; ``e2e`` streams it from
+page-locked host memory through the library's streamed entry point and reads
+the junction positions back, every step. The input (24 GB) is far larger than
+L2, so nothing is flushed between steps.
+
+Beside it the line carries the bacterial-size set (7 genomes of 4.6-5.6 Mbp,
+2^28 bits, 1 round; L2 flushed between steps), the batched 62-genome set and
+the served request stream.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload mammal_set|bacterial_set|plain_single] [--genome-len L]
 
-Under torchrun every rank runs an independent replica of the workload on
-its own GPU (the build of one genome set does not shard); ``value`` is the
-bases of all replicas over the slowest rank's time. ``--impl reference``
-times the CPU oracle on a bounded sample of the same workload instead.
+Under torchrun the build is split by k-mer class (one process per GPU, rounds
+r with r % N == rank, C_final merged by one all-reduce; at least N rounds):
+``value`` is the one genome set's bases over the slowest rank's time
+(strong scaling). ``--impl reference`` times the CPU oracle on a bounded
+sample of the same workload instead.
 """
 import argparse
 import json
@@ -31,46 +44,64 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gbp/s genome input through both passes, k=25, 1 GB300; % roofline; p99 latency"
 UNIT = "Gbp/s"
-WORKLOAD = "bacterial_set"
 K = 25
-FILTER_BITS = 1 << 28
-HASHES = 4
-ROUNDS = 1
 FLUSH_BYTES = 512 << 20
-CPU_SAMPLE_BASES = 8_000_000     # cpu_baseline leg: about 10 s of oracle work
-REF_STEP_BASES = 4_000_000   # reference arm: one bounded sample per step (all host cores)
+CPU_SAMPLE_BASES = 100_000_000   # cpu_baseline leg: about 15 s of oracle work on 16 cores
+REF_STEP_BASES = 4_000_000       # reference arm: one bounded sample per step (all host cores)
+MAMMAL_GENOME_LEN = 3_000_000_000
+
+WORKLOADS = {
+    "mammal_set": {
+        "filter_bits": 1 << 36, "hashes": 4, "rounds": 4,
+        "desc": "mammal_set: 8 genomes of ~3 Gbp (24 Gbp) at the leaves of a seeded random binary tree "
+                "(seed 1607, drawn on the GPU): 41% GC ancestor, 45% repeats (6 kbp and 300 bp families "
+                "at 10-15% divergence), per-edge 0.2-1.2% SNPs and 1-10 bp indels at 10:1 plus 0-2 "
+                "inversions/transpositions of 1-20 kbp"},
+    "bacterial_set": {
+        "filter_bits": 1 << 28, "hashes": 4, "rounds": 1,
+        "desc": "bacterial_set: 7 related genomes of 4.6-5.6 Mbp (seed 1603; 50% GC ancestor, 1% SNPs, "
+                "0.1% indels, 20 inversions/transpositions of 1-50 kbp, 1.5 kbp repeat x30)"},
+    "plain_single": {
+        "filter_bits": 1 << 24, "hashes": 3, "rounds": 1,
+        "desc": "plain_single: 4 related 1 Mbp genomes (seed 1602; uniform ancestor, 0.5% SNPs, "
+                "0.05% indels, 300 bp repeat x200 at 5%)"},
+}
 
 
-def workload_config(total_bases: int) -> dict:
-    desc = ("bacterial_set: 7 related genomes of 4.6-5.6 Mbp (seed 1603; 50% GC ancestor, "
-            "1% SNPs, 0.1% indels, 20 inversions/transpositions of 1-50 kbp, 1.5 kbp repeat x30)")
-    if WORKLOAD == "plain_single":
-        desc = ("plain_single: 4 related 1 Mbp genomes (seed 1602; uniform ancestor, 0.5% SNPs, "
-                "0.05% indels, 300 bp repeat x200 at 5%)")
+def workload_config(name: str, total_bases: int, rounds: int = None, world: int = 1) -> dict:
+    w = WORKLOADS[name]
+    big = total_bases > (256 << 20)
     return {
-        "workload": desc,
+        "workload": w["desc"],
         "total_bases": int(total_bases),
-        "k": K, "filter_bits": FILTER_BITS, "hashes": HASHES, "rounds": ROUNDS,
-        "both_strands": True,
-        "l2": f"flushed between timed steps ({FLUSH_BYTES >> 20} MiB write); input 35 MB < L2",
-        "launch": "one CUDA-graph replay of the whole run per step (twopaco_plan_launch)",
+        "k": K, "filter_bits": w["filter_bits"], "hashes": w["hashes"],
+        "rounds": rounds or w["rounds"], "both_strands": True,
+        "l2": (f"input ({total_bases / 1e9:.1f} GB) larger than L2: no flush" if big else
+               f"flushed between timed steps ({FLUSH_BYTES >> 20} MiB write); input < L2"),
+        "launch": "one CUDA-graph replay of the whole run per step (twopaco_plan_launch)" if world == 1
+                  else "class-sharded: twopaco_shard_begin/rounds per rank, C_final all-reduced, "
+                       "rank 0 writes the output",
     }
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
-    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--workload", default="mammal_set", choices=sorted(WORKLOADS))
+    p.add_argument("--genome-len", type=int, default=MAMMAL_GENOME_LEN,
+                   help="mammal_set: bases per genome (a smaller slice of the same recipe)")
+    p.add_argument("--rounds", type=int, default=0, help="override the workload's rounds")
+    p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--bacterial", type=int, default=1,
+                   help="1: add the bacterial-size set's own line (when the headline is another workload)")
     p.add_argument("--batched", type=int, default=1,
                    help="1: add the batched leg (62 genomes in one tuned build vs one build per genome)")
     p.add_argument("--serve-requests", type=int, default=100,
                    help="requests of the served leg (Poisson, 20/s); 0 skips it")
-    p.add_argument("--workload", default=WORKLOAD, choices=["bacterial_set", "plain_single"],
-                   help="plain_single: the 4 x 1 Mbp set (k=25, 2^24 bits, 3 hashes) for small captures")
     return p.parse_args()
 
 
@@ -151,6 +182,8 @@ def dist_init():
         import torch.distributed as dist
         import torch
         backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
         dist.init_process_group(backend=backend)
     return world, rank, local
 
@@ -172,22 +205,28 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
-# Algorithmic work of every kernel per launch, from the run's own counters:
-# (unit, amount, kind) where kind names the roofline denominator.
+# Algorithmic work of every kernel over one step, from the run's own counters:
+# (amount, kind) where kind names the roofline denominator: "rand_or" / "rand_read"
+# are random 64-bit atomic ORs / 8-byte loads into the structure the kernel hits
+# (one per unit), "hbm" streaming bytes.
 def kernel_work(name, st, m, n_seqs, table_bytes):
     pos = st["positions"]
     cand = st["pass1_marks"]
     junc = st["pass2_marks"]
     if name == "pass1_insert":
-        return pos, "l2_or"        # one random filter sector (read + ORs) per position
+        return pos, "rand_or"       # one random filter word OR per position
     if name == "pass1_probe":
-        return pos, "l2_read"      # one random filter sector read per position
+        return pos, "rand_read"     # one random filter word load per position
     if name == "pass2_insert":
-        return cand, "l2_or"       # one table slot (CAS + OR) per candidate
+        return cand, "rand_or"      # one table slot (CAS / OR) per candidate
     if name == "pass2_classify":
-        return cand, "l2_read"     # one table slot read per candidate
+        return cand, "rand_read"    # one table slot load per candidate
+    if name == "partition_count":
+        return pos, "rand_read"     # one random filter word test per position
     if name == "pack":
-        return m + m / 4, "hbm"    # ASCII read + packed write (bytes)
+        return m + m / 4, "hbm"     # ASCII read + packed write (bytes)
+    if name == "class_map":
+        return m / 4 + m, "hbm"     # packed read + one class byte written per position
     if name == "table_clear":
         return table_bytes, "hbm"
     if name == "emit":
@@ -223,6 +262,270 @@ def ncu_traffic(workload, kernel):
                 return int(m.group(3))
     return None
 
+
+# ---------------------------------------------------------------------------
+# inputs and sizes
+# ---------------------------------------------------------------------------
+
+def load_workload(name, genome_len, dev):
+    """(device bases, host offsets, host sequence views or None) of a workload."""
+    import torch
+    if name == "mammal_set":
+        from paper_1602_05856_gb300 import genomes_gpu as GG
+        leaves = GG.mammal_set(genome_len=genome_len, device=dev)
+        d_bases, off = GG.concat_device(leaves)
+        del leaves
+        torch.cuda.empty_cache()
+        return d_bases, off, None
+    from paper_1602_05856_gb300 import genomes
+    seqs = genomes.named_set(name)
+    bases, off = genomes.concat(seqs)
+    return torch.from_numpy(bases).to(dev), off, seqs
+
+
+def sized_options(T, name, m, rounds, stream=0):
+    """Options and output capacity: the defaults for inputs that fit them; for the
+    mammal-scale set a pass-2 table, candidate list and output sized from its measured
+    shares (28% of the positions survive pass 1 at 4 rounds, 26.6% are junctions, about
+    8% of a round's positions are distinct candidates) with room to spare -- a run that
+    still overflows fails loudly."""
+    w = WORKLOADS[name]
+    if name != "mammal_set":
+        return T.Options(hashes=w["hashes"], cuda_stream=stream), None
+    per_round = m // rounds
+    slots = 1 << max(20, int(np.ceil(np.log2(max(per_round * 0.3, 1)))))
+    return (T.Options(hashes=w["hashes"], table_slots=slots, candidate_records=per_round // 2,
+                      cuda_stream=stream), m // 3)
+
+
+def l2_or_hbm_peaks(build, filter_bytes):
+    """Random-access rates (accesses/s) of this GPU on a buffer of the filter's size:
+    64-bit atomic ORs and 8-byte loads, each the better of two address generators
+    (a 64-bit mixer per access, or a 32-bit linear congruential sequence)."""
+    import ctypes
+    peaks = ctypes.CDLL(build.build_peaks())
+    peaks.peaks_l2_random_rate.restype = ctypes.c_double
+    peaks.peaks_l2_random_rate.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int]
+    buf = max(1 << 20, min(int(filter_bytes), 8 << 30))
+    r = {"or_mix": peaks.peaks_l2_random_rate(1, buf, 64, 5),
+         "or_lcg": peaks.peaks_l2_random_rate(4, buf, 1024, 5),
+         "read_mix": peaks.peaks_l2_random_rate(2, buf, 64, 5),
+         "read_lcg": peaks.peaks_l2_random_rate(5, buf, 1024, 5),
+         "sector_read_lcg": peaks.peaks_l2_random_rate(3, buf, 1024, 5),
+         "buffer_bytes": buf}
+    r["or"] = max(r["or_mix"], r["or_lcg"])
+    r["read"] = max(r["read_mix"], r["read_lcg"])
+    return r
+
+
+def roofline(prof, st, m, n, table_bytes, peaks, hbm_peak, peaks_json, workload, in_l2):
+    """The roofline object of the dominant modelled kernel."""
+    modelled = [kv for kv in prof.items() if kernel_work(kv[0], st, m, n, table_bytes)[0] is not None]
+    name, rec = max(modelled or prof.items(), key=lambda kv: kv[1]["ms"])
+    ms = rec["ms"] / rec["launches"]
+    amount, kind = kernel_work(name, st, m, n, table_bytes)
+    amount = (amount or 0.0) / rec["launches"]  # the step's work shared over its launches
+    if kind in (None, "hbm"):
+        achieved = amount / (ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks_json
+                               else "fallback 6.8 TB/s (of fallback)"}
+    else:
+        pk = (peaks["read"] if kind == "rand_read" else peaks["or"]) / 1e9
+        achieved = amount / (ms * 1e-3) / 1e9
+        where = "L2-resident" if in_l2 else "in HBM, beyond L2"
+        roof = {"bound": "l2" if in_l2 else "hbm_random", "achieved": achieved, "peak": pk,
+                "unit": "Gaccess/s", "frac": achieved / pk if pk > 0 else None,
+                "peak_source": f"measured in this run: random "
+                               + ("8-byte loads" if kind == "rand_read" else "64-bit atomic ORs")
+                               + f" over a {peaks['buffer_bytes'] >> 20} MiB buffer ({where}, the "
+                               "filter's size), all SMs, the better of a 64-bit-mixer and a "
+                               "32-bit-LCG address stream, best of 5 (of measured)"}
+    roof["kernel"] = name
+    roof["traffic"] = ncu_traffic(workload, name)
+    roof["traffic_unit"] = "DRAM bytes per launch (ncu, cold cache)"
+    roof["kernel_ms"] = ms
+    return roof
+
+
+# ---------------------------------------------------------------------------
+# device-resident timing
+# ---------------------------------------------------------------------------
+
+def time_steps(T, step, stream, steps, warmup, flush, dev):
+    """Run warmup untimed steps, then time `steps` with CUDA events on `stream`."""
+    import torch
+    for _ in range(max(warmup, 0)):
+        step()
+    torch.cuda.synchronize(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    prof: dict = {}
+    T.twopaco_profile_enable(True)
+    launches0 = T.twopaco_kernel_launches()
+    wall0 = time.perf_counter()
+    for i in range(steps):
+        if flush is not None:
+            flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+        ends[i].synchronize()  # between steps: this step's kernel events are final
+        for name, rec in T.twopaco_profile_kernels().items():
+            p = prof.setdefault(name, {"launches": 0, "ms": 0.0})
+            p["launches"] += rec["launches"]
+            p["ms"] += rec["ms"]
+        T.twopaco_profile_enable(True)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    launches = T.twopaco_kernel_launches() - launches0
+    T.twopaco_profile_enable(False)
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)], prof, launches, wall
+
+
+def kernels_summary(prof, steps):
+    tot = sum(x["ms"] for x in prof.values()) or 1.0
+    return {k: {"launches": v["launches"], "launches_per_step": v["launches"] / max(steps, 1),
+                "ms_per_launch": v["ms"] / v["launches"], "ms_per_step": v["ms"] / max(steps, 1),
+                "share": v["ms"] / tot} for k, v in prof.items()}
+
+
+def device_leg(T, build, name, genome_len, rounds, args, world, rank, local, dist):
+    """Device-resident throughput of one workload (and its e2e), as one dict."""
+    import torch
+    from paper_1602_05856_gb300 import shard
+    dev = torch.device("cuda", local)
+    w = WORKLOADS[name]
+    rounds = rounds or w["rounds"]
+    if world > 1:
+        rounds = max(rounds, world)  # every rank owns at least one class
+    d_bases, off, seqs = load_workload(name, genome_len, dev)
+    m, n = int(off[-1]), len(off) - 1
+    stream = torch.cuda.current_stream(dev)
+    opts, capacity = sized_options(T, name, m, rounds)
+    run = T.DeviceBuild(d_bases, off, K, w["filter_bits"], rounds, opts, device=f"cuda:{local}",
+                        capacity=capacity)
+    in_l2 = w["filter_bits"] // 8 <= (64 << 20)
+    peaks = l2_or_hbm_peaks(build, w["filter_bits"] // 8)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev) if m <= (256 << 20) else None
+    if world == 1:
+        run.capture()  # the whole run as one CUDA graph
+
+        def step():
+            run.run(stream)
+    else:
+        def step():
+            shard.sharded_build(run, rank, world, dist)
+    props = torch.cuda.get_device_properties(dev)
+    sampler = ClockSampler(str(getattr(props, "uuid", "") or ""))
+    barrier(world)
+    sampler.start()
+    step_ms, prof, launches, wall = time_steps(T, step, stream, args.steps, args.warmup, flush, dev)
+    barrier(world)
+    clocks = sampler.stop()
+    run.release_plan()
+    st = run.stats(stream)  # raises on any recorded failure (overflow, bad base, timeout)
+    ms = statistics.mean(step_ms)
+    ms_max = max_over_ranks(ms, world)
+    junctions = int(run.out_offsets[-1].item()) if rank == 0 else st["pass2_marks"]
+    table_bytes = st["table_slots"] * (8 if K <= 27 else 16 if K <= 31 else 32)
+    peaks_json = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = float(peaks_json.get("hbm_gbs", 6800.0))
+    out = {"name": name, "m": m, "n": n, "rounds": rounds, "ms": ms_max, "step_ms": step_ms,
+           "value": m / (ms_max * 1e-3) / 1e9, "launches": launches, "clocks": clocks, "wall": wall,
+           "stats": {k: st[k] for k in ("positions", "pass1_marks", "pass2_marks", "table_slots")}
+                    | {"junctions": junctions},
+           "kernels": kernels_summary(prof, args.steps),
+           "roofline": roofline(prof, st, m, n, table_bytes, peaks, hbm_peak, peaks_json, name, in_l2),
+           "random_access_peaks_g_per_s": {k: (v / 1e9 if k != "buffer_bytes" else v)
+                                           for k, v in peaks.items()}}
+    out["e2e"] = e2e_leg(T, run, d_bases, off, seqs, name, opts, rounds, args, world, rank, dev,
+                         junctions) if args.e2e_steps > 0 else None
+    out["cpu_sample"] = cpu_sample(d_bases, off, seqs) if rank == 0 and not args.no_cpu_baseline else None
+    del run, d_bases
+    torch.cuda.empty_cache()
+    return out
+
+
+def e2e_leg(T, run, d_bases, off, seqs, name, opts, rounds, args, world, rank, dev, junctions):
+    """The same metric through the public API with host buffers, copies inside the timed
+    region: the mammal set streamed from page-locked host memory through
+    twopaco_run_streamed and the junction positions read back; the smaller sets through
+    twopaco_build_ctx on a reused context."""
+    import torch
+    m, n = int(off[-1]), len(off) - 1
+    w = WORKLOADS[name]
+    times = []
+    if name == "mammal_set" or world > 1:
+        host = torch.empty(m, dtype=torch.uint8, pin_memory=True)
+        host.copy_(d_bases)
+        staging = torch.empty(1 << 29, dtype=torch.uint8, device=dev)  # two 256 MiB halves
+        out_pos = torch.empty(max(junctions, 1), dtype=torch.int64, pin_memory=True)
+        out_off = torch.empty(n + 1, dtype=torch.int64, pin_memory=True)
+        stream = torch.cuda.current_stream(dev)
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            if world == 1:
+                run.run_streamed(host, staging, stream)
+            else:  # every rank copies its own input in, then the class-sharded rounds
+                from paper_1602_05856_gb300 import shard
+                run.bases.copy_(host, non_blocking=True)
+                shard.sharded_build(run, rank, world, torch.distributed)
+            if rank == 0:  # the rank that wrote the output reads it back
+                out_off.copy_(run.out_offsets, non_blocking=True)
+                stream.synchronize()
+                total = int(out_off[-1].item())
+                if total != junctions:
+                    raise RuntimeError("the streamed run and the device run disagree")
+                out_pos[:total].copy_(run.out_positions[:total], non_blocking=True)
+            stream.synchronize()
+            if i:
+                times.append(time.perf_counter() - t0)
+        api = ("twopaco_run_streamed: page-locked host ASCII streamed through two 256 MiB staging "
+               "halves (copies overlapped with the packing), run, D2H of offsets and positions into "
+               "page-locked memory")
+        h2d = m
+    else:
+        pinned = torch.empty(m, dtype=torch.uint8, pin_memory=True)
+        pinned.copy_(d_bases)
+        host = pinned.numpy()
+        host_seqs = [host[int(off[t]):int(off[t + 1])] for t in range(n)]
+        ctx = T.Context()
+        for i in range(args.e2e_steps + 1):
+            t0 = time.perf_counter()
+            got, _ = ctx.build(host_seqs, K, w["filter_bits"], rounds, T.Options(hashes=w["hashes"]),
+                               copy=False)
+            if i:
+                times.append(time.perf_counter() - t0)
+            if sum(g.size for g in got) != junctions:
+                raise RuntimeError("host API and device run disagree")
+        ctx.close()
+        api = ("twopaco_build_ctx: pinned host ASCII in, H2D, run, D2H of offsets and positions into "
+               "pinned memory, on a reused context")
+        h2d = m + 8 * (n + 1)
+    sec = max_over_ranks(statistics.mean(times), world)
+    return {"value": m / sec / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": 8 * (n + 1) + 8 * junctions, "api": api, "ms_per_step": sec * 1e3}
+
+
+def cpu_sample(d_bases, off, seqs):
+    """Prefixes of every genome, ~CPU_SAMPLE_BASES in all, as host arrays."""
+    n = len(off) - 1
+    per = max(1, CPU_SAMPLE_BASES // n)
+    out = []
+    for t in range(n):
+        a = int(off[t])
+        ln = min(per, int(off[t + 1]) - a)
+        out.append(d_bases[a:a + ln].cpu().numpy() if seqs is None else seqs[t][:ln])
+    return out
+
+
+# ---------------------------------------------------------------------------
+# batched and served legs
+# ---------------------------------------------------------------------------
 
 def batched_leg(T, genomes, dev):
     """The 62-genome set (310 Mbp) as one build with the autotuner's (b, h), against the
@@ -293,196 +596,106 @@ def batched_leg(T, genomes, dev):
                     "throughput only)"}
 
 
+def served_leg(args, local):
+    from paper_1602_05856_gb300 import genomes, serve
+    seqs = genomes.named_set("bacterial_set")
+    reqs = serve.served_requests(seqs, args.serve_requests, 20.0, seed=1606)
+    slots = [serve.GpuSlot(device=f"cuda:{local}") for _ in range(4)]
+    for sl in slots:  # resident buffers sized for the trace, as a server keeps them
+        sl.reserve(reqs)
+        for r in serve.served_requests(seqs, 2, 1000.0, seed=7):  # both request shapes (k 25, 31)
+            serve.run_alone(sl, [r])
+    import gc
+    gc.collect()
+    gc.disable()  # no collector pause inside the timed loops
+    try:
+        mix = serve.Scheduler(slots, 120 << 30).run(reqs).summary()
+        alone_reqs = serve.served_requests(seqs, args.serve_requests, 20.0, seed=1606)
+        alone = serve.run_alone(slots[0], alone_reqs).summary()
+    finally:
+        gc.enable()
+    keys = ("p50_ms", "p95_ms", "p99_ms", "max_ms", "throughput_gbps", "wall_s")
+    return {"requests": args.serve_requests, "rate_per_s": 20.0, "slots": 4, "budget_gb": 120,
+            "mix": {k: mix[k] for k in keys}, "alone": {k: alone[k] for k in keys},
+            "request_recipe": "2-7 prefixes of the 7 genomes, log-uniform 0.1-5 Mbp, k 25/31, "
+                              "~8 filter bits per base, 4 hashes"}
+
+
+# ---------------------------------------------------------------------------
+# the two arms
+# ---------------------------------------------------------------------------
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_1602_05856_gb300 import build, genomes, twopaco as T
-
-    global WORKLOAD, FILTER_BITS, HASHES
-    if args.workload == "plain_single":
-        WORKLOAD, FILTER_BITS, HASHES = "plain_single", 1 << 24, 3
 
     torch.cuda.set_device(local)
     if rank == 0:  # one rank compiles (if anything is out of date); the others wait for it
         build.build()
     barrier(world)
     build.build()  # up to date now: only checks
-    dev = torch.device("cuda", local)
-    seqs = genomes.named_set(WORKLOAD)
-    bases, off = genomes.concat(seqs)
-    m, n = int(off[-1]), len(seqs)
-    opts = T.Options(hashes=HASHES)
-    run = T.DeviceBuild(bases, off, K, FILTER_BITS, ROUNDS, opts, device=f"cuda:{local}")
-    stream = torch.cuda.current_stream(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    name = args.workload
+    head = device_leg(T, build, name, args.genome_len, args.rounds, args, world, rank, local, dist)
 
-    # roofline denominators measured on this GPU: random 32-byte sectors of a
-    # buffer the size of the filter
-    import ctypes
-    peaks = ctypes.CDLL(build.build_peaks())
-    peaks.peaks_l2_random_rate.restype = ctypes.c_double
-    peaks.peaks_l2_random_rate.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int]
-    l2_read = peaks.peaks_l2_random_rate(2, FILTER_BITS // 8, 64, 5)   # random 8-byte loads
-    l2_or = peaks.peaks_l2_random_rate(1, FILTER_BITS // 8, 64, 5)     # random 64-bit ORs
-    l2_sector = peaks.peaks_l2_random_rate(0, FILTER_BITS // 8, 64, 5)  # random 32-byte sectors
+    extra = {}
+    if rank == 0 and world == 1 and args.bacterial and name != "bacterial_set":
+        b = device_leg(T, build, "bacterial_set", 0, 0, args, 1, 0, local, None)
+        extra["bacterial_set"] = {
+            "value": b["value"], "unit": UNIT, "ms_per_step": b["ms"], "config":
+                workload_config("bacterial_set", b["m"]), "roofline": b["roofline"],
+            "e2e": b["e2e"], "stats": b["stats"], "kernels": b["kernels"], "gpu_launches": b["launches"],
+            "random_access_peaks_g_per_s": b["random_access_peaks_g_per_s"], "clocks": b["clocks"]}
+    if rank == 0 and world == 1 and args.batched:
+        extra["batched"] = batched_leg(T, genomes, torch.device("cuda", local))
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        extra["served"] = served_leg(args, local)
 
-    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    # the whole run is captured once as a CUDA graph (with its per-kernel events)
-    T.twopaco_profile_enable(True)
-    run.capture()
-    for _ in range(max(args.warmup, 0)):
-        run.run(stream)
-    st = run.stats(stream)  # raises on any recorded failure
-    torch.cuda.synchronize(dev)
-
-    props = torch.cuda.get_device_properties(dev)
-    uuid = str(getattr(props, "uuid", "") or "")
-    sampler = ClockSampler(uuid)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    prof: dict = {}
-    barrier(world)
-    torch.cuda.synchronize(dev)
-    sampler.start()
-    launches0 = T.twopaco_kernel_launches()
-    wall0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.zero_()
-        starts[i].record(stream)
-        run.run(stream)
-        ends[i].record(stream)
-        ends[i].synchronize()  # between steps: this replay's kernel events are final
-        for name, rec in T.twopaco_profile_kernels().items():
-            p = prof.setdefault(name, {"launches": 0, "ms": 0.0})
-            p["launches"] += rec["launches"]
-            p["ms"] += rec["ms"]
-    torch.cuda.synchronize(dev)
-    wall = time.perf_counter() - wall0
-    barrier(world)
-    clocks = sampler.stop()
-    launches = T.twopaco_kernel_launches() - launches0
-    T.twopaco_profile_enable(False)
-    run.release_plan()
-    st = run.stats(stream)
-
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = statistics.mean(step_ms)
-    ms_max = max_over_ranks(ms, world)
-    value = world * m / (ms_max * 1e-3) / 1e9
-
-    # end to end through the host API: pinned host input in, host result out
-    pinned = torch.empty(m, dtype=torch.uint8, pin_memory=True)
-    pinned.numpy()[:] = bases
-    host = pinned.numpy()
-    host_seqs = [host[int(off[t]):int(off[t + 1])] for t in range(n)]
-    e2e_t = []
-    junctions = st["pass2_marks"]
-    ctx = T.Context()
-    for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
-        t0 = time.perf_counter()
-        got, est = ctx.build(host_seqs, K, FILTER_BITS, ROUNDS, opts, copy=False)
-        if i:
-            e2e_t.append(time.perf_counter() - t0)
-        assert sum(g.size for g in got) == junctions, "host API and device run disagree"
-    ctx.close()
-    e2e_s = max_over_ranks(statistics.mean(e2e_t), world) if e2e_t else None
-    # served leg: a Poisson stream of build requests through the continuous-batching loop
-    served = None
-    if args.serve_requests > 0:
-        from paper_1602_05856_gb300 import serve
-        reqs = serve.served_requests(seqs, args.serve_requests, 20.0, seed=1606)
-        slots = [serve.GpuSlot(device=f"cuda:{local}") for _ in range(4)]
-        for sl in slots:  # resident buffers sized for the trace, as a server keeps them
-            sl.reserve(reqs)
-            for r in serve.served_requests(seqs, 2, 1000.0, seed=7):  # both request shapes (k 25, 31)
-                serve.run_alone(sl, [r])
-        import gc
-        gc.collect()
-        gc.disable()  # no collector pause inside the timed loops
-        try:
-            mix = serve.Scheduler(slots, 120 << 30).run(reqs).summary()
-            alone_reqs = serve.served_requests(seqs, args.serve_requests, 20.0, seed=1606)
-            alone = serve.run_alone(slots[0], alone_reqs).summary()
-        finally:
-            gc.enable()
-        keys = ("p50_ms", "p95_ms", "p99_ms", "max_ms", "throughput_gbps", "wall_s")
-        served = {"requests": args.serve_requests, "rate_per_s": 20.0, "slots": 4,
-                  "budget_gb": 120,
-                  "mix": {k: mix[k] for k in keys},
-                  "alone": {k: alone[k] for k in keys},
-                  "request_recipe": "2-7 prefixes of the 7 genomes, log-uniform 0.1-5 Mbp, k 25/31, "
-                                    "~8 filter bits per base, 4 hashes"}
-
-    batched = batched_leg(T, genomes, dev) if args.batched and rank == 0 else None
-
-    # roofline of the dominant kernel
-    table_bytes = st["table_slots"] * (8 if K <= 27 else 16 if K <= 31 else 32)
-    # the kernel with the largest share among those with a work model
-    modelled = [kv for kv in prof.items() if kernel_work(kv[0], st, m, n, table_bytes)[0] is not None]
-    top = max(modelled or prof.items(), key=lambda kv: kv[1]["ms"])
-    name, rec = top
-    per_launch_ms = rec["ms"] / rec["launches"]
-    amount, kind = kernel_work(name, st, m, n, table_bytes)
-    if amount is None:
-        amount, kind = 0.0, "hbm"
-    peaks_json = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    hbm_peak = float(peaks_json.get("hbm_gbs", 6800.0))
-    if kind == "hbm":
-        achieved = amount / (per_launch_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks_json else "fallback 6.8 TB/s"}
-    else:
-        pk = (l2_read if kind == "l2_read" else l2_or) / 1e9
-        achieved = amount / (per_launch_ms * 1e-3) / 1e9
-        roof = {"bound": "l2", "achieved": achieved, "peak": pk, "unit": "Gsector/s",
-                "frac": achieved / pk if pk > 0 else None, "traffic": None,
-                "peak_source": ("measured in this run: random "
-                                + ("8-byte loads" if kind == "l2_read" else "64-bit atomic ORs")
-                                + f" over a {FILTER_BITS // 8 >> 20} MiB buffer (the filter's size), "
-                                "all SMs, best of 5")}
-    roof["kernel"] = name
-    roof["traffic"] = ncu_traffic(WORKLOAD, name)
-    roof["traffic_unit"] = "DRAM bytes per launch (ncu, cold cache)"
-    roof["kernel_ms"] = per_launch_ms
-
-    kernels = {k: {"launches": v["launches"], "ms_per_launch": v["ms"] / v["launches"],
-                   "share": v["ms"] / sum(x["ms"] for x in prof.values())}
-               for k, v in prof.items()}
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        sample = sample_prefix(seqs, CPU_SAMPLE_BASES)
+    if rank == 0 and head["cpu_sample"] is not None:
+        sample = head["cpu_sample"]
         cores = host_cores()
         cpu = {"value": oracle_gbps(sample, K, threads=cores), "unit": UNIT, "cores": cores,
                "kind": "oracle",
-               "sample": f"{sum(s.size for s in sample)} bases: the first "
-                         f"{sample[0].size} bases of each of the 7 genomes; the definition split "
-                         f"over {cores} threads by k-mer hash class",
-               "single_thread_value": oracle_gbps(sample, K)}
-    lat = sorted(step_ms)
+               "sample": f"{sum(s.size for s in sample)} bases: the first {sample[0].size} bases of "
+                         f"each of the {len(sample)} genomes of the timed input; the definition split "
+                         f"over {cores} threads by k-mer hash class"}
+    lat = sorted(head["step_ms"])
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": workload_config(m) | {"parallelism": f"replicas{world}" if world > 1 else "single"},
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True,
+        "scaling": "weak" if world == 1 else "strong", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": workload_config(name, head["m"], head["rounds"], world)
+                  | {"parallelism": "single" if world == 1 else f"classes{world}"},
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
-        "e2e": {"value": world * m / e2e_s / 1e9, "unit": UNIT,
-                "h2d_bytes_per_step": m + 8 * (n + 1),
-                "d2h_bytes_per_step": 8 * (n + 1) + 8 * junctions,
-                "api": "twopaco_build_ctx: pinned host ASCII in, H2D, run, D2H of offsets and "
-                       "positions into pinned memory, on a reused context"} if e2e_s else None,
-        "gpu_launches": launches,
-        "roofline": roof,
+        "e2e": head["e2e"],
+        "gpu_launches": head["launches"],
+        "roofline": head["roofline"],
         "cpu_baseline": cpu,
-        "served": served,
-        "batched": batched,
-        "clocks": clocks,
-        "stats": {k: st[k] for k in ("positions", "pass1_marks", "pass2_marks", "table_slots")},
-        "kernels": kernels,
-        "l2_peaks_gsector_s": {"read8": l2_read / 1e9, "or64": l2_or / 1e9, "read32": l2_sector / 1e9},
-        "timed_wall_s": wall,
-    }
+        "clocks": head["clocks"],
+        "stats": head["stats"],
+        "kernels": head["kernels"],
+        "random_access_peaks_g_per_s": head["random_access_peaks_g_per_s"],
+        "timed_wall_s": head["wall"],
+    } | extra
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def reference_sample(name):
+    """One bounded sample of the workload for the reference arm (host arrays)."""
+    if name == "mammal_set":
+        from paper_1602_05856_gb300 import genomes_gpu as GG
+        leaves = GG.mammal_set(genome_len=REF_STEP_BASES // 8, device="cpu")
+        return [x.numpy() for x in leaves], ("8 leaves of the mammal-scale recipe drawn at "
+                                             f"{REF_STEP_BASES // 8} bases each")
+    from paper_1602_05856_gb300 import genomes
+    seqs = genomes.named_set(name)
+    sample = sample_prefix(seqs, REF_STEP_BASES)
+    return sample, f"the first {sample[0].size} bases of each of the {len(seqs)} genomes"
 
 
 def run_reference(args, world, rank):
@@ -490,9 +703,8 @@ def run_reference(args, world, rank):
         return
     from paper_1602_05856_gb300 import genomes
     import oracle
-    seqs = genomes.named_set(WORKLOAD)
-    m = sum(s.size for s in seqs)
-    sample = sample_prefix(seqs, REF_STEP_BASES)
+    name = args.workload
+    sample, what = reference_sample(name)
     sb, so = genomes.concat(sample)
     cores = host_cores()
     for _ in range(max(args.warmup, 0)):
@@ -504,13 +716,15 @@ def run_reference(args, world, rank):
         ts.append(time.perf_counter() - t)
     sec = statistics.mean(ts)
     value = sb.size / sec / 1e9
-    desc = (f"{sb.size} bases per step: the first {sample[0].size} bases of each of the 7 genomes; "
-            f"CPU oracle (plain definition) split over {cores} threads by k-mer hash class")
+    full = 8 * args.genome_len if name == "mammal_set" else sum(s.size for s in genomes.named_set(name))
+    desc = (f"{sb.size} bases per step: {what}; CPU oracle (plain definition) split over {cores} "
+            f"threads by k-mer hash class")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": "synthetic", "config": workload_config(m) | {"parallelism": "single"},
+        "data": "synthetic",
+        "config": workload_config(name, full, args.rounds or None) | {"parallelism": "single"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)

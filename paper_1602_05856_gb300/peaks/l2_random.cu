@@ -55,12 +55,76 @@ __global__ void __launch_bounds__(256) sector_ors(unsigned long long* __restrict
   }
 }
 
+// The same three access kinds with cheap addresses: a 32-bit linear
+// congruential sequence per thread (Numerical Recipes' constants; one
+// multiply-add per access), its high bits scaled to the buffer. Four
+// independent accesses per step keep more requests in flight; nothing depends
+// on loaded data, so the loop issues as fast as the memory system takes it.
+__device__ __forceinline__ uint32_t lcg(uint32_t x) { return x * 1664525u + 1013904223u; }
+
+__global__ void __launch_bounds__(256) sector_reads_lcg(const ulonglong2* __restrict__ buf, int lg_units,
+                                                        int iters, unsigned long long* sink) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t x[4];
+  for (int j = 0; j < 4; ++j) x[j] = (uint32_t)mix(4ull * tid + j + 1);
+  uint64_t acc = 0;
+  for (int it = 0; it < iters; it += 4) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      x[j] = lcg(x[j]);
+      const uint64_t b = lg_units ? (x[j] >> (32 - lg_units)) : 0;
+      const ulonglong2 a = __ldcg(buf + 2 * b), c = __ldcg(buf + 2 * b + 1);
+      acc ^= a.x ^ a.y ^ c.x ^ c.y;
+    }
+  }
+  if (acc == 0x1234567ull) sink[0] = acc;
+}
+
+__global__ void __launch_bounds__(256) word_reads_lcg(const unsigned long long* __restrict__ buf, int lg_units,
+                                                      int iters, unsigned long long* sink) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t x[4];
+  for (int j = 0; j < 4; ++j) x[j] = (uint32_t)mix(4ull * tid + j + 3);
+  uint64_t acc = 0;
+  for (int it = 0; it < iters; it += 4) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      x[j] = lcg(x[j]);
+      acc ^= __ldcg(buf + (lg_units ? (x[j] >> (32 - lg_units)) : 0));
+    }
+  }
+  if (acc == 0x1234567ull) sink[0] = acc;
+}
+
+__global__ void __launch_bounds__(256) sector_ors_lcg(unsigned long long* __restrict__ buf, int lg_units,
+                                                      int iters) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t x[4];
+  for (int j = 0; j < 4; ++j) x[j] = (uint32_t)mix(4ull * tid + j + 7);
+  for (int it = 0; it < iters; it += 4) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      x[j] = lcg(x[j]);
+      const uint64_t b = lg_units ? (x[j] >> (32 - lg_units)) : 0;
+      atomicOr(buf + 4 * b + (x[j] & 3u), 1ull << ((x[j] >> 2) & 63u));
+    }
+  }
+}
+
+int log2_of(uint64_t x) {
+  int l = 0;
+  while ((1ull << l) < x) ++l;
+  return l;
+}
+
 }  // namespace
 
 extern "C" {
 
 // mode 0: random 32-byte sector reads; mode 1: random 64-bit ORs (one per
-// sector); mode 2: random 8-byte reads.
+// sector); mode 2: random 8-byte reads; modes 3, 4, 5: the same with the
+// linear-congruential addresses (iters a multiple of 4; buffers of at most
+// 2^32 units of 32 or 8 bytes).
 // buf_bytes: power of two >= 32. Returns sector operations per second, or a
 // negative value on a CUDA error. Allocates and frees its own buffer.
 double peaks_l2_random_rate(int mode, uint64_t buf_bytes, int iters, int reps) {
@@ -74,7 +138,15 @@ double peaks_l2_random_rate(int mode, uint64_t buf_bytes, int iters, int reps) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (mode == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sector_reads, 256, 0);
   else if (mode == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sector_ors, 256, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, word_reads, 256, 0);
+  else if (mode == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, word_reads, 256, 0);
+  else if (mode == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sector_reads_lcg, 256, 0);
+  else if (mode == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sector_ors_lcg, 256, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, word_reads_lcg, 256, 0);
+  if (mode < 0 || mode > 5 || (mode >= 3 && (iters % 4 || buf_bytes / 8 > (1ull << 32)))) {
+    cudaFree(sink);
+    cudaFree(buf);
+    return -1.0;
+  }
   const unsigned grid = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
   const uint64_t mask = buf_bytes / 32 - 1;
   cudaEvent_t a, b;
@@ -85,7 +157,15 @@ double peaks_l2_random_rate(int mode, uint64_t buf_bytes, int iters, int reps) {
     cudaEventRecord(a);
     if (mode == 0) sector_reads<<<grid, 256>>>(static_cast<const ulonglong2*>(buf), mask, iters, sink);
     else if (mode == 1) sector_ors<<<grid, 256>>>(static_cast<unsigned long long*>(buf), mask, iters);
-    else word_reads<<<grid, 256>>>(static_cast<const unsigned long long*>(buf), buf_bytes / 8 - 1, iters, sink);
+    else if (mode == 2)
+      word_reads<<<grid, 256>>>(static_cast<const unsigned long long*>(buf), buf_bytes / 8 - 1, iters, sink);
+    else if (mode == 3)
+      sector_reads_lcg<<<grid, 256>>>(static_cast<const ulonglong2*>(buf), log2_of(buf_bytes / 32), iters, sink);
+    else if (mode == 4)
+      sector_ors_lcg<<<grid, 256>>>(static_cast<unsigned long long*>(buf), log2_of(buf_bytes / 32), iters);
+    else
+      word_reads_lcg<<<grid, 256>>>(static_cast<const unsigned long long*>(buf), log2_of(buf_bytes / 8), iters,
+                                    sink);
     cudaEventRecord(b);
     cudaEventSynchronize(b);
     float ms = 0.f;

@@ -69,14 +69,27 @@ def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
 def test_kernel_work_model():
     st = {"positions": 1000, "pass1_marks": 80, "pass2_marks": 50}
     m, n, tb = 1024, 3, 1 << 20
-    assert bench.kernel_work("pass1_insert", st, m, n, tb) == (1000, "l2_or")
-    assert bench.kernel_work("pass1_probe", st, m, n, tb) == (1000, "l2_read")
-    assert bench.kernel_work("pass2_insert", st, m, n, tb) == (80, "l2_or")
-    assert bench.kernel_work("pass2_classify", st, m, n, tb) == (80, "l2_read")
+    assert bench.kernel_work("pass1_insert", st, m, n, tb) == (1000, "rand_or")
+    assert bench.kernel_work("pass1_probe", st, m, n, tb) == (1000, "rand_read")
+    assert bench.kernel_work("partition_count", st, m, n, tb) == (1000, "rand_read")
+    assert bench.kernel_work("pass2_insert", st, m, n, tb) == (80, "rand_or")
+    assert bench.kernel_work("pass2_classify", st, m, n, tb) == (80, "rand_read")
     assert bench.kernel_work("pack", st, m, n, tb) == (m + m / 4, "hbm")
+    assert bench.kernel_work("class_map", st, m, n, tb) == (m / 4 + m, "hbm")
     assert bench.kernel_work("table_clear", st, m, n, tb) == (tb, "hbm")
     assert bench.kernel_work("emit", st, m, n, tb) == (m / 8 + 8 * 50, "hbm")
     assert bench.kernel_work("table_setup", st, m, n, tb) == (None, None)
+
+
+def test_roofline_takes_the_dominant_modelled_kernel_per_launch():
+    st = {"positions": 10**9, "pass1_marks": 80, "pass2_marks": 50}
+    prof = {"pass1_insert": {"launches": 4, "ms": 8.0}, "table_setup": {"launches": 4, "ms": 100.0},
+            "pass1_probe": {"launches": 4, "ms": 4.0}}
+    peaks = {"or": 250e9, "read": 400e9, "buffer_bytes": 1 << 30}
+    r = bench.roofline(prof, st, 1024, 3, 1 << 20, peaks, 6000.0, {}, "wl", False)
+    assert r["kernel"] == "pass1_insert" and r["bound"] == "hbm_random"
+    # 1e9 positions over 4 launches of 2 ms each: 2.5e8 / 2 ms = 125 G/s against 250 G/s
+    assert abs(r["achieved"] - 125.0) < 1e-6 and abs(r["frac"] - 0.5) < 1e-9
 
 
 def test_traffic_lookup_is_keyed_by_workload_kernel_and_code(tmp_path, monkeypatch):
@@ -100,7 +113,10 @@ def test_traffic_lookup_is_keyed_by_workload_kernel_and_code(tmp_path, monkeypat
 
 
 def test_workload_config_names_the_workload():
-    c = bench.workload_config(35_000_000)
+    c = bench.workload_config("bacterial_set", 35_000_000)
     assert c["workload"].startswith("bacterial_set") and c["k"] == 25
     assert c["filter_bits"] == 1 << 28 and c["rounds"] == 1 and "flushed" in c["l2"]
     assert "model" not in c
+    c = bench.workload_config("mammal_set", 24_000_000_000)
+    assert c["workload"].startswith("mammal_set") and c["filter_bits"] == 1 << 36
+    assert c["rounds"] == 4 and "no flush" in c["l2"]
