@@ -318,13 +318,13 @@ def l2_or_hbm_peaks(build, filter_bytes):
     return r
 
 
-def roofline(prof, st, m, n, table_bytes, peaks, hbm_peak, peaks_json, workload, in_l2):
-    """The roofline object of the dominant modelled kernel."""
+def roofline(prof, st, m, n, table_bytes, peaks, hbm_peak, peaks_json, workload, in_l2, steps):
+    """The roofline object of the dominant modelled kernel; prof sums `steps` steps."""
     modelled = [kv for kv in prof.items() if kernel_work(kv[0], st, m, n, table_bytes)[0] is not None]
     name, rec = max(modelled or prof.items(), key=lambda kv: kv[1]["ms"])
     ms = rec["ms"] / rec["launches"]
     amount, kind = kernel_work(name, st, m, n, table_bytes)
-    amount = (amount or 0.0) / rec["launches"]  # the step's work shared over its launches
+    amount = (amount or 0.0) * steps / rec["launches"]  # a step's work shared over its launches
     if kind in (None, "hbm"):
         achieved = amount / (ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -353,8 +353,10 @@ def roofline(prof, st, m, n, table_bytes, peaks, hbm_peak, peaks_json, workload,
 # device-resident timing
 # ---------------------------------------------------------------------------
 
-def time_steps(T, step, stream, steps, warmup, flush, dev):
-    """Run warmup untimed steps, then time `steps` with CUDA events on `stream`."""
+def time_steps(T, step, stream, steps, warmup, flush, dev, graph):
+    """Run warmup untimed steps, then time `steps` with CUDA events on `stream`.
+    graph: every step replays a graph captured with profiling on, whose kernel events
+    every replay records again (else the step's launches record new events)."""
     import torch
     for _ in range(max(warmup, 0)):
         step()
@@ -362,7 +364,8 @@ def time_steps(T, step, stream, steps, warmup, flush, dev):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     prof: dict = {}
-    T.twopaco_profile_enable(True)
+    if not graph:
+        T.twopaco_profile_enable(True)
     launches0 = T.twopaco_kernel_launches()
     wall0 = time.perf_counter()
     for i in range(steps):
@@ -376,7 +379,8 @@ def time_steps(T, step, stream, steps, warmup, flush, dev):
             p = prof.setdefault(name, {"launches": 0, "ms": 0.0})
             p["launches"] += rec["launches"]
             p["ms"] += rec["ms"]
-        T.twopaco_profile_enable(True)
+        if not graph:
+            T.twopaco_profile_enable(True)  # drop this step's records
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - wall0
     launches = T.twopaco_kernel_launches() - launches0
@@ -410,6 +414,7 @@ def device_leg(T, build, name, genome_len, rounds, args, world, rank, local, dis
     peaks = l2_or_hbm_peaks(build, w["filter_bits"] // 8)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev) if m <= (256 << 20) else None
     if world == 1:
+        T.twopaco_profile_enable(True)  # before the capture: replays record the captured events
         run.capture()  # the whole run as one CUDA graph
 
         def step():
@@ -421,7 +426,8 @@ def device_leg(T, build, name, genome_len, rounds, args, world, rank, local, dis
     sampler = ClockSampler(str(getattr(props, "uuid", "") or ""))
     barrier(world)
     sampler.start()
-    step_ms, prof, launches, wall = time_steps(T, step, stream, args.steps, args.warmup, flush, dev)
+    step_ms, prof, launches, wall = time_steps(T, step, stream, args.steps, args.warmup, flush, dev,
+                                               graph=world == 1)
     barrier(world)
     clocks = sampler.stop()
     run.release_plan()
@@ -438,7 +444,8 @@ def device_leg(T, build, name, genome_len, rounds, args, world, rank, local, dis
            "stats": {k: st[k] for k in ("positions", "pass1_marks", "pass2_marks", "table_slots")}
                     | {"junctions": junctions},
            "kernels": kernels_summary(prof, args.steps),
-           "roofline": roofline(prof, st, m, n, table_bytes, peaks, hbm_peak, peaks_json, name, in_l2),
+           "roofline": roofline(prof, st, m, n, table_bytes, peaks, hbm_peak, peaks_json, name, in_l2,
+                                args.steps),
            "random_access_peaks_g_per_s": {k: (v / 1e9 if k != "buffer_bytes" else v)
                                            for k, v in peaks.items()}}
     out["e2e"] = e2e_leg(T, run, d_bases, off, seqs, name, opts, rounds, args, world, rank, dev,
@@ -528,10 +535,12 @@ def cpu_sample(d_bases, off, seqs):
 # ---------------------------------------------------------------------------
 
 def batched_leg(T, genomes, dev):
-    """The 62-genome set (310 Mbp) as one build with the autotuner's (b, h), against the
-    same genomes built one at a time (the single-instance path) at the same filter bits per
-    base, both device-resident and timed with CUDA events. The two compute different graphs
-    (one joint graph vs 62 separate ones): this compares throughput, not output."""
+    """The 62-genome set (310 Mbp) as one build: with the autotuner's (b, h) in one launch per
+    loop replayed as a CUDA graph (the batched path), against the same build issued the way a
+    per-genome loop issues it -- every loop launched once per genome, without graph capture --
+    and against an untuned filter. All three compute the same graph; their outputs are
+    compared here. One build per genome (62 separate, smaller graphs) is reported beside them
+    as context."""
     import torch
     from paper_1602_05856_gb300 import autotune
     seqs = genomes.named_set("batched_set")
@@ -553,17 +562,27 @@ def batched_leg(T, genomes, dev):
         torch.cuda.synchronize()
         return statistics.mean(x.elapsed_time(y) for x, y in zip(a, b))
 
-    def joint(bits, hashes):
-        run = T.DeviceBuild(bases, off, K, bits, 1, T.Options(hashes=hashes), device=dev)
-        run.capture()
+    def joint(bits, hashes, per_string=False):
+        run = T.DeviceBuild(bases, off, K, bits, 1,
+                            T.Options(hashes=hashes, per_string_launches=per_string), device=dev)
+        if not per_string:
+            run.capture()
+        n0 = T.twopaco_kernel_launches()
         ms = timed(run.run, 5)
+        launches = (T.twopaco_kernel_launches() - n0) // 6
         st = run.stats()
+        res = run.result()
         run.release_plan()
-        return ms, st
+        return ms, st, res, launches
 
-    batched_ms, st = joint(choice.bits, choice.hashes)
-    plain_ms, _ = joint(1 << 30, 4)  # the paper's filter size for inputs of this scale, 4 hashes
-    # one genome at a time through twopaco_run_device, on one workspace and one output buffer
+    batched_ms, st, want, batched_launches = joint(choice.bits, choice.hashes)
+    per_ms, _, got, per_launches = joint(choice.bits, choice.hashes, per_string=True)
+    plain_ms, _, got_plain, _ = joint(1 << 30, 4)  # the paper's filter size at this scale, 4 hashes
+    same = all(np.array_equal(a, b) for a, b in zip(want, got)) and \
+        all(np.array_equal(a, b) for a, b in zip(want, got_plain))
+    if not same:
+        raise RuntimeError("the batched, per-genome and untuned launches disagree")
+    # context: one separate build per genome through twopaco_run_device, on one workspace
     d_bases = torch.from_numpy(bases).to(dev)
     lens = [int(off[t + 1] - off[t]) for t in range(len(seqs))]
     bits_of = [1 << max(8, int(np.ceil(np.log2(max(bpb * ln, 1.0))))) for ln in lens]
@@ -587,13 +606,18 @@ def batched_leg(T, genomes, dev):
             "tuned": {"filter_bits": choice.bits, "hashes": choice.hashes, "rounds": choice.rounds,
                       "trials": len(choice.trials)},
             "batched_gbps": m / (batched_ms * 1e-3) / 1e9, "batched_ms": batched_ms,
+            "batched_launches_per_build": batched_launches,
+            "per_genome_launches_gbps": m / (per_ms * 1e-3) / 1e9, "per_genome_launches_ms": per_ms,
+            "per_genome_launches_per_build": per_launches,
             "untuned_gbps": m / (plain_ms * 1e-3) / 1e9, "untuned": {"filter_bits": 1 << 30, "hashes": 4},
-            "single_instance_gbps": m / (single_ms * 1e-3) / 1e9, "single_instance_ms": single_ms,
+            "same_output": same,
+            "separate_builds_gbps": m / (single_ms * 1e-3) / 1e9, "separate_builds_ms": single_ms,
             "pass1_survivors": st["pass1_marks"] / max(1, st["positions"]),
-            "note": "batched: one joint build of all genomes (one launch per kernel, graph replay) "
-                    "with the tuned (b, h), and untuned with b = 2^30, h = 4; single instance: each "
-                    "genome built alone, back to back (62 separate, far less branched graphs, so "
-                    "throughput only)"}
+            "note": "batched: one joint build (one launch per loop, graph replay) with the tuned "
+                    "(b, h); per-genome launches: the same build with every loop launched once per "
+                    "genome, no graph (identical output, checked); untuned: b = 2^30, h = 4 "
+                    "(identical output, checked); separate builds: each genome built alone (62 "
+                    "smaller graphs), context only"}
 
 
 def served_leg(args, local):

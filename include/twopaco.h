@@ -35,7 +35,7 @@
  *     [256, 2^40]; rounds >= 1; n_seqs < 2^32; total_bases < 2^48;
  *     options->hashes in [1, 8]; options->partition_bins a power of two
  *     >= rounds (and >= 2 when rounds > 1); options->both_strands and
- *     options->split_at_n and options->partial 0 or 1; options->wide_layout 0, 1 or 2;
+ *     options->split_at_n, options->partial and options->per_string_launches 0 or 1; options->wide_layout 0, 1 or 2;
  *     options->run_capacity < 2^32. Anything else is TWOPACO_EINVAL.
  *   - Calls on different workspaces may run concurrently from different host
  *     threads; calls that share a workspace must be serialised by the caller.
@@ -96,6 +96,15 @@ typedef struct twopaco_options {
                               output positions are non-branching paths, though not
                               all maximal. pass2_marks then counts the output
                               positions. 0 (default): the exact junctions. */
+  int per_string_launches; /* 1: every first- and second-pass loop of a device run
+                              is launched once per input string (over the tiles of
+                              4096 positions that start in it) instead of once over
+                              all strings, and pass 2 walks C_temp instead of a
+                              candidate list: the same build and output, issued the
+                              way a per-genome loop would issue it (a baseline for
+                              the batched launch). The call reads the string offsets
+                              back and synchronises the stream; twopaco_plan_create
+                              refuses it. 0 (default): one launch per loop. */
 } twopaco_options;
 
 /* Counters of one run, in the spirit of Table 4 (marks after each pass). */

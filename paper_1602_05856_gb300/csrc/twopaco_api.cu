@@ -53,6 +53,7 @@ int validate(uint64_t n_seqs, int k, uint64_t filter_bits, int rounds, const two
   if (o.wide_layout < 0 || o.wide_layout > 2) return TWOPACO_EINVAL;
   if (o.run_capacity >= (1ull << 32)) return TWOPACO_EINVAL;  // piece ranks are 32-bit
   if (o.partial != 0 && o.partial != 1) return TWOPACO_EINVAL;
+  if (o.per_string_launches != 0 && o.per_string_launches != 1) return TWOPACO_EINVAL;
   return TWOPACO_OK;
 }
 
@@ -185,6 +186,11 @@ RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_
   v.partial = o.partial;
   v.lg_blocks = log2_exact(filter_bits / 256);
   v.qmask = o.partition_bins - 1u;
+  // the pre-pass counts every k-mer up to 2^29 bases, then a 2^-s sample with
+  // s = floor(log2(m / 2^28)), at most 2^-8 (2^-6 at 24 Gbp)
+  int sample_log2 = 0;
+  while (sample_log2 < 8 && (m >> (28 + sample_log2 + 1)) > 0) ++sample_log2;
+  v.part_sample = (1u << sample_log2) - 1u;
   v.hdr = reinterpret_cast<DevHeader*>(base + L.header);
   v.packed = reinterpret_cast<uint32_t*>(base + L.packed);
   v.packed_words = L.packed_words;
@@ -193,6 +199,8 @@ RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_
   v.ctemp = reinterpret_cast<uint32_t*>(base + L.ctemp);
   v.cfinal = reinterpret_cast<uint32_t*>(base + L.cfinal);
   v.bitmap_words = L.bitmap_words;
+  v.p_begin = 0;
+  v.p_end = m;
   v.table = base + L.table;
   v.table_max_slots = L.table_slots;
   v.cands = reinterpret_cast<uint64_t*>(base + L.cands);
@@ -275,6 +283,7 @@ void twopaco_default_options(twopaco_options* opt) {
   opt->run_capacity = 0;
   opt->wide_layout = 0;
   opt->partial = 0;
+  opt->per_string_launches = 0;
 }
 
 const char* twopaco_strerror(int code) {
@@ -326,6 +335,25 @@ int device_run_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t 
   return TWOPACO_OK;
 }
 
+// The position ranges of per-string launches: tiles of kRangeTile positions,
+// each launched with the string that holds its first position (so that every
+// position is visited exactly once), one range per string that owns a tile.
+// Reads the offsets back from the device (synchronises the stream).
+int string_ranges(const uint64_t* d_offsets, uint64_t n_seqs, uint64_t m, cudaStream_t s,
+                  std::vector<std::pair<uint64_t, uint64_t>>* out) {
+  std::vector<uint64_t> off(n_seqs + 1);
+  cudaError_t e = cudaMemcpyAsync(off.data(), d_offsets, (n_seqs + 1) * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_code(e);
+  out->clear();
+  for (uint64_t t = 0; t < n_seqs; ++t) {
+    const uint64_t a = (off[t] + kRangeTile - 1) / kRangeTile * kRangeTile;  // first tile starting in t
+    const uint64_t b = std::min(m, (off[t + 1] + kRangeTile - 1) / kRangeTile * kRangeTile);
+    if (a < b) out->push_back({a, b});
+  }
+  return TWOPACO_OK;
+}
+
 }  // namespace
 }  // namespace twopaco
 
@@ -350,8 +378,13 @@ int twopaco_run_rounds(const uint8_t* d_bases, const uint64_t* d_offsets, uint64
     if (rounds > 1 && launch_partition(v, rounds, s) < 0) return TWOPACO_ECUDA;
     if (launch_class_map(v, s) < 0) return TWOPACO_ECUDA;
   }
+  std::vector<std::pair<uint64_t, uint64_t>> ranges;
+  if (o.per_string_launches && round_begin < round_end) {
+    rc = string_ranges(d_offsets, n_seqs, total_bases, s, &ranges);
+    if (rc) return rc;
+  }
   for (int r = round_begin; r < round_end; ++r)
-    if (launch_round(v, r, rounds, s) < 0) return TWOPACO_ECUDA;
+    if (launch_round(v, r, rounds, s, o.per_string_launches ? &ranges : nullptr) < 0) return TWOPACO_ECUDA;
   if (round_end == rounds && launch_emit(v, s, round_begin == rounds) < 0) return TWOPACO_ECUDA;
   return TWOPACO_OK;
 }
@@ -910,6 +943,7 @@ int twopaco_plan_create(const uint8_t* d_bases, const uint64_t* d_offsets, uint6
   if (!plan) return TWOPACO_EINVAL;
   *plan = nullptr;
   twopaco_options o = resolve(opt);
+  if (o.per_string_launches) return TWOPACO_EINVAL;  // they read the offsets back: no capture
   cudaStream_t cs = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_code(e);

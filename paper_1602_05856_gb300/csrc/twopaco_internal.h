@@ -3,6 +3,9 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 namespace twopaco {
@@ -69,8 +72,12 @@ struct RunView {
   int rounds;               // classes of Algorithm 3
   int partial;              // omit pass 2: C_final gathers every round's C_temp
   int count_round;          // the round whose probe counts the input's k-mer positions
+  uint64_t p_begin, p_end;  // positions the first- and second-pass loops visit: all
+                            // ([0, m)) or, launched per string, whole tiles of kRangeTile
   int lg_blocks;            // log2(filter_bits / 256)
   uint32_t qmask;           // partition_bins - 1
+  uint32_t part_sample;     // the partition pre-pass counts the k-mers whose H has bits
+                            // 16 .. 16 + log2(part_sample + 1) - 1 all zero (0: every k-mer)
   DevHeader* hdr;
   uint32_t* packed;         // 2-bit packed input, ceil(m/16) + pad words
   uint64_t packed_words;    // words written by the pack kernel (incl. pad)
@@ -120,6 +127,7 @@ constexpr uint64_t kPackPadWords = 16;  // zero words after the packed input (wi
 constexpr uint32_t kMaxSegments = 65536; // candidate-list segments (probe warps) at most
 constexpr uint64_t kRunChunkWords = 1024;  // boundary-bitmap words per compaction chunk
 constexpr int kMaxMapRounds = 64;          // rounds a class map can tell apart (6 class bits)
+constexpr uint64_t kRangeTile = 4096;      // positions: the unit of per-string launch ranges
 
 // Kernel launch helpers (twopaco_kernels.cu). Each returns the number of
 // kernels it launched, or -1 after a launch error.
@@ -131,7 +139,10 @@ int launch_pack(const RunView& v, cudaStream_t s);
 int launch_pack_chunk(const RunView& v, uint64_t w_begin, uint64_t w_end, bool first, cudaStream_t s);
 int launch_pack_finish(const RunView& v, cudaStream_t s);
 int launch_partition(const RunView& v, int rounds, cudaStream_t s);
-int launch_round(const RunView& v, int round, int rounds, cudaStream_t s);
+// ranges: null, or the [begin, end) position ranges (multiples of kRangeTile but the
+// last) of launches issued one per string for every loop of the round.
+int launch_round(const RunView& v, int round, int rounds, cudaStream_t s,
+                 const std::vector<std::pair<uint64_t, uint64_t>>* ranges = nullptr);
 // The class map of a run with rounds > 1 (v.cmap), from the class cut in
 // v.cuts; launches nothing without a class map.
 int launch_class_map(const RunView& v, cudaStream_t s);
@@ -156,7 +167,8 @@ inline uint64_t cand_record_bytes(int) { return 8; }
 
 // The k > 63 halves of launch_round and of the partition pre-pass (compiled
 // in twopaco_kernels_wide.cu).
-int launch_round_wide(const RunView& v, int round, int rounds, cudaStream_t s);
+int launch_round_wide(const RunView& v, int round, int rounds, cudaStream_t s,
+                      const std::vector<std::pair<uint64_t, uint64_t>>* ranges);
 int launch_partition_count_wide(const RunView& v, cudaStream_t s);
 int launch_class_map_wide(const RunView& v, cudaStream_t s);
 

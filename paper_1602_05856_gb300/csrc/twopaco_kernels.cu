@@ -100,6 +100,8 @@ constexpr bool kInsertPrefetch = false;
 constexpr bool kClassifyPrefetch = true;
 constexpr int kR = 8;  // partition pre-pass
 
+using Ranges = std::vector<std::pair<uint64_t, uint64_t>>;
+
 // ---------------------------------------------------------------------------
 // k-mer words
 // ---------------------------------------------------------------------------
@@ -1073,7 +1075,7 @@ __global__ void __launch_bounds__(kBlock) pass1_insert_kernel(RunView v, int rou
   __shared__ ulonglong2 stage[DESC ? kTile / 2 : 1];
   const uint64_t stride = (uint64_t)gridDim.x * kTile;
   const int t = threadIdx.x;
-  for (uint64_t base = (uint64_t)blockIdx.x * kTile; base < v.m; base += stride) {
+  for (uint64_t base = v.p_begin + (uint64_t)blockIdx.x * kTile; base < v.p_end; base += stride) {
     const uint64_t p0 = base + (uint64_t)t * kInsertR;
     if (p0 < v.m) {
       uint64_t prev = 0;
@@ -1132,8 +1134,8 @@ __global__ void __launch_bounds__(kBlock, 3) pass1_probe_kernel(RunView v, int r
   uint64_t* seg = v.cands + (uint64_t)warp_id * v.seg_cap;  // wide records
   uint32_t* seg32 = reinterpret_cast<uint32_t*>(v.cands) + (uint64_t)warp_id * v.seg_cap;
   uint64_t seg_used = 0;
-  for (uint64_t wbase = ((uint64_t)blockIdx.x * kBlock + (threadIdx.x & ~31u)) * kR; wbase < v.m;
-       wbase += stride) {
+  for (uint64_t wbase = v.p_begin + ((uint64_t)blockIdx.x * kBlock + (threadIdx.x & ~31u)) * kR;
+       wbase < v.p_end; wbase += stride) {
     const uint64_t p0 = wbase + (uint64_t)lane * kR;
     uint64_t word[kR], G[kR];
     uint32_t probe_bits = 0, sent_bits = 0, valid_bits = 0;
@@ -1234,7 +1236,7 @@ __global__ void __launch_bounds__(kBlock) pass1_probe_desc_kernel(RunView v, int
   // the descriptors of a step are loaded one step ahead (kProbePrefetch), so
   // that their stream overlaps the previous step's filter loads
   uint64_t dn[kRows];
-  const uint64_t wfirst = ((uint64_t)blockIdx.x * kBlock + (threadIdx.x & ~31u)) * kRows;
+  const uint64_t wfirst = v.p_begin + ((uint64_t)blockIdx.x * kBlock + (threadIdx.x & ~31u)) * kRows;
   if (kProbePrefetch) {
 #pragma unroll
     for (int q = 0; q < kRows; ++q) {
@@ -1242,7 +1244,7 @@ __global__ void __launch_bounds__(kBlock) pass1_probe_desc_kernel(RunView v, int
       dn[q] = p < v.m ? __ldcs(v.desc + p) : 0ull;
     }
   }
-  for (uint64_t wbase = wfirst; wbase < v.m; wbase += stride) {
+  for (uint64_t wbase = wfirst; wbase < v.p_end; wbase += stride) {
     uint64_t d[kRows], word[kRows];
 #pragma unroll
     for (int q = 0; q < kRows; ++q) {
@@ -1397,7 +1399,8 @@ __global__ void __launch_bounds__(kBlock) pass1_insert_cm_kernel(RunView v, int 
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint16_t* idx = idx_s[wid];
   const uint64_t stride = (uint64_t)gridDim.x * kBlock * 16;
-  for (uint64_t wbase = ((uint64_t)blockIdx.x * kBlock + (threadIdx.x & ~31u)) * 16; wbase < v.m; wbase += stride) {
+  for (uint64_t wbase = v.p_begin + ((uint64_t)blockIdx.x * kBlock + (threadIdx.x & ~31u)) * 16; wbase < v.p_end;
+       wbase += stride) {
     uint32_t valid;
     const uint32_t n = compact_window(v, wbase, round, idx, &valid);
     for (uint32_t j = lane; j < n; j += 32) {
@@ -1434,7 +1437,8 @@ __global__ void __launch_bounds__(kBlock) pass1_probe_cm_kernel(RunView v, int r
   if (lane < kCmWindow / 32) keep_w[lane] = 0;
   __syncwarp();
   const uint64_t stride = (uint64_t)gridDim.x * kBlock * 16;
-  for (uint64_t wbase = ((uint64_t)blockIdx.x * kBlock + (threadIdx.x & ~31u)) * 16; wbase < v.m; wbase += stride) {
+  for (uint64_t wbase = v.p_begin + ((uint64_t)blockIdx.x * kBlock + (threadIdx.x & ~31u)) * 16; wbase < v.p_end;
+       wbase += stride) {
     uint32_t valid;
     const uint32_t n = compact_window(v, wbase, round, idx, &valid);
     valid_n += valid;
@@ -1669,7 +1673,7 @@ __global__ void __launch_bounds__(kBlock) pass2_insert_kernel(RunView v) {
     return;
   }
   const uint64_t stride = (uint64_t)gridDim.x * kBlock;
-  for (uint64_t g = (uint64_t)blockIdx.x * kBlock + threadIdx.x; g < v.m; g += stride) {
+  for (uint64_t g = v.p_begin + (uint64_t)blockIdx.x * kBlock + threadIdx.x; g < v.p_end; g += stride) {
     if (!((__ldg(v.ctemp + (g >> 5)) >> (g & 31)) & 1u)) continue;
     OccT<KW> oc;
     if (!read_occurrence<KW>(v, g, &oc)) continue;
@@ -1716,7 +1720,7 @@ __global__ void __launch_bounds__(kBlock) pass2_classify_kernel(RunView v) {
     }
   } else {
     const uint64_t stride = (uint64_t)gridDim.x * kBlock;
-    for (uint64_t g = (uint64_t)blockIdx.x * kBlock + threadIdx.x; g < v.m; g += stride) {
+    for (uint64_t g = v.p_begin + (uint64_t)blockIdx.x * kBlock + threadIdx.x; g < v.p_end; g += stride) {
       if (!((__ldg(v.ctemp + (g >> 5)) >> (g & 31)) & 1u)) continue;
       OccT<KW> oc;
       if (!read_occurrence<KW>(v, g, &oc)) continue;
@@ -1727,13 +1731,17 @@ __global__ void __launch_bounds__(kBlock) pass2_classify_kernel(RunView v) {
 }
 
 // Partition counters (section "Multiple Rounds"): a Bloom pre-pass over all
-// k-mers; counter f(k-mer) grows when the k-mer was not yet in the filter.
+// k-mers; counter f(k-mer) grows when the k-mer was not yet in the filter. On
+// large inputs only a hash-chosen sample of the k-mers is counted (bits of H
+// that neither the bin nor the filter block uses): every bin's count then
+// shrinks by the same factor in expectation, which keeps the cut's balance
+// while the random filter accesses drop by that factor.
 template <int KW, int HB>
 __global__ void __launch_bounds__(kBlock) partition_count_kernel(RunView v) {
   const uint64_t stride = (uint64_t)gridDim.x * kBlock * kR;
   for (uint64_t p0 = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) * kR; p0 < v.m; p0 += stride) {
     walk<KW, kR>(v, p0, [&](int, uint64_t, bool valid, const auto& oc) {
-      if (!valid) return;
+      if (!valid || ((uint32_t)(oc.H >> 16) & v.part_sample)) return;
       const uint64_t G = second_hash(oc.H);
       const uint64_t m = item_bits<HB>(G, 17u, v.hashes);
       unsigned long long* w = filter_word(v, oc.H, G);
@@ -2245,7 +2253,7 @@ int launch_partition(const RunView& v, int rounds, cudaStream_t s) {
 #endif  // TWOPACO_WIDE_ONLY
 
 template <int KW, bool RD, int HB, int TS>
-int round_impl(const RunView& v, int round, cudaStream_t s) {
+int round_impl(const RunView& v, int round, cudaStream_t s, const Ranges* ranges) {
   // the pack kernel cleared the filter and the LC bitmap for round 0; the
   // partition pre-pass (rounds > 1) uses the filter before round 0
   if (RD && cudaMemsetAsync(v.filter, 0, v.filter_words64 * 8, s) != cudaSuccess) return -1;
@@ -2253,36 +2261,56 @@ int round_impl(const RunView& v, int round, cudaStream_t s) {
   constexpr bool kDescOk = HB <= 6;
   const bool cm = RD && v.cmap != nullptr;  // rounds visit only their class's positions
   const bool desc = !cm && kDescOk && v.use_desc;
+  // every loop over all positions at once, or once per string (ranges)
+  const Ranges whole{{v.p_begin, v.p_end}};
+  const Ranges& rs = ranges ? *ranges : whole;
+  auto part = [&](const std::pair<uint64_t, uint64_t>& r) {
+    RunView x = v;
+    x.p_begin = r.first;
+    x.p_end = r.second;
+    return x;
+  };
+  int launched = 0;
   {
     Timed t("pass1_insert", s);
-    const uint64_t threads = (v.m + kInsertR - 1) / kInsertR;
-    if (cm)
-      pass1_insert_cm_kernel<KW, HB><<<grid_for(pass1_insert_cm_kernel<KW, HB>, kBlock, threads), kBlock, 0, s>>>(
-          v, round);
-    else if (desc)
-      pass1_insert_kernel<KW, RD, HB, kDescOk><<<grid_for(pass1_insert_kernel<KW, RD, HB, kDescOk>, kBlock, threads),
-                                                 kBlock, 0, s>>>(v, round);
-    else
-      pass1_insert_kernel<KW, RD, HB, false><<<grid_for(pass1_insert_kernel<KW, RD, HB, false>, kBlock, threads),
-                                               kBlock, 0, s>>>(v, round);
+    for (const auto& r : rs) {
+      const RunView x = part(r);
+      const uint64_t threads = (r.second - r.first + kInsertR - 1) / kInsertR;
+      if (cm)
+        pass1_insert_cm_kernel<KW, HB><<<grid_for(pass1_insert_cm_kernel<KW, HB>, kBlock, threads), kBlock, 0,
+                                         s>>>(x, round);
+      else if (desc)
+        pass1_insert_kernel<KW, RD, HB, kDescOk><<<grid_for(pass1_insert_kernel<KW, RD, HB, kDescOk>, kBlock,
+                                                            threads),
+                                                   kBlock, 0, s>>>(x, round);
+      else
+        pass1_insert_kernel<KW, RD, HB, false><<<grid_for(pass1_insert_kernel<KW, RD, HB, false>, kBlock, threads),
+                                                 kBlock, 0, s>>>(x, round);
+      ++launched;
+    }
   }
-  const uint64_t threads = (v.m + kProbeR - 1) / kProbeR;
-  // one candidate-list segment per probe warp
   RunView pv = v;
-  unsigned grid = cm     ? grid_for(pass1_probe_cm_kernel<KW, HB>, kBlock, (v.m + 15) / 16)
-                  : desc ? grid_for(pass1_probe_desc_kernel<kDescOk ? HB : 1>, kBlock, threads)
-                         : grid_for(pass1_probe_kernel<KW, RD, HB>, kBlock, threads);
-  if (grid * (kBlock / 32) > kMaxSegments) grid = kMaxSegments / (kBlock / 32);
-  pv.n_segments = grid * (kBlock / 32);
-  // the list region holds cand_cap 8-byte records, or twice as many 32-bit ones
-  pv.seg_cap = (v.narrow ? 2 * v.cand_cap : v.cand_cap) / pv.n_segments;
   {
     Timed t("pass1_probe", s);
-    if (cm) pass1_probe_cm_kernel<KW, HB><<<grid, kBlock, 0, s>>>(pv, round);
-    else if (desc) pass1_probe_desc_kernel<kDescOk ? HB : 1><<<grid, kBlock, 0, s>>>(pv, round);
-    else pass1_probe_kernel<KW, RD, HB><<<grid, kBlock, 0, s>>>(pv, round);
+    for (const auto& r : rs) {
+      pv = part(r);
+      const uint64_t threads = (r.second - r.first + kProbeR - 1) / kProbeR;
+      // one candidate-list segment per probe warp
+      unsigned grid = cm     ? grid_for(pass1_probe_cm_kernel<KW, HB>, kBlock, (r.second - r.first + 15) / 16)
+                      : desc ? grid_for(pass1_probe_desc_kernel<kDescOk ? HB : 1>, kBlock, threads)
+                             : grid_for(pass1_probe_kernel<KW, RD, HB>, kBlock, threads);
+      if (grid * (kBlock / 32) > kMaxSegments) grid = kMaxSegments / (kBlock / 32);
+      pv.n_segments = grid * (kBlock / 32);
+      // the list region holds cand_cap 8-byte records, or twice as many 32-bit
+      // ones; launched per string there is no list (pass 2 walks C_temp)
+      pv.seg_cap = ranges ? 0 : (v.narrow ? 2 * v.cand_cap : v.cand_cap) / pv.n_segments;
+      if (cm) pass1_probe_cm_kernel<KW, HB><<<grid, kBlock, 0, s>>>(pv, round);
+      else if (desc) pass1_probe_desc_kernel<kDescOk ? HB : 1><<<grid, kBlock, 0, s>>>(pv, round);
+      else pass1_probe_kernel<KW, RD, HB><<<grid, kBlock, 0, s>>>(pv, round);
+      ++launched;
+    }
   }
-  if (v.partial) return done(2);  // the partially compacted graph: no second pass
+  if (v.partial) return done(launched);  // the partially compacted graph: no second pass
   {
     Timed t("table_setup", s);
     table_setup_kernel<<<grid_for(table_setup_kernel, kBlock, (1ull << v.lc_log2) / 32), kBlock, 0, s>>>(pv);
@@ -2291,34 +2319,47 @@ int round_impl(const RunView& v, int round, cudaStream_t s) {
     Timed t("table_clear", s);
     table_clear_kernel<TS><<<grid_for(table_clear_kernel<TS>, kBlock, v.table_max_slots), kBlock, 0, s>>>(pv);
   }
+  launched += 2;
   // pass 2: one resident wave; the warps share out the list's segment parts
   const unsigned g2 = grid_for(pass2_insert_kernel<KW, TS>, kBlock, ~0ull >> 1);
   const unsigned g3 = grid_for(pass2_classify_kernel<KW, TS>, kBlock, ~0ull >> 1);
   {
     Timed t("pass2_insert", s);
-    pass2_insert_kernel<KW, TS><<<g2, kBlock, 0, s>>>(pv);
+    for (const auto& r : rs) {
+      RunView x = part(r);
+      x.n_segments = pv.n_segments;
+      x.seg_cap = pv.seg_cap;
+      pass2_insert_kernel<KW, TS><<<g2, kBlock, 0, s>>>(x);
+      ++launched;
+    }
   }
   {
     Timed t("pass2_classify", s);
-    pass2_classify_kernel<KW, TS><<<g3, kBlock, 0, s>>>(pv);
+    for (const auto& r : rs) {
+      RunView x = part(r);
+      x.n_segments = pv.n_segments;
+      x.seg_cap = pv.seg_cap;
+      pass2_classify_kernel<KW, TS><<<g3, kBlock, 0, s>>>(x);
+      ++launched;
+    }
   }
-  return done(6);
+  return done(launched);
 }
 
 #ifndef TWOPACO_WIDE_ONLY
-int launch_round(const RunView& v, int round, int rounds, cudaStream_t s) {
+int launch_round(const RunView& v, int round, int rounds, cudaStream_t s, const Ranges* ranges) {
   if (v.m == 0) return 0;
-  if (v.k > 63) return launch_round_wide(v, round, rounds, s);
+  if (v.k > 63) return launch_round_wide(v, round, rounds, s, ranges);
   int rc = 0;
   with_hashes(v.hashes, [&](auto hb) {
     constexpr int HB = decltype(hb)::value;
     const int ts = table_slot_kind(v.k);
     if (ts == 0)
-      rc = rounds > 1 ? round_impl<1, true, HB, 0>(v, round, s) : round_impl<1, false, HB, 0>(v, round, s);
+      rc = rounds > 1 ? round_impl<1, true, HB, 0>(v, round, s, ranges) : round_impl<1, false, HB, 0>(v, round, s, ranges);
     else if (ts == 1)
-      rc = rounds > 1 ? round_impl<1, true, HB, 1>(v, round, s) : round_impl<1, false, HB, 1>(v, round, s);
+      rc = rounds > 1 ? round_impl<1, true, HB, 1>(v, round, s, ranges) : round_impl<1, false, HB, 1>(v, round, s, ranges);
     else
-      rc = rounds > 1 ? round_impl<2, true, HB, 2>(v, round, s) : round_impl<2, false, HB, 2>(v, round, s);
+      rc = rounds > 1 ? round_impl<2, true, HB, 2>(v, round, s, ranges) : round_impl<2, false, HB, 2>(v, round, s, ranges);
   });
   return rc;
 }
@@ -2372,8 +2413,8 @@ int launch_edges(const DevHeader* hdr_dev, const uint64_t* d_offsets, uint64_t n
 
 #else
 // k > 63: four-word k-mers, reference slots, the bits per item a run-time value.
-int launch_round_wide(const RunView& v, int round, int rounds, cudaStream_t s) {
-  return rounds > 1 ? round_impl<4, true, 0, 3>(v, round, s) : round_impl<4, false, 0, 3>(v, round, s);
+int launch_round_wide(const RunView& v, int round, int rounds, cudaStream_t s, const Ranges* ranges) {
+  return rounds > 1 ? round_impl<4, true, 0, 3>(v, round, s, ranges) : round_impl<4, false, 0, 3>(v, round, s, ranges);
 }
 
 int launch_partition_count_wide(const RunView& v, cudaStream_t s) {

@@ -86,10 +86,14 @@ def test_roofline_takes_the_dominant_modelled_kernel_per_launch():
     prof = {"pass1_insert": {"launches": 4, "ms": 8.0}, "table_setup": {"launches": 4, "ms": 100.0},
             "pass1_probe": {"launches": 4, "ms": 4.0}}
     peaks = {"or": 250e9, "read": 400e9, "buffer_bytes": 1 << 30}
-    r = bench.roofline(prof, st, 1024, 3, 1 << 20, peaks, 6000.0, {}, "wl", False)
+    r = bench.roofline(prof, st, 1024, 3, 1 << 20, peaks, 6000.0, {}, "wl", False, 1)
     assert r["kernel"] == "pass1_insert" and r["bound"] == "hbm_random"
     # 1e9 positions over 4 launches of 2 ms each: 2.5e8 / 2 ms = 125 G/s against 250 G/s
     assert abs(r["achieved"] - 125.0) < 1e-6 and abs(r["frac"] - 0.5) < 1e-9
+    # the same per launch when the profile sums two steps (8 launches, 16 ms)
+    prof2 = {k: {"launches": 2 * v["launches"], "ms": 2 * v["ms"]} for k, v in prof.items()}
+    r2 = bench.roofline(prof2, st, 1024, 3, 1 << 20, peaks, 6000.0, {}, "wl", False, 2)
+    assert abs(r2["achieved"] - 125.0) < 1e-6
 
 
 def test_traffic_lookup_is_keyed_by_workload_kernel_and_code(tmp_path, monkeypatch):

@@ -385,3 +385,37 @@ def test_bounded_wait_gives_up_and_the_context_survives():
     got, _ = T().twopaco_build_ex(["TGGCACGTC", "TGGCACTTC"], 2, 1 << 12, 1,
                                   T().Options(both_strands=False))
     _eq(got, [[0, 4, 7], [0, 4, 7]])
+
+
+# --- one launch per string (the per-genome baseline of the batched launch) ---------
+
+@pytest.mark.parametrize("k,rounds,partial", [(25, 1, False), (31, 3, False), (63, 1, False),
+                                              (25, 2, True), (100, 2, False)])
+def test_per_string_launches_give_the_same_build(k, rounds, partial):
+    """Every loop launched once per genome (tiles owned by the genome holding their first
+    position, pass 2 over C_temp): the same junctions, C_temp and counters as the joint
+    launch -- and the oracle's junctions."""
+    seqs = _named("batched_set", 0.02)
+    bases, off = G.concat(seqs)
+    base = dict(hashes=4, partition_bins=256, partial=partial)
+    joint = T().DeviceBuild(bases, off, k, 1 << 22, rounds, T().Options(**base))
+    joint.run()
+    per = T().DeviceBuild(bases, off, k, 1 << 22, rounds, T().Options(per_string_launches=True, **base))
+    n0 = T().twopaco_kernel_launches()
+    per.run()
+    launched = T().twopaco_kernel_launches() - n0
+    a, b = joint.result(), per.result()
+    _eq(b, a)
+    if not partial:
+        _eq(b, _oracle_named("batched_set", 0.02, k))
+    sa, sb = joint.stats(), per.stats()
+    if rounds == 1:  # (more rounds: two separate class cuts may differ)
+        assert sa["pass1_marks"] == sb["pass1_marks"] and sa["positions"] == sb["positions"]
+        m = int(off[-1])
+        ca = _bits_to_marks(joint.state(T().STATE_CANDIDATES, (m + 31) // 32), m)
+        cb = _bits_to_marks(per.state(T().STATE_CANDIDATES, (m + 31) // 32), m)
+        assert np.array_equal(ca, cb)
+    assert launched > 62 * (2 if partial else 4) * rounds
+    with pytest.raises(T().TwopacoError) as e:
+        per.capture()
+    assert e.value.code == T().EINVAL
