@@ -35,7 +35,8 @@
  *     [256, 2^40]; rounds >= 1; n_seqs < 2^32; total_bases < 2^48;
  *     options->hashes in [1, 8]; options->partition_bins a power of two
  *     >= rounds (and >= 2 when rounds > 1); options->both_strands and
- *     options->split_at_n, options->partial and options->per_string_launches 0 or 1; options->wide_layout 0, 1 or 2;
+ *     options->split_at_n, options->partial and options->per_string_launches 0 or 1;
+ *     options->bucket_inserts 0, 1 or 2; options->wide_layout 0, 1 or 2;
  *     options->run_capacity < 2^32. Anything else is TWOPACO_EINVAL.
  *   - Calls on different workspaces may run concurrently from different host
  *     threads; calls that share a workspace must be serialised by the caller.
@@ -105,6 +106,21 @@ typedef struct twopaco_options {
                               the batched launch). The call reads the string offsets
                               back and synchronises the stream; twopaco_plan_create
                               refuses it. 0 (default): one launch per loop. */
+  int bucket_inserts;      /* first-pass inserts through region buckets: each OR into the
+                              filter becomes an 8-byte record in the bucket of its filter
+                              region (32 MiB, or a quarter of a smaller filter), and the
+                              records are then applied region by region while each region
+                              sits in L2 -- a filter beyond L2 otherwise takes its random
+                              ORs at DRAM's random-access rate. The workspace holds the
+                              buckets (records for a round's positions and a quarter more,
+                              at most 2^31); the positions go through in chunks that fill
+                              them to about 80%, and a full bucket takes the OR directly.
+                              Same results. 0 (default): for filters of more than 64 MiB
+                              whose chunks put at least 16 ORs on every 32-byte filter
+                              sector on average (sparser, the regions' cold misses cost
+                              more than direct ORs); 1: for any filter; 2: never. Needs
+                              hashes <= 6 and a filter of at most 2^38 bits (else the ORs
+                              are direct). */
 } twopaco_options;
 
 /* Counters of one run, in the spirit of Table 4 (marks after each pass). */

@@ -54,6 +54,7 @@ int validate(uint64_t n_seqs, int k, uint64_t filter_bits, int rounds, const two
   if (o.run_capacity >= (1ull << 32)) return TWOPACO_EINVAL;  // piece ranks are 32-bit
   if (o.partial != 0 && o.partial != 1) return TWOPACO_EINVAL;
   if (o.per_string_launches != 0 && o.per_string_launches != 1) return TWOPACO_EINVAL;
+  if (o.bucket_inserts < 0 || o.bucket_inserts > 2) return TWOPACO_EINVAL;
   return TWOPACO_OK;
 }
 
@@ -63,8 +64,11 @@ int validate_size(uint64_t total_bases) {
 
 struct Layout {
   uint64_t header, packed, filter, ctemp, cfinal, tile_count, tile_prefix, bins, cuts, table;
-  uint64_t cands, lc, segs, desc, cslot, nmask, bounds, chunks, runs, rank, cmap;
+  uint64_t cands, lc, segs, desc, cslot, nmask, bounds, chunks, runs, rank, cmap, bfill, brecs;
   int narrow, use_desc, use_slot, split, use_cmap;
+  uint32_t n_regions, n_sub;
+  int lg_region_words;
+  uint64_t bucket_cap, bucket_chunk;
   uint64_t n_chunks, run_cap;
   uint64_t total;
   uint64_t packed_words, bitmap_words, n_tiles, table_slots, cand_cap;
@@ -147,6 +151,38 @@ Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int roun
   L.use_desc = (L.narrow && o.hashes <= 6 && filter_bits <= (1ull << 37) && !L.use_cmap) ? 1 : 0;
   L.desc = at;
   if (L.use_desc) at += align_up((m + 16) * 8);
+  // region buckets for the first-pass inserts: filters beyond L2 (over 64 MiB),
+  // or any filter when asked; regions of up to 2^22 words (32 MiB), at most
+  // kMaxRegions of them; records carry up to 6 bits per item
+  const uint64_t fwords = filter_bits / 64;
+  const bool want_bkt = o.bucket_inserts == 1 || (o.bucket_inserts == 0 && filter_bits / 8 > (64ull << 20));
+  uint64_t region_words = std::min<uint64_t>(1ull << kRegionWordsLog2, fwords / 4);
+  L.n_regions = 0;
+  // automatically only where it measured faster: when a chunk's records put at
+  // least 16 ORs on every 32-byte filter sector on average (on a 24 Gbp input
+  // with a 2^36-bit filter, about 7 per sector, the cold misses of every region
+  // cost more than the direct ORs; on 310 Mbp with 2^30 bits, 77 per sector, the
+  // buckets win)
+  const uint64_t per_chunk = std::min<uint64_t>(per_round, 1ull << 31) * 4 / 5;
+  const bool dense = per_chunk >= 16 * (filter_bits / 256);
+  if (want_bkt && (o.bucket_inserts == 1 || dense) && o.hashes <= 6 && m > 0 && region_words >= 1 &&
+      fwords / region_words <= kMaxRegions) {
+    L.n_regions = (uint32_t)(fwords / region_words);
+    L.n_sub = 1;
+    while (L.n_regions * L.n_sub < kMinBuckets) L.n_sub *= 2;
+    L.lg_region_words = log2_exact(region_words);
+    // records for a round's positions and a quarter more (at most 2^31 of them),
+    // shared out evenly over the buckets; a chunk of positions fills about 80%
+    const uint64_t buckets = (uint64_t)L.n_regions * L.n_sub;
+    uint64_t recs = std::min<uint64_t>(per_round + per_round / 4 + 4096ull * buckets, 1ull << 31);
+    L.bucket_cap = recs / buckets;
+    const uint64_t chunk = L.bucket_cap * buckets / 5 * 4 * (uint64_t)rounds;
+    L.bucket_chunk = std::max<uint64_t>(kRangeTile, chunk / kRangeTile * kRangeTile);
+  }
+  L.bfill = at;
+  if (L.n_regions) at += align_up(((uint64_t)L.n_regions * L.n_sub + 1) * 128);
+  L.brecs = at;
+  if (L.n_regions) at += align_up(L.bucket_cap * L.n_regions * L.n_sub * 8);
   // N splitting: N mask and boundary bitmap (one bit per base), per-chunk
   // boundary counts, the sorted boundaries and their ranks
   L.split = o.split_at_n;
@@ -224,6 +260,15 @@ RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_
   v.bins = rounds > 1 ? reinterpret_cast<uint32_t*>(base + L.bins) : nullptr;
   v.cuts = reinterpret_cast<uint32_t*>(base + L.cuts);
   v.cmap = L.use_cmap ? reinterpret_cast<uint8_t*>(base + L.cmap) : nullptr;
+  v.n_regions = L.n_regions;
+  if (L.n_regions) {
+    v.lg_region_words = L.lg_region_words;
+    v.n_sub = L.n_sub;
+    v.bucket_fill = reinterpret_cast<uint32_t*>(base + L.bfill);
+    v.bucket_recs = reinterpret_cast<uint64_t*>(base + L.brecs);
+    v.bucket_cap = L.bucket_cap;
+    v.bucket_chunk = L.bucket_chunk;
+  }
   v.tile_count = reinterpret_cast<uint32_t*>(base + L.tile_count);
   v.tile_prefix = reinterpret_cast<uint64_t*>(base + L.tile_prefix);
   v.n_tiles = L.n_tiles;
@@ -284,6 +329,7 @@ void twopaco_default_options(twopaco_options* opt) {
   opt->wide_layout = 0;
   opt->partial = 0;
   opt->per_string_launches = 0;
+  opt->bucket_inserts = 0;
 }
 
 const char* twopaco_strerror(int code) {

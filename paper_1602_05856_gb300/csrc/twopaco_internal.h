@@ -102,6 +102,15 @@ struct RunView {
   uint32_t* run_rank;
   uint64_t run_cap;
   uint64_t* desc;           // per-position probe descriptors (use_desc), m + 16 entries
+  // region-bucketed first-pass inserts (n_regions > 0): records of the ORs into
+  // each filter region of 2^lg_region_words 64-bit words, applied region by region
+  uint32_t n_regions;
+  uint32_t n_sub;           // buckets per region (a power of two)
+  int lg_region_words;
+  uint32_t* bucket_fill;    // records appended per bucket, one counter per 128 bytes, then the apply ticket
+  uint64_t* bucket_recs;    // n_regions * n_sub buckets of bucket_cap records
+  uint64_t bucket_cap;
+  uint64_t bucket_chunk;    // positions per scatter-and-apply chunk (a multiple of kRangeTile)
   int use_desc;             // the insert leaves descriptors and the probe reads them
   uint64_t cand_cap;        // records the list can hold
   uint32_t* seg_count;      // candidates per list segment (one segment per probe warp)
@@ -128,6 +137,10 @@ constexpr uint32_t kMaxSegments = 65536; // candidate-list segments (probe warps
 constexpr uint64_t kRunChunkWords = 1024;  // boundary-bitmap words per compaction chunk
 constexpr int kMaxMapRounds = 64;          // rounds a class map can tell apart (6 class bits)
 constexpr uint64_t kRangeTile = 4096;      // positions: the unit of per-string launch ranges
+constexpr uint32_t kMaxRegions = 1024;     // filter regions of bucketed inserts, at most
+constexpr uint32_t kMinBuckets = 256;      // buckets of bucketed inserts, at least (sub-buckets per region)
+constexpr uint32_t kMaxBuckets = 1024;
+constexpr int kRegionWordsLog2 = 22;       // 32 MiB regions (words of 8 bytes)
 
 // Kernel launch helpers (twopaco_kernels.cu). Each returns the number of
 // kernels it launched, or -1 after a launch error.

@@ -551,6 +551,97 @@ __device__ __forceinline__ uint32_t present_items(uint64_t G, uint64_t w, int hb
   return pres & 0x1FFFFu;
 }
 
+// Index of a k-mer's filter word (the word filter_word points to).
+__device__ __forceinline__ uint64_t filter_index(const RunView& v, uint64_t H, uint64_t G) {
+  const uint32_t block = v.lg_blocks ? (uint32_t)(H >> (64 - v.lg_blocks)) : 0u;
+  return (uint64_t)block * 4u + (uint32_t)(G >> 62);
+}
+
+// ---------------------------------------------------------------------------
+// Region-bucketed first-pass inserts. A filter far larger than L2 takes its
+// random ORs at DRAM's random-access rate, about a tenth of the rate L2 takes
+// them at. So for such a filter the insert loop turns every OR into an 8-byte
+// record in the bucket of its filter region (32 MiB, which L2 holds), and the
+// apply kernel then performs the ORs bucket by bucket, while the region stays
+// in L2. A record: bits 0-21 the word within its region, 22-51 the bits 32-61
+// of G (the bit bases of up to 6 bits per item), 52-56 and 57-61 the items (two
+// for a palindrome's orientations). A full bucket takes the OR directly.
+// ---------------------------------------------------------------------------
+
+constexpr uint32_t kApplyPiece = 4096;  // records per apply work item
+constexpr uint32_t kFillStride = 32;    // bucket counters 128 bytes apart (one L2 line each)
+
+// A region's records go to one of its sub-buckets (chosen by the warp, so
+// that every region has at least 256 counters between them): the bucket
+// index is region * n_sub + sub, region-major, so that the apply's order
+// still takes one region after the other.
+__device__ __forceinline__ void stage_or(const RunView& v, uint64_t word, uint64_t G, uint32_t j1, uint32_t j2,
+                                         uint64_t mask) {
+  const uint32_t warp = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const uint32_t b = (uint32_t)(word >> v.lg_region_words) * v.n_sub + (warp & (v.n_sub - 1u));
+  const unsigned grp = __match_any_sync(__activemask(), b);
+  const int lane = threadIdx.x & 31, leader = __ffs(grp) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(v.bucket_fill + (uint64_t)b * kFillStride, (uint32_t)__popc(grp));
+  base = __shfl_sync(grp, base, leader);
+  const uint64_t slot = (uint64_t)base + __popc(grp & ((1u << lane) - 1u));
+  if (slot < v.bucket_cap) {
+    const uint64_t local = word & ((1ull << v.lg_region_words) - 1ull);
+    v.bucket_recs[(uint64_t)b * v.bucket_cap + slot] =
+        local | (((G >> 32) & 0x3FFFFFFFull) << 22) | ((uint64_t)j1 << 52) | ((uint64_t)j2 << 57);
+  } else {
+    atomicOr(v.filter + word, (unsigned long long)mask);
+  }
+}
+
+// The ORs of the staged records, in work items of kApplyPiece records taken in
+// bucket order from a ticket (so that the blocks in flight work on one or two
+// regions at a time). The counter after the last bucket's is the ticket.
+template <int HB>
+__global__ void __launch_bounds__(kBlock) filter_apply_kernel(RunView v) {
+  __shared__ uint32_t first_s[kMaxBuckets + 1];  // first work item of every bucket
+  __shared__ uint32_t item_s;
+  const uint32_t R = v.n_regions * v.n_sub;  // buckets
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (uint32_t b = 0; b < R; ++b) {
+      first_s[b] = acc;
+      const uint64_t n = min((uint64_t)__ldcg(v.bucket_fill + (uint64_t)b * kFillStride), v.bucket_cap);
+      acc += (uint32_t)((n + kApplyPiece - 1) / kApplyPiece);
+    }
+    first_s[R] = acc;
+  }
+  __syncthreads();
+  const uint32_t total = first_s[R];
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(v.bucket_fill + (uint64_t)R * kFillStride, 1u);
+    __syncthreads();
+    const uint32_t item = item_s;
+    __syncthreads();
+    if (item >= total) break;
+    uint32_t lo = 0, hi = R;  // the bucket b with first_s[b] <= item < first_s[b + 1]
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (first_s[mid] <= item) lo = mid; else hi = mid;
+    }
+    const uint32_t b = lo;
+    const uint64_t n = min((uint64_t)__ldcg(v.bucket_fill + (uint64_t)b * kFillStride), v.bucket_cap);
+    const uint64_t i0 = (uint64_t)(item - first_s[b]) * kApplyPiece;
+    const uint64_t i1 = min(i0 + kApplyPiece, n);
+    const uint64_t* recs = v.bucket_recs + (uint64_t)b * v.bucket_cap;
+    const uint64_t region = (uint64_t)(b / v.n_sub) << v.lg_region_words;
+    for (uint64_t i = i0 + threadIdx.x; i < i1; i += kBlock) {
+      const uint64_t r = __ldcs(recs + i);
+      const uint64_t G = ((r >> 22) & 0x3FFFFFFFull) << 32;  // the bits bit_base reads for u < 6
+      const ItemPattern pat = item_pattern<HB>(G, v.hashes);
+      const uint32_t j1 = (uint32_t)(r >> 52) & 31u, j2 = (uint32_t)(r >> 57) & 31u;
+      uint64_t m = item_bits(pat, j1);
+      if (j2 != j1) m |= item_bits(pat, j2);
+      atomicOr(v.filter + (region | (r & ((1ull << 22) - 1ull))), (unsigned long long)m);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Pass-2 table: open addressing with linear probing, keyed by the normalized
 // k-mer; the value is the 9-bit pass-2 mask. Empty keys are all ones, which
@@ -1068,7 +1159,7 @@ __device__ __forceinline__ uint64_t make_desc(const RunView& v, uint64_t H, uint
 // descriptors are staged in shared memory (16-byte pairs, columns swizzled by
 // the owning thread so that neither side conflicts) and written out in
 // order, whole sectors at a time.
-template <int KW, bool ROUNDS, int HB, bool DESC>
+template <int KW, bool ROUNDS, int HB, bool DESC, bool BKT = false>
 __global__ void __launch_bounds__(kBlock) pass1_insert_kernel(RunView v, int round) {
   constexpr int kTile = kBlock * kInsertR;  // positions per block per pass
   constexpr int kPairs = kInsertR / 2;      // 16-byte descriptor pairs per thread
@@ -1090,7 +1181,8 @@ __global__ void __launch_bounds__(kBlock) pass1_insert_kernel(RunView v, int rou
             const uint32_t j1 = __ffs(oc.items) - 1, j2 = 31 - __clz(oc.items);
             uint64_t m = item_bits(pat, j1);
             if (j2 != j1) m |= item_bits(pat, j2);  // a palindrome's two orientations
-            atomicOr(filter_word(v, oc.H, G), (unsigned long long)m);
+            if (BKT) stage_or(v, filter_index(v, oc.H, G), G, j1, j2, m);
+            else atomicOr(filter_word(v, oc.H, G), (unsigned long long)m);
             if (DESC) d = make_desc(v, oc.H, G, oc.sentinel);
           }
         }
@@ -1393,7 +1485,7 @@ __device__ __forceinline__ uint32_t compact_window(const RunView& v, uint64_t wb
 }
 
 // Algorithm 1, insert loop, first pass, over this round's class only.
-template <int KW, int HB>
+template <int KW, int HB, bool BKT = false>
 __global__ void __launch_bounds__(kBlock) pass1_insert_cm_kernel(RunView v, int round) {
   __shared__ uint16_t idx_s[kBlock / 32][kCmWindow];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1412,7 +1504,8 @@ __global__ void __launch_bounds__(kBlock) pass1_insert_cm_kernel(RunView v, int 
       const uint32_t j1 = __ffs(oc.items) - 1, j2 = 31 - __clz(oc.items);
       uint64_t m = item_bits(pat, j1);
       if (j2 != j1) m |= item_bits(pat, j2);  // a palindrome's two orientations
-      atomicOr(filter_word(v, oc.H, G), (unsigned long long)m);
+      if (BKT) stage_or(v, filter_index(v, oc.H, G), G, j1, j2, m);
+      else atomicOr(filter_word(v, oc.H, G), (unsigned long long)m);
     }
     __syncwarp();
   }
@@ -2271,22 +2364,48 @@ int round_impl(const RunView& v, int round, cudaStream_t s, const Ranges* ranges
     return x;
   };
   int launched = 0;
+  // filters beyond L2: the inserts go through region buckets, chunk by chunk
+  constexpr bool kBktOk = HB <= 6;  // a record carries the bit bases of up to 6 bits per item
+  const bool bkt = kBktOk && v.n_regions > 0;
   {
-    Timed t("pass1_insert", s);
     for (const auto& r : rs) {
-      const RunView x = part(r);
-      const uint64_t threads = (r.second - r.first + kInsertR - 1) / kInsertR;
-      if (cm)
-        pass1_insert_cm_kernel<KW, HB><<<grid_for(pass1_insert_cm_kernel<KW, HB>, kBlock, threads), kBlock, 0,
-                                         s>>>(x, round);
-      else if (desc)
-        pass1_insert_kernel<KW, RD, HB, kDescOk><<<grid_for(pass1_insert_kernel<KW, RD, HB, kDescOk>, kBlock,
-                                                            threads),
+      const uint64_t step = bkt ? v.bucket_chunk : r.second - r.first;
+      for (uint64_t c0 = r.first; c0 < r.second; c0 += step) {
+        const RunView x = part({c0, std::min(r.second, c0 + step)});
+        const uint64_t threads = (x.p_end - x.p_begin + kInsertR - 1) / kInsertR;
+        {
+        Timed t("pass1_insert", s);
+        if (bkt && cudaMemsetAsync(v.bucket_fill, 0, ((uint64_t)v.n_regions * v.n_sub + 1) * kFillStride * 4,
+                                   s) != cudaSuccess)
+          return -1;
+        if (cm && bkt)
+          pass1_insert_cm_kernel<KW, HB, kBktOk><<<grid_for(pass1_insert_cm_kernel<KW, HB, kBktOk>, kBlock, threads),
                                                    kBlock, 0, s>>>(x, round);
-      else
-        pass1_insert_kernel<KW, RD, HB, false><<<grid_for(pass1_insert_kernel<KW, RD, HB, false>, kBlock, threads),
-                                                 kBlock, 0, s>>>(x, round);
-      ++launched;
+        else if (cm)
+          pass1_insert_cm_kernel<KW, HB><<<grid_for(pass1_insert_cm_kernel<KW, HB>, kBlock, threads), kBlock, 0,
+                                           s>>>(x, round);
+        else if (desc && bkt)
+          pass1_insert_kernel<KW, RD, HB, kDescOk, kBktOk>
+              <<<grid_for(pass1_insert_kernel<KW, RD, HB, kDescOk, kBktOk>, kBlock, threads), kBlock, 0, s>>>(x, round);
+        else if (desc)
+          pass1_insert_kernel<KW, RD, HB, kDescOk><<<grid_for(pass1_insert_kernel<KW, RD, HB, kDescOk>, kBlock,
+                                                              threads),
+                                                     kBlock, 0, s>>>(x, round);
+        else if (bkt)
+          pass1_insert_kernel<KW, RD, HB, false, kBktOk>
+              <<<grid_for(pass1_insert_kernel<KW, RD, HB, false, kBktOk>, kBlock, threads), kBlock, 0, s>>>(x, round);
+        else
+          pass1_insert_kernel<KW, RD, HB, false><<<grid_for(pass1_insert_kernel<KW, RD, HB, false>, kBlock, threads),
+                                                   kBlock, 0, s>>>(x, round);
+        }
+        ++launched;
+        if (bkt) {
+          Timed ta("filter_apply", s);
+          filter_apply_kernel<kBktOk ? HB : 1><<<grid_for(filter_apply_kernel<kBktOk ? HB : 1>, kBlock, ~0ull >> 1),
+                                                 kBlock, 0, s>>>(v);
+          ++launched;
+        }
+      }
     }
   }
   RunView pv = v;

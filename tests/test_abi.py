@@ -40,7 +40,8 @@ def test_host_side_argument_checks():
            dict(options=T.Options(partition_bins=1000)), dict(rounds=8, options=T.Options(partition_bins=4)),
            dict(options=T.Options(wide_layout=3)), dict(options=T.Options(wide_layout=-1)),
            dict(options=T.Options(split_at_n=True, run_capacity=1 << 32)),
-           dict(filter_bits=1 << 41), dict(n_seqs=1 << 32), dict(rounds=2, options=T.Options(partition_bins=1))]
+           dict(filter_bits=1 << 41), dict(n_seqs=1 << 32), dict(rounds=2, options=T.Options(partition_bins=1)),
+           dict(options=T.Options(bucket_inserts=3)), dict(options=T.Options(bucket_inserts=-1))]
     for b in bad:
         args = dict(total_bases=1000, n_seqs=2, k=25, filter_bits=1 << 20, rounds=1)
         args.update(b)
@@ -177,3 +178,14 @@ def test_partial_option_checks_and_smaller_workspace():
     part = T.twopaco_workspace_size(m, 4, 25, 1 << 24, 1, T.Options(partial=True))
     table = 8 * (1 << 25)  # next power of two of 2m one-word slots
     assert full - part >= table
+
+
+def test_bucketed_inserts_follow_the_or_density():
+    """Automatic region buckets only where a chunk puts >= 16 ORs on each filter sector."""
+    from paper_1602_05856_gb300 import build, twopaco as T
+    build.build()
+    ws = lambda m, bits, b, r=1: T.twopaco_workspace_size(m, 8, 25, bits, r, T.Options(bucket_inserts=b))
+    assert ws(310_000_000, 1 << 30, 0) > ws(310_000_000, 1 << 30, 2)      # 77 ORs per sector
+    assert ws(24_000_000_000, 1 << 36, 0, 4) == ws(24_000_000_000, 1 << 36, 2, 4)  # about 7
+    assert ws(35_000_000, 1 << 28, 0) == ws(35_000_000, 1 << 28, 2)       # within L2
+    assert ws(35_000_000, 1 << 28, 1) > ws(35_000_000, 1 << 28, 2)        # forced

@@ -419,3 +419,57 @@ def test_per_string_launches_give_the_same_build(k, rounds, partial):
     with pytest.raises(T().TwopacoError) as e:
         per.capture()
     assert e.value.code == T().EINVAL
+
+
+# --- first-pass inserts through region buckets ------------------------------------
+
+@pytest.mark.parametrize("k,bits,h,rounds,extra", [
+    (25, 1 << 20, 4, 1, {}), (31, 1 << 22, 3, 3, {}), (63, 1 << 20, 6, 1, {}), (100, 1 << 20, 4, 2, {}),
+    (25, 1 << 20, 4, 1, {"per_string_launches": True}), (25, 1 << 20, 4, 2, {"partial": True}),
+    (21, 1 << 20, 4, 1, {"wide_layout": 1}),
+])
+def test_bucketed_inserts_give_the_same_filter(k, bits, h, rounds, extra):
+    """Every OR staged in the bucket of its filter region and applied region by region
+    (forced on small filters): C_temp bit-exact with the oracle's first pass (one round)
+    and with the direct inserts, and the oracle's junctions. A homopolymer string sends
+    all its records to one bucket, which overflows into direct ORs."""
+    seqs = [s for s in _named("plain_single", 0.05)] + [np.frombuffer(b"A" * 60000, np.uint8)]
+    bases, off = G.concat(seqs)
+    m = int(off[-1])
+    base = dict(hashes=h, partition_bins=256, **extra)
+    a = T().DeviceBuild(bases, off, k, bits, rounds, T().Options(bucket_inserts=2, **base))
+    b = T().DeviceBuild(bases, off, k, bits, rounds, T().Options(bucket_inserts=1, **base))
+    assert b.ws_bytes > a.ws_bytes  # the buckets
+    a.run()
+    b.run()
+    _eq(b.result(), a.result())
+    if not extra.get("partial"):
+        _eq(b.result(), O.junctions((bases, off), k))
+    if rounds == 1:
+        ca = _bits_to_marks(a.state(T().STATE_CANDIDATES, (m + 31) // 32), m)
+        cb = _bits_to_marks(b.state(T().STATE_CANDIDATES, (m + 31) // 32), m)
+        assert np.array_equal(ca, cb)
+        if not extra.get("wide_layout"):
+            marks, _, _, kept = O.pass1_marks((bases, off), k, bits, h)
+            assert np.array_equal(cb, marks) and b.stats()["pass1_marks"] == kept
+
+
+def test_bucketed_inserts_on_a_filter_beyond_l2():
+    """A 2^30-bit (128 MiB) filter: with buckets (4 regions of 32 MiB) the same C_temp and
+    junctions. Left automatic on this small input it stays direct (too few ORs per filter
+    sector); the full-size 62-genome set takes the buckets automatically (its parity test
+    is in test_gpu_timed_configs)."""
+    seqs = _named("batched_set", 0.02)
+    bases, off = G.concat(seqs)
+    auto = T().DeviceBuild(bases, off, 25, 1 << 30, 1, T().Options(hashes=4))
+    direct = T().DeviceBuild(bases, off, 25, 1 << 30, 1, T().Options(hashes=4, bucket_inserts=2))
+    forced = T().DeviceBuild(bases, off, 25, 1 << 30, 1, T().Options(hashes=4, bucket_inserts=1))
+    assert auto.ws_bytes == direct.ws_bytes < forced.ws_bytes
+    full = sum(G.named_set("batched_set", 1.0)[t].size for t in range(62))
+    assert T().twopaco_workspace_size(full, 62, 25, 1 << 30, 1) > \
+        T().twopaco_workspace_size(full, 62, 25, 1 << 30, 1, T().Options(bucket_inserts=2))
+    forced.run()
+    _eq(forced.result(), _oracle_named("batched_set", 0.02, 25))
+    m = int(off[-1])
+    marks, _, _, kept = O.pass1_marks((bases, off), 25, 1 << 30, 4)
+    assert np.array_equal(_bits_to_marks(forced.state(T().STATE_CANDIDATES, (m + 31) // 32), m), marks)
