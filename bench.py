@@ -94,6 +94,8 @@ def parse():
     p.add_argument("--genome-len", type=int, default=MAMMAL_GENOME_LEN,
                    help="mammal_set: bases per genome (a smaller slice of the same recipe)")
     p.add_argument("--rounds", type=int, default=0, help="override the workload's rounds")
+    p.add_argument("--filter-bits", type=int, default=0,
+                   help="override the workload's filter size (e.g. a slice at the same bits per base)")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--bacterial", type=int, default=1,
@@ -662,6 +664,8 @@ def run_ours(args, world, rank, local):
     if world > 1:
         import torch.distributed as dist
     name = args.workload
+    if args.filter_bits:
+        WORKLOADS[name] = dict(WORKLOADS[name], filter_bits=int(args.filter_bits))
     head = device_leg(T, build, name, args.genome_len, args.rounds, args, world, rank, local, dist)
 
     extra = {}
