@@ -102,8 +102,8 @@ def parse():
                    help="1: add the bacterial-size set's own line (when the headline is another workload)")
     p.add_argument("--batched", type=int, default=1,
                    help="1: add the batched leg (62 genomes in one tuned build vs one build per genome)")
-    p.add_argument("--serve-requests", type=int, default=100,
-                   help="requests of the served leg (Poisson, 20/s); 0 skips it")
+    p.add_argument("--serve-requests", type=int, default=600,
+                   help="requests of the served leg (Poisson, 20/s: 600 is 30 s); 0 skips it")
     return p.parse_args()
 
 
@@ -623,28 +623,48 @@ def batched_leg(T, genomes, dev):
 
 
 def served_leg(args, local):
-    from paper_1602_05856_gb300 import genomes, serve
-    seqs = genomes.named_set("bacterial_set")
-    reqs = serve.served_requests(seqs, args.serve_requests, 20.0, seed=1606)
+    """The served configuration: a Poisson stream (20/s) of requests of 2-50 genome windows
+    of 0.1-50 Mbp (log-uniform, from the bacterial recipe at 10x length), k 25/31, admitted
+    by device memory under 120 GB into 4 slots whose work overlaps on the GPU; against every
+    request run alone on an idle GPU."""
+    from paper_1602_05856_gb300 import serve
+    pool = serve.served_pool()
+
+    def trace():
+        return serve.served_requests(pool, args.serve_requests, serve.SERVED_RATE, seed=1606,
+                                     genomes_range=serve.SERVED_GENOMES, mbp_range=serve.SERVED_MBP)
+
+    reqs = trace()
     slots = [serve.GpuSlot(device=f"cuda:{local}") for _ in range(4)]
-    for sl in slots:  # resident buffers sized for the trace, as a server keeps them
+    for sl in slots:  # staging grown and the largest request run once: later requests hit the caches
         sl.reserve(reqs)
-        for r in serve.served_requests(seqs, 2, 1000.0, seed=7):  # both request shapes (k 25, 31)
-            serve.run_alone(sl, [r])
     import gc
     gc.collect()
     gc.disable()  # no collector pause inside the timed loops
     try:
-        mix = serve.Scheduler(slots, 120 << 30).run(reqs).summary()
-        alone_reqs = serve.served_requests(seqs, args.serve_requests, 20.0, seed=1606)
-        alone = serve.run_alone(slots[0], alone_reqs).summary()
+        mix_rep = serve.Scheduler(slots, serve.SERVED_BUDGET).run(reqs)
+        alone_rep = serve.run_alone(slots[0], trace())
     finally:
         gc.enable()
-    keys = ("p50_ms", "p95_ms", "p99_ms", "max_ms", "throughput_gbps", "wall_s")
-    return {"requests": args.serve_requests, "rate_per_s": 20.0, "slots": 4, "budget_gb": 120,
+    same = all(all(np.array_equal(a, b) for a, b in zip(x.result, y.result))
+               for x, y in zip(sorted(mix_rep.requests, key=lambda r: r.rid),
+                               sorted(alone_rep.requests, key=lambda r: r.rid)))
+    if not same:
+        raise RuntimeError("a served request's junctions differ alone and in the mix")
+    mix, alone = mix_rep.summary(), alone_rep.summary()
+    bases = sum(r.bases for r in reqs)
+    keys = ("p50_ms", "p95_ms", "p99_ms", "max_ms", "mean_ms", "throughput_gbps", "wall_s")
+    return {"requests": args.serve_requests, "rate_per_s": serve.SERVED_RATE, "slots": 4,
+            "budget_gb": serve.SERVED_BUDGET >> 30, "duration_s": reqs[-1].arrival,
+            "offered_gbps": bases / reqs[-1].arrival / 1e9,
             "mix": {k: mix[k] for k in keys}, "alone": {k: alone[k] for k in keys},
-            "request_recipe": "2-7 prefixes of the 7 genomes, log-uniform 0.1-5 Mbp, k 25/31, "
-                              "~8 filter bits per base, 4 hashes"}
+            "same_results_alone_and_in_mix": same,
+            "request_bases_mbp": {"mean": bases / len(reqs) / 1e6,
+                                  "max": max(r.bases for r in reqs) / 1e6},
+            "request_recipe": "2-50 windows of the 7 genomes of the bacterial recipe at 10x length "
+                              "(46-56 Mbp), window lengths log-uniform 0.1-50 Mbp at uniform offsets, "
+                              "k 25/31 alternating, ~8 filter bits per base, 4 hashes, pass-2 table "
+                              "reserve half a slot per base (grown on overflow)"}
 
 
 # ---------------------------------------------------------------------------

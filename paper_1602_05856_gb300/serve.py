@@ -6,10 +6,11 @@ is free and the device memory it needs -- its input, its workspace (filter,
 pass-2 table, bitmaps) and its output -- fits what the requests in flight
 leave of the budget; requests that arrive while others run are admitted as
 slots and memory free up, and the work of admitted requests overlaps on the
-device (one CUDA stream per slot). A slot keeps its buffers between requests
-and only grows them, so the budget bounds the memory of the requests in
-flight, while the memory held is, per slot, that of the largest request it
-has served (``GpuSlot.reserve`` sizes the slots up front). The loop records
+device (one CUDA stream per slot). A slot takes each request's device
+buffers from PyTorch's caching allocator and gives them back when the request
+is done, so the budget bounds the device memory of the requests in flight
+(the cache reuses the blocks: after the first requests nothing is allocated
+from the driver); its page-locked host staging only grows. The loop records
 each request's latency (completion minus arrival) and reports p50/p99 and
 throughput.
 
@@ -20,6 +21,7 @@ the scheduler with a fake slot on the CPU.
 from __future__ import annotations
 
 import collections
+import dataclasses
 import time
 from dataclasses import dataclass, field
 from typing import Callable, Deque, Dict, List, Optional, Sequence
@@ -27,6 +29,8 @@ from typing import Callable, Deque, Dict, List, Optional, Sequence
 import numpy as np
 
 from . import twopaco
+
+dataclasses_replace = dataclasses.replace
 
 
 @dataclass
@@ -51,8 +55,11 @@ class Request:
     def positions_upper(self) -> int:
         return int(sum(max(0, int(s.size) - self.k + 1) for s in self.seqs))
 
+    table_slots: int = 0          # pass-2 table reserve; 0 = half a slot per base (grown on overflow)
+
     def options(self, stream: int = 0) -> twopaco.Options:
-        return twopaco.Options(hashes=self.hashes, cuda_stream=stream)
+        slots = self.table_slots or max(1 << 16, 1 << int(np.ceil(np.log2(max(self.bases // 2, 1)))))
+        return twopaco.Options(hashes=self.hashes, cuda_stream=stream, table_slots=slots)
 
     def device_bytes(self) -> int:
         """Device memory of one run: input, offsets, workspace, outputs."""
@@ -78,12 +85,15 @@ class Slot:
 
 
 class GpuSlot(Slot):
-    """Runs requests on its own CUDA stream with buffers kept between requests.
+    """Runs requests on its own CUDA stream.
 
-    A request's host work -- staging its strings in pinned memory, waiting for
-    its counts, reading back exactly its junctions -- runs on the slot's own
+    A request's host work -- staging its strings in page-locked memory, waiting
+    for its counts, reading back exactly its junctions -- runs on the slot's own
     worker thread, so that the scheduler loop never blocks on one request while
-    others finish (numpy copies release the interpreter lock).
+    others finish (numpy copies release the interpreter lock). Its device
+    buffers come from PyTorch's caching allocator on the slot's stream and go
+    back to it when the request is done; a pass-2 table that overflows is grown
+    fourfold and the request run again.
     """
 
     def __init__(self, device: str = "cuda"):
@@ -94,17 +104,10 @@ class GpuSlot(Slot):
         if self.device.index is None:  # the worker thread needs an explicit device
             self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = torch.cuda.Stream(device=self.device)
-        self.buf: Dict[str, "torch.Tensor"] = {}
         self.pinned: Dict[str, "torch.Tensor"] = {}
         self.pool = concurrent.futures.ThreadPoolExecutor(max_workers=1)
         self.future = None
-
-    def _grow(self, name: str, nbytes: int):
-        t = self.buf.get(name)
-        if t is None or t.numel() < nbytes:
-            t = self.torch.empty(max(nbytes, 1), dtype=self.torch.uint8, device=self.device)
-            self.buf[name] = t
-        return t
+        self.current = 0  # device bytes of the request in flight
 
     def _grow_pinned(self, name: str, nbytes: int):
         t = self.pinned.get(name)
@@ -114,28 +117,19 @@ class GpuSlot(Slot):
         return t
 
     def held_bytes(self) -> int:
-        return int(sum(t.numel() for t in self.buf.values()))
-
-    @staticmethod
-    def _sizes(req: Request) -> Dict[str, int]:
-        n, m = len(req.seqs), req.bases
-        return {"n": n, "m": m, "cap": max(req.positions_upper(), 1),
-                "ws": twopaco.twopaco_workspace_size(m, n, req.k, req.filter_bits, req.rounds,
-                                                     req.options())}
+        return int(self.current)
 
     def reserve(self, reqs: Sequence[Request]) -> None:
-        """Grow the slot's device and pinned buffers for the largest of reqs up
-        front, so that serving them allocates nothing (buffers stay resident)."""
-        for r in reqs:
-            z = self._sizes(r)
-            n, m = z["n"], z["m"]
-            self._grow_pinned("input", m + 8 * (n + 1))
-            self._grow_pinned("out_offsets", 8 * (n + 1))
-            self._grow_pinned("out_positions", 8 * z["cap"])
-            self._grow("input", m + 8 * (n + 1) + 16)
-            self._grow("workspace", z["ws"] + 256)
-            self._grow("out_offsets", 8 * (n + 1))
-            self._grow("out_positions", 8 * z["cap"])
+        """Grow the page-locked staging for the largest of reqs up front, and run the
+        largest once, so that serving them later finds its blocks in the caches."""
+        if not reqs:
+            return
+        big = max(reqs, key=lambda r: r.bases)
+        self._grow_pinned("input", big.bases + 8 * (len(big.seqs) + 1))
+        self._grow_pinned("out_offsets", 8 * (max(len(r.seqs) for r in reqs) + 1))
+        self._grow_pinned("out_positions", 8 * max(big.positions_upper(), 1))
+        probe = Request(-1, big.seqs, big.k, big.filter_bits, big.rounds, big.hashes)
+        self._serve(probe)
 
     def start(self, req: Request) -> None:
         self.future = self.pool.submit(self._serve, req)
@@ -143,40 +137,53 @@ class GpuSlot(Slot):
     def _serve(self, req: Request) -> None:
         torch = self.torch
         torch.cuda.set_device(self.device)
-        z = self._sizes(req)
-        n, m, cap, ws_bytes = z["n"], z["m"], z["cap"], z["ws"]
+        n, m = len(req.seqs), req.bases
+        cap = max(req.positions_upper(), 1)
         off = np.zeros(n + 1, dtype=np.uint64)
         np.cumsum(np.array([s.size for s in req.seqs], dtype=np.uint64), out=off[1:])
-        # pinned staging of the request's input, copied on the slot's stream
+        # page-locked staging of the request's input, copied on the slot's stream
         host = self._grow_pinned("input", m + 8 * (n + 1))
         hv = host.numpy()
         if m:
             np.concatenate([np.asarray(s, dtype=np.uint8) for s in req.seqs], out=hv[:m])
         hv[m:m + 8 * (n + 1)] = off.view(np.uint8)
-        d_in = self._grow("input", m + 8 * (n + 1) + 16)
-        ws = self._grow("workspace", ws_bytes + 256)
-        d_out_off = self._grow("out_offsets", 8 * (n + 1))
-        d_out_pos = self._grow("out_positions", 8 * cap)
         off_at = (m + 15) // 16 * 16
+        stream = int(self.stream.cuda_stream)
+        slots = req.options().table_slots
         with torch.cuda.stream(self.stream):
+            d_in = torch.empty(off_at + 8 * (n + 1), dtype=torch.uint8, device=self.device)
             d_in[:m].copy_(host[:m], non_blocking=True)
             d_in[off_at:off_at + 8 * (n + 1)].copy_(host[m:m + 8 * (n + 1)], non_blocking=True)
-        ws_ptr = (ws.data_ptr() + 255) // 256 * 256
-        stream = int(self.stream.cuda_stream)
-        twopaco.twopaco_run_device(d_in.data_ptr() if m else 0, d_in.data_ptr() + off_at, n, m,
-                                   req.k, req.filter_bits, req.rounds, req.options(stream), ws_ptr,
-                                   ws_bytes, d_out_off.data_ptr(), d_out_pos.data_ptr(), cap)
-        h_off = self._grow_pinned("out_offsets", 8 * (n + 1))[:8 * (n + 1)]
-        with torch.cuda.stream(self.stream):
-            h_off.copy_(d_out_off[:8 * (n + 1)], non_blocking=True)
-        req.stats = twopaco.twopaco_read_stats(ws_ptr, stream)  # waits for the run and the offsets
-        offs = h_off.numpy().view(np.uint64)
-        total = int(offs[-1])
-        h_pos = self._grow_pinned("out_positions", 8 * max(total, 1))[:8 * total]
-        if total:  # exactly the junctions, not the capacity
-            with torch.cuda.stream(self.stream):
-                h_pos.copy_(d_out_pos[:8 * total], non_blocking=True)
+            d_out_off = torch.empty(n + 1, dtype=torch.int64, device=self.device)
+            d_out_pos = torch.empty(cap, dtype=torch.int64, device=self.device)
+            for attempt in range(4):
+                opts = dataclasses_replace(req.options(stream), table_slots=slots)
+                ws_bytes = twopaco.twopaco_workspace_size(m, n, req.k, req.filter_bits, req.rounds, opts)
+                ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=self.device)
+                self.current = d_in.numel() + ws.numel() + 8 * (n + 1 + cap)
+                ws_ptr = (ws.data_ptr() + 255) // 256 * 256
+                twopaco.twopaco_run_device(d_in.data_ptr() if m else 0, d_in.data_ptr() + off_at, n, m,
+                                           req.k, req.filter_bits, req.rounds, opts, ws_ptr, ws_bytes,
+                                           d_out_off.data_ptr(), d_out_pos.data_ptr(), cap)
+                h_off = self._grow_pinned("out_offsets", 8 * (n + 1))[:8 * (n + 1)]
+                h_off.copy_(d_out_off.view(torch.uint8), non_blocking=True)
+                st = twopaco.twopaco_read_stats(ws_ptr, stream, check=False)  # waits for the run
+                if st["rc"] == twopaco.EOVERFLOW and attempt < 3:
+                    slots *= 4  # the table was too small for this input: grow it and run again
+                    del ws
+                    continue
+                if st["rc"] != twopaco.OK:
+                    raise twopaco.TwopacoError(st["rc"], f"request {req.rid}")
+                break
+            req.stats = st
+            offs = h_off.numpy().view(np.uint64)
+            total = int(offs[-1])
+            h_pos = self._grow_pinned("out_positions", 8 * max(total, 1))[:8 * total]
+            if total:  # exactly the junctions, not the capacity
+                h_pos.copy_(d_out_pos[:total].view(torch.uint8), non_blocking=True)
             self.stream.synchronize()
+            del d_in, ws, d_out_off, d_out_pos  # back to the cache, on this stream
+        self.current = 0
         pos = h_pos.numpy().view(np.uint64)
         req.result = [pos[offs[t]:offs[t + 1]].copy() for t in range(n)]
 
@@ -269,9 +276,10 @@ def served_requests(pool: Sequence[np.ndarray], n: int, rate_per_s: float, seed:
                     bits_per_base: float = 8.0, hashes: int = 4) -> List[Request]:
     """A seeded stream of build requests over a pool of related genomes.
 
-    Each request takes 2-7 strings: prefixes of pool genomes whose lengths are
-    log-uniform in ``mbp_range`` (Mbp); k alternates over ``ks``; the filter has
-    about ``bits_per_base`` bits per base (a power of two); arrivals are Poisson.
+    Each request takes a number of strings uniform in ``genomes_range``: windows
+    of pool genomes at uniform offsets whose lengths are log-uniform in
+    ``mbp_range`` (Mbp); k alternates over ``ks``; the filter has about
+    ``bits_per_base`` bits per base (a power of two); arrivals are Poisson.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     arrivals = poisson_arrivals(n, rate_per_s, seed + 1)
@@ -290,6 +298,18 @@ def served_requests(pool: Sequence[np.ndarray], n: int, rate_per_s: float, seed:
         out.append(Request(i, seqs, int(ks[i % len(ks)]), bits, hashes=hashes,
                            arrival=float(arrivals[i])))
     return out
+
+
+# The served configuration: 2-50 genomes of 0.1-50 Mbp (log-uniform) per request,
+# k 25 or 31, Poisson arrivals at 20 per second, a 120 GB admission budget.
+SERVED_GENOMES, SERVED_MBP, SERVED_RATE, SERVED_BUDGET = (2, 50), (0.1, 50.0), 20.0, 120 << 30
+
+
+def served_pool():
+    """The genome pool of the served configuration: the bacterial-set recipe at ten
+    times its length (7 related genomes of 46-56 Mbp), so that a window can reach 50 Mbp."""
+    from . import genomes
+    return genomes.named_set("bacterial_set", 10.0)
 
 
 def run_alone(slot: Slot, requests: Sequence[Request],

@@ -44,18 +44,20 @@ def mammal():
 
 
 def _digest(run):
-    """(junctions per genome, order-free digest of the global junction positions)."""
-    import torch
+    """(junctions per genome, order-free digest of the global junction positions), computed
+    per genome in slices so that no temporary holds the whole output."""
     st = run.stats()
     off = run.out_offsets.cpu().numpy().view(np.uint64)
-    n = int(off[-1])
-    pos = run.out_positions[:n]
+    starts = run.offsets.cpu().numpy()
     per = np.diff(off).astype(np.int64)
-    start = torch.from_numpy(run.offsets.cpu().numpy()[:-1]).cuda()
-    which = torch.repeat_interleave(torch.arange(len(per), device="cuda"), torch.from_numpy(per).cuda())
-    g = pos + start[which]
-    h = (g * 0x5851F42D4C957F2D) ^ (g >> 29)
-    return per.tolist(), int(h.sum().item()), st, pos
+    h = 0
+    step = 1 << 27
+    for t in range(len(per)):
+        a, b = int(off[t]), int(off[t + 1])
+        for c in range(a, b, step):
+            g = run.out_positions[c:min(b, c + step)] + int(starts[t])
+            h += int(((g * 0x5851F42D4C957F2D) ^ (g >> 29)).sum().item())
+    return per.tolist(), h % (1 << 64), st, None
 
 
 def _run(d_bases, off, bits, rounds, table_slots, records):

@@ -110,3 +110,36 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
             want = O.junctions(genomes.concat(r.seqs), r.k)
             assert all(np.array_equal(a, b) for a, b in zip(want, r.result)), r.rid
     assert rep.summary()["p99_ms"] > 0
+
+
+@pytest.mark.gpu
+def test_served_recipe_same_alone_in_the_mix_and_by_definition():
+    """Requests of the served configuration (2-50 windows of 0.1-50 Mbp from the 10x
+    bacterial pool, k 25/31) arriving faster than they finish, over 3 slots under the
+    120 GB budget: every result equals the request run alone, and the smaller ones equal
+    the oracle's junctions."""
+    import os
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle as O
+    from paper_1602_05856_gb300 import build
+    build.build()
+    pool = serve.served_pool()
+    reqs = serve.served_requests(pool, 10, 200.0, seed=2024, genomes_range=serve.SERVED_GENOMES,
+                                 mbp_range=serve.SERVED_MBP)
+    slots = [serve.GpuSlot() for _ in range(3)]
+    rep = serve.Scheduler(slots, serve.SERVED_BUDGET).run(reqs)
+    assert len(rep.requests) == 10
+    alone = serve.served_requests(pool, 10, 200.0, seed=2024, genomes_range=serve.SERVED_GENOMES,
+                                  mbp_range=serve.SERVED_MBP)
+    serve.run_alone(slots[0], alone)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    checked = 0
+    for r, a in zip(sorted(rep.requests, key=lambda x: x.rid), alone):
+        assert all(np.array_equal(x, y) for x, y in zip(r.result, a.result)), r.rid
+        if r.bases <= 120_000_000 and checked < 2:
+            want = O.junctions(genomes.concat(r.seqs), r.k, threads=cores)
+            assert all(np.array_equal(x, y) for x, y in zip(want, r.result)), r.rid
+            checked += 1
+    assert checked >= 1
