@@ -124,6 +124,11 @@ def oracle_gbps(seqs, k, threads: int = 1) -> float:
     return bases.size / (time.perf_counter() - t) / 1e9
 
 
+def note(msg: str) -> None:
+    """Progress on stderr (stdout carries only the JSON line)."""
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def host_cores() -> int:
     return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
 
@@ -455,6 +460,8 @@ def device_leg(T, build, name, genome_len, rounds, args, world, rank, local, dis
     out["cpu_sample"] = cpu_sample(d_bases, off, seqs) if rank == 0 and not args.no_cpu_baseline else None
     del run, d_bases
     torch.cuda.empty_cache()
+    if hasattr(torch._C, "_host_emptyCache"):
+        torch._C._host_emptyCache()  # the page-locked e2e buffers (tens of GB at full size)
     return out
 
 
@@ -632,7 +639,8 @@ def served_leg(args, local):
 
     def trace():
         return serve.served_requests(pool, args.serve_requests, serve.SERVED_RATE, seed=1606,
-                                     genomes_range=serve.SERVED_GENOMES, mbp_range=serve.SERVED_MBP)
+                                     genomes_range=serve.SERVED_GENOMES, mbp_range=serve.SERVED_MBP,
+                                     digest_only=True)
 
     reqs = trace()
     slots = [serve.GpuSlot(device=f"cuda:{local}") for _ in range(4)]
@@ -646,7 +654,7 @@ def served_leg(args, local):
         alone_rep = serve.run_alone(slots[0], trace())
     finally:
         gc.enable()
-    same = all(all(np.array_equal(a, b) for a, b in zip(x.result, y.result))
+    same = all(x.digest == y.digest and x.digest is not None
                for x, y in zip(sorted(mix_rep.requests, key=lambda r: r.rid),
                                sorted(alone_rep.requests, key=lambda r: r.rid)))
     if not same:
@@ -686,7 +694,9 @@ def run_ours(args, world, rank, local):
     name = args.workload
     if args.filter_bits:
         WORKLOADS[name] = dict(WORKLOADS[name], filter_bits=int(args.filter_bits))
+    note(f"{name}: device leg")
     head = device_leg(T, build, name, args.genome_len, args.rounds, args, world, rank, local, dist)
+    note(f"{name}: {head['value']:.2f} Gbp/s")
 
     extra = {}
     if rank == 0 and world == 1 and args.bacterial and name != "bacterial_set":
@@ -697,12 +707,15 @@ def run_ours(args, world, rank, local):
             "e2e": b["e2e"], "stats": b["stats"], "kernels": b["kernels"], "gpu_launches": b["launches"],
             "random_access_peaks_g_per_s": b["random_access_peaks_g_per_s"], "clocks": b["clocks"]}
     if rank == 0 and world == 1 and args.batched:
+        note("batched leg")
         extra["batched"] = batched_leg(T, genomes, torch.device("cuda", local))
     if rank == 0 and world == 1 and args.serve_requests > 0:
+        note("served leg")
         extra["served"] = served_leg(args, local)
 
     cpu = None
     if rank == 0 and head["cpu_sample"] is not None:
+        note("cpu baseline")
         sample = head["cpu_sample"]
         cores = host_cores()
         cpu = {"value": oracle_gbps(sample, K, threads=cores), "unit": UNIT, "cores": cores,

@@ -56,6 +56,8 @@ class Request:
         return int(sum(max(0, int(s.size) - self.k + 1) for s in self.seqs))
 
     table_slots: int = 0          # pass-2 table reserve; 0 = half a slot per base (grown on overflow)
+    digest_only: bool = False     # keep (junctions per string, digest of the positions), not the arrays
+    digest: Optional[tuple] = None
 
     def options(self, stream: int = 0) -> twopaco.Options:
         slots = self.table_slots or max(1 << 16, 1 << int(np.ceil(np.log2(max(self.bases // 2, 1)))))
@@ -185,7 +187,10 @@ class GpuSlot(Slot):
             del d_in, ws, d_out_off, d_out_pos  # back to the cache, on this stream
         self.current = 0
         pos = h_pos.numpy().view(np.uint64)
-        req.result = [pos[offs[t]:offs[t + 1]].copy() for t in range(n)]
+        if req.digest_only:
+            req.digest = result_digest(offs, pos)
+        else:
+            req.result = [pos[offs[t]:offs[t + 1]].copy() for t in range(n)]
 
     def poll(self) -> bool:
         if self.future is None or not self.future.done():
@@ -265,6 +270,19 @@ class Scheduler:
         return ServeReport(finished, self.clock() - t0)
 
 
+def result_digest(offs: np.ndarray, pos: np.ndarray) -> tuple:
+    """(junctions per string, an order-dependent digest of the positions) of one result."""
+    counts = tuple(int(x) for x in np.diff(offs.astype(np.int64)))
+    with np.errstate(over="ignore"):
+        x = pos.astype(np.uint64) ^ (np.arange(pos.size, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15))
+        x ^= x >> np.uint64(30)
+        x *= np.uint64(0xBF58476D1CE4E5B9)
+        x ^= x >> np.uint64(27)
+        x *= np.uint64(0x94D049BB133111EB)
+        x ^= x >> np.uint64(31)
+        return counts, int(x.sum(dtype=np.uint64)) if x.size else 0
+
+
 def poisson_arrivals(n: int, rate_per_s: float, seed: int) -> np.ndarray:
     """Arrival times (seconds) of a seeded Poisson stream."""
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -273,7 +291,7 @@ def poisson_arrivals(n: int, rate_per_s: float, seed: int) -> np.ndarray:
 
 def served_requests(pool: Sequence[np.ndarray], n: int, rate_per_s: float, seed: int,
                     genomes_range=(2, 7), mbp_range=(0.1, 5.0), ks=(25, 31),
-                    bits_per_base: float = 8.0, hashes: int = 4) -> List[Request]:
+                    bits_per_base: float = 8.0, hashes: int = 4, digest_only: bool = False) -> List[Request]:
     """A seeded stream of build requests over a pool of related genomes.
 
     Each request takes a number of strings uniform in ``genomes_range``: windows
@@ -296,7 +314,7 @@ def served_requests(pool: Sequence[np.ndarray], n: int, rate_per_s: float, seed:
         bases = sum(s.size for s in seqs)
         bits = 1 << max(8, int(np.ceil(np.log2(bits_per_base * bases))))
         out.append(Request(i, seqs, int(ks[i % len(ks)]), bits, hashes=hashes,
-                           arrival=float(arrivals[i])))
+                           arrival=float(arrivals[i]), digest_only=digest_only))
     return out
 
 

@@ -143,3 +143,12 @@ def test_served_recipe_same_alone_in_the_mix_and_by_definition():
             assert all(np.array_equal(x, y) for x, y in zip(want, r.result)), r.rid
             checked += 1
     assert checked >= 1
+
+
+def test_result_digest_tells_results_apart():
+    o = np.array([0, 3, 5], np.uint64)
+    a = serve.result_digest(o, np.array([1, 2, 3, 7, 9], np.uint64))
+    assert a == serve.result_digest(o, np.array([1, 2, 3, 7, 9], np.uint64))
+    assert a != serve.result_digest(o, np.array([1, 2, 3, 9, 7], np.uint64))  # order counts
+    assert a != serve.result_digest(o, np.array([1, 2, 3, 7, 10], np.uint64))
+    assert a != serve.result_digest(np.array([0, 2, 5], np.uint64), np.array([1, 2, 3, 7, 9], np.uint64))
