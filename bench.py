@@ -635,7 +635,7 @@ def served_leg(args, local):
     by device memory under 120 GB into 4 slots whose work overlaps on the GPU; against every
     request run alone on an idle GPU."""
     from paper_1602_05856_gb300 import serve
-    pool = serve.served_pool()
+    pool = serve.served_pool(lock=True)  # the server's resident, page-locked genome store
 
     def trace():
         return serve.served_requests(pool, args.serve_requests, serve.SERVED_RATE, seed=1606,
@@ -670,7 +670,8 @@ def served_leg(args, local):
             "request_bases_mbp": {"mean": bases / len(reqs) / 1e6,
                                   "max": max(r.bases for r in reqs) / 1e6},
             "request_recipe": "2-50 windows of the 7 genomes of the bacterial recipe at 10x length "
-                              "(46-56 Mbp), window lengths log-uniform 0.1-50 Mbp at uniform offsets, "
+                              "(46-56 Mbp, a page-locked resident store the windows copy from), window "
+                              "lengths log-uniform 0.1-50 Mbp at uniform offsets, "
                               "k 25/31 alternating, ~8 filter bits per base, 4 hashes, pass-2 table "
                               "reserve half a slot per base (grown on overflow)"}
 

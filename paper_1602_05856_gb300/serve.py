@@ -143,19 +143,26 @@ class GpuSlot(Slot):
         cap = max(req.positions_upper(), 1)
         off = np.zeros(n + 1, dtype=np.uint64)
         np.cumsum(np.array([s.size for s in req.seqs], dtype=np.uint64), out=off[1:])
-        # page-locked staging of the request's input, copied on the slot's stream
-        host = self._grow_pinned("input", m + 8 * (n + 1))
-        hv = host.numpy()
-        if m:
-            np.concatenate([np.asarray(s, dtype=np.uint8) for s in req.seqs], out=hv[:m])
-        hv[m:m + 8 * (n + 1)] = off.view(np.uint8)
         off_at = (m + 15) // 16 * 16
         stream = int(self.stream.cuda_stream)
         slots = req.options().table_slots
+        direct = all(is_page_locked(s) for s in req.seqs)
+        if not direct:  # page-locked staging of the request's input
+            host = self._grow_pinned("input", m + 8 * (n + 1))
+            hv = host.numpy()
+            if m:
+                np.concatenate([np.asarray(s, dtype=np.uint8) for s in req.seqs], out=hv[:m])
+        offs_host = self._grow_pinned("offsets", 8 * (n + 1))
+        offs_host.numpy()[:8 * (n + 1)] = off.view(np.uint8)
         with torch.cuda.stream(self.stream):
             d_in = torch.empty(off_at + 8 * (n + 1), dtype=torch.uint8, device=self.device)
-            d_in[:m].copy_(host[:m], non_blocking=True)
-            d_in[off_at:off_at + 8 * (n + 1)].copy_(host[m:m + 8 * (n + 1)], non_blocking=True)
+            if direct:  # every string straight from the page-locked store it is a window of
+                for t, sq in enumerate(req.seqs):
+                    if sq.size:
+                        d_in[int(off[t]):int(off[t + 1])].copy_(torch.from_numpy(sq), non_blocking=True)
+            elif m:
+                d_in[:m].copy_(host[:m], non_blocking=True)
+            d_in[off_at:off_at + 8 * (n + 1)].copy_(offs_host[:8 * (n + 1)], non_blocking=True)
             d_out_off = torch.empty(n + 1, dtype=torch.int64, device=self.device)
             d_out_pos = torch.empty(cap, dtype=torch.int64, device=self.device)
             for attempt in range(4):
@@ -323,11 +330,39 @@ def served_requests(pool: Sequence[np.ndarray], n: int, rate_per_s: float, seed:
 SERVED_GENOMES, SERVED_MBP, SERVED_RATE, SERVED_BUDGET = (2, 50), (0.1, 50.0), 20.0, 120 << 30
 
 
-def served_pool():
+_LOCKED: List[np.ndarray] = []
+
+
+def page_lock(arrays: Sequence[np.ndarray]) -> List[np.ndarray]:
+    """Page-lock host arrays in place (cudaHostRegister), as a server keeps its genome
+    store, so that windows of them copy to the device without staging. They stay locked
+    (and referenced) for the life of the process."""
+    import torch
+    rt = torch.cuda.cudart()
+    out = []
+    for a in arrays:
+        a = np.ascontiguousarray(a)
+        if a.size and rt.cudaHostRegister(a.ctypes.data, a.nbytes, 0) == 0:
+            _LOCKED.append(a)
+        out.append(a)
+    return out
+
+
+def is_page_locked(a: np.ndarray) -> bool:
+    """a lies inside an array page_lock registered (a window of it, e.g.)."""
+    if not a.size:
+        return True
+    p = a.__array_interface__["data"][0]
+    return any(b.ctypes.data <= p and p + a.nbytes <= b.ctypes.data + b.nbytes for b in _LOCKED)
+
+
+def served_pool(lock: bool = False):
     """The genome pool of the served configuration: the bacterial-set recipe at ten
-    times its length (7 related genomes of 46-56 Mbp), so that a window can reach 50 Mbp."""
+    times its length (7 related genomes of 46-56 Mbp), so that a window can reach 50 Mbp;
+    with lock, page-locked as a server's resident store."""
     from . import genomes
-    return genomes.named_set("bacterial_set", 10.0)
+    pool = genomes.named_set("bacterial_set", 10.0)
+    return page_lock(pool) if lock else pool
 
 
 def run_alone(slot: Slot, requests: Sequence[Request],

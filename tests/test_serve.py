@@ -125,7 +125,8 @@ def test_served_recipe_same_alone_in_the_mix_and_by_definition():
     import oracle as O
     from paper_1602_05856_gb300 import build
     build.build()
-    pool = serve.served_pool()
+    pool = serve.served_pool(lock=True)
+    assert all(serve.is_page_locked(g) for g in pool) and serve.is_page_locked(pool[0][10:1000])
     reqs = serve.served_requests(pool, 10, 200.0, seed=2024, genomes_range=serve.SERVED_GENOMES,
                                  mbp_range=serve.SERVED_MBP)
     slots = [serve.GpuSlot() for _ in range(3)]
