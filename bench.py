@@ -556,7 +556,8 @@ def batched_leg(T, genomes, dev):
     bases, off = genomes.concat(seqs)
     m = int(off[-1])
     choice = autotune.tune(seqs, K, budget_bytes=120 << 30, bits_per_base=(2, 4, 8, 16),
-                           hashes=(3, 4, 6), rounds=(1,), sample_fraction=0.1, repeats=2)
+                           hashes=(3, 4, 6), rounds=(1,), sample_fraction=0.1, repeats=2,
+                           launch_shapes=(0, 2, 4))
     bpb = choice.bits / m
     stream = torch.cuda.current_stream()
 
@@ -571,9 +572,10 @@ def batched_leg(T, genomes, dev):
         torch.cuda.synchronize()
         return statistics.mean(x.elapsed_time(y) for x, y in zip(a, b))
 
-    def joint(bits, hashes, per_string=False):
+    def joint(bits, hashes, per_string=False, shape=0):
         run = T.DeviceBuild(bases, off, K, bits, 1,
-                            T.Options(hashes=hashes, per_string_launches=per_string), device=dev)
+                            T.Options(hashes=hashes, per_string_launches=per_string,
+                                      launch_blocks_per_sm=shape), device=dev)
         if not per_string:
             run.capture()
         n0 = T.twopaco_kernel_launches()
@@ -584,7 +586,7 @@ def batched_leg(T, genomes, dev):
         run.release_plan()
         return ms, st, res, launches
 
-    batched_ms, st, want, batched_launches = joint(choice.bits, choice.hashes)
+    batched_ms, st, want, batched_launches = joint(choice.bits, choice.hashes, shape=choice.blocks_per_sm)
     per_ms, _, got, per_launches = joint(choice.bits, choice.hashes, per_string=True)
     plain_ms, _, got_plain, _ = joint(1 << 30, 4)  # the paper's filter size at this scale, 4 hashes
     same = all(np.array_equal(a, b) for a, b in zip(want, got)) and \
@@ -613,7 +615,8 @@ def batched_leg(T, genomes, dev):
     single_ms = timed(per_genome, 3)
     return {"genomes": len(seqs), "bases": m, "k": K,
             "tuned": {"filter_bits": choice.bits, "hashes": choice.hashes, "rounds": choice.rounds,
-                      "trials": len(choice.trials)},
+                      "trials": len(choice.trials), "launch_blocks_per_sm": choice.blocks_per_sm,
+                      "launch_shape_ms": {str(k): v for k, v in choice.shape_ms.items()}},
             "batched_gbps": m / (batched_ms * 1e-3) / 1e9, "batched_ms": batched_ms,
             "batched_launches_per_build": batched_launches,
             "per_genome_launches_gbps": m / (per_ms * 1e-3) / 1e9, "per_genome_launches_ms": per_ms,

@@ -36,7 +36,7 @@
  *     options->hashes in [1, 8]; options->partition_bins a power of two
  *     >= rounds (and >= 2 when rounds > 1); options->both_strands and
  *     options->split_at_n, options->partial and options->per_string_launches 0 or 1;
- *     options->bucket_inserts 0, 1 or 2; options->wide_layout 0, 1 or 2;
+ *     options->bucket_inserts 0, 1 or 2; options->launch_blocks_per_sm 0..32; options->wide_layout 0, 1 or 2;
  *     options->run_capacity < 2^32. Anything else is TWOPACO_EINVAL.
  *   - Calls on different workspaces may run concurrently from different host
  *     threads; calls that share a workspace must be serialised by the caller.
@@ -121,6 +121,12 @@ typedef struct twopaco_options {
                               more than direct ORs); 1: for any filter; 2: never. Needs
                               hashes <= 6 and a filter of at most 2^38 bits (else the ORs
                               are direct). */
+  int launch_blocks_per_sm; /* launch shape of the pass kernels (insert, probe, pass-2
+                              insert and classify): at most this many resident blocks of
+                              256 threads per SM in their grids, 1..32; 0 (default): as
+                              many as fit. Same results (every loop strides over its
+                              work); a latency-bound kernel can gain from fewer blocks
+                              contending for L2. */
 } twopaco_options;
 
 /* Counters of one run, in the spirit of Table 4 (marks after each pass). */

@@ -13,7 +13,9 @@ full-size workspace fits the memory budget, raising the round count only when
 one round does not fit. A scaled-down filter can sit in L2 where the full one
 does not, so the sample misranks filters of different sizes: the fastest
 candidate of each filter size (up to ``refine`` sizes) is timed again on the
-whole input before the choice.
+whole input before the choice. Last, the chosen configuration is timed on the
+whole input with each launch shape of ``launch_shapes`` (resident blocks per
+SM of the pass kernels; 0 = as many as fit) and keeps the fastest.
 
 Every run goes through the C ABI (``twopaco.DeviceBuild``); nothing here
 computes junctions.
@@ -53,13 +55,15 @@ class Choice:
     trials: List[Trial] = field(default_factory=list)
     table_slots: int = 0
     candidate_records: int = 0
+    blocks_per_sm: int = 0               # the chosen launch shape (0 = all that fit)
+    shape_ms: Dict[int, float] = field(default_factory=dict)  # full-input ms per shape tried
 
     def options(self, **extra) -> twopaco.Options:
         """Options for the chosen configuration, with the table and list sizes its
         ``workspace`` was computed for (a table that still overflows is grown by the
-        host builds and reported by the device runs)."""
+        host builds and reported by the device runs) and its launch shape."""
         kw = dict(hashes=self.hashes, table_slots=self.table_slots,
-                  candidate_records=self.candidate_records)
+                  candidate_records=self.candidate_records, launch_blocks_per_sm=self.blocks_per_sm)
         kw.update(extra)
         return twopaco.Options(**kw)
 
@@ -102,7 +106,7 @@ def tune(seqs: Sequence[np.ndarray], k: int, budget_bytes: Optional[int] = None,
          bits_per_base: Sequence[float] = (4, 8, 16, 32), hashes: Sequence[int] = (3, 4, 6, 8),
          rounds: Sequence[int] = (1, 2, 4, 8, 16), sample_fraction: float = 0.1,
          repeats: int = 3, both_strands: bool = True, device: str = "cuda",
-         refine: int = 4) -> Choice:
+         refine: int = 4, launch_shapes: Sequence[int] = (0,)) -> Choice:
     """Measure candidate configurations on a sample; return the fastest that fits."""
     seqs = [np.ascontiguousarray(s, dtype=np.uint8) for s in seqs]
     total = sum(int(s.size) for s in seqs)
@@ -152,6 +156,18 @@ def tune(seqs: Sequence[np.ndarray], k: int, budget_bytes: Optional[int] = None,
                     del run
                 ranked = sorted(ranked, key=lambda t: (t.est_full_ms, t.workspace))
             best = ranked[0]
-            return Choice(best.bits, best.hashes, best.rounds, best.workspace, best.est_full_ms,
-                          trials, best.table_slots, best.candidate_records)
+            shape, shape_ms = 0, {}
+            if len(launch_shapes) > 1:
+                bases, off = genomes.concat(seqs)
+                for bps in launch_shapes:
+                    run = twopaco.DeviceBuild(bases, off, k, best.bits, best.rounds,
+                                              twopaco.Options(hashes=best.hashes, both_strands=both_strands,
+                                                              launch_blocks_per_sm=bps),
+                                              device=device)
+                    shape_ms[bps], _ = _time_run(run, max(1, repeats))
+                    del run
+                shape = min(shape_ms, key=lambda b: (shape_ms[b], b))
+            return Choice(best.bits, best.hashes, best.rounds, best.workspace,
+                          shape_ms.get(shape, best.est_full_ms), trials, best.table_slots,
+                          best.candidate_records, shape, shape_ms)
     raise ValueError("no configuration fits the memory budget")

@@ -55,6 +55,7 @@ int validate(uint64_t n_seqs, int k, uint64_t filter_bits, int rounds, const two
   if (o.partial != 0 && o.partial != 1) return TWOPACO_EINVAL;
   if (o.per_string_launches != 0 && o.per_string_launches != 1) return TWOPACO_EINVAL;
   if (o.bucket_inserts < 0 || o.bucket_inserts > 2) return TWOPACO_EINVAL;
+  if (o.launch_blocks_per_sm < 0 || o.launch_blocks_per_sm > 32) return TWOPACO_EINVAL;
   return TWOPACO_OK;
 }
 
@@ -237,6 +238,7 @@ RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_
   v.bitmap_words = L.bitmap_words;
   v.p_begin = 0;
   v.p_end = m;
+  v.blocks_per_sm = o.launch_blocks_per_sm;
   v.table = base + L.table;
   v.table_max_slots = L.table_slots;
   v.cands = reinterpret_cast<uint64_t*>(base + L.cands);
@@ -330,6 +332,7 @@ void twopaco_default_options(twopaco_options* opt) {
   opt->partial = 0;
   opt->per_string_launches = 0;
   opt->bucket_inserts = 0;
+  opt->launch_blocks_per_sm = 0;
 }
 
 const char* twopaco_strerror(int code) {

@@ -72,6 +72,7 @@ struct RunView {
   int rounds;               // classes of Algorithm 3
   int partial;              // omit pass 2: C_final gathers every round's C_temp
   int count_round;          // the round whose probe counts the input's k-mer positions
+  int blocks_per_sm;        // resident blocks per SM of the pass kernels' grids (0: all that fit)
   uint64_t p_begin, p_end;  // positions the first- and second-pass loops visit: all
                             // ([0, m)) or, launched per string, whole tiles of kRangeTile
   int lg_blocks;            // log2(filter_bits / 256)

@@ -1535,46 +1535,55 @@ __global__ void __launch_bounds__(kBlock) pass1_probe_cm_kernel(RunView v, int r
     uint32_t valid;
     const uint32_t n = compact_window(v, wbase, round, idx, &valid);
     valid_n += valid;
-    for (uint32_t j0 = 0; j0 < n; j0 += 32) {
-      const uint32_t j = j0 + lane;
-      bool keep = false;
-      uint64_t G = 0, g = 0;
-      uint32_t sentinel = 0;
-      if (j < n) {
-        const uint32_t e = idx[j];
-        g = wbase + (e & 511u);
-        sentinel = (e >> 9) & 1u;
-        if (sentinel) {
-          keep = true;
-          OccT<KW> oc;
-          read_listed<KW>(v, g, true, &oc);
-          G = second_hash(oc.H);
-        } else {
-          OccT<KW> oc;
-          read_listed<KW>(v, g, false, &oc);
-          G = second_hash(oc.H);
-          const uint64_t word = __ldcg(filter_word(v, oc.H, G));
-          const uint32_t pres = present_items<HB>(G, word, v.hashes);
-          keep = (pres >> 16) || __popc(pres & 0xFFFFu) >= 2;
+    // two entries per lane and step: both k-mers are read and hashed and both
+    // filter loads issued before either is tested, so that a lane keeps two
+    // random loads in flight
+    for (uint32_t j0 = 0; j0 < n; j0 += 64) {
+      uint64_t G[2] = {0, 0}, g[2] = {0, 0}, word[2] = {0, 0};
+      uint32_t e[2] = {0, 0}, sentinel[2] = {0, 0};
+      bool have[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const uint32_t j = j0 + 32 * u + lane;
+        have[u] = j < n;
+        if (!have[u]) continue;
+        e[u] = idx[j];
+        g[u] = wbase + (e[u] & 511u);
+        sentinel[u] = (e[u] >> 9) & 1u;
+        OccT<KW> oc;
+        read_listed<KW>(v, g[u], sentinel[u], &oc);
+        G[u] = second_hash(oc.H);
+        if (!sentinel[u]) word[u] = __ldcg(filter_word(v, oc.H, G[u]));
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        bool keep = false;
+        if (have[u]) {
+          if (sentinel[u]) {
+            keep = true;
+          } else {
+            const uint32_t pres = present_items<HB>(G[u], word[u], v.hashes);
+            keep = (pres >> 16) || __popc(pres & 0xFFFFu) >= 2;
+          }
+          if (keep) atomicOr(keep_w + ((e[u] & 511u) >> 5), 1u << (e[u] & 31u));
         }
-        if (keep) atomicOr(keep_w + ((e & 511u) >> 5), 1u << (e & 31u));
-      }
-      if (v.partial) {
-        kept += keep;
-        continue;
-      }
-      const uint32_t row = __ballot_sync(0xffffffffu, keep);
-      if (keep) {
-        const uint64_t x = (G * 0xff51afd7ed558ccdull) >> (64 - v.lc_log2);
-        atomicOr(v.lc_bits + (x >> 5), 1u << (x & 31));
-        const uint64_t at = seg_used + __popc(row & below);
-        if (at < v.seg_cap) {
-          if (v.narrow) seg32[at] = (uint32_t)g | (sentinel << 31);
-          else seg[at] = g | ((uint64_t)sentinel << 63);
+        if (v.partial) {
+          kept += keep;
+          continue;
         }
-        ++kept;
+        const uint32_t row = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+          const uint64_t x = (G[u] * 0xff51afd7ed558ccdull) >> (64 - v.lc_log2);
+          atomicOr(v.lc_bits + (x >> 5), 1u << (x & 31));
+          const uint64_t at = seg_used + __popc(row & below);
+          if (at < v.seg_cap) {
+            if (v.narrow) seg32[at] = (uint32_t)g[u] | (sentinel[u] << 31);
+            else seg[at] = g[u] | ((uint64_t)sentinel[u] << 63);
+          }
+          ++kept;
+        }
+        seg_used += __popc(row);
       }
-      seg_used += __popc(row);
     }
     __syncwarp();
     if (lane < kCmWindow / 32) {
@@ -2240,9 +2249,10 @@ int sm_count() {
 
 // Grid of at most (SMs x resident blocks per SM) blocks for work_items threads.
 template <typename K>
-unsigned grid_for(K kernel, int block, uint64_t work_items) {
+unsigned grid_for(K kernel, int block, uint64_t work_items, int cap_per_sm = 0) {
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0);
+  if (cap_per_sm > 0 && per_sm > cap_per_sm) per_sm = cap_per_sm;  // a chosen launch shape
   if (per_sm < 1) per_sm = 1;
   const uint64_t full = (uint64_t)sm_count() * per_sm;
   const uint64_t need = (work_items + block - 1) / block;
@@ -2379,23 +2389,23 @@ int round_impl(const RunView& v, int round, cudaStream_t s, const Ranges* ranges
                                    s) != cudaSuccess)
           return -1;
         if (cm && bkt)
-          pass1_insert_cm_kernel<KW, HB, kBktOk><<<grid_for(pass1_insert_cm_kernel<KW, HB, kBktOk>, kBlock, threads),
+          pass1_insert_cm_kernel<KW, HB, kBktOk><<<grid_for(pass1_insert_cm_kernel<KW, HB, kBktOk>, kBlock, threads, v.blocks_per_sm),
                                                    kBlock, 0, s>>>(x, round);
         else if (cm)
-          pass1_insert_cm_kernel<KW, HB><<<grid_for(pass1_insert_cm_kernel<KW, HB>, kBlock, threads), kBlock, 0,
+          pass1_insert_cm_kernel<KW, HB><<<grid_for(pass1_insert_cm_kernel<KW, HB>, kBlock, threads, v.blocks_per_sm), kBlock, 0,
                                            s>>>(x, round);
         else if (desc && bkt)
           pass1_insert_kernel<KW, RD, HB, kDescOk, kBktOk>
-              <<<grid_for(pass1_insert_kernel<KW, RD, HB, kDescOk, kBktOk>, kBlock, threads), kBlock, 0, s>>>(x, round);
+              <<<grid_for(pass1_insert_kernel<KW, RD, HB, kDescOk, kBktOk>, kBlock, threads, v.blocks_per_sm), kBlock, 0, s>>>(x, round);
         else if (desc)
           pass1_insert_kernel<KW, RD, HB, kDescOk><<<grid_for(pass1_insert_kernel<KW, RD, HB, kDescOk>, kBlock,
                                                               threads),
                                                      kBlock, 0, s>>>(x, round);
         else if (bkt)
           pass1_insert_kernel<KW, RD, HB, false, kBktOk>
-              <<<grid_for(pass1_insert_kernel<KW, RD, HB, false, kBktOk>, kBlock, threads), kBlock, 0, s>>>(x, round);
+              <<<grid_for(pass1_insert_kernel<KW, RD, HB, false, kBktOk>, kBlock, threads, v.blocks_per_sm), kBlock, 0, s>>>(x, round);
         else
-          pass1_insert_kernel<KW, RD, HB, false><<<grid_for(pass1_insert_kernel<KW, RD, HB, false>, kBlock, threads),
+          pass1_insert_kernel<KW, RD, HB, false><<<grid_for(pass1_insert_kernel<KW, RD, HB, false>, kBlock, threads, v.blocks_per_sm),
                                                    kBlock, 0, s>>>(x, round);
         }
         ++launched;
@@ -2415,9 +2425,9 @@ int round_impl(const RunView& v, int round, cudaStream_t s, const Ranges* ranges
       pv = part(r);
       const uint64_t threads = (r.second - r.first + kProbeR - 1) / kProbeR;
       // one candidate-list segment per probe warp
-      unsigned grid = cm     ? grid_for(pass1_probe_cm_kernel<KW, HB>, kBlock, (r.second - r.first + 15) / 16)
-                      : desc ? grid_for(pass1_probe_desc_kernel<kDescOk ? HB : 1>, kBlock, threads)
-                             : grid_for(pass1_probe_kernel<KW, RD, HB>, kBlock, threads);
+      unsigned grid = cm     ? grid_for(pass1_probe_cm_kernel<KW, HB>, kBlock, (r.second - r.first + 15) / 16, v.blocks_per_sm)
+                      : desc ? grid_for(pass1_probe_desc_kernel<kDescOk ? HB : 1>, kBlock, threads, v.blocks_per_sm)
+                             : grid_for(pass1_probe_kernel<KW, RD, HB>, kBlock, threads, v.blocks_per_sm);
       if (grid * (kBlock / 32) > kMaxSegments) grid = kMaxSegments / (kBlock / 32);
       pv.n_segments = grid * (kBlock / 32);
       // the list region holds cand_cap 8-byte records, or twice as many 32-bit
@@ -2440,8 +2450,8 @@ int round_impl(const RunView& v, int round, cudaStream_t s, const Ranges* ranges
   }
   launched += 2;
   // pass 2: one resident wave; the warps share out the list's segment parts
-  const unsigned g2 = grid_for(pass2_insert_kernel<KW, TS>, kBlock, ~0ull >> 1);
-  const unsigned g3 = grid_for(pass2_classify_kernel<KW, TS>, kBlock, ~0ull >> 1);
+  const unsigned g2 = grid_for(pass2_insert_kernel<KW, TS>, kBlock, ~0ull >> 1, v.blocks_per_sm);
+  const unsigned g3 = grid_for(pass2_classify_kernel<KW, TS>, kBlock, ~0ull >> 1, v.blocks_per_sm);
   {
     Timed t("pass2_insert", s);
     for (const auto& r : rs) {

@@ -39,7 +39,8 @@ class _Options(ctypes.Structure):
                 ("candidate_records", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p),
                 ("split_at_n", ctypes.c_int), ("run_capacity", ctypes.c_uint64),
                 ("wide_layout", ctypes.c_int), ("partial", ctypes.c_int),
-                ("per_string_launches", ctypes.c_int), ("bucket_inserts", ctypes.c_int)]
+                ("per_string_launches", ctypes.c_int), ("bucket_inserts", ctypes.c_int),
+                ("launch_blocks_per_sm", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
@@ -180,13 +181,15 @@ class Options:
     partial: bool = False     # omit pass 2: the partially compacted graph's positions
     per_string_launches: bool = False  # every loop launched once per string (a baseline)
     bucket_inserts: int = 0   # first-pass ORs through region buckets: 0 auto (> 64 MiB), 1 always, 2 never
+    launch_blocks_per_sm: int = 0  # launch shape of the pass kernels: resident blocks per SM (0: all)
 
     def _c(self) -> _Options:
         return _Options(int(self.hashes), int(bool(self.both_strands)), int(self.partition_bins),
                         int(self.table_slots), int(self.candidate_records),
                         ctypes.c_void_p(int(self.cuda_stream) or None), int(bool(self.split_at_n)),
                         int(self.run_capacity), int(self.wide_layout), int(bool(self.partial)),
-                        int(bool(self.per_string_launches)), int(self.bucket_inserts))
+                        int(bool(self.per_string_launches)), int(self.bucket_inserts),
+                        int(self.launch_blocks_per_sm))
 
 
 def _stats_dict(s: _Stats) -> Dict[str, int]:

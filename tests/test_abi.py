@@ -189,3 +189,14 @@ def test_bucketed_inserts_follow_the_or_density():
     assert ws(24_000_000_000, 1 << 36, 0, 4) == ws(24_000_000_000, 1 << 36, 2, 4)  # about 7
     assert ws(35_000_000, 1 << 28, 0) == ws(35_000_000, 1 << 28, 2)       # within L2
     assert ws(35_000_000, 1 << 28, 1) > ws(35_000_000, 1 << 28, 2)        # forced
+
+
+def test_launch_shape_option_range():
+    from paper_1602_05856_gb300 import build, twopaco as T
+    build.build()
+    for bad in (-1, 33):
+        with pytest.raises(T.TwopacoError) as e:
+            T.twopaco_workspace_size(1000, 2, 25, 1 << 20, 1, T.Options(launch_blocks_per_sm=bad))
+        assert e.value.code == T.EINVAL
+    assert T.twopaco_workspace_size(1000, 2, 25, 1 << 20, 1, T.Options(launch_blocks_per_sm=2)) == \
+        T.twopaco_workspace_size(1000, 2, 25, 1 << 20, 1)

@@ -23,6 +23,8 @@ def test_choice_options_reproduce_the_budgeted_workspace():
     assert T.twopaco_workspace_size(m, n, k, bits, rounds, c.options()) == ws
     assert ws < T.twopaco_workspace_size(m, n, k, bits, rounds, T.Options(hashes=4))
     assert c.options(hashes=6).hashes == 6
+    c2 = autotune.Choice(bits, 4, rounds, ws, 1.0, [], 1 << 20, 300000, blocks_per_sm=2)
+    assert c2.options().launch_blocks_per_sm == 2 and c.options().launch_blocks_per_sm == 0
 
 
 @pytest.mark.gpu
@@ -36,8 +38,9 @@ def test_tuned_configuration_is_exact_and_fits_the_budget():
     seqs = genomes.named_set("plain_single", 0.1)
     k = 25
     choice = autotune.tune(seqs, k, bits_per_base=(4, 16), hashes=(3, 6), rounds=(1, 2),
-                           sample_fraction=0.25, repeats=2)
+                           sample_fraction=0.25, repeats=2, launch_shapes=(0, 2))
     assert choice.rounds == 1 and len(choice.trials) == 4
+    assert set(choice.shape_ms) == {0, 2} and choice.blocks_per_sm in (0, 2)
     got, _ = T.twopaco_build_ex(seqs, k, choice.bits, choice.rounds, choice.options())
     want = O.junctions(genomes.concat(seqs), k)
     assert all(np.array_equal(g, w) for g, w in zip(got, want))

@@ -473,3 +473,13 @@ def test_bucketed_inserts_on_a_filter_beyond_l2():
     m = int(off[-1])
     marks, _, _, kept = O.pass1_marks((bases, off), 25, 1 << 30, 4)
     assert np.array_equal(_bits_to_marks(forced.state(T().STATE_CANDIDATES, (m + 31) // 32), m), marks)
+
+
+@pytest.mark.parametrize("shape,rounds", [(1, 1), (3, 1), (2, 3)])
+def test_launch_shape_changes_nothing(shape, rounds):
+    """Fewer resident blocks per SM in the pass kernels' grids: the same junctions."""
+    seqs = _named("plain_single", 0.05)
+    bases, off = G.concat(seqs)
+    got, _ = T().twopaco_build_ex(seqs, 25, 1 << 20, rounds,
+                                  T().Options(hashes=4, partition_bins=256, launch_blocks_per_sm=shape))
+    _eq(got, O.junctions((bases, off), 25))
