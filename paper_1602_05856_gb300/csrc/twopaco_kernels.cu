@@ -692,13 +692,12 @@ __device__ __forceinline__ uint64_t table_insert(const RunView& v, uint64_t cap,
   uint64_t i = start;
   for (uint64_t probe = 0; probe < cap; ++probe, i = next_slot(i, cap)) {
     if (TS == 0) {
-      // one word: key << 9 | mask bits; never all ones for a key < 2^54
+      // one word: key << 9 | mask bits; never all ones for a key < 2^54. The CAS
+      // claims an empty slot in one round trip; when it fails it returns the
+      // word, which tells whether the slot holds this key and which bits it has
       unsigned long long* s = static_cast<unsigned long long*>(v.table) + i;
-      unsigned long long cur = __ldcg(s);
-      if (cur == kEmpty) {
-        cur = atomicCAS(s, kEmpty, (key.lo << kMaskBits) | bits);
-        if (cur == kEmpty) return i;
-      }
+      const unsigned long long cur = atomicCAS(s, kEmpty, (key.lo << kMaskBits) | bits);
+      if (cur == kEmpty) return i;
       if ((cur >> kMaskBits) != key.lo) continue;
       if ((cur & bits) != bits) atomicOr(s, (unsigned long long)bits);
       return i;
@@ -1935,19 +1934,26 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(RunView v) {
     __syncthreads();
     const uint64_t tile = tile_s;
     if (tile >= v.n_tiles) break;
-    // word q * kBlock + threadIdx.x of the tile, for q < kEmitWordsPerThread:
-    // in step q the block holds kBlock consecutive words
-    const uint64_t base = tile * kEmitTileWords + threadIdx.x;
+    // thread t owns the kEmitWordsPerThread consecutive words starting at word
+    // t * kEmitWordsPerThread of the tile: one scan gives every thread its start
+    const uint64_t tile_base = tile * kEmitTileWords;
+    const uint64_t base = tile_base + (uint64_t)threadIdx.x * kEmitWordsPerThread;
     uint32_t words[kEmitWordsPerThread];
+    if (base + kEmitWordsPerThread <= v.bitmap_words) {
+      const uint4 a = __ldcg(reinterpret_cast<const uint4*>(v.cfinal + base));
+      const uint4 b = __ldcg(reinterpret_cast<const uint4*>(v.cfinal + base + 4));
+      words[0] = a.x; words[1] = a.y; words[2] = a.z; words[3] = a.w;
+      words[4] = b.x; words[5] = b.y; words[6] = b.z; words[7] = b.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < kEmitWordsPerThread; ++q)
+        words[q] = (base + q < v.bitmap_words) ? __ldcg(v.cfinal + base + q) : 0u;
+    }
     uint32_t c = 0;
 #pragma unroll
-    for (int q = 0; q < kEmitWordsPerThread; ++q) {
-      const uint64_t w = base + (uint64_t)q * kBlock;
-      words[q] = (w < v.bitmap_words) ? __ldcg(v.cfinal + w) : 0u;
-      c += __popc(words[q]);
-    }
+    for (int q = 0; q < kEmitWordsPerThread; ++q) c += __popc(words[q]);
     uint32_t tot;
-    block_exclusive_scan(c, &tot);
+    const uint32_t before = block_exclusive_scan(c, &tot);
     if (threadIdx.x == 0) {
       total_s = tot;
       unsigned long long prefix = 0;
@@ -1979,16 +1985,13 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(RunView v) {
       prefix_s = prefix;
     }
     __syncthreads();
-    uint64_t at_base = prefix_s;
+    uint64_t at = prefix_s + before;
     Bounds bd{1, 0};
 #pragma unroll
     for (int q = 0; q < kEmitWordsPerThread; ++q) {
-      uint32_t step_tot;
-      uint64_t at = at_base + block_exclusive_scan(__popc(words[q]), &step_tot);
-      at_base += step_tot;
-      before_s[q * kBlock + threadIdx.x] = (uint32_t)(at - prefix_s);
+      before_s[threadIdx.x * kEmitWordsPerThread + q] = (uint32_t)(at - prefix_s);
       uint32_t bits = words[q];
-      const uint64_t w = base + (uint64_t)q * kBlock;
+      const uint64_t w = base + q;
       while (bits) {
         const uint32_t b = __ffs(bits) - 1;
         bits &= bits - 1;
@@ -2000,7 +2003,6 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(RunView v) {
     }
     // out_offsets[t] (junctions before string t) for the strings that start in
     // this tile; the last tile also takes t = n_seqs (start m: the total)
-    const uint64_t tile_base = tile * kEmitTileWords;
     if (threadIdx.x == 0) {
       const uint64_t g_lo = tile_base * 32;
       const uint64_t g_hi = tile + 1 == v.n_tiles ? ~0ull : (tile_base + kEmitTileWords) * 32;

@@ -465,7 +465,7 @@ def test_bucketed_inserts_on_a_filter_beyond_l2():
     direct = T().DeviceBuild(bases, off, 25, 1 << 30, 1, T().Options(hashes=4, bucket_inserts=2))
     forced = T().DeviceBuild(bases, off, 25, 1 << 30, 1, T().Options(hashes=4, bucket_inserts=1))
     assert auto.ws_bytes == direct.ws_bytes < forced.ws_bytes
-    full = sum(G.named_set("batched_set", 1.0)[t].size for t in range(62))
+    full = sum(x.size for x in _named("batched_set", 1.0))
     assert T().twopaco_workspace_size(full, 62, 25, 1 << 30, 1) > \
         T().twopaco_workspace_size(full, 62, 25, 1 << 30, 1, T().Options(bucket_inserts=2))
     forced.run()
