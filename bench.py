@@ -448,7 +448,7 @@ def device_leg(T, build, name, genome_len, rounds, args, world, rank, local, dis
     hbm_peak = float(peaks_json.get("hbm_gbs", 6800.0))
     out = {"name": name, "m": m, "n": n, "rounds": rounds, "ms": ms_max, "step_ms": step_ms,
            "value": m / (ms_max * 1e-3) / 1e9, "launches": launches, "clocks": clocks, "wall": wall,
-           "stats": {k: st[k] for k in ("positions", "pass1_marks", "pass2_marks", "table_slots")}
+           "stats": {k: st[k] for k in ("positions", "pass1_marks", "pass2_marks", "table_slots", "ordered_rounds")}
                     | {"junctions": junctions},
            "kernels": kernels_summary(prof, args.steps),
            "roofline": roofline(prof, st, m, n, table_bytes, peaks, hbm_peak, peaks_json, name, in_l2,

@@ -36,7 +36,8 @@
  *     options->hashes in [1, 8]; options->partition_bins a power of two
  *     >= rounds (and >= 2 when rounds > 1); options->both_strands and
  *     options->split_at_n, options->partial and options->per_string_launches 0 or 1;
- *     options->bucket_inserts 0, 1 or 2; options->launch_blocks_per_sm 0..32; options->wide_layout 0, 1 or 2;
+ *     options->bucket_inserts 0, 1 or 2; options->launch_blocks_per_sm 0..32;
+ *     options->ordered_first_pass 0, 1 or 2; options->wide_layout 0, 1 or 2;
  *     options->run_capacity < 2^32. Anything else is TWOPACO_EINVAL.
  *   - Calls on different workspaces may run concurrently from different host
  *     threads; calls that share a workspace must be serialised by the caller.
@@ -127,6 +128,19 @@ typedef struct twopaco_options {
                               many as fit. Same results (every loop strides over its
                               work); a latency-bound kernel can gain from fewer blocks
                               contending for L2. */
+  int ordered_first_pass;  /* the first pass of a class-map run (rounds 2..64, k <= 63,
+                              hashes <= 6) in filter-region order: every position of a
+                              round's class becomes an 8-byte record in the bucket of its
+                              k-mer's filter region (at most 32 MiB, which L2 holds); the
+                              ORs and then the probes are applied bucket by bucket, and the
+                              decisions are gathered back in position order. A filter
+                              beyond L2 otherwise takes every OR and probe at DRAM's
+                              random-access rate. The workspace holds a region byte per
+                              position and records for a round's positions and a quarter
+                              more (the candidate list shares their room); a round with
+                              more positions takes the direct kernels. Same results. 0
+                              (default): for filters of 1 GiB (2^33 bits) and more; 1: for
+                              any filter; 2: never. Not with per_string_launches. */
 } twopaco_options;
 
 /* Counters of one run, in the spirit of Table 4 (marks after each pass). */
@@ -142,6 +156,9 @@ typedef struct twopaco_stats {
                               twopaco_run_rounds(..., rounds, rounds, ...) writes the
                               output again into a larger buffer */
   uint32_t timeout;        /* nonzero: a bounded device wait gave up */
+  uint32_t ordered_rounds; /* rounds whose first pass ran in filter-region order
+                              (options->ordered_first_pass) */
+  uint32_t pad;
 } twopaco_stats;
 
 /* Result of twopaco_build: library-owned host memory. */

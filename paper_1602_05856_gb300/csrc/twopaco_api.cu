@@ -56,6 +56,7 @@ int validate(uint64_t n_seqs, int k, uint64_t filter_bits, int rounds, const two
   if (o.per_string_launches != 0 && o.per_string_launches != 1) return TWOPACO_EINVAL;
   if (o.bucket_inserts < 0 || o.bucket_inserts > 2) return TWOPACO_EINVAL;
   if (o.launch_blocks_per_sm < 0 || o.launch_blocks_per_sm > 32) return TWOPACO_EINVAL;
+  if (o.ordered_first_pass < 0 || o.ordered_first_pass > 2) return TWOPACO_EINVAL;
   return TWOPACO_OK;
 }
 
@@ -69,6 +70,10 @@ struct Layout {
   int narrow, use_desc, use_slot, split, use_cmap;
   uint32_t n_regions, n_sub;
   int lg_region_words;
+  uint32_t o_regions;  // region-ordered first pass (0: off)
+  int o_lg_region_words;
+  uint64_t o_rec_cap, o_tiles;
+  uint64_t rplane, ohist, ostart, ofill, orecs, odec, ometa;
   uint64_t bucket_cap, bucket_chunk;
   uint64_t n_chunks, run_cap;
   uint64_t total;
@@ -126,8 +131,32 @@ Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int roun
   L.cand_cap = o.candidate_records ? o.candidate_records
                                    : (per_round / 2 > (1u << 16) ? per_round / 2 : (1u << 16));
   if (o.partial) L.cand_cap = 0;
+  // region-ordered first pass: class-map rounds (k <= 63, h <= 6, one launch
+  // per loop) with at most kOrdMaxRegions regions of at most 2^22 words and
+  // at most kOrdMaxHist (round, region) counters; automatically for filters of
+  // 1 GiB and more (far beyond L2), or for any filter when asked
+  L.o_regions = 0;
+  {
+    const uint64_t fwords = filter_bits / 64;
+    const uint64_t rw = std::max<uint64_t>(1, std::min<uint64_t>(1ull << kRegionWordsLog2, fwords / 64));
+    const uint64_t R = fwords / rw;
+    const bool want = o.ordered_first_pass == 1 || (o.ordered_first_pass == 0 && filter_bits / 8 >= (1ull << 30));
+    if (want && rounds > 1 && rounds <= kMaxMapRounds && k <= 63 && o.hashes <= 6 && !o.per_string_launches &&
+        m > 0 && R <= kOrdMaxRegions && R * (uint64_t)rounds <= kOrdMaxHist) {
+      L.o_regions = (uint32_t)R;
+      L.o_lg_region_words = log2_exact(rw);
+      // records for a round's positions and a quarter more (classes are cut
+      // to hold about m / rounds distinct k-mers each; repeats make their
+      // positions vary more), plus each bucket's rounding to 32; a round whose
+      // records do not fit takes the direct kernels
+      L.o_rec_cap = per_round + per_round / 4 + 32ull * R + 4096;
+      L.o_tiles = (m + kOrdTile - 1) / kOrdTile;
+    }
+  }
   L.cands = at;
-  at += align_up(L.cand_cap * cand_record_bytes(k));
+  // with the ordered first pass the list shares the records' room: the gather
+  // writes the list after the probe read the last record
+  if (!L.o_regions) at += align_up(L.cand_cap * cand_record_bytes(k));
   // the table slot of every listed candidate (32-bit slot indices), kept by
   // the second-pass insert for its probe loop; one per record of the list
   // (twice as many 32-bit records under 2^31 bases)
@@ -135,9 +164,12 @@ Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int roun
   L.use_slot = (L.table_slots < (1ull << 32) && o.wide_layout < 2) ? 1 : 0;
   L.cslot = at;
   if (L.use_slot) at += align_up(L.cand_cap * (L.narrow ? 2 : 1) * 4);
-  // linear-counting bitmap: 2^lc_log2 >= the list's capacity (at least 2^16 bits)
+  // linear-counting bitmap: 2^lc_log2 >= the list's capacity, at least 2^16
+  // bits and at most 2^28 (32 MiB, which stays in L2 while the probe sets its
+  // bits at random; linear counting stays exact to a small fraction of a
+  // percent up to about 7 distinct candidates per bit)
   L.lc_log2 = 16;
-  while ((1ull << L.lc_log2) < L.cand_cap && L.lc_log2 < 36) ++L.lc_log2;
+  while ((1ull << L.lc_log2) < L.cand_cap && L.lc_log2 < 28) ++L.lc_log2;
   L.lc = at;
   at += align_up((1ull << L.lc_log2) / 8);
   L.segs = at;
@@ -180,10 +212,30 @@ Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int roun
     const uint64_t chunk = L.bucket_cap * buckets / 5 * 4 * (uint64_t)rounds;
     L.bucket_chunk = std::max<uint64_t>(kRangeTile, chunk / kRangeTile * kRangeTile);
   }
+  if (L.o_regions) L.n_regions = 0;  // the ordered first pass applies the inserts by region itself
   L.bfill = at;
   if (L.n_regions) at += align_up(((uint64_t)L.n_regions * L.n_sub + 1) * 128);
   L.brecs = at;
   if (L.n_regions) at += align_up(L.bucket_cap * L.n_regions * L.n_sub * 8);
+  L.rplane = L.ohist = L.ostart = L.ofill = L.orecs = L.odec = L.ometa = at;
+  if (L.o_regions) {
+    const uint64_t R = L.o_regions;
+    L.rplane = at;
+    at += align_up(m + 64);
+    L.ohist = at;
+    at += align_up((uint64_t)rounds * R * 4);
+    L.ostart = at;
+    at += align_up((R + 1) * 8);
+    L.ofill = at;
+    at += align_up(R * kOrdFillStride * 4);
+    L.orecs = at;
+    L.cands = at;
+    at += align_up(std::max<uint64_t>(L.o_rec_cap * 8, L.cand_cap * cand_record_bytes(k)));
+    L.odec = at;
+    at += align_up((L.o_rec_cap + 31) / 32 * 4);
+    L.ometa = at;
+    at += align_up(L.o_tiles * R * 4);
+  }
   // N splitting: N mask and boundary bitmap (one bit per base), per-chunk
   // boundary counts, the sorted boundaries and their ranks
   L.split = o.split_at_n;
@@ -271,6 +323,18 @@ RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_
     v.bucket_cap = L.bucket_cap;
     v.bucket_chunk = L.bucket_chunk;
   }
+  v.o_regions = L.o_regions;
+  if (L.o_regions) {
+    v.o_lg_region_words = L.o_lg_region_words;
+    v.rplane = reinterpret_cast<uint8_t*>(base + L.rplane);
+    v.o_hist = reinterpret_cast<uint32_t*>(base + L.ohist);
+    v.o_start = reinterpret_cast<uint64_t*>(base + L.ostart);
+    v.o_fill = reinterpret_cast<uint32_t*>(base + L.ofill);
+    v.o_recs = reinterpret_cast<uint64_t*>(base + L.orecs);
+    v.o_rec_cap = L.o_rec_cap;
+    v.o_dec = reinterpret_cast<uint32_t*>(base + L.odec);
+    v.o_meta = reinterpret_cast<uint32_t*>(base + L.ometa);
+  }
   v.tile_count = reinterpret_cast<uint32_t*>(base + L.tile_count);
   v.tile_prefix = reinterpret_cast<uint64_t*>(base + L.tile_prefix);
   v.n_tiles = L.n_tiles;
@@ -333,6 +397,7 @@ void twopaco_default_options(twopaco_options* opt) {
   opt->per_string_launches = 0;
   opt->bucket_inserts = 0;
   opt->launch_blocks_per_sm = 0;
+  opt->ordered_first_pass = 0;
 }
 
 const char* twopaco_strerror(int code) {
@@ -596,6 +661,8 @@ int stats_from_header(const DevHeader& h, twopaco_stats* stats) {
   stats->bad_base_index = h.bad_inv ? ~h.bad_inv : ~0ull;
   stats->overflow = h.overflow | h.out_overflow;
   stats->timeout = h.timeout;
+  stats->ordered_rounds = h.ord_rounds;
+  stats->pad = 0;
   if (h.bad_inv) return TWOPACO_EBADBASE;
   if (h.timeout) return TWOPACO_ETIMEOUT;
   if (h.overflow || h.out_overflow) return TWOPACO_EOVERFLOW;

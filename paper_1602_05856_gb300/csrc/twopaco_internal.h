@@ -56,7 +56,10 @@ struct DevHeader {
   unsigned long long packed_words;
   unsigned long long input_digest;  // written by launch_digest
   unsigned int out_overflow;        // the output positions did not fit (the offsets are exact)
-  unsigned int pad1;
+  unsigned int ord_ok;              // region-ordered first pass: this round's records fit
+  unsigned int ord_ticket[2];       // region-ordered first pass: apply and probe work items
+  unsigned int ord_rounds;          // rounds the region-ordered kernels took
+  unsigned int pad2;
 };
 
 // Device view of one run: every buffer lives inside the workspace except the
@@ -112,6 +115,22 @@ struct RunView {
   uint64_t* bucket_recs;    // n_regions * n_sub buckets of bucket_cap records
   uint64_t bucket_cap;
   uint64_t bucket_chunk;    // positions per scatter-and-apply chunk (a multiple of kRangeTile)
+  // region-ordered first pass (o_regions > 0; class-map rounds): the class map
+  // also records every position's filter region (rplane) and counts the
+  // positions of every (class, region) pair (o_hist); a round then writes one
+  // 8-byte record per position of its class into the bucket of its region,
+  // applies the ORs and the probes bucket by bucket, and gathers the decisions
+  // back in position order
+  uint32_t o_regions;       // filter regions (buckets), at most kOrdMaxRegions
+  int o_lg_region_words;    // log2 of the 64-bit words per region (at most 22)
+  uint8_t* rplane;          // region of every position's k-mer, one byte per position
+  uint32_t* o_hist;         // rounds x o_regions position counts
+  uint64_t* o_start;        // o_regions + 1 bucket starts of the current round (multiples of 32)
+  uint32_t* o_fill;         // records claimed per bucket, one counter per 128 bytes
+  uint64_t* o_recs;         // o_rec_cap records
+  uint64_t o_rec_cap;
+  uint32_t* o_dec;          // one decision bit per record slot
+  uint32_t* o_meta;         // per tile and bucket: where the tile's records start in the bucket
   int use_desc;             // the insert leaves descriptors and the probe reads them
   uint64_t cand_cap;        // records the list can hold
   uint32_t* seg_count;      // candidates per list segment (one segment per probe warp)
@@ -142,6 +161,12 @@ constexpr uint32_t kMaxRegions = 1024;     // filter regions of bucketed inserts
 constexpr uint32_t kMinBuckets = 256;      // buckets of bucketed inserts, at least (sub-buckets per region)
 constexpr uint32_t kMaxBuckets = 1024;
 constexpr int kRegionWordsLog2 = 22;       // 32 MiB regions (words of 8 bytes)
+constexpr uint32_t kCmWindowPositions = 512;  // positions per class-map window (one warp's)
+constexpr int kOrdTileWindows = 32;        // region-ordered first pass: windows per tile
+constexpr uint64_t kOrdTile = (uint64_t)kOrdTileWindows * kCmWindowPositions;  // 16384 positions
+constexpr uint32_t kOrdMaxRegions = 256;   // buckets (filter regions), at most
+constexpr uint32_t kOrdMaxHist = 4096;     // rounds x regions, at most
+constexpr uint32_t kOrdFillStride = 32;    // bucket fill counters 128 bytes apart
 
 // Kernel launch helpers (twopaco_kernels.cu). Each returns the number of
 // kernels it launched, or -1 after a launch error.

@@ -692,12 +692,15 @@ __device__ __forceinline__ uint64_t table_insert(const RunView& v, uint64_t cap,
   uint64_t i = start;
   for (uint64_t probe = 0; probe < cap; ++probe, i = next_slot(i, cap)) {
     if (TS == 0) {
-      // one word: key << 9 | mask bits; never all ones for a key < 2^54. The CAS
-      // claims an empty slot in one round trip; when it fails it returns the
-      // word, which tells whether the slot holds this key and which bits it has
+      // one word: key << 9 | mask bits; never all ones for a key < 2^54. A
+      // plain load first: most candidates meet their k-mer already in the
+      // table, and a random load costs less than a random atomic
       unsigned long long* s = static_cast<unsigned long long*>(v.table) + i;
-      const unsigned long long cur = atomicCAS(s, kEmpty, (key.lo << kMaskBits) | bits);
-      if (cur == kEmpty) return i;
+      unsigned long long cur = __ldcg(s);
+      if (cur == kEmpty) {
+        cur = atomicCAS(s, kEmpty, (key.lo << kMaskBits) | bits);
+        if (cur == kEmpty) return i;
+      }
       if ((cur >> kMaskBits) != key.lo) continue;
       if ((cur & bits) != bits) atomicOr(s, (unsigned long long)bits);
       return i;
@@ -1429,21 +1432,45 @@ __device__ __forceinline__ uint32_t class_of_bin(const uint32_t* cuts, int round
   return (uint32_t)lo;
 }
 
-template <int KW>
+// Filter region of a k-mer's word (region-ordered first pass).
+__device__ __forceinline__ uint32_t ord_region(const RunView& v, uint64_t H, uint64_t G) {
+  return (uint32_t)(filter_index(v, H, G) >> v.o_lg_region_words);
+}
+
+// ORD: also the region plane (the filter region of every position's k-mer)
+// and the positions of every (class, region) pair, counted per block in
+// shared memory and added to o_hist at the end.
+template <int KW, bool ORD>
 __global__ void __launch_bounds__(kBlock) class_map_kernel(RunView v) {
   __shared__ uint32_t cuts_s[kMaxMapRounds + 1];
+  __shared__ uint32_t hist_s[ORD ? kOrdMaxHist : 1];
   for (int i = threadIdx.x; i <= v.rounds; i += kBlock) cuts_s[i] = v.cuts[i];
+  const uint32_t R = v.o_regions, nh = ORD ? (uint32_t)v.rounds * R : 0u;
+  if (ORD)
+    for (uint32_t i = threadIdx.x; i < nh; i += kBlock) hist_s[i] = 0;
   __syncthreads();
   const uint64_t stride = (uint64_t)gridDim.x * kBlock * kInsertR;
   for (uint64_t p0 = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) * kInsertR; p0 < v.m; p0 += stride) {
     uint32_t w[4] = {0x80808080u, 0x80808080u, 0x80808080u, 0x80808080u};
+    uint32_t r[4] = {0u, 0u, 0u, 0u};
     walk<KW, kInsertR>(v, p0, [&](int i, uint64_t, bool valid, const auto& oc) {
       if (!valid) return;
-      const uint32_t c = class_of_bin(cuts_s, v.rounds, (uint32_t)oc.H & v.qmask) |
-                         (oc.sentinel ? kCmSentinel : 0u);
+      const uint32_t cls = class_of_bin(cuts_s, v.rounds, (uint32_t)oc.H & v.qmask);
+      const uint32_t c = cls | (oc.sentinel ? kCmSentinel : 0u);
       w[i >> 2] = (w[i >> 2] & ~(0xFFu << (8 * (i & 3)))) | (c << (8 * (i & 3)));
+      if (ORD) {
+        const uint32_t reg = ord_region(v, oc.H, second_hash(oc.H));
+        r[i >> 2] |= reg << (8 * (i & 3));
+        atomicAdd(hist_s + cls * R + reg, 1u);
+      }
     });
     *reinterpret_cast<uint4*>(v.cmap + p0) = make_uint4(w[0], w[1], w[2], w[3]);
+    if (ORD) *reinterpret_cast<uint4*>(v.rplane + p0) = make_uint4(r[0], r[1], r[2], r[3]);
+  }
+  if (ORD) {
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nh; i += kBlock)
+      if (hist_s[i]) atomicAdd(v.o_hist + i, hist_s[i]);
   }
 }
 
@@ -1483,10 +1510,16 @@ __device__ __forceinline__ uint32_t compact_window(const RunView& v, uint64_t wb
   return __shfl_sync(0xffffffffu, inc, 31);
 }
 
+// The region-ordered kernels take the current round (its records fit).
+__device__ __forceinline__ bool ordered_round(const RunView& v) {
+  return v.o_regions && *reinterpret_cast<volatile const unsigned int*>(&v.hdr->ord_ok);
+}
+
 // Algorithm 1, insert loop, first pass, over this round's class only.
 template <int KW, int HB, bool BKT = false>
 __global__ void __launch_bounds__(kBlock) pass1_insert_cm_kernel(RunView v, int round) {
   __shared__ uint16_t idx_s[kBlock / 32][kCmWindow];
+  if (ordered_round(v)) return;  // the region-ordered kernels take this round
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint16_t* idx = idx_s[wid];
   const uint64_t stride = (uint64_t)gridDim.x * kBlock * 16;
@@ -1517,6 +1550,7 @@ template <int KW, int HB>
 __global__ void __launch_bounds__(kBlock) pass1_probe_cm_kernel(RunView v, int round) {
   __shared__ uint16_t idx_s[kBlock / 32][kCmWindow];
   __shared__ uint32_t keep_s[kBlock / 32][kCmWindow / 32];
+  if (ordered_round(v)) return;  // the region-ordered kernels take this round
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint16_t* idx = idx_s[wid];
   uint32_t* keep_w = keep_s[wid];
@@ -1534,55 +1568,46 @@ __global__ void __launch_bounds__(kBlock) pass1_probe_cm_kernel(RunView v, int r
     uint32_t valid;
     const uint32_t n = compact_window(v, wbase, round, idx, &valid);
     valid_n += valid;
-    // two entries per lane and step: both k-mers are read and hashed and both
-    // filter loads issued before either is tested, so that a lane keeps two
-    // random loads in flight
-    for (uint32_t j0 = 0; j0 < n; j0 += 64) {
-      uint64_t G[2] = {0, 0}, g[2] = {0, 0}, word[2] = {0, 0};
-      uint32_t e[2] = {0, 0}, sentinel[2] = {0, 0};
-      bool have[2];
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const uint32_t j = j0 + 32 * u + lane;
-        have[u] = j < n;
-        if (!have[u]) continue;
-        e[u] = idx[j];
-        g[u] = wbase + (e[u] & 511u);
-        sentinel[u] = (e[u] >> 9) & 1u;
-        OccT<KW> oc;
-        read_listed<KW>(v, g[u], sentinel[u], &oc);
-        G[u] = second_hash(oc.H);
-        if (!sentinel[u]) word[u] = __ldcg(filter_word(v, oc.H, G[u]));
+    for (uint32_t j0 = 0; j0 < n; j0 += 32) {
+      const uint32_t j = j0 + lane;
+      bool keep = false;
+      uint64_t G = 0, g = 0;
+      uint32_t sentinel = 0;
+      if (j < n) {
+        const uint32_t e = idx[j];
+        g = wbase + (e & 511u);
+        sentinel = (e >> 9) & 1u;
+        if (sentinel) {
+          keep = true;
+          OccT<KW> oc;
+          read_listed<KW>(v, g, true, &oc);
+          G = second_hash(oc.H);
+        } else {
+          OccT<KW> oc;
+          read_listed<KW>(v, g, false, &oc);
+          G = second_hash(oc.H);
+          const uint64_t word = __ldcg(filter_word(v, oc.H, G));
+          const uint32_t pres = present_items<HB>(G, word, v.hashes);
+          keep = (pres >> 16) || __popc(pres & 0xFFFFu) >= 2;
+        }
+        if (keep) atomicOr(keep_w + ((e & 511u) >> 5), 1u << (e & 31u));
       }
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        bool keep = false;
-        if (have[u]) {
-          if (sentinel[u]) {
-            keep = true;
-          } else {
-            const uint32_t pres = present_items<HB>(G[u], word[u], v.hashes);
-            keep = (pres >> 16) || __popc(pres & 0xFFFFu) >= 2;
-          }
-          if (keep) atomicOr(keep_w + ((e[u] & 511u) >> 5), 1u << (e[u] & 31u));
-        }
-        if (v.partial) {
-          kept += keep;
-          continue;
-        }
-        const uint32_t row = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-          const uint64_t x = (G[u] * 0xff51afd7ed558ccdull) >> (64 - v.lc_log2);
-          atomicOr(v.lc_bits + (x >> 5), 1u << (x & 31));
-          const uint64_t at = seg_used + __popc(row & below);
-          if (at < v.seg_cap) {
-            if (v.narrow) seg32[at] = (uint32_t)g[u] | (sentinel[u] << 31);
-            else seg[at] = g[u] | ((uint64_t)sentinel[u] << 63);
-          }
-          ++kept;
-        }
-        seg_used += __popc(row);
+      if (v.partial) {
+        kept += keep;
+        continue;
       }
+      const uint32_t row = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        const uint64_t x = (G * 0xff51afd7ed558ccdull) >> (64 - v.lc_log2);
+        atomicOr(v.lc_bits + (x >> 5), 1u << (x & 31));
+        const uint64_t at = seg_used + __popc(row & below);
+        if (at < v.seg_cap) {
+          if (v.narrow) seg32[at] = (uint32_t)g | (sentinel << 31);
+          else seg[at] = g | ((uint64_t)sentinel << 63);
+        }
+        ++kept;
+      }
+      seg_used += __popc(row);
     }
     __syncwarp();
     if (lane < kCmWindow / 32) {
@@ -1595,6 +1620,403 @@ __global__ void __launch_bounds__(kBlock) pass1_probe_cm_kernel(RunView v, int r
       }
     }
     __syncwarp();
+  }
+  if (lane == 0) {
+    v.seg_count[warp_id] = (uint32_t)(seg_used < v.seg_cap ? seg_used : v.seg_cap);
+    if (seg_used > v.seg_cap) v.hdr->cand_overflow = 1;
+  }
+  block_add(kept, &v.hdr->pass1_kept);
+  block_add(kept, v.partial ? &v.hdr->pass2_kept : &v.hdr->round_kept);
+  if (round == v.count_round) block_add(valid_n, &v.hdr->positions);
+}
+
+// ---------------------------------------------------------------------------
+// Region-ordered first pass (class-map rounds). A filter far beyond L2 takes
+// every random OR and every random probe at DRAM's random-access rate (about
+// 64 bytes moved per 8-byte access). Here a round instead writes one 8-byte
+// record per position of its class into the bucket of the position's filter
+// region (at most 2^22 words: 32 MiB, which L2 holds), applies the ORs and
+// then the probes bucket by bucket -- so that the random accesses of a region
+// all hit L2 -- and gathers the probe's decisions back in position order.
+//
+// Buckets: the class map counted the positions of every (class, region)
+// pair, so a round's buckets are laid out exactly (each a multiple of 32
+// slots). Tiles: kOrdTile consecutive positions, each warp of the block
+// taking kOrdTile / 8 of them (kOrdTileWindows / 8 windows) in order. A
+// tile's records for a bucket are consecutive in the bucket: the tile claims
+// their room with one atomic per bucket and records where it starts
+// (o_meta); a member's place in that room is its rank among the tile's
+// members of the same bucket in position order (warps in order, then windows,
+// then positions), which the gather recomputes from the class and region
+// planes to find the member's decision bit.
+//
+// A record: bits 0-21 the word within its region, 22-51 the bits 32-61 of G
+// (the bit bases of up to 6 bits per item), 52-56 and 57-61 the items (two
+// for a palindrome's orientations), bit 62 the sentinel flag.
+// ---------------------------------------------------------------------------
+
+constexpr int kOrdWarpWindows = kOrdTileWindows / (kBlock / 32);  // windows per warp and tile
+constexpr uint32_t kOrdPiece = 4096;  // records per apply or probe work item (a multiple of 32)
+constexpr unsigned long long kOrdSentinel = 1ull << 62;
+
+// compact_window with the region of every listed position in reg[0 .. n);
+// the planes are read through L2 (the tile reads them twice).
+__device__ __forceinline__ uint32_t compact_window_ord(const RunView& v, uint64_t wbase, int round, uint16_t* idx,
+                                                       uint8_t* reg, uint32_t* valid) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t p0 = wbase + 16 * (uint64_t)lane;
+  uint4 q = make_uint4(0x80808080u, 0x80808080u, 0x80808080u, 0x80808080u);
+  uint4 rq = make_uint4(0u, 0u, 0u, 0u);
+  if (p0 < v.m) {
+    q = __ldcg(reinterpret_cast<const uint4*>(v.cmap + p0));
+    rq = __ldcg(reinterpret_cast<const uint4*>(v.rplane + p0));
+  }
+  const uint32_t part[4] = {q.x, q.y, q.z, q.w};
+  const uint32_t rpart[4] = {rq.x, rq.y, rq.z, rq.w};
+  const uint32_t want = (uint32_t)round * 0x01010101u;
+  uint32_t act = 0, sent = 0, val = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    act |= byte_bits(__vcmpeq4(part[c] & 0xBFBFBFBFu, want)) << (4 * c);
+    sent |= byte_bits(__vcmpeq4(part[c] & 0x40404040u, 0x40404040u)) << (4 * c);
+    val |= byte_bits(__vcmpeq4(part[c] & 0x80808080u, 0u)) << (4 * c);
+  }
+  const uint32_t n = __popc(act);
+  uint32_t inc = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  uint32_t at = inc - n;
+  while (act) {
+    const uint32_t i = __ffs(act) - 1;
+    act &= act - 1;
+    idx[at] = (uint16_t)((16 * lane + i) | (((sent >> i) & 1u) << 9));
+    reg[at] = (uint8_t)(rpart[i >> 2] >> (8 * (i & 3)));
+    ++at;
+  }
+  *valid = __popc(val);
+  __syncwarp();
+  return __shfl_sync(0xffffffffu, inc, 31);
+}
+
+// The per-warp starts of a tile's members in every bucket, relative to the
+// bucket's start: slot_s[w][b] = tile's room in bucket b + members of b in
+// warps before w. claim: the tile claims its room (the scatter) and records
+// it in o_meta; else the room is read from o_meta (the gather).
+template <bool CLAIM>
+__device__ __forceinline__ void ord_tile_slots(const RunView& v, int round, uint64_t tile, uint64_t tbase,
+                                               uint16_t (*idx_s)[kCmWindow], uint8_t (*reg_s)[kCmWindow],
+                                               uint32_t (*slot_s)[kOrdMaxRegions]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t R = v.o_regions;
+  for (uint32_t b = lane; b < R; b += 32) slot_s[wid][b] = 0;
+  __syncwarp();
+  for (int q = 0; q < kOrdWarpWindows; ++q) {
+    const uint64_t wbase = tbase + (uint64_t)(wid * kOrdWarpWindows + q) * kCmWindow;
+    if (wbase >= v.p_end) break;
+    uint32_t valid;
+    const uint32_t n = compact_window_ord(v, wbase, round, idx_s[wid], reg_s[wid], &valid);
+    for (uint32_t j = lane; j < n; j += 32) atomicAdd(&slot_s[wid][reg_s[wid][j]], 1u);
+    __syncwarp();
+  }
+  __syncthreads();
+  for (uint32_t b = threadIdx.x; b < R; b += kBlock) {
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kBlock / 32; ++w) {
+      const uint32_t c = slot_s[w][b];
+      slot_s[w][b] = run;
+      run += c;
+    }
+    uint32_t room;
+    if (CLAIM) {
+      room = run ? atomicAdd(v.o_fill + (uint64_t)b * kOrdFillStride, run) : 0u;
+      v.o_meta[tile * R + b] = room;
+    } else {
+      room = __ldg(v.o_meta + tile * R + b);
+    }
+#pragma unroll
+    for (int w = 0; w < kBlock / 32; ++w) slot_s[w][b] += room;
+  }
+  __syncthreads();
+}
+
+// The slot of every listed member of a window, relative to its bucket's
+// start, in position order: its rank among the warp's earlier members of the
+// same bucket plus the warp's start in that bucket. Lanes take the members
+// j0 + lane; returns the member's bucket (or 0xFFFF past n).
+__device__ __forceinline__ uint32_t ord_member_slot(uint32_t* slot_w, const uint8_t* reg, uint32_t j, uint32_t n,
+                                                    uint32_t* slot) {
+  const int lane = threadIdx.x & 31;
+  const bool act = j < n;
+  const uint32_t b = act ? reg[j] : 0xFFFFu;
+  const unsigned peers = __match_any_sync(0xffffffffu, b);
+  if (act) *slot = slot_w[b] + __popc(peers & ((1u << lane) - 1u));
+  __syncwarp();
+  if (act && lane == __ffs(peers) - 1) slot_w[b] += __popc(peers);
+  __syncwarp();
+  return b;
+}
+
+// Before a round's scatter: the buckets' starts (each a multiple of 32), the
+// fill counters and work tickets cleared, and whether the round's records fit
+// (else the direct kernels take the round). One block.
+__global__ void __launch_bounds__(kBlock) ord_setup_kernel(RunView v, int round) {
+  const uint32_t R = v.o_regions;
+  for (uint32_t b = threadIdx.x; b < R; b += kBlock) v.o_fill[(uint64_t)b * kOrdFillStride] = 0;
+  if (threadIdx.x == 0) {
+    uint64_t at = 0;
+    bool fits = true;
+    for (uint32_t b = 0; b < R; ++b) {
+      v.o_start[b] = at;
+      const uint64_t n = v.o_hist[(uint64_t)round * R + b];
+      fits = fits && n < (1ull << 32);  // slots within a bucket are 32-bit
+      at += (n + 31) & ~31ull;
+    }
+    v.o_start[R] = at;
+    v.hdr->ord_ok = (fits && at <= v.o_rec_cap) ? 1u : 0u;
+    v.hdr->ord_rounds += v.hdr->ord_ok;
+    v.hdr->ord_ticket[0] = 0;
+    v.hdr->ord_ticket[1] = 0;
+  }
+}
+
+// Algorithm 1, insert loop, first pass, over this round's class: one record
+// per position into the bucket of its filter region (tiles grid-strided).
+template <int KW, int HB>
+__global__ void __launch_bounds__(kBlock) ord_scatter_kernel(RunView v, int round) {
+  __shared__ uint16_t idx_s[kBlock / 32][kCmWindow];
+  __shared__ uint8_t reg_s[kBlock / 32][kCmWindow];
+  __shared__ uint32_t slot_s[kBlock / 32][kOrdMaxRegions];
+  __shared__ unsigned long long start_s[kOrdMaxRegions];
+  if (!ordered_round(v)) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t R = v.o_regions;
+  for (uint32_t b = threadIdx.x; b < R; b += kBlock) start_s[b] = v.o_start[b];
+  const uint64_t local_mask = (1ull << v.o_lg_region_words) - 1ull;
+  const uint64_t n_tiles = (v.p_end - v.p_begin + kOrdTile - 1) / kOrdTile;
+  for (uint64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const uint64_t tbase = v.p_begin + t * kOrdTile;
+    ord_tile_slots<true>(v, round, t, tbase, idx_s, reg_s, slot_s);
+    for (int q = 0; q < kOrdWarpWindows; ++q) {
+      const uint64_t wbase = tbase + (uint64_t)(wid * kOrdWarpWindows + q) * kCmWindow;
+      if (wbase >= v.p_end) break;
+      uint32_t valid;
+      const uint32_t n = compact_window_ord(v, wbase, round, idx_s[wid], reg_s[wid], &valid);
+      for (uint32_t j0 = 0; j0 < n; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        uint32_t slot = 0;
+        const uint32_t b = ord_member_slot(slot_s[wid], reg_s[wid], j, n, &slot);
+        if (j < n) {
+          const uint32_t e = idx_s[wid][j];
+          const bool sentinel = (e >> 9) & 1u;
+          OccT<KW> oc;
+          read_listed<KW>(v, wbase + (e & 511u), sentinel, &oc);
+          const uint64_t G = second_hash(oc.H);
+          const uint32_t j1 = __ffs(oc.items) - 1, j2 = 31 - __clz(oc.items);
+          const uint64_t word = filter_index(v, oc.H, G);
+          v.o_recs[start_s[b] + slot] = (word & local_mask) | (((G >> 32) & 0x3FFFFFFFull) << 22) |
+                                        ((uint64_t)j1 << 52) | ((uint64_t)j2 << 57) |
+                                        (sentinel ? kOrdSentinel : 0ull);
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();  // slot_s and the windows' lists serve the next tile
+  }
+}
+
+// Work items of kOrdPiece records, taken in bucket order from a ticket, so
+// that the blocks in flight work on one or two regions at a time. first_s[b]:
+// the first item of bucket b (first_s[R]: the number of items).
+__device__ __forceinline__ void ord_items(const RunView& v, uint32_t* first_s) {
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (uint32_t b = 0; b < v.o_regions; ++b) {
+      first_s[b] = acc;
+      const uint64_t n = __ldcg(v.o_fill + (uint64_t)b * kOrdFillStride);
+      acc += (uint32_t)((n + kOrdPiece - 1) / kOrdPiece);
+    }
+    first_s[v.o_regions] = acc;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t ord_item_bucket(const uint32_t* first_s, uint32_t R, uint32_t item) {
+  uint32_t lo = 0, hi = R;  // the bucket b with first_s[b] <= item < first_s[b + 1]
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (first_s[mid] <= item) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// The ORs of the round's records, bucket by bucket (four records in flight
+// per thread).
+template <int HB>
+__global__ void __launch_bounds__(kBlock) ord_or_kernel(RunView v) {
+  __shared__ uint32_t first_s[kOrdMaxRegions + 1];
+  __shared__ uint32_t item_s;
+  if (!ordered_round(v)) return;
+  ord_items(v, first_s);
+  const uint32_t R = v.o_regions, total = first_s[R];
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(&v.hdr->ord_ticket[0], 1u);
+    __syncthreads();
+    const uint32_t item = item_s;
+    __syncthreads();
+    if (item >= total) break;
+    const uint32_t b = ord_item_bucket(first_s, R, item);
+    const uint64_t n = __ldcg(v.o_fill + (uint64_t)b * kOrdFillStride);
+    const uint64_t i0 = (uint64_t)(item - first_s[b]) * kOrdPiece, i1 = min(i0 + kOrdPiece, n);
+    const uint64_t* recs = v.o_recs + __ldg(v.o_start + b);
+    unsigned long long* region = v.filter + ((uint64_t)b << v.o_lg_region_words);
+    for (uint64_t i = i0 + threadIdx.x; i < i1; i += 4 * kBlock) {
+      uint64_t r[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) r[u] = i + u * kBlock < i1 ? __ldcs(recs + i + u * kBlock) : ~0ull;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (r[u] == ~0ull) continue;
+        const uint64_t G = ((r[u] >> 22) & 0x3FFFFFFFull) << 32;  // the bits bit_base reads for u < 6
+        const ItemPattern pat = item_pattern<HB>(G, v.hashes);
+        const uint32_t j1 = (uint32_t)(r[u] >> 52) & 31u, j2 = (uint32_t)(r[u] >> 57) & 31u;
+        uint64_t m = item_bits(pat, j1);
+        if (j2 != j1) m |= item_bits(pat, j2);
+        atomicOr(region + (r[u] & 0x3FFFFFull), (unsigned long long)m);
+      }
+    }
+  }
+}
+
+// Algorithm 1, probe loop, first pass, over the round's records, bucket by
+// bucket: a record's decision (its k-mer is a candidate: a sentinel, or its
+// filter word holds a sentinel item or two distinct items) goes to its slot's
+// bit; the linear-counting bit of every candidate is set from the k-mer's
+// filter word index and bit bases.
+template <int HB>
+__global__ void __launch_bounds__(kBlock) ord_probe_kernel(RunView v) {
+  __shared__ uint32_t first_s[kOrdMaxRegions + 1];
+  __shared__ uint32_t item_s;
+  if (!ordered_round(v)) return;
+  ord_items(v, first_s);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t R = v.o_regions, total = first_s[R];
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(&v.hdr->ord_ticket[1], 1u);
+    __syncthreads();
+    const uint32_t item = item_s;
+    __syncthreads();
+    if (item >= total) break;
+    const uint32_t b = ord_item_bucket(first_s, R, item);
+    const uint64_t n = __ldcg(v.o_fill + (uint64_t)b * kOrdFillStride);
+    const uint64_t i0 = (uint64_t)(item - first_s[b]) * kOrdPiece, i1 = min(i0 + kOrdPiece, n);
+    const uint64_t start = __ldg(v.o_start + b);  // a multiple of 32, as is i0
+    const uint64_t* recs = v.o_recs + start;
+    const uint64_t region = (uint64_t)b << v.o_lg_region_words;
+    for (uint64_t w0 = i0 + 32 * wid; w0 < i1; w0 += kBlock) {
+      const uint64_t i = w0 + lane;
+      bool keep = false;
+      if (i < i1) {
+        const uint64_t r = __ldcs(recs + i);
+        const uint64_t word_index = region | (r & 0x3FFFFFull);
+        if (r & kOrdSentinel) {
+          keep = true;
+        } else {
+          const uint64_t G = ((r >> 22) & 0x3FFFFFFFull) << 32;
+          const uint64_t word = __ldcg(v.filter + word_index);
+          const uint32_t pres = present_items<HB>(G, word, v.hashes);
+          keep = (pres >> 16) || __popc(pres & 0xFFFFu) >= 2;
+        }
+        if (keep && !v.partial) {
+          const uint64_t id = (word_index << 30) | ((r >> 22) & 0x3FFFFFFFull);
+          const uint64_t x = (id * 0xff51afd7ed558ccdull) >> (64 - v.lc_log2);
+          atomicOr(v.lc_bits + (x >> 5), 1u << (x & 31));
+        }
+      }
+      const uint32_t row = __ballot_sync(0xffffffffu, keep);
+      if (lane == 0) v.o_dec[(start + w0) >> 5] = row;
+    }
+  }
+}
+
+// The probe loop's outputs in position order: every member of the round's
+// class takes its decision from its record's slot (found as in the scatter);
+// C_temp words, the candidate list segment of the warp and the counts are as
+// pass1_probe_cm_kernel writes them.
+__global__ void __launch_bounds__(kBlock) ord_gather_kernel(RunView v, int round) {
+  __shared__ uint16_t idx_s[kBlock / 32][kCmWindow];
+  __shared__ uint8_t reg_s[kBlock / 32][kCmWindow];
+  __shared__ uint32_t slot_s[kBlock / 32][kOrdMaxRegions];
+  __shared__ unsigned long long start_s[kOrdMaxRegions];
+  __shared__ uint32_t keep_s[kBlock / 32][kCmWindow / 32];
+  if (!ordered_round(v)) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t R = v.o_regions;
+  for (uint32_t b = threadIdx.x; b < R; b += kBlock) start_s[b] = v.o_start[b];
+  uint32_t* keep_w = keep_s[wid];
+  const uint32_t below = (1u << lane) - 1u;
+  unsigned long long kept = 0, valid_n = 0;
+  const uint32_t warp_id = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  uint64_t* seg = v.cands + (uint64_t)warp_id * v.seg_cap;
+  uint32_t* seg32 = reinterpret_cast<uint32_t*>(v.cands) + (uint64_t)warp_id * v.seg_cap;
+  uint64_t seg_used = 0;
+  if (lane < kCmWindow / 32) keep_w[lane] = 0;
+  __syncwarp();
+  const uint64_t n_tiles = (v.p_end - v.p_begin + kOrdTile - 1) / kOrdTile;
+  for (uint64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const uint64_t tbase = v.p_begin + t * kOrdTile;
+    ord_tile_slots<false>(v, round, t, tbase, idx_s, reg_s, slot_s);
+    for (int q = 0; q < kOrdWarpWindows; ++q) {
+      const uint64_t wbase = tbase + (uint64_t)(wid * kOrdWarpWindows + q) * kCmWindow;
+      if (wbase >= v.p_end) break;
+      uint32_t valid;
+      const uint32_t n = compact_window_ord(v, wbase, round, idx_s[wid], reg_s[wid], &valid);
+      valid_n += valid;
+      for (uint32_t j0 = 0; j0 < n; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        uint32_t slot = 0;
+        const uint32_t b = ord_member_slot(slot_s[wid], reg_s[wid], j, n, &slot);
+        bool keep = false;
+        uint32_t e = 0;
+        if (j < n) {
+          e = idx_s[wid][j];
+          const uint64_t s = start_s[b] + slot;
+          keep = (__ldg(v.o_dec + (s >> 5)) >> (s & 31)) & 1u;
+          if (keep) atomicOr(keep_w + ((e & 511u) >> 5), 1u << (e & 31u));
+        }
+        if (v.partial) {
+          kept += keep;
+          continue;
+        }
+        const uint32_t row = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+          const uint64_t g = wbase + (e & 511u);
+          const uint32_t sentinel = (e >> 9) & 1u;
+          const uint64_t at = seg_used + __popc(row & below);
+          if (at < v.seg_cap) {
+            if (v.narrow) seg32[at] = (uint32_t)g | (sentinel << 31);
+            else seg[at] = g | ((uint64_t)sentinel << 63);
+          }
+          ++kept;
+        }
+        seg_used += __popc(row);
+      }
+      __syncwarp();
+      if (lane < kCmWindow / 32) {
+        const uint64_t w = (wbase >> 5) + lane;
+        const uint32_t word = keep_w[lane];
+        keep_w[lane] = 0;
+        if (w < v.bitmap_words) {
+          v.ctemp[w] = word;
+          if (v.partial) v.cfinal[w] |= word;  // rounds own disjoint positions; one writer per word
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
   }
   if (lane == 0) {
     v.seg_count[warp_id] = (uint32_t)(seg_used < v.seg_cap ? seg_used : v.seg_cap);
@@ -1639,7 +2061,7 @@ __global__ void __launch_bounds__(kBlock) table_setup_kernel(RunView v) {
   const unsigned long long set = *(volatile unsigned long long*)&v.hdr->lc_set;
   const double M = (double)(1ull << v.lc_log2);
   unsigned long long distinct = kept;
-  if ((double)set < 0.9 * M) {
+  if ((double)set < M - M / 1024.0) {  // at least 1/1024 of the bits still clear: about 7 per bit
     const double est = -M * log1p(-(double)set / M);
     const unsigned long long e = (unsigned long long)(est * 1.1) + 64ull;
     if (e < distinct) distinct = e;
@@ -1926,35 +2348,39 @@ constexpr uint32_t kSpinLimit = 1u << 22;
 __global__ void __launch_bounds__(kBlock) emit_kernel(RunView v) {
   __shared__ unsigned long long tile_s, prefix_s, total_s;
   __shared__ uint32_t before_s[kEmitTileWords];  // junctions of the tile before each of its words
+  __shared__ uint32_t warp_s[kBlock / 32];
+  __shared__ uint16_t stage_s[kBlock / 32][32 * 32];  // one batch's junctions: bit offsets within the tile
   __shared__ uint64_t t_lo_s, t_hi_s;
   volatile unsigned long long* status =
       reinterpret_cast<volatile unsigned long long*>(v.tile_prefix);  // n_tiles entries, zeroed per run
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (;;) {
     if (threadIdx.x == 0) tile_s = atomicAdd(&v.hdr->emit_ticket, 1ull);
     __syncthreads();
     const uint64_t tile = tile_s;
     if (tile >= v.n_tiles) break;
-    // thread t owns the kEmitWordsPerThread consecutive words starting at word
-    // t * kEmitWordsPerThread of the tile: one scan gives every thread its start
+    // warp w takes the tile's words [256 w, 256 w + 256) in kEmitWordsPerThread
+    // batches of 32 consecutive words, one word per lane
     const uint64_t tile_base = tile * kEmitTileWords;
-    const uint64_t base = tile_base + (uint64_t)threadIdx.x * kEmitWordsPerThread;
+    const uint32_t wbase = (uint32_t)wid * 32 * kEmitWordsPerThread;
     uint32_t words[kEmitWordsPerThread];
-    if (base + kEmitWordsPerThread <= v.bitmap_words) {
-      const uint4 a = __ldcg(reinterpret_cast<const uint4*>(v.cfinal + base));
-      const uint4 b = __ldcg(reinterpret_cast<const uint4*>(v.cfinal + base + 4));
-      words[0] = a.x; words[1] = a.y; words[2] = a.z; words[3] = a.w;
-      words[4] = b.x; words[5] = b.y; words[6] = b.z; words[7] = b.w;
-    } else {
-#pragma unroll
-      for (int q = 0; q < kEmitWordsPerThread; ++q)
-        words[q] = (base + q < v.bitmap_words) ? __ldcg(v.cfinal + base + q) : 0u;
-    }
     uint32_t c = 0;
 #pragma unroll
-    for (int q = 0; q < kEmitWordsPerThread; ++q) c += __popc(words[q]);
-    uint32_t tot;
-    const uint32_t before = block_exclusive_scan(c, &tot);
+    for (int q = 0; q < kEmitWordsPerThread; ++q) {
+      const uint64_t w = tile_base + wbase + 32 * q + lane;
+      words[q] = w < v.bitmap_words ? __ldcg(v.cfinal + w) : 0u;
+      c += __popc(words[q]);
+    }
+    c = warp_sum(c);
+    if (lane == 0) warp_s[wid] = c;
+    __syncthreads();
     if (threadIdx.x == 0) {
+      uint32_t tot = 0;
+      for (int w = 0; w < kBlock / 32; ++w) {
+        const uint32_t x = warp_s[w];
+        warp_s[w] = tot;
+        tot += x;
+      }
       total_s = tot;
       unsigned long long prefix = 0;
       if (tile == 0) {
@@ -1985,21 +2411,39 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(RunView v) {
       prefix_s = prefix;
     }
     __syncthreads();
-    uint64_t at = prefix_s + before;
+    // batch by batch: every lane expands its word into the warp's stage at its
+    // exclusive prefix, then the warp writes the batch with consecutive lanes
+    // on consecutive entries
+    uint32_t at = warp_s[wid];  // junctions of the tile before this batch
+    uint16_t* stage = stage_s[wid];
     Bounds bd{1, 0};
 #pragma unroll
     for (int q = 0; q < kEmitWordsPerThread; ++q) {
-      before_s[threadIdx.x * kEmitWordsPerThread + q] = (uint32_t)(at - prefix_s);
-      uint32_t bits = words[q];
-      const uint64_t w = base + q;
+      const uint32_t n = __popc(words[q]);
+      uint32_t inc = n;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      const uint32_t word_at = wbase + 32 * q + lane;  // the word's index within the tile
+      before_s[word_at] = at + inc - n;
+      uint32_t bits = words[q], i = inc - n;
       while (bits) {
         const uint32_t b = __ffs(bits) - 1;
         bits &= bits - 1;
-        const uint64_t g = w * 32 + b;
-        if (g < bd.start || g >= bd.end) bd = seq_bounds(v, g);
-        if (at < v.out_capacity) v.out_positions[at] = g - bd.start;
-        ++at;
+        stage[i++] = (uint16_t)(word_at * 32 + b);  // below 2^16: a tile is 65536 positions
       }
+      const uint32_t batch = __shfl_sync(0xffffffffu, inc, 31);
+      __syncwarp();
+      const uint64_t o0 = prefix_s + at;
+      for (uint32_t e = lane; e < batch; e += 32) {
+        const uint64_t g = tile_base * 32 + stage[e];
+        if (g < bd.start || g >= bd.end) bd = seq_bounds(v, g);
+        if (o0 + e < v.out_capacity) v.out_positions[o0 + e] = g - bd.start;
+      }
+      __syncwarp();
+      at += batch;
     }
     // out_offsets[t] (junctions before string t) for the strings that start in
     // this tile; the last tile also takes t = n_seqs (start m: the total)
@@ -2376,9 +2820,26 @@ int round_impl(const RunView& v, int round, cudaStream_t s, const Ranges* ranges
     return x;
   };
   int launched = 0;
-  // filters beyond L2: the inserts go through region buckets, chunk by chunk
+  // filters beyond L2: the region-ordered first pass (class-map rounds), or
+  // region buckets for the inserts alone, chunk by chunk
   constexpr bool kBktOk = HB <= 6;  // a record carries the bit bases of up to 6 bits per item
+  constexpr int HBO = kBktOk ? HB : 1;
   const bool bkt = kBktOk && v.n_regions > 0;
+  const bool ord = kBktOk && cm && v.o_regions > 0 && !ranges;
+  if (ord) {
+    {
+      Timed t("ord_scatter", s);
+      ord_setup_kernel<<<1, kBlock, 0, s>>>(v, round);
+      const uint64_t tiles = (v.p_end - v.p_begin + kOrdTile - 1) / kOrdTile;
+      ord_scatter_kernel<KW, HBO><<<grid_for(ord_scatter_kernel<KW, HBO>, kBlock, tiles * kBlock, v.blocks_per_sm),
+                                    kBlock, 0, s>>>(v, round);
+    }
+    {
+      Timed t("ord_or", s);
+      ord_or_kernel<HBO><<<grid_for(ord_or_kernel<HBO>, kBlock, ~0ull >> 1), kBlock, 0, s>>>(v);
+    }
+    launched += 3;
+  }
   {
     for (const auto& r : rs) {
       const uint64_t step = bkt ? v.bucket_chunk : r.second - r.first;
@@ -2421,25 +2882,34 @@ int round_impl(const RunView& v, int round, cudaStream_t s, const Ranges* ranges
     }
   }
   RunView pv = v;
-  {
-    Timed t("pass1_probe", s);
-    for (const auto& r : rs) {
-      pv = part(r);
-      const uint64_t threads = (r.second - r.first + kProbeR - 1) / kProbeR;
-      // one candidate-list segment per probe warp
-      unsigned grid = cm     ? grid_for(pass1_probe_cm_kernel<KW, HB>, kBlock, (r.second - r.first + 15) / 16, v.blocks_per_sm)
-                      : desc ? grid_for(pass1_probe_desc_kernel<kDescOk ? HB : 1>, kBlock, threads, v.blocks_per_sm)
-                             : grid_for(pass1_probe_kernel<KW, RD, HB>, kBlock, threads, v.blocks_per_sm);
-      if (grid * (kBlock / 32) > kMaxSegments) grid = kMaxSegments / (kBlock / 32);
-      pv.n_segments = grid * (kBlock / 32);
-      // the list region holds cand_cap 8-byte records, or twice as many 32-bit
-      // ones; launched per string there is no list (pass 2 walks C_temp)
-      pv.seg_cap = ranges ? 0 : (v.narrow ? 2 * v.cand_cap : v.cand_cap) / pv.n_segments;
-      if (cm) pass1_probe_cm_kernel<KW, HB><<<grid, kBlock, 0, s>>>(pv, round);
-      else if (desc) pass1_probe_desc_kernel<kDescOk ? HB : 1><<<grid, kBlock, 0, s>>>(pv, round);
-      else pass1_probe_kernel<KW, RD, HB><<<grid, kBlock, 0, s>>>(pv, round);
-      ++launched;
+  for (const auto& r : rs) {
+    pv = part(r);
+    const uint64_t threads = (r.second - r.first + kProbeR - 1) / kProbeR;
+    // one candidate-list segment per probe warp
+    unsigned grid = cm     ? grid_for(pass1_probe_cm_kernel<KW, HB>, kBlock, (r.second - r.first + 15) / 16, v.blocks_per_sm)
+                    : desc ? grid_for(pass1_probe_desc_kernel<kDescOk ? HB : 1>, kBlock, threads, v.blocks_per_sm)
+                           : grid_for(pass1_probe_kernel<KW, RD, HB>, kBlock, threads, v.blocks_per_sm);
+    if (grid * (kBlock / 32) > kMaxSegments) grid = kMaxSegments / (kBlock / 32);
+    pv.n_segments = grid * (kBlock / 32);
+    // the list region holds cand_cap 8-byte records, or twice as many 32-bit
+    // ones; launched per string there is no list (pass 2 walks C_temp)
+    pv.seg_cap = ranges ? 0 : (v.narrow ? 2 * v.cand_cap : v.cand_cap) / pv.n_segments;
+    if (ord) {  // the gather's warps own the list segments, as the probe's would
+      {
+        Timed t("ord_probe", s);
+        ord_probe_kernel<HBO><<<grid_for(ord_probe_kernel<HBO>, kBlock, ~0ull >> 1), kBlock, 0, s>>>(v);
+      }
+      {
+        Timed t("ord_gather", s);
+        ord_gather_kernel<<<grid, kBlock, 0, s>>>(pv, round);
+      }
+      launched += 2;
     }
+    Timed t("pass1_probe", s);
+    if (cm) pass1_probe_cm_kernel<KW, HB><<<grid, kBlock, 0, s>>>(pv, round);
+    else if (desc) pass1_probe_desc_kernel<kDescOk ? HB : 1><<<grid, kBlock, 0, s>>>(pv, round);
+    else pass1_probe_kernel<KW, RD, HB><<<grid, kBlock, 0, s>>>(pv, round);
+    ++launched;
   }
   if (v.partial) return done(launched);  // the partially compacted graph: no second pass
   {
@@ -2500,8 +2970,15 @@ int launch_class_map(const RunView& v, cudaStream_t s) {
   if (v.k > 63) return launch_class_map_wide(v, s) < 0 ? -1 : done(1);
   Timed t("class_map", s);
   const uint64_t threads = (v.m + kInsertR - 1) / kInsertR;
-  if (v.k <= 31) class_map_kernel<1><<<grid_for(class_map_kernel<1>, kBlock, threads), kBlock, 0, s>>>(v);
-  else class_map_kernel<2><<<grid_for(class_map_kernel<2>, kBlock, threads), kBlock, 0, s>>>(v);
+  if (v.o_regions) {
+    if (cudaMemsetAsync(v.o_hist, 0, (uint64_t)v.rounds * v.o_regions * 4, s) != cudaSuccess) return -1;
+    if (v.k <= 31) class_map_kernel<1, true><<<grid_for(class_map_kernel<1, true>, kBlock, threads), kBlock, 0, s>>>(v);
+    else class_map_kernel<2, true><<<grid_for(class_map_kernel<2, true>, kBlock, threads), kBlock, 0, s>>>(v);
+  } else if (v.k <= 31) {
+    class_map_kernel<1, false><<<grid_for(class_map_kernel<1, false>, kBlock, threads), kBlock, 0, s>>>(v);
+  } else {
+    class_map_kernel<2, false><<<grid_for(class_map_kernel<2, false>, kBlock, threads), kBlock, 0, s>>>(v);
+  }
   return done(1);
 }
 
@@ -2557,7 +3034,7 @@ int launch_partition_count_wide(const RunView& v, cudaStream_t s) {
 int launch_class_map_wide(const RunView& v, cudaStream_t s) {
   Timed t("class_map", s);
   const uint64_t threads = (v.m + kInsertR - 1) / kInsertR;
-  class_map_kernel<4><<<grid_for(class_map_kernel<4>, kBlock, threads), kBlock, 0, s>>>(v);
+  class_map_kernel<4, false><<<grid_for(class_map_kernel<4, false>, kBlock, threads), kBlock, 0, s>>>(v);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 #endif  // TWOPACO_WIDE_ONLY

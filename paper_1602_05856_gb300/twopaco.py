@@ -40,14 +40,14 @@ class _Options(ctypes.Structure):
                 ("split_at_n", ctypes.c_int), ("run_capacity", ctypes.c_uint64),
                 ("wide_layout", ctypes.c_int), ("partial", ctypes.c_int),
                 ("per_string_launches", ctypes.c_int), ("bucket_inserts", ctypes.c_int),
-                ("launch_blocks_per_sm", ctypes.c_int)]
+                ("launch_blocks_per_sm", ctypes.c_int), ("ordered_first_pass", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
     _fields_ = [("positions", ctypes.c_uint64), ("pass1_marks", ctypes.c_uint64),
                 ("pass2_marks", ctypes.c_uint64), ("table_slots", ctypes.c_uint64),
                 ("bad_base_index", ctypes.c_uint64), ("overflow", ctypes.c_uint32),
-                ("timeout", ctypes.c_uint32)]
+                ("timeout", ctypes.c_uint32), ("ordered_rounds", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
 class _Edge(ctypes.Structure):
@@ -182,6 +182,7 @@ class Options:
     per_string_launches: bool = False  # every loop launched once per string (a baseline)
     bucket_inserts: int = 0   # first-pass ORs through region buckets: 0 auto (> 64 MiB), 1 always, 2 never
     launch_blocks_per_sm: int = 0  # launch shape of the pass kernels: resident blocks per SM (0: all)
+    ordered_first_pass: int = 0    # first pass in filter-region order: 0 auto (>= 1 GiB), 1 always, 2 never
 
     def _c(self) -> _Options:
         return _Options(int(self.hashes), int(bool(self.both_strands)), int(self.partition_bins),
@@ -189,7 +190,7 @@ class Options:
                         ctypes.c_void_p(int(self.cuda_stream) or None), int(bool(self.split_at_n)),
                         int(self.run_capacity), int(self.wide_layout), int(bool(self.partial)),
                         int(bool(self.per_string_launches)), int(self.bucket_inserts),
-                        int(self.launch_blocks_per_sm))
+                        int(self.launch_blocks_per_sm), int(self.ordered_first_pass))
 
 
 def _stats_dict(s: _Stats) -> Dict[str, int]:

@@ -200,3 +200,32 @@ def test_launch_shape_option_range():
         assert e.value.code == T.EINVAL
     assert T.twopaco_workspace_size(1000, 2, 25, 1 << 20, 1, T.Options(launch_blocks_per_sm=2)) == \
         T.twopaco_workspace_size(1000, 2, 25, 1 << 20, 1)
+
+
+def test_ordered_first_pass_layout():
+    """The region-ordered first pass: automatic for class-map runs with a filter of
+    1 GiB and more, forced on any class-map run, never without a class map, for
+    k > 63 or more than 6 bits per item; the option takes 0, 1 or 2."""
+    from paper_1602_05856_gb300 import build, twopaco as T
+    build.build()
+    for bad in (-1, 3):
+        with pytest.raises(T.TwopacoError) as e:
+            T.twopaco_workspace_size(1000, 2, 25, 1 << 20, 2, T.Options(ordered_first_pass=bad))
+        assert e.value.code == T.EINVAL
+
+    def ws(m, bits, rounds, o, k=25, h=4, **kw):
+        return T.twopaco_workspace_size(m, 8, k, bits, rounds, T.Options(hashes=h, ordered_first_pass=o, **kw))
+
+    big = 24_000_000_000
+    # a region byte per position and 8-byte records for a round and a quarter, which
+    # hold the candidate list (by default half a round of 8-byte records)
+    per_round = big // 4
+    assert ws(big, 1 << 36, 4, 0) - ws(big, 1 << 36, 4, 2) >= big + 8 * (per_round * 5 // 4) - 8 * (per_round // 2)
+    assert ws(big, 1 << 36, 4, 0) == ws(big, 1 << 36, 4, 1)
+    assert ws(35_000_000, 1 << 28, 4, 0) == ws(35_000_000, 1 << 28, 4, 2)   # 32 MiB: within L2
+    assert ws(35_000_000, 1 << 28, 4, 1) > ws(35_000_000, 1 << 28, 4, 2)    # forced
+    assert ws(35_000_000, 1 << 28, 1, 1) == ws(35_000_000, 1 << 28, 1, 2)   # one round: no class map
+    assert ws(35_000_000, 1 << 28, 4, 1, k=100) == ws(35_000_000, 1 << 28, 4, 2, k=100)
+    assert ws(35_000_000, 1 << 28, 4, 1, h=7) == ws(35_000_000, 1 << 28, 4, 2, h=7)
+    assert ws(35_000_000, 1 << 28, 4, 1, per_string_launches=True) == \
+        ws(35_000_000, 1 << 28, 4, 2, per_string_launches=True)
