@@ -73,7 +73,7 @@ struct Layout {
   uint32_t o_regions;  // region-ordered first pass (0: off)
   int o_lg_region_words;
   uint64_t o_rec_cap, o_tiles;
-  uint64_t rplane, ohist, ostart, ofill, orecs, odec, ometa;
+  uint64_t rplane, ohist, ostart, ofill, orecs, odec, ometa, otcount, otbase, otsum, operm;
   uint64_t bucket_cap, bucket_chunk;
   uint64_t n_chunks, run_cap;
   uint64_t total;
@@ -218,6 +218,7 @@ Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int roun
   L.brecs = at;
   if (L.n_regions) at += align_up(L.bucket_cap * L.n_regions * L.n_sub * 8);
   L.rplane = L.ohist = L.ostart = L.ofill = L.orecs = L.odec = L.ometa = at;
+  L.otcount = L.otbase = L.otsum = L.operm = at;
   if (L.o_regions) {
     const uint64_t R = L.o_regions;
     L.rplane = at;
@@ -235,6 +236,14 @@ Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int roun
     at += align_up((L.o_rec_cap + 31) / 32 * 4);
     L.ometa = at;
     at += align_up(L.o_tiles * R * 4);
+    L.otcount = at;
+    at += align_up((uint64_t)rounds * L.o_tiles * 4);
+    L.otbase = at;
+    at += align_up((uint64_t)rounds * L.o_tiles * 8);
+    L.otsum = at;
+    at += align_up((uint64_t)rounds * ((L.o_tiles + kOrdScanTiles - 1) / kOrdScanTiles) * 8);
+    L.operm = at;
+    at += align_up(L.o_rec_cap * 2);
   }
   // N splitting: N mask and boundary bitmap (one bit per base), per-chunk
   // boundary counts, the sorted boundaries and their ranks
@@ -334,6 +343,13 @@ RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_
     v.o_rec_cap = L.o_rec_cap;
     v.o_dec = reinterpret_cast<uint32_t*>(base + L.odec);
     v.o_meta = reinterpret_cast<uint32_t*>(base + L.ometa);
+    v.o_tiles = L.o_tiles;
+    v.o_tcount = reinterpret_cast<uint32_t*>(base + L.otcount);
+    v.o_tbase = reinterpret_cast<unsigned long long*>(base + L.otbase);
+    v.o_tsum = reinterpret_cast<unsigned long long*>(base + L.otsum);
+    v.o_perm = reinterpret_cast<uint16_t*>(base + L.operm);
+    // large rounds count distinct candidates on an eighth of the k-mers
+    v.lc_sample_log2 = L.o_rec_cap >= (1ull << 26) ? 3 : 0;
   }
   v.tile_count = reinterpret_cast<uint32_t*>(base + L.tile_count);
   v.tile_prefix = reinterpret_cast<uint64_t*>(base + L.tile_prefix);

@@ -131,6 +131,11 @@ struct RunView {
   uint64_t o_rec_cap;
   uint32_t* o_dec;          // one decision bit per record slot
   uint32_t* o_meta;         // per tile and bucket: where the tile's records start in the bucket
+  uint64_t o_tiles;         // tiles of kOrdTile positions: ceil(m / kOrdTile)
+  uint32_t* o_tcount;       // positions of every class in every tile (rounds x o_tiles)
+  unsigned long long* o_tbase;  // members of the round in the tiles before (rounds x o_tiles)
+  unsigned long long* o_tsum;   // members of the round per scan chunk of tiles
+  uint16_t* o_perm;         // per member of the round: its rank within its tile's room
   int use_desc;             // the insert leaves descriptors and the probe reads them
   uint64_t cand_cap;        // records the list can hold
   uint32_t* seg_count;      // candidates per list segment (one segment per probe warp)
@@ -138,6 +143,7 @@ struct RunView {
   uint64_t seg_cap;         // records per segment (set per launch)
   uint32_t* lc_bits;        // linear-counting bitmap, 2^lc_log2 bits
   int lc_log2;
+  int lc_sample_log2;       // region-ordered rounds count a 2^-lc_sample_log2 sample of the k-mers
   uint32_t* bins;           // partition counters (q), rounds > 1
   uint32_t* cuts;           // rounds + 1 class boundaries
   uint8_t* cmap;            // class map, one byte per position (null: rounds walk every position)
@@ -167,6 +173,7 @@ constexpr uint64_t kOrdTile = (uint64_t)kOrdTileWindows * kCmWindowPositions;  /
 constexpr uint32_t kOrdMaxRegions = 256;   // buckets (filter regions), at most
 constexpr uint32_t kOrdMaxHist = 4096;     // rounds x regions, at most
 constexpr uint32_t kOrdFillStride = 32;    // bucket fill counters 128 bytes apart
+constexpr uint32_t kOrdScanTiles = 1024;   // tiles per block of the member-number scan
 
 // Kernel launch helpers (twopaco_kernels.cu). Each returns the number of
 // kernels it launched, or -1 after a launch error.

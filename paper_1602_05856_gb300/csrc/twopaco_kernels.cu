@@ -1437,38 +1437,56 @@ __device__ __forceinline__ uint32_t ord_region(const RunView& v, uint64_t H, uin
   return (uint32_t)(filter_index(v, H, G) >> v.o_lg_region_words);
 }
 
-// ORD: also the region plane (the filter region of every position's k-mer)
-// and the positions of every (class, region) pair, counted per block in
-// shared memory and added to o_hist at the end.
+// ORD: also the region plane (the filter region of every position's k-mer),
+// the positions of every (class, region) pair (counted per block in shared
+// memory and added to o_hist at the end) and the positions of every class in
+// every tile of kOrdTile positions (o_tcount, round-major; a block's chunk of
+// kBlock * kInsertR positions lies in one tile).
 template <int KW, bool ORD>
 __global__ void __launch_bounds__(kBlock) class_map_kernel(RunView v) {
   __shared__ uint32_t cuts_s[kMaxMapRounds + 1];
   __shared__ uint32_t hist_s[ORD ? kOrdMaxHist : 1];
+  __shared__ uint32_t tcls_s[ORD ? kMaxMapRounds : 1];
   for (int i = threadIdx.x; i <= v.rounds; i += kBlock) cuts_s[i] = v.cuts[i];
   const uint32_t R = v.o_regions, nh = ORD ? (uint32_t)v.rounds * R : 0u;
-  if (ORD)
+  if (ORD) {
     for (uint32_t i = threadIdx.x; i < nh; i += kBlock) hist_s[i] = 0;
+    for (int i = threadIdx.x; i < v.rounds; i += kBlock) tcls_s[i] = 0;
+  }
   __syncthreads();
-  const uint64_t stride = (uint64_t)gridDim.x * kBlock * kInsertR;
-  for (uint64_t p0 = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) * kInsertR; p0 < v.m; p0 += stride) {
-    uint32_t w[4] = {0x80808080u, 0x80808080u, 0x80808080u, 0x80808080u};
-    uint32_t r[4] = {0u, 0u, 0u, 0u};
-    walk<KW, kInsertR>(v, p0, [&](int i, uint64_t, bool valid, const auto& oc) {
-      if (!valid) return;
-      const uint32_t cls = class_of_bin(cuts_s, v.rounds, (uint32_t)oc.H & v.qmask);
-      const uint32_t c = cls | (oc.sentinel ? kCmSentinel : 0u);
-      w[i >> 2] = (w[i >> 2] & ~(0xFFu << (8 * (i & 3)))) | (c << (8 * (i & 3)));
-      if (ORD) {
-        const uint32_t reg = ord_region(v, oc.H, second_hash(oc.H));
-        r[i >> 2] |= reg << (8 * (i & 3));
-        atomicAdd(hist_s + cls * R + reg, 1u);
+  constexpr uint64_t chunk = (uint64_t)kBlock * kInsertR;
+  static_assert(kOrdTile % chunk == 0, "a block's chunk lies in one tile");
+  for (uint64_t c0 = (uint64_t)blockIdx.x * chunk; c0 < v.m; c0 += (uint64_t)gridDim.x * chunk) {
+    const uint64_t p0 = c0 + (uint64_t)threadIdx.x * kInsertR;
+    if (p0 < v.m) {
+      uint32_t w[4] = {0x80808080u, 0x80808080u, 0x80808080u, 0x80808080u};
+      uint32_t r[4] = {0u, 0u, 0u, 0u};
+      walk<KW, kInsertR>(v, p0, [&](int i, uint64_t, bool valid, const auto& oc) {
+        if (!valid) return;
+        const uint32_t cls = class_of_bin(cuts_s, v.rounds, (uint32_t)oc.H & v.qmask);
+        const uint32_t c = cls | (oc.sentinel ? kCmSentinel : 0u);
+        w[i >> 2] = (w[i >> 2] & ~(0xFFu << (8 * (i & 3)))) | (c << (8 * (i & 3)));
+        if (ORD) {
+          const uint32_t reg = ord_region(v, oc.H, second_hash(oc.H));
+          r[i >> 2] |= reg << (8 * (i & 3));
+          atomicAdd(hist_s + cls * R + reg, 1u);
+          atomicAdd(tcls_s + cls, 1u);
+        }
+      });
+      *reinterpret_cast<uint4*>(v.cmap + p0) = make_uint4(w[0], w[1], w[2], w[3]);
+      if (ORD) *reinterpret_cast<uint4*>(v.rplane + p0) = make_uint4(r[0], r[1], r[2], r[3]);
+    }
+    if (ORD) {
+      __syncthreads();
+      const uint64_t tile = c0 / kOrdTile;
+      for (int i = threadIdx.x; i < v.rounds; i += kBlock) {
+        if (tcls_s[i]) atomicAdd(v.o_tcount + (uint64_t)i * v.o_tiles + tile, tcls_s[i]);
+        tcls_s[i] = 0;
       }
-    });
-    *reinterpret_cast<uint4*>(v.cmap + p0) = make_uint4(w[0], w[1], w[2], w[3]);
-    if (ORD) *reinterpret_cast<uint4*>(v.rplane + p0) = make_uint4(r[0], r[1], r[2], r[3]);
+      __syncthreads();
+    }
   }
   if (ORD) {
-    __syncthreads();
     for (uint32_t i = threadIdx.x; i < nh; i += kBlock)
       if (hist_s[i]) atomicAdd(v.o_hist + i, hist_s[i]);
   }
@@ -1642,13 +1660,13 @@ __global__ void __launch_bounds__(kBlock) pass1_probe_cm_kernel(RunView v, int r
 // Buckets: the class map counted the positions of every (class, region)
 // pair, so a round's buckets are laid out exactly (each a multiple of 32
 // slots). Tiles: kOrdTile consecutive positions, each warp of the block
-// taking kOrdTile / 8 of them (kOrdTileWindows / 8 windows) in order. A
-// tile's records for a bucket are consecutive in the bucket: the tile claims
-// their room with one atomic per bucket and records where it starts
-// (o_meta); a member's place in that room is its rank among the tile's
-// members of the same bucket in position order (warps in order, then windows,
-// then positions), which the gather recomputes from the class and region
-// planes to find the member's decision bit.
+// taking kOrdTile / 8 of them (kOrdTileWindows / 8 windows). A tile's records
+// for a bucket are consecutive in the bucket: the tile claims their room with
+// one atomic per bucket and records where it starts (o_meta). The members of
+// a round are numbered in position order (the class map counted them per
+// tile, and o_tbase holds every tile's first number); o_perm[member] is the
+// member's rank within its tile's room, so that the gather finds the
+// member's decision bit at o_start[bucket] + room + rank.
 //
 // A record: bits 0-21 the word within its region, 22-51 the bits 32-61 of G
 // (the bit bases of up to 6 bits per item), 52-56 and 57-61 the items (two
@@ -1659,28 +1677,48 @@ constexpr int kOrdWarpWindows = kOrdTileWindows / (kBlock / 32);  // windows per
 constexpr uint32_t kOrdPiece = 4096;  // records per apply or probe work item (a multiple of 32)
 constexpr unsigned long long kOrdSentinel = 1ull << 62;
 
-// compact_window with the region of every listed position in reg[0 .. n);
-// the planes are read through L2 (the tile reads them twice).
-__device__ __forceinline__ uint32_t compact_window_ord(const RunView& v, uint64_t wbase, int round, uint16_t* idx,
-                                                       uint8_t* reg, uint32_t* valid) {
-  const int lane = threadIdx.x & 31;
-  const uint64_t p0 = wbase + 16 * (uint64_t)lane;
-  uint4 q = make_uint4(0x80808080u, 0x80808080u, 0x80808080u, 0x80808080u);
-  uint4 rq = make_uint4(0u, 0u, 0u, 0u);
+// A lane's 16 positions of the window at wbase: their class and region bytes.
+__device__ __forceinline__ void ord_lane_bytes(const RunView& v, uint64_t wbase, uint4* cls, uint4* reg) {
+  const uint64_t p0 = wbase + 16 * (uint64_t)(threadIdx.x & 31);
+  *cls = make_uint4(0x80808080u, 0x80808080u, 0x80808080u, 0x80808080u);
+  *reg = make_uint4(0u, 0u, 0u, 0u);
   if (p0 < v.m) {
-    q = __ldcg(reinterpret_cast<const uint4*>(v.cmap + p0));
-    rq = __ldcg(reinterpret_cast<const uint4*>(v.rplane + p0));
+    *cls = __ldcg(reinterpret_cast<const uint4*>(v.cmap + p0));
+    *reg = __ldcg(reinterpret_cast<const uint4*>(v.rplane + p0));
   }
+}
+
+// Bit i: the lane's position i is of this round's class (act), a sentinel
+// (sent), has a k-mer (val).
+__device__ __forceinline__ void ord_lane_bits(const uint4& q, int round, uint32_t* act, uint32_t* sent,
+                                              uint32_t* val) {
   const uint32_t part[4] = {q.x, q.y, q.z, q.w};
-  const uint32_t rpart[4] = {rq.x, rq.y, rq.z, rq.w};
   const uint32_t want = (uint32_t)round * 0x01010101u;
-  uint32_t act = 0, sent = 0, val = 0;
+  uint32_t a = 0, s = 0, l = 0;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    act |= byte_bits(__vcmpeq4(part[c] & 0xBFBFBFBFu, want)) << (4 * c);
-    sent |= byte_bits(__vcmpeq4(part[c] & 0x40404040u, 0x40404040u)) << (4 * c);
-    val |= byte_bits(__vcmpeq4(part[c] & 0x80808080u, 0u)) << (4 * c);
+    a |= byte_bits(__vcmpeq4(part[c] & 0xBFBFBFBFu, want)) << (4 * c);
+    s |= byte_bits(__vcmpeq4(part[c] & 0x40404040u, 0x40404040u)) << (4 * c);
+    l |= byte_bits(__vcmpeq4(part[c] & 0x80808080u, 0u)) << (4 * c);
   }
+  *act = a;
+  *sent = s;
+  *val = l;
+}
+
+__device__ __forceinline__ uint32_t uint4_byte(const uint4& q, uint32_t i) {
+  const uint32_t w = i < 8 ? (i < 4 ? q.x : q.y) : (i < 12 ? q.z : q.w);
+  return (w >> (8 * (i & 3))) & 0xFFu;
+}
+
+// compact_window with the region of every listed position in reg[0 .. n).
+__device__ __forceinline__ uint32_t compact_window_ord(const RunView& v, uint64_t wbase, int round, uint16_t* idx,
+                                                       uint8_t* reg) {
+  const int lane = threadIdx.x & 31;
+  uint4 q, rq;
+  ord_lane_bytes(v, wbase, &q, &rq);
+  uint32_t act, sent, val;
+  ord_lane_bits(q, round, &act, &sent, &val);
   const uint32_t n = __popc(act);
   uint32_t inc = n;
 #pragma unroll
@@ -1693,71 +1731,62 @@ __device__ __forceinline__ uint32_t compact_window_ord(const RunView& v, uint64_
     const uint32_t i = __ffs(act) - 1;
     act &= act - 1;
     idx[at] = (uint16_t)((16 * lane + i) | (((sent >> i) & 1u) << 9));
-    reg[at] = (uint8_t)(rpart[i >> 2] >> (8 * (i & 3)));
+    reg[at] = (uint8_t)uint4_byte(rq, i);
     ++at;
   }
-  *valid = __popc(val);
   __syncwarp();
   return __shfl_sync(0xffffffffu, inc, 31);
 }
 
-// The per-warp starts of a tile's members in every bucket, relative to the
-// bucket's start: slot_s[w][b] = tile's room in bucket b + members of b in
-// warps before w. claim: the tile claims its room (the scatter) and records
-// it in o_meta; else the room is read from o_meta (the gather).
-template <bool CLAIM>
-__device__ __forceinline__ void ord_tile_slots(const RunView& v, int round, uint64_t tile, uint64_t tbase,
-                                               uint16_t (*idx_s)[kCmWindow], uint8_t (*reg_s)[kCmWindow],
-                                               uint32_t (*slot_s)[kOrdMaxRegions]) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t R = v.o_regions;
-  for (uint32_t b = lane; b < R; b += 32) slot_s[wid][b] = 0;
-  __syncwarp();
-  for (int q = 0; q < kOrdWarpWindows; ++q) {
-    const uint64_t wbase = tbase + (uint64_t)(wid * kOrdWarpWindows + q) * kCmWindow;
-    if (wbase >= v.p_end) break;
-    uint32_t valid;
-    const uint32_t n = compact_window_ord(v, wbase, round, idx_s[wid], reg_s[wid], &valid);
-    for (uint32_t j = lane; j < n; j += 32) atomicAdd(&slot_s[wid][reg_s[wid][j]], 1u);
-    __syncwarp();
-  }
+// Members of every (round, tile): thread blocks of the scan below take
+// kOrdScanTiles tiles of one round each.
+
+// o_tsum[round * chunks + c] = members of the round in tiles [c * 1024, (c + 1) * 1024).
+__global__ void __launch_bounds__(kBlock) ord_tile_sum_kernel(RunView v, uint64_t chunks) {
+  const uint64_t r = blockIdx.x / chunks, c = blockIdx.x % chunks;
+  const uint32_t* cnt = v.o_tcount + r * v.o_tiles;
+  unsigned long long s = 0;
+  for (uint64_t t = c * kOrdScanTiles + threadIdx.x; t < min((c + 1) * kOrdScanTiles, v.o_tiles); t += kBlock)
+    s += cnt[t];
+  __shared__ unsigned long long part[kBlock / 32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
   __syncthreads();
-  for (uint32_t b = threadIdx.x; b < R; b += kBlock) {
-    uint32_t run = 0;
-#pragma unroll
-    for (int w = 0; w < kBlock / 32; ++w) {
-      const uint32_t c = slot_s[w][b];
-      slot_s[w][b] = run;
-      run += c;
-    }
-    uint32_t room;
-    if (CLAIM) {
-      room = run ? atomicAdd(v.o_fill + (uint64_t)b * kOrdFillStride, run) : 0u;
-      v.o_meta[tile * R + b] = room;
-    } else {
-      room = __ldg(v.o_meta + tile * R + b);
-    }
-#pragma unroll
-    for (int w = 0; w < kBlock / 32; ++w) slot_s[w][b] += room;
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < kBlock / 32; ++w) t += part[w];
+    v.o_tsum[blockIdx.x] = t;
   }
-  __syncthreads();
 }
 
-// The slot of every listed member of a window, relative to its bucket's
-// start, in position order: its rank among the warp's earlier members of the
-// same bucket plus the warp's start in that bucket. Lanes take the members
-// j0 + lane; returns the member's bucket (or 0xFFFF past n).
-__device__ __forceinline__ uint32_t ord_member_slot(uint32_t* slot_w, const uint8_t* reg, uint32_t j, uint32_t n,
-                                                    uint32_t* slot) {
-  const int lane = threadIdx.x & 31;
-  const bool act = j < n;
-  const uint32_t b = act ? reg[j] : 0xFFFFu;
-  const unsigned peers = __match_any_sync(0xffffffffu, b);
-  if (act) *slot = slot_w[b] + __popc(peers & ((1u << lane) - 1u));
-  __syncwarp();
-  if (act && lane == __ffs(peers) - 1) slot_w[b] += __popc(peers);
-  __syncwarp();
-  return b;
+// o_tbase[round * tiles + t] = members of the round in tiles before t.
+__global__ void __launch_bounds__(kBlock) ord_tile_scan_kernel(RunView v, uint64_t chunks) {
+  const uint64_t r = blockIdx.x / chunks, c = blockIdx.x % chunks;
+  unsigned long long before = 0;
+  for (uint64_t i = threadIdx.x; i < c; i += kBlock) before += v.o_tsum[r * chunks + i];
+  __shared__ unsigned long long part[kBlock / 32];
+  __shared__ unsigned long long carry_s;
+  before = warp_sum(before);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = before;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < kBlock / 32; ++w) t += part[w];
+    carry_s = t;
+  }
+  __syncthreads();
+  const uint32_t* cnt = v.o_tcount + r * v.o_tiles;
+  unsigned long long* base = v.o_tbase + r * v.o_tiles;
+  for (uint64_t t0 = c * kOrdScanTiles; t0 < min((c + 1) * kOrdScanTiles, v.o_tiles); t0 += kBlock) {
+    const uint64_t t = t0 + threadIdx.x;
+    const uint32_t x = t < v.o_tiles ? cnt[t] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_exclusive_scan(x, &tot);
+    if (t < v.o_tiles) base[t] = carry_s + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s += tot;
+    __syncthreads();
+  }
 }
 
 // Before a round's scatter: the buckets' starts (each a multiple of 32), the
@@ -1783,48 +1812,112 @@ __global__ void __launch_bounds__(kBlock) ord_setup_kernel(RunView v, int round)
   }
 }
 
+// Records a tile stages in shared memory, sorted by bucket, before writing
+// them out run by run (a tile with more members writes them one by one).
+constexpr uint32_t kOrdStage = 4352;  // four blocks of 256 threads per SM (228 KB of shared memory)
+constexpr size_t kOrdStageBytes = (size_t)kOrdStage * 9;  // the records, then their buckets
+
 // Algorithm 1, insert loop, first pass, over this round's class: one record
 // per position into the bucket of its filter region (tiles grid-strided).
 template <int KW, int HB>
 __global__ void __launch_bounds__(kBlock) ord_scatter_kernel(RunView v, int round) {
+  extern __shared__ __align__(16) unsigned char ord_dyn_s[];
+  unsigned long long* stage_rec = reinterpret_cast<unsigned long long*>(ord_dyn_s);
+  uint8_t* stage_b = ord_dyn_s + (size_t)kOrdStage * 8;
   __shared__ uint16_t idx_s[kBlock / 32][kCmWindow];
   __shared__ uint8_t reg_s[kBlock / 32][kCmWindow];
-  __shared__ uint32_t slot_s[kBlock / 32][kOrdMaxRegions];
+  __shared__ uint32_t cur_s[kOrdMaxRegions];   // members per bucket, then the next rank
+  __shared__ uint32_t room_s[kOrdMaxRegions];  // where the tile's room starts in every bucket
+  __shared__ uint32_t off_s[kOrdMaxRegions];   // where every bucket's run starts in the stage
   __shared__ unsigned long long start_s[kOrdMaxRegions];
+  __shared__ uint32_t wcnt_s[kBlock / 32];
   if (!ordered_round(v)) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t R = v.o_regions;
   for (uint32_t b = threadIdx.x; b < R; b += kBlock) start_s[b] = v.o_start[b];
   const uint64_t local_mask = (1ull << v.o_lg_region_words) - 1ull;
+  const unsigned long long* tbase = v.o_tbase + (uint64_t)round * v.o_tiles;
   const uint64_t n_tiles = (v.p_end - v.p_begin + kOrdTile - 1) / kOrdTile;
   for (uint64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    const uint64_t tbase = v.p_begin + t * kOrdTile;
-    ord_tile_slots<true>(v, round, t, tbase, idx_s, reg_s, slot_s);
+    const uint64_t tpos = v.p_begin + t * kOrdTile;
+    for (uint32_t b = threadIdx.x; b < R; b += kBlock) cur_s[b] = 0;
+    __syncthreads();
+    // the tile's members per bucket and per warp
+    uint32_t wc = 0;
     for (int q = 0; q < kOrdWarpWindows; ++q) {
-      const uint64_t wbase = tbase + (uint64_t)(wid * kOrdWarpWindows + q) * kCmWindow;
+      const uint64_t wbase = tpos + (uint64_t)(wid * kOrdWarpWindows + q) * kCmWindow;
       if (wbase >= v.p_end) break;
-      uint32_t valid;
-      const uint32_t n = compact_window_ord(v, wbase, round, idx_s[wid], reg_s[wid], &valid);
-      for (uint32_t j0 = 0; j0 < n; j0 += 32) {
-        const uint32_t j = j0 + lane;
-        uint32_t slot = 0;
-        const uint32_t b = ord_member_slot(slot_s[wid], reg_s[wid], j, n, &slot);
-        if (j < n) {
-          const uint32_t e = idx_s[wid][j];
-          const bool sentinel = (e >> 9) & 1u;
-          OccT<KW> oc;
-          read_listed<KW>(v, wbase + (e & 511u), sentinel, &oc);
-          const uint64_t G = second_hash(oc.H);
-          const uint32_t j1 = __ffs(oc.items) - 1, j2 = 31 - __clz(oc.items);
-          const uint64_t word = filter_index(v, oc.H, G);
-          v.o_recs[start_s[b] + slot] = (word & local_mask) | (((G >> 32) & 0x3FFFFFFFull) << 22) |
-                                        ((uint64_t)j1 << 52) | ((uint64_t)j2 << 57) |
-                                        (sentinel ? kOrdSentinel : 0ull);
+      uint4 cq, rq;
+      ord_lane_bytes(v, wbase, &cq, &rq);
+      uint32_t act, sent, val;
+      ord_lane_bits(cq, round, &act, &sent, &val);
+      wc += __popc(act);
+      while (act) {
+        const uint32_t i = __ffs(act) - 1;
+        act &= act - 1;
+        atomicAdd(&cur_s[uint4_byte(rq, i)], 1u);
+      }
+    }
+    wc = warp_sum(wc);
+    if (lane == 0) wcnt_s[wid] = wc;
+    __syncthreads();
+    // every bucket's run in the stage (R <= kBlock: one bucket per thread)
+    const uint32_t mine = threadIdx.x < R ? cur_s[threadIdx.x] : 0u;
+    uint32_t total;
+    const uint32_t off = block_exclusive_scan(mine, &total);
+    if (threadIdx.x < R) {
+      const uint32_t room = mine ? atomicAdd(v.o_fill + (uint64_t)threadIdx.x * kOrdFillStride, mine) : 0u;
+      v.o_meta[t * R + threadIdx.x] = room;
+      room_s[threadIdx.x] = room;
+      off_s[threadIdx.x] = off;
+      cur_s[threadIdx.x] = 0;
+    }
+    if (threadIdx.x == 0) {
+      uint32_t run = 0;
+      for (int w = 0; w < kBlock / 32; ++w) {
+        const uint32_t x = wcnt_s[w];
+        wcnt_s[w] = run;
+        run += x;
+      }
+    }
+    __syncthreads();
+    const bool staged = total <= kOrdStage;
+    uint64_t mi = tbase[t] + wcnt_s[wid];  // number of the warp's next member
+    for (int q = 0; q < kOrdWarpWindows; ++q) {
+      const uint64_t wbase = tpos + (uint64_t)(wid * kOrdWarpWindows + q) * kCmWindow;
+      if (wbase >= v.p_end) break;
+      const uint32_t n = compact_window_ord(v, wbase, round, idx_s[wid], reg_s[wid]);
+      for (uint32_t j = lane; j < n; j += 32) {
+        const uint32_t e = idx_s[wid][j], b = reg_s[wid][j];
+        const uint32_t rank = atomicAdd(&cur_s[b], 1u);
+        v.o_perm[mi + j] = (uint16_t)rank;
+        const bool sentinel = (e >> 9) & 1u;
+        OccT<KW> oc;
+        read_listed<KW>(v, wbase + (e & 511u), sentinel, &oc);
+        const uint64_t G = second_hash(oc.H);
+        const uint32_t j1 = __ffs(oc.items) - 1, j2 = 31 - __clz(oc.items);
+        const uint64_t word = filter_index(v, oc.H, G);
+        const unsigned long long rec = (word & local_mask) | (((G >> 32) & 0x3FFFFFFFull) << 22) |
+                                       ((uint64_t)j1 << 52) | ((uint64_t)j2 << 57) |
+                                       (sentinel ? kOrdSentinel : 0ull);
+        if (staged) {
+          stage_rec[off_s[b] + rank] = rec;
+          stage_b[off_s[b] + rank] = (uint8_t)b;
+        } else {
+          v.o_recs[start_s[b] + room_s[b] + rank] = rec;
         }
       }
+      mi += n;
       __syncwarp();
     }
-    __syncthreads();  // slot_s and the windows' lists serve the next tile
+    __syncthreads();
+    if (staged) {  // consecutive threads on consecutive records of a run
+      for (uint32_t i = threadIdx.x; i < total; i += kBlock) {
+        const uint32_t b = stage_b[i];
+        v.o_recs[start_s[b] + room_s[b] + (i - off_s[b])] = stage_rec[i];
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -1842,6 +1935,20 @@ __device__ __forceinline__ void ord_items(const RunView& v, uint32_t* first_s) {
     first_s[v.o_regions] = acc;
   }
   __syncthreads();
+}
+
+// Warm L2 with this work item's share of the next bucket's filter region, so
+// that the region's first accesses do not wait on DRAM one random sector at
+// a time (the items of a bucket together cover the whole next region).
+__device__ __forceinline__ void ord_prefetch_next(const RunView& v, const uint32_t* first_s, uint32_t b,
+                                                  uint32_t item) {
+  if (b + 1 >= v.o_regions) return;
+  const uint64_t rbytes = 8ull << v.o_lg_region_words;
+  const uint64_t share = (rbytes / (first_s[b + 1] - first_s[b]) + 127) & ~127ull;
+  const uint64_t off = (uint64_t)(item - first_s[b]) * share, end = min(off + share, rbytes);
+  const char* next = reinterpret_cast<const char*>(v.filter + ((uint64_t)(b + 1) << v.o_lg_region_words));
+  for (uint64_t o = off + 128 * (uint64_t)threadIdx.x; o < end; o += 128 * (uint64_t)kBlock)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(next + o));
 }
 
 __device__ __forceinline__ uint32_t ord_item_bucket(const uint32_t* first_s, uint32_t R, uint32_t item) {
@@ -1869,6 +1976,7 @@ __global__ void __launch_bounds__(kBlock) ord_or_kernel(RunView v) {
     __syncthreads();
     if (item >= total) break;
     const uint32_t b = ord_item_bucket(first_s, R, item);
+    ord_prefetch_next(v, first_s, b, item);
     const uint64_t n = __ldcg(v.o_fill + (uint64_t)b * kOrdFillStride);
     const uint64_t i0 = (uint64_t)(item - first_s[b]) * kOrdPiece, i1 = min(i0 + kOrdPiece, n);
     const uint64_t* recs = v.o_recs + __ldg(v.o_start + b);
@@ -1911,6 +2019,7 @@ __global__ void __launch_bounds__(kBlock) ord_probe_kernel(RunView v) {
     __syncthreads();
     if (item >= total) break;
     const uint32_t b = ord_item_bucket(first_s, R, item);
+    ord_prefetch_next(v, first_s, b, item);
     const uint64_t n = __ldcg(v.o_fill + (uint64_t)b * kOrdFillStride);
     const uint64_t i0 = (uint64_t)(item - first_s[b]) * kOrdPiece, i1 = min(i0 + kOrdPiece, n);
     const uint64_t start = __ldg(v.o_start + b);  // a multiple of 32, as is i0
@@ -1930,10 +2039,13 @@ __global__ void __launch_bounds__(kBlock) ord_probe_kernel(RunView v) {
           const uint32_t pres = present_items<HB>(G, word, v.hashes);
           keep = (pres >> 16) || __popc(pres & 0xFFFFu) >= 2;
         }
-        if (keep && !v.partial) {
+        if (keep && !v.partial) {  // linear counting over a 2^-lc_sample_log2 sample of the k-mers
           const uint64_t id = (word_index << 30) | ((r >> 22) & 0x3FFFFFFFull);
-          const uint64_t x = (id * 0xff51afd7ed558ccdull) >> (64 - v.lc_log2);
-          atomicOr(v.lc_bits + (x >> 5), 1u << (x & 31));
+          const uint64_t h = id * 0xff51afd7ed558ccdull;
+          if (((uint32_t)(h >> 24) & ((1u << v.lc_sample_log2) - 1u)) == 0) {
+            const uint64_t x = h >> (64 - v.lc_log2);
+            atomicOr(v.lc_bits + (x >> 5), 1u << (x & 31));
+          }
         }
       }
       const uint32_t row = __ballot_sync(0xffffffffu, keep);
@@ -1943,80 +2055,106 @@ __global__ void __launch_bounds__(kBlock) ord_probe_kernel(RunView v) {
 }
 
 // The probe loop's outputs in position order: every member of the round's
-// class takes its decision from its record's slot (found as in the scatter);
-// C_temp words, the candidate list segment of the warp and the counts are as
-// pass1_probe_cm_kernel writes them.
+// class takes its decision from its record's slot (its tile's room in its
+// bucket plus its rank, o_perm); C_temp words, the candidate list segment of
+// the warp and the counts are as pass1_probe_cm_kernel writes them. Every
+// lane takes its own 16 positions of a window.
 __global__ void __launch_bounds__(kBlock) ord_gather_kernel(RunView v, int round) {
-  __shared__ uint16_t idx_s[kBlock / 32][kCmWindow];
-  __shared__ uint8_t reg_s[kBlock / 32][kCmWindow];
-  __shared__ uint32_t slot_s[kBlock / 32][kOrdMaxRegions];
+  __shared__ uint32_t room_s[kOrdMaxRegions];
   __shared__ unsigned long long start_s[kOrdMaxRegions];
-  __shared__ uint32_t keep_s[kBlock / 32][kCmWindow / 32];
+  __shared__ uint32_t wcnt_s[kBlock / 32];
   if (!ordered_round(v)) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t R = v.o_regions;
   for (uint32_t b = threadIdx.x; b < R; b += kBlock) start_s[b] = v.o_start[b];
-  uint32_t* keep_w = keep_s[wid];
-  const uint32_t below = (1u << lane) - 1u;
   unsigned long long kept = 0, valid_n = 0;
   const uint32_t warp_id = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   uint64_t* seg = v.cands + (uint64_t)warp_id * v.seg_cap;
   uint32_t* seg32 = reinterpret_cast<uint32_t*>(v.cands) + (uint64_t)warp_id * v.seg_cap;
   uint64_t seg_used = 0;
-  if (lane < kCmWindow / 32) keep_w[lane] = 0;
-  __syncwarp();
+  const unsigned long long* tbase = v.o_tbase + (uint64_t)round * v.o_tiles;
   const uint64_t n_tiles = (v.p_end - v.p_begin + kOrdTile - 1) / kOrdTile;
   for (uint64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    const uint64_t tbase = v.p_begin + t * kOrdTile;
-    ord_tile_slots<false>(v, round, t, tbase, idx_s, reg_s, slot_s);
+    const uint64_t tpos = v.p_begin + t * kOrdTile;
+    for (uint32_t b = threadIdx.x; b < R; b += kBlock) room_s[b] = __ldg(v.o_meta + t * R + b);
+    uint32_t wc = 0;
     for (int q = 0; q < kOrdWarpWindows; ++q) {
-      const uint64_t wbase = tbase + (uint64_t)(wid * kOrdWarpWindows + q) * kCmWindow;
+      const uint64_t wbase = tpos + (uint64_t)(wid * kOrdWarpWindows + q) * kCmWindow;
       if (wbase >= v.p_end) break;
-      uint32_t valid;
-      const uint32_t n = compact_window_ord(v, wbase, round, idx_s[wid], reg_s[wid], &valid);
-      valid_n += valid;
-      for (uint32_t j0 = 0; j0 < n; j0 += 32) {
-        const uint32_t j = j0 + lane;
-        uint32_t slot = 0;
-        const uint32_t b = ord_member_slot(slot_s[wid], reg_s[wid], j, n, &slot);
-        bool keep = false;
-        uint32_t e = 0;
-        if (j < n) {
-          e = idx_s[wid][j];
-          const uint64_t s = start_s[b] + slot;
-          keep = (__ldg(v.o_dec + (s >> 5)) >> (s & 31)) & 1u;
-          if (keep) atomicOr(keep_w + ((e & 511u) >> 5), 1u << (e & 31u));
-        }
-        if (v.partial) {
-          kept += keep;
-          continue;
-        }
-        const uint32_t row = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-          const uint64_t g = wbase + (e & 511u);
-          const uint32_t sentinel = (e >> 9) & 1u;
-          const uint64_t at = seg_used + __popc(row & below);
-          if (at < v.seg_cap) {
-            if (v.narrow) seg32[at] = (uint32_t)g | (sentinel << 31);
-            else seg[at] = g | ((uint64_t)sentinel << 63);
-          }
-          ++kept;
-        }
-        seg_used += __popc(row);
+      uint4 cq, rq;
+      ord_lane_bytes(v, wbase, &cq, &rq);
+      uint32_t act, sent, val;
+      ord_lane_bits(cq, round, &act, &sent, &val);
+      wc += __popc(act);
+    }
+    wc = warp_sum(wc);
+    if (lane == 0) wcnt_s[wid] = wc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t run = 0;
+      for (int w = 0; w < kBlock / 32; ++w) {
+        const uint32_t x = wcnt_s[w];
+        wcnt_s[w] = run;
+        run += x;
       }
-      __syncwarp();
-      if (lane < kCmWindow / 32) {
-        const uint64_t w = (wbase >> 5) + lane;
-        const uint32_t word = keep_w[lane];
-        keep_w[lane] = 0;
+    }
+    __syncthreads();
+    uint64_t mi = tbase[t] + wcnt_s[wid];  // number of the warp's next member
+    for (int q = 0; q < kOrdWarpWindows; ++q) {
+      const uint64_t wbase = tpos + (uint64_t)(wid * kOrdWarpWindows + q) * kCmWindow;
+      if (wbase >= v.p_end) break;
+      uint4 cq, rq;
+      ord_lane_bytes(v, wbase, &cq, &rq);
+      uint32_t act, sent, val;
+      ord_lane_bits(cq, round, &act, &sent, &val);
+      valid_n += __popc(val);
+      const uint32_t n = __popc(act);
+      uint32_t inc = n;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      uint64_t at = mi + inc - n;  // number of the lane's first member
+      uint32_t keep = 0;
+      for (uint32_t a = act; a; a &= a - 1, ++at) {
+        const uint32_t i = __ffs(a) - 1, b = uint4_byte(rq, i);
+        const uint64_t s = start_s[b] + room_s[b] + __ldg(v.o_perm + at);
+        keep |= ((__ldg(v.o_dec + (s >> 5)) >> (s & 31)) & 1u) << i;
+      }
+      mi += __shfl_sync(0xffffffffu, inc, 31);
+      // C_temp: lanes 2i and 2i + 1 hold the halves of the window's word i
+      const uint32_t hi = __shfl_down_sync(0xffffffffu, keep, 1);
+      if (!(lane & 1)) {
+        const uint64_t w = (wbase >> 5) + (lane >> 1);
+        const uint32_t word = keep | (hi << 16);
         if (w < v.bitmap_words) {
           v.ctemp[w] = word;
           if (v.partial) v.cfinal[w] |= word;  // rounds own disjoint positions; one writer per word
         }
       }
-      __syncwarp();
+      const uint32_t kc = __popc(keep);
+      kept += kc;
+      if (v.partial) continue;
+      uint32_t kinc = kc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, kinc, o);
+        if (lane >= o) kinc += y;
+      }
+      uint64_t o = seg_used + kinc - kc;
+      for (uint32_t k = keep; k; k &= k - 1, ++o) {
+        const uint32_t i = __ffs(k) - 1;
+        const uint64_t g = wbase + 16 * (uint64_t)lane + i;
+        const uint32_t sentinel = (sent >> i) & 1u;
+        if (o < v.seg_cap) {
+          if (v.narrow) seg32[o] = (uint32_t)g | (sentinel << 31);
+          else seg[o] = g | ((uint64_t)sentinel << 63);
+        }
+      }
+      seg_used += __shfl_sync(0xffffffffu, kinc, 31);
     }
-    __syncthreads();
+    __syncthreads();  // room_s and wcnt_s serve the next tile
   }
   if (lane == 0) {
     v.seg_count[warp_id] = (uint32_t)(seg_used < v.seg_cap ? seg_used : v.seg_cap);
@@ -2062,8 +2200,12 @@ __global__ void __launch_bounds__(kBlock) table_setup_kernel(RunView v) {
   const double M = (double)(1ull << v.lc_log2);
   unsigned long long distinct = kept;
   if ((double)set < M - M / 1024.0) {  // at least 1/1024 of the bits still clear: about 7 per bit
-    const double est = -M * log1p(-(double)set / M);
-    const unsigned long long e = (unsigned long long)(est * 1.1) + 64ull;
+    // a region-ordered round counted a 2^-s sample of the k-mers: scale it up,
+    // with eight standard deviations of the sample's size to spare
+    const int sl = (v.o_regions && *(volatile unsigned int*)&v.hdr->ord_ok) ? v.lc_sample_log2 : 0;
+    const double f = (double)(1u << sl);
+    const double est = -M * log1p(-(double)set / M) * f;
+    const unsigned long long e = (unsigned long long)(est * 1.1 + (sl ? 8.0 * sqrt(est * f) : 0.0)) + 64ull;
     if (e < distinct) distinct = e;
   }
   unsigned long long cap =
@@ -2695,9 +2837,9 @@ int sm_count() {
 
 // Grid of at most (SMs x resident blocks per SM) blocks for work_items threads.
 template <typename K>
-unsigned grid_for(K kernel, int block, uint64_t work_items, int cap_per_sm = 0) {
+unsigned grid_for(K kernel, int block, uint64_t work_items, int cap_per_sm = 0, size_t dyn_smem = 0) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, dyn_smem);
   if (cap_per_sm > 0 && per_sm > cap_per_sm) per_sm = cap_per_sm;  // a chosen launch shape
   if (per_sm < 1) per_sm = 1;
   const uint64_t full = (uint64_t)sm_count() * per_sm;
@@ -2831,8 +2973,12 @@ int round_impl(const RunView& v, int round, cudaStream_t s, const Ranges* ranges
       Timed t("ord_scatter", s);
       ord_setup_kernel<<<1, kBlock, 0, s>>>(v, round);
       const uint64_t tiles = (v.p_end - v.p_begin + kOrdTile - 1) / kOrdTile;
-      ord_scatter_kernel<KW, HBO><<<grid_for(ord_scatter_kernel<KW, HBO>, kBlock, tiles * kBlock, v.blocks_per_sm),
-                                    kBlock, 0, s>>>(v, round);
+      auto kern = ord_scatter_kernel<KW, HBO>;
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOrdStageBytes) !=
+          cudaSuccess)
+        return -1;
+      kern<<<grid_for(kern, kBlock, tiles * kBlock, v.blocks_per_sm, kOrdStageBytes), kBlock, kOrdStageBytes, s>>>(
+          v, round);
     }
     {
       Timed t("ord_or", s);
@@ -2971,9 +3117,16 @@ int launch_class_map(const RunView& v, cudaStream_t s) {
   Timed t("class_map", s);
   const uint64_t threads = (v.m + kInsertR - 1) / kInsertR;
   if (v.o_regions) {
-    if (cudaMemsetAsync(v.o_hist, 0, (uint64_t)v.rounds * v.o_regions * 4, s) != cudaSuccess) return -1;
+    if (cudaMemsetAsync(v.o_hist, 0, (uint64_t)v.rounds * v.o_regions * 4, s) != cudaSuccess ||
+        cudaMemsetAsync(v.o_tcount, 0, (uint64_t)v.rounds * v.o_tiles * 4, s) != cudaSuccess)
+      return -1;
     if (v.k <= 31) class_map_kernel<1, true><<<grid_for(class_map_kernel<1, true>, kBlock, threads), kBlock, 0, s>>>(v);
     else class_map_kernel<2, true><<<grid_for(class_map_kernel<2, true>, kBlock, threads), kBlock, 0, s>>>(v);
+    // every tile's first member number, per round
+    const uint64_t chunks = (v.o_tiles + kOrdScanTiles - 1) / kOrdScanTiles;
+    ord_tile_sum_kernel<<<(unsigned)(chunks * v.rounds), kBlock, 0, s>>>(v, chunks);
+    ord_tile_scan_kernel<<<(unsigned)(chunks * v.rounds), kBlock, 0, s>>>(v, chunks);
+    return done(3);
   } else if (v.k <= 31) {
     class_map_kernel<1, false><<<grid_for(class_map_kernel<1, false>, kBlock, threads), kBlock, 0, s>>>(v);
   } else {
