@@ -294,15 +294,15 @@ def sized_options(T, name, m, rounds, stream=0):
     """Options and output capacity: the defaults for inputs that fit them; for the
     mammal-scale set a pass-2 table, candidate list and output sized from its measured
     shares (28% of the positions survive pass 1 at 4 rounds, 26.6% are junctions, about
-    8% of a round's positions are distinct candidates) with room to spare -- a run that
-    still overflows fails loudly."""
+    3% of a round's positions are distinct candidates, which a table of 2.5 times as
+    many slots takes) with room to spare -- a run that still overflows fails loudly."""
     w = WORKLOADS[name]
     if name != "mammal_set":
         return T.Options(hashes=w["hashes"], cuda_stream=stream), None
     per_round = m // rounds
-    slots = 1 << max(20, int(np.ceil(np.log2(max(per_round * 0.3, 1)))))
+    slots = 1 << max(20, int(np.ceil(np.log2(max(per_round * 0.15, 1)))))
     return (T.Options(hashes=w["hashes"], table_slots=slots, candidate_records=per_round // 2,
-                      cuda_stream=stream), m // 3)
+                      cuda_stream=stream), int(m * 0.285))
 
 
 def l2_or_hbm_peaks(build, filter_bytes):
@@ -411,6 +411,8 @@ def device_leg(T, build, name, genome_len, rounds, args, world, rank, local, dis
     rounds = rounds or w["rounds"]
     if world > 1:
         rounds = max(rounds, world)  # every rank owns at least one class
+    # the random-access rates first, while the device holds nothing else
+    peaks = l2_or_hbm_peaks(build, w["filter_bits"] // 8)
     d_bases, off, seqs = load_workload(name, genome_len, dev)
     m, n = int(off[-1]), len(off) - 1
     stream = torch.cuda.current_stream(dev)
@@ -418,7 +420,6 @@ def device_leg(T, build, name, genome_len, rounds, args, world, rank, local, dis
     run = T.DeviceBuild(d_bases, off, K, w["filter_bits"], rounds, opts, device=f"cuda:{local}",
                         capacity=capacity)
     in_l2 = w["filter_bits"] // 8 <= (64 << 20)
-    peaks = l2_or_hbm_peaks(build, w["filter_bits"] // 8)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev) if m <= (256 << 20) else None
     if world == 1:
         T.twopaco_profile_enable(True)  # before the capture: replays record the captured events

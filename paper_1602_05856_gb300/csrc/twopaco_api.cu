@@ -60,6 +60,12 @@ int validate(uint64_t n_seqs, int k, uint64_t filter_bits, int rounds, const two
   return TWOPACO_OK;
 }
 
+// A failed call of another library (an allocation, say) leaves its error for
+// cudaPeekAtLastError, which the launch helpers read after their launches:
+// clear it when a call of this library starts, so that only this call's
+// launches are judged.
+void clear_stale_error() { (void)cudaGetLastError(); }
+
 int validate_size(uint64_t total_bases) {
   return total_bases >= (1ull << 48) ? TWOPACO_EINVAL : TWOPACO_OK;  // positions fit 48 bits
 }
@@ -73,7 +79,8 @@ struct Layout {
   uint32_t o_regions;  // region-ordered first pass (0: off)
   int o_lg_region_words;
   uint64_t o_rec_cap, o_tiles;
-  uint64_t rplane, ohist, ostart, ofill, orecs, odec, ometa, otcount, otbase, otsum, operm;
+  uint64_t rplane, othist, owcount, ocsum, ocpre, obtot, ostart, ofill, orecs, odec, ometa, otcount, otbase, otsum,
+      operm;
   uint64_t bucket_cap, bucket_chunk;
   uint64_t n_chunks, run_cap;
   uint64_t total;
@@ -217,14 +224,23 @@ Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int roun
   if (L.n_regions) at += align_up(((uint64_t)L.n_regions * L.n_sub + 1) * 128);
   L.brecs = at;
   if (L.n_regions) at += align_up(L.bucket_cap * L.n_regions * L.n_sub * 8);
-  L.rplane = L.ohist = L.ostart = L.ofill = L.orecs = L.odec = L.ometa = at;
+  L.rplane = L.othist = L.owcount = L.ocsum = L.ocpre = L.obtot = L.ostart = L.ofill = L.orecs = L.odec = L.ometa = at;
   L.otcount = L.otbase = L.otsum = L.operm = at;
   if (L.o_regions) {
     const uint64_t R = L.o_regions;
     L.rplane = at;
     at += align_up(m + 64);
-    L.ohist = at;
-    at += align_up((uint64_t)rounds * R * 4);
+    const uint64_t chunks = (L.o_tiles + kOrdScanTiles - 1) / kOrdScanTiles;
+    L.othist = at;
+    at += align_up(L.o_tiles * rounds * R * 2);
+    L.owcount = at;
+    at += align_up((uint64_t)rounds * L.o_tiles * 8 * 2);
+    L.ocsum = at;
+    at += align_up(chunks * R * 4);
+    L.ocpre = at;
+    at += align_up(chunks * R * 8);
+    L.obtot = at;
+    at += align_up(R * 8);
     L.ostart = at;
     at += align_up((R + 1) * 8);
     L.ofill = at;
@@ -336,7 +352,11 @@ RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_
   if (L.o_regions) {
     v.o_lg_region_words = L.o_lg_region_words;
     v.rplane = reinterpret_cast<uint8_t*>(base + L.rplane);
-    v.o_hist = reinterpret_cast<uint32_t*>(base + L.ohist);
+    v.o_thist = reinterpret_cast<uint16_t*>(base + L.othist);
+    v.o_wcount = reinterpret_cast<uint16_t*>(base + L.owcount);
+    v.o_csum = reinterpret_cast<uint32_t*>(base + L.ocsum);
+    v.o_cpre = reinterpret_cast<unsigned long long*>(base + L.ocpre);
+    v.o_btot = reinterpret_cast<unsigned long long*>(base + L.obtot);
     v.o_start = reinterpret_cast<uint64_t*>(base + L.ostart);
     v.o_fill = reinterpret_cast<uint32_t*>(base + L.ofill);
     v.o_recs = reinterpret_cast<uint64_t*>(base + L.orecs);
@@ -494,6 +514,7 @@ int twopaco_run_rounds(const uint8_t* d_bases, const uint64_t* d_offsets, uint64
                        const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
                        int round_begin, int round_end, uint64_t* d_out_offsets,
                        uint64_t* d_out_positions, uint64_t out_capacity) {
+  clear_stale_error();
   const twopaco_options o = resolve(opt);
   RunView v;
   int rc = device_run_view(d_bases, d_offsets, n_seqs, total_bases, k, filter_bits, rounds, o, d_workspace,
@@ -524,6 +545,7 @@ int twopaco_run_streamed(const uint8_t* h_bases, const uint64_t* d_offsets, uint
                          const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
                          void* d_staging, uint64_t staging_bytes, uint64_t* d_out_offsets,
                          uint64_t* d_out_positions, uint64_t out_capacity) {
+  clear_stale_error();
   const twopaco_options o = resolve(opt);
   RunView v;
   int rc = device_run_view(h_bases, d_offsets, n_seqs, total_bases, k, filter_bits, rounds, o, d_workspace,
@@ -584,6 +606,7 @@ int twopaco_shard_begin(const uint8_t* d_bases, const uint64_t* d_offsets, uint6
                         uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
                         const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
                         int compute_cut) {
+  clear_stale_error();
   const twopaco_options o = resolve(opt);
   RunView v;
   int rc = device_run_view(d_bases, d_offsets, n_seqs, total_bases, k, filter_bits, rounds, o, d_workspace,
@@ -600,6 +623,7 @@ int twopaco_shard_rounds(const uint8_t* d_bases, const uint64_t* d_offsets, uint
                          uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
                          const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
                          int shard, int n_shards, const uint32_t* d_class_cut) {
+  clear_stale_error();
   const twopaco_options o = resolve(opt);
   RunView v;
   int rc = device_run_view(d_bases, d_offsets, n_seqs, total_bases, k, filter_bits, rounds, o, d_workspace,
@@ -652,6 +676,7 @@ int twopaco_edges_device(const void* d_workspace, const uint64_t* d_offsets, uin
                          const uint64_t* d_out_offsets, const uint64_t* d_out_positions,
                          uint64_t* d_edge_offsets, twopaco_edge* d_edges, uint64_t edge_capacity,
                          void* cuda_stream) {
+  clear_stale_error();
   static_assert(sizeof(twopaco_edge) == 56, "twopaco_edge layout");
   if (!d_workspace || !d_out_offsets || !d_edge_offsets || (n_seqs && !d_offsets)) return TWOPACO_EINVAL;
   if (edge_capacity && !d_edges) return TWOPACO_EINVAL;
@@ -848,6 +873,7 @@ int twopaco_checkpoint_load(const uint8_t* d_bases, const uint64_t* d_offsets, u
                             uint64_t total_bases, int k, uint64_t filter_bits, int rounds,
                             const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
                             const void* host_src, uint64_t bytes, int* next_round) {
+  clear_stale_error();
   const twopaco_options o = resolve(opt);
   int rc = validate(n_seqs, k, filter_bits, rounds, o);
   if (rc) return rc;
@@ -917,6 +943,7 @@ int twopaco_checkpoint_load(const uint8_t* d_bases, const uint64_t* d_offsets, u
 }
 
 int twopaco_selftest_bounded_wait(void* cuda_stream) {
+  clear_stale_error();
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   unsigned long long* word = nullptr;
   unsigned int* status = nullptr;
@@ -1072,6 +1099,7 @@ int twopaco_plan_create(const uint8_t* d_bases, const uint64_t* d_offsets, uint6
                         const twopaco_options* opt, void* d_workspace, uint64_t workspace_bytes,
                         uint64_t* d_out_offsets, uint64_t* d_out_positions, uint64_t out_capacity,
                         twopaco_plan** plan) {
+  clear_stale_error();
   if (!plan) return TWOPACO_EINVAL;
   *plan = nullptr;
   twopaco_options o = resolve(opt);
@@ -1239,6 +1267,7 @@ void twopaco_context_destroy(twopaco_context* c) {
 int twopaco_build_ctx(twopaco_context* c, const char* const* seqs, const uint64_t* lengths,
                       uint64_t n_seqs, int k, uint64_t filter_bits, int rounds,
                       const twopaco_options* opt, twopaco_result* out) {
+  clear_stale_error();
   if (!c || !out) return TWOPACO_EINVAL;
   twopaco_options o = resolve(opt);
   int rc = validate(n_seqs, k, filter_bits, rounds, o);
@@ -1330,6 +1359,7 @@ int twopaco_build_ctx(twopaco_context* c, const char* const* seqs, const uint64_
 }
 
 int twopaco_edges_ctx(twopaco_context* c, twopaco_edge_list* out) {
+  clear_stale_error();
   if (!c || !out || !c->have_last) return TWOPACO_EINVAL;
   int prev = 0;
   cudaGetDevice(&prev);

@@ -117,14 +117,18 @@ struct RunView {
   uint64_t bucket_chunk;    // positions per scatter-and-apply chunk (a multiple of kRangeTile)
   // region-ordered first pass (o_regions > 0; class-map rounds): the class map
   // also records every position's filter region (rplane) and counts the
-  // positions of every (class, region) pair (o_hist); a round then writes one
-  // 8-byte record per position of its class into the bucket of its region,
-  // applies the ORs and the probes bucket by bucket, and gathers the decisions
-  // back in position order
+  // positions of every tile per (class, region) pair and per (class, warp
+  // chunk); a round then writes one 8-byte record per position of its class
+  // into the bucket of its region, applies the ORs and the probes bucket by
+  // bucket, and gathers the decisions back in position order
   uint32_t o_regions;       // filter regions (buckets), at most kOrdMaxRegions
   int o_lg_region_words;    // log2 of the 64-bit words per region (at most 22)
   uint8_t* rplane;          // region of every position's k-mer, one byte per position
-  uint32_t* o_hist;         // rounds x o_regions position counts
+  uint16_t* o_thist;        // per tile, class and region: its positions (tile-major)
+  uint16_t* o_wcount;       // per class, tile and warp chunk of kOrdTile / 8 positions: its positions
+  uint32_t* o_csum;         // per chunk of kOrdScanTiles tiles and bucket: the round's members
+  unsigned long long* o_cpre;  // per chunk and bucket: the round's members in the chunks before
+  unsigned long long* o_btot;  // per bucket: the round's members
   uint64_t* o_start;        // o_regions + 1 bucket starts of the current round (multiples of 32)
   uint32_t* o_fill;         // records claimed per bucket, one counter per 128 bytes
   uint64_t* o_recs;         // o_rec_cap records

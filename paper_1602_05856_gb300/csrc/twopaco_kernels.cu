@@ -902,9 +902,12 @@ __device__ __forceinline__ uint32_t pack4(uint32_t x, uint32_t* bad, uint32_t* i
   return ((c & 3u) << 6) | (((c >> 8) & 3u) << 4) | (((c >> 16) & 3u) << 2) | ((c >> 24) & 3u);
 }
 
-// Bit j of the result: byte j of the __vcmpeq4 mask e is set.
+// Bit j of the result: the top bit of byte j of e (for a __vcmpeq4 mask:
+// byte j matched).
 __device__ __forceinline__ uint32_t byte_bits(uint32_t e) {
-  return ((e >> 7) & 1u) | ((e >> 14) & 2u) | ((e >> 21) & 4u) | ((e >> 28) & 8u);
+  // the top bit of every byte to bits 0-3: the multiply moves bits 7, 15, 23
+  // and 31 to bits 28-31, every other partial product lands elsewhere
+  return ((e & 0x80808080u) * 0x00204081u) >> 28;
 }
 
 // Sixteen ASCII bytes at g (or fewer at the end of the input) -> one word;
@@ -1437,58 +1440,76 @@ __device__ __forceinline__ uint32_t ord_region(const RunView& v, uint64_t H, uin
   return (uint32_t)(filter_index(v, H, G) >> v.o_lg_region_words);
 }
 
-// ORD: also the region plane (the filter region of every position's k-mer),
-// the positions of every (class, region) pair (counted per block in shared
-// memory and added to o_hist at the end) and the positions of every class in
-// every tile of kOrdTile positions (o_tcount, round-major; a block's chunk of
-// kBlock * kInsertR positions lies in one tile).
-template <int KW, bool ORD>
+template <int KW>
 __global__ void __launch_bounds__(kBlock) class_map_kernel(RunView v) {
   __shared__ uint32_t cuts_s[kMaxMapRounds + 1];
-  __shared__ uint32_t hist_s[ORD ? kOrdMaxHist : 1];
-  __shared__ uint32_t tcls_s[ORD ? kMaxMapRounds : 1];
   for (int i = threadIdx.x; i <= v.rounds; i += kBlock) cuts_s[i] = v.cuts[i];
-  const uint32_t R = v.o_regions, nh = ORD ? (uint32_t)v.rounds * R : 0u;
-  if (ORD) {
-    for (uint32_t i = threadIdx.x; i < nh; i += kBlock) hist_s[i] = 0;
-    for (int i = threadIdx.x; i < v.rounds; i += kBlock) tcls_s[i] = 0;
-  }
   __syncthreads();
-  constexpr uint64_t chunk = (uint64_t)kBlock * kInsertR;
-  static_assert(kOrdTile % chunk == 0, "a block's chunk lies in one tile");
-  for (uint64_t c0 = (uint64_t)blockIdx.x * chunk; c0 < v.m; c0 += (uint64_t)gridDim.x * chunk) {
-    const uint64_t p0 = c0 + (uint64_t)threadIdx.x * kInsertR;
-    if (p0 < v.m) {
+  const uint64_t stride = (uint64_t)gridDim.x * kBlock * kInsertR;
+  for (uint64_t p0 = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) * kInsertR; p0 < v.m; p0 += stride) {
+    uint32_t w[4] = {0x80808080u, 0x80808080u, 0x80808080u, 0x80808080u};
+    walk<KW, kInsertR>(v, p0, [&](int i, uint64_t, bool valid, const auto& oc) {
+      if (!valid) return;
+      const uint32_t c = class_of_bin(cuts_s, v.rounds, (uint32_t)oc.H & v.qmask) |
+                         (oc.sentinel ? kCmSentinel : 0u);
+      w[i >> 2] = (w[i >> 2] & ~(0xFFu << (8 * (i & 3)))) | (c << (8 * (i & 3)));
+    });
+    *reinterpret_cast<uint4*>(v.cmap + p0) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// The class map of a run with the region-ordered first pass, a tile of
+// kOrdTile positions per block: also the region plane (the filter region of
+// every position's k-mer) and, per tile, its positions of every (class,
+// region) pair (o_thist, tile-major) and of every (class, warp chunk of
+// kOrdTile / 8 positions) (o_wcount, class-major) and of every class
+// (o_tcount, class-major).
+template <int KW>
+__global__ void __launch_bounds__(kBlock) class_map_ord_kernel(RunView v) {
+  constexpr int kChunks = (int)(kOrdTile / ((uint64_t)kBlock * kInsertR));  // 4
+  constexpr int kWarpChunks = kBlock / 32;                                   // 8
+  __shared__ uint32_t cuts_s[kMaxMapRounds + 1];
+  __shared__ uint32_t thist_s[kOrdMaxHist];
+  __shared__ uint32_t wcnt_s[kWarpChunks * kMaxMapRounds];
+  for (int i = threadIdx.x; i <= v.rounds; i += kBlock) cuts_s[i] = v.cuts[i];
+  const uint32_t R = v.o_regions, L = (uint32_t)v.rounds, nh = L * R;
+  for (uint64_t t = blockIdx.x; t < v.o_tiles; t += gridDim.x) {
+    for (uint32_t i = threadIdx.x; i < nh; i += kBlock) thist_s[i] = 0;
+    for (uint32_t i = threadIdx.x; i < kWarpChunks * L; i += kBlock) wcnt_s[i] = 0;
+    __syncthreads();
+    for (int c = 0; c < kChunks; ++c) {
+      const uint64_t p0 = t * kOrdTile + ((uint64_t)c * kBlock + threadIdx.x) * kInsertR;
+      if (p0 >= v.m) break;
+      // the warp chunk of these positions: kOrdTile / 8 = 2048 positions, 128 threads' worth
+      const uint32_t wc = (uint32_t)((((uint64_t)c * kBlock + threadIdx.x) * kInsertR) / (kOrdTile / kWarpChunks));
       uint32_t w[4] = {0x80808080u, 0x80808080u, 0x80808080u, 0x80808080u};
       uint32_t r[4] = {0u, 0u, 0u, 0u};
       walk<KW, kInsertR>(v, p0, [&](int i, uint64_t, bool valid, const auto& oc) {
         if (!valid) return;
         const uint32_t cls = class_of_bin(cuts_s, v.rounds, (uint32_t)oc.H & v.qmask);
-        const uint32_t c = cls | (oc.sentinel ? kCmSentinel : 0u);
-        w[i >> 2] = (w[i >> 2] & ~(0xFFu << (8 * (i & 3)))) | (c << (8 * (i & 3)));
-        if (ORD) {
-          const uint32_t reg = ord_region(v, oc.H, second_hash(oc.H));
-          r[i >> 2] |= reg << (8 * (i & 3));
-          atomicAdd(hist_s + cls * R + reg, 1u);
-          atomicAdd(tcls_s + cls, 1u);
-        }
+        w[i >> 2] = (w[i >> 2] & ~(0xFFu << (8 * (i & 3)))) | ((cls | (oc.sentinel ? kCmSentinel : 0u)) << (8 * (i & 3)));
+        const uint32_t reg = ord_region(v, oc.H, second_hash(oc.H));
+        r[i >> 2] |= reg << (8 * (i & 3));
+        atomicAdd(thist_s + cls * R + reg, 1u);
+        atomicAdd(wcnt_s + wc * L + cls, 1u);
       });
       *reinterpret_cast<uint4*>(v.cmap + p0) = make_uint4(w[0], w[1], w[2], w[3]);
-      if (ORD) *reinterpret_cast<uint4*>(v.rplane + p0) = make_uint4(r[0], r[1], r[2], r[3]);
+      *reinterpret_cast<uint4*>(v.rplane + p0) = make_uint4(r[0], r[1], r[2], r[3]);
     }
-    if (ORD) {
-      __syncthreads();
-      const uint64_t tile = c0 / kOrdTile;
-      for (int i = threadIdx.x; i < v.rounds; i += kBlock) {
-        if (tcls_s[i]) atomicAdd(v.o_tcount + (uint64_t)i * v.o_tiles + tile, tcls_s[i]);
-        tcls_s[i] = 0;
-      }
-      __syncthreads();
+    __syncthreads();
+    // at most kOrdTile = 16384 positions per tile: every count fits 16 bits
+    uint16_t* th = v.o_thist + t * nh;
+    for (uint32_t i = threadIdx.x; i < nh; i += kBlock) th[i] = (uint16_t)thist_s[i];
+    for (uint32_t i = threadIdx.x; i < kWarpChunks * L; i += kBlock) {
+      const uint32_t cls = i % L, wc = i / L;
+      v.o_wcount[((uint64_t)cls * v.o_tiles + t) * kWarpChunks + wc] = (uint16_t)wcnt_s[i];
     }
-  }
-  if (ORD) {
-    for (uint32_t i = threadIdx.x; i < nh; i += kBlock)
-      if (hist_s[i]) atomicAdd(v.o_hist + i, hist_s[i]);
+    for (uint32_t cls = threadIdx.x; cls < L; cls += kBlock) {
+      uint32_t tot = 0;
+      for (int wc = 0; wc < kWarpChunks; ++wc) tot += wcnt_s[wc * L + cls];
+      v.o_tcount[(uint64_t)cls * v.o_tiles + t] = tot;
+    }
+    __syncthreads();
   }
 }
 
@@ -1507,8 +1528,8 @@ __device__ __forceinline__ uint32_t compact_window(const RunView& v, uint64_t wb
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     act |= byte_bits(__vcmpeq4(part[c] & 0xBFBFBFBFu, want)) << (4 * c);  // valid and in this class
-    sent |= byte_bits(__vcmpeq4(part[c] & 0x40404040u, 0x40404040u)) << (4 * c);
-    val |= byte_bits(__vcmpeq4(part[c] & 0x80808080u, 0u)) << (4 * c);
+    sent |= byte_bits(part[c] << 1) << (4 * c);  // bit 6: a sentinel
+    val |= byte_bits(~part[c]) << (4 * c);       // bit 7 clear: a k-mer
   }
   const uint32_t n = __popc(act);
   uint32_t inc = n;
@@ -1698,8 +1719,8 @@ __device__ __forceinline__ void ord_lane_bits(const uint4& q, int round, uint32_
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     a |= byte_bits(__vcmpeq4(part[c] & 0xBFBFBFBFu, want)) << (4 * c);
-    s |= byte_bits(__vcmpeq4(part[c] & 0x40404040u, 0x40404040u)) << (4 * c);
-    l |= byte_bits(__vcmpeq4(part[c] & 0x80808080u, 0u)) << (4 * c);
+    s |= byte_bits(part[c] << 1) << (4 * c);
+    l |= byte_bits(~part[c]) << (4 * c);
   }
   *act = a;
   *sent = s;
@@ -1789,18 +1810,87 @@ __global__ void __launch_bounds__(kBlock) ord_tile_scan_kernel(RunView v, uint64
   }
 }
 
+// Exclusive scan of x over the block (blockDim.x == kBlock), 64-bit.
+__device__ __forceinline__ unsigned long long block_exclusive_scan64(unsigned long long x, unsigned long long* total) {
+  __shared__ unsigned long long warp_tot[kBlock / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) warp_tot[wid] = inc;
+  __syncthreads();
+  unsigned long long before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < kBlock / 32; ++w) {
+    const unsigned long long t = warp_tot[w];
+    before += (w < wid) ? t : 0ull;
+    all += t;
+  }
+  __syncthreads();
+  *total = all;
+  return before + inc - x;
+}
+
+// The rooms of a round's tiles in its buckets, in tile order: o_meta[t * R + b]
+// = the round's members of bucket b in the tiles before t. Three steps over
+// chunks of kOrdScanTiles tiles: the chunks' sums, their prefix per bucket
+// (with every bucket's total, o_btot), then every tile's room.
+__global__ void __launch_bounds__(kBlock) ord_room_sum_kernel(RunView v, int round) {
+  const uint32_t R = v.o_regions, b = threadIdx.x, nh = (uint32_t)v.rounds * R;
+  if (b >= R) return;
+  const uint64_t c = blockIdx.x, t1 = min((c + 1) * kOrdScanTiles, v.o_tiles);
+  const uint16_t* th = v.o_thist + (uint64_t)round * R + b;
+  uint32_t s = 0;
+#pragma unroll 8
+  for (uint64_t t = c * kOrdScanTiles; t < t1; ++t) s += th[t * nh];
+  v.o_csum[c * R + b] = s;
+}
+
+__global__ void __launch_bounds__(kBlock) ord_room_prefix_kernel(RunView v, uint64_t chunks) {
+  const uint32_t R = v.o_regions, b = blockIdx.x;
+  __shared__ unsigned long long carry_s;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  for (uint64_t c0 = 0; c0 < chunks; c0 += kBlock) {
+    const uint64_t c = c0 + threadIdx.x;
+    const unsigned long long x = c < chunks ? v.o_csum[c * R + b] : 0ull;
+    unsigned long long tot;
+    const unsigned long long ex = block_exclusive_scan64(x, &tot);
+    if (c < chunks) v.o_cpre[c * R + b] = carry_s + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) v.o_btot[b] = carry_s;
+}
+
+__global__ void __launch_bounds__(kBlock) ord_room_scan_kernel(RunView v, int round) {
+  const uint32_t R = v.o_regions, b = threadIdx.x, nh = (uint32_t)v.rounds * R;
+  if (b >= R) return;
+  const uint64_t c = blockIdx.x, t1 = min((c + 1) * kOrdScanTiles, v.o_tiles);
+  const uint16_t* th = v.o_thist + (uint64_t)round * R + b;
+  unsigned long long run = v.o_cpre[c * R + b];
+  for (uint64_t t = c * kOrdScanTiles; t < t1; ++t) {
+    v.o_meta[t * R + b] = (uint32_t)run;  // within a bucket below 2^32 (the setup checks)
+    run += th[t * nh];
+  }
+}
+
 // Before a round's scatter: the buckets' starts (each a multiple of 32), the
-// fill counters and work tickets cleared, and whether the round's records fit
-// (else the direct kernels take the round). One block.
+// work tickets cleared, and whether the round's records fit (else the direct
+// kernels take the round). One block.
 __global__ void __launch_bounds__(kBlock) ord_setup_kernel(RunView v, int round) {
   const uint32_t R = v.o_regions;
-  for (uint32_t b = threadIdx.x; b < R; b += kBlock) v.o_fill[(uint64_t)b * kOrdFillStride] = 0;
+  for (uint32_t b = threadIdx.x; b < R; b += kBlock) v.o_fill[(uint64_t)b * kOrdFillStride] = (uint32_t)v.o_btot[b];
   if (threadIdx.x == 0) {
     uint64_t at = 0;
     bool fits = true;
     for (uint32_t b = 0; b < R; ++b) {
       v.o_start[b] = at;
-      const uint64_t n = v.o_hist[(uint64_t)round * R + b];
+      const uint64_t n = v.o_btot[b];
       fits = fits && n < (1ull << 32);  // slots within a bucket are 32-bit
       at += (n + 31) & ~31ull;
     }
@@ -1840,44 +1930,22 @@ __global__ void __launch_bounds__(kBlock) ord_scatter_kernel(RunView v, int roun
   const uint64_t n_tiles = (v.p_end - v.p_begin + kOrdTile - 1) / kOrdTile;
   for (uint64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const uint64_t tpos = v.p_begin + t * kOrdTile;
-    for (uint32_t b = threadIdx.x; b < R; b += kBlock) cur_s[b] = 0;
-    __syncthreads();
-    // the tile's members per bucket and per warp
-    uint32_t wc = 0;
-    for (int q = 0; q < kOrdWarpWindows; ++q) {
-      const uint64_t wbase = tpos + (uint64_t)(wid * kOrdWarpWindows + q) * kCmWindow;
-      if (wbase >= v.p_end) break;
-      uint4 cq, rq;
-      ord_lane_bytes(v, wbase, &cq, &rq);
-      uint32_t act, sent, val;
-      ord_lane_bits(cq, round, &act, &sent, &val);
-      wc += __popc(act);
-      while (act) {
-        const uint32_t i = __ffs(act) - 1;
-        act &= act - 1;
-        atomicAdd(&cur_s[uint4_byte(rq, i)], 1u);
-      }
-    }
-    wc = warp_sum(wc);
-    if (lane == 0) wcnt_s[wid] = wc;
-    __syncthreads();
-    // every bucket's run in the stage (R <= kBlock: one bucket per thread)
-    const uint32_t mine = threadIdx.x < R ? cur_s[threadIdx.x] : 0u;
+    // the tile's members per bucket (o_thist) and per warp chunk (o_wcount),
+    // and its rooms (o_meta)
+    const uint32_t mine = threadIdx.x < R ? v.o_thist[(t * v.rounds + round) * R + threadIdx.x] : 0u;
     uint32_t total;
     const uint32_t off = block_exclusive_scan(mine, &total);
     if (threadIdx.x < R) {
-      const uint32_t room = mine ? atomicAdd(v.o_fill + (uint64_t)threadIdx.x * kOrdFillStride, mine) : 0u;
-      v.o_meta[t * R + threadIdx.x] = room;
-      room_s[threadIdx.x] = room;
+      room_s[threadIdx.x] = __ldg(v.o_meta + t * R + threadIdx.x);
       off_s[threadIdx.x] = off;
       cur_s[threadIdx.x] = 0;
     }
     if (threadIdx.x == 0) {
+      const uint16_t* wcnt = v.o_wcount + ((uint64_t)round * v.o_tiles + t) * (kBlock / 32);
       uint32_t run = 0;
       for (int w = 0; w < kBlock / 32; ++w) {
-        const uint32_t x = wcnt_s[w];
         wcnt_s[w] = run;
-        run += x;
+        run += wcnt[w];
       }
     }
     __syncthreads();
@@ -2077,25 +2145,12 @@ __global__ void __launch_bounds__(kBlock) ord_gather_kernel(RunView v, int round
   for (uint64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const uint64_t tpos = v.p_begin + t * kOrdTile;
     for (uint32_t b = threadIdx.x; b < R; b += kBlock) room_s[b] = __ldg(v.o_meta + t * R + b);
-    uint32_t wc = 0;
-    for (int q = 0; q < kOrdWarpWindows; ++q) {
-      const uint64_t wbase = tpos + (uint64_t)(wid * kOrdWarpWindows + q) * kCmWindow;
-      if (wbase >= v.p_end) break;
-      uint4 cq, rq;
-      ord_lane_bytes(v, wbase, &cq, &rq);
-      uint32_t act, sent, val;
-      ord_lane_bits(cq, round, &act, &sent, &val);
-      wc += __popc(act);
-    }
-    wc = warp_sum(wc);
-    if (lane == 0) wcnt_s[wid] = wc;
-    __syncthreads();
     if (threadIdx.x == 0) {
+      const uint16_t* wcnt = v.o_wcount + ((uint64_t)round * v.o_tiles + t) * (kBlock / 32);
       uint32_t run = 0;
       for (int w = 0; w < kBlock / 32; ++w) {
-        const uint32_t x = wcnt_s[w];
         wcnt_s[w] = run;
-        run += x;
+        run += wcnt[w];
       }
     }
     __syncthreads();
@@ -2971,6 +3026,10 @@ int round_impl(const RunView& v, int round, cudaStream_t s, const Ranges* ranges
   if (ord) {
     {
       Timed t("ord_scatter", s);
+      const uint64_t chunks = (v.o_tiles + kOrdScanTiles - 1) / kOrdScanTiles;
+      ord_room_sum_kernel<<<(unsigned)chunks, kBlock, 0, s>>>(v, round);
+      ord_room_prefix_kernel<<<v.o_regions, kBlock, 0, s>>>(v, chunks);
+      ord_room_scan_kernel<<<(unsigned)chunks, kBlock, 0, s>>>(v, round);
       ord_setup_kernel<<<1, kBlock, 0, s>>>(v, round);
       const uint64_t tiles = (v.p_end - v.p_begin + kOrdTile - 1) / kOrdTile;
       auto kern = ord_scatter_kernel<KW, HBO>;
@@ -2984,7 +3043,7 @@ int round_impl(const RunView& v, int round, cudaStream_t s, const Ranges* ranges
       Timed t("ord_or", s);
       ord_or_kernel<HBO><<<grid_for(ord_or_kernel<HBO>, kBlock, ~0ull >> 1), kBlock, 0, s>>>(v);
     }
-    launched += 3;
+    launched += 6;
   }
   {
     for (const auto& r : rs) {
@@ -3117,21 +3176,18 @@ int launch_class_map(const RunView& v, cudaStream_t s) {
   Timed t("class_map", s);
   const uint64_t threads = (v.m + kInsertR - 1) / kInsertR;
   if (v.o_regions) {
-    if (cudaMemsetAsync(v.o_hist, 0, (uint64_t)v.rounds * v.o_regions * 4, s) != cudaSuccess ||
-        cudaMemsetAsync(v.o_tcount, 0, (uint64_t)v.rounds * v.o_tiles * 4, s) != cudaSuccess)
-      return -1;
-    if (v.k <= 31) class_map_kernel<1, true><<<grid_for(class_map_kernel<1, true>, kBlock, threads), kBlock, 0, s>>>(v);
-    else class_map_kernel<2, true><<<grid_for(class_map_kernel<2, true>, kBlock, threads), kBlock, 0, s>>>(v);
+    const unsigned grid = v.k <= 31 ? grid_for(class_map_ord_kernel<1>, kBlock, v.o_tiles * kBlock)
+                                    : grid_for(class_map_ord_kernel<2>, kBlock, v.o_tiles * kBlock);
+    if (v.k <= 31) class_map_ord_kernel<1><<<grid, kBlock, 0, s>>>(v);
+    else class_map_ord_kernel<2><<<grid, kBlock, 0, s>>>(v);
     // every tile's first member number, per round
     const uint64_t chunks = (v.o_tiles + kOrdScanTiles - 1) / kOrdScanTiles;
     ord_tile_sum_kernel<<<(unsigned)(chunks * v.rounds), kBlock, 0, s>>>(v, chunks);
     ord_tile_scan_kernel<<<(unsigned)(chunks * v.rounds), kBlock, 0, s>>>(v, chunks);
     return done(3);
-  } else if (v.k <= 31) {
-    class_map_kernel<1, false><<<grid_for(class_map_kernel<1, false>, kBlock, threads), kBlock, 0, s>>>(v);
-  } else {
-    class_map_kernel<2, false><<<grid_for(class_map_kernel<2, false>, kBlock, threads), kBlock, 0, s>>>(v);
   }
+  if (v.k <= 31) class_map_kernel<1><<<grid_for(class_map_kernel<1>, kBlock, threads), kBlock, 0, s>>>(v);
+  else class_map_kernel<2><<<grid_for(class_map_kernel<2>, kBlock, threads), kBlock, 0, s>>>(v);
   return done(1);
 }
 
@@ -3187,7 +3243,7 @@ int launch_partition_count_wide(const RunView& v, cudaStream_t s) {
 int launch_class_map_wide(const RunView& v, cudaStream_t s) {
   Timed t("class_map", s);
   const uint64_t threads = (v.m + kInsertR - 1) / kInsertR;
-  class_map_kernel<4, false><<<grid_for(class_map_kernel<4, false>, kBlock, threads), kBlock, 0, s>>>(v);
+  class_map_kernel<4><<<grid_for(class_map_kernel<4>, kBlock, threads), kBlock, 0, s>>>(v);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 #endif  // TWOPACO_WIDE_ONLY
