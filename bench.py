@@ -216,10 +216,19 @@ def max_over_ranks(x: float, world: int) -> float:
 # (amount, kind) where kind names the roofline denominator: "rand_or" / "rand_read"
 # are random 64-bit atomic ORs / 8-byte loads into the structure the kernel hits
 # (one per unit), "hbm" streaming bytes.
-def kernel_work(name, st, m, n_seqs, table_bytes):
+def kernel_work(name, st, m, n_seqs, table_bytes, rounds=1):
     pos = st["positions"]
     cand = st["pass1_marks"]
     junc = st["pass2_marks"]
+    # the region-ordered first pass: every round reads the class and region planes
+    if name == "ord_scatter":  # planes + the members' k-mers; an 8 B record and a 2 B rank per member
+        return rounds * (2 * m + m / 4) + 10 * pos, "hbm"
+    if name == "ord_or":
+        return pos, "l2_or"         # one OR per record into an L2-resident filter region
+    if name == "ord_probe":
+        return pos, "l2_read"       # one filter word load per record from an L2-resident region
+    if name == "ord_gather":  # planes + ranks + decision bits; C_temp and the list written
+        return rounds * (2 * m + m / 8) + 2 * pos + pos / 8 + 8 * cand, "hbm"
     if name == "pass1_insert":
         return pos, "rand_or"       # one random filter word OR per position
     if name == "pass1_probe":
@@ -322,17 +331,29 @@ def l2_or_hbm_peaks(build, filter_bytes):
          "buffer_bytes": buf}
     r["or"] = max(r["or_mix"], r["or_lcg"])
     r["read"] = max(r["read_mix"], r["read_lcg"])
+    # and on one filter region of the region-ordered first pass (32 MiB, in L2)
+    reg = min(int(filter_bytes), 32 << 20)
+    r["l2_or"] = max(peaks.peaks_l2_random_rate(1, reg, 64, 5), peaks.peaks_l2_random_rate(4, reg, 1024, 5))
+    r["l2_read"] = max(peaks.peaks_l2_random_rate(2, reg, 64, 5), peaks.peaks_l2_random_rate(5, reg, 1024, 5))
+    r["l2_bytes"] = reg
     return r
 
 
-def roofline(prof, st, m, n, table_bytes, peaks, hbm_peak, peaks_json, workload, in_l2, steps):
+def roofline(prof, st, m, n, table_bytes, peaks, hbm_peak, peaks_json, workload, in_l2, steps, rounds=1):
     """The roofline object of the dominant modelled kernel; prof sums `steps` steps."""
-    modelled = [kv for kv in prof.items() if kernel_work(kv[0], st, m, n, table_bytes)[0] is not None]
+    modelled = [kv for kv in prof.items() if kernel_work(kv[0], st, m, n, table_bytes, rounds)[0] is not None]
     name, rec = max(modelled or prof.items(), key=lambda kv: kv[1]["ms"])
     ms = rec["ms"] / rec["launches"]
-    amount, kind = kernel_work(name, st, m, n, table_bytes)
+    amount, kind = kernel_work(name, st, m, n, table_bytes, rounds)
     amount = (amount or 0.0) * steps / rec["launches"]  # a step's work shared over its launches
-    if kind in (None, "hbm"):
+    if kind in ("l2_or", "l2_read"):
+        pk = peaks[kind] / 1e9
+        achieved = amount / (ms * 1e-3) / 1e9
+        roof = {"bound": "l2", "achieved": achieved, "peak": pk, "unit": "Gaccess/s", "frac": achieved / pk,
+                "peak_source": "measured in this run: random " + ("8-byte loads" if kind == "l2_read" else
+                               "64-bit atomic ORs") + f" over a {peaks['l2_bytes'] >> 20} MiB buffer (one filter "
+                               "region, in L2), all SMs, the better of two address streams, best of 5 (of measured)"}
+    elif kind in (None, "hbm"):
         achieved = amount / (ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak,
@@ -453,8 +474,8 @@ def device_leg(T, build, name, genome_len, rounds, args, world, rank, local, dis
                     | {"junctions": junctions},
            "kernels": kernels_summary(prof, args.steps),
            "roofline": roofline(prof, st, m, n, table_bytes, peaks, hbm_peak, peaks_json, name, in_l2,
-                                args.steps),
-           "random_access_peaks_g_per_s": {k: (v / 1e9 if k != "buffer_bytes" else v)
+                                args.steps, rounds),
+           "random_access_peaks_g_per_s": {k: (v / 1e9 if k not in ("buffer_bytes", "l2_bytes") else v)
                                            for k, v in peaks.items()}}
     out["e2e"] = e2e_leg(T, run, d_bases, off, seqs, name, opts, rounds, args, world, rank, dev,
                          junctions) if args.e2e_steps > 0 else None

@@ -305,6 +305,10 @@ RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_
   int sample_log2 = 0;
   while (sample_log2 < 8 && (m >> (28 + sample_log2 + 1)) > 0) ++sample_log2;
   v.part_sample = (1u << sample_log2) - 1u;
+  // from 2^33 bases the pre-pass also walks only every fourth chunk of 65536
+  // positions: the walk, not the counting, is its cost, and the cut needs
+  // the bins' proportions only
+  v.part_chunks = m >= (1ull << 33) ? 3u : 0u;
   v.hdr = reinterpret_cast<DevHeader*>(base + L.header);
   v.packed = reinterpret_cast<uint32_t*>(base + L.packed);
   v.packed_words = L.packed_words;

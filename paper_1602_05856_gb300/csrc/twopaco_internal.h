@@ -82,6 +82,8 @@ struct RunView {
   uint32_t qmask;           // partition_bins - 1
   uint32_t part_sample;     // the partition pre-pass counts the k-mers whose H has bits
                             // 16 .. 16 + log2(part_sample + 1) - 1 all zero (0: every k-mer)
+  uint32_t part_chunks;     // ... and walks the chunks of 65536 positions whose index has these
+                            // bits zero (0: every chunk)
   DevHeader* hdr;
   uint32_t* packed;         // 2-bit packed input, ceil(m/16) + pad words
   uint64_t packed_words;    // words written by the pack kernel (incl. pad)

@@ -2460,6 +2460,7 @@ template <int KW, int HB>
 __global__ void __launch_bounds__(kBlock) partition_count_kernel(RunView v) {
   const uint64_t stride = (uint64_t)gridDim.x * kBlock * kR;
   for (uint64_t p0 = ((uint64_t)blockIdx.x * kBlock + threadIdx.x) * kR; p0 < v.m; p0 += stride) {
+    if ((uint32_t)(p0 >> 16) & v.part_chunks) continue;  // a sample of the 64K-position chunks
     walk<KW, kR>(v, p0, [&](int, uint64_t, bool valid, const auto& oc) {
       if (!valid || ((uint32_t)(oc.H >> 16) & v.part_sample)) return;
       const uint64_t G = second_hash(oc.H);

@@ -79,6 +79,22 @@ def test_kernel_work_model():
     assert bench.kernel_work("table_clear", st, m, n, tb) == (tb, "hbm")
     assert bench.kernel_work("emit", st, m, n, tb) == (m / 8 + 8 * 50, "hbm")
     assert bench.kernel_work("table_setup", st, m, n, tb) == (None, None)
+    # the region-ordered first pass, 4 rounds: records and ranks per member, planes per round
+    assert bench.kernel_work("ord_scatter", st, m, n, tb, 4) == (4 * (2 * m + m / 4) + 10 * 1000, "hbm")
+    assert bench.kernel_work("ord_or", st, m, n, tb, 4) == (1000, "l2_or")
+    assert bench.kernel_work("ord_probe", st, m, n, tb, 4) == (1000, "l2_read")
+    assert bench.kernel_work("ord_gather", st, m, n, tb, 4) == \
+        (4 * (2 * m + m / 8) + 2 * 1000 + 1000 / 8 + 8 * 80, "hbm")
+
+
+def test_roofline_of_an_ordered_kernel_takes_the_l2_peak():
+    st = {"positions": 10**9, "pass1_marks": 80, "pass2_marks": 50}
+    prof = {"ord_or": {"launches": 4, "ms": 8.0}, "ord_probe": {"launches": 4, "ms": 4.0}}
+    peaks = {"or": 25e9, "read": 40e9, "buffer_bytes": 1 << 33, "l2_or": 200e9, "l2_read": 300e9,
+             "l2_bytes": 32 << 20}
+    r = bench.roofline(prof, st, 1024, 3, 1 << 20, peaks, 6000.0, {}, "wl", False, 1, 4)
+    assert r["kernel"] == "ord_or" and r["bound"] == "l2" and r["unit"] == "Gaccess/s"
+    assert abs(r["achieved"] - 125.0) < 1e-6 and abs(r["frac"] - 125.0 / 200.0) < 1e-9
 
 
 def test_roofline_takes_the_dominant_modelled_kernel_per_launch():
