@@ -227,6 +227,8 @@ def kernel_work(name, st, m, n_seqs, table_bytes, rounds=1):
         return pos, "l2_or"         # one OR per record into an L2-resident filter region
     if name == "ord_probe":
         return pos, "l2_read"       # one filter word load per record from an L2-resident region
+    if name == "ord_classify":
+        return cand, "l2_read"      # one table lookup per candidate record in an L2-resident region
     if name == "ord_gather":  # planes + ranks + decision bits; C_temp and the list written
         return rounds * (2 * m + m / 8) + 2 * pos + pos / 8 + 8 * cand, "hbm"
     if name == "pass1_insert":

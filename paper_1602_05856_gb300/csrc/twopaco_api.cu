@@ -77,6 +77,8 @@ struct Layout {
   uint32_t n_regions, n_sub;
   int lg_region_words;
   uint32_t o_regions;  // region-ordered first pass (0: off)
+  int o_fused;         // ... with pass 2 on its records
+  uint32_t o_tcap;     // fused: table slots per region
   int o_lg_region_words;
   uint64_t o_rec_cap, o_tiles;
   uint64_t rplane, othist, owcount, ocsum, ocpre, obtot, ostart, ofill, orecs, odec, ometa, otcount, otbase, otsum,
@@ -158,6 +160,13 @@ Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int roun
       // records do not fit takes the direct kernels
       L.o_rec_cap = per_round + per_round / 4 + 32ull * R + 4096;
       L.o_tiles = (m + kOrdTile - 1) / kOrdTile;
+      // pass 2 on the records too (one-word table slots, k <= 27): the table
+      // reserve split into one part per region, at least 1024 slots each
+      const uint64_t tcap = L.table_slots / R;
+      if (k <= 27 && !o.partial && tcap >= 1024 && tcap < (1ull << 32)) {
+        L.o_fused = 1;
+        L.o_tcap = (uint32_t)tcap;
+      }
     }
   }
   L.cands = at;
@@ -249,7 +258,7 @@ Layout layout(uint64_t m, uint64_t n_seqs, int k, uint64_t filter_bits, int roun
     L.cands = at;
     at += align_up(std::max<uint64_t>(L.o_rec_cap * 8, L.cand_cap * cand_record_bytes(k)));
     L.odec = at;
-    at += align_up((L.o_rec_cap + 31) / 32 * 4);
+    at += align_up((L.o_rec_cap + 31) / 32 * 4 * (L.o_fused ? 2 : 1));
     L.ometa = at;
     at += align_up(L.o_tiles * R * 4);
     L.otcount = at;
@@ -372,6 +381,8 @@ RunView make_view(const uint8_t* d_bases, const uint64_t* d_offsets, uint64_t n_
     v.o_tbase = reinterpret_cast<unsigned long long*>(base + L.otbase);
     v.o_tsum = reinterpret_cast<unsigned long long*>(base + L.otsum);
     v.o_perm = reinterpret_cast<uint16_t*>(base + L.operm);
+    v.o_fused = L.o_fused;
+    v.o_tcap = L.o_tcap;
     // large rounds count distinct candidates on an eighth of the k-mers
     v.lc_sample_log2 = L.o_rec_cap >= (1ull << 26) ? 3 : 0;
   }

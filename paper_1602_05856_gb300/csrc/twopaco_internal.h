@@ -57,9 +57,8 @@ struct DevHeader {
   unsigned long long input_digest;  // written by launch_digest
   unsigned int out_overflow;        // the output positions did not fit (the offsets are exact)
   unsigned int ord_ok;              // region-ordered first pass: this round's records fit
-  unsigned int ord_ticket[2];       // region-ordered first pass: apply and probe work items
+  unsigned int ord_ticket[3];       // region-ordered first pass: apply, probe and classify work items
   unsigned int ord_rounds;          // rounds the region-ordered kernels took
-  unsigned int pad2;
 };
 
 // Device view of one run: every buffer lives inside the workspace except the
@@ -135,13 +134,16 @@ struct RunView {
   uint32_t* o_fill;         // records claimed per bucket, one counter per 128 bytes
   uint64_t* o_recs;         // o_rec_cap records
   uint64_t o_rec_cap;
-  uint32_t* o_dec;          // one decision bit per record slot
+  uint32_t* o_dec;          // one decision bit per record slot; fused: word pairs (candidates,
+                            // junctions) per 32 slots
   uint32_t* o_meta;         // per tile and bucket: where the tile's records start in the bucket
   uint64_t o_tiles;         // tiles of kOrdTile positions: ceil(m / kOrdTile)
   uint32_t* o_tcount;       // positions of every class in every tile (rounds x o_tiles)
   unsigned long long* o_tbase;  // members of the round in the tiles before (rounds x o_tiles)
   unsigned long long* o_tsum;   // members of the round per scan chunk of tiles
   uint16_t* o_perm;         // per member of the round: its rank within its tile's room
+  int o_fused;              // k <= 27, not partial: pass 2 runs on the records (fused records)
+  uint32_t o_tcap;          // fused: table slots per bucket (region), the table is o_regions x o_tcap slots
   int use_desc;             // the insert leaves descriptors and the probe reads them
   uint64_t cand_cap;        // records the list can hold
   uint32_t* seg_count;      // candidates per list segment (one segment per probe warp)

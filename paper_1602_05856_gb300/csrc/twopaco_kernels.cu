@@ -368,6 +368,30 @@ struct OccT {
   bool rc;         // the string reads the reverse complement of key here
 };
 
+// The filter items and pass-2 bits of one occurrence: its (predecessor,
+// successor) pair read in the orientation of the normalized form (both
+// orientations of a palindrome), or the sentinel item and bit.
+__device__ __forceinline__ void occ_bits(uint32_t pred, uint32_t succ, bool use_f, bool use_r, bool sentinel,
+                                         uint32_t* items_out, uint32_t* tbits_out) {
+  if (sentinel) {
+    *items_out = 1u << 16;
+    *tbits_out = 1u << 8;
+    return;
+  }
+  uint32_t items = 0, tb = 0;
+  if (use_f) {
+    items |= 1u << (4 * pred + succ);
+    tb |= (1u << pred) | (16u << succ);
+  }
+  if (use_r) {
+    const uint32_t a = 3u - succ, c = 3u - pred;  // predecessor / successor on the other strand
+    items |= 1u << (4 * a + c);
+    tb |= (1u << a) | (16u << c);
+  }
+  *items_out = items;
+  *tbits_out = tb;
+}
+
 template <int KW>
 __device__ __forceinline__ void make_occ(const RunView& v, const KeyT<KW>& f, const KeyT<KW>& r,
                                          uint32_t pred, uint32_t succ, bool sentinel, OccT<KW>* oc) {
@@ -377,23 +401,7 @@ __device__ __forceinline__ void make_occ(const RunView& v, const KeyT<KW>& f, co
   oc->H = key_hash<KW>(oc->key);
   oc->sentinel = sentinel;
   oc->rc = !use_f;
-  if (sentinel) {
-    oc->items = 1u << 16;
-    oc->tbits = 1u << 8;
-  } else {
-    uint32_t items = 0, tb = 0;
-    if (use_f) {
-      items |= 1u << (4 * pred + succ);
-      tb |= (1u << pred) | (16u << succ);
-    }
-    if (use_r) {
-      const uint32_t a = 3u - succ, c = 3u - pred;  // predecessor / successor on the other strand
-      items |= 1u << (4 * a + c);
-      tb |= (1u << a) | (16u << c);
-    }
-    oc->items = items;
-    oc->tbits = tb;
-  }
+  occ_bits(pred, succ, use_f, use_r, sentinel, &oc->items, &oc->tbits);
 }
 
 // The occurrence at global position g, read from scratch; false if no k-mer
@@ -1698,6 +1706,76 @@ constexpr int kOrdWarpWindows = kOrdTileWindows / (kBlock / 32);  // windows per
 constexpr uint32_t kOrdPiece = 4096;  // records per apply or probe work item (a multiple of 32)
 constexpr unsigned long long kOrdSentinel = 1ull << 62;
 
+// Fused records (k <= 27, o_fused): the round's pass 2 runs on the same
+// records. A record then holds the occurrence itself -- bits 7-60 the
+// normalized k-mer, 6 the sentinel flag, 5 and 4 whether the string reads the
+// k-mer's reverse complement and the k-mer itself there (both for a
+// palindrome), 2-3 and 0-1 the predecessor and successor bases -- and the
+// kernels that apply it recompute H, G, the filter word and the items.
+__device__ __forceinline__ unsigned long long fused_record(const RunView& v, uint64_t g, bool sentinel) {
+  const Key f = load_kmer<1>(v.packed, g, v.k);
+  const Key r = v.both ? revcomp<1>(f, v.k) : f;
+  const uint32_t pred = sentinel ? 0u : base_at(v.packed, g - 1);
+  const uint32_t succ = sentinel ? 0u : base_at(v.packed, g + v.k);
+  const bool use_f = !v.both || !key_less(r, f);
+  const bool use_r = v.both && !key_less(f, r);
+  const uint64_t key = use_f ? f.lo : r.lo;
+  return (key << 7) | ((uint64_t)sentinel << 6) | ((uint64_t)use_r << 5) | ((uint64_t)use_f << 4) |
+         ((uint64_t)pred << 2) | succ;
+}
+
+struct FusedOcc {
+  uint64_t key, H, G;
+  uint32_t items, tbits;
+  bool sentinel;
+};
+
+__device__ __forceinline__ FusedOcc fused_occ(unsigned long long rec) {
+  FusedOcc o;
+  o.key = rec >> 7;
+  o.sentinel = (rec >> 6) & 1u;
+  occ_bits((uint32_t)(rec >> 2) & 3u, (uint32_t)rec & 3u, (rec >> 4) & 1u, (rec >> 5) & 1u, o.sentinel, &o.items,
+           &o.tbits);
+  o.H = mix64(o.key);  // key_hash of a one-word k-mer
+  o.G = second_hash(o.H);
+  return o;
+}
+
+// The fused pass-2 table: bucket b owns the o_tcap one-word slots (key << 9 |
+// mask) from b * o_tcap, so that its inserts and lookups stay in L2 beside
+// the filter region; a k-mer starts at bits 16-47 of H scaled to o_tcap
+// (Lemire's multiply-high) and probes linearly within the region.
+__device__ __forceinline__ bool fused_table_insert(const RunView& v, uint32_t b, uint64_t key, uint64_t H,
+                                                   uint32_t tbits) {
+  const uint32_t cap = v.o_tcap;
+  unsigned long long* T = static_cast<unsigned long long*>(v.table) + (uint64_t)b * cap;
+  uint32_t i = __umulhi((uint32_t)(H >> 16), cap);
+  for (uint32_t probe = 0; probe < cap; ++probe, i = i + 1 == cap ? 0u : i + 1) {
+    unsigned long long cur = __ldcg(T + i);
+    if (cur == kEmpty) {
+      cur = atomicCAS(T + i, kEmpty, (key << kMaskBits) | tbits);
+      if (cur == kEmpty) return true;
+    }
+    if ((cur >> kMaskBits) != key) continue;
+    if ((cur & tbits) != tbits) atomicOr(T + i, (unsigned long long)tbits);
+    return true;
+  }
+  return false;
+}
+
+// Mask of key in the fused table, or -1 if absent.
+__device__ __forceinline__ int fused_table_find(const RunView& v, uint32_t b, uint64_t key, uint64_t H) {
+  const uint32_t cap = v.o_tcap;
+  const unsigned long long* T = static_cast<const unsigned long long*>(v.table) + (uint64_t)b * cap;
+  uint32_t i = __umulhi((uint32_t)(H >> 16), cap);
+  for (uint32_t probe = 0; probe < cap; ++probe, i = i + 1 == cap ? 0u : i + 1) {
+    const unsigned long long cur = __ldcg(T + i);
+    if (cur == kEmpty) return -1;
+    if ((cur >> kMaskBits) == key) return (int)(cur & ((1u << kMaskBits) - 1u));
+  }
+  return -1;
+}
+
 // A lane's 16 positions of the window at wbase: their class and region bytes.
 __device__ __forceinline__ void ord_lane_bytes(const RunView& v, uint64_t wbase, uint4* cls, uint4* reg) {
   const uint64_t p0 = wbase + 16 * (uint64_t)(threadIdx.x & 31);
@@ -1899,6 +1977,7 @@ __global__ void __launch_bounds__(kBlock) ord_setup_kernel(RunView v, int round)
     v.hdr->ord_rounds += v.hdr->ord_ok;
     v.hdr->ord_ticket[0] = 0;
     v.hdr->ord_ticket[1] = 0;
+    v.hdr->ord_ticket[2] = 0;
   }
 }
 
@@ -1909,7 +1988,7 @@ constexpr size_t kOrdStageBytes = (size_t)kOrdStage * 9;  // the records, then t
 
 // Algorithm 1, insert loop, first pass, over this round's class: one record
 // per position into the bucket of its filter region (tiles grid-strided).
-template <int KW, int HB>
+template <int KW, int HB, bool FUSED>
 __global__ void __launch_bounds__(kBlock) ord_scatter_kernel(RunView v, int round) {
   extern __shared__ __align__(16) unsigned char ord_dyn_s[];
   unsigned long long* stage_rec = reinterpret_cast<unsigned long long*>(ord_dyn_s);
@@ -1960,14 +2039,18 @@ __global__ void __launch_bounds__(kBlock) ord_scatter_kernel(RunView v, int roun
         const uint32_t rank = atomicAdd(&cur_s[b], 1u);
         v.o_perm[mi + j] = (uint16_t)rank;
         const bool sentinel = (e >> 9) & 1u;
-        OccT<KW> oc;
-        read_listed<KW>(v, wbase + (e & 511u), sentinel, &oc);
-        const uint64_t G = second_hash(oc.H);
-        const uint32_t j1 = __ffs(oc.items) - 1, j2 = 31 - __clz(oc.items);
-        const uint64_t word = filter_index(v, oc.H, G);
-        const unsigned long long rec = (word & local_mask) | (((G >> 32) & 0x3FFFFFFFull) << 22) |
-                                       ((uint64_t)j1 << 52) | ((uint64_t)j2 << 57) |
-                                       (sentinel ? kOrdSentinel : 0ull);
+        unsigned long long rec;
+        if constexpr (FUSED) {
+          rec = fused_record(v, wbase + (e & 511u), sentinel);
+        } else {
+          OccT<KW> oc;
+          read_listed<KW>(v, wbase + (e & 511u), sentinel, &oc);
+          const uint64_t G = second_hash(oc.H);
+          const uint32_t j1 = __ffs(oc.items) - 1, j2 = 31 - __clz(oc.items);
+          const uint64_t word = filter_index(v, oc.H, G);
+          rec = (word & local_mask) | (((G >> 32) & 0x3FFFFFFFull) << 22) | ((uint64_t)j1 << 52) |
+                ((uint64_t)j2 << 57) | (sentinel ? kOrdSentinel : 0ull);
+        }
         if (staged) {
           stage_rec[off_s[b] + rank] = rec;
           stage_b[off_s[b] + rank] = (uint8_t)b;
@@ -2030,7 +2113,7 @@ __device__ __forceinline__ uint32_t ord_item_bucket(const uint32_t* first_s, uin
 
 // The ORs of the round's records, bucket by bucket (four records in flight
 // per thread).
-template <int HB>
+template <int HB, bool FUSED>
 __global__ void __launch_bounds__(kBlock) ord_or_kernel(RunView v) {
   __shared__ uint32_t first_s[kOrdMaxRegions + 1];
   __shared__ uint32_t item_s;
@@ -2056,12 +2139,21 @@ __global__ void __launch_bounds__(kBlock) ord_or_kernel(RunView v) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (r[u] == ~0ull) continue;
-        const uint64_t G = ((r[u] >> 22) & 0x3FFFFFFFull) << 32;  // the bits bit_base reads for u < 6
-        const ItemPattern pat = item_pattern<HB>(G, v.hashes);
-        const uint32_t j1 = (uint32_t)(r[u] >> 52) & 31u, j2 = (uint32_t)(r[u] >> 57) & 31u;
-        uint64_t m = item_bits(pat, j1);
-        if (j2 != j1) m |= item_bits(pat, j2);
-        atomicOr(region + (r[u] & 0x3FFFFFull), (unsigned long long)m);
+        if constexpr (FUSED) {
+          const FusedOcc o = fused_occ(r[u]);
+          const ItemPattern pat = item_pattern<HB>(o.G, v.hashes);
+          const uint32_t j1 = __ffs(o.items) - 1, j2 = 31 - __clz(o.items);
+          uint64_t m = item_bits(pat, j1);
+          if (j2 != j1) m |= item_bits(pat, j2);
+          atomicOr(v.filter + filter_index(v, o.H, o.G), (unsigned long long)m);
+        } else {
+          const uint64_t G = ((r[u] >> 22) & 0x3FFFFFFFull) << 32;  // the bits bit_base reads for u < 6
+          const ItemPattern pat = item_pattern<HB>(G, v.hashes);
+          const uint32_t j1 = (uint32_t)(r[u] >> 52) & 31u, j2 = (uint32_t)(r[u] >> 57) & 31u;
+          uint64_t m = item_bits(pat, j1);
+          if (j2 != j1) m |= item_bits(pat, j2);
+          atomicOr(region + (r[u] & 0x3FFFFFull), (unsigned long long)m);
+        }
       }
     }
   }
@@ -2072,7 +2164,7 @@ __global__ void __launch_bounds__(kBlock) ord_or_kernel(RunView v) {
 // filter word holds a sentinel item or two distinct items) goes to its slot's
 // bit; the linear-counting bit of every candidate is set from the k-mer's
 // filter word index and bit bases.
-template <int HB>
+template <int HB, bool FUSED>
 __global__ void __launch_bounds__(kBlock) ord_probe_kernel(RunView v) {
   __shared__ uint32_t first_s[kOrdMaxRegions + 1];
   __shared__ uint32_t item_s;
@@ -2096,7 +2188,17 @@ __global__ void __launch_bounds__(kBlock) ord_probe_kernel(RunView v) {
     for (uint64_t w0 = i0 + 32 * wid; w0 < i1; w0 += kBlock) {
       const uint64_t i = w0 + lane;
       bool keep = false;
-      if (i < i1) {
+      if (FUSED && i < i1) {  // the decision, and the candidate's edges into the region's table
+        const FusedOcc o = fused_occ(__ldcs(recs + i));
+        if (o.sentinel) {
+          keep = true;
+        } else {
+          const uint64_t word = __ldcg(v.filter + filter_index(v, o.H, o.G));
+          const uint32_t pres = present_items<HB>(o.G, word, v.hashes);
+          keep = (pres >> 16) || __popc(pres & 0xFFFFu) >= 2;
+        }
+        if (keep && !fused_table_insert(v, b, o.key, o.H, o.tbits)) v.hdr->overflow = 1;
+      } else if (i < i1) {
         const uint64_t r = __ldcs(recs + i);
         const uint64_t word_index = region | (r & 0x3FFFFFull);
         if (r & kOrdSentinel) {
@@ -2117,7 +2219,47 @@ __global__ void __launch_bounds__(kBlock) ord_probe_kernel(RunView v) {
         }
       }
       const uint32_t row = __ballot_sync(0xffffffffu, keep);
-      if (lane == 0) v.o_dec[(start + w0) >> 5] = row;
+      // fused: word pairs, the candidates' bits then the junctions' (ord_classify)
+      if (lane == 0) v.o_dec[((start + w0) >> 5) << (FUSED ? 1 : 0)] = row;
+    }
+  }
+}
+
+// Algorithm 1, probe loop, second pass, on fused records, bucket by bucket:
+// every candidate record (decision bit set) looks its k-mer up in the
+// region's table; its bit in the junction word of o_dec says whether the
+// k-mer is a junction (the table mask holds the sentinel bit or more than
+// one in- or out-base).
+__global__ void __launch_bounds__(kBlock) ord_classify_kernel(RunView v) {
+  __shared__ uint32_t first_s[kOrdMaxRegions + 1];
+  __shared__ uint32_t item_s;
+  if (!ordered_round(v)) return;
+  ord_items(v, first_s);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t R = v.o_regions, total = first_s[R];
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(&v.hdr->ord_ticket[2], 1u);
+    __syncthreads();
+    const uint32_t item = item_s;
+    __syncthreads();
+    if (item >= total) break;
+    const uint32_t b = ord_item_bucket(first_s, R, item);
+    const uint64_t n = __ldcg(v.o_fill + (uint64_t)b * kOrdFillStride);
+    const uint64_t i0 = (uint64_t)(item - first_s[b]) * kOrdPiece, i1 = min(i0 + kOrdPiece, n);
+    const uint64_t start = __ldg(v.o_start + b);  // a multiple of 32, as is i0
+    const uint64_t* recs = v.o_recs + start;
+    for (uint64_t w0 = i0 + 32 * wid; w0 < i1; w0 += kBlock) {
+      const uint64_t i = w0 + lane;
+      const uint32_t cand = __ldcg(v.o_dec + (((start + w0) >> 5) << 1));
+      bool junction = false;
+      if (i < i1 && ((cand >> lane) & 1u)) {
+        const FusedOcc o = fused_occ(__ldcs(recs + i));
+        const int mk = fused_table_find(v, b, o.key, o.H);
+        if (mk < 0) v.hdr->overflow = 1;
+        junction = mk < 0 || is_junction_mask(mk);
+      }
+      const uint32_t row = __ballot_sync(0xffffffffu, junction);
+      if (lane == 0) v.o_dec[(((start + w0) >> 5) << 1) + 1] = row;
     }
   }
 }
@@ -2126,8 +2268,9 @@ __global__ void __launch_bounds__(kBlock) ord_probe_kernel(RunView v) {
 // class takes its decision from its record's slot (its tile's room in its
 // bucket plus its rank, o_perm); C_temp words, the candidate list segment of
 // the warp and the counts are as pass1_probe_cm_kernel writes them. Every
-// lane takes its own 16 positions of a window.
-__global__ void __launch_bounds__(kBlock) ord_gather_kernel(RunView v, int round) {
+// lane takes its own 16 positions of a window (at most 40 registers: six
+// blocks per SM).
+__global__ void __launch_bounds__(kBlock, 6) ord_gather_kernel(RunView v, int round) {
   __shared__ uint32_t room_s[kOrdMaxRegions];
   __shared__ unsigned long long start_s[kOrdMaxRegions];
   __shared__ uint32_t wcnt_s[kBlock / 32];
@@ -2135,7 +2278,7 @@ __global__ void __launch_bounds__(kBlock) ord_gather_kernel(RunView v, int round
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t R = v.o_regions;
   for (uint32_t b = threadIdx.x; b < R; b += kBlock) start_s[b] = v.o_start[b];
-  unsigned long long kept = 0, valid_n = 0;
+  unsigned long long kept = 0, valid_n = 0, junctions = 0;
   const uint32_t warp_id = (blockIdx.x * kBlock + threadIdx.x) >> 5;
   uint64_t* seg = v.cands + (uint64_t)warp_id * v.seg_cap;
   uint32_t* seg32 = reinterpret_cast<uint32_t*>(v.cands) + (uint64_t)warp_id * v.seg_cap;
@@ -2171,26 +2314,40 @@ __global__ void __launch_bounds__(kBlock) ord_gather_kernel(RunView v, int round
         if (lane >= o) inc += y;
       }
       uint64_t at = mi + inc - n;  // number of the lane's first member
-      uint32_t keep = 0;
+      uint32_t keep = 0, jun = 0;
       for (uint32_t a = act; a; a &= a - 1, ++at) {
         const uint32_t i = __ffs(a) - 1, b = uint4_byte(rq, i);
         const uint64_t s = start_s[b] + room_s[b] + __ldg(v.o_perm + at);
-        keep |= ((__ldg(v.o_dec + (s >> 5)) >> (s & 31)) & 1u) << i;
+        if (v.o_fused) {  // the candidate and junction words of the slot, in one load
+          const uint2 d = __ldg(reinterpret_cast<const uint2*>(v.o_dec) + (s >> 5));
+          keep |= ((d.x >> (s & 31)) & 1u) << i;
+          jun |= ((d.y >> (s & 31)) & 1u) << i;
+        } else {
+          keep |= ((__ldg(v.o_dec + (s >> 5)) >> (s & 31)) & 1u) << i;
+        }
       }
       mi += __shfl_sync(0xffffffffu, inc, 31);
-      // C_temp: lanes 2i and 2i + 1 hold the halves of the window's word i
+      // C_temp (and, fused, C_final): lanes 2i and 2i + 1 hold the halves of the window's word i
       const uint32_t hi = __shfl_down_sync(0xffffffffu, keep, 1);
+      const uint32_t jhi = __shfl_down_sync(0xffffffffu, jun, 1);
       if (!(lane & 1)) {
         const uint64_t w = (wbase >> 5) + (lane >> 1);
         const uint32_t word = keep | (hi << 16);
         if (w < v.bitmap_words) {
           v.ctemp[w] = word;
-          if (v.partial) v.cfinal[w] |= word;  // rounds own disjoint positions; one writer per word
+          // rounds own disjoint positions; one writer per word
+          if (v.partial) {
+            v.cfinal[w] |= word;
+          } else if (v.o_fused) {
+            const uint32_t jw = jun | (jhi << 16);
+            if (jw) atomicOr(v.cfinal + w, jw);  // no wait on the word's other rounds' bits
+          }
         }
       }
       const uint32_t kc = __popc(keep);
       kept += kc;
-      if (v.partial) continue;
+      junctions += __popc(jun);
+      if (v.partial || v.o_fused) continue;
       uint32_t kinc = kc;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -2217,6 +2374,7 @@ __global__ void __launch_bounds__(kBlock) ord_gather_kernel(RunView v, int round
   }
   block_add(kept, &v.hdr->pass1_kept);
   block_add(kept, v.partial ? &v.hdr->pass2_kept : &v.hdr->round_kept);
+  if (v.o_fused) block_add(junctions, &v.hdr->pass2_kept);
   if (round == v.count_round) block_add(valid_n, &v.hdr->positions);
 }
 
@@ -2236,6 +2394,18 @@ constexpr unsigned long long kPartRecords = 128, kMaxParts = 4096;
 // Every block counts its share of the bitmap; the last block to finish sizes
 // the table.
 __global__ void __launch_bounds__(kBlock) table_setup_kernel(RunView v) {
+  if (v.o_fused && ordered_round(v)) {  // the round's table was the fused one: nothing left to size or clear
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      const unsigned long long used = (unsigned long long)v.o_tcap * v.o_regions;
+      v.hdr->table_slots = 0;
+      if (used > v.hdr->table_max) v.hdr->table_max = used;
+      v.hdr->cand_overflow = 0;
+      v.hdr->round_kept = 0;
+      v.hdr->lc_set = 0;
+      v.hdr->lc_blocks_done = 0;
+    }
+    return;
+  }
   const uint64_t words = (1ull << v.lc_log2) / 32;
   const uint64_t stride = (uint64_t)gridDim.x * kBlock;
   unsigned long long c = 0;
@@ -2372,6 +2542,7 @@ __device__ __forceinline__ void for_listed_ahead(const RunView& v, bool last_use
 // loop; if the list overflowed, walks C_temp instead.
 template <int KW, int TS>
 __global__ void __launch_bounds__(kBlock) pass2_insert_kernel(RunView v) {
+  if (v.o_fused && ordered_round(v)) return;  // the fused records took this round's pass 2
   const uint64_t cap = *(volatile unsigned long long*)&v.hdr->table_slots;
   if (*(volatile unsigned int*)&v.hdr->round_listed) {
     auto insert_one = [&](uint64_t i, uint64_t g, bool sent, uint32_t) {
@@ -2408,6 +2579,7 @@ __global__ void __launch_bounds__(kBlock) pass2_insert_kernel(RunView v) {
 // k-mer up when no slots were kept).
 template <int KW, int TS>
 __global__ void __launch_bounds__(kBlock) pass2_classify_kernel(RunView v) {
+  if (v.o_fused && ordered_round(v)) return;  // the fused records took this round's pass 2
   const uint64_t cap = *(volatile unsigned long long*)&v.hdr->table_slots;
   unsigned long long found = 0;
   auto mark = [&](uint64_t g, int mk) {
@@ -3024,6 +3196,7 @@ int round_impl(const RunView& v, int round, cudaStream_t s, const Ranges* ranges
   constexpr int HBO = kBktOk ? HB : 1;
   const bool bkt = kBktOk && v.n_regions > 0;
   const bool ord = kBktOk && cm && v.o_regions > 0 && !ranges;
+  const bool fused = ord && v.o_fused;
   if (ord) {
     {
       Timed t("ord_scatter", s);
@@ -3033,7 +3206,9 @@ int round_impl(const RunView& v, int round, cudaStream_t s, const Ranges* ranges
       ord_room_scan_kernel<<<(unsigned)chunks, kBlock, 0, s>>>(v, round);
       ord_setup_kernel<<<1, kBlock, 0, s>>>(v, round);
       const uint64_t tiles = (v.p_end - v.p_begin + kOrdTile - 1) / kOrdTile;
-      auto kern = ord_scatter_kernel<KW, HBO>;
+      auto kern = ord_scatter_kernel<KW, HBO, false>;
+      if constexpr (KW == 1)
+        if (fused) kern = ord_scatter_kernel<KW, HBO, true>;
       if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOrdStageBytes) !=
           cudaSuccess)
         return -1;
@@ -3042,7 +3217,8 @@ int round_impl(const RunView& v, int round, cudaStream_t s, const Ranges* ranges
     }
     {
       Timed t("ord_or", s);
-      ord_or_kernel<HBO><<<grid_for(ord_or_kernel<HBO>, kBlock, ~0ull >> 1), kBlock, 0, s>>>(v);
+      auto kern = fused ? ord_or_kernel<HBO, true> : ord_or_kernel<HBO, false>;
+      kern<<<grid_for(kern, kBlock, ~0ull >> 1), kBlock, 0, s>>>(v);
     }
     launched += 6;
   }
@@ -3101,9 +3277,17 @@ int round_impl(const RunView& v, int round, cudaStream_t s, const Ranges* ranges
     // ones; launched per string there is no list (pass 2 walks C_temp)
     pv.seg_cap = ranges ? 0 : (v.narrow ? 2 * v.cand_cap : v.cand_cap) / pv.n_segments;
     if (ord) {  // the gather's warps own the list segments, as the probe's would
+      if (fused && cudaMemsetAsync(v.table, 0xFF, (uint64_t)v.o_tcap * v.o_regions * 8, s) != cudaSuccess)
+        return -1;  // every fused table slot empty (all ones)
       {
         Timed t("ord_probe", s);
-        ord_probe_kernel<HBO><<<grid_for(ord_probe_kernel<HBO>, kBlock, ~0ull >> 1), kBlock, 0, s>>>(v);
+        auto kern = fused ? ord_probe_kernel<HBO, true> : ord_probe_kernel<HBO, false>;
+        kern<<<grid_for(kern, kBlock, ~0ull >> 1), kBlock, 0, s>>>(v);
+      }
+      if (fused) {
+        Timed t("ord_classify", s);
+        ord_classify_kernel<<<grid_for(ord_classify_kernel, kBlock, ~0ull >> 1), kBlock, 0, s>>>(v);
+        ++launched;
       }
       {
         Timed t("ord_gather", s);

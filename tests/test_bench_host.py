@@ -83,6 +83,7 @@ def test_kernel_work_model():
     assert bench.kernel_work("ord_scatter", st, m, n, tb, 4) == (4 * (2 * m + m / 4) + 10 * 1000, "hbm")
     assert bench.kernel_work("ord_or", st, m, n, tb, 4) == (1000, "l2_or")
     assert bench.kernel_work("ord_probe", st, m, n, tb, 4) == (1000, "l2_read")
+    assert bench.kernel_work("ord_classify", st, m, n, tb, 4) == (80, "l2_read")
     assert bench.kernel_work("ord_gather", st, m, n, tb, 4) == \
         (4 * (2 * m + m / 8) + 2 * 1000 + 1000 / 8 + 8 * 80, "hbm")
 

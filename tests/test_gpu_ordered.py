@@ -4,9 +4,10 @@ Forced on small filters (64 regions of a 2^20-bit filter, 4 of a 256-bit one), e
 round's records go through the buckets: the junctions must equal the oracle's element
 by element, the last round's C_temp must equal the oracle's first pass over that
 round's class bit for bit (the same filter, applied in another order), and the
-counts must equal those of the direct kernels. A round whose records do not fit (a
-homopolymer puts most positions into one class) takes the direct kernels, and the
-other rounds stay ordered.
+counts must equal those of the direct kernels. For k <= 27 (and not the partially
+compacted graph) pass 2 runs on the same records, with one part of the table per
+filter region. A round whose records do not fit (a homopolymer puts most positions
+into one class) takes the direct kernels, and the other rounds stay ordered.
 """
 import functools
 
@@ -141,3 +142,19 @@ def test_ordered_run_repeats_and_replays():
         _eq(run.result(), first)
     assert run.stats()["ordered_rounds"] == 4
     run.release_plan()
+
+
+def test_fused_table_overflow_is_reported_and_recovered():
+    """Pass 2 on the records with a table of 4 regions x 1024 slots: a saturated filter keeps
+    every k-mer, which overflows the regions; the run reports it and the host build grows
+    the table and runs again."""
+    bases, off = _input()
+    opts = T().Options(hashes=2, partition_bins=256, ordered_first_pass=1, table_slots=4096)
+    run = T().DeviceBuild(bases, off, 25, 256, 2, opts)
+    run.run()
+    st = run.stats(check=False)
+    assert st["rc"] == T().EOVERFLOW and st["overflow"] and st["ordered_rounds"] == 2
+    seqs = [bases[int(off[t]):int(off[t + 1])] for t in range(len(off) - 1)]
+    got, st = T().twopaco_build_ex(seqs, 25, 256, 2, opts)  # grows the table and reruns
+    _eq(got, O.junctions((bases, off), 25))
+    assert st["table_slots"] > 4096
