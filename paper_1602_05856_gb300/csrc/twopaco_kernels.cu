@@ -2248,18 +2248,34 @@ __global__ void __launch_bounds__(kBlock) ord_classify_kernel(RunView v) {
     const uint64_t i0 = (uint64_t)(item - first_s[b]) * kOrdPiece, i1 = min(i0 + kOrdPiece, n);
     const uint64_t start = __ldg(v.o_start + b);  // a multiple of 32, as is i0
     const uint64_t* recs = v.o_recs + start;
-    for (uint64_t w0 = i0 + 32 * wid; w0 < i1; w0 += kBlock) {
-      const uint64_t i = w0 + lane;
-      const uint32_t cand = __ldcg(v.o_dec + (((start + w0) >> 5) << 1));
-      bool junction = false;
-      if (i < i1 && ((cand >> lane) & 1u)) {
-        const FusedOcc o = fused_occ(__ldcs(recs + i));
-        const int mk = fused_table_find(v, b, o.key, o.H);
-        if (mk < 0) v.hdr->overflow = 1;
-        junction = mk < 0 || is_junction_mask(mk);
+    // four chunks of 32 records per warp and step: their loads all in flight at once
+    constexpr int U = 4;
+    for (uint64_t w0 = i0 + 32 * wid; w0 < i1; w0 += U * kBlock) {
+      uint32_t cand[U];
+      unsigned long long rec[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint64_t c = w0 + (uint64_t)u * kBlock;
+        cand[u] = c < i1 ? __ldcg(v.o_dec + (((start + c) >> 5) << 1)) : 0u;
       }
-      const uint32_t row = __ballot_sync(0xffffffffu, junction);
-      if (lane == 0) v.o_dec[(((start + w0) >> 5) << 1) + 1] = row;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint64_t i = w0 + (uint64_t)u * kBlock + lane;
+        rec[u] = (i < i1 && ((cand[u] >> lane) & 1u)) ? __ldcs(recs + i) : ~0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint64_t c = w0 + (uint64_t)u * kBlock;
+        bool junction = false;
+        if (rec[u] != ~0ull) {
+          const FusedOcc o = fused_occ(rec[u]);
+          const int mk = fused_table_find(v, b, o.key, o.H);
+          if (mk < 0) v.hdr->overflow = 1;
+          junction = mk < 0 || is_junction_mask(mk);
+        }
+        const uint32_t row = __ballot_sync(0xffffffffu, junction);
+        if (lane == 0 && c < i1) v.o_dec[(((start + c) >> 5) << 1) + 1] = row;
+      }
     }
   }
 }
