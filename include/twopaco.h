@@ -66,7 +66,11 @@ typedef struct twopaco_options {
   int hashes;              /* bits per filter item, 1..8 (paper default 4) */
   int both_strands;        /* 1: comprehensive graph (default); 0: single strand */
   uint32_t partition_bins; /* q of the rounds heuristic, power of two (65536) */
-  uint64_t table_slots;    /* pass-2 table capacity in slots; 0 = automatic */
+  uint64_t table_slots;    /* pass-2 table reserve in slots (rounded up to a power of two);
+                              0 = automatic. A round sizes its table from an estimate of its
+                              distinct candidates, within the reserve; pass 2 on ordered
+                              records (ordered_first_pass) uses the whole reserve, one part
+                              per filter region */
   uint64_t candidate_records; /* pass-2 candidate list size in 8-byte units; 0 =
                                  automatic (half a round's positions). It
                                  holds twice as many candidates when the input has
@@ -135,12 +139,19 @@ typedef struct twopaco_options {
                               ORs and then the probes are applied bucket by bucket, and the
                               decisions are gathered back in position order. A filter
                               beyond L2 otherwise takes every OR and probe at DRAM's
-                              random-access rate. The workspace holds a region byte per
-                              position and records for a round's positions and a quarter
-                              more (the candidate list shares their room); a round with
-                              more positions takes the direct kernels. Same results. 0
-                              (default): for filters of 1 GiB (2^33 bits) and more; 1: for
-                              any filter; 2: never. Not with per_string_launches. */
+                              random-access rate. For k <= 27 (and partial 0) pass 2 runs
+                              on the same records: the table reserve (table_slots) is split
+                              into one part per filter region, each candidate's edges are
+                              inserted while its region is in L2, and a lookup per
+                              candidate record decides the junctions -- no candidate list
+                              and no table sizing per round; a part that fills up reports
+                              TWOPACO_EOVERFLOW (twopaco_build and twopaco_build_ctx grow
+                              the reserve and run again). The workspace holds a region byte
+                              per position and records for a round's positions and a
+                              quarter more (the candidate list shares their room); a round
+                              with more positions takes the direct kernels. Same results.
+                              0 (default): for filters of 1 GiB (2^33 bits) and more; 1:
+                              for any filter; 2: never. Not with per_string_launches. */
 } twopaco_options;
 
 /* Counters of one run, in the spirit of Table 4 (marks after each pass). */
