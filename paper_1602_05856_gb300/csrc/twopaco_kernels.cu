@@ -1687,19 +1687,20 @@ __global__ void __launch_bounds__(kBlock) pass1_probe_cm_kernel(RunView v, int r
 // all hit L2 -- and gathers the probe's decisions back in position order.
 //
 // Buckets: the class map counted the positions of every (class, region)
-// pair, so a round's buckets are laid out exactly (each a multiple of 32
-// slots). Tiles: kOrdTile consecutive positions, each warp of the block
+// pair per tile, so a round's buckets are laid out exactly (each a multiple
+// of 32 slots). Tiles: kOrdTile consecutive positions, each warp of the block
 // taking kOrdTile / 8 of them (kOrdTileWindows / 8 windows). A tile's records
-// for a bucket are consecutive in the bucket: the tile claims their room with
-// one atomic per bucket and records where it starts (o_meta). The members of
-// a round are numbered in position order (the class map counted them per
-// tile, and o_tbase holds every tile's first number); o_perm[member] is the
-// member's rank within its tile's room, so that the gather finds the
-// member's decision bit at o_start[bucket] + room + rank.
+// for a bucket are consecutive in the bucket, in tile order: a scan over the
+// tiles' counts gives every tile its room in every bucket (o_meta). The
+// members of a round are numbered in position order (o_tbase holds every
+// tile's first number); o_perm[member] is the member's rank within its
+// tile's room, so that the gather finds the member's decision bit at
+// o_start[bucket] + room + rank.
 //
 // A record: bits 0-21 the word within its region, 22-51 the bits 32-61 of G
 // (the bit bases of up to 6 bits per item), 52-56 and 57-61 the items (two
-// for a palindrome's orientations), bit 62 the sentinel flag.
+// for a palindrome's orientations), bit 62 the sentinel flag. With pass 2 on
+// the records (k <= 27) a record holds the occurrence instead (fused_record).
 // ---------------------------------------------------------------------------
 
 constexpr int kOrdWarpWindows = kOrdTileWindows / (kBlock / 32);  // windows per warp and tile
