@@ -2164,7 +2164,9 @@ __global__ void __launch_bounds__(kBlock) ord_or_kernel(RunView v) {
 // bucket: a record's decision (its k-mer is a candidate: a sentinel, or its
 // filter word holds a sentinel item or two distinct items) goes to its slot's
 // bit; the linear-counting bit of every candidate is set from the k-mer's
-// filter word index and bit bases.
+// filter word index and bit bases. FUSED: instead, every candidate inserts
+// its in/out bases into its region's part of the pass-2 table (Algorithm 1's
+// insert loop, second pass) while the region is in L2.
 template <int HB, bool FUSED>
 __global__ void __launch_bounds__(kBlock) ord_probe_kernel(RunView v) {
   __shared__ uint32_t first_s[kOrdMaxRegions + 1];
@@ -2284,7 +2286,9 @@ __global__ void __launch_bounds__(kBlock) ord_classify_kernel(RunView v) {
 // The probe loop's outputs in position order: every member of the round's
 // class takes its decision from its record's slot (its tile's room in its
 // bucket plus its rank, o_perm); C_temp words, the candidate list segment of
-// the warp and the counts are as pass1_probe_cm_kernel writes them. Every
+// the warp and the counts are as pass1_probe_cm_kernel writes them (with
+// fused records: C_temp words, and the junction bits ORed into C_final
+// instead of a list). Every
 // lane takes its own 16 positions of a window (at most 40 registers: six
 // blocks per SM).
 __global__ void __launch_bounds__(kBlock, 6) ord_gather_kernel(RunView v, int round) {
